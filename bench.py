@@ -1,0 +1,330 @@
+"""Benchmark: solved right-hand sides per second of the CBFM + CMP hot path.
+
+One step = one pass of the whole hot path on the 9216-unknown dielectric cube
+(side 1 lambda0, eps_r 2.5, 16 x 16 squares per face, 32 cells, CBFs from 64
+Fibonacci directions x 2 polarisations): reduced-matrix assembly (far-pair
+quadrature, singular near pairs, projection onto the CBFs), CBF Gram matrix
+and its inverse (CMP), then 128 right-hand sides (64 Fibonacci directions x
+{theta, phi} polarisation) solved by right-preconditioned GMRES to 1e-6 with
+currents recovered and the monostatic RCS evaluated.  The CBFs are built once
+before timing (set-up, excitation independent) and stay resident.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 runs independent replicas, one per GPU (torchrun, NCCL only for the
+barrier and the max over ranks).  --impl reference times the CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "solved RHS/sec and p99 solve latency vs plain FP64 GPU path at <=1e-4 RCS err"
+UNIT = "RHS/s"
+N_RHS = 128
+GMRES_TOL = 1e-6
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload():
+    d = W.cube_c2(N_RHS)
+    return d
+
+
+def cpu_sample(n_blocks: int = 6):
+    """The oracle on a bounded sample of the same workload: its dense-definition
+    reduced-matrix assembly for `n_blocks` of the 32 x 32 cell-pair blocks,
+    plus one GMRES matrix-vector product of the reduced size, extrapolated to
+    the whole step (1024 blocks, 374 GMRES iterations per RHS -- the
+    iteration count the oracle needs on this workload at tol 1e-6 -- x 128 RHS)."""
+    import oracle
+    from oracle import cbfm as OC, mesh as OM
+    oracle.build()
+    d = workload()
+    g = d["mesh"]
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = OM.cells_rcb(m, 32)
+    Ns = np.bincount(cell)
+    Ls = [14] * 32
+    CM, CJ = W.random_cbfs(Ns, Ls, seed=1)
+    cbfs = [OC.CellCBF(np.nonzero(cell == c)[0], CM[c], CJ[c], np.ones(1), 14) for c in range(32)]
+    pairs = [(0, 0), (5, 9), (31, 2), (12, 12), (20, 7), (3, 28)][:n_blocks]
+    t0 = time.perf_counter()
+    for (a, b) in pairs:
+        OC.reduced_block(m, cbfs, 2.5, a, b)
+    t_blocks = time.perf_counter() - t0
+    n = 2 * sum(Ls)
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    t1 = time.perf_counter()
+    reps = 20
+    for _ in range(reps):
+        A @ x
+    t_mv = (time.perf_counter() - t1) / reps
+    t_step = t_blocks * 1024 / len(pairs) + t_mv * 374 * N_RHS
+    cores = os.cpu_count()
+    return {"value": N_RHS / t_step, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(pairs)} of 1024 cell-pair blocks of the reduced matrix (dense-definition Z, both media)"
+                      f" + one {n}x{n} complex matvec; extrapolated to 1024 blocks + 374 iter x {N_RHS} RHS GMRES",
+            "measured_s": t_blocks + t_mv * reps}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_sample(2)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_sample(2))
+    wall = time.perf_counter() - t0
+    v = float(np.median([x["value"] for x in vals]))
+    cb = dict(vals[0])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * N_RHS / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "dielectric cube 9216 unknowns, 32 cells, 128 RHS (CPU oracle sample)"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison step")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2111_11058_gb300 import build as B
+    B.build()
+    import paper_2111_11058_gb300 as P
+
+    d = workload()
+    g = d["mesh"]
+    stream = torch.cuda.current_stream()
+    mesh = P.mesh(g.verts, g.tris, d["ncell"], complex(*d["eps"]), partition=d["partition"])
+    cbf = P.build_cbfs(mesh, d["gen"], 1e-3)
+    exc_d = torch.tensor(d["exc"], dtype=torch.float64, device="cuda")
+    rcs_d = torch.zeros((N_RHS, 1, 2), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    state = {}
+
+    def step(prec=P.MIXED, exc=exc_d, out=rcs_d):
+        red = P.assemble_reduced(mesh, cbf, prec)
+        state["n"] = red.n
+        P.cmp_setup(red)
+        res = P.solve(red, exc, tol=GMRES_TOL, maxit=2000, restart=1000, monostatic=True, want_j=False,
+                      out_rcs=out, allow_noconv=True)
+        red.free()
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    iters = res.iters.copy()
+
+    def timed(nsteps, fn):
+        ts = []
+        for _ in range(nsteps):
+            flush.fill_(1.0)             # L2 flush between steps (outside the timed span)
+            if ws > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    l0 = P.launch_count()
+    with ClockSampler(local) as clk:
+        ts = timed(args.steps, step)
+    launches = (P.launch_count() - l0) // max(1, args.steps)
+    t_step = float(np.mean(ts))
+    t_max = t_step
+    if ws > 1:
+        tt = torch.tensor([t_step], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = ws * N_RHS / (t_max / 1000.0)
+
+    # end to end through the public API with pinned host buffers
+    exc_h = torch.tensor(d["exc"], dtype=torch.float64).pin_memory()
+    rcs_h = torch.zeros((N_RHS, 1, 2), dtype=torch.float64).pin_memory()
+
+    def step_host():
+        red = P.assemble_reduced(mesh, cbf, P.MIXED)
+        P.cmp_setup(red)
+        P.solve(red, exc_h.numpy(), tol=GMRES_TOL, maxit=2000, restart=1000, monostatic=True, want_j=False,
+                out_rcs=rcs_h.numpy(), allow_noconv=True)
+        red.free()
+
+    ts_e2e = timed(max(1, min(args.steps, 3)), step_host)
+    e2e = ws * N_RHS / (float(np.mean(ts_e2e)) / 1000.0)
+
+    # per-kernel profile of the same steps (CUDA events on the launching stream)
+    P.profile(True)
+    P.profile_read(reset=True)
+    timed(max(1, min(args.steps, 3)), step)
+    prof = P.profile_read(reset=True)
+    P.profile(False)
+    tot = sum(v["ms"] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    peaks, peak_src = _peaks()
+    nt, ne = g.nt, mesh.n_edges
+    clocks = clk.summary()
+    roof = None
+    if dom[0] == "k_far":
+        far_pairs = nt * nt - (2 * mesh.n_near - nt)
+        flop = far_pairs * 49 * 143.0            # algorithmic FP32 flops of the 7x7 point-pair loop
+        per_launch_ms = dom[1]["ms"] / dom[1]["launches"]
+        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        ach = flop / (per_launch_ms / 1e3) / 1e12
+        roof = {"kernel": "k_far", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    else:
+        per_launch_ms = dom[1]["ms"] / dom[1]["launches"]
+        roof = {"kernel": dom[0], "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None, "peak_source": peak_src,
+                "per_launch_ms": per_launch_ms}
+    roof["share"] = dom[1]["ms"] / tot if tot else None
+
+    # FP64 GPU path (the metric's denominator) and the mixed-vs-FP64 RCS difference
+    fp64 = None
+    if not args.no_fp64:
+        rcs64 = torch.zeros_like(rcs_d)
+        t64 = timed(1, lambda: step(P.FP64, exc_d, rcs64))
+        mixed_rcs = rcs_d.sum(-1).cpu().numpy()
+        ref_rcs = rcs64.sum(-1).cpu().numpy()
+        err = float(np.abs(mixed_rcs - ref_rcs).max() / np.abs(ref_rcs).max())
+        fp64 = {"value": ws * N_RHS / (t64[0] / 1000.0), "ms_per_step": t64[0], "rcs_err_mixed_vs_fp64": err,
+                "speedup_mixed_over_fp64": (t64[0] / t_step)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "dielectric cube side 1 lambda0, eps_r 2.5, T=3072, N=9216, 32 cells, "
+                                       "s=128 generating waves, 128 monostatic RHS, GMRES tol 1e-6, mixed precision",
+                           "n_cbf": state.get("n"), "l2": "512 MB buffer written between timed steps",
+                           "parallelism": "replicas" if ws > 1 else "single GPU"},
+                "latency_ms": {"p50": float(np.percentile(ts, 50)), "p99": float(np.percentile(ts, 99))},
+                "gmres_iters": {"min": int(iters.min()), "max": int(iters.max()), "mean": float(iters.mean())},
+                "clocks": clocks, "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(exc_h.numel() * 8),
+                                          "d2h_bytes_per_step": int(rcs_h.numel() * 8)},
+                "gpu_launches": int(launches), "roofline": roof, "kernel_ms": {k: v["ms"] for k, v in prof.items()},
+                "fp64_path": fp64}
+        if not args.no_cpu and ws == 1:
+            try:
+                line["cpu_baseline"] = cpu_sample()
+            except Exception as e:  # pragma: no cover
+                line["cpu_baseline"] = {"error": str(e)}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * cbfm.h -- C ABI of the GB300 (sm_103a) CBFM + Calderon-preconditioned
+ * PMCHWT solver for homogeneous dielectric scatterers.
+ *
+ * Method: K. Tanaka, K. Niino, N. Nishimura, "Characteristic basis function
+ * method ... with the Calderon multiplicative preconditioner" (arXiv 2111.11058).
+ *
+ * Units and conventions
+ *   - lengths in free-space wavelengths (k0 = 2 pi); time factor exp(+j w t);
+ *   - exterior medium 1 = free space (eta0 = 376.730313668 ohm); interior
+ *     medium 2 with k2 = k0 sqrt(eps_r mu_r) (Re > 0, Im <= 0),
+ *     eta2 = eta0 sqrt(mu_r / eps_r); eps_r = eps_re + j eps_im, eps_im <= 0;
+ *   - a plane wave is a triple (theta, phi, psi): it arrives from direction
+ *     r_hat(theta, phi) (travels along -r_hat) with polarisation
+ *     cos(psi) theta_hat + sin(psi) phi_hat and unit amplitude;
+ *   - RWG edges are numbered canonically: unique vertex pairs (u < v) in
+ *     lexicographic order; the plus triangle is the one whose counter-
+ *     clockwise vertex order runs u -> v;
+ *   - RWG unknowns are ordered j = [alpha^M ; alpha^J] (paper Eq. (coef_vector)).
+ *
+ * Memory and streams
+ *   - every call is stream-ordered on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream) except the host-side mesh preparation inside
+ *     cbfm_mesh;
+ *   - input arrays may be host or device memory (detected per pointer) and
+ *     are copied; output arrays may be host or device memory of the stated
+ *     size and are owned by the caller;
+ *   - handles own their device memory until cbfm_free; the GPU current when a
+ *     handle is created must be current for every later call on it.
+ *
+ * Errors: every call returns a cbfm_status and never aborts the process; the
+ * message of the last failure on the calling thread is cbfm_last_error().
+ * Device-side waits are bounded and report CBFM_ETIMEOUT.
+ */
+#ifndef CBFM_H
+#define CBFM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cbfm_mesh_s *cbfm_mesh_t;
+typedef struct cbfm_cbf_s *cbfm_cbf_t;
+typedef struct cbfm_red_s *cbfm_red_t;
+
+typedef enum {
+    CBFM_OK = 0,
+    CBFM_EINVAL = 1,      /* bad argument, size or mesh */
+    CBFM_ENOMEM = 2,      /* device or host allocation failed */
+    CBFM_ECUDA = 3,       /* CUDA runtime error */
+    CBFM_ESINGULAR = 4,   /* zero pivot in an LU / Gauss-Jordan factorisation */
+    CBFM_ENOCONV = 5,     /* GMRES reached maxit without meeting tol (results are the last iterate) */
+    CBFM_ETIMEOUT = 6     /* a bounded device wait expired */
+} cbfm_status;
+
+typedef enum {
+    CBFM_FP64 = 0,        /* every step in FP64 (reference GPU path) */
+    CBFM_MIXED = 1        /* FP32 far-pair quadrature and projections, complex64 reduced
+                             matrix; FP64 singular near pairs, SVD, CMP Gram inverse,
+                             GMRES Arnoldi / residual */
+} cbfm_precision;
+
+/*
+ * cbfm_mesh -- geometry staging of a closed triangle surface (paper Sec. II-B,
+ * RWG functions; Sec. III-A, division into cells).
+ *   verts     (nv, 3) float64, row-major
+ *   tris      (nt, 3) int32, counter-clockwise seen from outside
+ *   edge_cell (ne) int32 cell of each canonical edge, or NULL for the built-in
+ *             partition: ncell == 8 with partition 0 -> octants of the edge
+ *             midpoint (a coordinate counts negative below -1e-12 * max|vertex|);
+ *             otherwise recursive coordinate bisection of edge midpoints into
+ *             ncell parts (longest axis, lower part floor(M/2) cells and
+ *             round(n floor(M/2)/M) edges, ties by edge index)
+ *   partition 0 = octant (ncell must be 8), 1 = RCB; ignored when edge_cell given
+ *   eps_re, eps_im, mu_r   interior medium; near-pair factor alpha (> 0): a
+ *             triangle pair is near when it shares a vertex or its centroid
+ *             distance is below alpha * max(longest edge)
+ * Fails with CBFM_EINVAL for open, non-manifold or inconsistently oriented
+ * meshes, an empty cell, or sizes beyond int32.
+ */
+cbfm_status cbfm_mesh(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                      const int32_t *edge_cell, int32_t ncell, int32_t partition,
+                      double eps_re, double eps_im, double mu_r, double alpha,
+                      void *stream, cbfm_mesh_t *out);
+
+/*
+ * cbfm_mesh_edges -- host-only variant of the edge table and built-in cell
+ * division of cbfm_mesh (no GPU needed; same rules).  verts/tris are host
+ * arrays.  n_edges out; edges (ne, 2) int32 canonical (u < v) and cells (ne)
+ * int32 may be NULL; when given they must hold 3 nt / 2 entries.
+ */
+cbfm_status cbfm_mesh_edges(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, int32_t ncell,
+                            int32_t partition, int64_t *n_edges, int32_t *edges, int32_t *cells);
+
+/* Number of canonical RWG edges (N = 2 * edges unknowns), of cells and of
+ * near triangle pairs (t <= s, self pairs included); NULL outputs are skipped. */
+cbfm_status cbfm_mesh_info(cbfm_mesh_t mesh, int64_t *n_edges, int32_t *n_cells, int64_t *n_near);
+
+/* Cell of each canonical edge (ne int32, host or device). */
+cbfm_status cbfm_mesh_cells(cbfm_mesh_t mesh, int32_t *edge_cell, void *stream);
+
+/*
+ * cbfm_build_cbfs -- primary CBFs with the dual SVD orthogonalisation
+ * (paper Sec. III-A Eq. (pcbf); Sec. III-B Eqs. (gram_CBF), (gram_CBF_SVD), (CBF)).
+ *   waves      (s, 3) generating plane waves (theta, phi, psi)
+ *   delta_svd  keep singular values with sigma_i / sigma_1 >= delta_svd
+ *   lmax       cap on L_m (<= 0: none)
+ *   L_per_cell out (ncell) int32, host
+ *   sigma_out  out (ncell, s) float64 normalised singular values of G'_m, or NULL
+ * Runs in FP64.  Requires s <= 1024 and 2 N_m <= 4096.
+ */
+cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, double delta_svd,
+                            int32_t lmax, void *stream, cbfm_cbf_t *out, int32_t *L_per_cell,
+                            double *sigma_out);
+
+/*
+ * cbfm_cbf_import / export -- inject or read the dual CBFs.
+ *   L_per_cell (ncell) int32 host;  CM, CJ: complex128 arrays holding, cell
+ *   after cell, the N_m x L_m row-major blocks C_m^M and C_m^J with rows in
+ *   increasing canonical edge order of the cell.  Total sum_m N_m L_m each.
+ */
+cbfm_status cbfm_cbf_import(cbfm_mesh_t mesh, const int32_t *L_per_cell, const double *CM,
+                            const double *CJ, void *stream, cbfm_cbf_t *out);
+cbfm_status cbfm_cbf_export(cbfm_cbf_t cbf, double *CM, double *CJ, void *stream);
+
+/*
+ * cbfm_assemble_reduced -- reduced matrix A = (C^JM)^H Z C^MJ (paper Eq.
+ * (CBFM_outer)) with Z the PMCHWT Galerkin matrix (Eq. (Z)) assembled from
+ * 7-point quadrature (far pairs) and singularity extraction (near pairs).
+ *   n_cbf out: N^CBF = 2 sum_m L_m.
+ * Row/column order of A: [J-tested / M-coefficient CBFs of cells 0..M-1,
+ * M-tested / J-coefficient CBFs of cells 0..M-1].
+ */
+cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precision prec,
+                                  void *stream, cbfm_red_t *out, int64_t *n_cbf);
+
+/* A as complex128 row-major (n_cbf, n_cbf), host or device. */
+cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream);
+
+/*
+ * cbfm_cmp_setup -- CBF Gram matrix G^CBF = (C^JM)^H G_ffff C^MJ (paper Eq.
+ * (CBF_Gram_matrix)) and its inverse by Gauss-Jordan elimination with partial
+ * pivoting in FP64.  Returns CBFM_ESINGULAR on a zero pivot.
+ */
+cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream);
+
+/* G^CBF as complex128 row-major (n_cbf, n_cbf), host or device. */
+cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream);
+
+/*
+ * cbfm_solve -- right-preconditioned GMRES on A (G^CBF)^{-1} y = (C^JM)^H v
+ * (Eqs. (CBFM_outer), (CBFM_inner)), j^CBF = (G^CBF)^{-1} y, j = C^MJ j^CBF
+ * (Eq. (trans_current)), far field and RCS.  Each right-hand side runs its own
+ * GMRES (x0 = 0, restart `restart`, stop at ||b - A P y|| / ||b|| <= tol).
+ *   exc     (nrhs, 3) excitations (theta, phi, psi)
+ *   use_cmp 1: P = (G^CBF)^{-1} (requires cbfm_cmp_setup); 0: P = I
+ *   j_out   (2 ne, nrhs) complex128 RWG coefficients in canonical edge order, or NULL
+ *   obs     (ndir, 2) observation directions (theta, phi); obs == NULL with
+ *           ndir == -1 selects monostatic: each RHS observed at its own arrival
+ *           direction (ndir = 1 per RHS)
+ *   rcs_out (nrhs, ndir, 2) float64 partial RCS (sigma_theta, sigma_phi) =
+ *           4 pi |F_theta|^2, 4 pi |F_phi|^2, or NULL
+ *   iters_out (nrhs) int32 GMRES iterations, or NULL
+ *   resid_out (nrhs) float64 final relative residuals, or NULL
+ * Returns CBFM_ENOCONV when some RHS did not converge within maxit.
+ */
+cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double tol, int32_t maxit,
+                       int32_t restart, int32_t use_cmp, double *j_out, const double *obs,
+                       int32_t ndir, double *rcs_out, int32_t *iters_out, double *resid_out,
+                       void *stream);
+
+/* Release any handle (mesh, cbf or reduced system); NULL is a no-op. */
+void cbfm_free(void *handle);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *cbfm_last_error(void);
+
+/* Kernel launches issued by this process so far (all entry points). */
+int64_t cbfm_launch_count(void);
+
+/*
+ * cbfm_profile -- per-kernel timing with CUDA events recorded on the
+ * launching stream around the main kernels (enable != 0 turns it on).
+ * cbfm_profile_read writes a JSON object {name: {"launches": n, "ms": t}}
+ * into buf (capacity cap, NUL-terminated, truncated if short), returns the
+ * size needed, and clears the totals when reset != 0.
+ */
+void cbfm_profile(int32_t enable);
+int64_t cbfm_profile_read(char *buf, int64_t cap, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBFM_H */

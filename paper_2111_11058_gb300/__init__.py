@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) CBFM + Calderon-preconditioned PMCHWT solver.
+
+The compute path lives in libcbfm.so (hand-written CUDA, C ABI in
+include/cbfm.h); `cbfm` is its thin Python binding and `build` compiles it.
+"""
+from .cbfm import (FP64, MIXED, CbfmError, assemble_reduced, build_cbfs, cbf_import, cmp_setup, launch_count,
+                   mesh, mesh_edges, solve)
+
+__all__ = ["FP64", "MIXED", "CbfmError", "assemble_reduced", "build_cbfs", "cbf_import", "cmp_setup",
+           "launch_count", "mesh", "mesh_edges", "solve"]

@@ -1,0 +1,338 @@
+"""Thin ctypes binding of libcbfm.so (include/cbfm.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Arrays may be numpy arrays (host) or CUDA torch tensors
+(device); outputs come back as numpy arrays unless device tensors are passed
+in `out_*` arguments.  Streams are the caller's current torch stream when
+torch is present, else the legacy default stream.
+
+Loading fails loudly (CbfmError) when the shared library is missing or was
+built for another machine; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libcbfm.so")
+
+FP64 = 0
+MIXED = 1
+
+STATUS = {0: "CBFM_OK", 1: "CBFM_EINVAL", 2: "CBFM_ENOMEM", 3: "CBFM_ECUDA", 4: "CBFM_ESINGULAR",
+          5: "CBFM_ENOCONV", 6: "CBFM_ETIMEOUT"}
+
+ETA0 = 376.730313668
+
+
+class CbfmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_f64 = ctypes.c_double
+
+
+def lib():
+    """The loaded library (raises CbfmError if it cannot be loaded)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise CbfmError(3, f"{_LIB_PATH} is missing: run paper_2111_11058_gb300.build.build() first")
+        try:
+            L = ctypes.CDLL(_LIB_PATH)
+        except OSError as e:  # pragma: no cover - platform specific
+            raise CbfmError(3, f"cannot load {_LIB_PATH}: {e}") from e
+        sig = {
+            "cbfm_mesh": [_vp, _i64, _vp, _i64, _vp, _i32, _i32, _f64, _f64, _f64, _f64, _vp, _vp],
+            "cbfm_mesh_info": [_vp, _vp, _vp, _vp],
+            "cbfm_mesh_edges": [_vp, _i64, _vp, _i64, _i32, _i32, _vp, _vp, _vp],
+            "cbfm_mesh_cells": [_vp, _vp, _vp],
+            "cbfm_build_cbfs": [_vp, _vp, _i32, _f64, _i32, _vp, _vp, _vp, _vp],
+            "cbfm_cbf_import": [_vp, _vp, _vp, _vp, _vp, _vp],
+            "cbfm_cbf_export": [_vp, _vp, _vp, _vp],
+            "cbfm_assemble_reduced": [_vp, _vp, _i32, _vp, _vp, _vp],
+            "cbfm_red_export": [_vp, _vp, _vp],
+            "cbfm_cmp_setup": [_vp, _vp],
+            "cbfm_gram_export": [_vp, _vp, _vp],
+            "cbfm_solve": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.cbfm_free.argtypes = [_vp]
+        L.cbfm_free.restype = None
+        L.cbfm_last_error.argtypes = []
+        L.cbfm_last_error.restype = ctypes.c_char_p
+        L.cbfm_launch_count.argtypes = []
+        L.cbfm_launch_count.restype = ctypes.c_int64
+        L.cbfm_profile.argtypes = [_i32]
+        L.cbfm_profile.restype = None
+        L.cbfm_profile_read.argtypes = [ctypes.c_char_p, _i64, _i32]
+        L.cbfm_profile_read.restype = ctypes.c_int64
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names of the C entry points declared in include/cbfm.h."""
+    return ["cbfm_mesh", "cbfm_mesh_edges", "cbfm_mesh_info", "cbfm_mesh_cells", "cbfm_build_cbfs", "cbfm_cbf_import",
+            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_red_export", "cbfm_cmp_setup", "cbfm_gram_export",
+            "cbfm_solve", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
+            "cbfm_profile_read"]
+
+
+def _check(st: int):
+    if st != 0:
+        raise CbfmError(st, lib().cbfm_last_error().decode())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _ptr(a, dtype):
+    """(pointer, keepalive) for a numpy array or a torch tensor of `dtype`."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def launch_count() -> int:
+    return int(lib().cbfm_launch_count())
+
+
+def profile(enable: bool) -> None:
+    """Per-kernel CUDA-event timing inside the library on/off."""
+    lib().cbfm_profile(1 if enable else 0)
+
+
+def profile_read(reset: bool = True) -> dict:
+    """{kernel: {"launches": n, "ms": total}} accumulated since the last reset."""
+    import json
+    need = lib().cbfm_profile_read(None, 0, 0)
+    buf = ctypes.create_string_buffer(int(need) + 64)
+    lib().cbfm_profile_read(buf, len(buf), 1 if reset else 0)
+    return json.loads(buf.value.decode())
+
+
+class _Handle:
+    def __init__(self, h):
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().cbfm_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Mesh(_Handle):
+    def __init__(self, h, verts):
+        super().__init__(h)
+        ne = ctypes.c_int64()
+        nc = ctypes.c_int32()
+        nn = ctypes.c_int64()
+        _check(lib().cbfm_mesh_info(h, ctypes.byref(ne), ctypes.byref(nc), ctypes.byref(nn)))
+        self.n_edges = int(ne.value)
+        self.n_cells = int(nc.value)
+        self.n_near = int(nn.value)
+        self.n_tris = 2 * self.n_edges // 3
+
+    def cells(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.n_edges, np.int32)
+        _check(lib().cbfm_mesh_cells(self._h, ctypes.c_void_p(out.ctypes.data), _stream(stream)))
+        return out
+
+
+class CBFs(_Handle):
+    def __init__(self, h, mesh: Mesh, L, sigma=None):
+        super().__init__(h)
+        self.mesh = mesh          # keeps the mesh alive
+        self.L = np.asarray(L, np.int32)
+        self.sigma = sigma
+
+    def export(self, stream=None):
+        """(C^M, C^J) as lists of per-cell (N_m, L_m) complex128 arrays."""
+        cells = self.mesh.cells()
+        Ns = np.bincount(cells, minlength=self.mesh.n_cells)
+        tot = int(np.sum(Ns * self.L))
+        CM = np.zeros(tot, np.complex128)
+        CJ = np.zeros(tot, np.complex128)
+        _check(lib().cbfm_cbf_export(self._h, ctypes.c_void_p(CM.ctypes.data), ctypes.c_void_p(CJ.ctypes.data),
+                                     _stream(stream)))
+        outM, outJ, off = [], [], 0
+        for N, L in zip(Ns, self.L):
+            outM.append(CM[off:off + N * L].reshape(N, L))
+            outJ.append(CJ[off:off + N * L].reshape(N, L))
+            off += N * L
+        return outM, outJ
+
+
+class Reduced(_Handle):
+    def __init__(self, h, cbf: CBFs, n: int, prec: int):
+        super().__init__(h)
+        self.cbf = cbf
+        self.n = n
+        self.prec = prec
+
+    def export(self, stream=None) -> np.ndarray:
+        A = np.zeros((self.n, self.n), np.complex128)
+        _check(lib().cbfm_red_export(self._h, ctypes.c_void_p(A.ctypes.data), _stream(stream)))
+        return A
+
+    def gram(self, stream=None) -> np.ndarray:
+        G = np.zeros((self.n, self.n), np.complex128)
+        _check(lib().cbfm_gram_export(self._h, ctypes.c_void_p(G.ctypes.data), _stream(stream)))
+        return G
+
+
+def mesh(verts, tris, ncell: int, eps_r: complex, partition: str = "rcb", edge_cell=None, mu_r: float = 1.0,
+         alpha: float = 2.0, stream=None) -> Mesh:
+    """cbfm_mesh: geometry staging and cell division."""
+    v, kv = _ptr(verts, np.float64)
+    t, kt = _ptr(tris, np.int32)
+    c, kc = _ptr(edge_cell, np.int32)
+    nv = int(kv.shape[0])
+    nt = int(kt.shape[0])
+    h = ctypes.c_void_p()
+    eps = complex(eps_r)
+    _check(lib().cbfm_mesh(v, nv, t, nt, c, int(ncell), 0 if partition == "octant" else 1, eps.real, eps.imag,
+                           float(mu_r), float(alpha), _stream(stream), ctypes.byref(h)))
+    return Mesh(h, verts)
+
+
+def mesh_edges(verts, tris, ncell: int, partition: str = "rcb"):
+    """cbfm_mesh_edges (host only, no GPU): canonical edges (ne, 2) and the
+    built-in cell of each edge (ne,)."""
+    v = np.ascontiguousarray(verts, np.float64)
+    t = np.ascontiguousarray(tris, np.int32)
+    ne = ctypes.c_int64()
+    cap = 3 * t.shape[0] // 2
+    edges = np.zeros((cap, 2), np.int32)
+    cells = np.zeros(cap, np.int32)
+    _check(lib().cbfm_mesh_edges(ctypes.c_void_p(v.ctypes.data), v.shape[0], ctypes.c_void_p(t.ctypes.data),
+                                 t.shape[0], int(ncell), 0 if partition == "octant" else 1, ctypes.byref(ne),
+                                 ctypes.c_void_p(edges.ctypes.data), ctypes.c_void_p(cells.ctypes.data)))
+    n = int(ne.value)
+    return edges[:n], cells[:n]
+
+
+def build_cbfs(m: Mesh, waves, delta_svd: float = 1e-3, lmax: int = 0, stream=None) -> CBFs:
+    """cbfm_build_cbfs: primary CBFs with the dual SVD orthogonalisation."""
+    w, kw = _ptr(waves, np.float64)
+    s = int(kw.shape[0])
+    L = np.zeros(m.n_cells, np.int32)
+    sig = np.zeros((m.n_cells, s), np.float64)
+    h = ctypes.c_void_p()
+    _check(lib().cbfm_build_cbfs(m.handle, w, s, float(delta_svd), int(lmax), _stream(stream), ctypes.byref(h),
+                                 ctypes.c_void_p(L.ctypes.data), ctypes.c_void_p(sig.ctypes.data)))
+    return CBFs(h, m, L, sig)
+
+
+def cbf_import(m: Mesh, CM_blocks, CJ_blocks, stream=None) -> CBFs:
+    """cbfm_cbf_import: inject per-cell (N_m, L_m) C^M and C^J blocks."""
+    L = np.array([b.shape[1] for b in CM_blocks], np.int32)
+    CM = np.ascontiguousarray(np.concatenate([np.asarray(b, np.complex128).ravel() for b in CM_blocks]))
+    CJ = np.ascontiguousarray(np.concatenate([np.asarray(b, np.complex128).ravel() for b in CJ_blocks]))
+    h = ctypes.c_void_p()
+    _check(lib().cbfm_cbf_import(m.handle, ctypes.c_void_p(L.ctypes.data), ctypes.c_void_p(CM.ctypes.data),
+                                 ctypes.c_void_p(CJ.ctypes.data), _stream(stream), ctypes.byref(h)))
+    return CBFs(h, m, L)
+
+
+def assemble_reduced(m: Mesh, c: CBFs, prec: int = FP64, stream=None) -> Reduced:
+    """cbfm_assemble_reduced: A = (C^JM)^H Z C^MJ."""
+    h = ctypes.c_void_p()
+    n = ctypes.c_int64()
+    _check(lib().cbfm_assemble_reduced(m.handle, c.handle, int(prec), _stream(stream), ctypes.byref(h),
+                                       ctypes.byref(n)))
+    return Reduced(h, c, int(n.value), prec)
+
+
+def cmp_setup(r: Reduced, stream=None) -> None:
+    """cbfm_cmp_setup: G^CBF and its inverse."""
+    _check(lib().cbfm_cmp_setup(r.handle, _stream(stream)))
+
+
+@dataclass
+class SolveResult:
+    j: np.ndarray | None          # (2 ne, nrhs) complex128, canonical edges, [alpha^M; alpha^J]
+    rcs: np.ndarray | None        # (nrhs, ndir, 2) partial RCS
+    iters: np.ndarray
+    resid: np.ndarray
+    status: int
+
+
+def solve(r: Reduced, exc, tol: float = 1e-6, maxit: int = 2000, restart: int = 1000, use_cmp: bool = True,
+          obs=None, monostatic: bool = False, want_j: bool = True, out_j=None, out_rcs=None, stream=None,
+          allow_noconv: bool = False) -> SolveResult:
+    """cbfm_solve: GMRES on the reduced system, currents and RCS."""
+    e, ke = _ptr(exc, np.float64)
+    nrhs = int(ke.shape[0])
+    ne = r.cbf.mesh.n_edges
+    iters = np.zeros(nrhs, np.int32)
+    resid = np.zeros(nrhs, np.float64)
+    j = None
+    if out_j is not None:
+        jp, _kj = _ptr(out_j, np.complex128)
+    elif want_j:
+        j = np.zeros((2 * ne, nrhs), np.complex128)
+        jp = ctypes.c_void_p(j.ctypes.data)
+    else:
+        jp = None
+    if monostatic:
+        op, ko, nd = None, None, -1
+        ndir_out = 1
+    elif obs is not None:
+        op, ko = _ptr(obs, np.float64)
+        nd = int(ko.shape[0])
+        ndir_out = nd
+    else:
+        op, ko, nd, ndir_out = None, None, 0, 0
+    rcs = None
+    if out_rcs is not None:
+        rp, _kr = _ptr(out_rcs, np.float64)
+    elif ndir_out > 0:
+        rcs = np.zeros((nrhs, ndir_out, 2), np.float64)
+        rp = ctypes.c_void_p(rcs.ctypes.data)
+    else:
+        rp = None
+    st = lib().cbfm_solve(r.handle, e, nrhs, float(tol), int(maxit), int(restart), 1 if use_cmp else 0, jp, op,
+                          int(nd), rp, ctypes.c_void_p(iters.ctypes.data), ctypes.c_void_p(resid.ctypes.data),
+                          _stream(stream))
+    if st != 0 and not (st == 5 and allow_noconv):
+        _check(st)
+    return SolveResult(j, rcs, iters, resid, st)

@@ -1,0 +1,916 @@
+// api.cu -- the C ABI (include/cbfm.h): handles, argument checks, error
+// reporting and the orchestration of the kernels of each step.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <memory>
+#include <cstring>
+#include <new>
+#include <map>
+#include <mutex>
+#include <numeric>
+
+#include "internal.cuh"
+
+namespace cbfm {
+
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_prof{false};
+static thread_local std::string t_err;
+
+// ------------------------------------------------------ kernel timing
+namespace {
+struct PendingEv {
+    std::string name;
+    cudaEvent_t a, b;
+};
+struct ProfAcc {
+    int64_t launches = 0;
+    double ms = 0.0;
+};
+std::mutex g_prof_mu;
+std::vector<PendingEv> g_pending;
+std::map<std::string, ProfAcc> g_acc;
+}  // namespace
+
+int prof_start(const char *name, cudaStream_t st) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1;
+    }
+    cudaEventRecord(a, st);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_pending.push_back(PendingEv{name, a, b});
+    return (int)g_pending.size() - 1;
+}
+
+void prof_stop(int token, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (token >= 0 && token < (int)g_pending.size()) cudaEventRecord(g_pending[token].b, st);
+}
+
+void prof_flush() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            ProfAcc &acc = g_acc[p.name];
+            acc.launches += 1;
+            acc.ms += ms;
+        }
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    g_pending.clear();
+}
+
+void set_error(const std::string &msg) { t_err = msg; }
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void copy_in(void *dst_dev, const void *src_any, size_t bytes, cudaStream_t st) {
+    if (bytes) CBFM_CUDA(cudaMemcpyAsync(dst_dev, src_any, bytes, cudaMemcpyDefault, st));
+}
+void copy_out(void *dst_any, const void *src_dev, size_t bytes, cudaStream_t st) {
+    if (bytes) CBFM_CUDA(cudaMemcpyAsync(dst_any, src_dev, bytes, cudaMemcpyDefault, st));
+}
+
+namespace {
+
+// ------------------------------------------------------- helper kernels
+// Z_mm = [[Ks, Ta], [Tb, Ks]] restricted to the cell's edges (paper Eq. (pcbf)).
+__global__ void k_extract_zmm(int ncell, const int32_t *__restrict__ cell_off, const int64_t *__restrict__ zoff,
+                              int64_t ne, const z64 *__restrict__ Z, z64 *__restrict__ out) {
+    const int c = blockIdx.y;
+    const int64_t off = cell_off[c], N = cell_off[c + 1] - off, n2 = 2 * N;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n2 * n2;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / n2, j = idx % n2;
+        int bi = i >= N, bj = j >= N;
+        int op = (bi == bj) ? 0 : (bi == 0 ? 1 : 2);
+        out[zoff[c] + idx] = Z[((int64_t)op * ne + off + (i - bi * N)) * ne + off + (j - bj * N)];
+    }
+}
+
+// V_m = [vE(Lambda_m); vH(Lambda_m)]
+__global__ void k_extract_v(int ncell, const int32_t *__restrict__ cell_off, const int64_t *__restrict__ voff, int s,
+                            const z64 *__restrict__ vE, const z64 *__restrict__ vH, z64 *__restrict__ out) {
+    const int c = blockIdx.y;
+    const int64_t off = cell_off[c], N = cell_off[c + 1] - off;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * N * s;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / s, w = idx % s;
+        out[voff[c] + idx] = (i < N) ? vE[(off + i) * s + w] : vH[(off + i - N) * s + w];
+    }
+}
+
+// dense G_m (N_m x N_m) of every cell from the sparse Gram rows
+__global__ void k_cell_gram(int ncell, const int32_t *__restrict__ cell_off, const int64_t *__restrict__ goff,
+                            const double *__restrict__ val, const int32_t *__restrict__ col, z64 *__restrict__ G) {
+    const int c = blockIdx.y;
+    const int64_t off = cell_off[c], N = cell_off[c + 1] - off;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        z64 *row = G + goff[c] + i * N;
+        for (int64_t j = 0; j < N; ++j) row[j] = z64(0, 0);
+        for (int sl = 0; sl < 6; ++sl) {
+            int64_t cc = col[6 * (off + i) + sl];
+            if (cc >= off && cc < off + N) row[cc - off].re += val[6 * (off + i) + sl];
+        }
+    }
+}
+
+// dst (column-major s x s) = src (row-major s x s), per cell
+__global__ void k_to_colmajor(int s, const z64 *__restrict__ src, z64 *__restrict__ dst) {
+    const int c = blockIdx.y;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)s * s;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / s, j = idx % s;
+        dst[(int64_t)c * s * s + j * s + i] = src[(int64_t)c * s * s + idx];
+    }
+}
+
+// U_L = X(:, perm(0:L)) / sigma, V_L = V(:, perm(0:L)), row-major s x L_m at loff[c]
+__global__ void k_select(int s, const int32_t *__restrict__ perm, const int32_t *__restrict__ L,
+                         const int64_t *__restrict__ loff, const z64 *__restrict__ X, const z64 *__restrict__ V,
+                         const double *__restrict__ sig, z64 *__restrict__ UL, z64 *__restrict__ VL) {
+    const int c = blockIdx.y;
+    const int Lc = L[c];
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)s * Lc;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = idx / Lc, l = idx % Lc;
+        int pc = perm[(int64_t)c * s + l];
+        double sg = sig[(int64_t)c * s + pc];
+        z64 x = X[(int64_t)c * s * s + (int64_t)pc * s + r];
+        UL[loff[c] + idx] = (sg > 0.0) ? x * (1.0 / sg) : z64(0, 0);
+        VL[loff[c] + idx] = V[(int64_t)c * s * s + (int64_t)pc * s + r];
+    }
+}
+
+// X = Gf * C_all (ne x nh), C_all block diagonal: X[i][coff_c + l] = sum_slots val * C_c[col - off_c][l]
+__global__ void k_gram_times_c(int64_t ne, int64_t nh, const int32_t *__restrict__ edge_cell,
+                               const int32_t *__restrict__ cell_off, const int64_t *__restrict__ coff,
+                               const int64_t *__restrict__ boff, const int32_t *__restrict__ Lc,
+                               const double *__restrict__ val, const int32_t *__restrict__ col,
+                               const z64 *__restrict__ C, z64 *__restrict__ X) {
+    const int64_t i = blockIdx.y;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nh; k += (int64_t)gridDim.x * blockDim.x) {
+        z64 acc(0, 0);
+        for (int sl = 0; sl < 6; ++sl) {
+            int cc = col[6 * i + sl];
+            int c = edge_cell[cc];
+            int64_t l = k - coff[c];
+            if (l < 0 || l >= Lc[c]) continue;
+            acc += val[6 * i + sl] * C[boff[c] + (int64_t)(cc - cell_off[c]) * Lc[c] + l];
+        }
+        X[i * nh + k] = acc;
+    }
+}
+
+// complex transpose: dst (cols x rows) = src (rows x cols)^T
+__global__ void k_transpose(int64_t rows, int64_t cols, const z64 *__restrict__ src, z64 *__restrict__ dst) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < rows * cols;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / cols, j = idx % cols;
+        dst[j * rows + i] = src[idx];
+    }
+}
+
+// j in canonical edge order: out[ce][w] = in[int(ce)][w] (M part), out[ne+ce][w] = in[ne+int(ce)][w]
+__global__ void k_to_canonical(int64_t ne, int nrhs, const int32_t *__restrict__ int_of_canon,
+                               const z64 *__restrict__ in, z64 *__restrict__ out) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * ne * nrhs;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row = idx / nrhs, w = idx % nrhs;
+        int64_t half = row >= ne, ce = row - half * ne;
+        out[idx] = in[(half * ne + int_of_canon[ce]) * nrhs + w];
+    }
+}
+
+// block-diagonal assembly of two half inverses into the n x n matrix
+__global__ void k_place_block(int64_t n, int64_t nh, int64_t r0, const z64 *__restrict__ blk, z64 *__restrict__ out) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nh * nh;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / nh, j = idx % nh;
+        out[(r0 + i) * n + r0 + j] = blk[idx];
+    }
+}
+
+__global__ void k_copy_block(int64_t n, int64_t nh, int64_t r0, const z64 *__restrict__ full, z64 *__restrict__ blk) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nh * nh;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / nh, j = idx % nh;
+        blk[idx] = full[(r0 + i) * n + r0 + j];
+    }
+}
+
+inline unsigned nblk(int64_t work, int64_t per = 256, int64_t cap = 65535) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + per - 1) / per, cap));
+}
+
+template <typename F>
+cbfm_status guarded(F &&f) {
+    struct Flush {
+        ~Flush() {
+            if (g_prof.load()) prof_flush();
+        }
+    } flush_on_exit;
+    try {
+        f();
+        t_err.clear();
+        return CBFM_OK;
+    } catch (const Fail &e) {
+        t_err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        t_err = "host allocation failed";
+        return CBFM_ENOMEM;
+    } catch (const std::exception &e) {
+        t_err = e.what();
+        return CBFM_EINVAL;
+    }
+}
+
+void check_device(const HandleBase *h, uint32_t kind, const char *what) {
+    CBFM_REQUIRE(h != nullptr, std::string(what) + " handle is NULL");
+    CBFM_REQUIRE(h->kind == kind, std::string(what) + " handle has the wrong type");
+    int dev = -1;
+    CBFM_CUDA(cudaGetDevice(&dev));
+    CBFM_REQUIRE(dev == h->device, std::string(what) + " handle belongs to another device");
+}
+
+template <typename T>
+void upload(DevBuf<T> &b, const std::vector<T> &v, cudaStream_t st) {
+    b.alloc(v.size());
+    if (!v.empty()) CBFM_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+void cbf_finish(Cbf &c) {
+    const HostMesh &h = c.mesh->h;
+    c.coff.assign(h.ncell + 1, 0);
+    c.boff.assign(h.ncell + 1, 0);
+    for (int m = 0; m < h.ncell; ++m) {
+        c.coff[m + 1] = c.coff[m] + c.L[m];
+        c.boff[m + 1] = c.boff[m] + (int64_t)(h.cell_off[m + 1] - h.cell_off[m]) * c.L[m];
+    }
+    c.nhalf = c.coff[h.ncell];
+}
+
+void cbf_make32(Cbf &c, cudaStream_t st) {
+    int64_t tot = c.boff.back();
+    c.CM32.alloc(tot);
+    c.CJ32.alloc(tot);
+    launch_z64_to_c32(c.CM.p, c.CM32.p, tot, st);
+    launch_z64_to_c32(c.CJ.p, c.CJ32.p, tot, st);
+}
+
+}  // namespace
+}  // namespace cbfm
+
+using namespace cbfm;
+
+extern "C" {
+
+const char *cbfm_last_error(void) { return t_err.c_str(); }
+
+int64_t cbfm_launch_count(void) { return g_launches.load(); }
+
+void cbfm_profile(int32_t enable) {
+    prof_flush();
+    g_prof.store(enable != 0);
+}
+
+int64_t cbfm_profile_read(char *buf, int64_t cap, int32_t reset) {
+    prof_flush();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::string js = "{";
+    bool first = true;
+    for (auto &kv : g_acc) {
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f}", first ? "" : ", ", kv.first.c_str(),
+                 (long long)kv.second.launches, kv.second.ms);
+        js += tmp;
+        first = false;
+    }
+    js += "}";
+    if (reset) g_acc.clear();
+    if (buf && cap > 0) {
+        int64_t n = std::min<int64_t>(cap - 1, (int64_t)js.size());
+        memcpy(buf, js.data(), n);
+        buf[n] = 0;
+    }
+    return (int64_t)js.size() + 1;
+}
+
+cbfm_status cbfm_mesh(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, const int32_t *edge_cell,
+                      int32_t ncell, int32_t partition, double eps_re, double eps_im, double mu_r, double alpha,
+                      void *stream, cbfm_mesh_t *out) {
+    return guarded([&] {
+        CBFM_REQUIRE(out != nullptr && verts != nullptr && tris != nullptr, "NULL argument");
+        *out = nullptr;
+        CBFM_REQUIRE(eps_im <= 0.0, "eps_im must be <= 0 (passive medium, exp(+j w t))");
+        CBFM_REQUIRE(mu_r > 0.0 && alpha > 0.0, "mu_r and alpha must be positive");
+        CBFM_REQUIRE(!(eps_re == 0.0 && eps_im == 0.0), "eps_r must be nonzero");
+        cudaStream_t st = (cudaStream_t)stream;
+        std::vector<double> hv(3 * nv);
+        std::vector<int32_t> ht(3 * nt);
+        CBFM_REQUIRE(nv > 0 && nt > 0, "empty mesh");
+        copy_out(hv.data(), verts, hv.size() * sizeof(double), st);
+        copy_out(ht.data(), tris, ht.size() * sizeof(int32_t), st);
+        std::vector<int32_t> hc;
+        if (edge_cell) {
+            hc.resize((size_t)(3 * nt / 2));
+            copy_out(hc.data(), edge_cell, hc.size() * sizeof(int32_t), st);
+        }
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        Mesh *m = new Mesh();
+        std::unique_ptr<Mesh> guard(m);
+        m->kind = H_MESH;
+        CBFM_CUDA(cudaGetDevice(&m->device));
+        build_host_mesh(hv.data(), nv, ht.data(), nt, edge_cell ? hc.data() : nullptr, ncell, partition, m->h);
+        m->eps_re = eps_re;
+        m->eps_im = eps_im;
+        m->mu_r = mu_r;
+        m->alpha = alpha;
+        std::complex<double> eps(eps_re, eps_im);
+        std::complex<double> n2 = std::sqrt(eps * mu_r);
+        if (n2.real() < 0) n2 = -n2;
+        std::complex<double> k2 = K0 * n2;
+        std::complex<double> eta2 = ETA0 * std::sqrt(std::complex<double>(mu_r, 0) / eps);
+        m->k1 = z64(K0, 0);
+        m->eta1 = z64(ETA0, 0);
+        m->k2 = z64(k2.real(), k2.imag());
+        m->eta2 = z64(eta2.real(), eta2.imag());
+        for (int d = 0; d < 3; ++d) {
+            double lo = INFINITY, hi = -INFINITY;
+            for (int64_t i = 0; i < nv; ++i) {
+                lo = std::min(lo, hv[3 * i + d]);
+                hi = std::max(hi, hv[3 * i + d]);
+            }
+            m->centre[d] = 0.5 * (lo + hi);
+        }
+        const HostMesh &h = m->h;
+        DevBuf<double> dv;
+        DevBuf<int32_t> dt;
+        upload(dv, h.verts, st);
+        upload(dt, h.tris, st);
+        upload(m->tri_vid, h.tris, st);
+        upload(m->tri_edge, h.tri_edge, st);
+        upload(m->edge_tri, h.edge_tri, st);
+        upload(m->edge_loc, h.edge_loc, st);
+        std::vector<int32_t> ecell(h.ne);
+        for (int c = 0; c < h.ncell; ++c)
+            for (int32_t e = h.cell_off[c]; e < h.cell_off[c + 1]; ++e) ecell[e] = c;
+        upload(m->edge_cell, ecell, st);
+        m->tri64.alloc((size_t)h.nt * TRI_REC);
+        m->tri32.alloc((size_t)h.nt * TRI_REC);
+        launch_tri_records(*m, dv.p, dt.p, st);
+        launch_near_pairs(*m, st);
+        launch_gram_rows(*m, st);
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        *out = (cbfm_mesh_t)guard.release();
+    });
+}
+
+cbfm_status cbfm_mesh_edges(const double *verts, int64_t nv, const int32_t *tris, int64_t nt, int32_t ncell,
+                            int32_t partition, int64_t *n_edges, int32_t *edges, int32_t *cells) {
+    return guarded([&] {
+        CBFM_REQUIRE(verts && tris && n_edges, "NULL argument");
+        HostMesh hm;
+        build_host_mesh(verts, nv, tris, nt, nullptr, ncell, partition, hm);
+        *n_edges = hm.ne;
+        for (int64_t e = 0; e < hm.ne; ++e) {
+            if (edges) {
+                edges[2 * e] = hm.canon_u[e];
+                edges[2 * e + 1] = hm.canon_v[e];
+            }
+            if (cells) cells[e] = hm.cell_of_canon[e];
+        }
+    });
+}
+
+cbfm_status cbfm_mesh_info(cbfm_mesh_t mesh, int64_t *n_edges, int32_t *n_cells, int64_t *n_near) {
+    return guarded([&] {
+        Mesh *m = (Mesh *)mesh;
+        CBFM_REQUIRE(m && m->kind == H_MESH, "bad mesh handle");
+        if (n_edges) *n_edges = m->h.ne;
+        if (n_cells) *n_cells = m->h.ncell;
+        if (n_near) *n_near = m->n_near;
+    });
+}
+
+cbfm_status cbfm_mesh_cells(cbfm_mesh_t mesh, int32_t *edge_cell, void *stream) {
+    return guarded([&] {
+        Mesh *m = (Mesh *)mesh;
+        check_device(m, H_MESH, "mesh");
+        CBFM_REQUIRE(edge_cell, "NULL edge_cell");
+        copy_out(edge_cell, m->h.cell_of_canon.data(), m->h.ne * sizeof(int32_t), (cudaStream_t)stream);
+        CBFM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    });
+}
+
+cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, double delta_svd, int32_t lmax,
+                            void *stream, cbfm_cbf_t *out, int32_t *L_per_cell, double *sigma_out) {
+    return guarded([&] {
+        Mesh *m = (Mesh *)mesh;
+        check_device(m, H_MESH, "mesh");
+        CBFM_REQUIRE(out && waves && L_per_cell, "NULL argument");
+        *out = nullptr;
+        CBFM_REQUIRE(s >= 1 && s <= 1024, "s must be in [1, 1024]");
+        CBFM_REQUIRE(delta_svd >= 0.0 && delta_svd <= 1.0, "delta_svd must be in [0, 1]");
+        cudaStream_t st = (cudaStream_t)stream;
+        const HostMesh &h = m->h;
+        const int nc = h.ncell;
+        const int64_t ne = h.ne;
+        for (int c = 0; c < nc; ++c) CBFM_REQUIRE(2 * (h.cell_off[c + 1] - h.cell_off[c]) <= 4096, "cell too large");
+        DevBuf<double> dw;
+        dw.alloc(3 * (size_t)s);
+        copy_in(dw.p, waves, 3 * sizeof(double) * s, st);
+        // RWG operators (FP64) and plane-wave RHS
+        DevBuf<z64> Z, vE, vH;
+        Z.alloc(3 * (size_t)ne * ne);
+        assemble_rwg<double>(*m, Z.p, st);
+        vE.alloc((size_t)ne * s);
+        vH.alloc((size_t)ne * s);
+        launch_rhs(*m, dw.p, s, vE.p, vH.p, st);
+        // per-cell systems
+        std::vector<int64_t> zoff(nc), voff(nc), goff(nc + 1, 0), soff(nc);
+        std::vector<int> nn(nc);
+        int64_t zt = 0, vt = 0;
+        for (int c = 0; c < nc; ++c) {
+            int64_t N = h.cell_off[c + 1] - h.cell_off[c];
+            zoff[c] = zt;
+            voff[c] = vt;
+            nn[c] = (int)(2 * N);
+            zt += 4 * N * N;
+            vt += 2 * N * s;
+            goff[c + 1] = goff[c] + N * N;
+            soff[c] = (int64_t)c * s * s;
+        }
+        DevBuf<z64> Zmm, Vm;
+        Zmm.alloc(zt);
+        Vm.alloc(vt);
+        DevBuf<int32_t> dcoff;
+        upload(dcoff, h.cell_off, st);
+        DevBuf<int64_t> dzoff, dvoff, dgoff;
+        upload(dzoff, zoff, st);
+        upload(dvoff, voff, st);
+        upload(dgoff, goff, st);
+        {
+            ProfScope ps_("k_extract_zmm", st);
+            k_extract_zmm<<<dim3(nblk(4096 * 16), nc), 256, 0, st>>>(nc, dcoff.p, dzoff.p, ne, Z.p, Zmm.p);
+            launched("k_extract_zmm");
+        }
+        {
+            ProfScope ps_("k_extract_v", st);
+            k_extract_v<<<dim3(nblk(4096 * 4), nc), 256, 0, st>>>(nc, dcoff.p, dvoff.p, s, vE.p, vH.p, Vm.p);
+            launched("k_extract_v");
+        }
+        Z.release();
+        DevBuf<int> info;
+        info.alloc(nc);
+        CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int) * nc, st));
+        lu_solve_batched(nc, zoff.data(), voff.data(), nn.data(), s, Zmm.p, Vm.p, info.p, st);
+        std::vector<int> hinfo(nc);
+        CBFM_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        for (int c = 0; c < nc; ++c)
+            if (hinfo[c]) throw Fail{CBFM_ESINGULAR, "singular Z_mm in cell " + std::to_string(c)};
+        Zmm.release();
+        // Gram of every cell, G'_m = (J^M)^H G_m J^J
+        DevBuf<z64> Gm, T1, Gp, X, Vs;
+        Gm.alloc(goff[nc]);
+        {
+            ProfScope ps_("k_cell_gram", st);
+            k_cell_gram<<<dim3(nblk(4096), nc), 256, 0, st>>>(nc, dcoff.p, dgoff.p, m->gram_val.p, m->gram_col.p, Gm.p);
+            launched("k_cell_gram");
+        }
+        std::vector<int64_t> t1off(nc);
+        int64_t t1t = 0;
+        for (int c = 0; c < nc; ++c) {
+            t1off[c] = t1t;
+            t1t += (int64_t)(nn[c] / 2) * s;
+        }
+        T1.alloc(t1t);
+        Gp.alloc((size_t)nc * s * s);
+        std::vector<GemmDesc> g1, g2;
+        for (int c = 0; c < nc; ++c) {
+            int64_t N = nn[c] / 2;
+            // T1 = G_m J^J  (J^J = rows N..2N-1 of V_m)
+            g1.push_back(GemmDesc{N, s, N, goff[c], N, voff[c] + N * s, s, t1off[c], s});
+            // G' = (J^M)^H T1
+            g2.push_back(GemmDesc{s, s, N, voff[c], s, t1off[c], s, soff[c], s});
+        }
+        gemm_grouped<double>(g1, 0, 0, Gm.p, Vm.p, T1.p, false, st);
+        gemm_grouped<double>(g2, 2, 0, Vm.p, T1.p, Gp.p, false, st);
+        X.alloc((size_t)nc * s * s);
+        Vs.alloc((size_t)nc * s * s);
+        {
+            ProfScope ps_("k_to_colmajor", st);
+            k_to_colmajor<<<dim3(nblk((int64_t)s * s), nc), 256, 0, st>>>(s, Gp.p, X.p);
+            launched("k_to_colmajor");
+        }
+        DevBuf<double> sig;
+        sig.alloc((size_t)nc * s);
+        CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int) * nc, st));
+        jacobi_svd_batched(nc, s, X.p, Vs.p, sig.p, info.p, st);
+        std::vector<double> hs((size_t)nc * s);
+        CBFM_CUDA(cudaMemcpyAsync(hs.data(), sig.p, sizeof(double) * nc * s, cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        for (int c = 0; c < nc; ++c)
+            if (hinfo[c]) throw Fail{CBFM_ECUDA, "Jacobi SVD did not converge in cell " + std::to_string(c)};
+        // truncation: keep sigma_i / sigma_1 >= delta_svd (paper Eq. (gram_CBF_SVD))
+        std::unique_ptr<Cbf> cb(new Cbf());
+        cb->kind = H_CBF;
+        cb->device = m->device;
+        cb->mesh = m;
+        cb->L.assign(nc, 0);
+        std::vector<int32_t> perm((size_t)nc * s);
+        std::vector<int64_t> loff(nc + 1, 0);
+        for (int c = 0; c < nc; ++c) {
+            int32_t *pc = perm.data() + (size_t)c * s;
+            std::iota(pc, pc + s, 0);
+            const double *sc = hs.data() + (size_t)c * s;
+            std::stable_sort(pc, pc + s, [&](int a, int b) { return sc[a] > sc[b]; });
+            double s1 = sc[pc[0]];
+            CBFM_REQUIRE(s1 > 0.0, "zero CBF Gram matrix in cell " + std::to_string(c));
+            int L = 0;
+            for (int i = 0; i < s; ++i)
+                if (sc[pc[i]] / s1 >= delta_svd) ++L;
+            if (lmax > 0) L = std::min(L, (int)lmax);
+            L = std::min<int>(L, nn[c] / 2);
+            L = std::max(L, 1);
+            cb->L[c] = L;
+            L_per_cell[c] = L;
+            if (sigma_out)
+                for (int i = 0; i < s; ++i) sigma_out[(size_t)c * s + i] = sc[pc[i]] / s1;
+            loff[c + 1] = loff[c] + (int64_t)s * L;
+        }
+        cbf_finish(*cb);
+        DevBuf<int32_t> dperm, dL;
+        DevBuf<int64_t> dloff;
+        upload(dperm, perm, st);
+        upload(dL, cb->L, st);
+        upload(dloff, loff, st);
+        DevBuf<z64> UL, VL;
+        UL.alloc(loff[nc]);
+        VL.alloc(loff[nc]);
+        {
+            ProfScope ps_("k_select", st);
+            k_select<<<dim3(nblk((int64_t)s * 64), nc), 256, 0, st>>>(s, dperm.p, dL.p, dloff.p, X.p, Vs.p, sig.p, UL.p,
+                                                                      VL.p);
+            launched("k_select");
+        }
+        // C^M = J^M U_L, C^J = J^J V_L (paper Eq. (CBF))
+        cb->CM.alloc(cb->boff[nc]);
+        cb->CJ.alloc(cb->boff[nc]);
+        std::vector<GemmDesc> gm, gj;
+        for (int c = 0; c < nc; ++c) {
+            int64_t N = nn[c] / 2, L = cb->L[c];
+            gm.push_back(GemmDesc{N, L, s, voff[c], s, loff[c], L, cb->boff[c], L});
+            gj.push_back(GemmDesc{N, L, s, voff[c] + N * s, s, loff[c], L, cb->boff[c], L});
+        }
+        gemm_grouped<double>(gm, 0, 0, Vm.p, UL.p, cb->CM.p, false, st);
+        gemm_grouped<double>(gj, 0, 0, Vm.p, VL.p, cb->CJ.p, false, st);
+        cbf_make32(*cb, st);
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        *out = (cbfm_cbf_t)cb.release();
+    });
+}
+
+cbfm_status cbfm_cbf_import(cbfm_mesh_t mesh, const int32_t *L_per_cell, const double *CM, const double *CJ,
+                            void *stream, cbfm_cbf_t *out) {
+    return guarded([&] {
+        Mesh *m = (Mesh *)mesh;
+        check_device(m, H_MESH, "mesh");
+        CBFM_REQUIRE(out && L_per_cell && CM && CJ, "NULL argument");
+        *out = nullptr;
+        cudaStream_t st = (cudaStream_t)stream;
+        std::unique_ptr<Cbf> cb(new Cbf());
+        cb->kind = H_CBF;
+        cb->device = m->device;
+        cb->mesh = m;
+        cb->L.assign(L_per_cell, L_per_cell + m->h.ncell);
+        for (int c = 0; c < m->h.ncell; ++c) {
+            CBFM_REQUIRE(cb->L[c] >= 1, "L_per_cell must be >= 1");
+            CBFM_REQUIRE(cb->L[c] <= m->h.cell_off[c + 1] - m->h.cell_off[c], "L_m larger than N_m");
+        }
+        cbf_finish(*cb);
+        int64_t tot = cb->boff.back();
+        cb->CM.alloc(tot);
+        cb->CJ.alloc(tot);
+        copy_in(cb->CM.p, CM, tot * sizeof(z64), st);
+        copy_in(cb->CJ.p, CJ, tot * sizeof(z64), st);
+        cbf_make32(*cb, st);
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        *out = (cbfm_cbf_t)cb.release();
+    });
+}
+
+cbfm_status cbfm_cbf_export(cbfm_cbf_t cbf, double *CM, double *CJ, void *stream) {
+    return guarded([&] {
+        Cbf *c = (Cbf *)cbf;
+        check_device(c, H_CBF, "cbf");
+        int64_t tot = c->boff.back();
+        if (CM) copy_out(CM, c->CM.p, tot * sizeof(z64), (cudaStream_t)stream);
+        if (CJ) copy_out(CJ, c->CJ.p, tot * sizeof(z64), (cudaStream_t)stream);
+        CBFM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    });
+}
+
+}  // extern "C"
+
+namespace {
+
+// A = (C^JM)^H Z C^MJ from the RWG blocks (T = double or float)
+template <typename T>
+void project(Red &r, cudaStream_t st) {
+    Mesh &m = *r.mesh;
+    Cbf &c = *r.cbf;
+    const int64_t ne = m.h.ne, nh = c.nhalf, n = 2 * nh;
+    const int nc = m.h.ncell;
+    DevBuf<cx<T>> Z;
+    Z.alloc(3 * (size_t)ne * ne);
+    assemble_rwg<T>(m, Z.p, st);
+    const cx<T> *CM, *CJ;
+    if constexpr (sizeof(T) == 8) { CM = c.CM.p; CJ = c.CJ.p; }
+    else { CM = c.CM32.p; CJ = c.CJ32.p; }
+    // chains: (operator, coefficient side of the columns, row test side, A row block, A column block)
+    struct Chain { int op; bool colM; bool rowJ; int64_t r0, c0; };
+    const Chain ch[4] = {{0, true, true, 0, 0}, {1, false, true, 0, nh}, {2, true, false, nh, 0}, {0, false, false, nh, nh}};
+    DevBuf<cx<T>> Y, A;
+    Y.alloc((size_t)ne * nh);
+    A.alloc((size_t)n * n);
+    for (int q = 0; q < 4; ++q) {
+        std::vector<GemmDesc> g1, g2;
+        for (int k = 0; k < nc; ++k) {
+            int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
+            // Y[:, coff_k + l] = Z_op[:, Lambda_k] C_k
+            g1.push_back(GemmDesc{ne, L, N, (int64_t)ch[q].op * ne * ne + off, ne, c.boff[k], L, c.coff[k], nh});
+            // A[r0 + coff_k + l, c0 + :] = C_k^H Y[Lambda_k, :]
+            g2.push_back(GemmDesc{L, nh, N, c.boff[k], L, off * nh, nh, (ch[q].r0 + c.coff[k]) * n + ch[q].c0, n});
+        }
+        gemm_grouped<T>(g1, 0, 0, Z.p, ch[q].colM ? CM : CJ, Y.p, false, st);
+        gemm_grouped<T>(g2, 2, 0, ch[q].rowJ ? CJ : CM, Y.p, A.p, false, st);
+    }
+    if constexpr (sizeof(T) == 8) {
+        r.A64.p = A.p; r.A64.n = A.n; A.p = nullptr; A.n = 0;
+    } else {
+        r.A32.p = A.p; r.A32.n = A.n; A.p = nullptr; A.n = 0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precision prec, void *stream, cbfm_red_t *out,
+                                  int64_t *n_cbf) {
+    return guarded([&] {
+        Mesh *m = (Mesh *)mesh;
+        Cbf *c = (Cbf *)cbf;
+        check_device(m, H_MESH, "mesh");
+        check_device(c, H_CBF, "cbf");
+        CBFM_REQUIRE(c->mesh == m, "cbf handle belongs to another mesh");
+        CBFM_REQUIRE(out, "NULL out");
+        CBFM_REQUIRE(prec == CBFM_FP64 || prec == CBFM_MIXED, "unknown precision");
+        *out = nullptr;
+        cudaStream_t st = (cudaStream_t)stream;
+        std::unique_ptr<Red> r(new Red());
+        r->kind = H_RED;
+        r->device = m->device;
+        r->mesh = m;
+        r->cbf = c;
+        r->prec = prec;
+        r->n = 2 * c->nhalf;
+        if (prec == CBFM_FP64) project<double>(*r, st);
+        else project<float>(*r, st);
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        if (n_cbf) *n_cbf = r->n;
+        *out = (cbfm_red_t)r.release();
+    });
+}
+
+cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream) {
+    return guarded([&] {
+        Red *r = (Red *)red;
+        check_device(r, H_RED, "reduced system");
+        CBFM_REQUIRE(A, "NULL A");
+        cudaStream_t st = (cudaStream_t)stream;
+        int64_t nn = r->n * r->n;
+        if (r->prec == CBFM_FP64) {
+            copy_out(A, r->A64.p, nn * sizeof(z64), st);
+        } else {
+            DevBuf<z64> t;
+            t.alloc(nn);
+            launch_c32_to_z64(r->A32.p, t.p, nn, st);
+            copy_out(A, t.p, nn * sizeof(z64), st);
+            CBFM_CUDA(cudaStreamSynchronize(st));
+        }
+        CBFM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
+    return guarded([&] {
+        Red *r = (Red *)red;
+        check_device(r, H_RED, "reduced system");
+        cudaStream_t st = (cudaStream_t)stream;
+        Mesh &m = *r->mesh;
+        Cbf &c = *r->cbf;
+        const int64_t ne = m.h.ne, nh = c.nhalf, n = r->n;
+        const int nc = m.h.ncell;
+        DevBuf<int32_t> dcoff, dL;
+        DevBuf<int64_t> dcoff64, dboff;
+        upload(dcoff, m.h.cell_off, st);
+        upload(dL, c.L, st);
+        upload(dcoff64, c.coff, st);
+        upload(dboff, c.boff, st);
+        DevBuf<z64> XM, XJ;
+        XM.alloc((size_t)ne * nh);
+        XJ.alloc((size_t)ne * nh);
+        dim3 gx(nblk(nh), (unsigned)ne);
+        CBFM_REQUIRE(ne <= 65535, "too many edges for the Gram product grid");
+        {
+            ProfScope ps_("k_gram_times_c", st);
+            k_gram_times_c<<<gx, 256, 0, st>>>(ne, nh, m.edge_cell.p, dcoff.p, dcoff64.p, dboff.p, dL.p, m.gram_val.p,
+                                               m.gram_col.p, c.CM.p, XM.p);
+            launched("k_gram_times_c");
+        }
+        {
+            ProfScope ps_("k_gram_times_c", st);
+            k_gram_times_c<<<gx, 256, 0, st>>>(ne, nh, m.edge_cell.p, dcoff.p, dcoff64.p, dboff.p, dL.p, m.gram_val.p,
+                                               m.gram_col.p, c.CJ.p, XJ.p);
+            launched("k_gram_times_c");
+        }
+        r->G.alloc((size_t)n * n);
+        CBFM_CUDA(cudaMemsetAsync(r->G.p, 0, sizeof(z64) * n * n, st));
+        std::vector<GemmDesc> gJ, gM;
+        for (int k = 0; k < nc; ++k) {
+            int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
+            // first half: (C^J)^H Gf C^M ; second half: (C^M)^H Gf C^J
+            gJ.push_back(GemmDesc{L, nh, N, c.boff[k], L, off * nh, nh, c.coff[k] * n, n});
+            gM.push_back(GemmDesc{L, nh, N, c.boff[k], L, off * nh, nh, (nh + c.coff[k]) * n + nh, n});
+        }
+        gemm_grouped<double>(gJ, 2, 0, c.CJ.p, XM.p, r->G.p, false, st);
+        gemm_grouped<double>(gM, 2, 0, c.CM.p, XJ.p, r->G.p, false, st);
+        XM.release();
+        XJ.release();
+        // inverse of each half by Gauss-Jordan (FP64)
+        r->Ginv.alloc((size_t)n * n);
+        CBFM_CUDA(cudaMemsetAsync(r->Ginv.p, 0, sizeof(z64) * n * n, st));
+        DevBuf<z64> blk, aug;
+        DevBuf<int> info;
+        blk.alloc((size_t)nh * nh);
+        aug.alloc((size_t)4 * nh * nh);
+        info.alloc(1);
+        CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int), st));
+        for (int half = 0; half < 2; ++half) {
+            int64_t r0 = half * nh;
+            {
+                ProfScope ps_("k_copy_block", st);
+                k_copy_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, r0, r->G.p, blk.p);
+                launched("k_copy_block");
+            }
+            gauss_jordan_inverse(nh, aug.p, blk.p, info.p, st);
+            {
+                ProfScope ps_("k_place_block", st);
+                k_place_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, r0, blk.p, r->Ginv.p);
+                launched("k_place_block");
+            }
+        }
+        int hinfo = 0;
+        CBFM_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        if (hinfo) throw Fail{CBFM_ESINGULAR, "G^CBF is singular"};
+        if (r->prec == CBFM_MIXED) {
+            r->Ginv32.alloc((size_t)n * n);
+            launch_z64_to_c32(r->Ginv.p, r->Ginv32.p, n * n, st);
+        }
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        r->cmp_ready = true;
+    });
+}
+
+cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream) {
+    return guarded([&] {
+        Red *r = (Red *)red;
+        check_device(r, H_RED, "reduced system");
+        CBFM_REQUIRE(r->cmp_ready, "call cbfm_cmp_setup first");
+        CBFM_REQUIRE(G, "NULL G");
+        copy_out(G, r->G.p, r->n * r->n * sizeof(z64), (cudaStream_t)stream);
+        CBFM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    });
+}
+
+cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double tol, int32_t maxit, int32_t restart,
+                       int32_t use_cmp, double *j_out, const double *obs, int32_t ndir, double *rcs_out,
+                       int32_t *iters_out, double *resid_out, void *stream) {
+    cbfm_status conv = CBFM_OK;
+    cbfm_status st_ = guarded([&] {
+        Red *r = (Red *)red;
+        check_device(r, H_RED, "reduced system");
+        CBFM_REQUIRE(exc && nrhs >= 1, "need at least one excitation");
+        CBFM_REQUIRE(tol > 0.0 && maxit >= 1 && restart >= 1, "tol, maxit and restart must be positive");
+        CBFM_REQUIRE(!use_cmp || r->cmp_ready, "use_cmp requires cbfm_cmp_setup");
+        const bool mono = (obs == nullptr && ndir == -1);
+        CBFM_REQUIRE(mono || ndir >= 0, "ndir must be >= 0, or -1 with obs == NULL for monostatic");
+        CBFM_REQUIRE(mono || ndir == 0 || obs != nullptr, "obs is NULL");
+        cudaStream_t st = (cudaStream_t)stream;
+        Mesh &m = *r->mesh;
+        Cbf &c = *r->cbf;
+        const int64_t ne = m.h.ne, nh = c.nhalf, n = r->n;
+        const int nc = m.h.ncell;
+        DevBuf<double> dexc, dobs, drcs;
+        dexc.alloc(3 * (size_t)nrhs);
+        copy_in(dexc.p, exc, 3 * sizeof(double) * nrhs, st);
+        DevBuf<z64> vE, vH, bt, b, x, jint;
+        vE.alloc((size_t)ne * nrhs);
+        vH.alloc((size_t)ne * nrhs);
+        launch_rhs(m, dexc.p, nrhs, vE.p, vH.p, st);
+        // b = (C^JM)^H v  -> (n x nrhs), then rows per rhs
+        bt.alloc((size_t)n * nrhs);
+        std::vector<GemmDesc> gE, gH;
+        for (int k = 0; k < nc; ++k) {
+            int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
+            gE.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, c.coff[k] * nrhs, nrhs});
+            gH.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, (nh + c.coff[k]) * nrhs, nrhs});
+        }
+        gemm_grouped<double>(gE, 2, 0, c.CJ.p, vE.p, bt.p, false, st);
+        gemm_grouped<double>(gH, 2, 0, c.CM.p, vH.p, bt.p, false, st);
+        b.alloc((size_t)nrhs * n);
+        {
+            ProfScope ps_("k_transpose", st);
+            k_transpose<<<nblk(n * nrhs), 256, 0, st>>>(n, nrhs, bt.p, b.p);
+            launched("k_transpose");
+        }
+        x.alloc((size_t)nrhs * n);
+        GmresOut go = gmres_solve(*r, b.p, nrhs, tol, maxit, restart, use_cmp != 0, x.p, st);
+        // j = C^MJ x  (internal order, (2 ne) x nrhs)
+        jint.alloc((size_t)2 * ne * nrhs);
+        std::vector<GemmDesc> jM, jJ;
+        for (int k = 0; k < nc; ++k) {
+            int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
+            jM.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, c.coff[k], n, off * nrhs, nrhs});
+            jJ.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, nh + c.coff[k], n, (ne + off) * nrhs, nrhs});
+        }
+        gemm_grouped<double>(jM, 0, 1, c.CM.p, x.p, jint.p, false, st);
+        gemm_grouped<double>(jJ, 0, 1, c.CJ.p, x.p, jint.p, false, st);
+        if (rcs_out && (mono || ndir > 0)) {
+            int nd = mono ? 1 : ndir;
+            if (!mono) {
+                dobs.alloc(2 * (size_t)ndir);
+                copy_in(dobs.p, obs, 2 * sizeof(double) * ndir, st);
+            }
+            drcs.alloc((size_t)nrhs * nd * 2);
+            launch_farfield(m, jint.p, nrhs, dobs.p, nd, mono, dexc.p, drcs.p, st);
+            copy_out(rcs_out, drcs.p, sizeof(double) * nrhs * nd * 2, st);
+        }
+        if (j_out) {
+            DevBuf<int32_t> dmap;
+            upload(dmap, m.h.int_of_canon, st);
+            DevBuf<z64> jc;
+            jc.alloc((size_t)2 * ne * nrhs);
+            {
+                ProfScope ps_("k_to_canonical", st);
+                k_to_canonical<<<nblk(2 * ne * nrhs), 256, 0, st>>>(ne, nrhs, dmap.p, jint.p, jc.p);
+                launched("k_to_canonical");
+            }
+            copy_out(j_out, jc.p, sizeof(z64) * 2 * ne * nrhs, st);
+            CBFM_CUDA(cudaStreamSynchronize(st));
+        }
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < nrhs; ++i) {
+            if (iters_out) iters_out[i] = go.iters[i] >= 0 ? go.iters[i] : -go.iters[i] - 1;
+            if (resid_out) resid_out[i] = go.resid[i];
+            if (go.iters[i] < 0) conv = CBFM_ENOCONV;
+        }
+    });
+    if (st_ == CBFM_OK && conv != CBFM_OK) {
+        t_err = "GMRES did not converge for at least one right-hand side";
+        return conv;
+    }
+    return st_;
+}
+
+void cbfm_free(void *handle) {
+    if (!handle) return;
+    HandleBase *h = (HandleBase *)handle;
+    switch (h->kind) {
+        case H_MESH: h->kind = 0; delete (Mesh *)h; break;
+        case H_CBF: h->kind = 0; delete (Cbf *)h; break;
+        case H_RED: h->kind = 0; delete (Red *)h; break;
+        default: break;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// internal.cuh -- handle structures and kernel entry points of the library.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace cbfm {
+
+enum HandleKind : uint32_t { H_MESH = 0x4d455348u, H_CBF = 0x43424621u, H_RED = 0x52454421u };
+
+struct HandleBase {
+    uint32_t kind;
+    int device;
+};
+
+// Host-side mesh tables (mesh_host.cpp).  Internal edge order: by cell,
+// then canonical index, so every cell's edges are contiguous.
+struct HostMesh {
+    int64_t nv = 0, nt = 0, ne = 0;
+    int ncell = 0;
+    std::vector<double> verts;       // nv*3
+    std::vector<int32_t> tris;       // nt*3
+    std::vector<int32_t> canon_u, canon_v;      // canonical edges
+    std::vector<int32_t> cell_of_canon;         // ne
+    std::vector<int32_t> int_of_canon, canon_of_int;
+    std::vector<int32_t> cell_off;              // ncell+1 (internal order)
+    std::vector<int32_t> edge_tri, edge_loc;    // (ne,2) internal order: plus, minus
+    std::vector<int32_t> tri_edge, tri_sign;    // (nt,3) internal edge ids
+    std::vector<double> edge_len;               // internal order
+};
+
+void build_host_mesh(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                     const int32_t *edge_cell, int32_t ncell, int32_t partition, HostMesh &hm);
+
+struct Mesh : HandleBase {
+    HostMesh h;
+    double eps_re, eps_im, mu_r, alpha;
+    z64 k1, k2, eta1, eta2;
+    DevBuf<double> tri64;        // nt * TRI_REC
+    DevBuf<float> tri32;         // nt * TRI_REC (centred coordinates)
+    DevBuf<int32_t> tri_vid;     // nt*3 vertex ids
+    DevBuf<int32_t> tri_edge;    // nt*3 internal edge id
+    DevBuf<int32_t> edge_tri;    // ne*2
+    DevBuf<int32_t> edge_loc;    // ne*2
+    DevBuf<int32_t> edge_cell;   // ne, cell of each internal edge
+    DevBuf<int32_t> near_pairs;  // n_near*2 (t, s), t <= s, both orders needed
+    int64_t n_near = 0;
+    DevBuf<double> gram_val;     // ne*6 sparse RWG Gram row values
+    DevBuf<int32_t> gram_col;    // ne*6 internal edge columns (-1 unused)
+    double centre[3];
+};
+
+struct Cbf : HandleBase {
+    Mesh *mesh;
+    std::vector<int32_t> L;       // per cell
+    std::vector<int64_t> coff;    // CBF offsets per cell (ncell+1), within one half
+    std::vector<int64_t> boff;    // block offsets sum N_m L_m (ncell+1)
+    int64_t nhalf = 0;            // sum L_m
+    DevBuf<z64> CM, CJ;           // blocks N_m x L_m row-major, cells in order
+    DevBuf<c32> CM32, CJ32;
+};
+
+struct Red : HandleBase {
+    Mesh *mesh;
+    Cbf *cbf;
+    cbfm_precision prec;
+    int64_t n = 0;                // N^CBF
+    DevBuf<z64> A64;
+    DevBuf<c32> A32;
+    DevBuf<z64> G;                // G^CBF dense (n x n)
+    DevBuf<z64> Ginv;             // its inverse (FP64)
+    DevBuf<c32> Ginv32;
+    bool cmp_ready = false;
+};
+
+// ------------------------------------------------------------- kernels
+// geometry (k_geom.cu)
+void launch_tri_records(Mesh &m, const double *d_verts, const int32_t *d_tris, cudaStream_t st);
+void launch_near_pairs(Mesh &m, cudaStream_t st);
+void launch_gram_rows(Mesh &m, cudaStream_t st);
+void launch_rhs(const Mesh &m, const double *d_waves, int nw, z64 *vE, z64 *vH, cudaStream_t st);
+void launch_farfield(const Mesh &m, const z64 *j, int nrhs, const double *d_obs, int ndir, bool monostatic,
+                     const double *d_exc, double *d_rcs, cudaStream_t st);
+
+// assembly (k_assembly.cu): local blocks of all triangle pairs, then the RWG
+// matrices Z_op (op = Ks, Ta, Tb), row-major ne x ne, internal edge order.
+template <typename T>
+void assemble_rwg(Mesh &m, cx<T> *Zrwg, cudaStream_t st);
+
+// dense complex linear algebra (k_dense.cu)
+struct GemmDesc {
+    int64_t M, N, K;
+    int64_t a_off, lda, b_off, ldb, c_off, ldc;
+};
+// C[g] = op(A[g]) * op(B[g]) (+ C when accumulate); opA/opB: 0 = N, 1 = T, 2 = H
+template <typename T>
+void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> *A, const cx<T> *B, cx<T> *C,
+                  bool accumulate, cudaStream_t st);
+// Solve Z_b X_b = V_b in place (V overwritten by X) for nb independent systems of size n_b x n_b, s columns;
+// Z and V are overwritten. Returns singular flag per system in d_info (1 = zero pivot).
+void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, const int *h_n, int s, z64 *Z, z64 *V,
+                      int *d_info, cudaStream_t st);
+// One-sided Jacobi SVD of nb column-major s x s complex matrices X (overwritten by U Sigma), V out.
+void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info, cudaStream_t st);
+// In-place Gauss-Jordan inverse of an n x n FP64 complex matrix (row-major); info=1 on zero pivot.
+void gauss_jordan_inverse(int64_t n, z64 *Aug, z64 *inv, int *d_info, cudaStream_t st);
+
+// GMRES (k_gmres.cu)
+struct GmresOut {
+    std::vector<int> iters;
+    std::vector<double> resid;
+};
+GmresOut gmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp,
+                     z64 *d_x, cudaStream_t st);
+
+// elementwise helpers (k_dense.cu)
+void launch_z64_to_c32(const z64 *src, c32 *dst, int64_t n, cudaStream_t st);
+void launch_c32_to_z64(const c32 *src, z64 *dst, int64_t n, cudaStream_t st);
+
+}  // namespace cbfm

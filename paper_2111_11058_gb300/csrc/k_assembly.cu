@@ -1,0 +1,528 @@
+// k_assembly.cu -- Galerkin assembly of the PMCHWT blocks (paper Sec. II-B,
+// Eqs. (K), (T), (Z)).
+//
+// Stage 1, far pairs (k_far): one thread per (test triangle t, trial triangle s)
+//   evaluates both media over the 7 x 7 point pairs and reduces them to 18
+//   complex moments per medium, from which the 3 x 3 local blocks follow:
+//     T_ab = -j k c_a c_b [ Mrs - pi'_b.Mr - pi_a.Ms + (pi_a.pi'_b - 4/k^2) M0 ]
+//     K_ab =      c_a c_b [ MrX - pi_a.MX - pi'_b.MrW + pi_a.(MW x pi'_b) ]
+//   with positions taken relative to each triangle's centroid (rho on t, rho'
+//   on s, pi = vertex - centroid) and d = r - r' = (c_t - c_s) + rho - rho':
+//     S0 = sum_q w_q G, S1 = sum_q w_q G rho', W = sum_q w_q g d,
+//     X = sum_q w_q g (d x rho'),  G = e^{-jkR}/(4 pi R), g = -(1+jkR) e^{-jkR}/(4 pi R^3)
+//     M0 = sum_p w_p S0, Mr = sum_p w_p rho S0, Ms = sum_p w_p S1, Mrs = sum_p w_p rho.S1,
+//     MW = sum_p w_p W, MrW = sum_p w_p rho x W, MX = sum_p w_p X, MrX = sum_p w_p rho.X
+//   The minus sign on T is the reading under which the paper's block matrix
+//   describes the exp(+j w t) problem.  Blocks are combined into
+//   Ks = K1 + K2, Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2.
+// Stage 2, near pairs (k_near_blocks, FP64 always): 1/R, 1/R^3 and k^2/(2R)
+//   integrated in closed form over the trial triangle (Wilton et al. 1984,
+//   Graglia 1993 edge sums), bounded remainders by the 7-point rule, blocks
+//   symmetrised L(t,s) = (L~(t,s) + L~(s,t)^T)/2; K of a triangle with itself is 0.
+// Stage 3 (k_gather): RWG entries Z_op[i][j] = sum over the 2 x 2 triangle
+//   pairs of the two supports.
+#include "internal.cuh"
+
+namespace cbfm {
+
+namespace {
+
+constexpr int NCOMP = 27;   // 3 operators x 3 x 3
+
+struct Media {
+    double k1r, k1i, k2r, k2i;
+    double e1r, e1i, e2r, e2i;   // eta1, eta2
+};
+
+// -------------------------------------------------------------- FP32 trig
+// sin/cos of x >= 0 with a two-constant Cody-Waite reduction by 2 pi (round
+// to nearest multiple with the 1.5*2^23 shifter) and the hardware
+// approximation on [-pi, pi].
+__device__ __forceinline__ void sincos_red(float x, float *s, float *c) {
+    const float INV2PI = 0.159154943091895335768883763372514362f;
+    const float TWOPI_HI = 6.28318548202514648437500f;      // float(2 pi)
+    const float TWOPI_LO = -1.7484555314695172e-7f;         // 2 pi - TWOPI_HI
+    const float SHIFT = 12582912.0f;                        // 1.5 * 2^23
+    float n = __fadd_rn(__fmaf_rn(x, INV2PI, SHIFT), -SHIFT);
+    float r = __fmaf_rn(-n, TWOPI_HI, x);
+    r = __fmaf_rn(-n, TWOPI_LO, r);
+    __sincosf(r, s, c);
+}
+__device__ __forceinline__ void sincos_red(double x, double *s, double *c) { sincos(x, s, c); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float exp_t(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+
+template <typename T>
+struct Mom {
+    cx<T> M0, Mrs, MrX;
+    cx<T> Mr[3], Ms[3], MW[3], MrW[3], MX[3];
+};
+
+template <typename T>
+__device__ __forceinline__ void zero(Mom<T> &m) {
+    m.M0 = m.Mrs = m.MrX = cx<T>(0, 0);
+    for (int d = 0; d < 3; ++d) m.Mr[d] = m.Ms[d] = m.MW[d] = m.MrW[d] = m.MX[d] = cx<T>(0, 0);
+}
+
+__device__ __forceinline__ bool shares_vertex(const int32_t *a, const int32_t *b) {
+    bool r = false;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) r |= (a[i] == b[j]);
+    return r;
+}
+
+__device__ __forceinline__ double norm3_rn(double x, double y, double z) {
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+}
+
+// identical to the classification used for the near list
+__device__ __forceinline__ bool is_near(const double *rt, const double *rs, const int32_t *vt, const int32_t *vs,
+                                        double alpha) {
+    if (shares_vertex(vt, vs)) return true;
+    double dx = __dsub_rn(rt[TR_CEN], rs[TR_CEN]);
+    double dy = __dsub_rn(rt[TR_CEN + 1], rs[TR_CEN + 1]);
+    double dz = __dsub_rn(rt[TR_CEN + 2], rs[TR_CEN + 2]);
+    double h = fmax(rt[TR_H], rs[TR_H]);
+    return norm3_rn(dx, dy, dz) < __dmul_rn(alpha, h);
+}
+
+// Entries of one medium from its moments; adds into out[27] with the
+// operator weights (wK for K into Ks; wTa, wTb for T into Ta, Tb).
+template <typename T>
+__device__ __forceinline__ void fold_entries(const Mom<T> &m, T kr, T ki, const T ca[3], const T cb[3],
+                                             const T pa[3][3], const T pb[3][3], cx<T> wTa, cx<T> wTb,
+                                             cx<T> *out) {
+    // -j k and 4/k^2 for complex k
+    cx<T> mjk(ki, -kr);
+    cx<T> kk = cx<T>(kr, ki) * cx<T>(kr, ki);
+    cx<T> four_k2 = cdiv(cx<T>(4, 0), kk);
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) {
+            T cc = ca[a] * cb[b];
+            T papb = pa[a][0] * pb[b][0] + pa[a][1] * pb[b][1] + pa[a][2] * pb[b][2];
+            // T bracket
+            cx<T> tb = m.Mrs;
+            for (int d = 0; d < 3; ++d) {
+                tb -= pb[b][d] * m.Mr[d];
+                tb -= pa[a][d] * m.Ms[d];
+            }
+            tb += (cx<T>(papb, 0) - four_k2) * m.M0;
+            cx<T> Tab = cc * (mjk * tb);
+            // K bracket: MrX - pa.MX - pb.MrW + pa.(MW x pb)
+            cx<T> kb = m.MrX;
+            for (int d = 0; d < 3; ++d) {
+                kb -= pa[a][d] * m.MX[d];
+                kb -= pb[b][d] * m.MrW[d];
+            }
+            cx<T> cr0 = m.MW[1] * pb[b][2] - m.MW[2] * pb[b][1];
+            cx<T> cr1 = m.MW[2] * pb[b][0] - m.MW[0] * pb[b][2];
+            cx<T> cr2 = m.MW[0] * pb[b][1] - m.MW[1] * pb[b][0];
+            kb += pa[a][0] * cr0 + pa[a][1] * cr1 + pa[a][2] * cr2;
+            cx<T> Kab = cc * kb;
+            out[0 * 9 + 3 * a + b] += Kab;
+            out[1 * 9 + 3 * a + b] += wTa * Tab;
+            out[2 * 9 + 3 * a + b] += wTb * Tab;
+        }
+    }
+}
+
+// Stage 1.  Grid: x over trial triangles (blockDim.x each), y over test triangles.
+template <typename T>
+__global__ void __launch_bounds__(128) k_far(int nt, const T *__restrict__ rec, const double *__restrict__ rec64,
+                                             const int32_t *__restrict__ vid, double alpha, Media md,
+                                             cx<T> *__restrict__ Zloc) {
+    __shared__ T sq[21], sw[7], sp[9], sc[3], scen[3];
+    __shared__ double sc64[TRI_REC];
+    __shared__ int32_t sv[3];
+    const int t = blockIdx.y;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (threadIdx.x < TRI_REC) {
+        int i = threadIdx.x;
+        T v = rec[(int64_t)t * TRI_REC + i];
+        if (i < 21) sq[i] = v;
+        else if (i < 28) sw[i - 21] = v;
+        else if (i < 37) sp[i - 28] = v;
+        else if (i < 40) sc[i - 37] = v;
+        else if (i < 43) scen[i - 40] = v;   // centroid in the same frame as the points
+        sc64[i] = rec64[(int64_t)t * TRI_REC + i];
+        if (i < 3) sv[i] = vid[3 * t + i];
+    }
+    __syncthreads();
+    if (s >= nt) return;
+    const T *rs = rec + (int64_t)s * TRI_REC;
+    const int64_t plane = (int64_t)nt * nt;
+    const int64_t base = (int64_t)t * nt + s;
+    int32_t vs[3] = {vid[3 * s], vid[3 * s + 1], vid[3 * s + 2]};
+    if (is_near(sc64, rec64 + (int64_t)s * TRI_REC, sv, vs, alpha)) {
+        for (int c = 0; c < NCOMP; ++c) Zloc[c * plane + base] = cx<T>(0, 0);
+        return;
+    }
+    // trial data (local to its centroid)
+    T cs[3] = {rs[TR_CEN], rs[TR_CEN + 1], rs[TR_CEN + 2]};
+    T ct[3] = {scen[0], scen[1], scen[2]};
+    // centroid difference in FP64 for accuracy
+    T dc[3];
+    {
+        const double *r64 = rec64 + (int64_t)s * TRI_REC;
+        for (int d = 0; d < 3; ++d) dc[d] = (T)(sc64[TR_CEN + d] - r64[TR_CEN + d]);
+    }
+    T rq[7][3], wq[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        for (int d = 0; d < 3; ++d) rq[q][d] = rs[TR_Q + 3 * q + d] - cs[d];
+        wq[q] = rs[TR_W + q];
+    }
+    const T kr[2] = {(T)md.k1r, (T)md.k2r};
+    const T ki[2] = {(T)md.k1i, (T)md.k2i};
+    const bool lossy2 = md.k2i != 0.0;
+    const T inv4pi = (T)(1.0 / (4.0 * PI));
+    Mom<T> mm[2];
+    zero(mm[0]);
+    zero(mm[1]);
+    for (int p = 0; p < 7; ++p) {
+        T rho[3] = {sq[3 * p] - ct[0], sq[3 * p + 1] - ct[1], sq[3 * p + 2] - ct[2]};
+        T Dp[3] = {dc[0] + rho[0], dc[1] + rho[1], dc[2] + rho[2]};
+        cx<T> S0[2], S1[2][3], W[2][3], X[2][3];
+        for (int i = 0; i < 2; ++i) {
+            S0[i] = cx<T>(0, 0);
+            for (int d = 0; d < 3; ++d) S1[i][d] = W[i][d] = X[i][d] = cx<T>(0, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            T d0 = Dp[0] - rq[q][0], d1 = Dp[1] - rq[q][1], d2 = Dp[2] - rq[q][2];
+            T R2 = d0 * d0 + d1 * d1 + d2 * d2;
+            T iR = rsqrt_t(R2);
+            T R = R2 * iR;
+            T iR2 = iR * iR;
+            // d x rho'
+            T x0 = d1 * rq[q][2] - d2 * rq[q][1];
+            T x1 = d2 * rq[q][0] - d0 * rq[q][2];
+            T x2 = d0 * rq[q][1] - d1 * rq[q][0];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                T sn, cs_;
+                sincos_red(kr[i] * R, &sn, &cs_);
+                T amp = iR * inv4pi * wq[q];
+                if (i == 1 && lossy2) amp *= exp_t(ki[i] * R);
+                // w G = amp (cos - j sin)
+                cx<T> wG(amp * cs_, -amp * sn);
+                // w g = -(1 + j k R) w G / R^2, with j k R = -ki R + j kr R
+                cx<T> one_jkR((T)1 - ki[i] * R, kr[i] * R);
+                cx<T> wg = (-iR2) * (one_jkR * wG);
+                S0[i] += wG;
+                S1[i][0] += rq[q][0] * wG; S1[i][1] += rq[q][1] * wG; S1[i][2] += rq[q][2] * wG;
+                W[i][0] += d0 * wg; W[i][1] += d1 * wg; W[i][2] += d2 * wg;
+                X[i][0] += x0 * wg; X[i][1] += x1 * wg; X[i][2] += x2 * wg;
+            }
+        }
+        const T wp = sw[p];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            Mom<T> &m = mm[i];
+            m.M0 += wp * S0[i];
+            cx<T> rS1(0, 0), rX(0, 0);
+            for (int d = 0; d < 3; ++d) {
+                m.Mr[d] += (wp * rho[d]) * S0[i];
+                m.Ms[d] += wp * S1[i][d];
+                rS1 += rho[d] * S1[i][d];
+                m.MW[d] += wp * W[i][d];
+                m.MX[d] += wp * X[i][d];
+                rX += rho[d] * X[i][d];
+            }
+            m.Mrs += wp * rS1;
+            m.MrX += wp * rX;
+            // rho x W
+            m.MrW[0] += wp * (rho[1] * W[i][2] - rho[2] * W[i][1]);
+            m.MrW[1] += wp * (rho[2] * W[i][0] - rho[0] * W[i][2]);
+            m.MrW[2] += wp * (rho[0] * W[i][1] - rho[1] * W[i][0]);
+        }
+    }
+    // local vertex offsets and coefficients
+    T pa[3][3], pb[3][3], ca[3], cb[3];
+    for (int a = 0; a < 3; ++a) {
+        for (int d = 0; d < 3; ++d) {
+            pa[a][d] = sp[3 * a + d] - ct[d];
+            pb[a][d] = rs[TR_P + 3 * a + d] - cs[d];
+        }
+        ca[a] = sc[a];
+        cb[a] = rs[TR_C + a];
+    }
+    cx<T> out[NCOMP];
+    for (int c = 0; c < NCOMP; ++c) out[c] = cx<T>(0, 0);
+    // Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2
+    cx<double> e1(md.e1r, md.e1i), e2(md.e2r, md.e2i);
+    cx<double> ie1 = cdiv(cx<double>(1, 0), e1), ie2 = cdiv(cx<double>(1, 0), e2);
+    fold_entries<T>(mm[0], kr[0], ki[0], ca, cb, pa, pb, cx<T>((T)-e1.re, (T)-e1.im), cx<T>((T)ie1.re, (T)ie1.im), out);
+    fold_entries<T>(mm[1], kr[1], ki[1], ca, cb, pa, pb, cx<T>((T)-e2.re, (T)-e2.im), cx<T>((T)ie2.re, (T)ie2.im), out);
+    for (int c = 0; c < NCOMP; ++c) Zloc[c * plane + base] = out[c];
+}
+
+// ------------------------------------------------------- near pairs (FP64)
+__device__ inline void sub3(const double *a, const double *b, double *c) {
+    c[0] = a[0] - b[0]; c[1] = a[1] - b[1]; c[2] = a[2] - b[2];
+}
+__device__ inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ inline void cross3(const double *a, const double *b, double *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// ln(R + l) without cancellation for l < 0: (R + l)(R - l) = R0^2
+__device__ inline double log_r_plus_l(double l, double R, double R02) {
+    return (l >= 0.0) ? log(R + l) : log(R02 / (R - l));
+}
+
+// Closed-form potentials of a flat triangle V at r:
+//   I1 = int 1/R, Iv = int (r' - r)/R, I3 = int (r - r')/R^3 (principal value in plane).
+__device__ void potentials(const double *V, const double *r, double &I1, double Iv[3], double I3[3]) {
+    double e1[3], e2[3], n[3];
+    sub3(V + 3, V, e1);
+    sub3(V + 6, V, e2);
+    cross3(e1, e2, n);
+    double nl = sqrt(dot3(n, n));
+    for (int d = 0; d < 3; ++d) n[d] /= nl;
+    double rv[3];
+    sub3(r, V, rv);
+    double h = dot3(n, rv), ah = fabs(h);
+    double rho[3] = {r[0] - h * n[0], r[1] - h * n[1], r[2] - h * n[2]};
+    double tiny = 1e-28 * nl;
+    double sum_tF = 0.0, sum_beta = 0.0, vrho[3] = {0, 0, 0}, vF[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i) {
+        const double *A = V + 3 * i, *B = V + 3 * ((i + 1) % 3);
+        double l[3];
+        sub3(B, A, l);
+        double ll = sqrt(dot3(l, l));
+        for (int d = 0; d < 3; ++d) l[d] /= ll;
+        double u[3];
+        cross3(l, n, u);
+        double Ar[3], Br[3], rA[3], rB[3];
+        sub3(A, rho, Ar);
+        sub3(B, rho, Br);
+        sub3(r, A, rA);
+        sub3(r, B, rB);
+        double t0 = dot3(Ar, u), lp = dot3(Br, l), lm = dot3(Ar, l);
+        double R02 = t0 * t0 + h * h;
+        double Rp = sqrt(dot3(rB, rB)), Rm = sqrt(dot3(rA, rA));
+        double F = (R02 > tiny) ? log_r_plus_l(lp, Rp, R02) - log_r_plus_l(lm, Rm, R02) : 0.0;
+        double beta = (ah > 0.0) ? atan(t0 * lp / (R02 + ah * Rp)) - atan(t0 * lm / (R02 + ah * Rm)) : 0.0;
+        sum_tF += t0 * F;
+        sum_beta += beta;
+        double cf = 0.5 * (R02 * F + lp * Rp - lm * Rm);
+        for (int d = 0; d < 3; ++d) {
+            vrho[d] += cf * u[d];
+            vF[d] += F * u[d];
+        }
+    }
+    I1 = sum_tF - ah * sum_beta;
+    double sg = (h > 0.0) ? 1.0 : ((h < 0.0) ? -1.0 : 0.0);
+    for (int d = 0; d < 3; ++d) {
+        Iv[d] = vrho[d] - h * n[d] * I1;
+        I3[d] = vF[d] + n[d] * sg * sum_beta;
+    }
+}
+
+// (e^{-jkR} - 1)/(4 pi R), limit -jk/(4 pi) at R = 0 (series for |kR| < 0.5)
+__device__ inline z64 green_rem(z64 k, double R) {
+    z64 x = z64(k.im * R, -k.re * R);   // -j k R
+    if (sqrt(norm2(x)) < 0.5) {
+        z64 term(1, 0), s(0, 0);
+        for (int m = 1; m < 30; ++m) {
+            if (m > 1) term = term * x * (1.0 / m);
+            s += term;
+        }
+        return z64(k.im, -k.re) * s * (1.0 / (4.0 * PI));
+    }
+    double e = exp(x.re), sn, cs;
+    sincos(x.im, &sn, &cs);
+    return z64(e * cs - 1.0, e * sn) * (1.0 / (4.0 * PI * R));
+}
+
+// g + 1/(4 pi R^3) + k^2/(8 pi R), limit j k^3/(12 pi) at R = 0
+__device__ inline z64 gradgreen_rem(z64 k, double R) {
+    z64 jk(-k.im, k.re);
+    z64 x = jk * R;
+    if (sqrt(norm2(x)) < 0.5) {
+        z64 pw = jk * jk * jk, s(0, 0);
+        double fact = 6.0;
+        for (int m = 3; m < 34; ++m) {
+            if (m > 3) { pw = pw * x; fact *= m; }
+            double cm = ((m & 1) ? -1.0 : 1.0) * (1.0 - m) / fact;
+            s += cm * pw;
+        }
+        return s * (-1.0 / (4.0 * PI));
+    }
+    double e = exp(-x.re), sn, cs;
+    sincos(-x.im, &sn, &cs);
+    z64 ex(e * cs, e * sn);   // e^{-jkR}
+    z64 g = (z64(1, 0) + x) * ex * (-1.0 / (4.0 * PI * R * R * R));
+    return g + z64(1.0 / (4.0 * PI * R * R * R), 0) + (k * k) * (1.0 / (8.0 * PI * R));
+}
+
+// One warp per near pair (t <= s): lanes (orientation o, test point p), o in {0,1}, p < 7.
+template <typename T>
+__global__ void k_near_blocks(int64_t npairs, int nt, const int32_t *__restrict__ pairs,
+                              const double *__restrict__ rec, Media md, cx<T> *__restrict__ Zloc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t pid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (pid >= npairs) return;
+    const int t = pairs[2 * pid], s = pairs[2 * pid + 1];
+    const int o = lane / 7, p = lane % 7;
+    const bool active = lane < 14;
+    // per lane contributions: [medium][K/T][a][b]
+    z64 acc[2][2][9];
+    for (int i = 0; i < 2; ++i)
+        for (int k = 0; k < 2; ++k)
+            for (int c = 0; c < 9; ++c) acc[i][k][c] = z64(0, 0);
+    if (active) {
+        const double *A = rec + (int64_t)(o == 0 ? t : s) * TRI_REC;
+        const double *B = rec + (int64_t)(o == 0 ? s : t) * TRI_REC;
+        const double *r = A + TR_Q + 3 * p;
+        double I1, Iv[3], I3[3];
+        potentials(B + TR_P, r, I1, Iv, I3);
+        const double wp = A[TR_W + p];
+        for (int i = 0; i < 2; ++i) {
+            z64 k = (i == 0) ? z64(md.k1r, md.k1i) : z64(md.k2r, md.k2i);
+            z64 kk = k * k;
+            z64 S0(I1 / (4.0 * PI), 0), Sr[3], Wv[3];
+            for (int d = 0; d < 3; ++d) {
+                Sr[d] = z64(Iv[d] / (4.0 * PI), 0);
+                Wv[d] = z64(-I3[d] / (4.0 * PI), 0) + kk * (Iv[d] / (8.0 * PI));
+            }
+            for (int q = 0; q < 7; ++q) {
+                double dv[3];
+                sub3(r, B + TR_Q + 3 * q, dv);
+                double R = sqrt(dot3(dv, dv));
+                z64 gs = green_rem(k, R) * B[TR_W + q];
+                z64 hs = gradgreen_rem(k, R) * B[TR_W + q];
+                S0 += gs;
+                for (int d = 0; d < 3; ++d) {
+                    Sr[d] += gs * (-dv[d]);
+                    Wv[d] += hs * dv[d];
+                }
+            }
+            z64 mjk(k.im, -k.re);
+            z64 four_k2 = cdiv(z64(4, 0), kk);
+            for (int a = 0; a < 3; ++a) {
+                double ta[3];
+                sub3(r, A + TR_P + 3 * a, ta);
+                for (int b = 0; b < 3; ++b) {
+                    double rb[3];
+                    sub3(r, B + TR_P + 3 * b, rb);
+                    double cc = A[TR_C + a] * B[TR_C + b] * wp;
+                    z64 tS(0, 0);
+                    for (int d = 0; d < 3; ++d) tS += ta[d] * (Sr[d] + rb[d] * S0);
+                    acc[i][1][3 * a + b] += cc * (mjk * (tS - four_k2 * S0));
+                    if (t != s) {
+                        z64 c0 = Wv[1] * rb[2] - Wv[2] * rb[1];
+                        z64 c1 = Wv[2] * rb[0] - Wv[0] * rb[2];
+                        z64 c2 = Wv[0] * rb[1] - Wv[1] * rb[0];
+                        acc[i][0][3 * a + b] += cc * (ta[0] * c0 + ta[1] * c1 + ta[2] * c2);
+                    }
+                }
+            }
+        }
+    }
+    // reduce over p within each orientation group (lanes 0-6 and 7-13)
+    z64 res[2][2][9];
+    for (int i = 0; i < 2; ++i)
+        for (int k = 0; k < 2; ++k)
+            for (int c = 0; c < 9; ++c) {
+                double re = acc[i][k][c].re, im = acc[i][k][c].im;
+                double sre0 = 0, sim0 = 0, sre1 = 0, sim1 = 0;
+                for (int l = 0; l < 14; ++l) {
+                    double vre = __shfl_sync(0xffffffffu, re, l), vim = __shfl_sync(0xffffffffu, im, l);
+                    if (l < 7) { sre0 += vre; sim0 += vim; }
+                    else { sre1 += vre; sim1 += vim; }
+                }
+                // res[i][k][c] for orientation 0 in slot, orientation 1 transposed below
+                res[i][k][c] = z64(sre0, sim0);
+                acc[i][k][c] = z64(sre1, sim1);
+            }
+    if (lane != 0) return;
+    z64 e1(md.e1r, md.e1i), e2(md.e2r, md.e2i);
+    z64 we[2][3];   // weights of (K, T) of medium i into Ks, Ta, Tb
+    we[0][0] = z64(1, 0); we[0][1] = -e1; we[0][2] = cdiv(z64(1, 0), e1);
+    we[1][0] = z64(1, 0); we[1][1] = -e2; we[1][2] = cdiv(z64(1, 0), e2);
+    const int64_t plane = (int64_t)nt * nt;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            z64 v[3] = {z64(0, 0), z64(0, 0), z64(0, 0)};
+            for (int i = 0; i < 2; ++i) {
+                z64 K = 0.5 * (res[i][0][3 * a + b] + acc[i][0][3 * b + a]);
+                z64 Tm = 0.5 * (res[i][1][3 * a + b] + acc[i][1][3 * b + a]);
+                v[0] += we[i][0] * K;
+                v[1] += we[i][1] * Tm;
+                v[2] += we[i][2] * Tm;
+            }
+            for (int op = 0; op < 3; ++op) {
+                cx<T> val((T)v[op].re, (T)v[op].im);
+                Zloc[(op * 9 + 3 * a + b) * plane + (int64_t)t * nt + s] = val;
+                if (t != s) Zloc[(op * 9 + 3 * b + a) * plane + (int64_t)s * nt + t] = val;
+            }
+        }
+}
+
+// Stage 3: Z_op[i][j] from the local blocks (deterministic gather).
+template <typename T>
+__global__ void k_gather(int64_t ne, int nt, const int32_t *__restrict__ edge_tri, const int32_t *__restrict__ edge_loc,
+                         const cx<T> *__restrict__ Zloc, cx<T> *__restrict__ Z) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t i = blockIdx.y;
+    if (j >= ne) return;
+    const int64_t plane = (int64_t)nt * nt;
+    int ti[2] = {edge_tri[2 * i], edge_tri[2 * i + 1]}, ai[2] = {edge_loc[2 * i], edge_loc[2 * i + 1]};
+    int tj[2] = {edge_tri[2 * j], edge_tri[2 * j + 1]}, aj[2] = {edge_loc[2 * j], edge_loc[2 * j + 1]};
+    for (int op = 0; op < 3; ++op) {
+        cx<T> v(0, 0);
+        for (int s = 0; s < 2; ++s)
+            for (int sp = 0; sp < 2; ++sp)
+                v += Zloc[(op * 9 + 3 * ai[s] + aj[sp]) * plane + (int64_t)ti[s] * nt + tj[sp]];
+        Z[(op * ne + i) * ne + j] = v;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+void assemble_rwg(Mesh &m, cx<T> *Zrwg, cudaStream_t st) {
+    const int nt = (int)m.h.nt;
+    const int64_t ne = m.h.ne;
+    Media md{m.k1.re, m.k1.im, m.k2.re, m.k2.im, m.eta1.re, m.eta1.im, m.eta2.re, m.eta2.im};
+    DevBuf<cx<T>> Zloc;
+    Zloc.alloc((size_t)NCOMP * nt * nt);
+    const T *rec;
+    if constexpr (sizeof(T) == 8) rec = (const T *)m.tri64.p;
+    else rec = (const T *)m.tri32.p;
+    CBFM_REQUIRE(nt <= 65535, "k_far grid: more than 65535 triangles");
+    dim3 g1((nt + 127) / 128, nt);
+    {
+        ProfScope ps_("k_far", st);
+        k_far<T><<<g1, 128, 0, st>>>(nt, rec, m.tri64.p, m.tri_vid.p, m.alpha, md, Zloc.p);
+        launched("k_far");
+    }
+    if (m.n_near > 0) {
+        int64_t threads = m.n_near * 32;
+        {
+            ProfScope ps_("k_near_blocks", st);
+            k_near_blocks<T><<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(m.n_near, nt, m.near_pairs.p, m.tri64.p,
+                                                                               md, Zloc.p);
+            launched("k_near_blocks");
+        }
+    }
+    CBFM_REQUIRE(ne <= 65535, "k_gather grid: more than 65535 edges");
+    dim3 g3((unsigned)((ne + 127) / 128), (unsigned)ne);
+    {
+        ProfScope ps_("k_gather", st);
+        k_gather<T><<<g3, 128, 0, st>>>(ne, nt, m.edge_tri.p, m.edge_loc.p, Zloc.p, Zrwg);
+        launched("k_gather");
+    }
+    CBFM_CUDA(cudaStreamSynchronize(st));   // Zloc is released on return
+}
+
+template void assemble_rwg<double>(Mesh &, z64 *, cudaStream_t);
+template void assemble_rwg<float>(Mesh &, c32 *, cudaStream_t);
+
+}  // namespace cbfm

@@ -1,0 +1,420 @@
+// k_dense.cu -- dense complex linear algebra on the GPU: grouped GEMM,
+// batched LU solves (primary CBFs, paper Eq. (pcbf)), batched one-sided
+// Jacobi SVD (dual orthogonalisation, Eq. (gram_CBF_SVD)) and Gauss-Jordan
+// inversion (CBF Gram matrix, Eq. (CBF_Gram_matrix)).
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace cbfm {
+
+namespace {
+
+// ------------------------------------------------------------ grouped GEMM
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+
+struct TileRef {
+    int32_t g, tm, tn;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> load_op(const cx<T> *__restrict__ X, int64_t off, int64_t ld, int64_t r, int64_t c,
+                                         int64_t R, int64_t C, int op) {
+    // element (r, c) of op(X) where op(X) is R x C
+    if (r >= R || c >= C) return cx<T>(0, 0);
+    if (op == 0) return X[off + r * ld + c];
+    cx<T> v = X[off + c * ld + r];
+    return (op == 2) ? conj(v) : v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(const GemmDesc *__restrict__ descs, const TileRef *__restrict__ tiles,
+                                              int opA, int opB, const cx<T> *__restrict__ A,
+                                              const cx<T> *__restrict__ B, cx<T> *__restrict__ C, int accumulate) {
+    __shared__ cx<T> As[GB_K][GB_M + 1];
+    __shared__ cx<T> Bs[GB_K][GB_N + 1];
+    const TileRef tr = tiles[blockIdx.x];
+    const GemmDesc d = descs[tr.g];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t m0 = (int64_t)tr.tm * GB_M, n0 = (int64_t)tr.tn * GB_N;
+    cx<T> acc[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] = cx<T>(0, 0);
+    for (int64_t k0 = 0; k0 < d.K; k0 += GB_K) {
+        // thread -> element maps chosen so that consecutive threads read consecutive addresses
+        for (int idx = threadIdx.x; idx < GB_M * GB_K; idx += 256) {
+            int mm = (opA == 0) ? idx / GB_K : idx % GB_M;
+            int kk = (opA == 0) ? idx % GB_K : idx / GB_M;
+            As[kk][mm] = load_op(A, d.a_off, d.lda, m0 + mm, k0 + kk, d.M, d.K, opA);
+        }
+        for (int idx = threadIdx.x; idx < GB_K * GB_N; idx += 256) {
+            int kk = (opB == 0) ? idx / GB_N : idx % GB_K;
+            int nn = (opB == 0) ? idx % GB_N : idx / GB_K;
+            Bs[kk][nn] = load_op(B, d.b_off, d.ldb, k0 + kk, n0 + nn, d.K, d.N, opB);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            cx<T> a[4], b[4];
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < 4; ++i) {
+        int64_t r = m0 + ty + 16 * i;
+        if (r >= d.M) continue;
+        for (int j = 0; j < 4; ++j) {
+            int64_t c = n0 + tx + 16 * j;
+            if (c >= d.N) continue;
+            cx<T> *p = C + d.c_off + r * d.ldc + c;
+            if (accumulate) *p += acc[i][j];
+            else *p = acc[i][j];
+        }
+    }
+}
+
+// ------------------------------------------------------ batched LU solve
+// Gaussian elimination with partial pivoting on [Z | V], then backward
+// substitution; one block per system.
+__global__ void __launch_bounds__(256) k_lu_solve(const int64_t *__restrict__ zoff, const int64_t *__restrict__ voff,
+                                                  const int *__restrict__ nsz, int s, z64 *__restrict__ Zall,
+                                                  z64 *__restrict__ Vall, int *__restrict__ info) {
+    const int b = blockIdx.x;
+    const int n = nsz[b];
+    z64 *Z = Zall + zoff[b];
+    z64 *V = Vall + voff[b];
+    __shared__ double sval[256];
+    __shared__ int sidx[256];
+    __shared__ int piv;
+    __shared__ z64 pinv;
+    for (int k = 0; k < n; ++k) {
+        // pivot search
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+            double v = norm2(Z[(int64_t)i * n + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+        sval[threadIdx.x] = best;
+        sidx[threadIdx.x] = bi;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+                double o = sval[threadIdx.x + w];
+                int oi = sidx[threadIdx.x + w];
+                if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+                    sval[threadIdx.x] = o;
+                    sidx[threadIdx.x] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            piv = sidx[0];
+            if (sval[0] <= 0.0) info[b] = 1;
+        }
+        __syncthreads();
+        const int p = piv;
+        if (p != k) {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                z64 t = Z[(int64_t)k * n + j];
+                Z[(int64_t)k * n + j] = Z[(int64_t)p * n + j];
+                Z[(int64_t)p * n + j] = t;
+            }
+            for (int j = threadIdx.x; j < s; j += blockDim.x) {
+                z64 t = V[(int64_t)k * s + j];
+                V[(int64_t)k * s + j] = V[(int64_t)p * s + j];
+                V[(int64_t)p * s + j] = t;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            z64 d = Z[(int64_t)k * n + k];
+            pinv = (norm2(d) > 0.0) ? cdiv(z64(1, 0), d) : z64(0, 0);
+        }
+        __syncthreads();
+        // eliminate below
+        const int rows = n - k - 1;
+        const int wcols = (n - k - 1) + s;
+        for (int64_t idx = threadIdx.x; idx < (int64_t)rows * wcols; idx += blockDim.x) {
+            int i = k + 1 + (int)(idx / wcols);
+            int c = (int)(idx % wcols);
+            z64 l = Z[(int64_t)i * n + k] * pinv;
+            if (c < n - k - 1) {
+                int j = k + 1 + c;
+                Z[(int64_t)i * n + j] -= l * Z[(int64_t)k * n + j];
+            } else {
+                int j = c - (n - k - 1);
+                V[(int64_t)i * s + j] -= l * V[(int64_t)k * s + j];
+            }
+        }
+        __syncthreads();
+    }
+    // backward substitution, column oriented
+    for (int k = n - 1; k >= 0; --k) {
+        z64 d = Z[(int64_t)k * n + k];
+        z64 dinv = (norm2(d) > 0.0) ? cdiv(z64(1, 0), d) : z64(0, 0);
+        for (int j = threadIdx.x; j < s; j += blockDim.x) V[(int64_t)k * s + j] = V[(int64_t)k * s + j] * dinv;
+        __syncthreads();
+        for (int64_t idx = threadIdx.x; idx < (int64_t)k * s; idx += blockDim.x) {
+            int i = (int)(idx / s), j = (int)(idx % s);
+            V[(int64_t)i * s + j] -= Z[(int64_t)i * n + k] * V[(int64_t)k * s + j];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------- one-sided Jacobi SVD
+// X (s x s, column-major, overwritten by U Sigma) and V (s x s, column-major).
+// Round-robin pairing over n2 = s rounded up to even; disjoint pairs of a
+// round are processed by different warps.  Stops after a sweep without any
+// rotation, or after 60 sweeps (info = 2).
+__global__ void __launch_bounds__(256) k_jacobi_svd(int s, z64 *__restrict__ Xall, z64 *__restrict__ Vall,
+                                                    double *__restrict__ sig, int *__restrict__ info, double tol) {
+    z64 *X = Xall + (int64_t)blockIdx.x * s * s;
+    z64 *V = Vall + (int64_t)blockIdx.x * s * s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t i = threadIdx.x; i < (int64_t)s * s; i += blockDim.x) V[i] = z64((i % s) == (i / s) ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    const int n2 = s + (s & 1);
+    __shared__ int rotated;
+    int sweep = 0;
+    for (; sweep < 60; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        __syncthreads();
+        for (int round = 0; round < n2 - 1; ++round) {
+            for (int pr = warp; pr < n2 / 2; pr += nw) {
+                // round-robin: position 0 fixed, others rotate
+                int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (n2 - 1);
+                int b = 1 + (n2 - 2 - pr + round) % (n2 - 1);
+                int i = min(a, b), j = max(a, b);
+                if (j >= s) continue;   // dummy column of odd sizes
+                z64 *xi = X + (int64_t)i * s, *xj = X + (int64_t)j * s;
+                double al = 0, be = 0;
+                z64 ga(0, 0);
+                for (int r = lane; r < s; r += 32) {
+                    z64 u = xi[r], v = xj[r];
+                    al += norm2(u);
+                    be += norm2(v);
+                    cfmaconj(ga, u, v);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
+                    ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
+                }
+                double ag = sqrt(norm2(ga));
+                if (ag <= tol * sqrt(al * be) || ag == 0.0) continue;
+                if (lane == 0) rotated = 1;
+                double zeta = (be - al) / (2.0 * ag);
+                double t = 1.0 / (zeta + copysign(sqrt(1.0 + zeta * zeta), zeta));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                z64 e(ga.re / ag, ga.im / ag);   // e^{i phi}
+                z64 sem = sn * conj(e), sep = sn * e;
+                for (int r = lane; r < s; r += 32) {
+                    z64 u = xi[r], v = xj[r];
+                    xi[r] = c * u - sem * v;
+                    xj[r] = sep * u + c * v;
+                    z64 vu = V[(int64_t)i * s + r], vv = V[(int64_t)j * s + r];
+                    V[(int64_t)i * s + r] = c * vu - sem * vv;
+                    V[(int64_t)j * s + r] = sep * vu + c * vv;
+                }
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!rotated) break;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && sweep >= 60) info[blockIdx.x] = 2;
+    for (int i = warp; i < s; i += nw) {
+        double al = 0;
+        for (int r = lane; r < s; r += 32) al += norm2(X[(int64_t)i * s + r]);
+        for (int o = 16; o > 0; o >>= 1) al += __shfl_xor_sync(0xffffffffu, al, o);
+        if (lane == 0) sig[(int64_t)blockIdx.x * s + i] = sqrt(al);
+    }
+}
+
+// ------------------------------------------------- Gauss-Jordan inverse
+// One launch per elimination step k with ping-pong buffers (no grid-wide
+// wait): every block finds the pivot of column k itself.
+__global__ void k_gj_step(int64_t n, int64_t k, const z64 *__restrict__ Ain, z64 *__restrict__ Aout,
+                          int *__restrict__ info) {
+    // pivot: max |A[i][k]|, i >= k (first max)
+    __shared__ double sval[256];
+    __shared__ int64_t sidx[256];
+    double best = -1.0;
+    int64_t bi = k;
+    for (int64_t i = k + threadIdx.x; i < n; i += blockDim.x) {
+        double v = norm2(Ain[i * 2 * n + k]);
+        if (v > best) { best = v; bi = i; }
+    }
+    sval[threadIdx.x] = best;
+    sidx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            double o = sval[threadIdx.x + w];
+            int64_t oi = sidx[threadIdx.x + w];
+            if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+                sval[threadIdx.x] = o;
+                sidx[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const int64_t p = sidx[0];
+    if (sval[0] <= 0.0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = 1;
+    }
+    const z64 piv = Ain[p * 2 * n + k];
+    const z64 pinv = (norm2(piv) > 0.0) ? cdiv(z64(1, 0), piv) : z64(0, 0);
+    const int64_t w2 = 2 * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * w2; idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / w2, j = idx % w2;
+        // source row of output row i after swapping rows k and p
+        int64_t src = (i == k) ? p : ((i == p) ? k : i);
+        z64 prow = Ain[p * w2 + j] * pinv;   // normalised pivot row
+        if (i == k) {
+            Aout[idx] = prow;
+        } else {
+            z64 f = Ain[src * w2 + k];
+            Aout[idx] = Ain[src * w2 + j] - f * prow;
+        }
+    }
+}
+
+__global__ void k_gj_pack(int64_t n, const z64 *__restrict__ A, z64 *__restrict__ Aug) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * 2 * n) return;
+    int64_t i = idx / (2 * n), j = idx % (2 * n);
+    Aug[idx] = (j < n) ? A[i * n + j] : z64(j - n == i ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void k_gj_unpack(int64_t n, const z64 *__restrict__ Aug, z64 *__restrict__ inv) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int64_t i = idx / n, j = idx % n;
+    inv[idx] = Aug[i * 2 * n + n + j];
+}
+
+__global__ void k_to32(const z64 *__restrict__ s, c32 *__restrict__ d, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) d[i] = c32((float)s[i].re, (float)s[i].im);
+}
+__global__ void k_to64(const c32 *__restrict__ s, z64 *__restrict__ d, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) d[i] = z64(s[i].re, s[i].im);
+}
+
+}  // namespace
+
+template <typename T>
+void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> *A, const cx<T> *B, cx<T> *C,
+                  bool accumulate, cudaStream_t st) {
+    if (g.empty()) return;
+    std::vector<TileRef> tiles;
+    for (size_t i = 0; i < g.size(); ++i) {
+        if (g[i].M <= 0 || g[i].N <= 0) continue;
+        int64_t tm = (g[i].M + GB_M - 1) / GB_M, tn = (g[i].N + GB_N - 1) / GB_N;
+        for (int64_t a = 0; a < tm; ++a)
+            for (int64_t b = 0; b < tn; ++b) tiles.push_back(TileRef{(int32_t)i, (int32_t)a, (int32_t)b});
+    }
+    if (tiles.empty()) return;
+    DevBuf<GemmDesc> dd;
+    DevBuf<TileRef> dt;
+    dd.alloc(g.size());
+    dt.alloc(tiles.size());
+    CBFM_CUDA(cudaMemcpyAsync(dd.p, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, st));
+    CBFM_CUDA(cudaMemcpyAsync(dt.p, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice, st));
+    for (size_t t0 = 0; t0 < tiles.size(); t0 += 2147483647u) {
+        unsigned nb = (unsigned)std::min<size_t>(tiles.size() - t0, 2147483647u);
+        {
+            ProfScope ps_("k_gemm", st);
+            k_gemm<T><<<nb, 256, 0, st>>>(dd.p, dt.p + t0, opA, opB, A, B, C, accumulate ? 1 : 0);
+            launched("k_gemm");
+        }
+    }
+    CBFM_CUDA(cudaStreamSynchronize(st));   // descriptor buffers are released on return
+}
+
+template void gemm_grouped<double>(const std::vector<GemmDesc> &, int, int, const z64 *, const z64 *, z64 *, bool,
+                                   cudaStream_t);
+template void gemm_grouped<float>(const std::vector<GemmDesc> &, int, int, const c32 *, const c32 *, c32 *, bool,
+                                  cudaStream_t);
+
+void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, const int *h_n, int s, z64 *Z, z64 *V,
+                      int *d_info, cudaStream_t st) {
+    DevBuf<int64_t> zo, vo;
+    DevBuf<int> nn;
+    zo.alloc(nb);
+    vo.alloc(nb);
+    nn.alloc(nb);
+    CBFM_CUDA(cudaMemcpyAsync(zo.p, h_zoff, nb * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CBFM_CUDA(cudaMemcpyAsync(vo.p, h_voff, nb * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CBFM_CUDA(cudaMemcpyAsync(nn.p, h_n, nb * sizeof(int), cudaMemcpyHostToDevice, st));
+    {
+        ProfScope ps_("k_lu_solve", st);
+        k_lu_solve<<<nb, 256, 0, st>>>(zo.p, vo.p, nn.p, s, Z, V, d_info);
+        launched("k_lu_solve");
+    }
+    CBFM_CUDA(cudaStreamSynchronize(st));
+}
+
+void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info, cudaStream_t st) {
+    // rotation threshold: a few units of round-off in the column dot products
+    {
+        ProfScope ps_("k_jacobi_svd", st);
+        k_jacobi_svd<<<nb, 256, 0, st>>>(s, X, V, sig, d_info, 1e-15 * (s > 8 ? s : 8));
+        launched("k_jacobi_svd");
+    }
+}
+
+void gauss_jordan_inverse(int64_t n, z64 *Aug, z64 *inv, int *d_info, cudaStream_t st) {
+    // Aug must hold 2 buffers of n x 2n; the first n x n of `inv` on entry is A.
+    z64 *b0 = Aug, *b1 = Aug + n * 2 * n;
+    int64_t tot = n * 2 * n;
+    {
+        ProfScope ps_("k_gj_pack", st);
+        k_gj_pack<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, inv, b0);
+        launched("k_gj_pack");
+    }
+    int blocks = (int)std::min<int64_t>((tot + 255) / 256, 4 * 152);
+    for (int64_t k = 0; k < n; ++k) {
+        {
+            ProfScope ps_("k_gj_step", st);
+            k_gj_step<<<blocks, 256, 0, st>>>(n, k, b0, b1, d_info);
+            launched("k_gj_step");
+        }
+        std::swap(b0, b1);
+    }
+    {
+        ProfScope ps_("k_gj_unpack", st);
+        k_gj_unpack<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(n, b0, inv);
+        launched("k_gj_unpack");
+    }
+}
+
+void launch_z64_to_c32(const z64 *src, c32 *dst, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    {
+        ProfScope ps_("k_to32", st);
+        k_to32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+        launched("k_to32");
+    }
+}
+void launch_c32_to_z64(const c32 *src, z64 *dst, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    {
+        ProfScope ps_("k_to64", st);
+        k_to64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
+        launched("k_to64");
+    }
+}
+
+}  // namespace cbfm

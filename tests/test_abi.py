@@ -1,0 +1,73 @@
+"""CPU tests of the C ABI library: it builds for sm_103a, loads, exports every
+entry point include/cbfm.h declares, and its host-side mesh logic (canonical
+RWG edges, octant / RCB cells) matches the oracle's independent code."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mesh as OM
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2111_11058_gb300 import build as B
+    B.build()
+    import paper_2111_11058_gb300 as pkg
+    return pkg
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cbfm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cbfm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(P):
+    lib = P.cbfm.lib()
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(P.cbfm.exported_symbols()) == names
+
+
+@pytest.mark.parametrize("case", ["sphere_octant", "cube_rcb", "cylinder_rcb7", "array_rcb"])
+def test_host_mesh_tables_match_oracle(P, case):
+    g, nc, part = {
+        "sphere_octant": (W.icosphere(2, 0.3), 8, "octant"),
+        "cube_rcb": (W.cube(16), 32, "rcb"),
+        "cylinder_rcb7": (W.cylinder(0.3, 0.6, 16, 5, 2), 7, "rcb"),
+        "array_rcb": (W.sphere_array(2, 2, 1, 0.5, level=1), 5, "rcb"),
+    }[case]
+    e, c = P.mesh_edges(g.verts, g.tris, nc, part)
+    m = OM.build_rwg(g.verts, g.tris)
+    oc = OM.cells_octant(m) if part == "octant" else OM.cells_rcb(m, nc)
+    assert np.array_equal(e, m.edges)
+    assert np.array_equal(c, oc)
+    assert np.bincount(c).min() > 0
+
+
+def test_rejects_open_and_inconsistent_meshes(P):
+    g = W.icosphere(1, 0.5)
+    with pytest.raises(P.CbfmError) as ei:
+        P.mesh_edges(g.verts, g.tris[:-1], 8, "octant")
+    assert ei.value.status == 1
+    bad = g.tris.copy()
+    bad[0] = bad[0][[0, 2, 1]]
+    with pytest.raises(P.CbfmError):
+        P.mesh_edges(g.verts, bad, 8, "octant")
+    with pytest.raises(P.CbfmError):
+        P.mesh_edges(g.verts, g.tris, 7, "octant")
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    import paper_2111_11058_gb300.cbfm as C
+    monkeypatch.setattr(C, "_lib", None)
+    monkeypatch.setattr(C, "_LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(C.CbfmError):
+        C.lib()

@@ -1,0 +1,253 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative, max-abs normalised unless stated):
+  * FP64 path: reduced matrix and CBF Gram <= 1e-11; currents <= 1e-7 and
+    RCS <= 1e-8 with both sides solved to tol 1e-10 (solver tolerance times
+    the conditioning of A dominates);
+  * mixed path: reduced matrix <= 1e-4 (FP32 quadrature / complex64
+    projections, derived in the design doc), peak-normalised RCS <= 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cbfm as OC, mesh as OM, mom as OMo
+
+pytestmark = pytest.mark.gpu
+
+TOL_SOLVE = 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    from paper_2111_11058_gb300 import build as B
+    B.build()
+    import paper_2111_11058_gb300 as pkg
+    return pkg
+
+
+def _relmax(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _peak_rcs_err(g, o):
+    return float(np.abs(g - o).max() / np.abs(o).max())
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """The 320-triangle sphere workload with its oracle pipeline."""
+    d = W.sphere_c1()
+    g = d["mesh"]
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = OM.cells_octant(m)
+    exc = np.array([[0.0, 0.0, 0.0], [1.2, 0.7, 0.4], [2.5, 4.0, math.pi / 2]])
+    ref = OC.run(m, cell, 8, 4.0, d["gen"], exc, 1e-3, TOL_SOLVE, restart=1000)
+    obs = W.bistatic_cut(2.0)
+    st, sp = OMo.rcs(*OMo.farfield(m, ref["sol"].j, obs))
+    return dict(d=d, g=g, m=m, cell=cell, exc=exc, ref=ref, obs=obs, rcs=np.stack([st, sp], -1))
+
+
+def _gpu_mesh(P, c1):
+    return P.mesh(c1["g"].verts, c1["g"].tris, 8, 4.0, partition="octant")
+
+
+def _inject(P, gm, cbfs):
+    return P.cbf_import(gm, [c.CM for c in cbfs], [c.CJ for c in cbfs])
+
+
+def test_mesh_cells(P, c1):
+    gm = _gpu_mesh(P, c1)
+    assert gm.n_edges == 480
+    assert np.array_equal(gm.cells(), c1["cell"])
+
+
+def test_reduced_fp64_c1(P, c1):
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
+    assert red.n == c1["ref"]["A"].shape[0]
+    assert _relmax(red.export(), c1["ref"]["A"]) < 1e-11
+
+
+def test_reduced_mixed_c1(P, c1):
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.MIXED)
+    err = _relmax(red.export(), c1["ref"]["A"])
+    print(f"mixed reduced-matrix error {err:.2e}")
+    assert err < 1e-4
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-4)])
+def test_reduced_lossy_random_cbfs(P, prec, tol):
+    g = W.icosphere(1, 0.4)
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = OM.cells_rcb(m, 3)
+    Ns = np.bincount(cell)
+    CM, CJ = W.random_cbfs(Ns, [min(5, n) for n in Ns], seed=11)
+    cbfs = [OC.CellCBF(np.nonzero(cell == c)[0], CM[c], CJ[c], np.ones(1), CM[c].shape[1]) for c in range(3)]
+    A, _, _ = OC.reduced_system(m, cbfs, 3.0 - 0.1j)
+    gm = P.mesh(g.verts, g.tris, 3, 3.0 - 0.1j, partition="rcb")
+    red = P.assemble_reduced(gm, P.cbf_import(gm, CM, CJ), prec)
+    assert _relmax(red.export(), A) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-4)])
+def test_reduced_cube_full_size_sampled(P, prec, tol):
+    """Full-size cube (T = 3072, 32 cells) with seeded injected CBFs; blocks
+    the oracle can compute on their own (Z restricted to two cells)."""
+    d = W.cube_c2()
+    g = d["mesh"]
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = OM.cells_rcb(m, 32)
+    Ns = np.bincount(cell)
+    Ls = [14 if c % 3 else 13 for c in range(32)]
+    CM, CJ = W.random_cbfs(Ns, Ls, seed=5)
+    cbfs = [OC.CellCBF(np.nonzero(cell == c)[0], CM[c], CJ[c], np.ones(1), Ls[c]) for c in range(32)]
+    gm = P.mesh(g.verts, g.tris, 32, 2.5, partition="rcb")
+    red = P.assemble_reduced(gm, P.cbf_import(gm, CM, CJ), prec)
+    A = red.export()
+    offs = np.cumsum([0] + Ls)
+    nh = offs[-1]
+    for (mi, ni) in [(0, 0), (3, 17), (31, 5)]:
+        blocks = OC.reduced_block(m, cbfs, 2.5, mi, ni)
+        rm, rn = slice(offs[mi], offs[mi + 1]), slice(offs[ni], offs[ni + 1])
+        rm2, rn2 = slice(nh + offs[mi], nh + offs[mi + 1]), slice(nh + offs[ni], nh + offs[ni + 1])
+        got = [A[rm, rn], A[rm, rn2], A[rm2, rn], A[rm2, rn2]]
+        for gb, ob in zip(got, blocks):
+            assert _relmax(gb, ob) < tol, (mi, ni)
+
+
+def test_build_cbfs_c1(P, c1):
+    gm = _gpu_mesh(P, c1)
+    cb = P.build_cbfs(gm, c1["d"]["gen"], 1e-3)
+    ref = c1["ref"]["cbfs"]
+    assert cb.L.tolist() == [c.L for c in ref]
+    CMg, CJg = cb.export()
+    for c in range(8):
+        L = ref[c].L
+        so = ref[c].sigma / ref[c].sigma[0]
+        assert np.abs(cb.sigma[c, :L + 2] - so[:L + 2]).max() < 1e-9
+        lam = ref[c].edges
+        Gm = OC.rwg_gram(c1["m"], lam, lam)
+        D = CMg[c].conj().T @ Gm @ CJg[c]
+        sig = ref[c].sigma[:L]
+        assert np.abs(D - np.diag(sig)).max() < 1e-9 * sig[0]
+        # same subspaces as the oracle's CBFs (singular vectors are unique only up to unitary mixing)
+        for Cg, Co in ((CMg[c], ref[c].CM), (CJg[c], ref[c].CJ)):
+            Qg, _ = np.linalg.qr(Cg)
+            Qo, _ = np.linalg.qr(Co)
+            cosines = np.linalg.svd(Qg.conj().T @ Qo, compute_uv=False)
+            assert cosines.min() > 1 - 1e-8
+
+
+def test_cmp_gram_c1(P, c1):
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
+    P.cmp_setup(red)
+    G = red.gram()
+    Go = c1["ref"]["G"]
+    assert _relmax(G, Go) < 1e-12
+
+
+def test_solve_fp64_c1(P, c1):
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
+    P.cmp_setup(red)
+    res = P.solve(red, c1["exc"], tol=TOL_SOLVE, obs=c1["obs"])
+    jo = c1["ref"]["sol"].j
+    assert np.linalg.norm(res.j - jo) / np.linalg.norm(jo) < 1e-7
+    assert _peak_rcs_err(res.rcs.sum(-1), c1["rcs"].sum(-1)) < 1e-8
+    for a, b in zip(res.iters, c1["ref"]["sol"].iters):
+        assert abs(int(a) - int(b)) <= 3
+    assert (res.resid <= TOL_SOLVE).all()
+
+
+def test_solve_mixed_c1_rcs_within_1e4(P, c1):
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.MIXED)
+    P.cmp_setup(red)
+    res = P.solve(red, c1["exc"], tol=1e-6, obs=c1["obs"])
+    err = _peak_rcs_err(res.rcs.sum(-1), c1["rcs"].sum(-1))
+    print(f"mixed RCS error {err:.2e}, iterations {res.iters.tolist()}")
+    assert err < 1e-4
+
+
+def test_end_to_end_gpu_cbfs_c1(P, c1):
+    """Whole GPU pipeline (own CBFs): same subspaces, so the same currents."""
+    gm = _gpu_mesh(P, c1)
+    cb = P.build_cbfs(gm, c1["d"]["gen"], 1e-3)
+    red = P.assemble_reduced(gm, cb, P.FP64)
+    P.cmp_setup(red)
+    res = P.solve(red, c1["exc"], tol=TOL_SOLVE, obs=c1["obs"])
+    assert _peak_rcs_err(res.rcs.sum(-1), c1["rcs"].sum(-1)) < 1e-6
+
+
+def test_monostatic_matches_bistatic(P, c1):
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
+    P.cmp_setup(red)
+    exc = c1["exc"]
+    mono = P.solve(red, exc, tol=1e-8, monostatic=True)
+    bi = P.solve(red, exc, tol=1e-8, obs=exc[:, :2])
+    for r in range(len(exc)):
+        assert np.allclose(mono.rcs[r, 0], bi.rcs[r, r], rtol=1e-12, atol=0)
+
+
+def test_no_cmp_and_noconv_status(P, c1):
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
+    res = P.solve(red, c1["exc"][:1], tol=1e-12, maxit=3, restart=3, use_cmp=False, allow_noconv=True)
+    assert res.status == 5
+    with pytest.raises(P.CbfmError) as ei:
+        P.solve(red, c1["exc"][:1], tol=1e-6, use_cmp=True)     # cmp_setup not called
+    assert ei.value.status == 1
+
+
+def test_invalid_arguments(P):
+    g = W.icosphere(1, 0.3)
+    with pytest.raises(P.CbfmError) as ei:
+        P.mesh(g.verts, g.tris, 8, 2.0 + 0.1j, partition="octant")   # active medium
+    assert ei.value.status == 1
+    with pytest.raises(P.CbfmError):
+        P.mesh(g.verts, g.tris[:-2], 8, 2.0, partition="octant")    # open mesh
+
+
+def test_device_buffers_match_host(P, c1):
+    import torch
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.MIXED)
+    P.cmp_setup(red)
+    host = P.solve(red, c1["exc"], tol=1e-6, obs=c1["obs"])
+    exc_d = torch.tensor(c1["exc"], dtype=torch.float64, device="cuda")
+    obs_d = torch.tensor(c1["obs"], dtype=torch.float64, device="cuda")
+    j_d = torch.zeros((2 * gm.n_edges, 3), dtype=torch.complex128, device="cuda")
+    rcs_d = torch.zeros((3, len(c1["obs"]), 2), dtype=torch.float64, device="cuda")
+    P.solve(red, exc_d, tol=1e-6, obs=obs_d, out_j=j_d, out_rcs=rcs_d)
+    torch.cuda.synchronize()
+    assert np.array_equal(j_d.cpu().numpy(), host.j)
+    assert np.array_equal(rcs_d.cpu().numpy(), host.rcs)
+
+
+def test_degenerate_eps1_matches_oracle(P):
+    """eps_r = 1 (interior = exterior medium), the method's degenerate case:
+    GPU-built CBFs end to end against the oracle pipeline."""
+    g = W.icosphere(2, 0.3)
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = OM.cells_octant(m)
+    gen = W.plane_wave_set(W.fibonacci_dirs(12))
+    exc = np.array([[0.4, 0.7, 0.3]])
+    obs = W.bistatic_cut(10.0)
+    ref = OC.run(m, cell, 8, 1.0, gen, exc, 1e-3, TOL_SOLVE, restart=1000)
+    st, sp = OMo.rcs(*OMo.farfield(m, ref["sol"].j, obs))
+    gm = P.mesh(g.verts, g.tris, 8, 1.0, partition="octant")
+    cb = P.build_cbfs(gm, gen, 1e-3)
+    red = P.assemble_reduced(gm, cb, P.FP64)
+    P.cmp_setup(red)
+    res = P.solve(red, exc, tol=TOL_SOLVE, obs=obs)
+    assert _peak_rcs_err(res.rcs.sum(-1), st + sp) < 1e-6

@@ -307,3 +307,12 @@ def scatterer_mix(count: int, seed: int = 0):
             m = cylinder(size / 2, size, nphi, int(rng.integers(3, 10)), 2)
         out.append(dict(mesh=m, eps=(eps, 0.0)))
     return out
+
+
+def random_cbfs(Ns, Ls, seed: int = 0):
+    """Seeded complex Gaussian blocks (N_m, L_m) standing in for C^M and C^J
+    when the projection is tested on its own (the projection is linear in C)."""
+    rng = np.random.default_rng(seed)
+    CM = [(rng.standard_normal((n, l)) + 1j * rng.standard_normal((n, l))) / np.sqrt(2 * n) for n, l in zip(Ns, Ls)]
+    CJ = [(rng.standard_normal((n, l)) + 1j * rng.standard_normal((n, l))) / np.sqrt(2 * n) for n, l in zip(Ns, Ls)]
+    return CM, CJ
