@@ -4,7 +4,7 @@ The compute path lives in libcbfm.so (hand-written CUDA, C ABI in
 include/cbfm.h); `cbfm` is its thin Python binding and `build` compiles it.
 """
 from .cbfm import (FP64, MIXED, CbfmError, assemble_reduced, build_cbfs, cbf_import, cmp_setup, launch_count,
-                   mesh, mesh_edges, solve)
+                   mesh, mesh_edges, profile, profile_read, solve)
 
 __all__ = ["FP64", "MIXED", "CbfmError", "assemble_reduced", "build_cbfs", "cbf_import", "cmp_setup",
-           "launch_count", "mesh", "mesh_edges", "solve"]
+           "launch_count", "mesh", "mesh_edges", "profile", "profile_read", "solve"]
