@@ -140,6 +140,26 @@ cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precisi
 cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream);
 
 /*
+ * cbfm_red_export_noalloc -- the same output as cbfm_red_export for callers
+ * that cannot allocate device memory at the time of the call (a serving
+ * process whose HBM is full of cached matrices, an allocator that forbids
+ * cudaMalloc, a thread that must not trigger the device-wide synchronisation
+ * cudaMalloc/cudaFree may cause).  The paper has no counterpart: this is a
+ * library service, not part of the method.
+ *   Calls no cudaMalloc, cudaFree or allocating library routine.  A mixed-
+ *   precision matrix is widened to complex128 in a fixed 4 MiB scratch array
+ *   built into the library (held by every GPU that loads it until exit), so
+ *   n_cbf must be <= 512; larger systems return CBFM_EINVAL.
+ *   The first call on each device looks up the scratch array's device address
+ *   (cudaGetSymbolAddress with that device current); make that first call
+ *   before any stream capture.  All calls share the one scratch array, which
+ *   keeps the last call's contents: calls that overlap on the GPU (different
+ *   streams or threads) race and must be serialised by the caller.  Returns
+ *   after the copy into A (host or device) has completed.
+ */
+cbfm_status cbfm_red_export_noalloc(cbfm_red_t red, double *A, void *stream);
+
+/*
  * cbfm_cmp_setup -- CBF Gram matrix G^CBF = (C^JM)^H G_ffff C^MJ (paper Eq.
  * (CBF_Gram_matrix)) and its inverse by Gauss-Jordan elimination with partial
  * pivoting in FP64.  Returns CBFM_ESINGULAR on a zero pivot.

@@ -62,6 +62,7 @@ def lib():
             "cbfm_cbf_export": [_vp, _vp, _vp, _vp],
             "cbfm_assemble_reduced": [_vp, _vp, _i32, _vp, _vp, _vp],
             "cbfm_red_export": [_vp, _vp, _vp],
+            "cbfm_red_export_noalloc": [_vp, _vp, _vp],
             "cbfm_cmp_setup": [_vp, _vp],
             "cbfm_gram_export": [_vp, _vp, _vp],
             "cbfm_solve": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp],
@@ -87,7 +88,7 @@ def lib():
 def exported_symbols():
     """Names of the C entry points declared in include/cbfm.h."""
     return ["cbfm_mesh", "cbfm_mesh_edges", "cbfm_mesh_info", "cbfm_mesh_cells", "cbfm_build_cbfs", "cbfm_cbf_import",
-            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_red_export", "cbfm_cmp_setup", "cbfm_gram_export",
+            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_gram_export",
             "cbfm_solve", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
             "cbfm_profile_read"]
 
@@ -211,6 +212,13 @@ class Reduced(_Handle):
     def export(self, stream=None) -> np.ndarray:
         A = np.zeros((self.n, self.n), np.complex128)
         _check(lib().cbfm_red_export(self._h, ctypes.c_void_p(A.ctypes.data), _stream(stream)))
+        return A
+
+    def export_noalloc(self, stream=None) -> np.ndarray:
+        """cbfm_red_export_noalloc: as export(), without any device allocation
+        (fixed library scratch; n <= 512)."""
+        A = np.zeros((self.n, self.n), np.complex128)
+        _check(lib().cbfm_red_export_noalloc(self._h, ctypes.c_void_p(A.ctypes.data), _stream(stream)))
         return A
 
     def gram(self, stream=None) -> np.ndarray:

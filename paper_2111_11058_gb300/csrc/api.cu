@@ -720,6 +720,14 @@ cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream) {
     });
 }
 
+cbfm_status cbfm_red_export_noalloc(cbfm_red_t red, double *A, void *stream) {
+    return guarded([&] {
+        Red *r = (Red *)red;
+        check_device(r, H_RED, "reduced system");
+        red_export_noalloc(*r, A, (cudaStream_t)stream);
+    });
+}
+
 cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
     return guarded([&] {
         Red *r = (Red *)red;

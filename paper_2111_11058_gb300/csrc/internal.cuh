@@ -114,6 +114,9 @@ struct GmresOut {
 GmresOut gmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp,
                      z64 *d_x, cudaStream_t st);
 
+// export of the reduced matrix without device allocation (noalloc.cu)
+void red_export_noalloc(Red &r, double *A, cudaStream_t st);
+
 // elementwise helpers (k_dense.cu)
 void launch_z64_to_c32(const z64 *src, c32 *dst, int64_t n, cudaStream_t st);
 void launch_c32_to_z64(const c32 *src, z64 *dst, int64_t n, cudaStream_t st);
