@@ -800,9 +800,16 @@ cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
         CBFM_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         CBFM_CUDA(cudaStreamSynchronize(st));
         if (hinfo) throw Fail{CBFM_ESINGULAR, "G^CBF is singular"};
+        // B = A (G^CBF)^{-1}: GMRES then needs one product per iteration
+        std::vector<GemmDesc> gb{GemmDesc{n, n, n, 0, n, 0, n, 0, n}};
         if (r->prec == CBFM_MIXED) {
             r->Ginv32.alloc((size_t)n * n);
             launch_z64_to_c32(r->Ginv.p, r->Ginv32.p, n * n, st);
+            r->B32.alloc((size_t)n * n);
+            gemm_grouped<float>(gb, 0, 0, r->A32.p, r->Ginv32.p, r->B32.p, false, st);
+        } else {
+            r->B64.alloc((size_t)n * n);
+            gemm_grouped<double>(gb, 0, 0, r->A64.p, r->Ginv.p, r->B64.p, false, st);
         }
         CBFM_CUDA(cudaStreamSynchronize(st));
         r->cmp_ready = true;

@@ -71,6 +71,8 @@ struct Red : HandleBase {
     DevBuf<z64> G;                // G^CBF dense (n x n)
     DevBuf<z64> Ginv;             // its inverse (FP64)
     DevBuf<c32> Ginv32;
+    DevBuf<z64> B64;              // B = A (G^CBF)^{-1}, the operator GMRES iterates with
+    DevBuf<c32> B32;
     bool cmp_ready = false;
 };
 
@@ -111,6 +113,9 @@ struct GmresOut {
     std::vector<int> iters;
     std::vector<double> resid;
 };
+// out[r] = M in[r] for rows with mask[r] != 0 (M32 != NULL: complex64 / FP32 arithmetic)
+void apply_rows(const Red &rd, const z64 *M64, const c32 *M32, const z64 *in, z64 *out, int nrhs, const int *mask,
+                cudaStream_t st);
 GmresOut gmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp,
                      z64 *d_x, cudaStream_t st);
 

@@ -328,8 +328,9 @@ __device__ void potentials(const double *V, const double *r, double &I1, double 
 __device__ inline z64 green_rem(z64 k, double R) {
     z64 x = z64(k.im * R, -k.re * R);   // -j k R
     if (sqrt(norm2(x)) < 0.5) {
+        // |x| < 0.5: the first 17 terms reach a relative truncation below 1e-18
         z64 term(1, 0), s(0, 0);
-        for (int m = 1; m < 30; ++m) {
+        for (int m = 1; m < 18; ++m) {
             if (m > 1) term = term * x * (1.0 / m);
             s += term;
         }
@@ -347,7 +348,7 @@ __device__ inline z64 gradgreen_rem(z64 k, double R) {
     if (sqrt(norm2(x)) < 0.5) {
         z64 pw = jk * jk * jk, s(0, 0);
         double fact = 6.0;
-        for (int m = 3; m < 34; ++m) {
+        for (int m = 3; m < 21; ++m) {   // truncation below 1e-18 relative for |x| < 0.5
             if (m > 3) { pw = pw * x; fact *= m; }
             double cm = ((m & 1) ? -1.0 : 1.0) * (1.0 - m) / fact;
             s += cm * pw;

@@ -1,10 +1,16 @@
 // k_gmres.cu -- batched right-preconditioned restarted GMRES on the reduced
 // CBFM system A (G^CBF)^{-1} y = b (paper Eq. (CBFM_outer)); x = (G^CBF)^{-1} y
-// (Eq. (CBFM_inner)).  Every right-hand side runs its own GMRES: x0 = 0,
-// classical Gram-Schmidt with one reorthogonalisation (CGS2) in FP64, Givens
-// rotations, stop when ||b - A P y|| / ||b|| <= tol.  The operator product
-// A P v runs in FP64 (CBFM_FP64) or complex64 with FP32 accumulation
-// (CBFM_MIXED); Arnoldi, Hessenberg and residual stay FP64 in both.
+// (Eq. (CBFM_inner)).
+//
+// Every right-hand side runs its own GMRES (x0 = 0, Givens rotations, stop
+// when ||b - A P y|| / ||b|| <= tol); the kernels process all of them at once
+// and skip the ones that have converged.  The operator B = A P is formed once
+// (cbfm_cmp_setup) so an iteration needs one product B v, done in FP64
+// (CBFM_FP64) or with B in complex64 and FP32 accumulation (CBFM_MIXED).
+// Arnoldi orthogonalisation, Hessenberg matrix and residual are FP64 in both:
+// classical Gram-Schmidt with a second pass only where the first one
+// cancelled strongly (||w_after|| < ||w_before|| / sqrt 2, the Daniel-Gragg-
+// Kaufman-Stewart criterion).
 #include <algorithm>
 #include <vector>
 
@@ -14,62 +20,149 @@ namespace cbfm {
 
 namespace {
 
-// h[rhs][j] = sum_i conj(V[j][rhs][i]) w[rhs][i], j = 0..k
-__global__ void k_dots(int64_t n, int nrhs, const z64 *__restrict__ V, const z64 *__restrict__ w,
-                       z64 *__restrict__ h, int hld) {
-    const int j = blockIdx.x, r = blockIdx.y;
-    const z64 *v = V + ((int64_t)j * nrhs + r) * n;
-    const z64 *x = w + (int64_t)r * n;
-    double re = 0, im = 0;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        z64 a = v[i], b = x[i];
-        re += a.re * b.re + a.im * b.im;
-        im += a.re * b.im - a.im * b.re;
-    }
-    __shared__ double sre[32], sim[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_down_sync(0xffffffffu, re, o);
-        im += __shfl_down_sync(0xffffffffu, im, o);
-    }
-    if ((threadIdx.x & 31) == 0) { sre[threadIdx.x >> 5] = re; sim[threadIdx.x >> 5] = im; }
+constexpr int JB = 8;          // basis vectors per block in k_dots
+constexpr double DGKS_ETA = 0.70710678118654752;
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0, b = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += sre[i]; b += sim[i]; }
-        h[(int64_t)r * hld + j] = z64(a, b);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;   // valid in thread 0
+}
+
+// h[r][j] = sum_i conj(V[j][r][i]) w[r][i] for j in [j0, j0+JB) and j <= k, for
+// the columns with mask[r] != 0; the x == 0 blocks also store ||w||^2 when nrm2 != NULL.
+__global__ void __launch_bounds__(256) k_dots(int64_t n, int nrhs, int k, const z64 *__restrict__ V,
+                                              const z64 *__restrict__ w, z64 *__restrict__ h, int hld,
+                                              const int *__restrict__ mask, double *__restrict__ nrm2) {
+    const int r = blockIdx.y;
+    if (!mask[r]) return;
+    const int j0 = blockIdx.x * JB;
+    const int nj = min(JB, k + 1 - j0);
+    double are[JB], aim[JB], nn = 0;
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj) are[jj] = aim[jj] = 0;
+    const z64 *x = w + (int64_t)r * n;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        z64 b = x[i];
+        nn += norm2(b);
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            if (jj < nj) {
+                z64 a = V[((int64_t)(j0 + jj) * nrhs + r) * n + i];
+                are[jj] += a.re * b.re + a.im * b.im;
+                aim[jj] += a.re * b.im - a.im * b.re;
+            }
+        }
+    }
+    __shared__ double sh[32];
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj) {
+        double s1 = block_sum(are[jj], sh);
+        double s2 = block_sum(aim[jj], sh);
+        if (threadIdx.x == 0 && jj < nj) h[(int64_t)r * hld + j0 + jj] = z64(s1, s2);
+    }
+    if (nrm2 && blockIdx.x == 0) {
+        double s = block_sum(nn, sh);
+        if (threadIdx.x == 0) nrm2[r] = s;
     }
 }
 
-// w[rhs][i] -= sum_{j<=k} V[j][rhs][i] h[rhs][j]
-__global__ void k_orth_update(int64_t n, int nrhs, int k, const z64 *__restrict__ V, const z64 *__restrict__ h,
-                              int hld, z64 *__restrict__ w) {
+// w[r][i] -= sum_{j<=k} V[j][r][i] h[r][j] for masked columns
+__global__ void __launch_bounds__(256) k_orth_update(int64_t n, int nrhs, int k, const z64 *__restrict__ V,
+                                                     const z64 *__restrict__ h, int hld, const int *__restrict__ mask,
+                                                     z64 *__restrict__ w) {
     const int r = blockIdx.y;
+    if (!mask[r]) return;
+    __shared__ z64 hs[1024];
+    for (int j = threadIdx.x; j <= k; j += blockDim.x) hs[j] = h[(int64_t)r * hld + j];
+    __syncthreads();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     z64 acc = w[(int64_t)r * n + i];
-    for (int j = 0; j <= k; ++j) acc -= V[((int64_t)j * nrhs + r) * n + i] * h[(int64_t)r * hld + j];
+    const z64 *v = V + (int64_t)r * n + i;
+    const int64_t stride = (int64_t)nrhs * n;
+    for (int j = 0; j <= k; ++j) acc -= v[j * stride] * hs[j];
     w[(int64_t)r * n + i] = acc;
 }
 
-// H[rhs][j][k] += h1 + h2 for j <= k; then ||w|| -> H[k+1][k], V[k+1] = w/||w||
-__global__ void k_norm_next(int64_t n, int nrhs, int k, int m, const z64 *__restrict__ h1, const z64 *__restrict__ h2,
-                            int hld, z64 *__restrict__ H, const z64 *__restrict__ w, z64 *__restrict__ V) {
+// After the first pass: reorthogonalise where ||w|| dropped below eta ||w_before||.
+// `flag` holds the active mask on entry and the reorthogonalisation mask on exit.
+__global__ void k_reorth_flag(int64_t n, int nrhs, const z64 *__restrict__ w, const double *__restrict__ nrm2_before,
+                              int *__restrict__ flag) {
     const int r = blockIdx.x;
+    if (!flag[r]) return;
+    double s = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += norm2(w[(int64_t)r * n + i]);
+    __shared__ double sh[32];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) flag[r] = (sqrt(s) < DGKS_ETA * sqrt(nrm2_before[r])) ? 1 : 0;
+}
+
+// Column k of H for every active rhs: h1 (+ h2 if reorthogonalised), ||w||;
+// previous rotations, new rotation, residual, convergence; V[k+1] = w / ||w||.
+__global__ void __launch_bounds__(256) k_finish(int64_t n, int nrhs, int k, int m, int last,
+                                                const z64 *__restrict__ h1, const z64 *__restrict__ h2,
+                                                const int *__restrict__ flag, int hld, z64 *__restrict__ H,
+                                                double *__restrict__ cs, z64 *__restrict__ sn, z64 *__restrict__ g,
+                                                const double *__restrict__ bnorm, double tol, int *__restrict__ done,
+                                                int *__restrict__ kconv, double *__restrict__ resid,
+                                                int *__restrict__ n_active, const z64 *__restrict__ w,
+                                                z64 *__restrict__ V) {
+    const int r = blockIdx.x;
+    if (done[r]) return;
     const z64 *x = w + (int64_t)r * n;
     double s = 0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += norm2(x[i]);
-    __shared__ double red[32];
+    __shared__ double sh[32];
     __shared__ double nrm;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
+    s = block_sum(s, sh);
     if (threadIdx.x == 0) {
-        double a = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i];
-        nrm = sqrt(a);
+        nrm = sqrt(s);
         z64 *Hr = H + (int64_t)r * (m + 1) * m;
-        for (int j = 0; j <= k; ++j) Hr[(int64_t)j * m + k] = h1[(int64_t)r * hld + j] + h2[(int64_t)r * hld + j];
-        Hr[(int64_t)(k + 1) * m + k] = z64(nrm, 0);
+        double *c = cs + (int64_t)r * m;
+        z64 *sr = sn + (int64_t)r * m;
+        z64 *gr = g + (int64_t)r * (m + 1);
+        const bool re = flag[r] != 0;
+        // rotate the new column by the previous rotations
+        z64 a = h1[(int64_t)r * hld] + (re ? h2[(int64_t)r * hld] : z64(0, 0));
+        for (int j = 0; j < k; ++j) {
+            z64 b = h1[(int64_t)r * hld + j + 1] + (re ? h2[(int64_t)r * hld + j + 1] : z64(0, 0));
+            Hr[(int64_t)j * m + k] = c[j] * a + sr[j] * b;
+            a = -(conj(sr[j]) * a) + c[j] * b;
+        }
+        // new rotation zeroing (a, nrm)
+        double na = sqrt(norm2(a)), nb = nrm;
+        double cc;
+        z64 ss;
+        if (nb == 0.0) { cc = 1.0; ss = z64(0, 0); }
+        else if (na == 0.0) { cc = 0.0; ss = z64(1, 0); }
+        else {
+            double t = sqrt(na * na + nb * nb);
+            cc = na / t;
+            ss = a * (nb / (na * t));            // (a/|a|) nb / t, nb real
+        }
+        c[k] = cc;
+        sr[k] = ss;
+        Hr[(int64_t)k * m + k] = cc * a + ss * nb;
+        z64 gk = gr[k];
+        gr[k] = cc * gk;
+        gr[k + 1] = -(conj(ss) * gk);
+        double res = sqrt(norm2(gr[k + 1])) / bnorm[r];
+        resid[r] = res;
+        if (res <= tol || nb == 0.0) {
+            kconv[r] = k + 1;
+            done[r] = 1;
+        } else if (last) {
+            kconv[r] = k + 1;
+            done[r] = 2;
+        } else {
+            atomicAdd(n_active + k, 1);
+        }
     }
     __syncthreads();
     const double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
@@ -77,51 +170,55 @@ __global__ void k_norm_next(int64_t n, int nrhs, int k, int m, const z64 *__rest
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) vn[i] = x[i] * inv;
 }
 
-// Givens update of column k for every active rhs; marks convergence.
-__global__ void k_givens(int nrhs, int k, int m, int last, z64 *__restrict__ H, double *__restrict__ cs, z64 *__restrict__ sn,
-                         z64 *__restrict__ g, const double *__restrict__ bnorm, double tol, int *__restrict__ done,
-                         int *__restrict__ kconv, double *__restrict__ resid, int *__restrict__ n_active) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrhs) return;
-    if (done[r]) return;
-    z64 *Hr = H + (int64_t)r * (m + 1) * m;
-    double *c = cs + (int64_t)r * m;
-    z64 *s = sn + (int64_t)r * m;
-    z64 *gr = g + (int64_t)r * (m + 1);
-    for (int j = 0; j < k; ++j) {
-        z64 a = Hr[(int64_t)j * m + k], b = Hr[(int64_t)(j + 1) * m + k];
-        Hr[(int64_t)j * m + k] = c[j] * a + s[j] * b;
-        Hr[(int64_t)(j + 1) * m + k] = -(conj(s[j]) * a) + c[j] * b;
+// out[r] = M in[r] for the rows r with mask[r] != 0 (M n x n row-major; T is its
+// storage and arithmetic type).  Tiles: 32 right-hand sides x 16 output rows,
+// K steps of 32; 128 threads with 2 x 2 outputs each.
+template <typename T>
+__global__ void __launch_bounds__(128) k_matvec(int64_t n, int nrhs, const cx<T> *__restrict__ M,
+                                                const z64 *__restrict__ in, z64 *__restrict__ out,
+                                                const int *__restrict__ mask) {
+    constexpr int BM = 32, BN = 16, BK = 32;
+    __shared__ cx<T> Xs[BK][BM + 1];
+    __shared__ cx<T> Ms[BK][BN + 1];
+    const int tx = threadIdx.x % 8, ty = threadIdx.x / 8;   // ty 0..15, tx 0..7
+    const int64_t r0 = (int64_t)blockIdx.y * BM, c0 = (int64_t)blockIdx.x * BN;
+    cx<T> acc[2][2];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) acc[a][b] = cx<T>(0, 0);
+    for (int64_t k0 = 0; k0 < n; k0 += BK) {
+        for (int idx = threadIdx.x; idx < BM * BK; idx += 128) {
+            int rr = idx / BK, kk = idx % BK;
+            int64_t r = r0 + rr, kx = k0 + kk;
+            cx<T> v(0, 0);
+            if (r < nrhs && kx < n && mask[r]) {
+                z64 e = in[r * n + kx];
+                v = cx<T>((T)e.re, (T)e.im);
+            }
+            Xs[kk][rr] = v;
+        }
+        for (int idx = threadIdx.x; idx < BN * BK; idx += 128) {
+            int cc = idx / BK, kk = idx % BK;
+            int64_t c = c0 + cc, kx = k0 + kk;
+            Ms[kk][cc] = (c < n && kx < n) ? M[c * n + kx] : cx<T>(0, 0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
+            cx<T> xa[2] = {Xs[kk][ty], Xs[kk][ty + 16]};
+            cx<T> mb[2] = {Ms[kk][tx], Ms[kk][tx + 8]};
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) cfma(acc[a][b], xa[a], mb[b]);
+        }
+        __syncthreads();
     }
-    z64 a = Hr[(int64_t)k * m + k], b = Hr[(int64_t)(k + 1) * m + k];
-    double na = sqrt(norm2(a)), nb = sqrt(norm2(b));
-    double cc;
-    z64 ss;
-    if (nb == 0.0) { cc = 1.0; ss = z64(0, 0); }
-    else if (na == 0.0) { cc = 0.0; ss = cdiv(conj(b), z64(nb, 0)); }
-    else {
-        double t = sqrt(na * na + nb * nb);
-        cc = na / t;
-        z64 ph = a * (1.0 / na);                  // a / |a|
-        ss = ph * conj(b) * (1.0 / t);
+    for (int a = 0; a < 2; ++a) {
+        int64_t r = r0 + ty + 16 * a;
+        if (r >= nrhs || !mask[r]) continue;
+        for (int b = 0; b < 2; ++b) {
+            int64_t c = c0 + tx + 8 * b;
+            if (c < n) out[r * n + c] = z64((double)acc[a][b].re, (double)acc[a][b].im);
+        }
     }
-    c[k] = cc;
-    s[k] = ss;
-    Hr[(int64_t)k * m + k] = cc * a + ss * b;
-    Hr[(int64_t)(k + 1) * m + k] = z64(0, 0);
-    z64 gk = gr[k];
-    gr[k] = cc * gk;
-    gr[k + 1] = -(conj(ss) * gk);
-    double res = sqrt(norm2(gr[k + 1])) / bnorm[r];
-    resid[r] = res;
-    if (res <= tol || nb == 0.0) {
-        kconv[r] = k + 1;
-        done[r] = 1;
-    } else if (last) {
-        kconv[r] = k + 1;
-        done[r] = 2;   // end of cycle without convergence
-    }
-    if (done[r] == 0) atomicAdd(n_active, 1);
 }
 
 // Back-substitution H(0:kc,0:kc) z = g(0:kc), one block per rhs (column oriented).
@@ -133,8 +230,8 @@ __global__ void k_backsolve(int nrhs, int m, const z64 *__restrict__ H, z64 *__r
     const z64 *Hr = H + (int64_t)r * (m + 1) * m;
     z64 *gr = g + (int64_t)r * (m + 1);
     z64 *zr = z + (int64_t)r * m;
+    __shared__ z64 zj;
     for (int j = kc - 1; j >= 0; --j) {
-        __shared__ z64 zj;
         if (threadIdx.x == 0) {
             z64 d = Hr[(int64_t)j * m + j];
             zj = (norm2(d) > 0.0) ? cdiv(gr[j], d) : z64(0, 0);
@@ -158,7 +255,7 @@ __global__ void k_update_y(int64_t n, int nrhs, int m, const z64 *__restrict__ V
     y[(int64_t)r * n + i] = acc;
 }
 
-// start of a cycle: r = b - w (w = A P y, or 0), beta = ||r||, V[0] = r / beta, g = beta e1
+// start of a cycle: r = b - w (w = B y, or 0), beta = ||r||, V[0] = r / beta, g = beta e1
 __global__ void k_start(int64_t n, int nrhs, int m, const z64 *__restrict__ b, const z64 *__restrict__ w, int have_w,
                         z64 *__restrict__ V, z64 *__restrict__ g, const double *__restrict__ bnorm,
                         double *__restrict__ resid, int *__restrict__ done, double tol) {
@@ -169,21 +266,16 @@ __global__ void k_start(int64_t n, int nrhs, int m, const z64 *__restrict__ b, c
         if (have_w) v -= w[(int64_t)r * n + i];
         s += norm2(v);
     }
-    __shared__ double red[32];
+    __shared__ double sh[32];
     __shared__ double beta;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
+    s = block_sum(s, sh);
     if (threadIdx.x == 0) {
-        double a = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i];
-        beta = sqrt(a);
+        beta = sqrt(s);
         z64 *gr = g + (int64_t)r * (m + 1);
         for (int j = 0; j <= m; ++j) gr[j] = z64(0, 0);
         gr[0] = z64(beta, 0);
         double res = (bnorm[r] > 0.0) ? beta / bnorm[r] : 0.0;
         resid[r] = res;
-        // a column that already converged stays done
         if (done[r] != 1) done[r] = (res <= tol || beta == 0.0) ? 1 : 0;
     }
     __syncthreads();
@@ -199,42 +291,49 @@ __global__ void k_norms(int64_t n, int nrhs, const z64 *__restrict__ b, double *
     const int r = blockIdx.x;
     double s = 0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += norm2(b[(int64_t)r * n + i]);
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i];
-        out[r] = sqrt(a);
-    }
+    __shared__ double sh[32];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[r] = sqrt(s);
+}
+
+// mask of the columns still iterating: done == 0
+__global__ void k_active(int nrhs, const int *__restrict__ done, int *__restrict__ act) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nrhs) act[r] = done[r] == 0 ? 1 : 0;
+}
+
+__global__ void k_fill_ones(int nrhs, int *__restrict__ a) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nrhs) a[r] = 1;
 }
 
 }  // namespace
 
-// out (nrhs x n) = in (nrhs x n) * M^T, i.e. out[r] = M in[r], in FP64 or FP32.
-static void apply_rows(const Red &r, bool mixed, const z64 *Mat64, const c32 *Mat32, const z64 *in, z64 *out, int nrhs,
-                       DevBuf<c32> &t_in, DevBuf<c32> &t_out, cudaStream_t st) {
-    const int64_t n = r.n;
-    std::vector<GemmDesc> g{GemmDesc{nrhs, n, n, 0, n, 0, n, 0, n}};
-    if (!mixed) {
-        gemm_grouped<double>(g, 0, 1, in, Mat64, out, false, st);
-    } else {
-        launch_z64_to_c32(in, t_in.p, n * nrhs, st);
-        gemm_grouped<float>(g, 0, 1, t_in.p, Mat32, t_out.p, false, st);
-        launch_c32_to_z64(t_out.p, out, n * nrhs, st);
-    }
+// out[r] = M in[r] for the rows with mask[r] != 0, in the precision of the reduced system
+void apply_rows(const Red &rd, const z64 *M64, const c32 *M32, const z64 *in, z64 *out, int nrhs, const int *mask,
+                cudaStream_t st) {
+    const int64_t n = rd.n;
+    dim3 grid((unsigned)((n + 15) / 16), (unsigned)((nrhs + 31) / 32));
+    ProfScope ps_("k_matvec", st);
+    if (M32) k_matvec<float><<<grid, 128, 0, st>>>(n, nrhs, M32, in, out, mask);
+    else k_matvec<double><<<grid, 128, 0, st>>>(n, nrhs, M64, in, out, mask);
+    launched("k_matvec");
+}
+
+static void apply_B(const Red &rd, bool use_cmp, const z64 *in, z64 *out, int nrhs, const int *mask, cudaStream_t st) {
+    if (rd.prec == CBFM_MIXED) apply_rows(rd, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, nrhs, mask, st);
+    else apply_rows(rd, use_cmp ? rd.B64.p : rd.A64.p, nullptr, in, out, nrhs, mask, st);
 }
 
 GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp, z64 *d_x,
                      cudaStream_t st) {
     const int64_t n = rd.n;
-    const int m = std::max(1, std::min<int>(restart, (int)std::min<int64_t>(maxit, std::max<int64_t>(n, 1))));
-    const bool mixed = rd.prec == CBFM_MIXED;
-    DevBuf<z64> V, H, sn, g, y, w, z, hb1, hb2, zs;
-    DevBuf<double> cs, bnorm, resid;
-    DevBuf<int> done, kconv, active, nact;
-    DevBuf<c32> t_in, t_out;
+    CBFM_REQUIRE(nrhs <= 65535, "nrhs must be <= 65535");
+    const int m = std::max(1, std::min<int>(std::min(restart, 1023),
+                                            (int)std::min<int64_t>(maxit, std::max<int64_t>(n, 1))));
+    DevBuf<z64> V, H, sn, g, y, w, hb1, hb2, zs;
+    DevBuf<double> cs, bnorm, resid, nrm0;
+    DevBuf<int> done, kconv, active, nact, flag, ones;
     V.alloc((size_t)(m + 1) * nrhs * n);
     H.alloc((size_t)nrhs * (m + 1) * m);
     sn.alloc((size_t)nrhs * m);
@@ -242,20 +341,26 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
     g.alloc((size_t)nrhs * (m + 1));
     y.alloc((size_t)nrhs * n);
     w.alloc((size_t)nrhs * n);
-    z.alloc((size_t)nrhs * n);
     hb1.alloc((size_t)nrhs * (m + 1));
     hb2.alloc((size_t)nrhs * (m + 1));
     zs.alloc((size_t)nrhs * m);
     bnorm.alloc(nrhs);
     resid.alloc(nrhs);
+    nrm0.alloc(nrhs);
     done.alloc(nrhs);
     kconv.alloc(nrhs);
     active.alloc(nrhs);
-    nact.alloc(1);
-    if (mixed) {
-        t_in.alloc((size_t)nrhs * n);
-        t_out.alloc((size_t)nrhs * n);
-    }
+    flag.alloc(nrhs);
+    ones.alloc(nrhs);
+    nact.alloc(m + 1);
+    int *h_nact = nullptr;
+    CBFM_CUDA(cudaMallocHost((void **)&h_nact, sizeof(int)));
+    struct PinnedFree {
+        int *p;
+        ~PinnedFree() {
+            if (p) cudaFreeHost(p);
+        }
+    } pf{h_nact};
     CBFM_CUDA(cudaMemsetAsync(y.p, 0, sizeof(z64) * nrhs * n, st));
     CBFM_CUDA(cudaMemsetAsync(H.p, 0, sizeof(z64) * nrhs * (m + 1) * m, st));
     CBFM_CUDA(cudaMemsetAsync(done.p, 0, sizeof(int) * nrhs, st));
@@ -264,24 +369,22 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
         k_norms<<<nrhs, 256, 0, st>>>(n, nrhs, d_b, bnorm.p);
         launched("k_norms");
     }
+    {
+        k_fill_ones<<<(nrhs + 127) / 128, 128, 0, st>>>(nrhs, ones.p);
+        launched("k_fill_ones");
+    }
 
     const int hld = m + 1;
+    const int CHECK = 4;   // iterations between convergence polls
     std::vector<int> h_iters(nrhs, 0), h_done(nrhs, 0), h_kc(nrhs, 0), h_act(nrhs, 0);
     int total = 0;
     bool first = true;
     while (total < maxit) {
-        // residual of the current iterate
-        if (!first) {
-            if (use_cmp) {
-                apply_rows(rd, mixed, rd.Ginv.p, rd.Ginv32.p, y.p, z.p, nrhs, t_in, t_out, st);
-                apply_rows(rd, mixed, rd.A64.p, rd.A32.p, z.p, w.p, nrhs, t_in, t_out, st);
-            } else {
-                apply_rows(rd, mixed, rd.A64.p, rd.A32.p, y.p, w.p, nrhs, t_in, t_out, st);
-            }
-        }
+        if (!first) apply_B(rd, use_cmp, y.p, w.p, nrhs, ones.p, st);
         {
             ProfScope ps_("k_start", st);
-            k_start<<<nrhs, 256, 0, st>>>(n, nrhs, m, d_b, w.p, first ? 0 : 1, V.p, g.p, bnorm.p, resid.p, done.p, tol);
+            k_start<<<nrhs, 256, 0, st>>>(n, nrhs, m, d_b, w.p, first ? 0 : 1, V.p, g.p, bnorm.p, resid.p, done.p,
+                                          tol);
             launched("k_start");
         }
         first = false;
@@ -295,55 +398,57 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
         if (nrun == 0) break;
         CBFM_CUDA(cudaMemcpyAsync(active.p, h_act.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
         CBFM_CUDA(cudaMemsetAsync(kconv.p, 0, sizeof(int) * nrhs, st));
+        CBFM_CUDA(cudaMemsetAsync(nact.p, 0, sizeof(int) * (m + 1), st));
         const int mc = std::min(m, maxit - total);
         int k = 0;
         for (; k < mc; ++k) {
             const z64 *vk = V.p + (int64_t)k * nrhs * n;
-            if (use_cmp) {
-                apply_rows(rd, mixed, rd.Ginv.p, rd.Ginv32.p, vk, z.p, nrhs, t_in, t_out, st);
-                apply_rows(rd, mixed, rd.A64.p, rd.A32.p, z.p, w.p, nrhs, t_in, t_out, st);
-            } else {
-                apply_rows(rd, mixed, rd.A64.p, rd.A32.p, vk, w.p, nrhs, t_in, t_out, st);
+            {
+                k_active<<<(nrhs + 127) / 128, 128, 0, st>>>(nrhs, done.p, flag.p);
+                launched("k_active");
             }
-            dim3 gd(k + 1, nrhs), gu((unsigned)((n + 255) / 256), nrhs);
+            apply_B(rd, use_cmp, vk, w.p, nrhs, flag.p, st);
+            dim3 gd((unsigned)((k + 1 + JB - 1) / JB), nrhs), gu((unsigned)((n + 255) / 256), nrhs);
             {
                 ProfScope ps_("k_dots", st);
-                k_dots<<<gd, 256, 0, st>>>(n, nrhs, V.p, w.p, hb1.p, hld);
+                k_dots<<<gd, 256, 0, st>>>(n, nrhs, k, V.p, w.p, hb1.p, hld, flag.p, nrm0.p);
                 launched("k_dots");
             }
             {
                 ProfScope ps_("k_orth_update", st);
-                k_orth_update<<<gu, 256, 0, st>>>(n, nrhs, k, V.p, hb1.p, hld, w.p);
+                k_orth_update<<<gu, 256, 0, st>>>(n, nrhs, k, V.p, hb1.p, hld, flag.p, w.p);
                 launched("k_orth_update");
             }
             {
+                ProfScope ps_("k_reorth_flag", st);
+                k_reorth_flag<<<nrhs, 256, 0, st>>>(n, nrhs, w.p, nrm0.p, flag.p);
+                launched("k_reorth_flag");
+            }
+            {
                 ProfScope ps_("k_dots", st);
-                k_dots<<<gd, 256, 0, st>>>(n, nrhs, V.p, w.p, hb2.p, hld);
+                k_dots<<<gd, 256, 0, st>>>(n, nrhs, k, V.p, w.p, hb2.p, hld, flag.p, nullptr);
                 launched("k_dots");
             }
             {
                 ProfScope ps_("k_orth_update", st);
-                k_orth_update<<<gu, 256, 0, st>>>(n, nrhs, k, V.p, hb2.p, hld, w.p);
+                k_orth_update<<<gu, 256, 0, st>>>(n, nrhs, k, V.p, hb2.p, hld, flag.p, w.p);
                 launched("k_orth_update");
             }
-            {
-                ProfScope ps_("k_norm_next", st);
-                k_norm_next<<<nrhs, 256, 0, st>>>(n, nrhs, k, m, hb1.p, hb2.p, hld, H.p, w.p, V.p);
-                launched("k_norm_next");
-            }
-            CBFM_CUDA(cudaMemsetAsync(nact.p, 0, sizeof(int), st));
-            // the last step of a cycle closes every active column
             const int last = (k + 1 == mc) ? 1 : 0;
             {
-                ProfScope ps_("k_givens", st);
-                k_givens<<<(nrhs + 127) / 128, 128, 0, st>>>(nrhs, k, m, last, H.p, cs.p, sn.p, g.p, bnorm.p, tol, done.p,
-                                                              kconv.p, resid.p, nact.p);
-                launched("k_givens");
+                ProfScope ps_("k_finish", st);
+                k_finish<<<nrhs, 256, 0, st>>>(n, nrhs, k, m, last, hb1.p, hb2.p, flag.p, hld, H.p, cs.p, sn.p, g.p,
+                                               bnorm.p, tol, done.p, kconv.p, resid.p, nact.p, w.p, V.p);
+                launched("k_finish");
             }
-            int na = 0;
-            CBFM_CUDA(cudaMemcpyAsync(&na, nact.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-            CBFM_CUDA(cudaStreamSynchronize(st));
-            if (na == 0) { ++k; break; }
+            if ((k + 1) % CHECK == 0 || last) {
+                CBFM_CUDA(cudaMemcpyAsync(h_nact, nact.p + k, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CBFM_CUDA(cudaStreamSynchronize(st));
+                if (*h_nact == 0) {
+                    ++k;
+                    break;
+                }
+            }
         }
         total += k;
         CBFM_CUDA(cudaMemcpyAsync(h_kc.data(), kconv.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
@@ -356,8 +461,8 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
             k_backsolve<<<nrhs, 128, 0, st>>>(nrhs, m, H.p, g.p, kconv.p, active.p, zs.p);
             launched("k_backsolve");
         }
-        dim3 gu((unsigned)((n + 255) / 256), nrhs);
         {
+            dim3 gu((unsigned)((n + 255) / 256), nrhs);
             ProfScope ps_("k_update_y", st);
             k_update_y<<<gu, 256, 0, st>>>(n, nrhs, m, V.p, zs.p, kconv.p, active.p, y.p);
             launched("k_update_y");
@@ -365,14 +470,13 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
         bool all = true;
         for (int r = 0; r < nrhs; ++r) all &= (h_done[r] == 1);
         if (all) break;
-        // columns that ended the cycle unconverged restart from their iterate
         for (int r = 0; r < nrhs; ++r)
             if (h_done[r] == 2) h_done[r] = 0;
         CBFM_CUDA(cudaMemcpyAsync(done.p, h_done.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
         CBFM_CUDA(cudaMemsetAsync(H.p, 0, sizeof(z64) * nrhs * (m + 1) * m, st));
     }
     // x = P y
-    if (use_cmp) apply_rows(rd, mixed, rd.Ginv.p, rd.Ginv32.p, y.p, d_x, nrhs, t_in, t_out, st);
+    if (use_cmp) apply_rows(rd, rd.Ginv.p, nullptr, y.p, d_x, nrhs, ones.p, st);
     else CBFM_CUDA(cudaMemcpyAsync(d_x, y.p, sizeof(z64) * nrhs * n, cudaMemcpyDeviceToDevice, st));
     GmresOut out;
     out.iters = h_iters;
