@@ -34,45 +34,58 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return s;   // valid in thread 0
 }
 
-// h[r][j] = sum_i conj(V[j][r][i]) w[r][i] for j in [j0, j0+JB) and j <= k, for
-// the columns with mask[r] != 0; the x == 0 blocks also store ||w||^2 when nrm2 != NULL.
-__global__ void __launch_bounds__(256) k_dots(int64_t n, int nrhs, int k, const z64 *__restrict__ V,
-                                              const z64 *__restrict__ w, z64 *__restrict__ h, int hld,
-                                              const int *__restrict__ mask, double *__restrict__ nrm2) {
+// h[r][j] = sum_i conj(V[j][r][i]) w[r][i], j = j0 + warp, for the columns with
+// mask[r] != 0: one warp per basis vector (JB warps per block), four partial
+// sums per lane to keep the FP64 pipe busy, warp-shuffle reduction only.  The
+// x == 0 blocks also store ||w||^2 when nrm2 != NULL.
+__global__ void __launch_bounds__(32 * JB) k_dots(int64_t n, int nrhs, int k, const z64 *__restrict__ V,
+                                                  const z64 *__restrict__ w, z64 *__restrict__ h, int hld,
+                                                  const int *__restrict__ mask, double *__restrict__ nrm2) {
     const int r = blockIdx.y;
     if (!mask[r]) return;
-    const int j0 = blockIdx.x * JB;
-    const int nj = min(JB, k + 1 - j0);
-    double are[JB], aim[JB], nn = 0;
-#pragma unroll
-    for (int jj = 0; jj < JB; ++jj) are[jj] = aim[jj] = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = blockIdx.x * JB + warp;
     const z64 *x = w + (int64_t)r * n;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        z64 b = x[i];
-        nn += norm2(b);
+    if (j <= k) {
+        const z64 *v = V + ((int64_t)j * nrhs + r) * n;
+        double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+        int64_t i = lane;
+        for (; i + 96 < n; i += 128) {
 #pragma unroll
-        for (int jj = 0; jj < JB; ++jj) {
-            if (jj < nj) {
-                z64 a = V[((int64_t)(j0 + jj) * nrhs + r) * n + i];
-                are[jj] += a.re * b.re + a.im * b.im;
-                aim[jj] += a.re * b.im - a.im * b.re;
+            for (int u = 0; u < 4; ++u) {
+                z64 a = v[i + 32 * u], b = x[i + 32 * u];
+                re[u] += a.re * b.re + a.im * b.im;
+                im[u] += a.re * b.im - a.im * b.re;
             }
         }
+        for (; i < n; i += 32) {
+            z64 a = v[i], b = x[i];
+            re[0] += a.re * b.re + a.im * b.im;
+            im[0] += a.re * b.im - a.im * b.re;
+        }
+        double sr = (re[0] + re[1]) + (re[2] + re[3]), si = (im[0] + im[1]) + (im[2] + im[3]);
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) h[(int64_t)r * hld + j] = z64(sr, si);
     }
-    __shared__ double sh[32];
-#pragma unroll
-    for (int jj = 0; jj < JB; ++jj) {
-        double s1 = block_sum(are[jj], sh);
-        double s2 = block_sum(aim[jj], sh);
-        if (threadIdx.x == 0 && jj < nj) h[(int64_t)r * hld + j0 + jj] = z64(s1, s2);
-    }
-    if (nrm2 && blockIdx.x == 0) {
-        double s = block_sum(nn, sh);
-        if (threadIdx.x == 0) nrm2[r] = s;
+    if (nrm2 && blockIdx.x == 0 && warp == JB - 1) {
+        double s0 = 0, s1 = 0;
+        int64_t i = lane;
+        for (; i + 32 < n; i += 64) {
+            s0 += norm2(x[i]);
+            s1 += norm2(x[i + 32]);
+        }
+        for (; i < n; i += 32) s0 += norm2(x[i]);
+        double s = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) nrm2[r] = s;
     }
 }
 
-// w[r][i] -= sum_{j<=k} V[j][r][i] h[r][j] for masked columns
+// w[r][i] -= sum_{j<=k} V[j][r][i] h[r][j] for masked columns (four
+// independent accumulator pairs per thread)
 __global__ void __launch_bounds__(256) k_orth_update(int64_t n, int nrhs, int k, const z64 *__restrict__ V,
                                                      const z64 *__restrict__ h, int hld, const int *__restrict__ mask,
                                                      z64 *__restrict__ w) {
@@ -83,11 +96,16 @@ __global__ void __launch_bounds__(256) k_orth_update(int64_t n, int nrhs, int k,
     __syncthreads();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    z64 acc = w[(int64_t)r * n + i];
     const z64 *v = V + (int64_t)r * n + i;
     const int64_t stride = (int64_t)nrhs * n;
-    for (int j = 0; j <= k; ++j) acc -= v[j * stride] * hs[j];
-    w[(int64_t)r * n + i] = acc;
+    z64 acc[4] = {w[(int64_t)r * n + i], z64(0, 0), z64(0, 0), z64(0, 0)};
+    int j = 0;
+    for (; j + 3 <= k; j += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] -= v[(j + u) * stride] * hs[j + u];
+    }
+    for (; j <= k; ++j) acc[0] -= v[j * stride] * hs[j];
+    w[(int64_t)r * n + i] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
 // After the first pass: reorthogonalise where ||w|| dropped below eta ||w_before||.
@@ -105,6 +123,8 @@ __global__ void k_reorth_flag(int64_t n, int nrhs, const z64 *__restrict__ w, co
 
 // Column k of H for every active rhs: h1 (+ h2 if reorthogonalised), ||w||;
 // previous rotations, new rotation, residual, convergence; V[k+1] = w / ||w||.
+// The column and the previous rotations are staged in shared memory so the
+// sequential rotation sweep of thread 0 does not wait on global loads.
 __global__ void __launch_bounds__(256) k_finish(int64_t n, int nrhs, int k, int m, int last,
                                                 const z64 *__restrict__ h1, const z64 *__restrict__ h2,
                                                 const int *__restrict__ flag, int hld, z64 *__restrict__ H,
@@ -115,25 +135,33 @@ __global__ void __launch_bounds__(256) k_finish(int64_t n, int nrhs, int k, int 
                                                 z64 *__restrict__ V) {
     const int r = blockIdx.x;
     if (done[r]) return;
+    __shared__ z64 col[1024];
+    __shared__ z64 ssn[1024];
+    __shared__ double scs[1024];
+    const bool re = flag[r] != 0;
+    for (int j = threadIdx.x; j <= k; j += blockDim.x) {
+        z64 v = h1[(int64_t)r * hld + j];
+        if (re) v += h2[(int64_t)r * hld + j];
+        col[j] = v;
+        if (j < k) {
+            scs[j] = cs[(int64_t)r * m + j];
+            ssn[j] = sn[(int64_t)r * m + j];
+        }
+    }
     const z64 *x = w + (int64_t)r * n;
     double s = 0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += norm2(x[i]);
     __shared__ double sh[32];
     __shared__ double nrm;
-    s = block_sum(s, sh);
+    s = block_sum(s, sh);   // contains __syncthreads: col/scs/ssn are visible afterwards
     if (threadIdx.x == 0) {
         nrm = sqrt(s);
-        z64 *Hr = H + (int64_t)r * (m + 1) * m;
-        double *c = cs + (int64_t)r * m;
-        z64 *sr = sn + (int64_t)r * m;
         z64 *gr = g + (int64_t)r * (m + 1);
-        const bool re = flag[r] != 0;
-        // rotate the new column by the previous rotations
-        z64 a = h1[(int64_t)r * hld] + (re ? h2[(int64_t)r * hld] : z64(0, 0));
+        z64 a = col[0];
         for (int j = 0; j < k; ++j) {
-            z64 b = h1[(int64_t)r * hld + j + 1] + (re ? h2[(int64_t)r * hld + j + 1] : z64(0, 0));
-            Hr[(int64_t)j * m + k] = c[j] * a + sr[j] * b;
-            a = -(conj(sr[j]) * a) + c[j] * b;
+            z64 b = col[j + 1];
+            col[j] = scs[j] * a + ssn[j] * b;
+            a = -(conj(ssn[j]) * a) + scs[j] * b;
         }
         // new rotation zeroing (a, nrm)
         double na = sqrt(norm2(a)), nb = nrm;
@@ -146,9 +174,9 @@ __global__ void __launch_bounds__(256) k_finish(int64_t n, int nrhs, int k, int 
             cc = na / t;
             ss = a * (nb / (na * t));            // (a/|a|) nb / t, nb real
         }
-        c[k] = cc;
-        sr[k] = ss;
-        Hr[(int64_t)k * m + k] = cc * a + ss * nb;
+        cs[(int64_t)r * m + k] = cc;
+        sn[(int64_t)r * m + k] = ss;
+        col[k] = cc * a + ss * nb;
         z64 gk = gr[k];
         gr[k] = cc * gk;
         gr[k + 1] = -(conj(ss) * gk);
@@ -165,6 +193,10 @@ __global__ void __launch_bounds__(256) k_finish(int64_t n, int nrhs, int k, int 
         }
     }
     __syncthreads();
+    {
+        z64 *Hr = H + (int64_t)r * (m + 1) * m;
+        for (int j = threadIdx.x; j <= k; j += blockDim.x) Hr[(int64_t)j * m + k] = col[j];
+    }
     const double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
     z64 *vn = V + ((int64_t)(k + 1) * nrhs + r) * n;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) vn[i] = x[i] * inv;
@@ -411,7 +443,7 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
             dim3 gd((unsigned)((k + 1 + JB - 1) / JB), nrhs), gu((unsigned)((n + 255) / 256), nrhs);
             {
                 ProfScope ps_("k_dots", st);
-                k_dots<<<gd, 256, 0, st>>>(n, nrhs, k, V.p, w.p, hb1.p, hld, flag.p, nrm0.p);
+                k_dots<<<gd, 32 * JB, 0, st>>>(n, nrhs, k, V.p, w.p, hb1.p, hld, flag.p, nrm0.p);
                 launched("k_dots");
             }
             {
@@ -426,7 +458,7 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
             }
             {
                 ProfScope ps_("k_dots", st);
-                k_dots<<<gd, 256, 0, st>>>(n, nrhs, k, V.p, w.p, hb2.p, hld, flag.p, nullptr);
+                k_dots<<<gd, 32 * JB, 0, st>>>(n, nrhs, k, V.p, w.p, hb2.p, hld, flag.p, nullptr);
                 launched("k_dots");
             }
             {
