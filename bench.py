@@ -100,6 +100,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (CUDA cores)
+FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+FP64_KERNELS = {"k_dots", "k_orth_update", "k_near_blocks", "k_gj_step", "k_finish", "k_lu_solve", "k_jacobi_svd"}
+FP32_KERNELS = {"k_far", "k_matvec", "k_gemm"}
+
+
+def roofline(name, rec, peaks, peak_src):
+    """Roofline entry for one kernel from the library's CUDA-event profile:
+    achieved = algorithmic work / measured time (both summed over the launches)."""
+    secs = rec["ms"] / 1e3
+    out = {"kernel": name, "launches": rec["launches"], "per_launch_ms": rec["ms"] / max(1, rec["launches"]),
+           "traffic": None}
+    if name in FP64_KERNELS or name in FP32_KERNELS:
+        fp64 = name in FP64_KERNELS
+        peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+        ach = rec.get("flop", 0.0) / secs / 1e12 if secs > 0 and rec.get("flop") else None
+        out.update({"bound": "alu", "unit": "TFLOP/s", "peak": peak, "achieved": ach,
+                    "frac": (ach / peak) if ach else None,
+                    "peak_source": ("nominal FP64 1.25 TFLOP/s (FP64 units, 2070 MHz)" if fp64 else
+                                    "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz")})
+    else:
+        peak = peaks.get("hbm_gbs")
+        ach = rec.get("bytes", 0.0) / secs / 1e9 if secs > 0 and rec.get("bytes") else None
+        out.update({"bound": "hbm", "unit": "GB/s", "peak": peak, "achieved": ach,
+                    "frac": (ach / peak) if ach else None, "peak_source": peak_src})
+    return out
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -107,9 +135,22 @@ def _dist():
     return ws, rank, local
 
 
+WORKLOAD = "cube9216"
+
+
 def workload():
-    d = W.cube_c2(N_RHS)
-    return d
+    """The benchmark workload (cube9216); smaller cases exist for profiler captures."""
+    if WORKLOAD == "cube9216":
+        return W.cube_c2(N_RHS)
+    if WORKLOAD == "cube2304":      # same construction, 8 x 8 squares per face, 16 cells
+        d = W.cube_c2(N_RHS)
+        d.update(mesh=W.cube(8, 1.0), ncell=16)
+        return d
+    if WORKLOAD == "sphere960":
+        d = W.sphere_c1()
+        d["exc"] = W.plane_wave_set(W.fibonacci_dirs(N_RHS // 2))[:N_RHS]
+        return d
+    raise ValueError(WORKLOAD)
 
 
 def cpu_sample(n_blocks: int = 6):
@@ -182,7 +223,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--workload", default="cube9216", choices=["cube9216", "cube2304", "sphere960"],
+                    help="cube9216 is the benchmark; the others are small cases for profiler captures")
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = args.workload
     if args.impl == "reference":
         return run_reference(args)
 
@@ -266,30 +311,17 @@ def main():
     # per-kernel profile of the same steps (CUDA events on the launching stream)
     P.profile(True)
     P.profile_read(reset=True)
-    timed(max(1, min(args.steps, 3)), step)
+    n_prof = max(1, min(args.steps, 3))
+    timed(n_prof, step)
     prof = P.profile_read(reset=True)
     P.profile(False)
     tot = sum(v["ms"] for v in prof.values())
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     peaks, peak_src = _peaks()
     nt, ne = g.nt, mesh.n_edges
     clocks = clk.summary()
-    roof = None
-    if dom[0] == "k_far":
-        far_pairs = nt * nt - (2 * mesh.n_near - nt)
-        flop = far_pairs * 49 * 143.0            # algorithmic FP32 flops of the 7x7 point-pair loop
-        per_launch_ms = dom[1]["ms"] / dom[1]["launches"]
-        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        ach = flop / (per_launch_ms / 1e3) / 1e12
-        roof = {"kernel": "k_far", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz"}
-    else:
-        per_launch_ms = dom[1]["ms"] / dom[1]["launches"]
-        roof = {"kernel": dom[0], "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": None, "traffic": None, "peak_source": peak_src,
-                "per_launch_ms": per_launch_ms}
-    roof["share"] = dom[1]["ms"] / tot if tot else None
+    roof = roofline(dom_name, dom, peaks, peak_src)
+    roof["share"] = dom["ms"] / tot if tot else None
 
     # FP64 GPU path (the metric's denominator) and the mixed-vs-FP64 RCS difference
     fp64 = None
@@ -314,9 +346,11 @@ def main():
                 "gmres_iters": {"min": int(iters.min()), "max": int(iters.max()), "mean": float(iters.mean())},
                 "clocks": clocks, "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(exc_h.numel() * 8),
                                           "d2h_bytes_per_step": int(rcs_h.numel() * 8)},
-                "gpu_launches": int(launches), "roofline": roof, "kernel_ms": {k: v["ms"] for k, v in prof.items()},
+                "gpu_launches": int(launches), "roofline": roof,
+                "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
+                            for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
                 "fp64_path": fp64}
-        if not args.no_cpu and ws == 1:
+        if not args.no_cpu and ws == 1 and WORKLOAD == "cube9216":
             try:
                 line["cpu_baseline"] = cpu_sample()
             except Exception as e:  # pragma: no cover

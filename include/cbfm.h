@@ -203,7 +203,9 @@ int64_t cbfm_launch_count(void);
 /*
  * cbfm_profile -- per-kernel timing with CUDA events recorded on the
  * launching stream around the main kernels (enable != 0 turns it on).
- * cbfm_profile_read writes a JSON object {name: {"launches": n, "ms": t}}
+ * cbfm_profile_read writes a JSON object {name: {"launches": n, "ms": t,
+ * "flop": f, "bytes": b}} (f, b: algorithmic floating-point operations and
+ * bytes attributed to the kernel, 0 where not counted)
  * into buf (capacity cap, NUL-terminated, truncated if short), returns the
  * size needed, and clears the totals when reset != 0.
  */

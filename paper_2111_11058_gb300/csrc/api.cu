@@ -27,6 +27,8 @@ struct PendingEv {
 struct ProfAcc {
     int64_t launches = 0;
     double ms = 0.0;
+    double flop = 0.0;
+    double bytes = 0.0;
 };
 std::mutex g_prof_mu;
 std::vector<PendingEv> g_pending;
@@ -49,6 +51,14 @@ int prof_start(const char *name, cudaStream_t st) {
 void prof_stop(int token, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (token >= 0 && token < (int)g_pending.size()) cudaEventRecord(g_pending[token].b, st);
+}
+
+void prof_add_work(const char *name, double flop, double bytes) {
+    if (!g_prof.load()) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfAcc &a = g_acc[name];
+    a.flop += flop;
+    a.bytes += bytes;
 }
 
 void prof_flush() {
@@ -294,9 +304,10 @@ int64_t cbfm_profile_read(char *buf, int64_t cap, int32_t reset) {
     std::string js = "{";
     bool first = true;
     for (auto &kv : g_acc) {
-        char tmp[256];
-        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f}", first ? "" : ", ", kv.first.c_str(),
-                 (long long)kv.second.launches, kv.second.ms);
+        char tmp[320];
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flop\": %.6e, \"bytes\": %.6e}",
+                 first ? "" : ", ", kv.first.c_str(), (long long)kv.second.launches, kv.second.ms, kv.second.flop,
+                 kv.second.bytes);
         js += tmp;
         first = false;
     }

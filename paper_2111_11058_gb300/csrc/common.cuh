@@ -39,6 +39,8 @@ extern std::atomic<bool> g_prof;
 int prof_start(const char *name, cudaStream_t st);
 void prof_stop(int token, cudaStream_t st);
 void prof_flush();
+// algorithmic work attributed to a kernel name (FP operations, bytes), reported by cbfm_profile_read
+void prof_add_work(const char *name, double flop, double bytes);
 struct ProfScope {
     int tok;
     cudaStream_t st;

@@ -28,6 +28,11 @@ namespace cbfm {
 namespace {
 
 constexpr int NCOMP = 27;   // 3 operators x 3 x 3
+// Floating-point operations of one point pair (both media) in k_far's inner
+// loop, counting an FMA as 2: shared geometry d, R^2, R, 1/R^2, d x rho' (19);
+// per medium: k R, 2-pi reduction, sin/cos argument scaling, amplitude,
+// w G, (1 + jkR), w g, and the S0, S1, W, X accumulations (62).
+constexpr double FAR_FLOP_PER_POINT_PAIR = 19.0 + 2.0 * 62.0;
 
 struct Media {
     double k1r, k1i, k2r, k2i;
@@ -503,6 +508,11 @@ void assemble_rwg(Mesh &m, cx<T> *Zrwg, cudaStream_t st) {
         ProfScope ps_("k_far", st);
         k_far<T><<<g1, 128, 0, st>>>(nt, rec, m.tri64.p, m.tri_vid.p, m.alpha, md, Zloc.p);
         launched("k_far");
+    }
+    {
+        // algorithmic work: far ordered pairs x 49 point pairs x FAR_FLOP_PER_POINT_PAIR; bytes: the local blocks written
+        const double far_pairs = (double)nt * nt - (2.0 * m.n_near - nt);
+        prof_add_work("k_far", far_pairs * 49.0 * FAR_FLOP_PER_POINT_PAIR, (double)NCOMP * nt * nt * sizeof(cx<T>));
     }
     if (m.n_near > 0) {
         int64_t threads = m.n_near * 32;

@@ -326,6 +326,14 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
             for (int64_t b = 0; b < tn; ++b) tiles.push_back(TileRef{(int32_t)i, (int32_t)a, (int32_t)b});
     }
     if (tiles.empty()) return;
+    {
+        double fl = 0, by = 0;
+        for (auto &d : g) {
+            fl += 8.0 * d.M * d.N * d.K;
+            by += (double)(d.M * d.K + d.K * d.N + d.M * d.N) * sizeof(cx<T>);
+        }
+        prof_add_work("k_gemm", fl, by);
+    }
     DevBuf<GemmDesc> dd;
     DevBuf<TileRef> dt;
     dd.alloc(g.size());

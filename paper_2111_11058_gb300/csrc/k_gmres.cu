@@ -110,15 +110,21 @@ __global__ void __launch_bounds__(256) k_orth_update(int64_t n, int nrhs, int k,
 
 // After the first pass: reorthogonalise where ||w|| dropped below eta ||w_before||.
 // `flag` holds the active mask on entry and the reorthogonalisation mask on exit.
-__global__ void k_reorth_flag(int64_t n, int nrhs, const z64 *__restrict__ w, const double *__restrict__ nrm2_before,
-                              int *__restrict__ flag) {
+// `reo_work` accumulates (k + 1) for every reorthogonalised column (work of the second pass).
+__global__ void k_reorth_flag(int64_t n, int nrhs, int k, const z64 *__restrict__ w,
+                              const double *__restrict__ nrm2_before, int *__restrict__ flag,
+                              unsigned long long *__restrict__ reo_work) {
     const int r = blockIdx.x;
     if (!flag[r]) return;
     double s = 0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += norm2(w[(int64_t)r * n + i]);
     __shared__ double sh[32];
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) flag[r] = (sqrt(s) < DGKS_ETA * sqrt(nrm2_before[r])) ? 1 : 0;
+    if (threadIdx.x == 0) {
+        const int f = (sqrt(s) < DGKS_ETA * sqrt(nrm2_before[r])) ? 1 : 0;
+        flag[r] = f;
+        if (f) atomicAdd(reo_work, (unsigned long long)(k + 1));
+    }
 }
 
 // Column k of H for every active rhs: h1 (+ h2 if reorthogonalised), ||w||;
@@ -366,6 +372,8 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
     DevBuf<z64> V, H, sn, g, y, w, hb1, hb2, zs;
     DevBuf<double> cs, bnorm, resid, nrm0;
     DevBuf<int> done, kconv, active, nact, flag, ones;
+    DevBuf<unsigned long long> reo;
+    reo.alloc(1);
     V.alloc((size_t)(m + 1) * nrhs * n);
     H.alloc((size_t)nrhs * (m + 1) * m);
     sn.alloc((size_t)nrhs * m);
@@ -396,6 +404,8 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
     CBFM_CUDA(cudaMemsetAsync(y.p, 0, sizeof(z64) * nrhs * n, st));
     CBFM_CUDA(cudaMemsetAsync(H.p, 0, sizeof(z64) * nrhs * (m + 1) * m, st));
     CBFM_CUDA(cudaMemsetAsync(done.p, 0, sizeof(int) * nrhs, st));
+    CBFM_CUDA(cudaMemsetAsync(reo.p, 0, sizeof(unsigned long long), st));
+    double pass1 = 0.0, nmatvec = 0.0;   // algorithmic work counters (profiling)
     {
         ProfScope ps_("k_norms", st);
         k_norms<<<nrhs, 256, 0, st>>>(n, nrhs, d_b, bnorm.p);
@@ -453,7 +463,7 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
             }
             {
                 ProfScope ps_("k_reorth_flag", st);
-                k_reorth_flag<<<nrhs, 256, 0, st>>>(n, nrhs, w.p, nrm0.p, flag.p);
+                k_reorth_flag<<<nrhs, 256, 0, st>>>(n, nrhs, k, w.p, nrm0.p, flag.p, reo.p);
                 launched("k_reorth_flag");
             }
             {
@@ -487,7 +497,11 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
         CBFM_CUDA(cudaMemcpyAsync(h_done.data(), done.p, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
         CBFM_CUDA(cudaStreamSynchronize(st));
         for (int r = 0; r < nrhs; ++r)
-            if (h_act[r]) h_iters[r] += h_kc[r];
+            if (h_act[r]) {
+                h_iters[r] += h_kc[r];
+                pass1 += 0.5 * (double)h_kc[r] * (h_kc[r] + 1);
+                nmatvec += h_kc[r] + 1;
+            }
         {
             ProfScope ps_("k_backsolve", st);
             k_backsolve<<<nrhs, 128, 0, st>>>(nrhs, m, H.p, g.p, kconv.p, active.p, zs.p);
@@ -518,6 +532,16 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
     CBFM_CUDA(cudaStreamSynchronize(st));
     for (int r = 0; r < nrhs; ++r)
         if (h_done[r] != 1) out.iters[r] = -std::abs(out.iters[r]) - 1;   // marks non-convergence
+    if (g_prof.load()) {
+        unsigned long long p2 = 0;
+        CBFM_CUDA(cudaMemcpy(&p2, reo.p, sizeof(p2), cudaMemcpyDeviceToHost));
+        const double cb = sizeof(z64);
+        // dot products and updates: 8 flops per complex multiply-add, one basis element read each
+        prof_add_work("k_dots", 8.0 * n * (pass1 + p2), cb * n * (pass1 + p2));
+        prof_add_work("k_orth_update", 8.0 * n * (pass1 + p2), cb * n * (pass1 + p2));
+        const double eb = rd.prec == CBFM_MIXED ? sizeof(c32) : sizeof(z64);
+        prof_add_work("k_matvec", 8.0 * n * n * (nmatvec + (use_cmp ? nrhs : 0)), eb * n * n * (nmatvec + 1.0));
+    }
     return out;
 }
 
