@@ -104,9 +104,10 @@ constexpr double K0 = 2.0 * PI;          // lengths in free-space wavelengths
 //   [0,21)  7 quadrature points (x,y,z)      [21,28) weights * area
 //   [28,37) vertices p_0..p_2 (x,y,z)        [37,40) c_a = sign_a l_a / (2 A)
 //   [40,43) centroid                         [43]    longest edge
-//   [44,48) padding
+//   [44,47) FP32 copy only: low parts of the centroid (centroid = hi + lo)
+//   [47]    padding
 constexpr int TRI_REC = 48;
-constexpr int TR_Q = 0, TR_W = 21, TR_P = 28, TR_C = 37, TR_CEN = 40, TR_H = 43;
+constexpr int TR_Q = 0, TR_W = 21, TR_P = 28, TR_C = 37, TR_CEN = 40, TR_H = 43, TR_CLO = 44;
 
 // ---------------------------------------------------------- device memory
 template <typename T>

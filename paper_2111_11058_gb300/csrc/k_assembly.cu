@@ -39,6 +39,38 @@ struct Media {
     double e1r, e1i, e2r, e2i;   // eta1, eta2
 };
 
+// Per-medium constants in the arithmetic type of the far-pair kernel,
+// computed once on the host: k, 4/k^2 and the operator weights of T into
+// Ta = -(eta1 T1 + eta2 T2) and Tb = T1/eta1 + T2/eta2.
+template <typename T>
+struct MediaT {
+    T kr[2], ki[2];
+    T fk2r[2], fk2i[2];          // 4 / k^2
+    T wTar[2], wTai[2];          // -eta_i
+    T wTbr[2], wTbi[2];          // 1 / eta_i
+};
+
+template <typename T>
+MediaT<T> media_t(const Media &md) {
+    MediaT<T> o;
+    const double kr[2] = {md.k1r, md.k2r}, ki[2] = {md.k1i, md.k2i};
+    const double er[2] = {md.e1r, md.e2r}, ei[2] = {md.e1i, md.e2i};
+    for (int i = 0; i < 2; ++i) {
+        o.kr[i] = (T)kr[i];
+        o.ki[i] = (T)ki[i];
+        z64 kk = z64(kr[i], ki[i]) * z64(kr[i], ki[i]);
+        z64 f = cdiv(z64(4.0, 0.0), kk);
+        o.fk2r[i] = (T)f.re;
+        o.fk2i[i] = (T)f.im;
+        o.wTar[i] = (T)-er[i];
+        o.wTai[i] = (T)-ei[i];
+        z64 ie = cdiv(z64(1.0, 0.0), z64(er[i], ei[i]));
+        o.wTbr[i] = (T)ie.re;
+        o.wTbi[i] = (T)ie.im;
+    }
+    return o;
+}
+
 // -------------------------------------------------------------- FP32 trig
 // sin/cos of x >= 0 with a two-constant Cody-Waite reduction by 2 pi (round
 // to nearest multiple with the 1.5*2^23 shifter) and the hardware
@@ -96,13 +128,11 @@ __device__ __forceinline__ bool is_near(const double *rt, const double *rs, cons
 // Entries of one medium from its moments; adds into out[27] with the
 // operator weights (wK for K into Ks; wTa, wTb for T into Ta, Tb).
 template <typename T>
-__device__ __forceinline__ void fold_entries(const Mom<T> &m, T kr, T ki, const T ca[3], const T cb[3],
+__device__ __forceinline__ void fold_entries(const Mom<T> &m, T kr, T ki, cx<T> four_k2, const T ca[3], const T cb[3],
                                              const T pa[3][3], const T pb[3][3], cx<T> wTa, cx<T> wTb,
                                              cx<T> *out) {
-    // -j k and 4/k^2 for complex k
+    // -j k for complex k
     cx<T> mjk(ki, -kr);
-    cx<T> kk = cx<T>(kr, ki) * cx<T>(kr, ki);
-    cx<T> four_k2 = cdiv(cx<T>(4, 0), kk);
     for (int a = 0; a < 3; ++a) {
         for (int b = 0; b < 3; ++b) {
             T cc = ca[a] * cb[b];
@@ -134,11 +164,32 @@ __device__ __forceinline__ void fold_entries(const Mom<T> &m, T kr, T ki, const 
 }
 
 // Stage 1.  Grid: x over trial triangles (blockDim.x each), y over test triangles.
+// Near test for the far kernel: the squared centroid distance in the kernel's
+// type decides all pairs clear of the threshold by a relative margin of 1e-5;
+// only pairs inside that band repeat the exact FP64 test of the near list.
+template <typename T>
+__device__ __forceinline__ bool is_near_t(const T *rt_cen, const T *rt_lo, T ht, const T *rs, const double *rt64,
+                                          const double *rs64, const int32_t *vt, const int32_t *vs, double alpha) {
+    if (shares_vertex(vt, vs)) return true;
+    T d2 = 0;
+    for (int d = 0; d < 3; ++d) {
+        T dd = (rt_cen[d] - rs[TR_CEN + d]);
+        if constexpr (sizeof(T) == 4) dd += (rt_lo[d] - rs[TR_CLO + d]);
+        d2 += dd * dd;
+    }
+    T h = ht > rs[TR_H] ? ht : rs[TR_H];
+    T thr = (T)alpha * h;
+    T thr2 = thr * thr;
+    if (d2 < thr2 * (T)(1.0 - 1e-5)) return true;
+    if (d2 > thr2 * (T)(1.0 + 1e-5)) return false;
+    return is_near(rt64, rs64, vt, vs, alpha);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_far(int nt, const T *__restrict__ rec, const double *__restrict__ rec64,
-                                             const int32_t *__restrict__ vid, double alpha, Media md,
+                                             const int32_t *__restrict__ vid, double alpha, MediaT<T> md,
                                              cx<T> *__restrict__ Zloc) {
-    __shared__ T sq[21], sw[7], sp[9], sc[3], scen[3];
+    __shared__ T sq[21], sw[7], sp[9], sc[3], scen[3], sclo[3], sh_t;
     __shared__ double sc64[TRI_REC];
     __shared__ int32_t sv[3];
     const int t = blockIdx.y;
@@ -151,6 +202,8 @@ __global__ void __launch_bounds__(128) k_far(int nt, const T *__restrict__ rec, 
         else if (i < 37) sp[i - 28] = v;
         else if (i < 40) sc[i - 37] = v;
         else if (i < 43) scen[i - 40] = v;   // centroid in the same frame as the points
+        else if (i == 43) sh_t = v;
+        else if (i < 47) sclo[i - 44] = v;
         sc64[i] = rec64[(int64_t)t * TRI_REC + i];
         if (i < 3) sv[i] = vid[3 * t + i];
     }
@@ -160,18 +213,18 @@ __global__ void __launch_bounds__(128) k_far(int nt, const T *__restrict__ rec, 
     const int64_t plane = (int64_t)nt * nt;
     const int64_t base = (int64_t)t * nt + s;
     int32_t vs[3] = {vid[3 * s], vid[3 * s + 1], vid[3 * s + 2]};
-    if (is_near(sc64, rec64 + (int64_t)s * TRI_REC, sv, vs, alpha)) {
+    if (is_near_t<T>(scen, sclo, sh_t, rs, sc64, rec64 + (int64_t)s * TRI_REC, sv, vs, alpha)) {
         for (int c = 0; c < NCOMP; ++c) Zloc[c * plane + base] = cx<T>(0, 0);
         return;
     }
     // trial data (local to its centroid)
     T cs[3] = {rs[TR_CEN], rs[TR_CEN + 1], rs[TR_CEN + 2]};
     T ct[3] = {scen[0], scen[1], scen[2]};
-    // centroid difference in FP64 for accuracy
+    // centroid difference: hi/lo parts in the FP32 records keep it FP64-accurate
     T dc[3];
-    {
-        const double *r64 = rec64 + (int64_t)s * TRI_REC;
-        for (int d = 0; d < 3; ++d) dc[d] = (T)(sc64[TR_CEN + d] - r64[TR_CEN + d]);
+    for (int d = 0; d < 3; ++d) {
+        dc[d] = ct[d] - cs[d];
+        if constexpr (sizeof(T) == 4) dc[d] += sclo[d] - rs[TR_CLO + d];
     }
     T rq[7][3], wq[7];
 #pragma unroll
@@ -179,9 +232,9 @@ __global__ void __launch_bounds__(128) k_far(int nt, const T *__restrict__ rec, 
         for (int d = 0; d < 3; ++d) rq[q][d] = rs[TR_Q + 3 * q + d] - cs[d];
         wq[q] = rs[TR_W + q];
     }
-    const T kr[2] = {(T)md.k1r, (T)md.k2r};
-    const T ki[2] = {(T)md.k1i, (T)md.k2i};
-    const bool lossy2 = md.k2i != 0.0;
+    const T kr[2] = {md.kr[0], md.kr[1]};
+    const T ki[2] = {md.ki[0], md.ki[1]};
+    const bool lossy2 = md.ki[1] != (T)0;
     const T inv4pi = (T)(1.0 / (4.0 * PI));
     Mom<T> mm[2];
     zero(mm[0]);
@@ -257,10 +310,10 @@ __global__ void __launch_bounds__(128) k_far(int nt, const T *__restrict__ rec, 
     cx<T> out[NCOMP];
     for (int c = 0; c < NCOMP; ++c) out[c] = cx<T>(0, 0);
     // Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2
-    cx<double> e1(md.e1r, md.e1i), e2(md.e2r, md.e2i);
-    cx<double> ie1 = cdiv(cx<double>(1, 0), e1), ie2 = cdiv(cx<double>(1, 0), e2);
-    fold_entries<T>(mm[0], kr[0], ki[0], ca, cb, pa, pb, cx<T>((T)-e1.re, (T)-e1.im), cx<T>((T)ie1.re, (T)ie1.im), out);
-    fold_entries<T>(mm[1], kr[1], ki[1], ca, cb, pa, pb, cx<T>((T)-e2.re, (T)-e2.im), cx<T>((T)ie2.re, (T)ie2.im), out);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        fold_entries<T>(mm[i], kr[i], ki[i], cx<T>(md.fk2r[i], md.fk2i[i]), ca, cb, pa, pb,
+                        cx<T>(md.wTar[i], md.wTai[i]), cx<T>(md.wTbr[i], md.wTbi[i]), out);
     for (int c = 0; c < NCOMP; ++c) Zloc[c * plane + base] = out[c];
 }
 
@@ -506,7 +559,7 @@ void assemble_rwg(Mesh &m, cx<T> *Zrwg, cudaStream_t st) {
     dim3 g1((nt + 127) / 128, nt);
     {
         ProfScope ps_("k_far", st);
-        k_far<T><<<g1, 128, 0, st>>>(nt, rec, m.tri64.p, m.tri_vid.p, m.alpha, md, Zloc.p);
+        k_far<T><<<g1, 128, 0, st>>>(nt, rec, m.tri64.p, m.tri_vid.p, m.alpha, media_t<T>(md), Zloc.p);
         launched("k_far");
     }
     {

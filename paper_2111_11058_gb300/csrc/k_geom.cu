@@ -79,6 +79,12 @@ __global__ void k_tri_records(int64_t nt, const double *__restrict__ V, const in
         else if (i >= TR_CEN && i < TR_H) x -= c[(i - TR_CEN) % 3];
         rec32[t * TRI_REC + i] = (float)x;
     }
+    // centroid as an unevaluated float sum hi + lo, so centroid differences keep FP64-level accuracy
+    for (int d = 0; d < 3; ++d) {
+        double x = r[TR_CEN + d] - c[d];
+        float hi = (float)x;
+        rec32[t * TRI_REC + TR_CLO + d] = (float)(x - (double)hi);
+    }
 }
 
 __device__ inline bool shares_vertex(const int32_t *a, const int32_t *b) {
