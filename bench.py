@@ -323,6 +323,34 @@ def main():
     roof = roofline(dom_name, dom, peaks, peak_src)
     roof["share"] = dom["ms"] / tot if tot else None
 
+    # block GMRES over the 128 right-hand sides (same step otherwise)
+    rcs_blk = torch.zeros_like(rcs_d)
+    blk_state = {}
+
+    def step_block(prec=P.MIXED, out=rcs_blk):
+        red = P.assemble_reduced(mesh, cbf, prec)
+        P.cmp_setup(red)
+        res = P.solve(red, exc_d, tol=GMRES_TOL, maxit=2000, restart=1000, monostatic=True, want_j=False,
+                      out_rcs=out, allow_noconv=True, solver=P.BLOCK)
+        blk_state["iters"] = res.iters.copy()
+        red.free()
+
+    step_block()
+    ts_blk = timed(args.steps, step_block)
+    P.profile(True)
+    P.profile_read(reset=True)
+    timed(1, step_block)
+    prof_blk = P.profile_read(reset=True)
+    P.profile(False)
+    dbn, dbr = max(prof_blk.items(), key=lambda kv: kv[1]["ms"])
+    blk_err = float(np.abs(rcs_blk.sum(-1).cpu().numpy() - rcs_d.sum(-1).cpu().numpy()).max()
+                    / np.abs(rcs_d.sum(-1).cpu().numpy()).max())
+    block = {"value": ws * N_RHS / (float(np.mean(ts_blk)) / 1000.0), "ms_per_step": float(np.mean(ts_blk)),
+             "p99_ms": float(np.percentile(ts_blk, 99)),
+             "block_iters_max": int(blk_state["iters"].max()), "rcs_err_vs_per_rhs": blk_err,
+             "roofline": roofline(dbn, dbr, peaks, peak_src),
+             "kernels_ms": {k: v["ms"] for k, v in sorted(prof_blk.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
+
     # FP64 GPU path (the metric's denominator) and the mixed-vs-FP64 RCS difference
     fp64 = None
     if not args.no_fp64:
@@ -349,7 +377,7 @@ def main():
                 "gpu_launches": int(launches), "roofline": roof,
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
-                "fp64_path": fp64}
+                "fp64_path": fp64, "block_gmres": block}
         if not args.no_cpu and ws == 1 and WORKLOAD == "cube9216":
             try:
                 line["cpu_baseline"] = cpu_sample()

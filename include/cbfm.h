@@ -184,10 +184,16 @@ cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream);
  *           4 pi |F_theta|^2, 4 pi |F_phi|^2, or NULL
  *   iters_out (nrhs) int32 GMRES iterations, or NULL
  *   resid_out (nrhs) float64 final relative residuals, or NULL
+ *   solver  0: one GMRES per right-hand side (maxit / restart count Arnoldi
+ *           steps, iters_out the steps to convergence);
+ *           1: block GMRES over groups of up to 256 right-hand sides sharing one
+ *           block Krylov space (maxit counts block iterations, restart caps the
+ *           basis dimension, iters_out is the block iteration of convergence);
+ *           each right-hand side still stops on its own residual criterion.
  * Returns CBFM_ENOCONV when some RHS did not converge within maxit.
  */
 cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double tol, int32_t maxit,
-                       int32_t restart, int32_t use_cmp, double *j_out, const double *obs,
+                       int32_t restart, int32_t use_cmp, int32_t solver, double *j_out, const double *obs,
                        int32_t ndir, double *rcs_out, int32_t *iters_out, double *resid_out,
                        void *stream);
 

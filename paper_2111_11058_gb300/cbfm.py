@@ -65,7 +65,7 @@ def lib():
             "cbfm_red_export_noalloc": [_vp, _vp, _vp],
             "cbfm_cmp_setup": [_vp, _vp],
             "cbfm_gram_export": [_vp, _vp, _vp],
-            "cbfm_solve": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp],
+            "cbfm_solve": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -304,10 +304,14 @@ class SolveResult:
     status: int
 
 
+PER_RHS = 0
+BLOCK = 1
+
+
 def solve(r: Reduced, exc, tol: float = 1e-6, maxit: int = 2000, restart: int = 1000, use_cmp: bool = True,
           obs=None, monostatic: bool = False, want_j: bool = True, out_j=None, out_rcs=None, stream=None,
-          allow_noconv: bool = False) -> SolveResult:
-    """cbfm_solve: GMRES on the reduced system, currents and RCS."""
+          allow_noconv: bool = False, solver: int = PER_RHS) -> SolveResult:
+    """cbfm_solve: GMRES on the reduced system (solver PER_RHS or BLOCK), currents and RCS."""
     e, ke = _ptr(exc, np.float64)
     nrhs = int(ke.shape[0])
     ne = r.cbf.mesh.n_edges
@@ -338,7 +342,7 @@ def solve(r: Reduced, exc, tol: float = 1e-6, maxit: int = 2000, restart: int = 
         rp = ctypes.c_void_p(rcs.ctypes.data)
     else:
         rp = None
-    st = lib().cbfm_solve(r.handle, e, nrhs, float(tol), int(maxit), int(restart), 1 if use_cmp else 0, jp, op,
+    st = lib().cbfm_solve(r.handle, e, nrhs, float(tol), int(maxit), int(restart), 1 if use_cmp else 0, int(solver), jp, op,
                           int(nd), rp, ctypes.c_void_p(iters.ctypes.data), ctypes.c_void_p(resid.ctypes.data),
                           _stream(stream))
     if st != 0 and not (st == 5 and allow_noconv):

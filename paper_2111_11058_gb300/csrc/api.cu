@@ -839,8 +839,8 @@ cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream) {
 }
 
 cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double tol, int32_t maxit, int32_t restart,
-                       int32_t use_cmp, double *j_out, const double *obs, int32_t ndir, double *rcs_out,
-                       int32_t *iters_out, double *resid_out, void *stream) {
+                       int32_t use_cmp, int32_t solver, double *j_out, const double *obs, int32_t ndir,
+                       double *rcs_out, int32_t *iters_out, double *resid_out, void *stream) {
     cbfm_status conv = CBFM_OK;
     cbfm_status st_ = guarded([&] {
         Red *r = (Red *)red;
@@ -879,8 +879,20 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
             k_transpose<<<nblk(n * nrhs), 256, 0, st>>>(n, nrhs, bt.p, b.p);
             launched("k_transpose");
         }
+        CBFM_REQUIRE(solver == 0 || solver == 1, "solver must be 0 (per right-hand side) or 1 (block)");
         x.alloc((size_t)nrhs * n);
-        GmresOut go = gmres_solve(*r, b.p, nrhs, tol, maxit, restart, use_cmp != 0, x.p, st);
+        GmresOut go;
+        if (solver == 0) {
+            go = gmres_solve(*r, b.p, nrhs, tol, maxit, restart, use_cmp != 0, x.p, st);
+        } else {
+            for (int r0 = 0; r0 < nrhs; r0 += 256) {
+                const int cnt = std::min(256, nrhs - r0);
+                GmresOut g = bgmres_solve(*r, b.p + (int64_t)r0 * n, cnt, tol, maxit, restart, use_cmp != 0,
+                                          x.p + (int64_t)r0 * n, st);
+                go.iters.insert(go.iters.end(), g.iters.begin(), g.iters.end());
+                go.resid.insert(go.resid.end(), g.resid.begin(), g.resid.end());
+            }
+        }
         // j = C^MJ x  (internal order, (2 ne) x nrhs)
         jint.alloc((size_t)2 * ne * nrhs);
         std::vector<GemmDesc> jM, jJ;

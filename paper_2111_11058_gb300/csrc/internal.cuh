@@ -95,10 +95,11 @@ struct GemmDesc {
     int64_t M, N, K;
     int64_t a_off, lda, b_off, ldb, c_off, ldc;
 };
-// C[g] = op(A[g]) * op(B[g]) (+ C when accumulate); opA/opB: 0 = N, 1 = T, 2 = H
+// C[g] = op(A[g]) * op(B[g]) (+ C when accumulate); opA/opB: 0 = N, 1 = T, 2 = H, 3 = conj
+// alpha scales the product (C = alpha op(A) op(B) [+ C]).
 template <typename T>
 void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> *A, const cx<T> *B, cx<T> *C,
-                  bool accumulate, cudaStream_t st);
+                  bool accumulate, cudaStream_t st, double alpha = 1.0);
 // Solve Z_b X_b = V_b in place (V overwritten by X) for nb independent systems of size n_b x n_b, s columns;
 // Z and V are overwritten. Returns singular flag per system in d_info (1 = zero pivot).
 void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, const int *h_n, int s, z64 *Z, z64 *V,
@@ -118,6 +119,10 @@ void apply_rows(const Red &rd, const z64 *M64, const c32 *M32, const z64 *in, z6
                 cudaStream_t st);
 GmresOut gmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp,
                      z64 *d_x, cudaStream_t st);
+// Block GMRES over all right-hand sides at once (k_bgmres.cu); maxit counts block iterations,
+// restart caps the basis dimension; iters report the block iteration of convergence.
+GmresOut bgmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp,
+                      z64 *d_x, cudaStream_t st);
 
 // export of the reduced matrix without device allocation (noalloc.cu)
 void red_export_noalloc(Red &r, double *A, cudaStream_t st);

@@ -1,0 +1,508 @@
+// k_bgmres.cu -- block GMRES: the right-preconditioned GMRES of paper Eqs.
+// (CBFM_outer)/(CBFM_inner) run on all right-hand sides together, which share
+// the operator B = A (G^CBF)^{-1}.  One block Krylov space
+//   span{R0, B R0, B^2 R0, ...}   (R0 = the block of residuals)
+// serves every right-hand side; each one still stops on its own criterion
+// ||b_c - B y_c|| / ||b_c|| <= tol and the iteration ends when all have.
+// With p right-hand sides the space grows by up to p directions per block
+// iteration, so the orthogonalisation becomes matrix-matrix products.
+//
+// FP64 throughout except the operator product (complex64 B and FP32
+// accumulation in CBFM_MIXED):
+//   * block Arnoldi with block classical Gram-Schmidt applied twice (BCGS2);
+//   * the new block is orthonormalised by Cholesky QR applied twice, the
+//     first Cholesky pivoted so that numerically dependent directions
+//     (saturation of the space, dependent right-hand sides) are dropped;
+//   * the block Hessenberg least-squares problem min ||E1 S - Hbar Z|| is
+//     solved through a QR of Hbar kept up to date block column by block
+//     column (block Gram-Schmidt + Cholesky QR, again applied twice).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace cbfm {
+
+namespace {
+
+constexpr int PCHOL_MAX = 256;
+
+// Pivoted Cholesky M = (P R)^H-style: the symmetrically permuted matrix
+// P^T M P = R^H R with R upper trapezoidal (rank x m).  One block, all data in
+// global memory.  pivot == 0 keeps the order.  A diagonal below
+// tol * max(initial diagonal) ends the factorisation (rank).  Also returns
+// Rinv = R11^{-1} for the leading rank x rank block.  Row-major m x m buffers.
+__global__ void __launch_bounds__(256) k_pchol(int m, const z64 *__restrict__ M, z64 *__restrict__ A,
+                                               int *__restrict__ perm, z64 *__restrict__ R, z64 *__restrict__ Rinv,
+                                               int *__restrict__ rank_out, double tol, int pivot) {
+    __shared__ double sval[256];
+    __shared__ int sidx[256];
+    __shared__ int s_rank, s_q;
+    __shared__ double s_max0;
+    for (int64_t i = threadIdx.x; i < (int64_t)m * m; i += blockDim.x) {
+        A[i] = M[i];
+        R[i] = z64(0, 0);
+        Rinv[i] = z64(0, 0);
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = i;
+    __syncthreads();
+    // largest initial diagonal
+    {
+        double best = 0.0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) best = fmax(best, A[(int64_t)i * m + i].re);
+        sval[threadIdx.x] = best;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sval[threadIdx.x] = fmax(sval[threadIdx.x], sval[threadIdx.x + w]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s_max0 = sval[0];
+            s_rank = m;
+        }
+        __syncthreads();
+    }
+    const double thr = tol * s_max0;
+    for (int i = 0; i < m; ++i) {
+        // pivot
+        if (pivot) {
+            double best = -1.0;
+            int bi = i;
+            for (int l = i + threadIdx.x; l < m; l += blockDim.x) {
+                double v = A[(int64_t)l * m + l].re;
+                if (v > best) { best = v; bi = l; }
+            }
+            sval[threadIdx.x] = best;
+            sidx[threadIdx.x] = bi;
+            __syncthreads();
+            for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+                if (threadIdx.x < w) {
+                    double o = sval[threadIdx.x + w];
+                    int oi = sidx[threadIdx.x + w];
+                    if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+                        sval[threadIdx.x] = o;
+                        sidx[threadIdx.x] = oi;
+                    }
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) s_q = sidx[0];
+        } else if (threadIdx.x == 0) {
+            s_q = i;
+        }
+        __syncthreads();
+        const int q = s_q;
+        const double dq = A[(int64_t)q * m + q].re;
+        if (!(dq > thr) || dq <= 0.0) {
+            if (threadIdx.x == 0) s_rank = i;
+            __syncthreads();
+            break;
+        }
+        if (q != i) {
+            // swap rows i, q of A, then columns i, q; swap columns i, q of R's finished rows; swap perm
+            for (int c = threadIdx.x; c < m; c += blockDim.x) {
+                z64 t = A[(int64_t)i * m + c];
+                A[(int64_t)i * m + c] = A[(int64_t)q * m + c];
+                A[(int64_t)q * m + c] = t;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < m; r += blockDim.x) {
+                z64 t = A[(int64_t)r * m + i];
+                A[(int64_t)r * m + i] = A[(int64_t)r * m + q];
+                A[(int64_t)r * m + q] = t;
+                if (r < i) {
+                    z64 u = R[(int64_t)r * m + i];
+                    R[(int64_t)r * m + i] = R[(int64_t)r * m + q];
+                    R[(int64_t)r * m + q] = u;
+                }
+            }
+            if (threadIdx.x == 0) {
+                int t = perm[i];
+                perm[i] = perm[q];
+                perm[q] = t;
+            }
+            __syncthreads();
+        }
+        const double d = sqrt(A[(int64_t)i * m + i].re);
+        for (int l = i + threadIdx.x; l < m; l += blockDim.x)
+            R[(int64_t)i * m + l] = (l == i) ? z64(d, 0) : A[(int64_t)i * m + l] * (1.0 / d);
+        __syncthreads();
+        const int rem = m - i - 1;
+        for (int64_t idx = threadIdx.x; idx < (int64_t)rem * rem; idx += blockDim.x) {
+            int l = i + 1 + (int)(idx / rem), c = i + 1 + (int)(idx % rem);
+            A[(int64_t)l * m + c] -= conj(R[(int64_t)i * m + l]) * R[(int64_t)i * m + c];
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    const int r = s_rank;
+    // Rinv = R11^{-1}, row by row from the bottom
+    for (int k = r - 1; k >= 0; --k) {
+        const z64 dk = cdiv(z64(1, 0), R[(int64_t)k * m + k]);
+        for (int j = k + threadIdx.x; j < r; j += blockDim.x) {
+            if (j == k) {
+                Rinv[(int64_t)k * m + k] = dk;
+            } else {
+                z64 s(0, 0);
+                for (int l = k + 1; l <= j; ++l) s += R[(int64_t)k * m + l] * Rinv[(int64_t)l * m + j];
+                Rinv[(int64_t)k * m + j] = -(s * dk);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *rank_out = r;
+}
+
+// X (r x m): X[i][perm[l]] = Rinv[l][i] (l <= i < r), else 0  -> Q = X W for row vectors W.
+// Launched as a single block (r x m <= 65536), so zeroing and filling are ordered by one barrier.
+__global__ void k_make_x(int m, int r, const int *__restrict__ perm, const z64 *__restrict__ Rinv,
+                         z64 *__restrict__ X) {
+    for (int64_t idx = threadIdx.x; idx < (int64_t)r * m; idx += blockDim.x) X[idx] = z64(0, 0);
+    __syncthreads();
+    for (int64_t idx = threadIdx.x; idx < (int64_t)r * r; idx += blockDim.x) {
+        int i = (int)(idx / r), l = (int)(idx % r);
+        if (l <= i) X[(int64_t)i * m + perm[l]] = Rinv[(int64_t)l * m + i];
+    }
+}
+
+// Rfull (r x m, ld m): Rfull[i][perm[l]] = R[i][l]
+__global__ void k_unpermute_r(int m, int r, const int *__restrict__ perm, const z64 *__restrict__ R,
+                              z64 *__restrict__ Rfull) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)r * m;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(idx / m), l = (int)(idx % m);
+        Rfull[(int64_t)i * m + perm[l]] = R[idx];
+    }
+}
+
+// dst[i * ldd + j] = src[j * lds + i] for i < rows, j < cols (transposing copy)
+__global__ void k_copy_t(int rows, int cols, const z64 *__restrict__ src, int64_t lds, z64 *__restrict__ dst,
+                         int64_t ldd) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)rows * cols;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(idx / cols), j = (int)(idx % cols);
+        dst[(int64_t)i * ldd + j] = src[(int64_t)j * lds + i];
+    }
+}
+
+// dst[i * ldd + j] = src[i * lds + j] (+= when add)
+__global__ void k_copy2d(int rows, int cols, const z64 *__restrict__ src, int64_t lds, z64 *__restrict__ dst,
+                         int64_t ldd, int add) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)rows * cols;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(idx / cols), j = (int)(idx % cols);
+        if (add) dst[(int64_t)i * ldd + j] += src[(int64_t)i * lds + j];
+        else dst[(int64_t)i * ldd + j] = src[(int64_t)i * lds + j];
+    }
+}
+
+__global__ void k_zero2d(int rows, int cols, z64 *__restrict__ dst, int64_t ldd) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)rows * cols;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(idx / cols), j = (int)(idx % cols);
+        dst[(int64_t)i * ldd + j] = z64(0, 0);
+    }
+}
+
+// column norms of a rows x cols row-major matrix (one block per column)
+__global__ void k_colnorm(int rows, int cols, const z64 *__restrict__ X, int64_t ld, double *__restrict__ out) {
+    const int c = blockIdx.x;
+    double s = 0;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) s += norm2(X[(int64_t)i * ld + c]);
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += sh[i];
+        out[c] = sqrt(a);
+    }
+}
+
+// row norms of a rows x n matrix (one block per row)
+__global__ void k_rownorm(int64_t n, const z64 *__restrict__ X, double *__restrict__ out) {
+    const int r = blockIdx.x;
+    double s = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += norm2(X[(int64_t)r * n + i]);
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += sh[i];
+        out[r] = sqrt(a);
+    }
+}
+
+__global__ void k_sub_rows(int64_t count, const z64 *__restrict__ a, const z64 *__restrict__ b, z64 *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) out[i] = a[i] - b[i];
+}
+
+__global__ void k_ones(int n, int *a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 1;
+}
+
+inline unsigned nb(int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096)); }
+
+struct Ctx {
+    cudaStream_t st;
+    DevBuf<z64> M, A, R, Rinv, X, T1, Rf;
+    DevBuf<int> perm, rank;
+    int *h_rank = nullptr;
+};
+
+// Pivoted / plain Cholesky on the m x m Gram matrix already in ctx.M; returns rank (host sync).
+int pchol(Ctx &c, int m, double tol, bool pivot) {
+    {
+        ProfScope ps_("k_pchol", c.st);
+        k_pchol<<<1, 256, 0, c.st>>>(m, c.M.p, c.A.p, c.perm.p, c.R.p, c.Rinv.p, c.rank.p, tol, pivot ? 1 : 0);
+        launched("k_pchol");
+    }
+    int r = 0;
+    CBFM_CUDA(cudaMemcpyAsync(&r, c.rank.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    CBFM_CUDA(cudaStreamSynchronize(c.st));
+    return r;
+}
+
+// Cholesky QR (twice) of m row vectors W (m x n, ld n): Q (r x n) to Qdst, and
+// Rfull (r x m, ld m) with W[c] = sum_i Rfull[i][c] Q[i].  Returns r.
+int cholqr2_rows(Ctx &c, const z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double tol) {
+    // pass 1 (pivoted): M[a][b] = sum_k conj(W[a][k]) W[b][k]
+    gemm_grouped<double>({GemmDesc{m, m, n, 0, n, 0, n, 0, m}}, 3, 1, W, W, c.M.p, false, c.st);
+    const int r = pchol(c, m, tol, true);
+    if (r == 0) return 0;
+    k_make_x<<<1, 256, 0, c.st>>>(m, r, c.perm.p, c.Rinv.p, c.X.p);
+    launched("k_make_x");
+    k_zero2d<<<nb((int64_t)r * m), 256, 0, c.st>>>(r, m, c.Rf.p, m);
+    launched("k_zero2d");
+    k_unpermute_r<<<nb((int64_t)r * m), 256, 0, c.st>>>(m, r, c.perm.p, c.R.p, c.Rf.p);
+    launched("k_unpermute_r");
+    // Q1 = X W  -> T1 (r x n)
+    gemm_grouped<double>({GemmDesc{r, n, m, 0, m, 0, n, 0, n}}, 0, 0, c.X.p, W, c.T1.p, false, c.st);
+    // pass 2 (no pivoting) on Q1
+    gemm_grouped<double>({GemmDesc{r, r, n, 0, n, 0, n, 0, r}}, 3, 1, c.T1.p, c.T1.p, c.M.p, false, c.st);
+    const int r2 = pchol(c, r, 0.0, false);
+    if (r2 != r) throw Fail{CBFM_ESINGULAR, "block GMRES: second Cholesky QR pass lost rank"};
+    // Q = Rinv2^T Q1 : X2[i][l] = Rinv2[l][i]  (identity permutation)
+    k_make_x<<<1, 256, 0, c.st>>>(r, r, c.perm.p, c.Rinv.p, c.X.p);
+    launched("k_make_x");
+    gemm_grouped<double>({GemmDesc{r, n, r, 0, r, 0, n, 0, n}}, 0, 0, c.X.p, c.T1.p, Qdst, false, c.st);
+    // Rfull = R2 Rfull1 (r x m), R2 is r x r with leading dimension r
+    gemm_grouped<double>({GemmDesc{r, m, r, 0, r, 0, m, 0, m}}, 0, 0, c.R.p, c.Rf.p, Rfull, false, c.st);
+    return r;
+}
+
+// Cholesky QR (twice) of the p columns of a d x p matrix H (ld ldh) in place:
+// H <- Q (d x p), Rout (p x p, ld p) with H_in = Q Rout; RinvOut = Rout^{-1}
+// (= R1^{-1} R2^{-1} from the two passes).
+void cholqr2_cols(Ctx &c, z64 *H, int d, int p, int64_t ldh, z64 *Rout, z64 *RinvOut, DevBuf<z64> &tmp) {
+    for (int pass = 0; pass < 2; ++pass) {
+        gemm_grouped<double>({GemmDesc{p, p, d, 0, ldh, 0, ldh, 0, p}}, 2, 0, H, H, c.M.p, false, c.st);
+        const int r = pchol(c, p, 0.0, false);
+        if (r != p) throw Fail{CBFM_ESINGULAR, "block GMRES: block Hessenberg lost column rank"};
+        // H <- H Rinv  (via tmp)
+        gemm_grouped<double>({GemmDesc{d, p, p, 0, ldh, 0, p, 0, p}}, 0, 0, H, c.Rinv.p, tmp.p, false, c.st);
+        k_copy2d<<<nb((int64_t)d * p), 256, 0, c.st>>>(d, p, tmp.p, p, H, ldh, 0);
+        launched("k_copy2d");
+        if (pass == 0) {
+            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, c.R.p, p, Rout, p, 0);
+            launched("k_copy2d");
+            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, c.Rinv.p, p, RinvOut, p, 0);
+            launched("k_copy2d");
+        } else {
+            // Rout = R2 R1, RinvOut = R1^{-1} R2^{-1}
+            gemm_grouped<double>({GemmDesc{p, p, p, 0, p, 0, p, 0, p}}, 0, 0, c.R.p, Rout, tmp.p, false, c.st);
+            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, tmp.p, p, Rout, p, 0);
+            launched("k_copy2d");
+            gemm_grouped<double>({GemmDesc{p, p, p, 0, p, 0, p, 0, p}}, 0, 0, RinvOut, c.Rinv.p, tmp.p, false, c.st);
+            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, tmp.p, p, RinvOut, p, 0);
+            launched("k_copy2d");
+        }
+    }
+}
+
+}  // namespace
+
+GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp, z64 *d_x,
+                      cudaStream_t st) {
+    const int64_t n = rd.n;
+    CBFM_REQUIRE(nrhs >= 1 && nrhs <= PCHOL_MAX, "block GMRES handles at most 256 right-hand sides per call");
+    const int p = nrhs;
+    const double rank_tol = 1e-15;
+    // basis capacity (dimensions), at least one block beyond the first
+    const int64_t dcap = std::max<int64_t>(2 * p, std::min<int64_t>((int64_t)std::max(restart, 2 * p), n + p));
+    const int64_t dcap2 = dcap + p;
+    Ctx c;
+    c.st = st;
+    c.M.alloc((size_t)p * p);
+    c.A.alloc((size_t)p * p);
+    c.R.alloc((size_t)p * p);
+    c.Rinv.alloc((size_t)p * p);
+    c.X.alloc((size_t)p * p);
+    c.Rf.alloc((size_t)p * p);
+    c.T1.alloc((size_t)p * n);
+    c.perm.alloc(p);
+    c.rank.alloc(1);
+    DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw;
+    DevBuf<double> bnorm, rnorm;
+    DevBuf<int> ones;
+    V.alloc((size_t)dcap * n);
+    W.alloc((size_t)p * n);
+    HcT.alloc((size_t)p * dcap);
+    Hn.alloc((size_t)dcap2 * p);
+    Qh.alloc((size_t)dcap2 * dcap);
+    Rh.alloc((size_t)dcap * dcap);
+    Gv.alloc((size_t)dcap * p);
+    E1S.alloc((size_t)dcap2 * p);
+    Rv.alloc((size_t)dcap2 * p);
+    Y.alloc((size_t)p * n);
+    Z.alloc((size_t)dcap * p);
+    tmp.alloc((size_t)std::max<int64_t>(dcap2 * p, p * n));
+    tmp2.alloc((size_t)dcap * p);
+    RinvBlk.alloc((size_t)dcap * p);   // diagonal blocks of Rh^{-1}, stacked (p_j x p_j each, ld p)
+    Rw.alloc((size_t)p * p);
+    bnorm.alloc(p);
+    rnorm.alloc(p);
+    ones.alloc(p);
+    k_ones<<<(p + 127) / 128, 128, 0, st>>>(p, ones.p);
+    launched("k_ones");
+    CBFM_CUDA(cudaMemsetAsync(Y.p, 0, sizeof(z64) * p * n, st));
+    k_rownorm<<<p, 256, 0, st>>>(n, d_b, bnorm.p);
+    launched("k_rownorm");
+    std::vector<double> h_bn(p), h_rn(p);
+    CBFM_CUDA(cudaMemcpyAsync(h_bn.data(), bnorm.p, sizeof(double) * p, cudaMemcpyDeviceToHost, st));
+    CBFM_CUDA(cudaStreamSynchronize(st));
+
+    auto applyB = [&](const z64 *in, z64 *out, int rows) {
+        if (rd.prec == CBFM_MIXED) apply_rows(rd, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, rows, ones.p, st);
+        else apply_rows(rd, use_cmp ? rd.B64.p : rd.A64.p, nullptr, in, out, rows, ones.p, st);
+    };
+
+    GmresOut out;
+    out.iters.assign(p, -1);
+    out.resid.assign(p, 1.0);
+    std::vector<int> conv_at(p, -1);
+    int total_blocks = 0;
+    bool all_conv = false, breakdown = false;
+    DevBuf<z64> Rout;
+    Rout.alloc((size_t)p * p);
+    while (!all_conv && !breakdown && total_blocks < maxit) {
+        // residual block R0 = Bm - B Y (rows), orthonormalised: R0[c] = sum_i S[i][c] V1[i]
+        if (total_blocks == 0) {
+            CBFM_CUDA(cudaMemcpyAsync(tmp.p, d_b, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            applyB(Y.p, W.p, p);
+            k_sub_rows<<<nb(p * n), 256, 0, st>>>(p * n, d_b, W.p, tmp.p);
+            launched("k_sub_rows");
+        }
+        CBFM_CUDA(cudaMemsetAsync(E1S.p, 0, sizeof(z64) * dcap2 * p, st));
+        CBFM_CUDA(cudaMemsetAsync(Qh.p, 0, sizeof(z64) * dcap2 * dcap, st));
+        CBFM_CUDA(cudaMemsetAsync(Rh.p, 0, sizeof(z64) * dcap * dcap, st));
+        const int p1 = cholqr2_rows(c, tmp.p, p, n, V.p, E1S.p, rank_tol);
+        if (p1 == 0) {   // residual block is zero: current iterate is exact
+            for (int r = 0; r < p; ++r) {
+                out.resid[r] = 0.0;
+                if (conv_at[r] < 0) conv_at[r] = total_blocks;
+            }
+            all_conv = true;
+            break;
+        }
+        std::vector<int64_t> dims{0, p1};   // dims[i] = first basis index of block i
+        int J = 0;                          // block columns of Hbar processed in this cycle
+        while (true) {
+            const int64_t d0 = dims[J], d1 = dims[J + 1];
+            const int pjc = (int)(d1 - d0);
+            if (dcap - d1 < pjc) break;   // no room for another block: solve and restart
+            // W = B V_J
+            applyB(V.p + d0 * n, W.p, pjc);
+            // block classical Gram-Schmidt, twice; HcT (pjc x d1) collects the coefficients
+            for (int pass = 0; pass < 2; ++pass) {
+                gemm_grouped<double>({GemmDesc{pjc, d1, n, 0, n, 0, n, 0, dcap}}, 0, 2, W.p, V.p, tmp2.p, false, st);
+                gemm_grouped<double>({GemmDesc{pjc, n, d1, 0, dcap, 0, n, 0, n}}, 0, 0, tmp2.p, V.p, W.p, true, st,
+                                     -1.0);
+                k_copy2d<<<nb(pjc * d1), 256, 0, st>>>(pjc, (int)d1, tmp2.p, dcap, HcT.p, dcap, pass);
+                launched("k_copy2d");
+            }
+            // orthonormalise the new block (pivoted: drops dependent directions)
+            const int r = cholqr2_rows(c, W.p, pjc, n, V.p + d1 * n, Rw.p, rank_tol);
+            const int rr = r;
+            const int64_t d2 = d1 + rr;
+            // new block column of Hbar (d2 x pjc, ld p): [C; R_W]
+            k_copy_t<<<nb(d1 * pjc), 256, 0, st>>>((int)d1, pjc, HcT.p, dcap, Hn.p, p);
+            launched("k_copy_t");
+            if (rr > 0) {
+                k_copy2d<<<nb(rr * pjc), 256, 0, st>>>(rr, pjc, Rw.p, pjc, Hn.p + d1 * p, p, 0);
+                launched("k_copy2d");
+            }
+            // QR update of Hbar: project the new column block on the previous Q (twice)
+            if (d0 > 0) {
+                for (int pass = 0; pass < 2; ++pass) {
+                    gemm_grouped<double>({GemmDesc{d0, pjc, d2, 0, dcap, 0, p, 0, p}}, 2, 0, Qh.p, Hn.p, tmp2.p, false,
+                                         st);
+                    gemm_grouped<double>({GemmDesc{d2, pjc, d0, 0, dcap, 0, p, 0, p}}, 0, 0, Qh.p, tmp2.p, Hn.p, true,
+                                         st, -1.0);
+                    k_copy2d<<<nb(d0 * pjc), 256, 0, st>>>((int)d0, pjc, tmp2.p, p, Rh.p + d0, dcap, pass);
+                    launched("k_copy2d");
+                }
+            }
+            cholqr2_cols(c, Hn.p, (int)d2, pjc, p, Rout.p, RinvBlk.p + d0 * p, tmp);
+            k_copy2d<<<nb(d2 * pjc), 256, 0, st>>>((int)d2, pjc, Hn.p, p, Qh.p + d0, dcap, 0);
+            launched("k_copy2d");
+            k_copy2d<<<nb(pjc * pjc), 256, 0, st>>>(pjc, pjc, Rout.p, p, Rh.p + d0 * dcap + d0, dcap, 0);
+            launched("k_copy2d");
+            // projected right-hand side rows and the residual of the least-squares problem
+            gemm_grouped<double>({GemmDesc{pjc, p, d2, 0, p, 0, p, d0 * p, p}}, 2, 0, Hn.p, E1S.p, Gv.p, false, st);
+            CBFM_CUDA(cudaMemcpyAsync(Rv.p, E1S.p, sizeof(z64) * d2 * p, cudaMemcpyDeviceToDevice, st));
+            gemm_grouped<double>({GemmDesc{d2, p, d1, 0, dcap, 0, p, 0, p}}, 0, 0, Qh.p, Gv.p, Rv.p, true, st, -1.0);
+            k_colnorm<<<p, 256, 0, st>>>((int)d2, p, Rv.p, p, rnorm.p);
+            launched("k_colnorm");
+            CBFM_CUDA(cudaMemcpyAsync(h_rn.data(), rnorm.p, sizeof(double) * p, cudaMemcpyDeviceToHost, st));
+            CBFM_CUDA(cudaStreamSynchronize(st));
+            ++J;
+            ++total_blocks;
+            bool all = true;
+            for (int q = 0; q < p; ++q) {
+                const double rel = h_bn[q] > 0 ? h_rn[q] / h_bn[q] : 0.0;
+                out.resid[q] = rel;
+                if (rel <= tol && conv_at[q] < 0) conv_at[q] = total_blocks;
+                all &= (rel <= tol);
+            }
+            dims.push_back(d2);
+            all_conv = all;
+            if (r == 0) breakdown = !all;   // invariant subspace: least-squares solution is final
+            if (all || r == 0 || total_blocks >= maxit) break;
+        }
+        // solve Rh Z = Gv (block back substitution) and update Y += Z^T V
+        const int64_t dJ = dims[J];
+        for (int i = J - 1; i >= 0; --i) {
+            const int64_t a0 = dims[i], a1 = dims[i + 1];
+            const int pi = (int)(a1 - a0);
+            k_copy2d<<<nb(pi * p), 256, 0, st>>>(pi, p, Gv.p + a0 * p, p, tmp2.p, p, 0);
+            launched("k_copy2d");
+            if (a1 < dJ)
+                gemm_grouped<double>({GemmDesc{pi, p, dJ - a1, a0 * dcap + a1, dcap, a1 * p, p, 0, p}}, 0, 0, Rh.p,
+                                     Z.p, tmp2.p, true, st, -1.0);
+            gemm_grouped<double>({GemmDesc{pi, p, pi, a0 * p, p, 0, p, a0 * p, p}}, 0, 0, RinvBlk.p, tmp2.p, Z.p,
+                                 false, st);
+        }
+        gemm_grouped<double>({GemmDesc{p, n, dJ, 0, p, 0, n, 0, n}}, 1, 0, Z.p, V.p, Y.p, true, st);
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        if (breakdown) break;
+    }
+    // x = P y
+    if (use_cmp) apply_rows(rd, rd.Ginv.p, nullptr, Y.p, d_x, p, ones.p, st);
+    else CBFM_CUDA(cudaMemcpyAsync(d_x, Y.p, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
+    CBFM_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < p; ++q) out.iters[q] = conv_at[q] >= 0 ? conv_at[q] : -total_blocks - 1;
+    if (breakdown)
+        for (int q = 0; q < p; ++q)
+            if (conv_at[q] < 0) out.iters[q] = total_blocks;   // exact within the saturated space
+    return out;
+}
+
+}  // namespace cbfm

@@ -21,9 +21,10 @@ struct TileRef {
 template <typename T>
 __device__ __forceinline__ cx<T> load_op(const cx<T> *__restrict__ X, int64_t off, int64_t ld, int64_t r, int64_t c,
                                          int64_t R, int64_t C, int op) {
-    // element (r, c) of op(X) where op(X) is R x C
+    // element (r, c) of op(X) where op(X) is R x C; op 0 = X, 1 = X^T, 2 = X^H, 3 = conj(X)
     if (r >= R || c >= C) return cx<T>(0, 0);
     if (op == 0) return X[off + r * ld + c];
+    if (op == 3) return conj(X[off + r * ld + c]);
     cx<T> v = X[off + c * ld + r];
     return (op == 2) ? conj(v) : v;
 }
@@ -31,7 +32,8 @@ __device__ __forceinline__ cx<T> load_op(const cx<T> *__restrict__ X, int64_t of
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *__restrict__ descs, const TileRef *__restrict__ tiles,
                                               int opA, int opB, const cx<T> *__restrict__ A,
-                                              const cx<T> *__restrict__ B, cx<T> *__restrict__ C, int accumulate) {
+                                              const cx<T> *__restrict__ B, cx<T> *__restrict__ C, int accumulate,
+                                              T alpha) {
     __shared__ cx<T> As[GB_K][GB_M + 1];
     __shared__ cx<T> Bs[GB_K][GB_N + 1];
     const TileRef tr = tiles[blockIdx.x];
@@ -44,13 +46,15 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *__restrict__ descs
     for (int64_t k0 = 0; k0 < d.K; k0 += GB_K) {
         // thread -> element maps chosen so that consecutive threads read consecutive addresses
         for (int idx = threadIdx.x; idx < GB_M * GB_K; idx += 256) {
-            int mm = (opA == 0) ? idx / GB_K : idx % GB_M;
-            int kk = (opA == 0) ? idx % GB_K : idx / GB_M;
+            const bool rowA = (opA == 0 || opA == 3);
+            int mm = rowA ? idx / GB_K : idx % GB_M;
+            int kk = rowA ? idx % GB_K : idx / GB_M;
             As[kk][mm] = load_op(A, d.a_off, d.lda, m0 + mm, k0 + kk, d.M, d.K, opA);
         }
         for (int idx = threadIdx.x; idx < GB_K * GB_N; idx += 256) {
-            int kk = (opB == 0) ? idx / GB_N : idx % GB_K;
-            int nn = (opB == 0) ? idx % GB_N : idx / GB_K;
+            const bool rowB = (opB == 0 || opB == 3);
+            int kk = rowB ? idx / GB_N : idx % GB_K;
+            int nn = rowB ? idx % GB_N : idx / GB_K;
             Bs[kk][nn] = load_op(B, d.b_off, d.ldb, k0 + kk, n0 + nn, d.K, d.N, opB);
         }
         __syncthreads();
@@ -71,8 +75,9 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *__restrict__ descs
             int64_t c = n0 + tx + 16 * j;
             if (c >= d.N) continue;
             cx<T> *p = C + d.c_off + r * d.ldc + c;
-            if (accumulate) *p += acc[i][j];
-            else *p = acc[i][j];
+            cx<T> v = alpha * acc[i][j];
+            if (accumulate) *p += v;
+            else *p = v;
         }
     }
 }
@@ -316,7 +321,7 @@ __global__ void k_to64(const c32 *__restrict__ s, z64 *__restrict__ d, int64_t n
 
 template <typename T>
 void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> *A, const cx<T> *B, cx<T> *C,
-                  bool accumulate, cudaStream_t st) {
+                  bool accumulate, cudaStream_t st, double alpha) {
     if (g.empty()) return;
     std::vector<TileRef> tiles;
     for (size_t i = 0; i < g.size(); ++i) {
@@ -344,7 +349,7 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
         unsigned nb = (unsigned)std::min<size_t>(tiles.size() - t0, 2147483647u);
         {
             ProfScope ps_("k_gemm", st);
-            k_gemm<T><<<nb, 256, 0, st>>>(dd.p, dt.p + t0, opA, opB, A, B, C, accumulate ? 1 : 0);
+            k_gemm<T><<<nb, 256, 0, st>>>(dd.p, dt.p + t0, opA, opB, A, B, C, accumulate ? 1 : 0, (T)alpha);
             launched("k_gemm");
         }
     }
@@ -352,9 +357,9 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
 }
 
 template void gemm_grouped<double>(const std::vector<GemmDesc> &, int, int, const z64 *, const z64 *, z64 *, bool,
-                                   cudaStream_t);
+                                   cudaStream_t, double);
 template void gemm_grouped<float>(const std::vector<GemmDesc> &, int, int, const c32 *, const c32 *, c32 *, bool,
-                                  cudaStream_t);
+                                  cudaStream_t, double);
 
 void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, const int *h_n, int s, z64 *Z, z64 *V,
                       int *d_info, cudaStream_t st) {

@@ -251,3 +251,52 @@ def test_degenerate_eps1_matches_oracle(P):
     P.cmp_setup(red)
     res = P.solve(red, exc, tol=TOL_SOLVE, obs=obs)
     assert _peak_rcs_err(res.rcs.sum(-1), st + sp) < 1e-6
+
+
+# ------------------------------------------------------------ block GMRES
+@pytest.mark.parametrize("prec,tol_rcs", [(0, 1e-8), (1, 1e-4)])
+def test_block_gmres_c1(P, c1, prec, tol_rcs):
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), prec)
+    P.cmp_setup(red)
+    res = P.solve(red, c1["exc"], tol=TOL_SOLVE if prec == 0 else 1e-6, obs=c1["obs"], solver=P.BLOCK)
+    assert _peak_rcs_err(res.rcs.sum(-1), c1["rcs"].sum(-1)) < tol_rcs
+    if prec == 0:
+        jo = c1["ref"]["sol"].j
+        assert np.linalg.norm(res.j - jo) / np.linalg.norm(jo) < 1e-7
+    assert (res.iters >= 1).all()
+
+
+def test_block_matches_per_rhs_many_and_dependent(P, c1):
+    """40 right-hand sides, two of them repeated (the first block is rank deficient):
+    block and per-right-hand-side GMRES reach the same solutions."""
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
+    P.cmp_setup(red)
+    exc = W.plane_wave_set(W.fibonacci_dirs(19))
+    exc = np.vstack([exc, exc[:2]])
+    a = P.solve(red, exc, tol=1e-10, solver=P.PER_RHS)
+    b = P.solve(red, exc, tol=1e-10, solver=P.BLOCK)
+    err = np.linalg.norm(a.j - b.j, axis=0) / np.linalg.norm(a.j, axis=0)
+    assert err.max() < 1e-7
+    assert np.allclose(b.j[:, -2:], b.j[:, :2], rtol=0, atol=1e-9 * np.abs(b.j).max())
+
+
+def test_block_single_rhs_is_gmres(P, c1):
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
+    P.cmp_setup(red)
+    a = P.solve(red, c1["exc"][:1], tol=1e-10, solver=P.PER_RHS)
+    b = P.solve(red, c1["exc"][:1], tol=1e-10, solver=P.BLOCK)
+    assert np.linalg.norm(a.j - b.j) / np.linalg.norm(a.j) < 1e-7
+    assert abs(int(a.iters[0]) - int(b.iters[0])) <= 2
+
+
+def test_block_restart_small_basis(P, c1):
+    """A basis cap far below the saturation size forces restarts; the result is unchanged."""
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
+    P.cmp_setup(red)
+    a = P.solve(red, c1["exc"], tol=1e-9, solver=P.PER_RHS)
+    b = P.solve(red, c1["exc"], tol=1e-9, solver=P.BLOCK, restart=24, maxit=5000)
+    assert np.linalg.norm(a.j - b.j) / np.linalg.norm(a.j) < 1e-6
