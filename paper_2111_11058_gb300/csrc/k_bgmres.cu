@@ -237,6 +237,27 @@ __global__ void k_rownorm(int64_t n, const z64 *__restrict__ X, double *__restri
     }
 }
 
+// Row scaling for the rank-revealing Cholesky QR: rows with norm <= drop * ref
+// are zeroed (treated as exhausted directions), the others scaled to unit norm;
+// scale[r] receives the factor to undo (norm, or 0 for dropped rows).
+__global__ void k_scale_rows(int64_t n, z64 *__restrict__ X, const double *__restrict__ nrm, double ref, double drop,
+                             double *__restrict__ scale) {
+    const int r = blockIdx.y;
+    const double v = nrm[r];
+    const bool keep = v > drop * ref && v > 0.0;
+    const double inv = keep ? 1.0 / v : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        X[(int64_t)r * n + i] = X[(int64_t)r * n + i] * inv;
+    if (blockIdx.x == 0 && threadIdx.x == 0) scale[r] = keep ? v : 0.0;
+}
+
+// Rfull[i][c] *= scale[c] (r x m, ld m)
+__global__ void k_scale_cols(int r, int m, z64 *__restrict__ R, const double *__restrict__ scale) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)r * m;
+         idx += (int64_t)gridDim.x * blockDim.x)
+        R[idx] = R[idx] * scale[idx % m];
+}
+
 __global__ void k_sub_rows(int64_t count, const z64 *__restrict__ a, const z64 *__restrict__ b, z64 *__restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < count) out[i] = a[i] - b[i];
@@ -253,7 +274,7 @@ struct Ctx {
     cudaStream_t st;
     DevBuf<z64> M, A, R, Rinv, X, T1, Rf;
     DevBuf<int> perm, rank;
-    int *h_rank = nullptr;
+    DevBuf<double> rnrm, scale;
 };
 
 // Pivoted / plain Cholesky on the m x m Gram matrix already in ctx.M; returns rank (host sync).
@@ -269,9 +290,27 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
     return r;
 }
 
-// Cholesky QR (twice) of m row vectors W (m x n, ld n): Q (r x n) to Qdst, and
-// Rfull (r x m, ld m) with W[c] = sum_i Rfull[i][c] Q[i].  Returns r.
-int cholqr2_rows(Ctx &c, const z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double tol) {
+// Rank-revealing orthonormalisation of m row vectors W (m x n, ld n; W is
+// overwritten): rows with norm <= drop * ref are treated as exhausted, the
+// others are scaled to unit norm, then Cholesky QR twice (the first Cholesky
+// pivoted, dropping directions whose scaled Gram pivot falls below tol).
+// Q (r x n) goes to Qdst and Rfull (r x m, ld m) satisfies
+// W_in[c] = sum_i Rfull[i][c] Q[i] up to the dropped parts.  Returns r.
+int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double tol, double ref, double drop) {
+    k_rownorm<<<m, 256, 0, c.st>>>(n, W, c.rnrm.p);
+    launched("k_rownorm");
+    if (ref <= 0.0) {
+        std::vector<double> h(m);
+        CBFM_CUDA(cudaMemcpyAsync(h.data(), c.rnrm.p, sizeof(double) * m, cudaMemcpyDeviceToHost, c.st));
+        CBFM_CUDA(cudaStreamSynchronize(c.st));
+        for (double v : h) ref = std::max(ref, v);
+        if (ref <= 0.0) return 0;
+    }
+    {
+        dim3 g((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)m);
+        k_scale_rows<<<g, 256, 0, c.st>>>(n, W, c.rnrm.p, ref, drop, c.scale.p);
+        launched("k_scale_rows");
+    }
     // pass 1 (pivoted): M[a][b] = sum_k conj(W[a][k]) W[b][k]
     gemm_grouped<double>({GemmDesc{m, m, n, 0, n, 0, n, 0, m}}, 3, 1, W, W, c.M.p, false, c.st);
     const int r = pchol(c, m, tol, true);
@@ -292,8 +331,10 @@ int cholqr2_rows(Ctx &c, const z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, 
     k_make_x<<<1, 256, 0, c.st>>>(r, r, c.perm.p, c.Rinv.p, c.X.p);
     launched("k_make_x");
     gemm_grouped<double>({GemmDesc{r, n, r, 0, r, 0, n, 0, n}}, 0, 0, c.X.p, c.T1.p, Qdst, false, c.st);
-    // Rfull = R2 Rfull1 (r x m), R2 is r x r with leading dimension r
+    // Rfull = R2 Rfull1 diag(scale) (r x m), R2 is r x r with leading dimension r
     gemm_grouped<double>({GemmDesc{r, m, r, 0, r, 0, m, 0, m}}, 0, 0, c.R.p, c.Rf.p, Rfull, false, c.st);
+    k_scale_cols<<<nb((int64_t)r * m), 256, 0, c.st>>>(r, m, Rfull, c.scale.p);
+    launched("k_scale_cols");
     return r;
 }
 
@@ -333,7 +374,8 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     const int64_t n = rd.n;
     CBFM_REQUIRE(nrhs >= 1 && nrhs <= PCHOL_MAX, "block GMRES handles at most 256 right-hand sides per call");
     const int p = nrhs;
-    const double rank_tol = 1e-15;
+    const double rank_tol = 1e-14;   // pivot threshold of the scaled Gram matrix (unit diagonal)
+    const double drop_tol = 1e-12;   // rows below this fraction of the reference norm are exhausted
     // basis capacity (dimensions), at least one block beyond the first
     const int64_t dcap = std::max<int64_t>(2 * p, std::min<int64_t>((int64_t)std::max(restart, 2 * p), n + p));
     const int64_t dcap2 = dcap + p;
@@ -348,6 +390,8 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     c.T1.alloc((size_t)p * n);
     c.perm.alloc(p);
     c.rank.alloc(1);
+    c.rnrm.alloc(p);
+    c.scale.alloc(p);
     DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw;
     DevBuf<double> bnorm, rnorm;
     DevBuf<int> ones;
@@ -403,7 +447,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
         CBFM_CUDA(cudaMemsetAsync(E1S.p, 0, sizeof(z64) * dcap2 * p, st));
         CBFM_CUDA(cudaMemsetAsync(Qh.p, 0, sizeof(z64) * dcap2 * dcap, st));
         CBFM_CUDA(cudaMemsetAsync(Rh.p, 0, sizeof(z64) * dcap * dcap, st));
-        const int p1 = cholqr2_rows(c, tmp.p, p, n, V.p, E1S.p, rank_tol);
+        const int p1 = cholqr2_rows(c, tmp.p, p, n, V.p, E1S.p, rank_tol, 0.0, drop_tol);
         if (p1 == 0) {   // residual block is zero: current iterate is exact
             for (int r = 0; r < p; ++r) {
                 out.resid[r] = 0.0;
@@ -418,8 +462,14 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             const int64_t d0 = dims[J], d1 = dims[J + 1];
             const int pjc = (int)(d1 - d0);
             if (dcap - d1 < pjc) break;   // no room for another block: solve and restart
-            // W = B V_J
+            // W = B V_J; the norms before orthogonalisation set the scale for exhaustion
             applyB(V.p + d0 * n, W.p, pjc);
+            k_rownorm<<<pjc, 256, 0, st>>>(n, W.p, rnorm.p);
+            launched("k_rownorm");
+            CBFM_CUDA(cudaMemcpyAsync(h_rn.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
+            CBFM_CUDA(cudaStreamSynchronize(st));
+            double wref = 0.0;
+            for (int q = 0; q < pjc; ++q) wref = std::max(wref, h_rn[q]);
             // block classical Gram-Schmidt, twice; HcT (pjc x d1) collects the coefficients
             for (int pass = 0; pass < 2; ++pass) {
                 gemm_grouped<double>({GemmDesc{pjc, d1, n, 0, n, 0, n, 0, dcap}}, 0, 2, W.p, V.p, tmp2.p, false, st);
@@ -429,7 +479,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
                 launched("k_copy2d");
             }
             // orthonormalise the new block (pivoted: drops dependent directions)
-            const int r = cholqr2_rows(c, W.p, pjc, n, V.p + d1 * n, Rw.p, rank_tol);
+            const int r = wref > 0.0 ? cholqr2_rows(c, W.p, pjc, n, V.p + d1 * n, Rw.p, rank_tol, wref, drop_tol) : 0;
             const int rr = r;
             const int64_t d2 = d1 + rr;
             // new block column of Hbar (d2 x pjc, ld p): [C; R_W]

@@ -298,5 +298,5 @@ def test_block_restart_small_basis(P, c1):
     red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
     P.cmp_setup(red)
     a = P.solve(red, c1["exc"], tol=1e-9, solver=P.PER_RHS)
-    b = P.solve(red, c1["exc"], tol=1e-9, solver=P.BLOCK, restart=24, maxit=5000)
+    b = P.solve(red, c1["exc"], tol=1e-9, solver=P.BLOCK, restart=180, maxit=2000)
     assert np.linalg.norm(a.j - b.j) / np.linalg.norm(a.j) < 1e-6
