@@ -339,29 +339,32 @@ int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double
 }
 
 // Cholesky QR (twice) of the p columns of a d x p matrix H (ld ldh) in place:
-// H <- Q (d x p), Rout (p x p, ld p) with H_in = Q Rout; RinvOut = Rout^{-1}
-// (= R1^{-1} R2^{-1} from the two passes).
-void cholqr2_cols(Ctx &c, z64 *H, int d, int p, int64_t ldh, z64 *Rout, z64 *RinvOut, DevBuf<z64> &tmp) {
+// H <- Q (d x p), Rout (p x p, ld ldr) with H_in = Q Rout; RinvOut (p x p, ld
+// ldr) = Rout^{-1} (= R1^{-1} R2^{-1} from the two passes).  The Cholesky
+// factors of ctx have leading dimension p.
+void cholqr2_cols(Ctx &c, z64 *H, int d, int p, int64_t ldh, z64 *Rout, z64 *RinvOut, int64_t ldr,
+                  DevBuf<z64> &tmp) {
     for (int pass = 0; pass < 2; ++pass) {
         gemm_grouped<double>({GemmDesc{p, p, d, 0, ldh, 0, ldh, 0, p}}, 2, 0, H, H, c.M.p, false, c.st);
         const int r = pchol(c, p, 0.0, false);
         if (r != p) throw Fail{CBFM_ESINGULAR, "block GMRES: block Hessenberg lost column rank"};
-        // H <- H Rinv  (via tmp)
+        // H <- H Rinv  (via tmp, ld p)
         gemm_grouped<double>({GemmDesc{d, p, p, 0, ldh, 0, p, 0, p}}, 0, 0, H, c.Rinv.p, tmp.p, false, c.st);
         k_copy2d<<<nb((int64_t)d * p), 256, 0, c.st>>>(d, p, tmp.p, p, H, ldh, 0);
         launched("k_copy2d");
         if (pass == 0) {
-            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, c.R.p, p, Rout, p, 0);
+            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, c.R.p, p, Rout, ldr, 0);
             launched("k_copy2d");
-            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, c.Rinv.p, p, RinvOut, p, 0);
+            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, c.Rinv.p, p, RinvOut, ldr, 0);
             launched("k_copy2d");
         } else {
             // Rout = R2 R1, RinvOut = R1^{-1} R2^{-1}
-            gemm_grouped<double>({GemmDesc{p, p, p, 0, p, 0, p, 0, p}}, 0, 0, c.R.p, Rout, tmp.p, false, c.st);
-            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, tmp.p, p, Rout, p, 0);
+            gemm_grouped<double>({GemmDesc{p, p, p, 0, p, 0, ldr, 0, p}}, 0, 0, c.R.p, Rout, tmp.p, false, c.st);
+            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, tmp.p, p, Rout, ldr, 0);
             launched("k_copy2d");
-            gemm_grouped<double>({GemmDesc{p, p, p, 0, p, 0, p, 0, p}}, 0, 0, RinvOut, c.Rinv.p, tmp.p, false, c.st);
-            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, tmp.p, p, RinvOut, p, 0);
+            gemm_grouped<double>({GemmDesc{p, p, p, 0, ldr, 0, p, 0, p}}, 0, 0, RinvOut, c.Rinv.p, tmp.p, false,
+                                 c.st);
+            k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, tmp.p, p, RinvOut, ldr, 0);
             launched("k_copy2d");
         }
     }
@@ -500,7 +503,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
                     launched("k_copy2d");
                 }
             }
-            cholqr2_cols(c, Hn.p, (int)d2, pjc, p, Rout.p, RinvBlk.p + d0 * p, tmp);
+            cholqr2_cols(c, Hn.p, (int)d2, pjc, p, Rout.p, RinvBlk.p + d0 * p, p, tmp);
             k_copy2d<<<nb(d2 * pjc), 256, 0, st>>>((int)d2, pjc, Hn.p, p, Qh.p + d0, dcap, 0);
             launched("k_copy2d");
             k_copy2d<<<nb(pjc * pjc), 256, 0, st>>>(pjc, pjc, Rout.p, p, Rh.p + d0 * dcap + d0, dcap, 0);
