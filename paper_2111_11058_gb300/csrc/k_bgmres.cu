@@ -137,18 +137,21 @@ __global__ void __launch_bounds__(256) k_pchol(int m, const z64 *__restrict__ M,
     }
     __syncthreads();
     const int r = s_rank;
-    // Rinv = R11^{-1}, row by row from the bottom
+    // Rinv = R11^{-1}, row by row from the bottom; one warp per entry (k, j),
+    // lanes split the sum over l so the global-memory latency overlaps
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int k = r - 1; k >= 0; --k) {
         const z64 dk = cdiv(z64(1, 0), R[(int64_t)k * m + k]);
-        for (int j = k + threadIdx.x; j < r; j += blockDim.x) {
-            if (j == k) {
-                Rinv[(int64_t)k * m + k] = dk;
-            } else {
-                z64 s(0, 0);
-                for (int l = k + 1; l <= j; ++l) s += R[(int64_t)k * m + l] * Rinv[(int64_t)l * m + j];
-                Rinv[(int64_t)k * m + j] = -(s * dk);
+        for (int j = k + 1 + warp; j < r; j += nwarp) {
+            z64 s(0, 0);
+            for (int l = k + 1 + lane; l <= j; l += 32) s += R[(int64_t)k * m + l] * Rinv[(int64_t)l * m + j];
+            for (int o = 16; o > 0; o >>= 1) {
+                s.re += __shfl_xor_sync(0xffffffffu, s.re, o);
+                s.im += __shfl_xor_sync(0xffffffffu, s.im, o);
             }
+            if (lane == 0) Rinv[(int64_t)k * m + j] = -(s * dk);
         }
+        if (threadIdx.x == 0) Rinv[(int64_t)k * m + k] = dk;
         __syncthreads();
     }
     if (threadIdx.x == 0) *rank_out = r;

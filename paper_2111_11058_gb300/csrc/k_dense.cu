@@ -14,8 +14,18 @@ namespace {
 // ------------------------------------------------------------ grouped GEMM
 constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
 
-struct TileRef {
-    int32_t g, tm, tn;
+// Up to GB_MAXG problems per launch travel in the kernel parameters (no
+// device allocation, no host synchronisation).  A single large-K problem with
+// few output tiles is split along K into `ksplit` slices whose partial results
+// are summed in a fixed order by k_splitk_reduce.
+constexpr int GB_MAXG = 160;
+
+struct GemmBatch {
+    int ng;
+    int ksplit;          // >= 1; > 1 only when ng == 1
+    int64_t kchunk;      // K range per slice
+    int64_t tile_off[GB_MAXG + 1];
+    GemmDesc d[GB_MAXG];
 };
 
 template <typename T>
@@ -30,32 +40,51 @@ __device__ __forceinline__ cx<T> load_op(const cx<T> *__restrict__ X, int64_t of
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm(const GemmDesc *__restrict__ descs, const TileRef *__restrict__ tiles,
-                                              int opA, int opB, const cx<T> *__restrict__ A,
-                                              const cx<T> *__restrict__ B, cx<T> *__restrict__ C, int accumulate,
+__global__ void __launch_bounds__(256) k_gemm(const __grid_constant__ GemmBatch bt, int opA, int opB,
+                                              const cx<T> *__restrict__ A, const cx<T> *__restrict__ B,
+                                              cx<T> *__restrict__ C, cx<T> *__restrict__ part, int accumulate,
                                               T alpha) {
     __shared__ cx<T> As[GB_K][GB_M + 1];
     __shared__ cx<T> Bs[GB_K][GB_N + 1];
-    const TileRef tr = tiles[blockIdx.x];
-    const GemmDesc d = descs[tr.g];
+    int64_t tile = blockIdx.x;
+    int ks = 0;
+    if (bt.ksplit > 1) {
+        ks = (int)(tile % bt.ksplit);
+        tile /= bt.ksplit;
+    }
+    int g = 0;
+    {
+        int lo = 0, hi = bt.ng - 1;
+        while (lo < hi) {   // last group with tile_off[g] <= tile
+            int mid = (lo + hi + 1) / 2;
+            if (bt.tile_off[mid] <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        g = lo;
+    }
+    const GemmDesc d = bt.d[g];
+    const int64_t local = tile - bt.tile_off[g];
+    const int64_t ntn = (d.N + GB_N - 1) / GB_N;
+    const int64_t m0 = (local / ntn) * GB_M, n0 = (local % ntn) * GB_N;
+    const int64_t kb = (bt.ksplit > 1) ? (int64_t)ks * bt.kchunk : 0;
+    const int64_t ke = (bt.ksplit > 1) ? min(d.K, kb + bt.kchunk) : d.K;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int64_t m0 = (int64_t)tr.tm * GB_M, n0 = (int64_t)tr.tn * GB_N;
     cx<T> acc[4][4];
     for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) acc[i][j] = cx<T>(0, 0);
-    for (int64_t k0 = 0; k0 < d.K; k0 += GB_K) {
+    for (int64_t k0 = kb; k0 < ke; k0 += GB_K) {
         // thread -> element maps chosen so that consecutive threads read consecutive addresses
         for (int idx = threadIdx.x; idx < GB_M * GB_K; idx += 256) {
             const bool rowA = (opA == 0 || opA == 3);
             int mm = rowA ? idx / GB_K : idx % GB_M;
             int kk = rowA ? idx % GB_K : idx / GB_M;
-            As[kk][mm] = load_op(A, d.a_off, d.lda, m0 + mm, k0 + kk, d.M, d.K, opA);
+            As[kk][mm] = (k0 + kk < ke) ? load_op(A, d.a_off, d.lda, m0 + mm, k0 + kk, d.M, d.K, opA) : cx<T>(0, 0);
         }
         for (int idx = threadIdx.x; idx < GB_K * GB_N; idx += 256) {
             const bool rowB = (opB == 0 || opB == 3);
             int kk = rowB ? idx / GB_N : idx % GB_K;
             int nn = rowB ? idx % GB_N : idx / GB_K;
-            Bs[kk][nn] = load_op(B, d.b_off, d.ldb, k0 + kk, n0 + nn, d.K, d.N, opB);
+            Bs[kk][nn] = (k0 + kk < ke) ? load_op(B, d.b_off, d.ldb, k0 + kk, n0 + nn, d.K, d.N, opB) : cx<T>(0, 0);
         }
         __syncthreads();
 #pragma unroll
@@ -74,11 +103,31 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmDesc *__restrict__ descs
         for (int j = 0; j < 4; ++j) {
             int64_t c = n0 + tx + 16 * j;
             if (c >= d.N) continue;
-            cx<T> *p = C + d.c_off + r * d.ldc + c;
-            cx<T> v = alpha * acc[i][j];
-            if (accumulate) *p += v;
-            else *p = v;
+            if (bt.ksplit > 1) {
+                part[((int64_t)ks * d.M + r) * d.N + c] = acc[i][j];
+            } else {
+                cx<T> *p = C + d.c_off + r * d.ldc + c;
+                cx<T> v = alpha * acc[i][j];
+                if (accumulate) *p += v;
+                else *p = v;
+            }
         }
+    }
+}
+
+// C = alpha * sum_s part[s] (+ C): fixed summation order (deterministic)
+template <typename T>
+__global__ void k_splitk_reduce(GemmDesc d, int ksplit, const cx<T> *__restrict__ part, cx<T> *__restrict__ C,
+                                int accumulate, T alpha) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < d.M * d.N;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / d.N, c = idx % d.N;
+        cx<T> v(0, 0);
+        for (int s = 0; s < ksplit; ++s) v += part[(int64_t)s * d.M * d.N + idx];
+        cx<T> *p = C + d.c_off + r * d.ldc + c;
+        v = alpha * v;
+        if (accumulate) *p += v;
+        else *p = v;
     }
 }
 
@@ -323,14 +372,6 @@ template <typename T>
 void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> *A, const cx<T> *B, cx<T> *C,
                   bool accumulate, cudaStream_t st, double alpha) {
     if (g.empty()) return;
-    std::vector<TileRef> tiles;
-    for (size_t i = 0; i < g.size(); ++i) {
-        if (g[i].M <= 0 || g[i].N <= 0) continue;
-        int64_t tm = (g[i].M + GB_M - 1) / GB_M, tn = (g[i].N + GB_N - 1) / GB_N;
-        for (int64_t a = 0; a < tm; ++a)
-            for (int64_t b = 0; b < tn; ++b) tiles.push_back(TileRef{(int32_t)i, (int32_t)a, (int32_t)b});
-    }
-    if (tiles.empty()) return;
     {
         double fl = 0, by = 0;
         for (auto &d : g) {
@@ -339,21 +380,49 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
         }
         prof_add_work("k_gemm", fl, by);
     }
-    DevBuf<GemmDesc> dd;
-    DevBuf<TileRef> dt;
-    dd.alloc(g.size());
-    dt.alloc(tiles.size());
-    CBFM_CUDA(cudaMemcpyAsync(dd.p, g.data(), g.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice, st));
-    CBFM_CUDA(cudaMemcpyAsync(dt.p, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice, st));
-    for (size_t t0 = 0; t0 < tiles.size(); t0 += 2147483647u) {
-        unsigned nb = (unsigned)std::min<size_t>(tiles.size() - t0, 2147483647u);
+    for (size_t g0 = 0; g0 < g.size(); g0 += GB_MAXG) {
+        GemmBatch bt;
+        bt.ng = (int)std::min<size_t>(GB_MAXG, g.size() - g0);
+        bt.ksplit = 1;
+        bt.kchunk = 0;
+        bt.tile_off[0] = 0;
+        for (int i = 0; i < bt.ng; ++i) {
+            const GemmDesc &d = g[g0 + i];
+            bt.d[i] = d;
+            int64_t t = (d.M > 0 && d.N > 0) ? ((d.M + GB_M - 1) / GB_M) * ((d.N + GB_N - 1) / GB_N) : 0;
+            bt.tile_off[i + 1] = bt.tile_off[i] + t;
+        }
+        const int64_t tiles = bt.tile_off[bt.ng];
+        if (tiles == 0) continue;
+        // few output tiles and a long K: split K so that the GPU fills up
+        const GemmDesc &d0 = bt.d[0];
+        if (bt.ng == 1 && tiles < 2 * 152 && d0.K >= 512) {
+            int64_t S = std::min<int64_t>((2 * 152 + tiles - 1) / tiles, (d0.K + 255) / 256);
+            if (S > 1) {
+                int64_t chunk = (d0.K + S - 1) / S;
+                chunk = (chunk + GB_K - 1) / GB_K * GB_K;
+                bt.kchunk = chunk;
+                bt.ksplit = (int)((d0.K + chunk - 1) / chunk);
+            }
+        }
+        cx<T> *part = nullptr;
+        if (bt.ksplit > 1) {
+            CBFM_CUDA(cudaMallocAsync((void **)&part, sizeof(cx<T>) * bt.ksplit * d0.M * d0.N, st));
+        }
         {
             ProfScope ps_("k_gemm", st);
-            k_gemm<T><<<nb, 256, 0, st>>>(dd.p, dt.p + t0, opA, opB, A, B, C, accumulate ? 1 : 0, (T)alpha);
+            k_gemm<T><<<(unsigned)(tiles * bt.ksplit), 256, 0, st>>>(bt, opA, opB, A, B, C, part,
+                                                                     accumulate ? 1 : 0, (T)alpha);
             launched("k_gemm");
         }
+        if (bt.ksplit > 1) {
+            const int64_t mn = d0.M * d0.N;
+            k_splitk_reduce<T><<<(unsigned)std::min<int64_t>((mn + 255) / 256, 4096), 256, 0, st>>>(
+                d0, bt.ksplit, part, C, accumulate ? 1 : 0, (T)alpha);
+            launched("k_splitk_reduce");
+            CBFM_CUDA(cudaFreeAsync(part, st));
+        }
     }
-    CBFM_CUDA(cudaStreamSynchronize(st));   // descriptor buffers are released on return
 }
 
 template void gemm_grouped<double>(const std::vector<GemmDesc> &, int, int, const z64 *, const z64 *, z64 *, bool,
