@@ -102,8 +102,9 @@ class ClockSampler:
 
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (CUDA cores)
 FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
-FP64_KERNELS = {"k_dots", "k_orth_update", "k_near_blocks", "k_gj_step", "k_finish", "k_lu_solve", "k_jacobi_svd"}
-FP32_KERNELS = {"k_far", "k_matvec", "k_gemm"}
+FP64_KERNELS = {"k_dots", "k_orth_update", "k_near_blocks", "k_gj_step", "k_finish", "k_lu_solve", "k_jacobi_svd",
+                "k_gemm_z64", "k_pchol", "k_trinv"}
+FP32_KERNELS = {"k_far", "k_matvec", "k_gemm_c32"}
 
 
 def roofline(name, rec, peaks, peak_src):
@@ -223,6 +224,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--solver", default="block", choices=["block", "per_rhs"],
+                    help="GMRES variant of the timed step: block GMRES over all right-hand sides, or one per RHS")
     ap.add_argument("--workload", default="cube9216", choices=["cube9216", "cube2304", "sphere960"],
                     help="cube9216 is the benchmark; the others are small cases for profiler captures")
     args = ap.parse_args()
@@ -252,19 +255,24 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     state = {}
+    solver = P.BLOCK if args.solver == "block" else P.PER_RHS
+    other = P.PER_RHS if solver == P.BLOCK else P.BLOCK
 
-    def step(prec=P.MIXED, exc=exc_d, out=rcs_d):
-        red = P.assemble_reduced(mesh, cbf, prec)
-        state["n"] = red.n
-        P.cmp_setup(red)
-        res = P.solve(red, exc, tol=GMRES_TOL, maxit=2000, restart=1000, monostatic=True, want_j=False,
-                      out_rcs=out, allow_noconv=True)
-        red.free()
-        return res
+    def make_step(prec, out, slv, exc=exc_d):
+        def fn():
+            red = P.assemble_reduced(mesh, cbf, prec)
+            state["n"] = red.n
+            P.cmp_setup(red)
+            res = P.solve(red, exc, tol=GMRES_TOL, maxit=2000, restart=1000, monostatic=True, want_j=False,
+                          out_rcs=out, allow_noconv=True, solver=slv)
+            state["iters"] = res.iters.copy()
+            red.free()
+        return fn
 
+    step = make_step(P.MIXED, rcs_d, solver)
     for _ in range(args.warmup):
-        res = step()
-    iters = res.iters.copy()
+        step()
+    iters = state["iters"].copy()
 
     def timed(nsteps, fn):
         ts = []
@@ -297,14 +305,7 @@ def main():
     # end to end through the public API with pinned host buffers
     exc_h = torch.tensor(d["exc"], dtype=torch.float64).pin_memory()
     rcs_h = torch.zeros((N_RHS, 1, 2), dtype=torch.float64).pin_memory()
-
-    def step_host():
-        red = P.assemble_reduced(mesh, cbf, P.MIXED)
-        P.cmp_setup(red)
-        P.solve(red, exc_h.numpy(), tol=GMRES_TOL, maxit=2000, restart=1000, monostatic=True, want_j=False,
-                out_rcs=rcs_h.numpy(), allow_noconv=True)
-        red.free()
-
+    step_host = make_step(P.MIXED, rcs_h.numpy(), solver, exc=exc_h.numpy())
     ts_e2e = timed(max(1, min(args.steps, 3)), step_host)
     e2e = ws * N_RHS / (float(np.mean(ts_e2e)) / 1000.0)
 
@@ -318,45 +319,28 @@ def main():
     tot = sum(v["ms"] for v in prof.values())
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     peaks, peak_src = _peaks()
-    nt, ne = g.nt, mesh.n_edges
     clocks = clk.summary()
     roof = roofline(dom_name, dom, peaks, peak_src)
     roof["share"] = dom["ms"] / tot if tot else None
+    mixed_rcs = rcs_d.sum(-1).cpu().numpy()
 
-    # block GMRES over the 128 right-hand sides (same step otherwise)
-    rcs_blk = torch.zeros_like(rcs_d)
-    blk_state = {}
+    # the other GMRES variant on the same step, for comparison
+    rcs_alt = torch.zeros_like(rcs_d)
+    step_alt = make_step(P.MIXED, rcs_alt, other)
+    step_alt()
+    alt_iters = state["iters"].copy()
+    ts_alt = timed(max(1, min(args.steps, 3)), step_alt)
+    alt_rcs = rcs_alt.sum(-1).cpu().numpy()
+    alt = {"solver": "per_rhs" if other == P.PER_RHS else "block",
+           "value": ws * N_RHS / (float(np.mean(ts_alt)) / 1000.0), "ms_per_step": float(np.mean(ts_alt)),
+           "iters_max": int(alt_iters.max()),
+           "rcs_err_vs_headline": float(np.abs(alt_rcs - mixed_rcs).max() / np.abs(mixed_rcs).max())}
 
-    def step_block(prec=P.MIXED, out=rcs_blk):
-        red = P.assemble_reduced(mesh, cbf, prec)
-        P.cmp_setup(red)
-        res = P.solve(red, exc_d, tol=GMRES_TOL, maxit=2000, restart=1000, monostatic=True, want_j=False,
-                      out_rcs=out, allow_noconv=True, solver=P.BLOCK)
-        blk_state["iters"] = res.iters.copy()
-        red.free()
-
-    step_block()
-    ts_blk = timed(args.steps, step_block)
-    P.profile(True)
-    P.profile_read(reset=True)
-    timed(1, step_block)
-    prof_blk = P.profile_read(reset=True)
-    P.profile(False)
-    dbn, dbr = max(prof_blk.items(), key=lambda kv: kv[1]["ms"])
-    blk_err = float(np.abs(rcs_blk.sum(-1).cpu().numpy() - rcs_d.sum(-1).cpu().numpy()).max()
-                    / np.abs(rcs_d.sum(-1).cpu().numpy()).max())
-    block = {"value": ws * N_RHS / (float(np.mean(ts_blk)) / 1000.0), "ms_per_step": float(np.mean(ts_blk)),
-             "p99_ms": float(np.percentile(ts_blk, 99)),
-             "block_iters_max": int(blk_state["iters"].max()), "rcs_err_vs_per_rhs": blk_err,
-             "roofline": roofline(dbn, dbr, peaks, peak_src),
-             "kernels_ms": {k: v["ms"] for k, v in sorted(prof_blk.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
-
-    # FP64 GPU path (the metric's denominator) and the mixed-vs-FP64 RCS difference
+    # plain FP64 GPU path (the metric's denominator, same solver) and the mixed-vs-FP64 RCS difference
     fp64 = None
     if not args.no_fp64:
         rcs64 = torch.zeros_like(rcs_d)
-        t64 = timed(1, lambda: step(P.FP64, exc_d, rcs64))
-        mixed_rcs = rcs_d.sum(-1).cpu().numpy()
+        t64 = timed(1, make_step(P.FP64, rcs64, solver))
         ref_rcs = rcs64.sum(-1).cpu().numpy()
         err = float(np.abs(mixed_rcs - ref_rcs).max() / np.abs(ref_rcs).max())
         fp64 = {"value": ws * N_RHS / (t64[0] / 1000.0), "ms_per_step": t64[0], "rcs_err_mixed_vs_fp64": err,
@@ -368,6 +352,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": "dielectric cube side 1 lambda0, eps_r 2.5, T=3072, N=9216, 32 cells, "
                                        "s=128 generating waves, 128 monostatic RHS, GMRES tol 1e-6, mixed precision",
+                           "solver": args.solver,
                            "n_cbf": state.get("n"), "l2": "512 MB buffer written between timed steps",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "latency_ms": {"p50": float(np.percentile(ts, 50)), "p99": float(np.percentile(ts, 99))},
@@ -377,7 +362,7 @@ def main():
                 "gpu_launches": int(launches), "roofline": roof,
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
-                "fp64_path": fp64, "block_gmres": block}
+                "fp64_path": fp64, "other_solver": alt}
         if not args.no_cpu and ws == 1 and WORKLOAD == "cube9216":
             try:
                 line["cpu_baseline"] = cpu_sample()

@@ -186,7 +186,7 @@ cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream);
  *   resid_out (nrhs) float64 final relative residuals, or NULL
  *   solver  0: one GMRES per right-hand side (maxit / restart count Arnoldi
  *           steps, iters_out the steps to convergence);
- *           1: block GMRES over groups of up to 256 right-hand sides sharing one
+ *           1: block GMRES over groups of up to 128 right-hand sides sharing one
  *           block Krylov space (maxit counts block iterations, restart caps the
  *           basis dimension, iters_out is the block iteration of convergence);
  *           each right-hand side still stops on its own residual criterion.

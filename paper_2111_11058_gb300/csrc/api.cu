@@ -885,8 +885,8 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
         if (solver == 0) {
             go = gmres_solve(*r, b.p, nrhs, tol, maxit, restart, use_cmp != 0, x.p, st);
         } else {
-            for (int r0 = 0; r0 < nrhs; r0 += 256) {
-                const int cnt = std::min(256, nrhs - r0);
+            for (int r0 = 0; r0 < nrhs; r0 += 128) {
+                const int cnt = std::min(128, nrhs - r0);
                 GmresOut g = bgmres_solve(*r, b.p + (int64_t)r0 * n, cnt, tol, maxit, restart, use_cmp != 0,
                                           x.p + (int64_t)r0 * n, st);
                 go.iters.insert(go.iters.end(), g.iters.begin(), g.iters.end());

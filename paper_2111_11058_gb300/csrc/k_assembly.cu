@@ -382,13 +382,14 @@ __device__ void potentials(const double *V, const double *r, double &I1, double 
     }
 }
 
-// (e^{-jkR} - 1)/(4 pi R), limit -jk/(4 pi) at R = 0 (series for |kR| < 0.5)
+// (e^{-jkR} - 1)/(4 pi R), limit -jk/(4 pi) at R = 0 (power series for |kR| < 0.2,
+// where the direct form would lose digits to cancellation)
 __device__ inline z64 green_rem(z64 k, double R) {
     z64 x = z64(k.im * R, -k.re * R);   // -j k R
-    if (sqrt(norm2(x)) < 0.5) {
-        // |x| < 0.5: the first 17 terms reach a relative truncation below 1e-18
+    if (sqrt(norm2(x)) < 0.2) {
+        // sum_{m>=1} x^{m-1}/m!; for |x| < 0.2 the first 12 terms leave < 1e-19
         z64 term(1, 0), s(0, 0);
-        for (int m = 1; m < 18; ++m) {
+        for (int m = 1; m <= 12; ++m) {
             if (m > 1) term = term * x * (1.0 / m);
             s += term;
         }
@@ -399,14 +400,15 @@ __device__ inline z64 green_rem(z64 k, double R) {
     return z64(e * cs - 1.0, e * sn) * (1.0 / (4.0 * PI * R));
 }
 
-// g + 1/(4 pi R^3) + k^2/(8 pi R), limit j k^3/(12 pi) at R = 0
+// g + 1/(4 pi R^3) + k^2/(8 pi R), limit j k^3/(12 pi) at R = 0 (power series for |kR| < 0.2)
 __device__ inline z64 gradgreen_rem(z64 k, double R) {
     z64 jk(-k.im, k.re);
     z64 x = jk * R;
-    if (sqrt(norm2(x)) < 0.5) {
+    if (sqrt(norm2(x)) < 0.2) {
+        // sum_{m>=3} (-1)^m (1-m)/m! x^m / R^3; 12 terms leave < 1e-19 relative
         z64 pw = jk * jk * jk, s(0, 0);
         double fact = 6.0;
-        for (int m = 3; m < 21; ++m) {   // truncation below 1e-18 relative for |x| < 0.5
+        for (int m = 3; m < 15; ++m) {
             if (m > 3) { pw = pw * x; fact *= m; }
             double cm = ((m & 1) ? -1.0 : 1.0) * (1.0 - m) / fact;
             s += cm * pw;
@@ -420,108 +422,107 @@ __device__ inline z64 gradgreen_rem(z64 k, double R) {
     return g + z64(1.0 / (4.0 * PI * R * R * R), 0) + (k * k) * (1.0 / (8.0 * PI * R));
 }
 
-// One warp per near pair (t <= s): lanes (orientation o, test point p), o in {0,1}, p < 7.
+// One warp per near pair (t <= s).  Lane = 16 o + 8 i + p: orientation o (0:
+// test t / trial s, 1: test s / trial t), medium i, test point p < 7 (lane p = 7
+// of each group of eight idles).  Each lane forms its test point's
+// contribution to the 3 x 3 K and T blocks; groups of eight reduce over p, and
+// lane 0 symmetrises, weights the media into Ks, Ta, Tb and stores both (t,s)
+// and (s,t).
 template <typename T>
-__global__ void k_near_blocks(int64_t npairs, int nt, const int32_t *__restrict__ pairs,
-                              const double *__restrict__ rec, Media md, cx<T> *__restrict__ Zloc) {
+__global__ void __launch_bounds__(128) k_near_blocks(int64_t npairs, int nt, const int32_t *__restrict__ pairs,
+                                                     const double *__restrict__ rec, Media md,
+                                                     cx<T> *__restrict__ Zloc) {
     const int lane = threadIdx.x & 31;
     const int64_t pid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (pid >= npairs) return;
     const int t = pairs[2 * pid], s = pairs[2 * pid + 1];
-    const int o = lane / 7, p = lane % 7;
-    const bool active = lane < 14;
-    // per lane contributions: [medium][K/T][a][b]
-    z64 acc[2][2][9];
-    for (int i = 0; i < 2; ++i)
-        for (int k = 0; k < 2; ++k)
-            for (int c = 0; c < 9; ++c) acc[i][k][c] = z64(0, 0);
-    if (active) {
+    const int o = lane >> 4, med = (lane >> 3) & 1, p = lane & 7;
+    z64 accK[9], accT[9];
+    for (int c = 0; c < 9; ++c) accK[c] = accT[c] = z64(0, 0);
+    if (p < 7) {
         const double *A = rec + (int64_t)(o == 0 ? t : s) * TRI_REC;
         const double *B = rec + (int64_t)(o == 0 ? s : t) * TRI_REC;
         const double *r = A + TR_Q + 3 * p;
         double I1, Iv[3], I3[3];
         potentials(B + TR_P, r, I1, Iv, I3);
         const double wp = A[TR_W + p];
-        for (int i = 0; i < 2; ++i) {
-            z64 k = (i == 0) ? z64(md.k1r, md.k1i) : z64(md.k2r, md.k2i);
-            z64 kk = k * k;
-            z64 S0(I1 / (4.0 * PI), 0), Sr[3], Wv[3];
+        const z64 k = (med == 0) ? z64(md.k1r, md.k1i) : z64(md.k2r, md.k2i);
+        const z64 kk = k * k;
+        z64 S0(I1 / (4.0 * PI), 0), Sr[3], Wv[3];
+        for (int d = 0; d < 3; ++d) {
+            Sr[d] = z64(Iv[d] / (4.0 * PI), 0);
+            Wv[d] = z64(-I3[d] / (4.0 * PI), 0) + kk * (Iv[d] / (8.0 * PI));
+        }
+        for (int q = 0; q < 7; ++q) {
+            double dv[3];
+            sub3(r, B + TR_Q + 3 * q, dv);
+            double R = sqrt(dot3(dv, dv));
+            z64 gs = green_rem(k, R) * B[TR_W + q];
+            z64 hs = gradgreen_rem(k, R) * B[TR_W + q];
+            S0 += gs;
             for (int d = 0; d < 3; ++d) {
-                Sr[d] = z64(Iv[d] / (4.0 * PI), 0);
-                Wv[d] = z64(-I3[d] / (4.0 * PI), 0) + kk * (Iv[d] / (8.0 * PI));
+                Sr[d] += gs * (-dv[d]);
+                Wv[d] += hs * dv[d];
             }
-            for (int q = 0; q < 7; ++q) {
-                double dv[3];
-                sub3(r, B + TR_Q + 3 * q, dv);
-                double R = sqrt(dot3(dv, dv));
-                z64 gs = green_rem(k, R) * B[TR_W + q];
-                z64 hs = gradgreen_rem(k, R) * B[TR_W + q];
-                S0 += gs;
-                for (int d = 0; d < 3; ++d) {
-                    Sr[d] += gs * (-dv[d]);
-                    Wv[d] += hs * dv[d];
-                }
-            }
-            z64 mjk(k.im, -k.re);
-            z64 four_k2 = cdiv(z64(4, 0), kk);
-            for (int a = 0; a < 3; ++a) {
-                double ta[3];
-                sub3(r, A + TR_P + 3 * a, ta);
-                for (int b = 0; b < 3; ++b) {
-                    double rb[3];
-                    sub3(r, B + TR_P + 3 * b, rb);
-                    double cc = A[TR_C + a] * B[TR_C + b] * wp;
-                    z64 tS(0, 0);
-                    for (int d = 0; d < 3; ++d) tS += ta[d] * (Sr[d] + rb[d] * S0);
-                    acc[i][1][3 * a + b] += cc * (mjk * (tS - four_k2 * S0));
-                    if (t != s) {
-                        z64 c0 = Wv[1] * rb[2] - Wv[2] * rb[1];
-                        z64 c1 = Wv[2] * rb[0] - Wv[0] * rb[2];
-                        z64 c2 = Wv[0] * rb[1] - Wv[1] * rb[0];
-                        acc[i][0][3 * a + b] += cc * (ta[0] * c0 + ta[1] * c1 + ta[2] * c2);
-                    }
+        }
+        const z64 mjk(k.im, -k.re);
+        const z64 four_k2 = cdiv(z64(4, 0), kk);
+        for (int a = 0; a < 3; ++a) {
+            double ta[3];
+            sub3(r, A + TR_P + 3 * a, ta);
+            for (int b = 0; b < 3; ++b) {
+                double rb[3];
+                sub3(r, B + TR_P + 3 * b, rb);
+                const double cc = A[TR_C + a] * B[TR_C + b] * wp;
+                z64 tS(0, 0);
+                for (int d = 0; d < 3; ++d) tS += ta[d] * (Sr[d] + rb[d] * S0);
+                accT[3 * a + b] = cc * (mjk * (tS - four_k2 * S0));
+                if (t != s) {
+                    z64 c0 = Wv[1] * rb[2] - Wv[2] * rb[1];
+                    z64 c1 = Wv[2] * rb[0] - Wv[0] * rb[2];
+                    z64 c2 = Wv[0] * rb[1] - Wv[1] * rb[0];
+                    accK[3 * a + b] = cc * (ta[0] * c0 + ta[1] * c1 + ta[2] * c2);
                 }
             }
         }
     }
-    // reduce over p within each orientation group (lanes 0-6 and 7-13)
-    z64 res[2][2][9];
-    for (int i = 0; i < 2; ++i)
-        for (int k = 0; k < 2; ++k)
-            for (int c = 0; c < 9; ++c) {
-                double re = acc[i][k][c].re, im = acc[i][k][c].im;
-                double sre0 = 0, sim0 = 0, sre1 = 0, sim1 = 0;
-                for (int l = 0; l < 14; ++l) {
-                    double vre = __shfl_sync(0xffffffffu, re, l), vim = __shfl_sync(0xffffffffu, im, l);
-                    if (l < 7) { sre0 += vre; sim0 += vim; }
-                    else { sre1 += vre; sim1 += vim; }
-                }
-                // res[i][k][c] for orientation 0 in slot, orientation 1 transposed below
-                res[i][k][c] = z64(sre0, sim0);
-                acc[i][k][c] = z64(sre1, sim1);
-            }
-    if (lane != 0) return;
-    z64 e1(md.e1r, md.e1i), e2(md.e2r, md.e2i);
-    z64 we[2][3];   // weights of (K, T) of medium i into Ks, Ta, Tb
-    we[0][0] = z64(1, 0); we[0][1] = -e1; we[0][2] = cdiv(z64(1, 0), e1);
-    we[1][0] = z64(1, 0); we[1][1] = -e2; we[1][2] = cdiv(z64(1, 0), e2);
-    const int64_t plane = (int64_t)nt * nt;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            z64 v[3] = {z64(0, 0), z64(0, 0), z64(0, 0)};
-            for (int i = 0; i < 2; ++i) {
-                z64 K = 0.5 * (res[i][0][3 * a + b] + acc[i][0][3 * b + a]);
-                z64 Tm = 0.5 * (res[i][1][3 * a + b] + acc[i][1][3 * b + a]);
-                v[0] += we[i][0] * K;
-                v[1] += we[i][1] * Tm;
-                v[2] += we[i][2] * Tm;
-            }
-            for (int op = 0; op < 3; ++op) {
-                cx<T> val((T)v[op].re, (T)v[op].im);
-                Zloc[(op * 9 + 3 * a + b) * plane + (int64_t)t * nt + s] = val;
-                if (t != s) Zloc[(op * 9 + 3 * b + a) * plane + (int64_t)s * nt + t] = val;
-            }
+    // reduce over the eight lanes of each (o, medium) group
+    for (int c = 0; c < 9; ++c) {
+        for (int off = 1; off < 8; off <<= 1) {
+            accK[c].re += __shfl_xor_sync(0xffffffffu, accK[c].re, off);
+            accK[c].im += __shfl_xor_sync(0xffffffffu, accK[c].im, off);
+            accT[c].re += __shfl_xor_sync(0xffffffffu, accT[c].re, off);
+            accT[c].im += __shfl_xor_sync(0xffffffffu, accT[c].im, off);
         }
+    }
+    // group sums to shared memory: sm[o][i][K|T][c]
+    __shared__ z64 sm_all[4][2][2][2][9];
+    z64 (*sm)[2][2][9] = sm_all[(threadIdx.x >> 5) & 3];
+    if (p == 0)
+        for (int c = 0; c < 9; ++c) {
+            sm[o][med][0][c] = accK[c];
+            sm[o][med][1][c] = accT[c];
+        }
+    __syncwarp();
+    if (lane >= 9) return;
+    // lane c = 3 a + b: symmetrise, weight the media into Ks, Ta, Tb and store
+    const int a = lane / 3, b = lane % 3;
+    const z64 e1(md.e1r, md.e1i), e2(md.e2r, md.e2i);
+    z64 v[3] = {z64(0, 0), z64(0, 0), z64(0, 0)};
+    for (int i = 0; i < 2; ++i) {
+        const z64 ei = i == 0 ? e1 : e2;
+        z64 Ks = 0.5 * (sm[0][i][0][3 * a + b] + sm[1][i][0][3 * b + a]);
+        z64 Ts = 0.5 * (sm[0][i][1][3 * a + b] + sm[1][i][1][3 * b + a]);
+        v[0] += Ks;
+        v[1] += -ei * Ts;
+        v[2] += cdiv(Ts, ei);
+    }
+    const int64_t plane = (int64_t)nt * nt;
+    for (int op = 0; op < 3; ++op) {
+        cx<T> val((T)v[op].re, (T)v[op].im);
+        Zloc[(op * 9 + 3 * a + b) * plane + (int64_t)t * nt + s] = val;
+        if (t != s) Zloc[(op * 9 + 3 * b + a) * plane + (int64_t)s * nt + t] = val;
+    }
 }
 
 // Stage 3: Z_op[i][j] from the local blocks (deterministic gather).

@@ -26,135 +26,174 @@ namespace cbfm {
 
 namespace {
 
-constexpr int PCHOL_MAX = 256;
+constexpr int PCHOL_MAX = 128;
+constexpr int PCHOL_THREADS = 256;
+// dynamic shared memory of k_pchol: packed upper triangle, one row, the pivot order
+constexpr size_t pchol_smem(int m) {
+    return (size_t)(m * (m + 1) / 2 + m) * sizeof(z64) + (size_t)m * sizeof(int);
+}
 
-// Pivoted Cholesky M = (P R)^H-style: the symmetrically permuted matrix
-// P^T M P = R^H R with R upper trapezoidal (rank x m).  One block, all data in
-// global memory.  pivot == 0 keeps the order.  A diagonal below
-// tol * max(initial diagonal) ends the factorisation (rank).  Also returns
-// Rinv = R11^{-1} for the leading rank x rank block.  Row-major m x m buffers.
-__global__ void __launch_bounds__(256) k_pchol(int m, const z64 *__restrict__ M, z64 *__restrict__ A,
-                                               int *__restrict__ perm, z64 *__restrict__ R, z64 *__restrict__ Rinv,
-                                               int *__restrict__ rank_out, double tol, int pivot) {
-    __shared__ double sval[256];
-    __shared__ int sidx[256];
-    __shared__ int s_rank, s_q;
-    __shared__ double s_max0;
-    for (int64_t i = threadIdx.x; i < (int64_t)m * m; i += blockDim.x) {
-        A[i] = M[i];
-        R[i] = z64(0, 0);
-        Rinv[i] = z64(0, 0);
+// Pivoted Cholesky of the Hermitian m x m matrix M (row-major): with the
+// order perm, M[perm[a]][perm[b]] = sum_i conj(R[i][a]) R[i][b], R upper
+// trapezoidal (rank x m, row-major, ld m, rows >= rank zero).  pivot == 0
+// keeps the order.  A remaining diagonal below tol * max(initial diagonal)
+// ends the factorisation (rank).
+//
+// One block; the Schur complement lives in shared memory as the packed upper
+// triangle in the ORIGINAL index order (U[P(a, b)], a <= b), so a pivot step
+// swaps two entries of perm (and two columns of the finished rows of R)
+// instead of two rows and columns.  FP64 throughput of one SM bounds this
+// kernel, so every scalar of a step is computed once, and the rank-1 update
+// runs over the flattened triangle of remaining pairs (no idle lanes).
+__global__ void __launch_bounds__(PCHOL_THREADS) k_pchol(int m, const z64 *__restrict__ M, int *__restrict__ perm,
+                                                         z64 *__restrict__ R, int *__restrict__ rank_out, double tol,
+                                                         int pivot) {
+    extern __shared__ z64 U[];
+    z64 *rb = U + (int64_t)m * (m + 1) / 2;      // current row of R, by position
+    int *piv = reinterpret_cast<int *>(rb + m);  // position -> original index
+    __shared__ int s_rank;
+    __shared__ double s_thr, s_d, s_rd;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto PU = [m](int a, int b) { return a * m - a * (a - 1) / 2 + (b - a); };
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+        const int a = idx / m, b = idx - a * m;
+        if (b >= a) U[PU(a, b)] = M[idx];
+        R[idx] = z64(0, 0);
     }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = i;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) piv[i] = i;
     __syncthreads();
-    // largest initial diagonal
-    {
+    if (warp == 0) {
         double best = 0.0;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) best = fmax(best, A[(int64_t)i * m + i].re);
-        sval[threadIdx.x] = best;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sval[threadIdx.x] = fmax(sval[threadIdx.x], sval[threadIdx.x + w]);
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            s_max0 = sval[0];
+        for (int i = lane; i < m; i += 32) best = fmax(best, U[PU(i, i)].re);
+        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) {
+            s_thr = tol * best;
             s_rank = m;
         }
-        __syncthreads();
-    }
-    const double thr = tol * s_max0;
-    for (int i = 0; i < m; ++i) {
-        // pivot
-        if (pivot) {
-            double best = -1.0;
-            int bi = i;
-            for (int l = i + threadIdx.x; l < m; l += blockDim.x) {
-                double v = A[(int64_t)l * m + l].re;
-                if (v > best) { best = v; bi = l; }
-            }
-            sval[threadIdx.x] = best;
-            sidx[threadIdx.x] = bi;
-            __syncthreads();
-            for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-                if (threadIdx.x < w) {
-                    double o = sval[threadIdx.x + w];
-                    int oi = sidx[threadIdx.x + w];
-                    if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
-                        sval[threadIdx.x] = o;
-                        sidx[threadIdx.x] = oi;
-                    }
-                }
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) s_q = sidx[0];
-        } else if (threadIdx.x == 0) {
-            s_q = i;
-        }
-        __syncthreads();
-        const int q = s_q;
-        const double dq = A[(int64_t)q * m + q].re;
-        if (!(dq > thr) || dq <= 0.0) {
-            if (threadIdx.x == 0) s_rank = i;
-            __syncthreads();
-            break;
-        }
-        if (q != i) {
-            // swap rows i, q of A, then columns i, q; swap columns i, q of R's finished rows; swap perm
-            for (int c = threadIdx.x; c < m; c += blockDim.x) {
-                z64 t = A[(int64_t)i * m + c];
-                A[(int64_t)i * m + c] = A[(int64_t)q * m + c];
-                A[(int64_t)q * m + c] = t;
-            }
-            __syncthreads();
-            for (int r = threadIdx.x; r < m; r += blockDim.x) {
-                z64 t = A[(int64_t)r * m + i];
-                A[(int64_t)r * m + i] = A[(int64_t)r * m + q];
-                A[(int64_t)r * m + q] = t;
-                if (r < i) {
-                    z64 u = R[(int64_t)r * m + i];
-                    R[(int64_t)r * m + i] = R[(int64_t)r * m + q];
-                    R[(int64_t)r * m + q] = u;
-                }
-            }
-            if (threadIdx.x == 0) {
-                int t = perm[i];
-                perm[i] = perm[q];
-                perm[q] = t;
-            }
-            __syncthreads();
-        }
-        const double d = sqrt(A[(int64_t)i * m + i].re);
-        for (int l = i + threadIdx.x; l < m; l += blockDim.x)
-            R[(int64_t)i * m + l] = (l == i) ? z64(d, 0) : A[(int64_t)i * m + l] * (1.0 / d);
-        __syncthreads();
-        const int rem = m - i - 1;
-        for (int64_t idx = threadIdx.x; idx < (int64_t)rem * rem; idx += blockDim.x) {
-            int l = i + 1 + (int)(idx / rem), c = i + 1 + (int)(idx % rem);
-            A[(int64_t)l * m + c] -= conj(R[(int64_t)i * m + l]) * R[(int64_t)i * m + c];
-        }
-        __syncthreads();
     }
     __syncthreads();
-    const int r = s_rank;
-    // Rinv = R11^{-1}, row by row from the bottom; one warp per entry (k, j),
-    // lanes split the sum over l so the global-memory latency overlaps
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int k = r - 1; k >= 0; --k) {
-        const z64 dk = cdiv(z64(1, 0), R[(int64_t)k * m + k]);
-        for (int j = k + 1 + warp; j < r; j += nwarp) {
+    for (int i = 0; i < m; ++i) {
+        // pivot: largest remaining diagonal, lowest position on ties
+        if (warp == 0) {
+            if (pivot) {
+                double bv = -1.0;
+                int bp = i;
+                for (int pos = i + lane; pos < m; pos += 32) {
+                    const int l = piv[pos];
+                    const double v = U[PU(l, l)].re;
+                    if (v > bv) { bv = v; bp = pos; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+                    if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; }
+                }
+                if (bp != i) {
+                    // the finished rows of R follow the new order of positions i and bp
+                    for (int rr = lane; rr < i; rr += 32) {
+                        const z64 t = R[(int64_t)rr * m + i];
+                        R[(int64_t)rr * m + i] = R[(int64_t)rr * m + bp];
+                        R[(int64_t)rr * m + bp] = t;
+                    }
+                    if (lane == 0) {
+                        const int t = piv[i];
+                        piv[i] = piv[bp];
+                        piv[bp] = t;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const double dq = U[PU(piv[i], piv[i])].re;
+                if (!(dq > s_thr) || dq <= 0.0) {
+                    s_rank = i;
+                } else {
+                    s_d = sqrt(dq);
+                    s_rd = 1.0 / s_d;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_rank == i) break;
+        // row i of R: R[i][pos] = U'(q, piv[pos]) / d
+        const int q = piv[i];
+        const double d = s_d, rd = s_rd;
+        for (int pos = i + threadIdx.x; pos < m; pos += blockDim.x) {
+            const int l = piv[pos];
+            z64 v = q <= l ? U[PU(q, l)] : conj(U[PU(l, q)]);
+            v = pos == i ? z64(d, 0) : v * rd;
+            rb[pos] = v;
+            R[(int64_t)i * m + pos] = v;
+        }
+        __syncthreads();
+        // Schur complement update U'(a, b) -= conj(R[i][pa]) R[i][pb] over the
+        // remaining position pairs pa <= pb, flattened: row u of the triangle
+        // starts at S(u) = u n - u (u - 1) / 2
+        const int n = m - i - 1;
+        const int npairs = n * (n + 1) / 2;
+        for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
+            const float tn = 2.0f * n + 1.0f;
+            int u = (int)((tn - sqrtf(tn * tn - 8.0f * idx)) * 0.5f);
+            u = u < 0 ? 0 : (u >= n ? n - 1 : u);
+            while (u > 0 && u * n - u * (u - 1) / 2 > idx) --u;
+            while (u + 1 < n && (u + 1) * n - (u + 1) * u / 2 <= idx) ++u;
+            const int pa = i + 1 + u, pb = pa + (idx - (u * n - u * (u - 1) / 2));
+            const int a = piv[pa], b = piv[pb];
+            const z64 ra = rb[pa], rbb = rb[pb];
+            // conj(ra) * rbb
+            const double pr = ra.re * rbb.re + ra.im * rbb.im;
+            const double pi = ra.re * rbb.im - ra.im * rbb.re;
+            const bool up = a <= b;   // stored at (a, b); else at (b, a), conjugated
+            const int off = up ? PU(a, b) : PU(b, a);
+            U[off].re -= pr;
+            U[off].im -= up ? pi : -pi;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = piv[i];
+    if (threadIdx.x == 0) *rank_out = s_rank;
+}
+
+// Rinv = R11^{-1} for the leading r x r block of the upper-triangular Cholesky
+// factor R (r = *rank; row-major, ld m, real positive diagonal), zero
+// elsewhere in the m x m output.  One warp per column j: back substitution
+// x_k = (delta_kj - sum_{k<l<=j} R[k][l] x_l) / R[k][k] with the sum split
+// over the lanes; lane owns rows lane + 32 t.  The columns run on separate SMs,
+// so the FP64 work spreads over the GPU.
+__global__ void __launch_bounds__(32) k_trinv(int m, const z64 *__restrict__ R, const int *__restrict__ rank,
+                                              z64 *__restrict__ Rinv) {
+    const int j = blockIdx.x, lane = threadIdx.x;
+    const int r = *rank;
+    z64 x[PCHOL_MAX / 32];
+#pragma unroll
+    for (int t = 0; t < PCHOL_MAX / 32; ++t) x[t] = z64(0, 0);
+    if (j < r) {
+        for (int k = j; k >= 0; --k) {
+            const z64 *Rk = R + (int64_t)k * m;
             z64 s(0, 0);
-            for (int l = k + 1 + lane; l <= j; l += 32) s += R[(int64_t)k * m + l] * Rinv[(int64_t)l * m + j];
+#pragma unroll
+            for (int t = 0; t < PCHOL_MAX / 32; ++t) {
+                const int l = lane + 32 * t;
+                if (l > k && l <= j) s += Rk[l] * x[t];
+            }
             for (int o = 16; o > 0; o >>= 1) {
                 s.re += __shfl_xor_sync(0xffffffffu, s.re, o);
                 s.im += __shfl_xor_sync(0xffffffffu, s.im, o);
             }
-            if (lane == 0) Rinv[(int64_t)k * m + j] = -(s * dk);
+            if (lane == (k & 31)) {
+                const double inv = 1.0 / Rk[k].re;
+                const z64 xk = ((k == j ? z64(1, 0) : z64(0, 0)) - s) * inv;
+#pragma unroll
+                for (int t = 0; t < PCHOL_MAX / 32; ++t)
+                    if (t == (k >> 5)) x[t] = xk;
+            }
         }
-        if (threadIdx.x == 0) Rinv[(int64_t)k * m + k] = dk;
-        __syncthreads();
     }
-    if (threadIdx.x == 0) *rank_out = r;
+#pragma unroll
+    for (int t = 0; t < PCHOL_MAX / 32; ++t) {
+        const int l = lane + 32 * t;
+        if (l < m) Rinv[(int64_t)l * m + j] = x[t];
+    }
 }
 
 // X (r x m): X[i][perm[l]] = Rinv[l][i] (l <= i < r), else 0  -> Q = X W for row vectors W.
@@ -275,17 +314,34 @@ inline unsigned nb(int64_t work) { return (unsigned)std::max<int64_t>(1, std::mi
 
 struct Ctx {
     cudaStream_t st;
-    DevBuf<z64> M, A, R, Rinv, X, T1, Rf;
+    DevBuf<z64> M, R, Rinv, X, T1, Rf;
     DevBuf<int> perm, rank;
     DevBuf<double> rnrm, scale;
 };
 
 // Pivoted / plain Cholesky on the m x m Gram matrix already in ctx.M; returns rank (host sync).
 int pchol(Ctx &c, int m, double tol, bool pivot) {
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    CBFM_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !attr_set[dev]) {
+        CBFM_CUDA(cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)pchol_smem(PCHOL_MAX)));
+        attr_set[dev] = true;
+    }
     {
+        CBFM_REQUIRE(m >= 1 && m <= PCHOL_MAX, "pivoted Cholesky: block width out of range");
+        // algorithmic work of a full-rank factorisation and of the triangular inverse: m^3/6 complex MACs each
+        prof_add_work("k_pchol", 8.0 * m * m * m / 6.0, 16.0 * m * m);
+        prof_add_work("k_trinv", 8.0 * m * m * m / 6.0, 32.0 * m * m);
         ProfScope ps_("k_pchol", c.st);
-        k_pchol<<<1, 256, 0, c.st>>>(m, c.M.p, c.A.p, c.perm.p, c.R.p, c.Rinv.p, c.rank.p, tol, pivot ? 1 : 0);
+        k_pchol<<<1, PCHOL_THREADS, pchol_smem(m), c.st>>>(m, c.M.p, c.perm.p, c.R.p, c.rank.p, tol, pivot ? 1 : 0);
         launched("k_pchol");
+    }
+    {
+        ProfScope ps_("k_trinv", c.st);
+        k_trinv<<<m, 32, 0, c.st>>>(m, c.R.p, c.rank.p, c.Rinv.p);
+        launched("k_trinv");
     }
     int r = 0;
     CBFM_CUDA(cudaMemcpyAsync(&r, c.rank.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
@@ -378,7 +434,7 @@ void cholqr2_cols(Ctx &c, z64 *H, int d, int p, int64_t ldh, z64 *Rout, z64 *Rin
 GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp, z64 *d_x,
                       cudaStream_t st) {
     const int64_t n = rd.n;
-    CBFM_REQUIRE(nrhs >= 1 && nrhs <= PCHOL_MAX, "block GMRES handles at most 256 right-hand sides per call");
+    CBFM_REQUIRE(nrhs >= 1 && nrhs <= PCHOL_MAX, "block GMRES handles at most 128 right-hand sides per call");
     const int p = nrhs;
     const double rank_tol = 1e-14;   // pivot threshold of the scaled Gram matrix (unit diagonal)
     const double drop_tol = 1e-12;   // rows below this fraction of the reference norm are exhausted
@@ -388,7 +444,6 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     Ctx c;
     c.st = st;
     c.M.alloc((size_t)p * p);
-    c.A.alloc((size_t)p * p);
     c.R.alloc((size_t)p * p);
     c.Rinv.alloc((size_t)p * p);
     c.X.alloc((size_t)p * p);

@@ -378,7 +378,7 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
             fl += 8.0 * d.M * d.N * d.K;
             by += (double)(d.M * d.K + d.K * d.N + d.M * d.N) * sizeof(cx<T>);
         }
-        prof_add_work("k_gemm", fl, by);
+        prof_add_work(sizeof(T) == 8 ? "k_gemm_z64" : "k_gemm_c32", fl, by);
     }
     for (size_t g0 = 0; g0 < g.size(); g0 += GB_MAXG) {
         GemmBatch bt;
@@ -396,8 +396,8 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
         if (tiles == 0) continue;
         // few output tiles and a long K: split K so that the GPU fills up
         const GemmDesc &d0 = bt.d[0];
-        if (bt.ng == 1 && tiles < 2 * 152 && d0.K >= 512) {
-            int64_t S = std::min<int64_t>((2 * 152 + tiles - 1) / tiles, (d0.K + 255) / 256);
+        if (bt.ng == 1 && tiles < 4 * 152 && d0.K >= 256) {
+            int64_t S = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, (d0.K + 63) / 64);
             if (S > 1) {
                 int64_t chunk = (d0.K + S - 1) / S;
                 chunk = (chunk + GB_K - 1) / GB_K * GB_K;
@@ -410,7 +410,7 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
             CBFM_CUDA(cudaMallocAsync((void **)&part, sizeof(cx<T>) * bt.ksplit * d0.M * d0.N, st));
         }
         {
-            ProfScope ps_("k_gemm", st);
+            ProfScope ps_(sizeof(T) == 8 ? "k_gemm_z64" : "k_gemm_c32", st);
             k_gemm<T><<<(unsigned)(tiles * bt.ksplit), 256, 0, st>>>(bt, opA, opB, A, B, C, part,
                                                                      accumulate ? 1 : 0, (T)alpha);
             launched("k_gemm");
