@@ -57,9 +57,12 @@ typedef enum {
 
 typedef enum {
     CBFM_FP64 = 0,        /* every step in FP64 (reference GPU path) */
-    CBFM_MIXED = 1        /* FP32 far-pair quadrature and projections, complex64 reduced
+    CBFM_MIXED = 1,       /* FP32 far-pair quadrature; projections on the tensor cores
+                             (split-TF32 products, FP32 accumulation); complex64 reduced
                              matrix; FP64 singular near pairs, SVD, CMP Gram inverse,
                              GMRES Arnoldi / residual */
+    CBFM_MIXED_SIMT = 2   /* as CBFM_MIXED, but the projections run as FP32 products on
+                             the CUDA cores (for comparison with the tensor-core path) */
 } cbfm_precision;
 
 /*

@@ -3,8 +3,8 @@
 The compute path lives in libcbfm.so (hand-written CUDA, C ABI in
 include/cbfm.h); `cbfm` is its thin Python binding and `build` compiles it.
 """
-from .cbfm import (BLOCK, FP64, MIXED, PER_RHS, CbfmError, assemble_reduced, build_cbfs, cbf_import, cmp_setup, launch_count,
+from .cbfm import (BLOCK, FP64, MIXED, MIXED_SIMT, PER_RHS, CbfmError, assemble_reduced, build_cbfs, cbf_import, cmp_setup, launch_count,
                    mesh, mesh_edges, profile, profile_read, solve)
 
-__all__ = ["BLOCK", "PER_RHS", "FP64", "MIXED", "CbfmError", "assemble_reduced", "build_cbfs", "cbf_import", "cmp_setup",
+__all__ = ["BLOCK", "PER_RHS", "FP64", "MIXED", "MIXED_SIMT", "CbfmError", "assemble_reduced", "build_cbfs", "cbf_import", "cmp_setup",
            "launch_count", "mesh", "mesh_edges", "profile", "profile_read", "solve"]

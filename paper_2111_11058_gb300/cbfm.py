@@ -22,6 +22,7 @@ _LIB_PATH = os.path.join(_HERE, "libcbfm.so")
 
 FP64 = 0
 MIXED = 1
+MIXED_SIMT = 2   # mixed precision with the projections on the CUDA cores instead of the tensor cores
 
 STATUS = {0: "CBFM_OK", 1: "CBFM_EINVAL", 2: "CBFM_ENOMEM", 3: "CBFM_ECUDA", 4: "CBFM_ESINGULAR",
           5: "CBFM_ENOCONV", 6: "CBFM_ETIMEOUT"}

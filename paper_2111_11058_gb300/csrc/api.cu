@@ -652,15 +652,23 @@ void project(Red &r, cudaStream_t st) {
     DevBuf<cx<T>> Z;
     Z.alloc(3 * (size_t)ne * ne);
     assemble_rwg<T>(m, Z.p, st);
+    DevBuf<cx<T>> A;
+    A.alloc((size_t)n * n);
+    if constexpr (sizeof(T) == 4) {
+        if (r.prec == CBFM_MIXED) {
+            project_tc(m, c, Z.p, A.p, st);
+            r.A32.p = A.p; r.A32.n = A.n; A.p = nullptr; A.n = 0;
+            return;
+        }
+    }
     const cx<T> *CM, *CJ;
     if constexpr (sizeof(T) == 8) { CM = c.CM.p; CJ = c.CJ.p; }
     else { CM = c.CM32.p; CJ = c.CJ32.p; }
     // chains: (operator, coefficient side of the columns, row test side, A row block, A column block)
     struct Chain { int op; bool colM; bool rowJ; int64_t r0, c0; };
     const Chain ch[4] = {{0, true, true, 0, 0}, {1, false, true, 0, nh}, {2, true, false, nh, 0}, {0, false, false, nh, nh}};
-    DevBuf<cx<T>> Y, A;
+    DevBuf<cx<T>> Y;
     Y.alloc((size_t)ne * nh);
-    A.alloc((size_t)n * n);
     for (int q = 0; q < 4; ++q) {
         std::vector<GemmDesc> g1, g2;
         for (int k = 0; k < nc; ++k) {
@@ -693,7 +701,7 @@ cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precisi
         check_device(c, H_CBF, "cbf");
         CBFM_REQUIRE(c->mesh == m, "cbf handle belongs to another mesh");
         CBFM_REQUIRE(out, "NULL out");
-        CBFM_REQUIRE(prec == CBFM_FP64 || prec == CBFM_MIXED, "unknown precision");
+        CBFM_REQUIRE(prec == CBFM_FP64 || prec == CBFM_MIXED || prec == CBFM_MIXED_SIMT, "unknown precision");
         *out = nullptr;
         cudaStream_t st = (cudaStream_t)stream;
         std::unique_ptr<Red> r(new Red());
@@ -813,7 +821,7 @@ cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
         if (hinfo) throw Fail{CBFM_ESINGULAR, "G^CBF is singular"};
         // B = A (G^CBF)^{-1}: GMRES then needs one product per iteration
         std::vector<GemmDesc> gb{GemmDesc{n, n, n, 0, n, 0, n, 0, n}};
-        if (r->prec == CBFM_MIXED) {
+        if (r->prec != CBFM_FP64) {
             r->Ginv32.alloc((size_t)n * n);
             launch_z64_to_c32(r->Ginv.p, r->Ginv32.p, n * n, st);
             r->B32.alloc((size_t)n * n);

@@ -484,7 +484,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     CBFM_CUDA(cudaStreamSynchronize(st));
 
     auto applyB = [&](const z64 *in, z64 *out, int rows) {
-        if (rd.prec == CBFM_MIXED) apply_rows(rd, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, rows, ones.p, st);
+        if (rd.prec != CBFM_FP64) apply_rows(rd, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, rows, ones.p, st);
         else apply_rows(rd, use_cmp ? rd.B64.p : rd.A64.p, nullptr, in, out, rows, ones.p, st);
     };
 

@@ -359,7 +359,7 @@ void apply_rows(const Red &rd, const z64 *M64, const c32 *M32, const z64 *in, z6
 }
 
 static void apply_B(const Red &rd, bool use_cmp, const z64 *in, z64 *out, int nrhs, const int *mask, cudaStream_t st) {
-    if (rd.prec == CBFM_MIXED) apply_rows(rd, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, nrhs, mask, st);
+    if (rd.prec != CBFM_FP64) apply_rows(rd, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, nrhs, mask, st);
     else apply_rows(rd, use_cmp ? rd.B64.p : rd.A64.p, nullptr, in, out, nrhs, mask, st);
 }
 
@@ -539,7 +539,7 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
         // dot products and updates: 8 flops per complex multiply-add, one basis element read each
         prof_add_work("k_dots", 8.0 * n * (pass1 + p2), cb * n * (pass1 + p2));
         prof_add_work("k_orth_update", 8.0 * n * (pass1 + p2), cb * n * (pass1 + p2));
-        const double eb = rd.prec == CBFM_MIXED ? sizeof(c32) : sizeof(z64);
+        const double eb = rd.prec != CBFM_FP64 ? sizeof(c32) : sizeof(z64);
         prof_add_work("k_matvec", 8.0 * n * n * (nmatvec + (use_cmp ? nrhs : 0)), eb * n * n * (nmatvec + 1.0));
     }
     return out;
