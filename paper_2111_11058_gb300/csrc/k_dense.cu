@@ -295,66 +295,136 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(int s, z64 *__restrict__ Xal
 }
 
 // ------------------------------------------------- Gauss-Jordan inverse
-// One launch per elimination step k with ping-pong buffers (no grid-wide
-// wait): every block finds the pivot of column k itself.
-__global__ void k_gj_step(int64_t n, int64_t k, const z64 *__restrict__ Ain, z64 *__restrict__ Aout,
-                          int *__restrict__ info) {
-    // pivot: max |A[i][k]|, i >= k (first max)
-    __shared__ double sval[256];
-    __shared__ int64_t sidx[256];
-    double best = -1.0;
-    int64_t bi = k;
-    for (int64_t i = k + threadIdx.x; i < n; i += blockDim.x) {
-        double v = norm2(Ain[i * 2 * n + k]);
-        if (v > best) { best = v; bi = i; }
+// In-place Gauss-Jordan ("sweep") with row interchanges, one launch per pivot
+// k and ping-pong buffers (no grid-wide wait).  With O the matrix after
+// swapping rows k and p, pinv = 1 / O[k][k], f_i = O[i][k] pinv:
+//   new[i][j] = O[i][j] - f_i O[k][j]   (i != k, j != k)
+//   new[i][k] = -f_i,  new[k][j] = O[k][j] pinv,  new[k][k] = pinv.
+// After n sweeps the matrix is the inverse of the row-permuted input; undoing
+// the interchanges on the columns, last first, gives A^{-1}.  Each sweep also
+// finds the pivot of the next column (largest |.|^2 below the diagonal, lowest
+// row on ties) through a 64-bit atomicMax on key = (|v|^2 bits, ~row).
+constexpr int GJ_IBITS = 20;
+constexpr unsigned long long GJ_IMASK = (1ull << GJ_IBITS) - 1;
+
+__device__ __forceinline__ unsigned long long gj_key(double v2, int row) {
+    if (!(v2 > 0.0)) return 0ull;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v2);
+    return ((b >> GJ_IBITS) << GJ_IBITS) | (GJ_IMASK - (unsigned long long)row);
+}
+
+// block-wide max of a key, then one atomicMax
+__device__ __forceinline__ void gj_push_key(unsigned long long key, unsigned long long *dst) {
+    __shared__ unsigned long long s_k[32];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+        key = other > key ? other : key;
     }
-    sval[threadIdx.x] = best;
-    sidx[threadIdx.x] = bi;
+    if (lane == 0) s_k[w] = key;
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            double o = sval[threadIdx.x + w];
-            int64_t oi = sidx[threadIdx.x + w];
-            if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
-                sval[threadIdx.x] = o;
-                sidx[threadIdx.x] = oi;
+    if (t == 0) {
+        unsigned long long best = 0;
+        for (int i = 0; i < (int)(blockDim.x * blockDim.y + 31) / 32; ++i) best = s_k[i] > best ? s_k[i] : best;
+        if (best) atomicMax(dst, best);
+    }
+}
+
+// copy A into the first buffer and find the pivot of column 0
+__global__ void __launch_bounds__(256) k_gj_init(int n, const z64 *__restrict__ A, z64 *__restrict__ X,
+                                                 unsigned long long *__restrict__ keys) {
+    unsigned long long key = 0;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const z64 v = A[idx];
+        X[idx] = v;
+        if (idx % n == 0) {
+            const unsigned long long kk = gj_key(norm2(v), (int)(idx / n));
+            key = kk > key ? kk : key;
+        }
+    }
+    gj_push_key(key, &keys[0]);
+}
+
+// 16 x 16 threads, each 2 rows x 2 columns of a 32 x 32 tile
+__global__ void __launch_bounds__(256) k_gj_sweep(int n, int k, const z64 *__restrict__ Ain, z64 *__restrict__ Aout,
+                                                  unsigned long long *__restrict__ keys, int *__restrict__ pivrow,
+                                                  int *__restrict__ info) {
+    __shared__ z64 s_pinv;
+    __shared__ int s_p;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const unsigned long long key = keys[k];
+        int p = k;
+        z64 pinv(0, 0);
+        if (key == 0ull) {
+            if (blockIdx.x == 0 && blockIdx.y == 0) info[0] = 1;   // no non-zero pivot in column k
+        } else {
+            p = (int)(GJ_IMASK - (key & GJ_IMASK));
+            pinv = cdiv(z64(1, 0), Ain[(int64_t)p * n + k]);
+        }
+        if (blockIdx.x == 0 && blockIdx.y == 0) pivrow[k] = p;
+        s_p = p;
+        s_pinv = pinv;
+    }
+    __syncthreads();
+    const int p = s_p;
+    const z64 pinv = s_pinv;
+    const int j0 = blockIdx.x * 32 + threadIdx.x, i0 = blockIdx.y * 32 + threadIdx.y;
+    z64 r[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int j = j0 + 16 * c;
+        r[c] = j < n ? Ain[(int64_t)p * n + j] : z64(0, 0);   // O[k][j]
+    }
+    unsigned long long key = 0;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const int i = i0 + 16 * rr;
+        if (i >= n) continue;
+        z64 *out = Aout + (int64_t)i * n;
+        if (i == k) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int j = j0 + 16 * c;
+                if (j < n) out[j] = j == k ? pinv : r[c] * pinv;
+            }
+        } else {
+            const int src = i == p ? k : i;
+            const z64 *in = Ain + (int64_t)src * n;
+            const z64 f = in[k] * pinv;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int j = j0 + 16 * c;
+                if (j >= n) continue;
+                const z64 v = j == k ? -f : in[j] - f * r[c];
+                out[j] = v;
+                if (j == k + 1 && i > k) {
+                    const unsigned long long kk = gj_key(norm2(v), i);
+                    key = kk > key ? kk : key;
+                }
             }
         }
-        __syncthreads();
     }
-    const int64_t p = sidx[0];
-    if (sval[0] <= 0.0) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = 1;
-    }
-    const z64 piv = Ain[p * 2 * n + k];
-    const z64 pinv = (norm2(piv) > 0.0) ? cdiv(z64(1, 0), piv) : z64(0, 0);
-    const int64_t w2 = 2 * n;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * w2; idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = idx / w2, j = idx % w2;
-        // source row of output row i after swapping rows k and p
-        int64_t src = (i == k) ? p : ((i == p) ? k : i);
-        z64 prow = Ain[p * w2 + j] * pinv;   // normalised pivot row
-        if (i == k) {
-            Aout[idx] = prow;
-        } else {
-            z64 f = Ain[src * w2 + k];
-            Aout[idx] = Ain[src * w2 + j] - f * prow;
-        }
+    if (k + 1 < n && (k + 1) / 32 == (int)blockIdx.x) gj_push_key(key, &keys[k + 1]);
+}
+
+// column order of the result: undo the interchanges, last first (one thread)
+__global__ void k_gj_perm(int n, const int *__restrict__ pivrow, int *__restrict__ src) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int j = 0; j < n; ++j) src[j] = j;
+    for (int k = n - 1; k >= 0; --k) {
+        const int p = pivrow[k], t = src[k];
+        src[k] = src[p];
+        src[p] = t;
     }
 }
 
-__global__ void k_gj_pack(int64_t n, const z64 *__restrict__ A, z64 *__restrict__ Aug) {
-    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= n * 2 * n) return;
-    int64_t i = idx / (2 * n), j = idx % (2 * n);
-    Aug[idx] = (j < n) ? A[i * n + j] : z64(j - n == i ? 1.0 : 0.0, 0.0);
-}
-
-__global__ void k_gj_unpack(int64_t n, const z64 *__restrict__ Aug, z64 *__restrict__ inv) {
-    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
-    int64_t i = idx / n, j = idx % n;
-    inv[idx] = Aug[i * 2 * n + n + j];
+__global__ void k_gj_unpack(int n, const z64 *__restrict__ X, const int *__restrict__ src, z64 *__restrict__ inv) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / n, j = idx % n;
+        inv[idx] = X[i * n + src[j]];
+    }
 }
 
 __global__ void k_to32(const z64 *__restrict__ s, c32 *__restrict__ d, int64_t n) {
@@ -394,10 +464,13 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
         }
         const int64_t tiles = bt.tile_off[bt.ng];
         if (tiles == 0) continue;
-        // few output tiles and a long K: split K so that the GPU fills up
+        // few output tiles: split K (chunks of at least GB_K) until about two
+        // CTAs per SM exist.  A CTA of this kernel keeps its SM's FP64 pipe
+        // busy on its own, so for FP64 products the grid size, not the tile
+        // shape, decides the speed of the small GEMMs of block GMRES.
         const GemmDesc &d0 = bt.d[0];
-        if (bt.ng == 1 && tiles < 4 * 152 && d0.K >= 256) {
-            int64_t S = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, (d0.K + 63) / 64);
+        if (bt.ng == 1 && tiles < 2 * 152 && d0.K > GB_K) {
+            int64_t S = std::min<int64_t>((2 * 152 + tiles - 1) / tiles, (d0.K + GB_K - 1) / GB_K);
             if (S > 1) {
                 int64_t chunk = (d0.K + S - 1) / S;
                 chunk = (chunk + GB_K - 1) / GB_K * GB_K;
@@ -458,28 +531,40 @@ void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info,
 }
 
 void gauss_jordan_inverse(int64_t n, z64 *Aug, z64 *inv, int *d_info, cudaStream_t st) {
-    // Aug must hold 2 buffers of n x 2n; the first n x n of `inv` on entry is A.
-    z64 *b0 = Aug, *b1 = Aug + n * 2 * n;
-    int64_t tot = n * 2 * n;
+    // Aug holds two n x n buffers; `inv` is A on entry and A^{-1} on return.
+    if (n <= 0) return;
+    CBFM_REQUIRE(n < (int64_t)GJ_IMASK, "Gauss-Jordan: matrix too large for the pivot key");
+    z64 *b0 = Aug, *b1 = Aug + n * n;
+    DevBuf<unsigned long long> keys;
+    DevBuf<int> pivrow, src;
+    keys.alloc(n);
+    pivrow.alloc(n);
+    src.alloc(n);
+    CBFM_CUDA(cudaMemsetAsync(keys.p, 0, sizeof(unsigned long long) * n, st));
+    const unsigned nb = (unsigned)std::min<int64_t>((n * n + 255) / 256, 4 * 152);
     {
-        ProfScope ps_("k_gj_pack", st);
-        k_gj_pack<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n, inv, b0);
-        launched("k_gj_pack");
+        ProfScope ps_("k_gj_init", st);
+        k_gj_init<<<nb, 256, 0, st>>>((int)n, inv, b0, keys.p);
+        launched("k_gj_init");
     }
-    int blocks = (int)std::min<int64_t>((tot + 255) / 256, 4 * 152);
+    const dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), blk(16, 16);
     for (int64_t k = 0; k < n; ++k) {
         {
-            ProfScope ps_("k_gj_step", st);
-            k_gj_step<<<blocks, 256, 0, st>>>(n, k, b0, b1, d_info);
-            launched("k_gj_step");
+            ProfScope ps_("k_gj_sweep", st);
+            k_gj_sweep<<<g, blk, 0, st>>>((int)n, (int)k, b0, b1, keys.p, pivrow.p, d_info);
+            launched("k_gj_sweep");
         }
         std::swap(b0, b1);
     }
+    prof_add_work("k_gj_sweep", 8.0 * (double)n * n * n, 32.0 * (double)n * n * n);
+    k_gj_perm<<<1, 32, 0, st>>>((int)n, pivrow.p, src.p);
+    launched("k_gj_perm");
     {
         ProfScope ps_("k_gj_unpack", st);
-        k_gj_unpack<<<(unsigned)((n * n + 255) / 256), 256, 0, st>>>(n, b0, inv);
+        k_gj_unpack<<<nb, 256, 0, st>>>((int)n, b0, src.p, inv);
         launched("k_gj_unpack");
     }
+    CBFM_CUDA(cudaStreamSynchronize(st));   // the scratch arrays are released on return
 }
 
 void launch_z64_to_c32(const z64 *src, c32 *dst, int64_t n, cudaStream_t st) {
