@@ -797,23 +797,20 @@ cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
         CBFM_CUDA(cudaMemsetAsync(r->Ginv.p, 0, sizeof(z64) * n * n, st));
         DevBuf<z64> blk, aug;
         DevBuf<int> info;
-        blk.alloc((size_t)nh * nh);
+        blk.alloc((size_t)2 * nh * nh);   // the two halves, inverted as one batch
         aug.alloc((size_t)4 * nh * nh);
         info.alloc(1);
         CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int), st));
         for (int half = 0; half < 2; ++half) {
-            int64_t r0 = half * nh;
-            {
-                ProfScope ps_("k_copy_block", st);
-                k_copy_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, r0, r->G.p, blk.p);
-                launched("k_copy_block");
-            }
-            gauss_jordan_inverse(nh, aug.p, blk.p, info.p, st);
-            {
-                ProfScope ps_("k_place_block", st);
-                k_place_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, r0, blk.p, r->Ginv.p);
-                launched("k_place_block");
-            }
+            ProfScope ps_("k_copy_block", st);
+            k_copy_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, half * nh, r->G.p, blk.p + half * nh * nh);
+            launched("k_copy_block");
+        }
+        gauss_jordan_inverse(nh, 2, aug.p, blk.p, info.p, st);
+        for (int half = 0; half < 2; ++half) {
+            ProfScope ps_("k_place_block", st);
+            k_place_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, half * nh, blk.p + half * nh * nh, r->Ginv.p);
+            launched("k_place_block");
         }
         int hinfo = 0;
         CBFM_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -109,7 +109,7 @@ void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info,
 // In-place Gauss-Jordan inverse of an n x n FP64 complex matrix (row-major); info=1 on zero pivot.
 // tensor-core projection of Z (3 x ne x ne, c32) onto the CBFs into A (k_tc.cu)
 void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st);
-void gauss_jordan_inverse(int64_t n, z64 *Aug, z64 *inv, int *d_info, cudaStream_t st);
+void gauss_jordan_inverse(int64_t n, int nbatch, z64 *Aug, z64 *inv, int *d_info, cudaStream_t st);
 
 // GMRES (k_gmres.cu)
 struct GmresOut {

@@ -382,44 +382,42 @@ __device__ void potentials(const double *V, const double *r, double &I1, double 
     }
 }
 
-// (e^{-jkR} - 1)/(4 pi R), limit -jk/(4 pi) at R = 0 (power series for |kR| < 0.2,
-// where the direct form would lose digits to cancellation)
-__device__ inline z64 green_rem(z64 k, double R) {
-    z64 x = z64(k.im * R, -k.re * R);   // -j k R
-    if (sqrt(norm2(x)) < 0.2) {
-        // sum_{m>=1} x^{m-1}/m!; for |x| < 0.2 the first 12 terms leave < 1e-19
-        z64 term(1, 0), s(0, 0);
-        for (int m = 1; m <= 12; ++m) {
-            if (m > 1) term = term * x * (1.0 / m);
-            s += term;
+// The two smooth remainders of the singularity extraction, from one
+// evaluation of e^{-jkR}:
+//   gr = (e^{-jkR} - 1)/(4 pi R),                limit -jk/(4 pi) at R = 0
+//   hr = g + 1/(4 pi R^3) + k^2/(8 pi R),         limit j k^3/(12 pi) at R = 0
+// with g = -(1 + jkR) e^{-jkR}/(4 pi R^3).  For |kR| < 0.2 both come from their
+// power series in y = jkR (the direct forms would cancel):
+//   gr = -jk/(4 pi)      sum_{j>=0} (-y)^j / (j+1)!
+//   hr = -(jk)^3/(4 pi)  sum_{j>=0} (-1)^j (j+2)/(j+3)! y^j
+// where 12 terms leave < 1e-19 relative.
+__device__ inline void green_rems(z64 k, double R, z64 &gr, z64 &hr) {
+    const z64 jk(-k.im, k.re);
+    const z64 y = jk * R;
+    if (sqrt(norm2(y)) < 0.2) {
+        z64 pw(1, 0), s1(0, 0), s2(0, 0);
+        double f1 = 1.0, f3 = 6.0;   // (j+1)!, (j+3)!
+        for (int j = 0; j < 12; ++j) {
+            if (j > 0) {
+                pw = pw * y;
+                f1 *= (j + 1);
+                f3 *= (j + 3);
+            }
+            const double sg = (j & 1) ? -1.0 : 1.0;
+            s1 += (sg / f1) * pw;
+            s2 += (sg * (j + 2) / f3) * pw;
         }
-        return z64(k.im, -k.re) * s * (1.0 / (4.0 * PI));
+        gr = z64(k.im, -k.re) * s1 * (1.0 / (4.0 * PI));
+        hr = (jk * jk * jk) * s2 * (-1.0 / (4.0 * PI));
+        return;
     }
-    double e = exp(x.re), sn, cs;
-    sincos(x.im, &sn, &cs);
-    return z64(e * cs - 1.0, e * sn) * (1.0 / (4.0 * PI * R));
-}
-
-// g + 1/(4 pi R^3) + k^2/(8 pi R), limit j k^3/(12 pi) at R = 0 (power series for |kR| < 0.2)
-__device__ inline z64 gradgreen_rem(z64 k, double R) {
-    z64 jk(-k.im, k.re);
-    z64 x = jk * R;
-    if (sqrt(norm2(x)) < 0.2) {
-        // sum_{m>=3} (-1)^m (1-m)/m! x^m / R^3; 12 terms leave < 1e-19 relative
-        z64 pw = jk * jk * jk, s(0, 0);
-        double fact = 6.0;
-        for (int m = 3; m < 15; ++m) {
-            if (m > 3) { pw = pw * x; fact *= m; }
-            double cm = ((m & 1) ? -1.0 : 1.0) * (1.0 - m) / fact;
-            s += cm * pw;
-        }
-        return s * (-1.0 / (4.0 * PI));
-    }
-    double e = exp(-x.re), sn, cs;
-    sincos(-x.im, &sn, &cs);
-    z64 ex(e * cs, e * sn);   // e^{-jkR}
-    z64 g = (z64(1, 0) + x) * ex * (-1.0 / (4.0 * PI * R * R * R));
-    return g + z64(1.0 / (4.0 * PI * R * R * R), 0) + (k * k) * (1.0 / (8.0 * PI * R));
+    double sn, cs;
+    sincos(k.re * R, &sn, &cs);
+    const double e = exp(k.im * R);
+    const z64 ex(e * cs, -e * sn);   // e^{-jkR}
+    const double iR = 1.0 / R, i4pR = iR * (1.0 / (4.0 * PI)), i4pR3 = i4pR * iR * iR;
+    gr = z64(ex.re - 1.0, ex.im) * i4pR;
+    hr = (z64(1, 0) + y) * ex * (-i4pR3) + z64(i4pR3, 0) + (k * k) * (0.5 * i4pR);
 }
 
 // One warp per near pair (t <= s).  Lane = 16 o + 8 i + p: orientation o (0:
@@ -457,8 +455,10 @@ __global__ void __launch_bounds__(128) k_near_blocks(int64_t npairs, int nt, con
             double dv[3];
             sub3(r, B + TR_Q + 3 * q, dv);
             double R = sqrt(dot3(dv, dv));
-            z64 gs = green_rem(k, R) * B[TR_W + q];
-            z64 hs = gradgreen_rem(k, R) * B[TR_W + q];
+            z64 gs, hs;
+            green_rems(k, R, gs, hs);
+            gs = gs * B[TR_W + q];
+            hs = hs * B[TR_W + q];
             S0 += gs;
             for (int d = 0; d < 3; ++d) {
                 Sr[d] += gs * (-dv[d]);

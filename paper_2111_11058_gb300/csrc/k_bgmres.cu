@@ -140,13 +140,19 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol(int m, const z64 *__res
             const int pa = i + 1 + u, pb = pa + (idx - (u * n - u * (u - 1) / 2));
             const int a = piv[pa], b = piv[pb];
             const z64 ra = rb[pa], rbb = rb[pb];
-            // conj(ra) * rbb
-            const double pr = ra.re * rbb.re + ra.im * rbb.im;
-            const double pi = ra.re * rbb.im - ra.im * rbb.re;
-            const bool up = a <= b;   // stored at (a, b); else at (b, a), conjugated
+            // U -= conj(ra) rbb (stored at (a, b)) or its conjugate (stored at (b, a)): four FMAs
+            const bool up = a <= b;
             const int off = up ? PU(a, b) : PU(b, a);
-            U[off].re -= pr;
-            U[off].im -= up ? pi : -pi;
+            // conditional sign flip on the integer side (keeps the FP64 pipe for the FMAs)
+            const long long sgn = up ? 0ll : (long long)0x8000000000000000ull;
+            const double are = __longlong_as_double(__double_as_longlong(ra.re) ^ sgn);
+            const double aim = __longlong_as_double(__double_as_longlong(ra.im) ^ sgn);
+            z64 w = U[off];
+            w.re = fma(-ra.re, rbb.re, w.re);
+            w.re = fma(-ra.im, rbb.im, w.re);
+            w.im = fma(-are, rbb.im, w.im);
+            w.im = fma(aim, rbb.re, w.im);
+            U[off] = w;
         }
         __syncthreads();
     }

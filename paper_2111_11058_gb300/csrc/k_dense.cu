@@ -333,6 +333,10 @@ __device__ __forceinline__ void gj_push_key(unsigned long long key, unsigned lon
 // copy A into the first buffer and find the pivot of column 0
 __global__ void __launch_bounds__(256) k_gj_init(int n, const z64 *__restrict__ A, z64 *__restrict__ X,
                                                  unsigned long long *__restrict__ keys) {
+    // matrix blockIdx.y of the batch
+    A += (int64_t)blockIdx.y * n * n;
+    X += (int64_t)blockIdx.y * n * n;
+    keys += (int64_t)blockIdx.y * n;
     unsigned long long key = 0;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -350,6 +354,11 @@ __global__ void __launch_bounds__(256) k_gj_init(int n, const z64 *__restrict__ 
 __global__ void __launch_bounds__(256) k_gj_sweep(int n, int k, const z64 *__restrict__ Ain, z64 *__restrict__ Aout,
                                                   unsigned long long *__restrict__ keys, int *__restrict__ pivrow,
                                                   int *__restrict__ info) {
+    // matrix blockIdx.z of the batch
+    Ain += (int64_t)blockIdx.z * n * n;
+    Aout += (int64_t)blockIdx.z * n * n;
+    keys += (int64_t)blockIdx.z * n;
+    pivrow += (int64_t)blockIdx.z * n;
     __shared__ z64 s_pinv;
     __shared__ int s_p;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -410,7 +419,9 @@ __global__ void __launch_bounds__(256) k_gj_sweep(int n, int k, const z64 *__res
 
 // column order of the result: undo the interchanges, last first (one thread)
 __global__ void k_gj_perm(int n, const int *__restrict__ pivrow, int *__restrict__ src) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (threadIdx.x != 0) return;
+    pivrow += (int64_t)blockIdx.x * n;   // one block per matrix of the batch
+    src += (int64_t)blockIdx.x * n;
     for (int j = 0; j < n; ++j) src[j] = j;
     for (int k = n - 1; k >= 0; --k) {
         const int p = pivrow[k], t = src[k];
@@ -420,6 +431,9 @@ __global__ void k_gj_perm(int n, const int *__restrict__ pivrow, int *__restrict
 }
 
 __global__ void k_gj_unpack(int n, const z64 *__restrict__ X, const int *__restrict__ src, z64 *__restrict__ inv) {
+    X += (int64_t)blockIdx.y * n * n;
+    inv += (int64_t)blockIdx.y * n * n;
+    src += (int64_t)blockIdx.y * n;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx / n, j = idx % n;
@@ -530,24 +544,27 @@ void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info,
     }
 }
 
-void gauss_jordan_inverse(int64_t n, z64 *Aug, z64 *inv, int *d_info, cudaStream_t st) {
-    // Aug holds two n x n buffers; `inv` is A on entry and A^{-1} on return.
-    if (n <= 0) return;
+void gauss_jordan_inverse(int64_t n, int nbatch, z64 *Aug, z64 *inv, int *d_info, cudaStream_t st) {
+    // nbatch matrices n x n, consecutive in `inv` (A on entry, A^{-1} on
+    // return); Aug holds 2 nbatch n x n scratch matrices.  The batch shares
+    // every launch.
+    if (n <= 0 || nbatch <= 0) return;
     CBFM_REQUIRE(n < (int64_t)GJ_IMASK, "Gauss-Jordan: matrix too large for the pivot key");
-    z64 *b0 = Aug, *b1 = Aug + n * n;
+    CBFM_REQUIRE(nbatch <= 65535, "Gauss-Jordan: batch too large");
+    z64 *b0 = Aug, *b1 = Aug + (int64_t)nbatch * n * n;
     DevBuf<unsigned long long> keys;
     DevBuf<int> pivrow, src;
-    keys.alloc(n);
-    pivrow.alloc(n);
-    src.alloc(n);
-    CBFM_CUDA(cudaMemsetAsync(keys.p, 0, sizeof(unsigned long long) * n, st));
-    const unsigned nb = (unsigned)std::min<int64_t>((n * n + 255) / 256, 4 * 152);
+    keys.alloc((size_t)nbatch * n);
+    pivrow.alloc((size_t)nbatch * n);
+    src.alloc((size_t)nbatch * n);
+    CBFM_CUDA(cudaMemsetAsync(keys.p, 0, sizeof(unsigned long long) * nbatch * n, st));
+    const unsigned nb = (unsigned)std::min<int64_t>((n * n + 255) / 256, 2 * 152);
     {
         ProfScope ps_("k_gj_init", st);
-        k_gj_init<<<nb, 256, 0, st>>>((int)n, inv, b0, keys.p);
+        k_gj_init<<<dim3(nb, nbatch), 256, 0, st>>>((int)n, inv, b0, keys.p);
         launched("k_gj_init");
     }
-    const dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), blk(16, 16);
+    const dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)nbatch), blk(16, 16);
     for (int64_t k = 0; k < n; ++k) {
         {
             ProfScope ps_("k_gj_sweep", st);
@@ -556,12 +573,12 @@ void gauss_jordan_inverse(int64_t n, z64 *Aug, z64 *inv, int *d_info, cudaStream
         }
         std::swap(b0, b1);
     }
-    prof_add_work("k_gj_sweep", 8.0 * (double)n * n * n, 32.0 * (double)n * n * n);
-    k_gj_perm<<<1, 32, 0, st>>>((int)n, pivrow.p, src.p);
+    prof_add_work("k_gj_sweep", 8.0 * nbatch * (double)n * n * n, 32.0 * nbatch * (double)n * n * n);
+    k_gj_perm<<<nbatch, 32, 0, st>>>((int)n, pivrow.p, src.p);
     launched("k_gj_perm");
     {
         ProfScope ps_("k_gj_unpack", st);
-        k_gj_unpack<<<nb, 256, 0, st>>>((int)n, b0, src.p, inv);
+        k_gj_unpack<<<dim3(nb, nbatch), 256, 0, st>>>((int)n, b0, src.p, inv);
         launched("k_gj_unpack");
     }
     CBFM_CUDA(cudaStreamSynchronize(st));   // the scratch arrays are released on return
