@@ -224,6 +224,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-alt", action="store_true", help="skip the comparison with the other GMRES variant")
     ap.add_argument("--solver", default="block", choices=["block", "per_rhs"],
                     help="GMRES variant of the timed step: block GMRES over all right-hand sides, or one per RHS")
     ap.add_argument("--workload", default="cube9216", choices=["cube9216", "cube2304", "sphere960"],
@@ -325,16 +326,18 @@ def main():
     mixed_rcs = rcs_d.sum(-1).cpu().numpy()
 
     # the other GMRES variant on the same step, for comparison
-    rcs_alt = torch.zeros_like(rcs_d)
-    step_alt = make_step(P.MIXED, rcs_alt, other)
-    step_alt()
-    alt_iters = state["iters"].copy()
-    ts_alt = timed(max(1, min(args.steps, 3)), step_alt)
-    alt_rcs = rcs_alt.sum(-1).cpu().numpy()
-    alt = {"solver": "per_rhs" if other == P.PER_RHS else "block",
-           "value": ws * N_RHS / (float(np.mean(ts_alt)) / 1000.0), "ms_per_step": float(np.mean(ts_alt)),
-           "iters_max": int(alt_iters.max()),
-           "rcs_err_vs_headline": float(np.abs(alt_rcs - mixed_rcs).max() / np.abs(mixed_rcs).max())}
+    alt = None
+    if not args.no_alt:
+        rcs_alt = torch.zeros_like(rcs_d)
+        step_alt = make_step(P.MIXED, rcs_alt, other)
+        step_alt()
+        alt_iters = state["iters"].copy()
+        ts_alt = timed(max(1, min(args.steps, 3)), step_alt)
+        alt_rcs = rcs_alt.sum(-1).cpu().numpy()
+        alt = {"solver": "per_rhs" if other == P.PER_RHS else "block",
+               "value": ws * N_RHS / (float(np.mean(ts_alt)) / 1000.0), "ms_per_step": float(np.mean(ts_alt)),
+               "iters_max": int(alt_iters.max()),
+               "rcs_err_vs_headline": float(np.abs(alt_rcs - mixed_rcs).max() / np.abs(mixed_rcs).max())}
 
     # plain FP64 GPU path (the metric's denominator, same solver) and the mixed-vs-FP64 RCS difference
     fp64 = None
