@@ -154,56 +154,171 @@ def workload():
     raise ValueError(WORKLOAD)
 
 
-def cpu_sample(n_blocks: int = 6):
-    """The oracle on a bounded sample of the same workload: its dense-definition
-    reduced-matrix assembly for `n_blocks` of the 32 x 32 cell-pair blocks,
-    plus one GMRES matrix-vector product of the reduced size, extrapolated to
-    the whole step (1024 blocks, 374 GMRES iterations per RHS -- the
-    iteration count the oracle needs on this workload at tol 1e-6 -- x 128 RHS)."""
-    import oracle
+# ---- oracle baseline on the host cores (spawned worker processes, one thread each)
+_CPU = {}
+GMRES_ITERS_ORACLE = 374   # iterations the oracle needs on the bench cube at tol 1e-6
+
+
+def _cpu_init():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
     from oracle import cbfm as OC, mesh as OM
-    oracle.build()
-    d = workload()
+    d = W.cube_c2(N_RHS)
     g = d["mesh"]
     m = OM.build_rwg(g.verts, g.tris)
     cell = OM.cells_rcb(m, 32)
     Ns = np.bincount(cell)
     Ls = [14] * 32
     CM, CJ = W.random_cbfs(Ns, Ls, seed=1)
-    cbfs = [OC.CellCBF(np.nonzero(cell == c)[0], CM[c], CJ[c], np.ones(1), 14) for c in range(32)]
-    pairs = [(0, 0), (5, 9), (31, 2), (12, 12), (20, 7), (3, 28)][:n_blocks]
-    t0 = time.perf_counter()
+    _CPU.update(OC=OC, m=m, cbfs=[OC.CellCBF(np.nonzero(cell == c)[0], CM[c], CJ[c], np.ones(1), 14)
+                                  for c in range(32)], n=2 * sum(Ls))
+
+
+def _cpu_noop(_):
+    return os.getpid()
+
+
+def _cpu_blocks(pairs):
     for (a, b) in pairs:
-        OC.reduced_block(m, cbfs, 2.5, a, b)
-    t_blocks = time.perf_counter() - t0
-    n = 2 * sum(Ls)
+        _CPU["OC"].reduced_block(_CPU["m"], _CPU["cbfs"], 2.5, a, b)
+    return len(pairs)
+
+
+def _cpu_gmres(seed):
+    import scipy.linalg as sla
+    n = _CPU["n"]
+    rng = np.random.default_rng(seed)
+    A = np.eye(n) * 4 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    G = np.eye(n) * 2 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(4 * n)
+    lu = sla.lu_factor(G)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    _x, it, _h = _CPU["OC"].gmres(lambda v: A @ v, b, 0.0, 1000, GMRES_ITERS_ORACLE,
+                                  precond=lambda z: sla.lu_solve(lu, z))
+    return it
+
+
+def cpu_step(pool, cores: int) -> dict:
+    """One bounded oracle sample of the bench step on the host cores
+    (4 x cores cell-pair blocks of the reduced matrix by the oracle's dense
+    definition, both media, seeded stand-in CBFs of the workload's sizes; and
+    the oracle's GMRES -- MGS, CMP applied as an LU solve, 374 iterations --
+    for `cores` right-hand sides on a stand-in system of the same order),
+    extrapolated to the whole step: 1024 blocks and 128 right-hand sides."""
+    pairs = [(a, b) for a in range(32) for b in range(32)]
     rng = np.random.default_rng(0)
-    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
-    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    pick = [pairs[i] for i in rng.choice(len(pairs), 4 * cores, replace=False)]
+    t0 = time.perf_counter()
+    assert sum(pool.map(_cpu_blocks, [[p] for p in pick])) == len(pick)
+    t_asm = time.perf_counter() - t0
     t1 = time.perf_counter()
-    reps = 20
-    for _ in range(reps):
-        A @ x
-    t_mv = (time.perf_counter() - t1) / reps
-    t_step = t_blocks * 1024 / len(pairs) + t_mv * 374 * N_RHS
-    cores = os.cpu_count()
+    its = list(pool.map(_cpu_gmres, range(cores)))
+    t_gm = time.perf_counter() - t1
+    assert min(its) == GMRES_ITERS_ORACLE
+    t_step = t_asm * len(pairs) / len(pick) + t_gm * N_RHS / cores
     return {"value": N_RHS / t_step, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(pairs)} of 1024 cell-pair blocks of the reduced matrix (dense-definition Z, both media)"
-                      f" + one {n}x{n} complex matvec; extrapolated to 1024 blocks + 374 iter x {N_RHS} RHS GMRES",
-            "measured_s": t_blocks + t_mv * reps}
+            "sample": f"{len(pick)} of 1024 cell-pair blocks of the reduced matrix (oracle dense definition, both "
+                      f"media, seeded stand-in CBFs) + oracle GMRES ({GMRES_ITERS_ORACLE} MGS iterations, CMP as LU "
+                      f"solve) for {cores} of {N_RHS} RHS on a same-order stand-in system; extrapolated to 1024 "
+                      f"blocks and {N_RHS} RHS; {cores} worker processes, one thread each",
+            "measured_s": t_asm + t_gm}
+
+
+def cpu_pool():
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import oracle
+    oracle.build()                      # compile once before the workers load it
+    cores = os.cpu_count() or 1
+    # one thread per worker: the variables must be in the environment the
+    # spawned processes inherit, before they import numpy or load the oracle
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        pool = cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"), initializer=_cpu_init)
+        assert len(set(pool.map(_cpu_noop, range(4 * cores)))) >= 1   # start and initialise the workers
+        for f in [pool.submit(_cpu_noop, i) for i in range(cores)]:
+            f.result()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return pool, cores
+
+
+def cpu_sample() -> dict:
+    pool, cores = cpu_pool()
+    try:
+        return cpu_step(pool, cores)
+    finally:
+        pool.shutdown()
+
+
+def run_serving(budget_bytes: int) -> dict:
+    """Serving workload: Poisson arrivals of requests for scatterers of the
+    cube class (cube, sphere, finite cylinder of about one wavelength),
+    frequencies from a 16-point sweep 0.8-1.2 f0 (each frequency its own CBFs
+    and reduced system) and 1-128 monostatic excitations each, through the
+    continuous-batching service on three streams.  The closed-loop capacity is
+    measured first; then the same request class is offered at 0.5, 0.8 and
+    1.2 times that rate."""
+    from paper_2111_11058_gb300 import serve as S
+    cub, sph, cyl = W.cube(8, 1.0), W.icosphere(3, 0.5), W.cylinder(0.4, 1.0, 28, 10, 3)
+    scs = [S.Scatterer("cube", cub.verts, cub.tris, 2.5, 16, "rcb"),
+           S.Scatterer("sphere", sph.verts, sph.tris, 4.0, 16, "rcb"),
+           S.Scatterer("cylinder", cyl.verts, cyl.tris, 3.0, 16, "rcb")]
+    freqs = np.linspace(0.8, 1.2, 16)
+    pool = W.plane_wave_set(W.fibonacci_dirs(128))
+
+    def draw(count, seed):
+        rng = np.random.default_rng(seed)
+        out = []
+        for _ in range(count):
+            nrhs = int(rng.integers(1, 129))
+            exc = pool[rng.choice(pool.shape[0], nrhs, replace=False)]
+            out.append(S.Request(scs[int(rng.integers(0, 3))], float(freqs[int(rng.integers(0, 16))]), exc))
+        return out
+
+    be = S.GpuBackend(gen_dirs=64)
+    srv = S.Server(be, hbm_budget=budget_bytes, n_streams=3)
+    S.replay(srv, draw(12, 100), np.zeros(12))          # warm-up (library, pools)
+    reqs = draw(48, 101)
+    res, wall = S.replay(srv, reqs, np.zeros(len(reqs)))
+    closed = S.summarize(res, srv.log[-len(res):], wall, srv)
+    cap_req_per_s = len(reqs) / wall
+    loads = []
+    for k, f in enumerate((0.5, 0.8, 1.2)):
+        reqs = draw(48, 200 + k)
+        nlog = len(srv.log)
+        res, wall = S.replay(srv, reqs, S.poisson_arrivals(f * cap_req_per_s, len(reqs), seed=300 + k))
+        st = S.summarize(res, srv.log[nlog:], wall, srv)
+        st["offered_x_capacity"] = f
+        loads.append(st)
+    srv.close()
+    return {"recipe": "cube 2304 / sphere 3840 / cylinder unknowns, 16 cells, s=128, 16 frequencies 0.8-1.2, "
+                      "1-128 RHS per request, 48 requests per load, 3 streams, MIXED, block GMRES tol 1e-6",
+            "budget_bytes": int(budget_bytes), "closed_loop": closed, "capacity_req_per_s": cap_req_per_s,
+            "loads": loads}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        cpu_sample(2)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(cpu_sample(2))
-    wall = time.perf_counter() - t0
+    pool, cores = cpu_pool()
+    try:
+        for _ in range(args.warmup):
+            cpu_step(pool, cores)
+        vals = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            vals.append(cpu_step(pool, cores))
+        wall = time.perf_counter() - t0
+    finally:
+        pool.shutdown()
     v = float(np.median([x["value"] for x in vals]))
     cb = dict(vals[0])
     cb["value"] = v
@@ -225,6 +340,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-alt", action="store_true", help="skip the comparison with the other GMRES variant")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) run")
     ap.add_argument("--solver", default="block", choices=["block", "per_rhs"],
                     help="GMRES variant of the timed step: block GMRES over all right-hand sides, or one per RHS")
     ap.add_argument("--workload", default="cube9216", choices=["cube9216", "cube2304", "sphere960"],
@@ -349,6 +465,11 @@ def main():
         fp64 = {"value": ws * N_RHS / (t64[0] / 1000.0), "ms_per_step": t64[0], "rcs_err_mixed_vs_fp64": err,
                 "speedup_mixed_over_fp64": (t64[0] / t_step)}
 
+    serving = None
+    if not args.no_serve and ws == 1 and WORKLOAD == "cube9216":
+        free, _tot = torch.cuda.mem_get_info()
+        serving = run_serving(int(free * 0.6))
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
@@ -365,7 +486,7 @@ def main():
                 "gpu_launches": int(launches), "roofline": roof,
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
-                "fp64_path": fp64, "other_solver": alt}
+                "fp64_path": fp64, "other_solver": alt, "serving": serving}
         if not args.no_cpu and ws == 1 and WORKLOAD == "cube9216":
             try:
                 line["cpu_baseline"] = cpu_sample()

@@ -15,6 +15,20 @@
 namespace cbfm {
 
 std::atomic<int64_t> g_launches{0};
+thread_local CallStream g_call;
+
+void pool_setup() {
+    static std::atomic<uint64_t> done{0};   // one bit per device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    if (done.load(std::memory_order_acquire) & (1ull << dev)) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = 8ull << 30;   // freed scratch stays cached up to 8 GiB between calls
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done.fetch_or(1ull << dev, std::memory_order_acq_rel);
+}
 std::atomic<bool> g_prof{false};
 static thread_local std::string t_err;
 
@@ -325,6 +339,7 @@ cbfm_status cbfm_mesh(const double *verts, int64_t nv, const int32_t *tris, int6
                       int32_t ncell, int32_t partition, double eps_re, double eps_im, double mu_r, double alpha,
                       void *stream, cbfm_mesh_t *out) {
     return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         CBFM_REQUIRE(out != nullptr && verts != nullptr && tris != nullptr, "NULL argument");
         *out = nullptr;
         CBFM_REQUIRE(eps_im <= 0.0, "eps_im must be <= 0 (passive medium, exp(+j w t))");
@@ -420,6 +435,7 @@ cbfm_status cbfm_mesh_info(cbfm_mesh_t mesh, int64_t *n_edges, int32_t *n_cells,
 
 cbfm_status cbfm_mesh_cells(cbfm_mesh_t mesh, int32_t *edge_cell, void *stream) {
     return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Mesh *m = (Mesh *)mesh;
         check_device(m, H_MESH, "mesh");
         CBFM_REQUIRE(edge_cell, "NULL edge_cell");
@@ -431,6 +447,7 @@ cbfm_status cbfm_mesh_cells(cbfm_mesh_t mesh, int32_t *edge_cell, void *stream) 
 cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, double delta_svd, int32_t lmax,
                             void *stream, cbfm_cbf_t *out, int32_t *L_per_cell, double *sigma_out) {
     return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Mesh *m = (Mesh *)mesh;
         check_device(m, H_MESH, "mesh");
         CBFM_REQUIRE(out && waves && L_per_cell, "NULL argument");
@@ -601,6 +618,7 @@ cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, do
 cbfm_status cbfm_cbf_import(cbfm_mesh_t mesh, const int32_t *L_per_cell, const double *CM, const double *CJ,
                             void *stream, cbfm_cbf_t *out) {
     return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Mesh *m = (Mesh *)mesh;
         check_device(m, H_MESH, "mesh");
         CBFM_REQUIRE(out && L_per_cell && CM && CJ, "NULL argument");
@@ -629,6 +647,7 @@ cbfm_status cbfm_cbf_import(cbfm_mesh_t mesh, const int32_t *L_per_cell, const d
 
 cbfm_status cbfm_cbf_export(cbfm_cbf_t cbf, double *CM, double *CJ, void *stream) {
     return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Cbf *c = (Cbf *)cbf;
         check_device(c, H_CBF, "cbf");
         int64_t tot = c->boff.back();
@@ -657,7 +676,7 @@ void project(Red &r, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (r.prec == CBFM_MIXED) {
             project_tc(m, c, Z.p, A.p, st);
-            r.A32.p = A.p; r.A32.n = A.n; A.p = nullptr; A.n = 0;
+            A.give(r.A32);
             return;
         }
     }
@@ -682,9 +701,9 @@ void project(Red &r, cudaStream_t st) {
         gemm_grouped<T>(g2, 2, 0, ch[q].rowJ ? CJ : CM, Y.p, A.p, false, st);
     }
     if constexpr (sizeof(T) == 8) {
-        r.A64.p = A.p; r.A64.n = A.n; A.p = nullptr; A.n = 0;
+        A.give(r.A64);
     } else {
-        r.A32.p = A.p; r.A32.n = A.n; A.p = nullptr; A.n = 0;
+        A.give(r.A32);
     }
 }
 
@@ -695,6 +714,7 @@ extern "C" {
 cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precision prec, void *stream, cbfm_red_t *out,
                                   int64_t *n_cbf) {
     return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Mesh *m = (Mesh *)mesh;
         Cbf *c = (Cbf *)cbf;
         check_device(m, H_MESH, "mesh");
@@ -721,6 +741,7 @@ cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precisi
 
 cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream) {
     return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Red *r = (Red *)red;
         check_device(r, H_RED, "reduced system");
         CBFM_REQUIRE(A, "NULL A");
@@ -749,6 +770,7 @@ cbfm_status cbfm_red_export_noalloc(cbfm_red_t red, double *A, void *stream) {
 
 cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
     return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Red *r = (Red *)red;
         check_device(r, H_RED, "reduced system");
         cudaStream_t st = (cudaStream_t)stream;
@@ -834,6 +856,7 @@ cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
 
 cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream) {
     return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Red *r = (Red *)red;
         check_device(r, H_RED, "reduced system");
         CBFM_REQUIRE(r->cmp_ready, "call cbfm_cmp_setup first");
@@ -848,6 +871,7 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
                        double *rcs_out, int32_t *iters_out, double *resid_out, void *stream) {
     cbfm_status conv = CBFM_OK;
     cbfm_status st_ = guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Red *r = (Red *)red;
         check_device(r, H_RED, "reduced system");
         CBFM_REQUIRE(exc && nrhs >= 1, "need at least one excitation");

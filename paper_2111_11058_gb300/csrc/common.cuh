@@ -110,29 +110,79 @@ constexpr int TRI_REC = 48;
 constexpr int TR_Q = 0, TR_W = 21, TR_P = 28, TR_C = 37, TR_CEN = 40, TR_H = 43, TR_CLO = 44;
 
 // ---------------------------------------------------------- device memory
+// The stream of the API call that runs on this thread.  Scratch buffers
+// allocated during a call come from the stream-ordered pool on that stream and
+// go back to it on the same stream, so concurrent calls on different streams
+// do not synchronise the device through cudaMalloc / cudaFree.
+struct CallStream {
+    cudaStream_t st = nullptr;
+    bool valid = false;
+};
+extern thread_local CallStream g_call;
+void pool_setup();   // once per device: keep freed pool memory cached for the next call
+
+struct StreamScope {
+    CallStream saved;
+    explicit StreamScope(cudaStream_t s) : saved(g_call) {
+        pool_setup();
+        g_call.st = s;
+        g_call.valid = true;
+    }
+    ~StreamScope() { g_call = saved; }
+    StreamScope(const StreamScope &) = delete;
+    StreamScope &operator=(const StreamScope &) = delete;
+};
+
+// Device buffer.  Inside an API call it is stream-ordered on the call's
+// stream; a buffer that outlives the call (owned by a handle, or released
+// from another call or stream) is returned with cudaFree, which also accepts
+// pool memory.
 template <typename T>
 struct DevBuf {
     T *p = nullptr;
     size_t n = 0;
+    cudaStream_t st = nullptr;
+    bool pooled = false;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (pooled && g_call.valid && g_call.st == st) cudaFreeAsync(p, st);
+            else cudaFree(p);
+        }
         p = nullptr;
         n = 0;
+        pooled = false;
     }
     void alloc(size_t count) {
         release();
         if (count == 0) return;
-        cudaError_t e = cudaMalloc((void **)&p, count * sizeof(T));
+        cudaError_t e;
+        if (g_call.valid) {
+            e = cudaMallocAsync((void **)&p, count * sizeof(T), g_call.st);
+            pooled = e == cudaSuccess;
+            st = g_call.st;
+        } else {
+            e = cudaMalloc((void **)&p, count * sizeof(T));
+        }
         if (e != cudaSuccess) {
             p = nullptr;
-            throw Fail{CBFM_ENOMEM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+            pooled = false;
+            throw Fail{CBFM_ENOMEM, std::string("device allocation of ") + std::to_string(count * sizeof(T)) +
                                         " bytes: " + cudaGetErrorString(e)};
         }
         n = count;
+    }
+    // hand the allocation to another buffer (it will be returned with cudaFree)
+    void give(DevBuf &dst) {
+        dst.release();
+        dst.p = p;
+        dst.n = n;
+        p = nullptr;
+        n = 0;
+        pooled = false;
     }
 };
 

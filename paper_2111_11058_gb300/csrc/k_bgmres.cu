@@ -18,6 +18,7 @@
 //     column (block Gram-Schmidt + Cholesky QR, again applied twice).
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <vector>
 
 #include "internal.cuh"
@@ -327,13 +328,13 @@ struct Ctx {
 
 // Pivoted / plain Cholesky on the m x m Gram matrix already in ctx.M; returns rank (host sync).
 int pchol(Ctx &c, int m, double tol, bool pivot) {
-    static bool attr_set[64] = {false};
+    static std::atomic<bool> attr_set[64];   // zero-initialised (static storage)
     int dev = 0;
     CBFM_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !attr_set[dev]) {
+    if (dev < 64 && !attr_set[dev].load(std::memory_order_acquire)) {
         CBFM_CUDA(cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)pchol_smem(PCHOL_MAX)));
-        attr_set[dev] = true;
+        attr_set[dev].store(true, std::memory_order_release);
     }
     {
         CBFM_REQUIRE(m >= 1 && m <= PCHOL_MAX, "pivoted Cholesky: block width out of range");

@@ -32,6 +32,7 @@
 #include <cuda.h>   // CUtensorMap and its enums (the encoder is looked up in the driver at run time)
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "internal.cuh"
@@ -432,14 +433,14 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, vo
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeFn encoder() {
-    static EncodeFn fn = nullptr;
-    if (!fn) {
+    // thread-safe one-time lookup (a failed lookup is retried on the next call)
+    static const EncodeFn fn = [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         CBFM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
         CBFM_REQUIRE(q == cudaDriverEntryPointSuccess && p, "cuTensorMapEncodeTiled not available from the driver");
-        fn = (EncodeFn)p;
-    }
+        return (EncodeFn)p;
+    }();
     return fn;
 }
 
@@ -472,13 +473,13 @@ void launch_tc(const TcMaps &maps, const std::vector<TcTask> &tasks, TcParams P,
     P.stages = (int)std::min<size_t>(4, TC_SMEM_BUDGET / P.stage_bytes);
     CBFM_REQUIRE(P.stages >= 2, "tensor-core tile: stages do not fit in shared memory");
     const size_t smem = (size_t)P.stages * P.stage_bytes + 1024;   // + alignment slack
-    static bool attr[64] = {false};
+    static std::atomic<bool> attr[64];   // zero-initialised (static storage)
     int dev = 0;
     CBFM_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !attr[dev]) {
+    if (dev < 64 && !attr[dev].load(std::memory_order_acquire)) {
         CBFM_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(TC_SMEM_BUDGET + 1024)));
-        attr[dev] = true;
+        attr[dev].store(true, std::memory_order_release);
     }
     DevBuf<TcTask> dt;
     dt.alloc(tasks.size());
