@@ -139,6 +139,33 @@ cbfm_status cbfm_cbf_export(cbfm_cbf_t cbf, double *CM, double *CJ, void *stream
 cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precision prec,
                                   void *stream, cbfm_red_t *out, int64_t *n_cbf);
 
+/*
+ * cbfm_assemble_reduced_batch -- cbfm_assemble_reduced for `count` scatterers
+ * at once (mixed precision only: prec must be CBFM_MIXED).  Each stage of the
+ * assembly (far pairs, near pairs, RWG gather, the two tensor-core projection
+ * products) is one launch over the work of all scatterers: the far stage runs
+ * persistent CTAs that take (scatterer, test triangle, strip of trial
+ * triangles) tasks from an atomic counter, so scatterers of uneven size share
+ * the GPU.  The strip width is picked on the first call per device by timing
+ * the candidates (see cbfm_tuning).  Scatterers are processed in waves whose
+ * transient operators fit in half of the free device memory.
+ *   meshes, cbfs  count handles (cbfs[k] built on meshes[k])
+ *   out           count new reduced-system handles (NULL on failure)
+ *   n_cbf         out, count values of N^CBF (may be NULL)
+ * Each out[k] equals what cbfm_assemble_reduced(meshes[k], cbfs[k],
+ * CBFM_MIXED) returns.  Returns after the work has completed.
+ */
+cbfm_status cbfm_assemble_reduced_batch(const cbfm_mesh_t *meshes, const cbfm_cbf_t *cbfs, int32_t count,
+                                        cbfm_precision prec, void *stream, cbfm_red_t *out, int64_t *n_cbf);
+
+/*
+ * cbfm_tuning -- the launch parameters tuned so far in this process, as a
+ * JSON object {"name": value, ...} written to buf (NUL-terminated, truncated
+ * to cap bytes).  Returns the length of the full text.  Library service; the
+ * paper has no counterpart.
+ */
+int64_t cbfm_tuning(char *buf, int64_t cap);
+
 /* A as complex128 row-major (n_cbf, n_cbf), host or device. */
 cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream);
 

@@ -1,10 +1,13 @@
 """GB300 (sm_103a) CBFM + Calderon-preconditioned PMCHWT solver.
 
 The compute path lives in libcbfm.so (hand-written CUDA, C ABI in
-include/cbfm.h); `cbfm` is its thin Python binding and `build` compiles it.
+include/cbfm.h); `cbfm` is its thin Python binding, `build` compiles it and
+`serve` is the continuous-batching solve service built on the binding.
 """
-from .cbfm import (BLOCK, FP64, MIXED, MIXED_SIMT, PER_RHS, CbfmError, assemble_reduced, build_cbfs, cbf_import, cmp_setup, launch_count,
-                   mesh, mesh_edges, profile, profile_read, solve)
+from .cbfm import (BLOCK, FP64, MIXED, MIXED_SIMT, PER_RHS, CbfmError, assemble_reduced, assemble_reduced_batch,
+                   build_cbfs, cbf_import, cmp_setup, launch_count, mesh, mesh_edges, profile, profile_read, solve,
+                   tuning)
 
-__all__ = ["BLOCK", "PER_RHS", "FP64", "MIXED", "MIXED_SIMT", "CbfmError", "assemble_reduced", "build_cbfs", "cbf_import", "cmp_setup",
-           "launch_count", "mesh", "mesh_edges", "profile", "profile_read", "solve"]
+__all__ = ["BLOCK", "PER_RHS", "FP64", "MIXED", "MIXED_SIMT", "CbfmError", "assemble_reduced", "assemble_reduced_batch",
+           "build_cbfs", "cbf_import", "cmp_setup", "launch_count", "mesh", "mesh_edges", "profile", "profile_read",
+           "solve", "tuning"]

@@ -12,6 +12,7 @@ built for another machine; there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 from dataclasses import dataclass
 
@@ -62,6 +63,7 @@ def lib():
             "cbfm_cbf_import": [_vp, _vp, _vp, _vp, _vp, _vp],
             "cbfm_cbf_export": [_vp, _vp, _vp, _vp],
             "cbfm_assemble_reduced": [_vp, _vp, _i32, _vp, _vp, _vp],
+            "cbfm_assemble_reduced_batch": [_vp, _vp, _i32, _i32, _vp, _vp, _vp],
             "cbfm_red_export": [_vp, _vp, _vp],
             "cbfm_red_export_noalloc": [_vp, _vp, _vp],
             "cbfm_cmp_setup": [_vp, _vp],
@@ -82,6 +84,8 @@ def lib():
         L.cbfm_profile.restype = None
         L.cbfm_profile_read.argtypes = [ctypes.c_char_p, _i64, _i32]
         L.cbfm_profile_read.restype = ctypes.c_int64
+        L.cbfm_tuning.argtypes = [ctypes.c_char_p, _i64]
+        L.cbfm_tuning.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -89,7 +93,7 @@ def lib():
 def exported_symbols():
     """Names of the C entry points declared in include/cbfm.h."""
     return ["cbfm_mesh", "cbfm_mesh_edges", "cbfm_mesh_info", "cbfm_mesh_cells", "cbfm_build_cbfs", "cbfm_cbf_import",
-            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_gram_export",
+            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_gram_export",
             "cbfm_solve", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
             "cbfm_profile_read"]
 
@@ -289,6 +293,29 @@ def assemble_reduced(m: Mesh, c: CBFs, prec: int = FP64, stream=None) -> Reduced
     _check(lib().cbfm_assemble_reduced(m.handle, c.handle, int(prec), _stream(stream), ctypes.byref(h),
                                        ctypes.byref(n)))
     return Reduced(h, c, int(n.value), prec)
+
+
+def assemble_reduced_batch(meshes, cbfs, prec: int = MIXED, stream=None) -> list:
+    """cbfm_assemble_reduced_batch: reduced systems of several scatterers, one launch per stage."""
+    cnt = len(meshes)
+    if len(cbfs) != cnt:
+        raise ValueError("meshes and cbfs differ in length")
+    hm = (ctypes.c_void_p * max(1, cnt))(*[m.handle for m in meshes])
+    hc = (ctypes.c_void_p * max(1, cnt))(*[c.handle for c in cbfs])
+    out = (ctypes.c_void_p * max(1, cnt))()
+    n = np.zeros(max(1, cnt), np.int64)
+    _check(lib().cbfm_assemble_reduced_batch(ctypes.cast(hm, ctypes.c_void_p), ctypes.cast(hc, ctypes.c_void_p), cnt,
+                                             int(prec), _stream(stream), ctypes.cast(out, ctypes.c_void_p),
+                                             ctypes.c_void_p(n.ctypes.data)))
+    return [Reduced(ctypes.c_void_p(out[k]), cbfs[k], int(n[k]), prec) for k in range(cnt)]
+
+
+def tuning() -> dict:
+    """cbfm_tuning: launch parameters tuned so far in this process."""
+    n = lib().cbfm_tuning(None, 0)
+    buf = ctypes.create_string_buffer(int(n) + 1)
+    lib().cbfm_tuning(buf, len(buf))
+    return json.loads(buf.value.decode())
 
 
 def cmp_setup(r: Reduced, stream=None) -> None:

@@ -17,6 +17,23 @@ namespace cbfm {
 std::atomic<int64_t> g_launches{0};
 thread_local CallStream g_call;
 
+// tuned launch parameters (first use on a device picks them by timing)
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+}  // namespace
+
+int tuning_get(const std::string &key) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    return it == g_tune.end() ? 0 : it->second;
+}
+
+void tuning_set(const std::string &key, int value) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = value;
+}
+
 void pool_setup() {
     static std::atomic<uint64_t> done{0};   // one bit per device
     int dev = 0;
@@ -306,6 +323,25 @@ extern "C" {
 const char *cbfm_last_error(void) { return t_err.c_str(); }
 
 int64_t cbfm_launch_count(void) { return g_launches.load(); }
+
+int64_t cbfm_tuning(char *buf, int64_t cap) {
+    std::string j = "{";
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        bool first = true;
+        for (auto &kv : g_tune) {
+            j += (first ? "\"" : ", \"") + kv.first + "\": " + std::to_string(kv.second);
+            first = false;
+        }
+    }
+    j += "}";
+    if (buf && cap > 0) {
+        const size_t n = std::min<size_t>((size_t)cap - 1, j.size());
+        std::memcpy(buf, j.data(), n);
+        buf[n] = 0;
+    }
+    return (int64_t)j.size();
+}
 
 void cbfm_profile(int32_t enable) {
     prof_flush();
@@ -737,6 +773,76 @@ cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precisi
         if (n_cbf) *n_cbf = r->n;
         *out = (cbfm_red_t)r.release();
     });
+}
+
+cbfm_status cbfm_assemble_reduced_batch(const cbfm_mesh_t *meshes, const cbfm_cbf_t *cbfs, int32_t count,
+                                        cbfm_precision prec, void *stream, cbfm_red_t *out, int64_t *n_cbf) {
+    // created handles are freed again if a later wave fails
+    std::vector<std::unique_ptr<Red>> made;
+    cbfm_status st_ = guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
+        CBFM_REQUIRE(count >= 0, "negative count");
+        CBFM_REQUIRE(count == 0 || (meshes && cbfs && out), "NULL array");
+        CBFM_REQUIRE(prec == CBFM_MIXED, "batched assembly runs the mixed-precision path (CBFM_MIXED) only");
+        for (int32_t k = 0; k < count; ++k) out[k] = nullptr;
+        cudaStream_t st = (cudaStream_t)stream;
+        std::vector<Mesh *> ms(count);
+        std::vector<Cbf *> cs(count);
+        for (int32_t k = 0; k < count; ++k) {
+            ms[k] = (Mesh *)meshes[k];
+            cs[k] = (Cbf *)cbfs[k];
+            check_device(ms[k], H_MESH, "mesh");
+            check_device(cs[k], H_CBF, "cbf");
+            CBFM_REQUIRE(cs[k]->mesh == ms[k], "cbf handle belongs to another mesh");
+        }
+        // waves of scatterers whose transient operators fit in half of the free device memory
+        size_t free_b = 0, total_b = 0;
+        CBFM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        const double budget = 0.5 * (double)free_b;
+        auto transient = [&](int k) {
+            const double nt = (double)ms[k]->h.nt, ne = (double)ms[k]->h.ne, nh = (double)cs[k]->nhalf;
+            const double ldz = std::ceil(2.0 * ne / 32.0) * 32.0;
+            return 27.0 * nt * nt * 8 + 3.0 * ne * ne * 8 + 6.0 * ne * ldz * 4 + 8.0 * 2 * nh * ldz * 4 +
+                   4.0 * nh * nh * 8;
+        };
+        made.resize(count);
+        int32_t k0 = 0;
+        while (k0 < count) {
+            int32_t k1 = k0;
+            double used = 0.0;
+            while (k1 < count && (k1 == k0 || used + transient(k1) <= budget)) used += transient(k1++);
+            std::vector<Mesh *> wm(ms.begin() + k0, ms.begin() + k1);
+            std::vector<Cbf *> wc(cs.begin() + k0, cs.begin() + k1);
+            std::vector<DevBuf<c32>> Z(k1 - k0);
+            std::vector<c32 *> Zp, Ap;
+            std::vector<const c32 *> Zc;
+            for (int32_t k = k0; k < k1; ++k) {
+                std::unique_ptr<Red> r(new Red());
+                r->kind = H_RED;
+                r->device = ms[k]->device;
+                r->mesh = ms[k];
+                r->cbf = cs[k];
+                r->prec = CBFM_MIXED;
+                r->n = 2 * cs[k]->nhalf;
+                r->A32.alloc((size_t)r->n * r->n);
+                const int64_t ne = ms[k]->h.ne;
+                Z[k - k0].alloc((size_t)3 * ne * ne);
+                Zp.push_back(Z[k - k0].p);
+                Zc.push_back(Z[k - k0].p);
+                Ap.push_back(r->A32.p);
+                made[k] = std::move(r);
+            }
+            assemble_rwg_batch<float>(wm, Zp, st);
+            project_tc_batch(wm, wc, Zc, Ap, st);
+            CBFM_CUDA(cudaStreamSynchronize(st));
+            k0 = k1;
+        }
+        for (int32_t k = 0; k < count; ++k) {
+            if (n_cbf) n_cbf[k] = made[k]->n;
+            out[k] = (cbfm_red_t)made[k].release();
+        }
+    });
+    return st_;   // on failure `made` frees what was built
 }
 
 cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream) {

@@ -1,6 +1,7 @@
 // internal.cuh -- handle structures and kernel entry points of the library.
 #pragma once
 
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -107,8 +108,16 @@ void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, cons
 // One-sided Jacobi SVD of nb column-major s x s complex matrices X (overwritten by U Sigma), V out.
 void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info, cudaStream_t st);
 // In-place Gauss-Jordan inverse of an n x n FP64 complex matrix (row-major); info=1 on zero pivot.
+// local blocks and RWG operators of several meshes, one launch per stage (k_assembly.cu)
+template <typename T>
+void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st);
+// tuned launch parameters, per key (api.cu); 0 when not tuned yet
+int tuning_get(const std::string &key);
+void tuning_set(const std::string &key, int value);
 // tensor-core projection of Z (3 x ne x ne, c32) onto the CBFs into A (k_tc.cu)
 void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st);
+void project_tc_batch(const std::vector<Mesh *> &ms, const std::vector<Cbf *> &cs, const std::vector<const c32 *> &Z,
+                      const std::vector<c32 *> &A, cudaStream_t st);
 void gauss_jordan_inverse(int64_t n, int nbatch, z64 *Aug, z64 *inv, int *d_info, cudaStream_t st);
 
 // GMRES (k_gmres.cu)

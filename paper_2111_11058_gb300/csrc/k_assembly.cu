@@ -1,8 +1,11 @@
 // k_assembly.cu -- Galerkin assembly of the PMCHWT blocks (paper Sec. II-B,
 // Eqs. (K), (T), (Z)).
 //
-// Stage 1, far pairs (k_far): one thread per (test triangle t, trial triangle s)
-//   evaluates both media over the 7 x 7 point pairs and reduces them to 18
+// Every stage runs over any number of meshes in one launch (a single mesh is
+// a batch of one).
+// Stage 1, far pairs (k_far): persistent CTAs take tasks (mesh, test triangle
+//   t, strip of trial triangles) from an atomic counter; one thread per trial
+//   triangle s evaluates both media over the 7 x 7 point pairs and reduces them to 18
 //   complex moments per medium, from which the 3 x 3 local blocks follow:
 //     T_ab = -j k c_a c_b [ Mrs - pi'_b.Mr - pi_a.Ms + (pi_a.pi'_b - 4/k^2) M0 ]
 //     K_ab =      c_a c_b [ MrX - pi_a.MX - pi'_b.MrW + pi_a.(MW x pi'_b) ]
@@ -15,12 +18,16 @@
 //   The minus sign on T is the reading under which the paper's block matrix
 //   describes the exp(+j w t) problem.  Blocks are combined into
 //   Ks = K1 + K2, Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2.
-// Stage 2, near pairs (k_near_blocks, FP64 always): 1/R, 1/R^3 and k^2/(2R)
+// Stage 2, near pairs (k_near_blocks, FP64 always, one warp per pair): 1/R, 1/R^3 and k^2/(2R)
 //   integrated in closed form over the trial triangle (Wilton et al. 1984,
 //   Graglia 1993 edge sums), bounded remainders by the 7-point rule, blocks
 //   symmetrised L(t,s) = (L~(t,s) + L~(s,t)^T)/2; K of a triangle with itself is 0.
-// Stage 3 (k_gather): RWG entries Z_op[i][j] = sum over the 2 x 2 triangle
-//   pairs of the two supports.
+// Stage 3 (k_gather, one block per RWG row): RWG entries Z_op[i][j] = sum over
+//   the 2 x 2 triangle pairs of the two supports.
+#include <algorithm>
+#include <string>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace cbfm {
@@ -163,7 +170,6 @@ __device__ __forceinline__ void fold_entries(const Mom<T> &m, T kr, T ki, cx<T> 
     }
 }
 
-// Stage 1.  Grid: x over trial triangles (blockDim.x each), y over test triangles.
 // Near test for the far kernel: the squared centroid distance in the kernel's
 // type decides all pairs clear of the threshold by a relative margin of 1e-5;
 // only pairs inside that band repeat the exact FP64 test of the near list.
@@ -185,30 +191,46 @@ __device__ __forceinline__ bool is_near_t(const T *rt_cen, const T *rt_lo, T ht,
     return is_near(rt64, rs64, vt, vs, alpha);
 }
 
+// Test-triangle data of the far kernel, staged in shared memory once per
+// test triangle and read by every trial-triangle thread.
 template <typename T>
-__global__ void __launch_bounds__(128) k_far(int nt, const T *__restrict__ rec, const double *__restrict__ rec64,
-                                             const int32_t *__restrict__ vid, double alpha, MediaT<T> md,
-                                             cx<T> *__restrict__ Zloc) {
-    __shared__ T sq[21], sw[7], sp[9], sc[3], scen[3], sclo[3], sh_t;
-    __shared__ double sc64[TRI_REC];
-    __shared__ int32_t sv[3];
-    const int t = blockIdx.y;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (threadIdx.x < TRI_REC) {
-        int i = threadIdx.x;
-        T v = rec[(int64_t)t * TRI_REC + i];
-        if (i < 21) sq[i] = v;
-        else if (i < 28) sw[i - 21] = v;
-        else if (i < 37) sp[i - 28] = v;
-        else if (i < 40) sc[i - 37] = v;
-        else if (i < 43) scen[i - 40] = v;   // centroid in the same frame as the points
-        else if (i == 43) sh_t = v;
-        else if (i < 47) sclo[i - 44] = v;
-        sc64[i] = rec64[(int64_t)t * TRI_REC + i];
-        if (i < 3) sv[i] = vid[3 * t + i];
+struct FarShared {
+    T sq[21], sw[7], sp[9], sc[3], scen[3], sclo[3], sh_t;
+    double sc64[TRI_REC];
+    int32_t sv[3];
+};
+
+template <typename T>
+__device__ __forceinline__ void far_load(FarShared<T> &S, const T *__restrict__ rec, const double *__restrict__ rec64,
+                                         const int32_t *__restrict__ vid, int t) {
+    for (int i = threadIdx.x; i < TRI_REC; i += blockDim.x) {
+        const T v = rec[(int64_t)t * TRI_REC + i];
+        if (i < 21) S.sq[i] = v;
+        else if (i < 28) S.sw[i - 21] = v;
+        else if (i < 37) S.sp[i - 28] = v;
+        else if (i < 40) S.sc[i - 37] = v;
+        else if (i < 43) S.scen[i - 40] = v;   // centroid in the same frame as the points
+        else if (i == 43) S.sh_t = v;
+        else if (i < 47) S.sclo[i - 44] = v;
+        S.sc64[i] = rec64[(int64_t)t * TRI_REC + i];
+        if (i < 3) S.sv[i] = vid[3 * t + i];
     }
-    __syncthreads();
-    if (s >= nt) return;
+}
+
+template <typename T>
+__device__ __forceinline__ void far_pair(const FarShared<T> &S, int nt, const T *__restrict__ rec,
+                                         const double *__restrict__ rec64, const int32_t *__restrict__ vid,
+                                         double alpha, const MediaT<T> &md, cx<T> *__restrict__ Zloc, int t, int s);
+
+// One far (or, by the classification, near -> zero) triangle pair (t, s).
+template <typename T>
+__device__ __forceinline__ void far_pair(const FarShared<T> &S, int nt, const T *__restrict__ rec,
+                                         const double *__restrict__ rec64, const int32_t *__restrict__ vid,
+                                         double alpha, const MediaT<T> &md, cx<T> *__restrict__ Zloc, int t, int s) {
+    const T *sq = S.sq, *sw = S.sw, *sp = S.sp, *sc = S.sc, *scen = S.scen, *sclo = S.sclo;
+    const T sh_t = S.sh_t;
+    const double *sc64 = S.sc64;
+    const int32_t *sv = S.sv;
     const T *rs = rec + (int64_t)s * TRI_REC;
     const int64_t plane = (int64_t)nt * nt;
     const int64_t base = (int64_t)t * nt + s;
@@ -426,14 +448,13 @@ __device__ inline void green_rems(z64 k, double R, z64 &gr, z64 &hr) {
 // contribution to the 3 x 3 K and T blocks; groups of eight reduce over p, and
 // lane 0 symmetrises, weights the media into Ks, Ta, Tb and stores both (t,s)
 // and (s,t).
+// One near pair (t, s), called by a whole warp; `sm` is the warp's slot of
+// shared memory (4 x 9 complex K and T sums).
 template <typename T>
-__global__ void __launch_bounds__(128) k_near_blocks(int64_t npairs, int nt, const int32_t *__restrict__ pairs,
-                                                     const double *__restrict__ rec, Media md,
-                                                     cx<T> *__restrict__ Zloc) {
+__device__ __forceinline__ void near_pair(int t, int s, int nt, const double *__restrict__ rec, const Media &md,
+                                          cx<T> *__restrict__ Zloc, z64 (*sm)[2][2][9]) {
     const int lane = threadIdx.x & 31;
-    const int64_t pid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (pid >= npairs) return;
-    const int t = pairs[2 * pid], s = pairs[2 * pid + 1];
+    __syncwarp();   // the slot's previous readers are done
     const int o = lane >> 4, med = (lane >> 3) & 1, p = lane & 7;
     z64 accK[9], accT[9];
     for (int c = 0; c < 9; ++c) accK[c] = accT[c] = z64(0, 0);
@@ -496,8 +517,6 @@ __global__ void __launch_bounds__(128) k_near_blocks(int64_t npairs, int nt, con
         }
     }
     // group sums to shared memory: sm[o][i][K|T][c]
-    __shared__ z64 sm_all[4][2][2][2][9];
-    z64 (*sm)[2][2][9] = sm_all[(threadIdx.x >> 5) & 3];
     if (p == 0)
         for (int c = 0; c < 9; ++c) {
             sm[o][med][0][c] = accK[c];
@@ -525,69 +544,207 @@ __global__ void __launch_bounds__(128) k_near_blocks(int64_t npairs, int nt, con
     }
 }
 
-// Stage 3: Z_op[i][j] from the local blocks (deterministic gather).
+// ------------------------------------------------ several meshes at once
+// One job per mesh; the batch kernels flatten the meshes' work items and find
+// the job of an item by binary search over the jobs' first item.
 template <typename T>
-__global__ void k_gather(int64_t ne, int nt, const int32_t *__restrict__ edge_tri, const int32_t *__restrict__ edge_loc,
-                         const cx<T> *__restrict__ Zloc, cx<T> *__restrict__ Z) {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t i = blockIdx.y;
-    if (j >= ne) return;
-    const int64_t plane = (int64_t)nt * nt;
-    int ti[2] = {edge_tri[2 * i], edge_tri[2 * i + 1]}, ai[2] = {edge_loc[2 * i], edge_loc[2 * i + 1]};
-    int tj[2] = {edge_tri[2 * j], edge_tri[2 * j + 1]}, aj[2] = {edge_loc[2 * j], edge_loc[2 * j + 1]};
-    for (int op = 0; op < 3; ++op) {
-        cx<T> v(0, 0);
-        for (int s = 0; s < 2; ++s)
-            for (int sp = 0; sp < 2; ++sp)
-                v += Zloc[(op * 9 + 3 * ai[s] + aj[sp]) * plane + (int64_t)ti[s] * nt + tj[sp]];
-        Z[(op * ne + i) * ne + j] = v;
+struct AsmJob {
+    const T *rec;
+    const double *rec64;
+    const int32_t *vid, *pairs, *edge_tri, *edge_loc;
+    cx<T> *Zloc, *Z;
+    MediaT<T> mdt;
+    Media md;
+    double alpha;
+    int nt, nstrip;
+    int64_t ne, far0, near0, row0;   // first far task, near pair and gather row of the job
+};
+
+template <typename T, int64_t AsmJob<T>::*F>
+__device__ __forceinline__ int find_job(const AsmJob<T> *jobs, int njobs, int64_t item) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].*F <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Far pairs of all meshes: persistent CTAs take tasks (mesh, test triangle,
+// strip of blockDim.x trial triangles) from an atomic counter, so meshes of
+// uneven size share the GPU without a tail per mesh.
+template <typename T>
+__global__ void __launch_bounds__(128) k_far(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t ntasks,
+                                                   unsigned long long *__restrict__ counter) {
+    __shared__ FarShared<T> S;
+    __shared__ int64_t s_task;
+    while (true) {
+        if (threadIdx.x == 0) s_task = (int64_t)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t task = s_task;
+        if (task >= ntasks) break;
+        const AsmJob<T> &J = jobs[find_job<T, &AsmJob<T>::far0>(jobs, njobs, task)];
+        const int64_t local = task - J.far0;
+        const int t = (int)(local / J.nstrip), s = (int)(local % J.nstrip) * blockDim.x + threadIdx.x;
+        far_load(S, J.rec, J.rec64, J.vid, t);
+        __syncthreads();
+        if (s < J.nt) far_pair(S, J.nt, J.rec, J.rec64, J.vid, J.alpha, J.mdt, J.Zloc, t, s);
+        __syncthreads();   // S and s_task are rewritten by the next task
+    }
+}
+
+// Near pairs of all meshes: one warp per pair, grid-stride.
+template <typename T>
+__global__ void __launch_bounds__(128) k_near_blocks(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t npairs) {
+    __shared__ z64 sm_all[4][2][2][2][9];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t pid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; pid < npairs; pid += nw) {
+        const AsmJob<T> &J = jobs[find_job<T, &AsmJob<T>::near0>(jobs, njobs, pid)];
+        const int64_t l = pid - J.near0;
+        near_pair<T>(J.pairs[2 * l], J.pairs[2 * l + 1], J.nt, J.rec64, J.md, J.Zloc, sm_all[(threadIdx.x >> 5) & 3]);
+    }
+}
+
+// Gather of all meshes: one block per RWG row, grid-stride over the rows of all meshes.
+template <typename T>
+__global__ void k_gather(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t nrows) {
+    for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+        const AsmJob<T> &J = jobs[find_job<T, &AsmJob<T>::row0>(jobs, njobs, row)];
+        const int64_t i = row - J.row0, ne = J.ne;
+        const int64_t plane = (int64_t)J.nt * J.nt;
+        const int ti[2] = {J.edge_tri[2 * i], J.edge_tri[2 * i + 1]}, ai[2] = {J.edge_loc[2 * i], J.edge_loc[2 * i + 1]};
+        for (int64_t j = threadIdx.x; j < ne; j += blockDim.x) {
+            const int tj[2] = {J.edge_tri[2 * j], J.edge_tri[2 * j + 1]};
+            const int aj[2] = {J.edge_loc[2 * j], J.edge_loc[2 * j + 1]};
+            for (int op = 0; op < 3; ++op) {
+                cx<T> v(0, 0);
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b)
+                        v += J.Zloc[(op * 9 + 3 * ai[a] + aj[b]) * plane + (int64_t)ti[a] * J.nt + tj[b]];
+                J.Z[(op * ne + i) * ne + j] = v;
+            }
+        }
     }
 }
 
 }  // namespace
 
 template <typename T>
+void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st);
+
+// One mesh: the batched stages with a batch of one (one code path, so a
+// mesh assembled alone and in a batch gets the same bits).
+template <typename T>
 void assemble_rwg(Mesh &m, cx<T> *Zrwg, cudaStream_t st) {
-    const int nt = (int)m.h.nt;
-    const int64_t ne = m.h.ne;
-    Media md{m.k1.re, m.k1.im, m.k2.re, m.k2.im, m.eta1.re, m.eta1.im, m.eta2.re, m.eta2.im};
-    DevBuf<cx<T>> Zloc;
-    Zloc.alloc((size_t)NCOMP * nt * nt);
-    const T *rec;
-    if constexpr (sizeof(T) == 8) rec = (const T *)m.tri64.p;
-    else rec = (const T *)m.tri32.p;
-    CBFM_REQUIRE(nt <= 65535, "k_far grid: more than 65535 triangles");
-    dim3 g1((nt + 127) / 128, nt);
-    {
-        ProfScope ps_("k_far", st);
-        k_far<T><<<g1, 128, 0, st>>>(nt, rec, m.tri64.p, m.tri_vid.p, m.alpha, media_t<T>(md), Zloc.p);
-        launched("k_far");
-    }
-    {
-        // algorithmic work: far ordered pairs x 49 point pairs x FAR_FLOP_PER_POINT_PAIR; bytes: the local blocks written
-        const double far_pairs = (double)nt * nt - (2.0 * m.n_near - nt);
-        prof_add_work("k_far", far_pairs * 49.0 * FAR_FLOP_PER_POINT_PAIR, (double)NCOMP * nt * nt * sizeof(cx<T>));
-    }
-    if (m.n_near > 0) {
-        int64_t threads = m.n_near * 32;
-        {
-            ProfScope ps_("k_near_blocks", st);
-            k_near_blocks<T><<<(unsigned)((threads + 127) / 128), 128, 0, st>>>(m.n_near, nt, m.near_pairs.p, m.tri64.p,
-                                                                               md, Zloc.p);
-            launched("k_near_blocks");
-        }
-    }
-    CBFM_REQUIRE(ne <= 65535, "k_gather grid: more than 65535 edges");
-    dim3 g3((unsigned)((ne + 127) / 128), (unsigned)ne);
-    {
-        ProfScope ps_("k_gather", st);
-        k_gather<T><<<g3, 128, 0, st>>>(ne, nt, m.edge_tri.p, m.edge_loc.p, Zloc.p, Zrwg);
-        launched("k_gather");
-    }
-    CBFM_CUDA(cudaStreamSynchronize(st));   // Zloc is released on return
+    assemble_rwg_batch<T>(std::vector<Mesh *>{&m}, std::vector<cx<T> *>{Zrwg}, st);
 }
 
 template void assemble_rwg<double>(Mesh &, z64 *, cudaStream_t);
 template void assemble_rwg<float>(Mesh &, c32 *, cudaStream_t);
+// Local blocks, far/near pairs and RWG gather of several meshes, one launch
+// per stage.  The far stage's strip width (trial triangles per task) is
+// picked once per device and precision by timing the candidates on the first
+// batch (every candidate writes the same values, so no run is repeated).
+template <typename T>
+void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st) {
+    const int nj = (int)ms.size();
+    if (nj == 0) return;
+    std::vector<DevBuf<cx<T>>> Zloc(nj);
+    std::vector<AsmJob<T>> jobs(nj);
+    int64_t npairs = 0, nrows = 0;
+    double far_flop = 0.0, far_bytes = 0.0;
+    for (int k = 0; k < nj; ++k) {
+        Mesh &m = *ms[k];
+        const int nt = (int)m.h.nt;
+        Zloc[k].alloc((size_t)NCOMP * nt * nt);
+        Media md{m.k1.re, m.k1.im, m.k2.re, m.k2.im, m.eta1.re, m.eta1.im, m.eta2.re, m.eta2.im};
+        AsmJob<T> &J = jobs[k];
+        if constexpr (sizeof(T) == 8) J.rec = (const T *)m.tri64.p;
+        else J.rec = (const T *)m.tri32.p;
+        J.rec64 = m.tri64.p;
+        J.vid = m.tri_vid.p;
+        J.pairs = m.near_pairs.p;
+        J.edge_tri = m.edge_tri.p;
+        J.edge_loc = m.edge_loc.p;
+        J.Zloc = Zloc[k].p;
+        J.Z = Z[k];
+        J.mdt = media_t<T>(md);
+        J.md = md;
+        J.alpha = m.alpha;
+        J.nt = nt;
+        J.ne = m.h.ne;
+        J.near0 = npairs;
+        J.row0 = nrows;
+        npairs += m.n_near;
+        nrows += m.h.ne;
+        far_flop += ((double)nt * nt - (2.0 * m.n_near - nt)) * 49.0 * FAR_FLOP_PER_POINT_PAIR;
+        far_bytes += (double)NCOMP * nt * nt * sizeof(cx<T>);
+    }
+    int dev = 0, nsm = 0;
+    CBFM_CUDA(cudaGetDevice(&dev));
+    CBFM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    DevBuf<AsmJob<T>> djobs;
+    djobs.alloc(nj);
+    DevBuf<unsigned long long> counter;
+    counter.alloc(1);
+    const std::string key = std::string("far_strip_") + (sizeof(T) == 8 ? "f64" : "f32") + "_dev" + std::to_string(dev);
+    int tuned = tuning_get(key);
+    const std::vector<int> cands = tuned > 0 ? std::vector<int>{tuned} : std::vector<int>{32, 64, 128};
+    float best_ms = 1e30f;
+    int best = cands[0];
+    for (int W : cands) {
+        int64_t ntask = 0;
+        for (auto &J : jobs) {
+            J.nstrip = (J.nt + W - 1) / W;
+            J.far0 = ntask;
+            ntask += (int64_t)J.nt * J.nstrip;
+        }
+        CBFM_CUDA(cudaMemcpyAsync(djobs.p, jobs.data(), sizeof(AsmJob<T>) * nj, cudaMemcpyHostToDevice, st));
+        CBFM_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), st));
+        int occ = 0;
+        CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_far<T>, W, 0));
+        const unsigned grid = (unsigned)std::max(1, occ) * (unsigned)nsm;
+        cudaEvent_t e0, e1;
+        CBFM_CUDA(cudaEventCreate(&e0));
+        CBFM_CUDA(cudaEventCreate(&e1));
+        CBFM_CUDA(cudaEventRecord(e0, st));
+        {
+            ProfScope ps_("k_far", st);
+            k_far<T><<<grid, W, 0, st>>>(djobs.p, nj, ntask, counter.p);
+            launched("k_far");
+        }
+        CBFM_CUDA(cudaEventRecord(e1, st));
+        CBFM_CUDA(cudaEventSynchronize(e1));
+        float ms_ = 0.f;
+        CBFM_CUDA(cudaEventElapsedTime(&ms_, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (ms_ < best_ms) {
+            best_ms = ms_;
+            best = W;
+        }
+    }
+    if (tuned <= 0) tuning_set(key, best);
+    prof_add_work("k_far", far_flop, far_bytes);
+    if (npairs > 0) {
+        int occ = 0;
+        CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_near_blocks<T>, 128, 0));
+        const unsigned grid = (unsigned)std::min<int64_t>((int64_t)std::max(1, occ) * nsm, (npairs * 32 + 127) / 128);
+        ProfScope ps_("k_near_blocks", st);
+        k_near_blocks<T><<<grid, 128, 0, st>>>(djobs.p, nj, npairs);
+        launched("k_near_blocks");
+    }
+    {
+        const unsigned grid = (unsigned)std::min<int64_t>(nrows, 8 * (int64_t)nsm);
+        ProfScope ps_("k_gather", st);
+        k_gather<T><<<grid, 128, 0, st>>>(djobs.p, nj, nrows);
+        launched("k_gather");
+    }
+    CBFM_CUDA(cudaStreamSynchronize(st));   // the local blocks are released on return
+}
+
+template void assemble_rwg_batch<double>(const std::vector<Mesh *> &, const std::vector<z64 *> &, cudaStream_t);
+template void assemble_rwg_batch<float>(const std::vector<Mesh *> &, const std::vector<c32 *> &, cudaStream_t);
 
 }  // namespace cbfm

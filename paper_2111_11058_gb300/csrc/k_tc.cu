@@ -32,6 +32,7 @@
 #include <cuda.h>   // CUtensorMap and its enums (the encoder is looked up in the driver at run time)
 
 #include <algorithm>
+#include <memory>
 #include <atomic>
 #include <vector>
 
@@ -62,7 +63,7 @@ struct TcMaps {
 struct TcTask {
     int32_t amap, bmap, a_c2, b_c2;
     int32_t a_row0, b_row0, a_k0, b_k0;
-    int32_t nk, n, mode, pad;
+    int32_t nk, n, mode, sidx;   // sidx: scatterer of the task (batched launches)
     int32_t e[6];   // epilogue parameters (see k_tc_gemm)
 };
 
@@ -188,8 +189,13 @@ __device__ __forceinline__ void split64(double x, float &hi, float &lo) {
 //   pair (2j, 2j+1) of panel row pr: set M if pr < P_k else J, CBF coff_k + j.
 // mode 1 (GEMM2, rows = CBFs of one half): e = {A row offset, A column offset,
 //   valid rows, unused...}; accumulator column pair j -> A column b_row0/2 + j.
+// BATCH: the task's scatterer selects its tensor maps and parameters from
+// global-memory arrays (stages and stage size stay launch-wide).
+template <bool BATCH>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant__ TcMaps maps,
-                                                           const TcTask *__restrict__ tasks, const TcParams P) {
+                                                           const TcTask *__restrict__ tasks, const TcParams P0,
+                                                           const TcMaps *__restrict__ maps_g,
+                                                           const TcParams *__restrict__ params_g) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full_bar[8], empty_bar[8], done_bar;
     __shared__ uint32_t s_tmem;
@@ -197,7 +203,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const TcTask t = tasks[blockIdx.x];
-    const int S = P.stages;
+    const TcParams P = BATCH ? params_g[t.sidx] : P0;
+    const TcMaps *mp = BATCH ? &maps_g[t.sidx] : &maps;
+    const int S = P0.stages;
     const int nb = (t.n + TC_BROWS - 1) / TC_BROWS;   // B boxes per plane
     const uint32_t tx_bytes = (uint32_t)(2 * TC_A_BYTES + 2 * nb * TC_B_BOX_BYTES);
 
@@ -221,14 +229,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_gemm(const __grid_constant
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    auto stage_a = [&](int s, int plane) { return smem + (size_t)s * P.stage_bytes + plane * TC_A_BYTES; };
+    auto stage_a = [&](int s, int plane) { return smem + (size_t)s * P0.stage_bytes + plane * TC_A_BYTES; };
     auto stage_b = [&](int s, int plane) {
-        return smem + (size_t)s * P.stage_bytes + 2 * TC_A_BYTES + (size_t)plane * nb * TC_B_BOX_BYTES;
+        return smem + (size_t)s * P0.stage_bytes + 2 * TC_A_BYTES + (size_t)plane * nb * TC_B_BOX_BYTES;
     };
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
-        const CUtensorMap *ma = &maps.m[t.amap], *mb = &maps.m[t.bmap];
+        const CUtensorMap *ma = &mp->m[t.amap], *mb = &mp->m[t.bmap];
+        if (BATCH) {   // maps written by the host into global memory: acquire them for the tensor proxy
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)ma) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)mb) : "memory");
+        }
         int issued = 0;
         for (int kb = 0; kb < t.nk; ++kb) {
             const int s = kb % S, it = kb / S;
@@ -460,7 +472,10 @@ void make_map(CUtensorMap *m, float *base, int64_t d0, int64_t d1, int64_t d2, i
 
 inline int64_t up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-void launch_tc(const TcMaps &maps, const std::vector<TcTask> &tasks, TcParams P, cudaStream_t st, const char *name) {
+// One launch over `tasks`.  maps_g / params_g non-null: batched launch (the
+// tasks' sidx index those arrays); otherwise the single-scatterer maps and P.
+void launch_tc(const TcMaps &maps, const TcMaps *maps_g, const TcParams *params_g, const std::vector<TcTask> &tasks,
+               TcParams P, cudaStream_t st, const char *name) {
     if (tasks.empty()) return;
     int nbmax = 1;
     for (auto &t : tasks) {
@@ -477,7 +492,9 @@ void launch_tc(const TcMaps &maps, const std::vector<TcTask> &tasks, TcParams P,
     int dev = 0;
     CBFM_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && !attr[dev].load(std::memory_order_acquire)) {
-        CBFM_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CBFM_CUDA(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(TC_SMEM_BUDGET + 1024)));
+        CBFM_CUDA(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(TC_SMEM_BUDGET + 1024)));
         attr[dev].store(true, std::memory_order_release);
     }
@@ -486,7 +503,10 @@ void launch_tc(const TcMaps &maps, const std::vector<TcTask> &tasks, TcParams P,
     CBFM_CUDA(cudaMemcpyAsync(dt.p, tasks.data(), sizeof(TcTask) * tasks.size(), cudaMemcpyHostToDevice, st));
     {
         ProfScope ps_(name, st);
-        k_tc_gemm<<<(unsigned)tasks.size(), TC_THREADS, smem, st>>>(maps, dt.p, P);
+        if (maps_g)
+            k_tc_gemm<true><<<(unsigned)tasks.size(), TC_THREADS, smem, st>>>(maps, dt.p, P, maps_g, params_g);
+        else
+            k_tc_gemm<false><<<(unsigned)tasks.size(), TC_THREADS, smem, st>>>(maps, dt.p, P, nullptr, nullptr);
         launched(name);
     }
     CBFM_CUDA(cudaStreamSynchronize(st));   // dt is released on return
@@ -494,20 +514,32 @@ void launch_tc(const TcMaps &maps, const std::vector<TcTask> &tasks, TcParams P,
 
 }  // namespace
 
-// A (nred x nred, c32) = the four CBF projections of Z (3 x ne x ne, c32) on
-// the tensor cores.  Z is consumed (released by the caller afterwards).
-void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st) {
+namespace {
+
+// Per-scatterer operands of the projection (split planes, panels, index
+// tables), its tensor maps and launch parameters, and its work counts.
+struct TcPrep {
+    DevBuf<float> Zs, Bp, Cp, YT;
+    DevBuf<int32_t> dLs, dPk, dprow, dkk0, dcell_off, dcell_of_cbf, dks;
+    DevBuf<int64_t> dboff, dcoff;
+    TcMaps maps;
+    TcParams P;
+    double fl1 = 0, fl2 = 0, by1 = 0, by2 = 0;
+};
+
+// Builds the operands and appends the scatterer's GEMM1 and GEMM2 tasks
+// (tagged sidx).  Returns false when the scatterer has no CBFs.
+bool tc_prepare(Mesh &m, Cbf &c, const c32 *Z, c32 *A, int sidx, int *errp, TcPrep &pp, std::vector<TcTask> &t1,
+                std::vector<TcTask> &t2, cudaStream_t st) {
     const int nc = m.h.ncell;
+
     const int64_t ne = m.h.ne, nh = c.nhalf, nred = 2 * nh;
-    if (nh == 0) return;
+    if (nh == 0) return false;
     const int64_t ldz = up(2 * ne, TC_KB);
     CBFM_REQUIRE(ne < (1ll << 30) / 2 && ldz < (1ll << 31), "mesh too large for 32-bit tile coordinates");
-    DevBuf<int> err;
-    err.alloc(1);
-    CBFM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
 
     // --- Z hi/lo planes
-    DevBuf<float> Zs;
+    DevBuf<float> &Zs = pp.Zs;
     Zs.alloc((size_t)2 * 3 * ne * ldz);
     {
         ProfScope ps_("k_split_z", st);
@@ -529,8 +561,8 @@ void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st) {
         ldb = std::max<int64_t>(ldb, up(2 * (off + N), TC_KB) - kk0[k]);
     }
     brows = std::max<int64_t>(brows, 1);
-    DevBuf<int32_t> dLs, dPk, dprow, dkk0, dcell_off;
-    DevBuf<int64_t> dboff, dcoff;
+    DevBuf<int32_t> &dLs = pp.dLs, &dPk = pp.dPk, &dprow = pp.dprow, &dkk0 = pp.dkk0, &dcell_off = pp.dcell_off;
+    DevBuf<int64_t> &dboff = pp.dboff, &dcoff = pp.dcoff;
     dLs.alloc(nc); dPk.alloc(nc); dprow.alloc(nc); dkk0.alloc(nc); dcell_off.alloc(nc + 1);
     dboff.alloc(nc + 1); dcoff.alloc(nc + 1);
     CBFM_CUDA(cudaMemcpyAsync(dLs.p, Ls.data(), 4 * nc, cudaMemcpyHostToDevice, st));
@@ -540,7 +572,7 @@ void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st) {
     CBFM_CUDA(cudaMemcpyAsync(dcell_off.p, m.h.cell_off.data(), 4 * (nc + 1), cudaMemcpyHostToDevice, st));
     CBFM_CUDA(cudaMemcpyAsync(dboff.p, c.boff.data(), 8 * (nc + 1), cudaMemcpyHostToDevice, st));
     CBFM_CUDA(cudaMemcpyAsync(dcoff.p, c.coff.data(), 8 * (nc + 1), cudaMemcpyHostToDevice, st));
-    DevBuf<float> Bp;
+    DevBuf<float> &Bp = pp.Bp;
     Bp.alloc((size_t)2 * brows * ldb);
     {
         dim3 g(64, nc);
@@ -562,12 +594,12 @@ void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st) {
         ke[ti] = (int32_t)up(2 * (int64_t)m.h.cell_off[kb + 1], TC_KB);
         ldc = std::max<int64_t>(ldc, ke[ti] - ks[ti]);
     }
-    DevBuf<int32_t> dcell_of_cbf, dks;
+    DevBuf<int32_t> &dcell_of_cbf = pp.dcell_of_cbf, &dks = pp.dks;
     dcell_of_cbf.alloc(cell_of_cbf.size());
     dks.alloc(ntile);
     CBFM_CUDA(cudaMemcpyAsync(dcell_of_cbf.p, cell_of_cbf.data(), 4 * cell_of_cbf.size(), cudaMemcpyHostToDevice, st));
     CBFM_CUDA(cudaMemcpyAsync(dks.p, ks.data(), 4 * ntile, cudaMemcpyHostToDevice, st));
-    DevBuf<float> Cp;
+    DevBuf<float> &Cp = pp.Cp;
     Cp.alloc((size_t)2 * 2 * ntile * TC_M * ldc);
     {
         dim3 g(128, 2);
@@ -577,21 +609,21 @@ void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st) {
     }
 
     // --- YT planes, zero padding columns (GEMM2 may read up to the next 32-float boundary)
-    DevBuf<float> YT;
+    DevBuf<float> &YT = pp.YT;
     YT.alloc((size_t)2 * 4 * 2 * nh * ldz);
     if (ldz > 2 * ne)
         CBFM_CUDA(cudaMemset2DAsync(YT.p + 2 * ne, ldz * 4, 0, (ldz - 2 * ne) * 4, (size_t)2 * 4 * 2 * nh, st));
 
-    TcMaps maps;
+    TcMaps &maps = pp.maps;
     make_map(&maps.m[MAP_Z], Zs.p, ldz, ne, 3, 2, TC_M);
     make_map(&maps.m[MAP_BP], Bp.p, ldb, brows, 1, 2, TC_BROWS);
     make_map(&maps.m[MAP_CP], Cp.p, ldc, (int64_t)ntile * TC_M, 2, 2, TC_M);
     make_map(&maps.m[MAP_YT], YT.p, ldz, 2 * nh, 4, 2, TC_BROWS);
-    TcParams P{};
-    P.ne = ne; P.nh = nh; P.nred = nred; P.ldz = ldz; P.yt = YT.p; P.A = A; P.err = err.p;
+    TcParams &P = pp.P;
+    P = TcParams{};
+    P.ne = ne; P.nh = nh; P.nred = nred; P.ldz = ldz; P.yt = YT.p; P.A = A; P.err = errp;
 
     // --- GEMM1 tasks: (op, cell, 128-row tile of RWGs, chunk of panel rows)
-    std::vector<TcTask> t1;
     const int mt = (int)((ne + TC_M - 1) / TC_M);
     double fl1 = 0.0;
     for (int op = 0; op < 3; ++op)
@@ -607,22 +639,20 @@ void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st) {
                     TcTask t{};
                     t.amap = MAP_Z; t.bmap = MAP_BP; t.a_c2 = op; t.b_c2 = 0;
                     t.a_row0 = i * TC_M; t.b_row0 = prow[k] + r; t.a_k0 = kk0[k]; t.b_k0 = 0;
-                    t.nk = nk; t.n = n; t.mode = 0;
+                    t.nk = nk; t.n = n; t.mode = 0; t.sidx = sidx;
                     t.e[0] = op; t.e[1] = c.L[k]; t.e[2] = Pk[k]; t.e[3] = (int32_t)c.coff[k]; t.e[4] = r;
                     t1.push_back(t);
                 }
                 fl1 += 8.0 * ne * N * (n / 2);
             }
         }
-    launch_tc(maps, t1, P, st, "k_tc_gemm1");
-    prof_add_work("k_tc_gemm1", fl1, (double)2 * 3 * ne * ldz * 4 + (double)2 * 4 * 2 * nh * ldz * 4);
-    Zs.release();
+    pp.fl1 = fl1;
+    pp.by1 = (double)2 * 3 * ne * ldz * 4 + (double)2 * 4 * 2 * nh * ldz * 4;
 
     // --- GEMM2 tasks: (chain, 128-row tile of CBFs, 256-row chunk of YT)
     // chains: 0 C^J^H Ks C^M (rows J, cols M), 1 C^J^H Ta C^J, 2 C^M^H Tb C^M, 3 C^M^H Ks C^J
     const int half_of_rows[4] = {1, 1, 0, 0};
     const int64_t r0q[4] = {0, 0, nh, nh}, c0q[4] = {0, nh, 0, nh};
-    std::vector<TcTask> t2;
     double fl2 = 0.0;
     for (int q = 0; q < 4; ++q)
         for (int ti = 0; ti < ntile; ++ti)
@@ -633,18 +663,80 @@ void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st) {
                 t.nk = (ke[ti] - ks[ti]) / TC_KB;
                 t.n = (int)std::min<int64_t>(TC_NMAX, up(2 * nh - b, 16));
                 t.mode = 1;
+                t.sidx = sidx;
                 t.e[0] = (int32_t)r0q[q]; t.e[1] = (int32_t)c0q[q]; t.e[2] = (int32_t)nh;
                 t2.push_back(t);
                 fl2 += 8.0 * TC_M * ((ke[ti] - ks[ti]) / 2) * (t.n / 2);
             }
-    launch_tc(maps, t2, P, st, "k_tc_gemm2");
-    prof_add_work("k_tc_gemm2", fl2, (double)2 * 4 * 2 * nh * ldz * 4 + (double)nred * nred * 8);
+    pp.fl2 = fl2;
+    pp.by2 = (double)2 * 4 * 2 * nh * ldz * 4 + (double)nred * nred * 8;
+    return true;
+}
 
+void check_err(const int *errp, cudaStream_t st) {
     int herr = 0;
-    CBFM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBFM_CUDA(cudaMemcpyAsync(&herr, errp, sizeof(int), cudaMemcpyDeviceToHost, st));
     CBFM_CUDA(cudaStreamSynchronize(st));
     if (herr) throw Fail{CBFM_ETIMEOUT, "tensor-core projection: a pipeline wait expired (stage " +
                                             std::to_string(herr) + ")"};
+}
+
+}  // namespace
+
+// A (nred x nred, c32) = the four CBF projections of Z (3 x ne x ne, c32) on
+// the tensor cores.  Z is consumed (released by the caller afterwards).
+void project_tc(Mesh &m, Cbf &c, const c32 *Z, c32 *A, cudaStream_t st) {
+    DevBuf<int> err;
+    err.alloc(1);
+    CBFM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    TcPrep pp;
+    std::vector<TcTask> t1, t2;
+    if (!tc_prepare(m, c, Z, A, 0, err.p, pp, t1, t2, st)) return;
+    launch_tc(pp.maps, nullptr, nullptr, t1, pp.P, st, "k_tc_gemm1");
+    prof_add_work("k_tc_gemm1", pp.fl1, pp.by1);
+    pp.Zs.release();
+    launch_tc(pp.maps, nullptr, nullptr, t2, pp.P, st, "k_tc_gemm2");
+    prof_add_work("k_tc_gemm2", pp.fl2, pp.by2);
+    check_err(err.p, st);
+}
+
+// The same for several scatterers: one GEMM1 launch and one GEMM2 launch over
+// the tasks of all of them (tensor maps and parameters in global memory).
+void project_tc_batch(const std::vector<Mesh *> &ms, const std::vector<Cbf *> &cs, const std::vector<const c32 *> &Z,
+                      const std::vector<c32 *> &A, cudaStream_t st) {
+    DevBuf<int> err;
+    err.alloc(1);
+    CBFM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    std::vector<std::unique_ptr<TcPrep>> preps;
+    std::vector<TcTask> t1, t2;
+    std::vector<TcMaps> hmaps;
+    std::vector<TcParams> hpar;
+    double fl1 = 0, fl2 = 0, by1 = 0, by2 = 0;
+    for (size_t k = 0; k < ms.size(); ++k) {
+        std::unique_ptr<TcPrep> pp(new TcPrep());
+        if (!tc_prepare(*ms[k], *cs[k], Z[k], A[k], (int)hmaps.size(), err.p, *pp, t1, t2, st)) continue;
+        hmaps.push_back(pp->maps);
+        hpar.push_back(pp->P);
+        fl1 += pp->fl1;
+        fl2 += pp->fl2;
+        by1 += pp->by1;
+        by2 += pp->by2;
+        preps.push_back(std::move(pp));
+    }
+    if (hmaps.empty()) return;
+    DevBuf<TcMaps> dmaps;
+    DevBuf<TcParams> dpar;
+    dmaps.alloc(hmaps.size());
+    dpar.alloc(hpar.size());
+    CBFM_REQUIRE(((uintptr_t)dmaps.p & 63) == 0, "tensor maps in global memory must be 64-byte aligned");
+    CBFM_CUDA(cudaMemcpyAsync(dmaps.p, hmaps.data(), sizeof(TcMaps) * hmaps.size(), cudaMemcpyHostToDevice, st));
+    CBFM_CUDA(cudaMemcpyAsync(dpar.p, hpar.data(), sizeof(TcParams) * hpar.size(), cudaMemcpyHostToDevice, st));
+    launch_tc(hmaps[0], dmaps.p, dpar.p, t1, hpar[0], st, "k_tc_gemm1");
+    prof_add_work("k_tc_gemm1", fl1, by1);
+    for (auto &pp : preps) pp->Zs.release();
+    launch_tc(hmaps[0], dmaps.p, dpar.p, t2, hpar[0], st, "k_tc_gemm2");
+    prof_add_work("k_tc_gemm2", fl2, by2);
+    check_err(err.p, st);
 }
 
 }  // namespace cbfm

@@ -71,3 +71,10 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(C, "_LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(C.CbfmError):
         C.lib()
+
+
+def test_tuning_query_is_host_only(P):
+    """cbfm_tuning needs no device: an empty JSON object before any tuned launch."""
+    t = P.cbfm.tuning()
+    assert isinstance(t, dict)
+    assert all(isinstance(v, int) for v in t.values())

@@ -1,0 +1,73 @@
+"""Batched reduced-matrix assembly (one launch per stage over all
+scatterers): every reduced system equals the one assembled on its own, for a
+seeded mix of spheres, cubes and cylinders of uneven size with injected
+seeded CBFs, and batched systems solve to the same RCS as single ones."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    from paper_2111_11058_gb300 import build as B
+    B.build()
+    import paper_2111_11058_gb300 as pkg
+    return pkg
+
+
+def _mix(P, count, seed):
+    meshes, cbfs = [], []
+    for k, d in enumerate(W.scatterer_mix(count, seed=seed)):
+        g = d["mesh"]
+        ne = 3 * g.tris.shape[0] // 2
+        ncell = max(2, ne // 200)                       # cells of about 200 RWGs (uneven across scatterers)
+        gm = P.mesh(g.verts, g.tris, ncell, complex(*d["eps"]), partition="rcb")
+        Ns = np.bincount(gm.cells(), minlength=ncell)
+        CM, CJ = W.random_cbfs(Ns, [int(min(3 + (k + c) % 14, n)) for c, n in enumerate(Ns)], seed=seed + k)
+        meshes.append(gm)
+        cbfs.append(P.cbf_import(gm, CM, CJ))
+    return meshes, cbfs
+
+
+def test_batch_equals_single_on_uneven_mix(P):
+    meshes, cbfs = _mix(P, 10, seed=3)
+    reds = P.assemble_reduced_batch(meshes, cbfs, P.MIXED)
+    assert len(reds) == 10
+    for gm, c, rb in zip(meshes, cbfs, reds):
+        rs = P.assemble_reduced(gm, c, P.MIXED)
+        a, b = rs.export(), rb.export()
+        assert a.shape == b.shape and rb.n == rs.n
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
+    tuned = P.tuning()
+    assert any(k.startswith("far_strip_f32") and v in (32, 64, 128) for k, v in tuned.items()), tuned
+
+
+def test_batch_solves_like_single(P):
+    sph = W.icosphere(2, 0.3)
+    cub = W.cube(6, 0.6)
+    gen = W.plane_wave_set(W.fibonacci_dirs(12))
+    exc = W.plane_wave_set(W.fibonacci_dirs(8))
+    ms = [P.mesh(sph.verts, sph.tris, 8, 4.0, partition="octant"), P.mesh(cub.verts, cub.tris, 6, 2.5 - 0.1j)]
+    cs = [P.build_cbfs(m, gen, 1e-3) for m in ms]
+    reds = P.assemble_reduced_batch(ms, cs, P.MIXED)
+    for m, c, rb in zip(ms, cs, reds):
+        rs = P.assemble_reduced(m, c, P.MIXED)
+        for r in (rs, rb):
+            P.cmp_setup(r)
+        a = P.solve(rs, exc, tol=1e-8, monostatic=True, want_j=False, solver=P.BLOCK).rcs.sum(-1)
+        b = P.solve(rb, exc, tol=1e-8, monostatic=True, want_j=False, solver=P.BLOCK).rcs.sum(-1)
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
+
+
+def test_batch_rejects_other_precisions_and_empty(P):
+    meshes, cbfs = _mix(P, 2, seed=5)
+    with pytest.raises(P.CbfmError):
+        P.assemble_reduced_batch(meshes, cbfs, P.FP64)
+    assert P.assemble_reduced_batch([], [], P.MIXED) == []
