@@ -304,6 +304,63 @@ def run_serving(budget_bytes: int) -> dict:
             "loads": loads}
 
 
+def run_batch(count: int = 200) -> dict:
+    """Batched-scatterer workload: a seeded mix of `count` spheres, cubes and
+    finite cylinders (0.2-1.2 wavelengths, eps_r in [1.5, 6], 500-6000
+    unknowns, cells of about 200 RWGs) with seeded stand-in CBFs (L_m =
+    min(N_m, 16)); all reduced matrices assembled by the batched call (one
+    launch per stage) and, for comparison, one scatterer at a time.  Both
+    timed with CUDA events; the batched matrices must equal the single ones."""
+    import torch
+    import paper_2111_11058_gb300 as P
+    meshes, cbfs, unknowns = [], [], 0
+    for k, d in enumerate(W.scatterer_mix(count, seed=0)):
+        g = d["mesh"]
+        ne = 3 * g.tris.shape[0] // 2
+        unknowns += 2 * ne
+        ncell = max(2, ne // 200)
+        gm = P.mesh(g.verts, g.tris, ncell, complex(*d["eps"]), partition="rcb")
+        Ns = np.bincount(gm.cells(), minlength=ncell)
+        CM, CJ = W.random_cbfs(Ns, [int(min(16, n)) for n in Ns], seed=k)
+        meshes.append(gm)
+        cbfs.append(P.cbf_import(gm, CM, CJ))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), out
+
+    for r in P.assemble_reduced_batch(meshes[:4], cbfs[:4], P.MIXED):   # warm-up and tuning
+        r.free()
+    t_batch, reds = timed(lambda: P.assemble_reduced_batch(meshes, cbfs, P.MIXED))
+    for r in reds:
+        r.free()
+    P.profile(True)
+    P.profile_read(reset=True)
+    _t, reds = timed(lambda: P.assemble_reduced_batch(meshes, cbfs, P.MIXED))
+    prof = P.profile_read(reset=True)
+    P.profile(False)
+    t_single, singles = timed(lambda: [P.assemble_reduced(m, c, P.MIXED) for m, c in zip(meshes, cbfs)])
+    worst = 0.0
+    for k in range(0, count, max(1, count // 20)):
+        a, b = singles[k].export(), reds[k].export()
+        worst = max(worst, float(np.abs(a - b).max()))
+    for r in reds + singles:
+        r.free()
+    return {"recipe": f"{count} scatterers (seeded sphere/cube/cylinder mix, {unknowns} unknowns in total), "
+                      "cells of ~200 RWGs, stand-in CBFs L_m = min(N_m, 16), MIXED",
+            "batched_ms": t_batch, "one_at_a_time_ms": t_single, "speedup": t_single / t_batch,
+            "scatterers_per_s": count / (t_batch / 1e3), "max_abs_diff_batched_vs_single": worst,
+            "batched_kernels_ms": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+            "tuning": P.tuning()}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -341,6 +398,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-alt", action="store_true", help="skip the comparison with the other GMRES variant")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) run")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-scatterer assembly run")
     ap.add_argument("--solver", default="block", choices=["block", "per_rhs"],
                     help="GMRES variant of the timed step: block GMRES over all right-hand sides, or one per RHS")
     ap.add_argument("--workload", default="cube9216", choices=["cube9216", "cube2304", "sphere960"],
@@ -465,6 +523,10 @@ def main():
         fp64 = {"value": ws * N_RHS / (t64[0] / 1000.0), "ms_per_step": t64[0], "rcs_err_mixed_vs_fp64": err,
                 "speedup_mixed_over_fp64": (t64[0] / t_step)}
 
+    batch = None
+    if not args.no_batch and ws == 1 and WORKLOAD == "cube9216":
+        batch = run_batch()
+
     serving = None
     if not args.no_serve and ws == 1 and WORKLOAD == "cube9216":
         free, _tot = torch.cuda.mem_get_info()
@@ -486,7 +548,7 @@ def main():
                 "gpu_launches": int(launches), "roofline": roof,
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
-                "fp64_path": fp64, "other_solver": alt, "serving": serving}
+                "fp64_path": fp64, "other_solver": alt, "batch": batch, "serving": serving}
         if not args.no_cpu and ws == 1 and WORKLOAD == "cube9216":
             try:
                 line["cpu_baseline"] = cpu_sample()

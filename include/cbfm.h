@@ -148,7 +148,7 @@ cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precisi
  * triangles) tasks from an atomic counter, so scatterers of uneven size share
  * the GPU.  The strip width is picked on the first call per device by timing
  * the candidates (see cbfm_tuning).  Scatterers are processed in waves whose
- * transient operators fit in half of the free device memory.
+ * transient operators fit in half of the free device memory and in 6 GiB.
  *   meshes, cbfs  count handles (cbfs[k] built on meshes[k])
  *   out           count new reduced-system handles (NULL on failure)
  *   n_cbf         out, count values of N^CBF (may be NULL)

@@ -795,10 +795,12 @@ cbfm_status cbfm_assemble_reduced_batch(const cbfm_mesh_t *meshes, const cbfm_cb
             check_device(cs[k], H_CBF, "cbf");
             CBFM_REQUIRE(cs[k]->mesh == ms[k], "cbf handle belongs to another mesh");
         }
-        // waves of scatterers whose transient operators fit in half of the free device memory
+        // waves of scatterers whose transient operators fit in half of the free
+        // device memory and in the 8 GiB the stream-ordered pool keeps between
+        // calls (larger waves would map fresh memory every call)
         size_t free_b = 0, total_b = 0;
         CBFM_CUDA(cudaMemGetInfo(&free_b, &total_b));
-        const double budget = 0.5 * (double)free_b;
+        const double budget = std::min(0.5 * (double)free_b, 6.0 * (1ull << 30));
         auto transient = [&](int k) {
             const double nt = (double)ms[k]->h.nt, ne = (double)ms[k]->h.ne, nh = (double)cs[k]->nhalf;
             const double ldz = std::ceil(2.0 * ne / 32.0) * 32.0;

@@ -18,7 +18,8 @@
 //   The minus sign on T is the reading under which the paper's block matrix
 //   describes the exp(+j w t) problem.  Blocks are combined into
 //   Ks = K1 + K2, Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2.
-// Stage 2, near pairs (k_near_blocks, FP64 always, one warp per pair): 1/R, 1/R^3 and k^2/(2R)
+// Stage 2, near pairs (k_near_blocks, one warp per pair; FP64 for the closed
+//   forms and all sums, FP32 for the smooth remainders on the mixed path): 1/R, 1/R^3 and k^2/(2R)
 //   integrated in closed form over the trial triangle (Wilton et al. 1984,
 //   Graglia 1993 edge sums), bounded remainders by the 7-point rule, blocks
 //   symmetrised L(t,s) = (L~(t,s) + L~(s,t)^T)/2; K of a triangle with itself is 0.
@@ -448,94 +449,175 @@ __device__ inline void green_rems(z64 k, double R, z64 &gr, z64 &hr) {
 // contribution to the 3 x 3 K and T blocks; groups of eight reduce over p, and
 // lane 0 symmetrises, weights the media into Ks, Ta, Tb and stores both (t,s)
 // and (s,t).
-// One near pair (t, s), called by a whole warp; `sm` is the warp's slot of
-// shared memory (4 x 9 complex K and T sums).
+// FP32 form of the same remainders for the mixed path.  The series branch is
+// widened to |kR| < 0.6 so that the direct forms cancel at most a factor
+// (kR)^-3 < 5 in single precision; 12 terms leave < 1e-11 relative there.
+__device__ inline void green_rems_f(float kre, float kim, float R, c32 &gr, c32 &hr) {
+    const float PIf = 3.14159265358979f;
+    const c32 jk(-kim, kre);
+    const c32 y = jk * R;
+    if (sqrtf(y.re * y.re + y.im * y.im) < 0.6f) {
+        c32 pw(1, 0), s1(0, 0), s2(0, 0);
+        float f1 = 1.0f, f3 = 6.0f;
+        for (int j = 0; j < 12; ++j) {
+            if (j > 0) {
+                pw = pw * y;
+                f1 *= (float)(j + 1);
+                f3 *= (float)(j + 3);
+            }
+            const float sg = (j & 1) ? -1.0f : 1.0f;
+            s1 += (sg / f1) * pw;
+            s2 += (sg * (float)(j + 2) / f3) * pw;
+        }
+        gr = c32(kim, -kre) * s1 * (1.0f / (4.0f * PIf));
+        hr = (jk * jk * jk) * s2 * (-1.0f / (4.0f * PIf));
+        return;
+    }
+    float sn, cs;
+    sincosf(kre * R, &sn, &cs);
+    const float e = expf(kim * R);
+    const c32 ex(e * cs, -e * sn);
+    const float iR = 1.0f / R, i4pR = iR * (1.0f / (4.0f * PIf)), i4pR3 = i4pR * iR * iR;
+    gr = c32(ex.re - 1.0f, ex.im) * i4pR;
+    hr = (c32(1, 0) + y) * ex * (-i4pR3) + c32(i4pR3, 0) + (c32(kre, kim) * c32(kre, kim)) * (0.5f * i4pR);
+}
+
+// Near pairs, two per warp.  Lane = 16 slot + 8 o + p: pair slot (0, 1),
+// orientation o (0: test t / trial s, 1: test s / trial t), test point p < 7
+// (lane p = 7 of each group of eight idles).  Each lane evaluates the closed-
+// form potentials of the trial triangle at its test point once, then for both
+// media adds the bounded remainders and forms its weighted share of the test-
+// point moments, with r relative to the test triangle's centroid:
+//   M0 = sum w S0, Mr0 = sum w r S0, Mrr0 = sum w |r|^2 S0, MS = sum w Sr,
+//   MrS = sum w r.Sr, MW = sum w Wv, MX = sum w Wv x r.
+// Expanding the bilinear point terms in r gives the 3 x 3 entries from the
+// moments (P = test vertex a, Q = trial vertex b, both relative):
+//   T~_ab = c_a d_b (-jk) [MrS - P.MS + Mrr0 - (P + Q).Mr0 + (P.Q - 4/k^2) M0]
+//   K~_ab = c_a d_b [(Q - P).MX + P.(MW x Q)]        (0 when t = s)
+// The moments are summed over the 7 test points by shuffles and staged in
+// shared memory; lanes (slot, a, b) then symmetrise, weight the media into
+// Ks, Ta, Tb and store (t, s) and (s, t).
+constexpr int NEAR_MOM = 15;   // complex moments per (orientation, medium)
+
 template <typename T>
-__device__ __forceinline__ void near_pair(int t, int s, int nt, const double *__restrict__ rec, const Media &md,
-                                          cx<T> *__restrict__ Zloc, z64 (*sm)[2][2][9]) {
+__device__ __forceinline__ void near_pair2(int t, int s, int nt, const double *__restrict__ rec, const Media &md,
+                                           cx<T> *__restrict__ Zloc, z64 (*sm)[2][2][NEAR_MOM]) {
+    // (t, s): the pair of this lane's slot (t < 0: none); every lane reads only
+    // its own slot's mesh, and all 32 lanes reach the shuffles and barriers
     const int lane = threadIdx.x & 31;
+    const int slot = lane >> 4, o = (lane >> 3) & 1, p = lane & 7;
     __syncwarp();   // the slot's previous readers are done
-    const int o = lane >> 4, med = (lane >> 3) & 1, p = lane & 7;
-    z64 accK[9], accT[9];
-    for (int c = 0; c < 9; ++c) accK[c] = accT[c] = z64(0, 0);
-    if (p < 7) {
+    z64 mom[2][NEAR_MOM];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int c = 0; c < NEAR_MOM; ++c) mom[i][c] = z64(0, 0);
+    if (p < 7 && t >= 0) {
         const double *A = rec + (int64_t)(o == 0 ? t : s) * TRI_REC;
         const double *B = rec + (int64_t)(o == 0 ? s : t) * TRI_REC;
         const double *r = A + TR_Q + 3 * p;
         double I1, Iv[3], I3[3];
         potentials(B + TR_P, r, I1, Iv, I3);
         const double wp = A[TR_W + p];
-        const z64 k = (med == 0) ? z64(md.k1r, md.k1i) : z64(md.k2r, md.k2i);
-        const z64 kk = k * k;
-        z64 S0(I1 / (4.0 * PI), 0), Sr[3], Wv[3];
-        for (int d = 0; d < 3; ++d) {
-            Sr[d] = z64(Iv[d] / (4.0 * PI), 0);
-            Wv[d] = z64(-I3[d] / (4.0 * PI), 0) + kk * (Iv[d] / (8.0 * PI));
-        }
-        for (int q = 0; q < 7; ++q) {
-            double dv[3];
-            sub3(r, B + TR_Q + 3 * q, dv);
-            double R = sqrt(dot3(dv, dv));
-            z64 gs, hs;
-            green_rems(k, R, gs, hs);
-            gs = gs * B[TR_W + q];
-            hs = hs * B[TR_W + q];
-            S0 += gs;
+        const double rr[3] = {r[0] - A[TR_CEN], r[1] - A[TR_CEN + 1], r[2] - A[TR_CEN + 2]};
+        const double r2 = dot3(rr, rr);
+#pragma unroll
+        for (int med = 0; med < 2; ++med) {
+            const z64 k = med == 0 ? z64(md.k1r, md.k1i) : z64(md.k2r, md.k2i);
+            const z64 kk = k * k;
+            z64 S0(I1 / (4.0 * PI), 0), Sr[3], Wv[3];
             for (int d = 0; d < 3; ++d) {
-                Sr[d] += gs * (-dv[d]);
-                Wv[d] += hs * dv[d];
+                Sr[d] = z64(Iv[d] / (4.0 * PI), 0);
+                Wv[d] = z64(-I3[d] / (4.0 * PI), 0) + kk * (Iv[d] / (8.0 * PI));
             }
-        }
-        const z64 mjk(k.im, -k.re);
-        const z64 four_k2 = cdiv(z64(4, 0), kk);
-        for (int a = 0; a < 3; ++a) {
-            double ta[3];
-            sub3(r, A + TR_P + 3 * a, ta);
-            for (int b = 0; b < 3; ++b) {
-                double rb[3];
-                sub3(r, B + TR_P + 3 * b, rb);
-                const double cc = A[TR_C + a] * B[TR_C + b] * wp;
-                z64 tS(0, 0);
-                for (int d = 0; d < 3; ++d) tS += ta[d] * (Sr[d] + rb[d] * S0);
-                accT[3 * a + b] = cc * (mjk * (tS - four_k2 * S0));
-                if (t != s) {
-                    z64 c0 = Wv[1] * rb[2] - Wv[2] * rb[1];
-                    z64 c1 = Wv[2] * rb[0] - Wv[0] * rb[2];
-                    z64 c2 = Wv[0] * rb[1] - Wv[1] * rb[0];
-                    accK[3 * a + b] = cc * (ta[0] * c0 + ta[1] * c1 + ta[2] * c2);
+            for (int q = 0; q < 7; ++q) {
+                double dv[3];
+                sub3(r, B + TR_Q + 3 * q, dv);
+                const double R = sqrt(dot3(dv, dv));
+                z64 gs, hs;
+                if constexpr (sizeof(T) == 4) {   // mixed path: smooth remainders in FP32
+                    c32 g32, h32;
+                    green_rems_f((float)k.re, (float)k.im, (float)R, g32, h32);
+                    gs = z64(g32.re, g32.im);
+                    hs = z64(h32.re, h32.im);
+                } else {
+                    green_rems(k, R, gs, hs);
+                }
+                gs = gs * B[TR_W + q];
+                hs = hs * B[TR_W + q];
+                S0 += gs;
+                for (int d = 0; d < 3; ++d) {
+                    Sr[d] += gs * (-dv[d]);
+                    Wv[d] += hs * dv[d];
                 }
             }
+            z64 *m = mom[med];
+            const z64 wS0 = wp * S0;
+            m[0] = wS0;
+            m[1] = rr[0] * wS0; m[2] = rr[1] * wS0; m[3] = rr[2] * wS0;
+            m[4] = r2 * wS0;
+            m[5] = wp * Sr[0]; m[6] = wp * Sr[1]; m[7] = wp * Sr[2];
+            m[8] = rr[0] * m[5] + rr[1] * m[6] + rr[2] * m[7];
+            m[9] = wp * Wv[0]; m[10] = wp * Wv[1]; m[11] = wp * Wv[2];
+            // Wv x r
+            m[12] = rr[2] * m[10] - rr[1] * m[11];
+            m[13] = rr[0] * m[11] - rr[2] * m[9];
+            m[14] = rr[1] * m[9] - rr[0] * m[10];
         }
     }
-    // reduce over the eight lanes of each (o, medium) group
-    for (int c = 0; c < 9; ++c) {
-        for (int off = 1; off < 8; off <<= 1) {
-            accK[c].re += __shfl_xor_sync(0xffffffffu, accK[c].re, off);
-            accK[c].im += __shfl_xor_sync(0xffffffffu, accK[c].im, off);
-            accT[c].re += __shfl_xor_sync(0xffffffffu, accT[c].re, off);
-            accT[c].im += __shfl_xor_sync(0xffffffffu, accT[c].im, off);
-        }
-    }
-    // group sums to shared memory: sm[o][i][K|T][c]
+    // sum over the eight lanes of each (slot, o) group
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int c = 0; c < NEAR_MOM; ++c)
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1) {
+                mom[i][c].re += __shfl_xor_sync(0xffffffffu, mom[i][c].re, off);
+                mom[i][c].im += __shfl_xor_sync(0xffffffffu, mom[i][c].im, off);
+            }
     if (p == 0)
-        for (int c = 0; c < 9; ++c) {
-            sm[o][med][0][c] = accK[c];
-            sm[o][med][1][c] = accT[c];
-        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int c = 0; c < NEAR_MOM; ++c) sm[slot][o][i][c] = mom[i][c];
     __syncwarp();
-    if (lane >= 9) return;
-    // lane c = 3 a + b: symmetrise, weight the media into Ks, Ta, Tb and store
-    const int a = lane / 3, b = lane % 3;
-    const z64 e1(md.e1r, md.e1i), e2(md.e2r, md.e2i);
-    z64 v[3] = {z64(0, 0), z64(0, 0), z64(0, 0)};
-    for (int i = 0; i < 2; ++i) {
-        const z64 ei = i == 0 ? e1 : e2;
-        z64 Ks = 0.5 * (sm[0][i][0][3 * a + b] + sm[1][i][0][3 * b + a]);
-        z64 Ts = 0.5 * (sm[0][i][1][3 * a + b] + sm[1][i][1][3 * b + a]);
-        v[0] += Ks;
-        v[1] += -ei * Ts;
-        v[2] += cdiv(Ts, ei);
+    const int e = lane & 15;
+    if (e >= 9 || t < 0) return;
+    // lane (slot, e = 3 a + b): entry (a, b) of (t, s) = 1/2 [L~_o0(a, b) + L~_o1(b, a)]
+    const int a = e / 3, b = e % 3;
+    z64 ks(0, 0), ta(0, 0), tb(0, 0);
+#pragma unroll
+    for (int oo = 0; oo < 2; ++oo) {
+        const double *A = rec + (int64_t)(oo == 0 ? t : s) * TRI_REC;
+        const double *B = rec + (int64_t)(oo == 0 ? s : t) * TRI_REC;
+        const int ia = oo == 0 ? a : b, ib = oo == 0 ? b : a;   // test vertex, trial vertex
+        double P[3], Q[3];
+        for (int d = 0; d < 3; ++d) {
+            P[d] = A[TR_P + 3 * ia + d] - A[TR_CEN + d];
+            Q[d] = B[TR_P + 3 * ib + d] - A[TR_CEN + d];
+        }
+        const double cc = 0.5 * A[TR_C + ia] * B[TR_C + ib];
+        const double PQ = dot3(P, Q);
+        const double PpQ[3] = {P[0] + Q[0], P[1] + Q[1], P[2] + Q[2]};
+        const double QmP[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
+        // P x Q: P.(MW x Q) = MW.(Q x P)
+        const double QxP[3] = {Q[1] * P[2] - Q[2] * P[1], Q[2] * P[0] - Q[0] * P[2], Q[0] * P[1] - Q[1] * P[0]};
+#pragma unroll
+        for (int med = 0; med < 2; ++med) {
+            const z64 *m = sm[slot][oo][med];
+            const z64 k = med == 0 ? z64(md.k1r, md.k1i) : z64(md.k2r, md.k2i);
+            const z64 eta = med == 0 ? z64(md.e1r, md.e1i) : z64(md.e2r, md.e2i);
+            z64 br = m[8] + m[4] - (P[0] * m[5] + P[1] * m[6] + P[2] * m[7]) -
+                     (PpQ[0] * m[1] + PpQ[1] * m[2] + PpQ[2] * m[3]) + PQ * m[0] - cdiv(z64(4, 0), k * k) * m[0];
+            const z64 Tv = cc * (z64(k.im, -k.re) * br);
+            ta += -eta * Tv;
+            tb += cdiv(Tv, eta);
+            if (t != s)
+                ks += cc * (QmP[0] * m[12] + QmP[1] * m[13] + QmP[2] * m[14] + QxP[0] * m[9] + QxP[1] * m[10] +
+                            QxP[2] * m[11]);
+        }
     }
+    const z64 v[3] = {ks, ta, tb};
     const int64_t plane = (int64_t)nt * nt;
     for (int op = 0; op < 3; ++op) {
         cx<T> val((T)v[op].re, (T)v[op].im);
@@ -594,15 +676,25 @@ __global__ void __launch_bounds__(128) k_far(const AsmJob<T> *__restrict__ jobs,
     }
 }
 
-// Near pairs of all meshes: one warp per pair, grid-stride.
+// Near pairs of all meshes: two pairs per warp (the pairs of one warp may
+// belong to different meshes), grid-stride over pair couples.
 template <typename T>
 __global__ void __launch_bounds__(128) k_near_blocks(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t npairs) {
-    __shared__ z64 sm_all[4][2][2][2][9];
+    __shared__ z64 sm_all[4][2][2][2][NEAR_MOM];
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t pid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; pid < npairs; pid += nw) {
-        const AsmJob<T> &J = jobs[find_job<T, &AsmJob<T>::near0>(jobs, njobs, pid)];
-        const int64_t l = pid - J.near0;
-        near_pair<T>(J.pairs[2 * l], J.pairs[2 * l + 1], J.nt, J.rec64, J.md, J.Zloc, sm_all[(threadIdx.x >> 5) & 3]);
+    const int64_t ncouple = (npairs + 1) / 2;
+    const int slot = (threadIdx.x >> 4) & 1;
+    for (int64_t cp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; cp < ncouple; cp += nw) {
+        const int64_t pid = 2 * cp + slot;
+        int t = -1, s = -1;
+        const AsmJob<T> *J = &jobs[0];
+        if (pid < npairs) {
+            J = &jobs[find_job<T, &AsmJob<T>::near0>(jobs, njobs, pid)];
+            const int64_t l = pid - J->near0;
+            t = J->pairs[2 * l];
+            s = J->pairs[2 * l + 1];
+        }
+        near_pair2<T>(t, s, J->nt, J->rec64, J->md, J->Zloc, sm_all[(threadIdx.x >> 5) & 3]);
     }
 }
 
@@ -730,7 +822,7 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
     if (npairs > 0) {
         int occ = 0;
         CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_near_blocks<T>, 128, 0));
-        const unsigned grid = (unsigned)std::min<int64_t>((int64_t)std::max(1, occ) * nsm, (npairs * 32 + 127) / 128);
+        const unsigned grid = (unsigned)std::min<int64_t>((int64_t)std::max(1, occ) * nsm, ((npairs + 1) / 2 * 32 + 127) / 128);
         ProfScope ps_("k_near_blocks", st);
         k_near_blocks<T><<<grid, 128, 0, st>>>(djobs.p, nj, npairs);
         launched("k_near_blocks");
