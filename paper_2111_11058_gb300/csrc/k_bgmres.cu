@@ -163,43 +163,48 @@ __global__ void __launch_bounds__(PCHOL_THREADS) k_pchol(int m, const z64 *__res
 
 // Rinv = R11^{-1} for the leading r x r block of the upper-triangular Cholesky
 // factor R (r = *rank; row-major, ld m, real positive diagonal), zero
-// elsewhere in the m x m output.  One warp per column j: back substitution
-// x_k = (delta_kj - sum_{k<l<=j} R[k][l] x_l) / R[k][k] with the sum split
-// over the lanes; lane owns rows lane + 32 t.  The columns run on separate SMs,
-// so the FP64 work spreads over the GPU.
+// elsewhere in the m x m output.  One warp per column j, column-oriented back
+// substitution: x_k = b_k / R[k][k] for k = j .. 0, then b_i -= R[i][k] x_k
+// for the rows i < k still open (b = e_j at the start); lane owns rows
+// lane + 32 t.  On GB300 a warp-wide FP64 instruction occupies its SMSP's FP64
+// pipe for ~64 cycles, so the step is kept to one real-complex product and
+// the multiply-adds of the row groups that are still open; the reciprocal
+// diagonals are formed up front.  The columns run on separate SMs.
 __global__ void __launch_bounds__(32) k_trinv(int m, const z64 *__restrict__ R, const int *__restrict__ rank,
                                               z64 *__restrict__ Rinv) {
+    constexpr int NT = PCHOL_MAX / 32;
     const int j = blockIdx.x, lane = threadIdx.x;
     const int r = *rank;
-    z64 x[PCHOL_MAX / 32];
+    z64 b[NT];
+    double inv[NT];
 #pragma unroll
-    for (int t = 0; t < PCHOL_MAX / 32; ++t) x[t] = z64(0, 0);
+    for (int t = 0; t < NT; ++t) {
+        const int i = lane + 32 * t;
+        b[t] = z64(i == j && j < r ? 1.0 : 0.0, 0.0);
+        inv[t] = i < r ? 1.0 / R[(int64_t)i * m + i].re : 0.0;
+    }
     if (j < r) {
         for (int k = j; k >= 0; --k) {
-            const z64 *Rk = R + (int64_t)k * m;
-            z64 s(0, 0);
+            const int tk = k >> 5, owner = k & 31;
+            z64 xk(0, 0);
 #pragma unroll
-            for (int t = 0; t < PCHOL_MAX / 32; ++t) {
-                const int l = lane + 32 * t;
-                if (l > k && l <= j) s += Rk[l] * x[t];
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                s.re += __shfl_xor_sync(0xffffffffu, s.re, o);
-                s.im += __shfl_xor_sync(0xffffffffu, s.im, o);
-            }
-            if (lane == (k & 31)) {
-                const double inv = 1.0 / Rk[k].re;
-                const z64 xk = ((k == j ? z64(1, 0) : z64(0, 0)) - s) * inv;
+            for (int t = 0; t < NT; ++t)
+                if (t == tk) xk = b[t] * inv[t];
+            xk.re = __shfl_sync(0xffffffffu, xk.re, owner);
+            xk.im = __shfl_sync(0xffffffffu, xk.im, owner);
 #pragma unroll
-                for (int t = 0; t < PCHOL_MAX / 32; ++t)
-                    if (t == (k >> 5)) x[t] = xk;
+            for (int t = 0; t < NT; ++t) {
+                if (32 * t > k) break;   // warp-uniform: rows of this group are all >= k
+                const int i = lane + 32 * t;
+                if (i == k) b[t] = xk;
+                else if (i < k) b[t] -= R[(int64_t)i * m + k] * xk;
             }
         }
     }
 #pragma unroll
-    for (int t = 0; t < PCHOL_MAX / 32; ++t) {
-        const int l = lane + 32 * t;
-        if (l < m) Rinv[(int64_t)l * m + j] = x[t];
+    for (int t = 0; t < NT; ++t) {
+        const int i = lane + 32 * t;
+        if (i < m) Rinv[(int64_t)i * m + j] = i <= j ? b[t] : z64(0, 0);
     }
 }
 
