@@ -16,7 +16,10 @@
 //   * the block Hessenberg least-squares problem min ||E1 S - Hbar Z|| is
 //     solved through a QR of Hbar kept up to date block column by block
 //     column (block Gram-Schmidt + Cholesky QR, again applied twice).
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <atomic>
 #include <vector>
@@ -29,136 +32,244 @@ namespace {
 
 constexpr int PCHOL_MAX = 128;
 constexpr int PCHOL_THREADS = 256;
-// dynamic shared memory of k_pchol: packed upper triangle, one row, the pivot order
-constexpr size_t pchol_smem(int m) {
-    return (size_t)(m * (m + 1) / 2 + m) * sizeof(z64) + (size_t)m * sizeof(int);
+// ------------------------------------------------ pivoted Cholesky factor
+// Pivoted Cholesky of the Hermitian m x m matrix M (row-major): with the order
+// perm, M[perm[a]][perm[b]] = sum_i conj(R[i][a]) R[i][b], R upper trapezoidal
+// (rank x m, row-major, ld m, rows >= rank zero).  pivot == 0 keeps the
+// order.  A remaining diagonal below tol * max(initial diagonal) ends the
+// factorisation (rank).
+//
+// It runs on a cluster of PC_CL CTAs (one per SM).  CTA c owns the rows of
+// original index a = c + PC_CL l of the Schur complement, stored in full in
+// its shared memory.  Step i: every CTA proposes its largest remaining
+// diagonal (lowest position on ties; without pivoting only the owner of
+// position i proposes) and writes that row, unscaled, with the diagonal and
+// its inverse square root into the shared memory of every CTA of the
+// cluster; after one cluster-wide synchronisation all CTAs pick the same
+// winner q, CTA 0 writes row i of R (by original index; permuted to positions
+// after the loop), and each CTA updates its own rows only,
+//   U(a, b) -= conj(U(q, a)) U(q, b) / U(q, q).
+// The FP64 work of the updates is spread over the cluster's SMs.  The per-step
+// synchronisation is an mbarrier that every CTA arrives on remotely; its wait
+// gives up after one second (error flag, loop ends).  Hardware cluster
+// barriers are used only where every CTA arrives unconditionally: after
+// set-up and before exit.
+namespace cg = cooperative_groups;
+constexpr int PC_CL = 8;
+constexpr int PC_ROWS = (PCHOL_MAX + PC_CL - 1) / PC_CL;
+constexpr uint64_t PC_WAIT_NS = 1000000000ull;
+
+// dynamic shared memory: own rows [PC_ROWS][m] and proposals [2][PC_CL][m]
+constexpr size_t pchol_cl_smem(int m) { return (size_t)(PC_ROWS + 2 * PC_CL) * m * sizeof(z64); }
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// Pivoted Cholesky of the Hermitian m x m matrix M (row-major): with the
-// order perm, M[perm[a]][perm[b]] = sum_i conj(R[i][a]) R[i][b], R upper
-// trapezoidal (rank x m, row-major, ld m, rows >= rank zero).  pivot == 0
-// keeps the order.  A remaining diagonal below tol * max(initial diagonal)
-// ends the factorisation (rank).
-//
-// One block; the Schur complement lives in shared memory as the packed upper
-// triangle in the ORIGINAL index order (U[P(a, b)], a <= b), so a pivot step
-// swaps two entries of perm (and two columns of the finished rows of R)
-// instead of two rows and columns.  FP64 throughput of one SM bounds this
-// kernel, so every scalar of a step is computed once, and the rank-1 update
-// runs over the flattened triangle of remaining pairs (no idle lanes).
-__global__ void __launch_bounds__(PCHOL_THREADS) k_pchol(int m, const z64 *__restrict__ M, int *__restrict__ perm,
-                                                         z64 *__restrict__ R, int *__restrict__ rank_out, double tol,
-                                                         int pivot) {
-    extern __shared__ z64 U[];
-    z64 *rb = U + (int64_t)m * (m + 1) / 2;      // current row of R, by position
-    int *piv = reinterpret_cast<int *>(rb + m);  // position -> original index
-    __shared__ int s_rank;
+// Cluster-wide synchronisation on the mbarriers `bar` (count PC_CL) of every
+// CTA; releases this CTA's shared-memory writes (local and remote) and
+// acquires the others'.  False (and the error flag set) when the wait expires.
+__device__ __forceinline__ bool cl_sync(uint64_t *bar, uint32_t parity, int *abort_flag, int *err) {
+    __syncthreads();   // this CTA's writes happen before thread 0's release-arrives (cumulative)
+    if (threadIdx.x == 0) {
+        const uint32_t local = su32(bar);
+        for (int r = 0; r < PC_CL; ++r) {
+            uint32_t remote;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
+            asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+        }
+        uint32_t ok = 0;
+        const uint64_t t0 = gtime();
+        while (true) {
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+                " selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(ok)
+                : "r"(local), "r"(parity)
+                : "memory");
+            if (ok || gtime() - t0 > PC_WAIT_NS) break;
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+        }
+    }
+    __syncthreads();   // the others' writes, acquired by thread 0, are visible to the CTA
+    return *(volatile int *)abort_flag == 0;
+}
+
+__global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
+    k_pchol_cl(int m, const z64 *__restrict__ M, int *__restrict__ perm, z64 *__restrict__ R,
+               int *__restrict__ rank_out, double tol, int pivot, int *__restrict__ err) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int me = (int)cl.block_rank();
+    extern __shared__ __align__(16) unsigned char pc_raw[];
+    z64 *Uloc = reinterpret_cast<z64 *>(pc_raw);   // [PC_ROWS][m]
+    z64 *crow = Uloc + (size_t)PC_ROWS * m;        // [2][PC_CL][m], by original index
+    __shared__ uint64_t cbar;
+    __shared__ double cval[2][PC_CL], crd[2][PC_CL];   // proposal: diagonal, 1 / sqrt(diagonal)
+    __shared__ int cpos[2][PC_CL];
+    __shared__ z64 s_coef[PC_ROWS];                     // conj(U(q, a)) / U(q, q) per own row
+    __shared__ int piv[PCHOL_MAX], posof[PCHOL_MAX];
+    __shared__ int s_abort, s_rank, s_ls, s_stop;
     __shared__ double s_thr, s_d, s_rd;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    auto PU = [m](int a, int b) { return a * m - a * (a - 1) / 2 + (b - a); };
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-        const int a = idx / m, b = idx - a * m;
-        if (b >= a) U[PU(a, b)] = M[idx];
-        R[idx] = z64(0, 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nth = blockDim.x;
+    const int nloc = me < m ? (m - me + PC_CL - 1) / PC_CL : 0;
+    for (int idx = threadIdx.x; idx < nloc * m; idx += nth) {
+        const int ls = idx / m, b = idx - ls * m, a = me + PC_CL * ls;
+        Uloc[idx] = M[(int64_t)a * m + b];
+        R[(int64_t)a * m + b] = z64(0, 0);
     }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) piv[i] = i;
-    __syncthreads();
+    for (int k = threadIdx.x; k < m; k += nth) {
+        piv[k] = k;
+        posof[k] = k;
+    }
     if (warp == 0) {
-        double best = 0.0;
-        for (int i = lane; i < m; i += 32) best = fmax(best, U[PU(i, i)].re);
-        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+        double mx = 0.0;
+        for (int k = lane; k < m; k += 32) mx = fmax(mx, M[(int64_t)k * m + k].re);
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) {
-            s_thr = tol * best;
+            s_thr = tol * mx;
+            s_abort = 0;
             s_rank = m;
+            s_stop = m;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&cbar)), "r"(PC_CL) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
     }
     __syncthreads();
+    cl.sync();   // every CTA's barrier is initialised before the first remote arrive
+    const double thr = s_thr;
     for (int i = 0; i < m; ++i) {
-        // pivot: largest remaining diagonal, lowest position on ties
+        const int par = i & 1;
+        // ---- this CTA's proposal: its largest remaining diagonal and that row, unscaled
         if (warp == 0) {
-            if (pivot) {
-                double bv = -1.0;
-                int bp = i;
-                for (int pos = i + lane; pos < m; pos += 32) {
-                    const int l = piv[pos];
-                    const double v = U[PU(l, l)].re;
-                    if (v > bv) { bv = v; bp = pos; }
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                    const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-                    if (ov > bv || (ov == bv && op < bp)) { bv = ov; bp = op; }
-                }
-                if (bp != i) {
-                    // the finished rows of R follow the new order of positions i and bp
-                    for (int rr = lane; rr < i; rr += 32) {
-                        const z64 t = R[(int64_t)rr * m + i];
-                        R[(int64_t)rr * m + i] = R[(int64_t)rr * m + bp];
-                        R[(int64_t)rr * m + bp] = t;
-                    }
-                    if (lane == 0) {
-                        const int t = piv[i];
-                        piv[i] = piv[bp];
-                        piv[bp] = t;
-                    }
+            long long best = LLONG_MIN;
+            int bp = INT_MAX, bls = -1;
+            for (int ls = lane; ls < nloc; ls += 32) {
+                const int a = me + PC_CL * ls, pa = posof[a];
+                if (pa < i || (!pivot && pa != i)) continue;
+                const long long v = __double_as_longlong(Uloc[ls * m + a].re);   // orders positive doubles
+                if (bls < 0 || v > best || (v == best && pa < bp)) {
+                    best = v;
+                    bp = pa;
+                    bls = ls;
                 }
             }
-            __syncwarp();
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int op = __shfl_xor_sync(0xffffffffu, bp, o), ol = __shfl_xor_sync(0xffffffffu, bls, o);
+                if (ol >= 0 && (bls < 0 || ov > best || (ov == best && op < bp))) {
+                    best = ov;
+                    bp = op;
+                    bls = ol;
+                }
+            }
             if (lane == 0) {
-                const double dq = U[PU(piv[i], piv[i])].re;
-                if (!(dq > s_thr) || dq <= 0.0) {
-                    s_rank = i;
-                } else {
-                    s_d = sqrt(dq);
-                    s_rd = 1.0 / s_d;
-                }
+                s_ls = bls;
+                s_rank = bp;   // position of the proposal (scratch until the loop ends)
+                s_d = bls >= 0 ? __longlong_as_double(best) : -1.0;
             }
         }
         __syncthreads();
-        if (s_rank == i) break;
-        // row i of R: R[i][pos] = U'(q, piv[pos]) / d
-        const int q = piv[i];
-        const double d = s_d, rd = s_rd;
-        for (int pos = i + threadIdx.x; pos < m; pos += blockDim.x) {
-            const int l = piv[pos];
-            z64 v = q <= l ? U[PU(q, l)] : conj(U[PU(l, q)]);
-            v = pos == i ? z64(d, 0) : v * rd;
-            rb[pos] = v;
-            R[(int64_t)i * m + pos] = v;
+        const int pls = s_ls;
+        if (pls >= 0) {
+            // raw row to every CTA; meanwhile lane 0 of warp 0 forms 1 / sqrt(diagonal)
+            if (threadIdx.x == 0) {
+                const double val = s_d;
+                s_rd = val > 0.0 ? 1.0 / sqrt(val) : 0.0;
+            }
+            for (int idx = threadIdx.x; idx < PC_CL * m; idx += nth) {
+                const int r = idx / m, b = idx - r * m;
+                *cl.map_shared_rank(crow + ((size_t)par * PC_CL + me) * m + b, r) = Uloc[pls * m + b];
+            }
         }
         __syncthreads();
-        // Schur complement update U'(a, b) -= conj(R[i][pa]) R[i][pb] over the
-        // remaining position pairs pa <= pb, flattened: row u of the triangle
-        // starts at S(u) = u n - u (u - 1) / 2
-        const int n = m - i - 1;
-        const int npairs = n * (n + 1) / 2;
-        for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
-            const float tn = 2.0f * n + 1.0f;
-            int u = (int)((tn - sqrtf(tn * tn - 8.0f * idx)) * 0.5f);
-            u = u < 0 ? 0 : (u >= n ? n - 1 : u);
-            while (u > 0 && u * n - u * (u - 1) / 2 > idx) --u;
-            while (u + 1 < n && (u + 1) * n - (u + 1) * u / 2 <= idx) ++u;
-            const int pa = i + 1 + u, pb = pa + (idx - (u * n - u * (u - 1) / 2));
-            const int a = piv[pa], b = piv[pb];
-            const z64 ra = rb[pa], rbb = rb[pb];
-            // U -= conj(ra) rbb (stored at (a, b)) or its conjugate (stored at (b, a)): four FMAs
-            const bool up = a <= b;
-            const int off = up ? PU(a, b) : PU(b, a);
-            // conditional sign flip on the integer side (keeps the FP64 pipe for the FMAs)
-            const long long sgn = up ? 0ll : (long long)0x8000000000000000ull;
-            const double are = __longlong_as_double(__double_as_longlong(ra.re) ^ sgn);
-            const double aim = __longlong_as_double(__double_as_longlong(ra.im) ^ sgn);
-            z64 w = U[off];
-            w.re = fma(-ra.re, rbb.re, w.re);
-            w.re = fma(-ra.im, rbb.im, w.re);
-            w.im = fma(-are, rbb.im, w.im);
-            w.im = fma(aim, rbb.re, w.im);
-            U[off] = w;
+        if (threadIdx.x < PC_CL) {   // the scalars of the proposal, one CTA per lane
+            const int r = threadIdx.x;
+            *cl.map_shared_rank(&cval[par][me], r) = pls >= 0 ? s_d : -1.0;
+            *cl.map_shared_rank(&crd[par][me], r) = pls >= 0 ? s_rd : 0.0;
+            *cl.map_shared_rank(&cpos[par][me], r) = pls >= 0 ? s_rank : INT_MAX;
+        }
+        if (!cl_sync(&cbar, (uint32_t)par, &s_abort, err)) break;
+        // ---- the same decision in every CTA
+        int w = -1, bpos = INT_MAX;
+        long long bv = 0;
+        for (int r = 0; r < PC_CL; ++r) {
+            const int pr = cpos[par][r];
+            if (pr == INT_MAX) continue;
+            const long long vb = __double_as_longlong(cval[par][r]);
+            if (w < 0 || vb > bv || (vb == bv && pr < bpos)) {
+                w = r;
+                bv = vb;
+                bpos = pr;
+            }
+        }
+        const double dq = w >= 0 ? cval[par][w] : -1.0;
+        if (w < 0 || !(dq > thr) || dq <= 0.0) {
+            if (threadIdx.x == 0) s_stop = i;
+            break;
+        }
+        const z64 *Ri = crow + ((size_t)par * PC_CL + w) * m;   // row q of the Schur complement, unscaled
+        const double rdq = crd[par][w];                         // 1 / sqrt(U(q, q))
+        __syncthreads();   // everyone has read the positions of step i - 1
+        if (threadIdx.x == 0 && bpos != i) {
+            const int t = piv[i];
+            piv[i] = piv[bpos];
+            piv[bpos] = t;
+            posof[piv[i]] = i;
+            posof[piv[bpos]] = bpos;
+        }
+        if (threadIdx.x < nloc) {   // per own row: conj(U(q, a)) / U(q, q)
+            const double inv = rdq * rdq;
+            s_coef[threadIdx.x] = conj(Ri[me + PC_CL * threadIdx.x]) * inv;
+        }
+        __syncthreads();
+        // row i of R = row q / sqrt(U(q, q)), by original index for now (permuted to positions after the loop)
+        if (me == 0) {
+            const int q = piv[i];
+            for (int b = threadIdx.x; b < m; b += nth)
+                R[(int64_t)i * m + b] = posof[b] < i ? z64(0, 0) : (b == q ? z64(dq * rdq, 0) : Ri[b] * rdq);
+        }
+        // ---- rank-1 update of this CTA's remaining rows over the remaining positions:
+        // U(a, b) -= conj(U(q, a)) U(q, b) / U(q, q)
+        const int rem = m - i - 1;
+        for (int idx = threadIdx.x; idx < nloc * rem; idx += nth) {
+            const int ls = idx / rem, pos = i + 1 + (idx - ls * rem);
+            const int a = me + PC_CL * ls;
+            if (posof[a] <= i) continue;
+            const int b = piv[pos];
+            const z64 c = s_coef[ls], rb_ = Ri[b];
+            z64 u = Uloc[ls * m + b];
+            u.re = fma(-c.re, rb_.re, u.re);
+            u.re = fma(c.im, rb_.im, u.re);
+            u.im = fma(-c.re, rb_.im, u.im);
+            u.im = fma(-c.im, rb_.re, u.im);
+            Uloc[ls * m + b] = u;
         }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = piv[i];
-    if (threadIdx.x == 0) *rank_out = s_rank;
+    __syncthreads();
+    if (threadIdx.x == 0) s_rank = s_stop;
+    __syncthreads();
+    cl.sync();   // rows of R written by CTA 0 are visible to every CTA; no proposal is in flight any more
+    // R[i][pos] = row i by original index at piv[pos] (rows distributed over the CTAs)
+    const int rk = s_rank;
+    for (int i = me; i < rk; i += PC_CL) {
+        for (int b = threadIdx.x; b < m; b += nth) crow[b] = R[(int64_t)i * m + b];
+        __syncthreads();
+        for (int pos = threadIdx.x; pos < m; pos += nth) R[(int64_t)i * m + pos] = crow[piv[pos]];
+        __syncthreads();
+    }
+    if (me == 0) {
+        for (int k = threadIdx.x; k < m; k += nth) perm[k] = piv[k];
+        if (threadIdx.x == 0) *rank_out = rk;
+    }
+    cl.sync();   // no CTA leaves while another may still use the cluster's shared memory
 }
 
 // Rinv = R11^{-1} for the leading r x r block of the upper-triangular Cholesky
@@ -327,7 +438,7 @@ inline unsigned nb(int64_t work) { return (unsigned)std::max<int64_t>(1, std::mi
 struct Ctx {
     cudaStream_t st;
     DevBuf<z64> M, R, Rinv, X, T1, Rf;
-    DevBuf<int> perm, rank;
+    DevBuf<int> perm, rank, err;
     DevBuf<double> rnrm, scale;
 };
 
@@ -337,8 +448,8 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
     int dev = 0;
     CBFM_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && !attr_set[dev].load(std::memory_order_acquire)) {
-        CBFM_CUDA(cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)pchol_smem(PCHOL_MAX)));
+        CBFM_CUDA(cudaFuncSetAttribute(k_pchol_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)pchol_cl_smem(PCHOL_MAX)));
         attr_set[dev].store(true, std::memory_order_release);
     }
     {
@@ -347,7 +458,8 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
         prof_add_work("k_pchol", 8.0 * m * m * m / 6.0, 16.0 * m * m);
         prof_add_work("k_trinv", 8.0 * m * m * m / 6.0, 32.0 * m * m);
         ProfScope ps_("k_pchol", c.st);
-        k_pchol<<<1, PCHOL_THREADS, pchol_smem(m), c.st>>>(m, c.M.p, c.perm.p, c.R.p, c.rank.p, tol, pivot ? 1 : 0);
+        k_pchol_cl<<<PC_CL, PCHOL_THREADS, pchol_cl_smem(m), c.st>>>(m, c.M.p, c.perm.p, c.R.p, c.rank.p, tol,
+                                                                     pivot ? 1 : 0, c.err.p);
         launched("k_pchol");
     }
     {
@@ -355,10 +467,12 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
         k_trinv<<<m, 32, 0, c.st>>>(m, c.R.p, c.rank.p, c.Rinv.p);
         launched("k_trinv");
     }
-    int r = 0;
-    CBFM_CUDA(cudaMemcpyAsync(&r, c.rank.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    int hr[2] = {0, 0};
+    CBFM_CUDA(cudaMemcpyAsync(&hr[0], c.rank.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    CBFM_CUDA(cudaMemcpyAsync(&hr[1], c.err.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
     CBFM_CUDA(cudaStreamSynchronize(c.st));
-    return r;
+    if (hr[1]) throw Fail{CBFM_ETIMEOUT, "pivoted Cholesky: a cluster synchronisation expired"};
+    return hr[0];
 }
 
 // Rank-revealing orthonormalisation of m row vectors W (m x n, ld n; W is
@@ -463,6 +577,8 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     c.T1.alloc((size_t)p * n);
     c.perm.alloc(p);
     c.rank.alloc(1);
+    c.err.alloc(1);
+    CBFM_CUDA(cudaMemsetAsync(c.err.p, 0, sizeof(int), st));
     c.rnrm.alloc(p);
     c.scale.alloc(p);
     DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw;
