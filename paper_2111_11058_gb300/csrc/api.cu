@@ -426,6 +426,15 @@ cbfm_status cbfm_mesh(const double *verts, int64_t nv, const int32_t *tris, int6
         upload(dt, h.tris, st);
         upload(m->tri_vid, h.tris, st);
         upload(m->tri_edge, h.tri_edge, st);
+        {
+            // cell of each RWG of each triangle (edges are sorted by cell)
+            std::vector<int32_t> tc((size_t)3 * h.nt);
+            for (size_t k = 0; k < tc.size(); ++k) {
+                const int32_t e = h.tri_edge[k];
+                tc[k] = (int32_t)(std::upper_bound(h.cell_off.begin(), h.cell_off.end(), e) - h.cell_off.begin()) - 1;
+            }
+            upload(m->tri_cell, tc, st);
+        }
         upload(m->edge_tri, h.edge_tri, st);
         upload(m->edge_loc, h.edge_loc, st);
         std::vector<int32_t> ecell(h.ne);
@@ -501,7 +510,7 @@ cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, do
         // RWG operators (FP64) and plane-wave RHS
         DevBuf<z64> Z, vE, vH;
         Z.alloc(3 * (size_t)ne * ne);
-        assemble_rwg<double>(*m, Z.p, st);
+        assemble_rwg<double>(*m, Z.p, st, true);   // the cells' diagonal blocks Z_mm only
         vE.alloc((size_t)ne * s);
         vH.alloc((size_t)ne * s);
         launch_rhs(*m, dw.p, s, vE.p, vH.p, st);
@@ -591,7 +600,9 @@ cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, do
         CBFM_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
         CBFM_CUDA(cudaStreamSynchronize(st));
         for (int c = 0; c < nc; ++c)
-            if (hinfo[c]) throw Fail{CBFM_ECUDA, "Jacobi SVD did not converge in cell " + std::to_string(c)};
+            if (hinfo[c]) throw Fail{hinfo[c] == 1 ? CBFM_ETIMEOUT : CBFM_ECUDA,
+                                     (hinfo[c] == 1 ? "Jacobi SVD: a cluster synchronisation expired in cell "
+                                                    : "Jacobi SVD did not converge in cell ") + std::to_string(c)};
         // truncation: keep sigma_i / sigma_1 >= delta_svd (paper Eq. (gram_CBF_SVD))
         std::unique_ptr<Cbf> cb(new Cbf());
         cb->kind = H_CBF;

@@ -42,6 +42,7 @@ struct Mesh : HandleBase {
     DevBuf<float> tri32;         // nt * TRI_REC (centred coordinates)
     DevBuf<int32_t> tri_vid;     // nt*3 vertex ids
     DevBuf<int32_t> tri_edge;    // nt*3 internal edge id
+    DevBuf<int32_t> tri_cell;    // nt*3 cell of each of the triangle's RWGs
     DevBuf<int32_t> edge_tri;    // ne*2
     DevBuf<int32_t> edge_loc;    // ne*2
     DevBuf<int32_t> edge_cell;   // ne, cell of each internal edge
@@ -89,7 +90,7 @@ void launch_farfield(const Mesh &m, const z64 *j, int nrhs, const double *d_obs,
 // assembly (k_assembly.cu): local blocks of all triangle pairs, then the RWG
 // matrices Z_op (op = Ks, Ta, Tb), row-major ne x ne, internal edge order.
 template <typename T>
-void assemble_rwg(Mesh &m, cx<T> *Zrwg, cudaStream_t st);
+void assemble_rwg(Mesh &m, cx<T> *Zrwg, cudaStream_t st, bool diag_cells = false);
 
 // dense complex linear algebra (k_dense.cu)
 struct GemmDesc {
@@ -109,8 +110,11 @@ void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, cons
 void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info, cudaStream_t st);
 // In-place Gauss-Jordan inverse of an n x n FP64 complex matrix (row-major); info=1 on zero pivot.
 // local blocks and RWG operators of several meshes, one launch per stage (k_assembly.cu)
+// diag_cells: only triangle pairs that support RWGs of a common cell are
+// evaluated (the cells' diagonal blocks of Z); every other entry is zero
 template <typename T>
-void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st);
+void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st,
+                        bool diag_cells = false);
 // tuned launch parameters, per key (api.cu); 0 when not tuned yet
 int tuning_get(const std::string &key);
 void tuning_set(const std::string &key, int value);

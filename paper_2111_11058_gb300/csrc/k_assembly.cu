@@ -634,6 +634,7 @@ struct AsmJob {
     const T *rec;
     const double *rec64;
     const int32_t *vid, *pairs, *edge_tri, *edge_loc;
+    const int32_t *tri_cell;   // non-null: evaluate only pairs of triangles that share a cell
     cx<T> *Zloc, *Z;
     MediaT<T> mdt;
     Media md;
@@ -651,6 +652,16 @@ __device__ __forceinline__ int find_job(const AsmJob<T> *jobs, int njobs, int64_
         else hi = mid - 1;
     }
     return lo;
+}
+
+__device__ __forceinline__ bool share_cell(const int32_t *__restrict__ tc, int t, int s) {
+    const int a0 = tc[3 * t], a1 = tc[3 * t + 1], a2 = tc[3 * t + 2];
+    bool r = false;
+    for (int k = 0; k < 3; ++k) {
+        const int b = tc[3 * s + k];
+        r |= (b == a0) | (b == a1) | (b == a2);
+    }
+    return r;
 }
 
 // Far pairs of all meshes: persistent CTAs take tasks (mesh, test triangle,
@@ -671,7 +682,14 @@ __global__ void __launch_bounds__(128) k_far(const AsmJob<T> *__restrict__ jobs,
         const int t = (int)(local / J.nstrip), s = (int)(local % J.nstrip) * blockDim.x + threadIdx.x;
         far_load(S, J.rec, J.rec64, J.vid, t);
         __syncthreads();
-        if (s < J.nt) far_pair(S, J.nt, J.rec, J.rec64, J.vid, J.alpha, J.mdt, J.Zloc, t, s);
+        if (s < J.nt) {
+            if (J.tri_cell && !share_cell(J.tri_cell, t, s)) {
+                const int64_t plane = (int64_t)J.nt * J.nt, base = (int64_t)t * J.nt + s;
+                for (int c = 0; c < NCOMP; ++c) J.Zloc[c * plane + base] = cx<T>(0, 0);
+            } else {
+                far_pair(S, J.nt, J.rec, J.rec64, J.vid, J.alpha, J.mdt, J.Zloc, t, s);
+            }
+        }
         __syncthreads();   // S and s_task are rewritten by the next task
     }
 }
@@ -693,6 +711,7 @@ __global__ void __launch_bounds__(128) k_near_blocks(const AsmJob<T> *__restrict
             const int64_t l = pid - J->near0;
             t = J->pairs[2 * l];
             s = J->pairs[2 * l + 1];
+            if (J->tri_cell && !share_cell(J->tri_cell, t, s)) t = s = -1;   // stays zero (written by k_far)
         }
         near_pair2<T>(t, s, J->nt, J->rec64, J->md, J->Zloc, sm_all[(threadIdx.x >> 5) & 3]);
     }
@@ -723,23 +742,25 @@ __global__ void k_gather(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t 
 }  // namespace
 
 template <typename T>
-void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st);
+void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st,
+                        bool diag_cells);
 
 // One mesh: the batched stages with a batch of one (one code path, so a
 // mesh assembled alone and in a batch gets the same bits).
 template <typename T>
-void assemble_rwg(Mesh &m, cx<T> *Zrwg, cudaStream_t st) {
-    assemble_rwg_batch<T>(std::vector<Mesh *>{&m}, std::vector<cx<T> *>{Zrwg}, st);
+void assemble_rwg(Mesh &m, cx<T> *Zrwg, cudaStream_t st, bool diag_cells) {
+    assemble_rwg_batch<T>(std::vector<Mesh *>{&m}, std::vector<cx<T> *>{Zrwg}, st, diag_cells);
 }
 
-template void assemble_rwg<double>(Mesh &, z64 *, cudaStream_t);
-template void assemble_rwg<float>(Mesh &, c32 *, cudaStream_t);
+template void assemble_rwg<double>(Mesh &, z64 *, cudaStream_t, bool);
+template void assemble_rwg<float>(Mesh &, c32 *, cudaStream_t, bool);
 // Local blocks, far/near pairs and RWG gather of several meshes, one launch
 // per stage.  The far stage's strip width (trial triangles per task) is
 // picked once per device and precision by timing the candidates on the first
 // batch (every candidate writes the same values, so no run is repeated).
 template <typename T>
-void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st) {
+void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st,
+                        bool diag_cells) {
     const int nj = (int)ms.size();
     if (nj == 0) return;
     std::vector<DevBuf<cx<T>>> Zloc(nj);
@@ -759,6 +780,7 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
         J.pairs = m.near_pairs.p;
         J.edge_tri = m.edge_tri.p;
         J.edge_loc = m.edge_loc.p;
+        J.tri_cell = diag_cells ? m.tri_cell.p : nullptr;
         J.Zloc = Zloc[k].p;
         J.Z = Z[k];
         J.mdt = media_t<T>(md);
@@ -836,7 +858,7 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
     CBFM_CUDA(cudaStreamSynchronize(st));   // the local blocks are released on return
 }
 
-template void assemble_rwg_batch<double>(const std::vector<Mesh *> &, const std::vector<z64 *> &, cudaStream_t);
-template void assemble_rwg_batch<float>(const std::vector<Mesh *> &, const std::vector<c32 *> &, cudaStream_t);
+template void assemble_rwg_batch<double>(const std::vector<Mesh *> &, const std::vector<z64 *> &, cudaStream_t, bool);
+template void assemble_rwg_batch<float>(const std::vector<Mesh *> &, const std::vector<c32 *> &, cudaStream_t, bool);
 
 }  // namespace cbfm

@@ -24,6 +24,7 @@
 #include <atomic>
 #include <vector>
 
+#include "cluster.cuh"
 #include "internal.cuh"
 
 namespace cbfm {
@@ -57,50 +58,9 @@ constexpr int PCHOL_THREADS = 256;
 namespace cg = cooperative_groups;
 constexpr int PC_CL = 8;
 constexpr int PC_ROWS = (PCHOL_MAX + PC_CL - 1) / PC_CL;
-constexpr uint64_t PC_WAIT_NS = 1000000000ull;
 
 // dynamic shared memory: own rows [PC_ROWS][m] and proposals [2][PC_CL][m]
 constexpr size_t pchol_cl_smem(int m) { return (size_t)(PC_ROWS + 2 * PC_CL) * m * sizeof(z64); }
-
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtime() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Cluster-wide synchronisation on the mbarriers `bar` (count PC_CL) of every
-// CTA; releases this CTA's shared-memory writes (local and remote) and
-// acquires the others'.  False (and the error flag set) when the wait expires.
-__device__ __forceinline__ bool cl_sync(uint64_t *bar, uint32_t parity, int *abort_flag, int *err) {
-    __syncthreads();   // this CTA's writes happen before thread 0's release-arrives (cumulative)
-    if (threadIdx.x == 0) {
-        const uint32_t local = su32(bar);
-        for (int r = 0; r < PC_CL; ++r) {
-            uint32_t remote;
-            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
-            asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
-        }
-        uint32_t ok = 0;
-        const uint64_t t0 = gtime();
-        while (true) {
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-                " selp.u32 %0, 1, 0, p;\n}"
-                : "=r"(ok)
-                : "r"(local), "r"(parity)
-                : "memory");
-            if (ok || gtime() - t0 > PC_WAIT_NS) break;
-        }
-        if (!ok) {
-            *abort_flag = 1;
-            atomicExch(err, 1);
-        }
-    }
-    __syncthreads();   // the others' writes, acquired by thread 0, are visible to the CTA
-    return *(volatile int *)abort_flag == 0;
-}
 
 __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
     k_pchol_cl(int m, const z64 *__restrict__ M, int *__restrict__ perm, z64 *__restrict__ R,
@@ -137,8 +97,7 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
             s_abort = 0;
             s_rank = m;
             s_stop = m;
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&cbar)), "r"(PC_CL) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            cl_bar_init(&cbar, PC_CL);
         }
     }
     __syncthreads();
@@ -195,7 +154,7 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
             *cl.map_shared_rank(&crd[par][me], r) = pls >= 0 ? s_rd : 0.0;
             *cl.map_shared_rank(&cpos[par][me], r) = pls >= 0 ? s_rank : INT_MAX;
         }
-        if (!cl_sync(&cbar, (uint32_t)par, &s_abort, err)) break;
+        if (!cl_sync(&cbar, (uint32_t)par, PC_CL, &s_abort, err)) break;
         // ---- the same decision in every CTA
         int w = -1, bpos = INT_MAX;
         long long bv = 0;

@@ -5,9 +5,14 @@
 #include <algorithm>
 #include <vector>
 
+#include <cooperative_groups.h>
+
+#include "cluster.cuh"
 #include "internal.cuh"
 
 namespace cbfm {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -227,21 +232,65 @@ __global__ void __launch_bounds__(256) k_lu_solve(const int64_t *__restrict__ zo
 // Round-robin pairing over n2 = s rounded up to even; disjoint pairs of a
 // round are processed by different warps.  Stops after a sweep without any
 // rotation, or after 60 sweeps (info = 2).
-__global__ void __launch_bounds__(256) k_jacobi_svd(int s, z64 *__restrict__ Xall, z64 *__restrict__ Vall,
-                                                    double *__restrict__ sig, int *__restrict__ info, double tol) {
-    z64 *X = Xall + (int64_t)blockIdx.x * s * s;
-    z64 *V = Vall + (int64_t)blockIdx.x * s * s;
+// One cluster of JS_CL CTAs per matrix: the s/2 column pairs of a round are
+// spread over the cluster's warps (one pair per warp), the columns stay in
+// global memory (read through L2 only, since other SMs write them), and the
+// rounds are separated by a bounded cluster synchronisation.  Every CTA finds
+// the same largest squared column norm and the same "anything rotated" answer
+// (flags exchanged through distributed shared memory), so all CTAs run the
+// same number of rounds and sweeps.  info[mat] = 2: no convergence in 60
+// sweeps; 1: a cluster synchronisation expired.
+constexpr int JS_CL = 8;
+
+__device__ __forceinline__ double norm2d(double2 a) { return a.x * a.x + a.y * a.y; }
+
+__global__ void __cluster_dims__(JS_CL, 1, 1) __launch_bounds__(256)
+    k_jacobi_svd(int s, z64 *__restrict__ Xall, z64 *__restrict__ Vall, double *__restrict__ sig,
+                 int *__restrict__ info, double tol) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int me = (int)cl.block_rank(), mat = blockIdx.x / JS_CL;
+    z64 *X = Xall + (int64_t)mat * s * s;
+    z64 *V = Vall + (int64_t)mat * s * s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t i = threadIdx.x; i < (int64_t)s * s; i += blockDim.x) V[i] = z64((i % s) == (i / s) ? 1.0 : 0.0, 0.0);
+    const int gw = me * nw + warp, ngw = JS_CL * nw;
+    __shared__ uint64_t cbar;
+    __shared__ int s_abort, rot_local, rotflag[JS_CL];
+    __shared__ double s_wmax[32], s_big;
+    for (int64_t i = (int64_t)me * blockDim.x + threadIdx.x; i < (int64_t)s * s; i += (int64_t)JS_CL * blockDim.x)
+        V[i] = z64((i % s) == (i / s) ? 1.0 : 0.0, 0.0);
+    if (threadIdx.x == 0) {
+        cl_bar_init(&cbar, JS_CL);
+        s_abort = 0;
+    }
     __syncthreads();
+    cl.sync();   // barriers initialised and V set in every CTA (unconditional)
     const int n2 = s + (s & 1);
-    __shared__ int rotated;
+    uint32_t phase = 0;
+    bool ok = true;
     int sweep = 0;
     for (; sweep < 60; ++sweep) {
-        if (threadIdx.x == 0) rotated = 0;
+        // largest squared column norm: a pair whose coupling is below tol times it is
+        // left alone (rotations at that level only stir the columns of singular values
+        // far below the largest, which carry no accuracy anyway)
+        double mx = 0.0;
+        for (int i = warp; i < s; i += nw) {
+            double al = 0;
+            for (int r = lane; r < s; r += 32) al += norm2d(__ldcg(reinterpret_cast<const double2 *>(X) + (int64_t)i * s + r));
+            for (int o = 16; o > 0; o >>= 1) al += __shfl_xor_sync(0xffffffffu, al, o);
+            mx = fmax(mx, al);
+        }
+        if (lane == 0) s_wmax[warp] = mx;
+        if (threadIdx.x == 0) rot_local = 0;
         __syncthreads();
-        for (int round = 0; round < n2 - 1; ++round) {
-            for (int pr = warp; pr < n2 / 2; pr += nw) {
+        if (threadIdx.x == 0) {
+            double bmax = 0.0;
+            for (int w = 0; w < nw; ++w) bmax = fmax(bmax, s_wmax[w]);
+            s_big = bmax;
+        }
+        __syncthreads();
+        const double floor_abs = tol * s_big;
+        for (int round = 0; round < n2 - 1 && ok; ++round) {
+            for (int pr = gw; pr < n2 / 2; pr += ngw) {
                 // round-robin: position 0 fixed, others rotate
                 int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (n2 - 1);
                 int b = 1 + (n2 - 2 - pr + round) % (n2 - 1);
@@ -251,7 +300,9 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(int s, z64 *__restrict__ Xal
                 double al = 0, be = 0;
                 z64 ga(0, 0);
                 for (int r = lane; r < s; r += 32) {
-                    z64 u = xi[r], v = xj[r];
+                    const double2 u2 = __ldcg(reinterpret_cast<const double2 *>(xi) + r);
+                    const double2 v2 = __ldcg(reinterpret_cast<const double2 *>(xj) + r);
+                    const z64 u(u2.x, u2.y), v(v2.x, v2.y);
                     al += norm2(u);
                     be += norm2(v);
                     cfmaconj(ga, u, v);
@@ -263,35 +314,46 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(int s, z64 *__restrict__ Xal
                     ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
                 }
                 double ag = sqrt(norm2(ga));
-                if (ag <= tol * sqrt(al * be) || ag == 0.0) continue;
-                if (lane == 0) rotated = 1;
+                if (ag <= tol * sqrt(al * be) || ag <= floor_abs || ag == 0.0) continue;
+                if (lane == 0) rot_local = 1;
                 double zeta = (be - al) / (2.0 * ag);
                 double t = 1.0 / (zeta + copysign(sqrt(1.0 + zeta * zeta), zeta));
                 double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
                 z64 e(ga.re / ag, ga.im / ag);   // e^{i phi}
                 z64 sem = sn * conj(e), sep = sn * e;
+                z64 *vi = V + (int64_t)i * s, *vj = V + (int64_t)j * s;
                 for (int r = lane; r < s; r += 32) {
-                    z64 u = xi[r], v = xj[r];
+                    const double2 u2 = __ldcg(reinterpret_cast<const double2 *>(xi) + r);
+                    const double2 v2 = __ldcg(reinterpret_cast<const double2 *>(xj) + r);
+                    const z64 u(u2.x, u2.y), v(v2.x, v2.y);
                     xi[r] = c * u - sem * v;
                     xj[r] = sep * u + c * v;
-                    z64 vu = V[(int64_t)i * s + r], vv = V[(int64_t)j * s + r];
-                    V[(int64_t)i * s + r] = c * vu - sem * vv;
-                    V[(int64_t)j * s + r] = sep * vu + c * vv;
+                    const double2 p2 = __ldcg(reinterpret_cast<const double2 *>(vi) + r);
+                    const double2 q2 = __ldcg(reinterpret_cast<const double2 *>(vj) + r);
+                    const z64 vu(p2.x, p2.y), vv(q2.x, q2.y);
+                    vi[r] = c * vu - sem * vv;
+                    vj[r] = sep * vu + c * vv;
                 }
             }
-            __syncthreads();
+            ok = cl_sync(&cbar, phase++ & 1u, JS_CL, &s_abort, info + mat);
         }
-        __syncthreads();
-        if (!rotated) break;
-        __syncthreads();
+        if (!ok) break;
+        // has any CTA rotated in this sweep?  (flags to every CTA, then one synchronisation)
+        if (threadIdx.x < JS_CL) *cl.map_shared_rank(&rotflag[me], threadIdx.x) = rot_local;
+        if (!(ok = cl_sync(&cbar, phase++ & 1u, JS_CL, &s_abort, info + mat))) break;
+        int any = 0;
+        for (int r = 0; r < JS_CL; ++r) any |= rotflag[r];
+        if (!any) break;
     }
-    if (threadIdx.x == 0 && sweep >= 60) info[blockIdx.x] = 2;
-    for (int i = warp; i < s; i += nw) {
+    if (ok && me == 0 && threadIdx.x == 0 && sweep >= 60) info[mat] = 2;
+    for (int i = gw; i < s; i += ngw) {
         double al = 0;
-        for (int r = lane; r < s; r += 32) al += norm2(X[(int64_t)i * s + r]);
+        for (int r = lane; r < s; r += 32)
+            al += norm2d(__ldcg(reinterpret_cast<const double2 *>(X) + (int64_t)i * s + r));
         for (int o = 16; o > 0; o >>= 1) al += __shfl_xor_sync(0xffffffffu, al, o);
-        if (lane == 0) sig[(int64_t)blockIdx.x * s + i] = sqrt(al);
+        if (lane == 0) sig[(int64_t)mat * s + i] = sqrt(al);
     }
+    cl.sync();   // no CTA leaves while another may still write into its shared memory
 }
 
 // ------------------------------------------------- Gauss-Jordan inverse
@@ -539,7 +601,7 @@ void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info,
     // rotation threshold: a few units of round-off in the column dot products
     {
         ProfScope ps_("k_jacobi_svd", st);
-        k_jacobi_svd<<<nb, 256, 0, st>>>(s, X, V, sig, d_info, 1e-15 * (s > 8 ? s : 8));
+        k_jacobi_svd<<<nb * JS_CL, 256, 0, st>>>(s, X, V, sig, d_info, 1e-15 * (s > 8 ? s : 8));
         launched("k_jacobi_svd");
     }
 }
