@@ -357,9 +357,9 @@ __global__ void __cluster_dims__(JS_CL, 1, 1) __launch_bounds__(256)
 }
 
 // ------------------------------------------------- Gauss-Jordan inverse
-// In-place Gauss-Jordan ("sweep") with row interchanges, one launch per pivot
-// k and ping-pong buffers (no grid-wide wait).  With O the matrix after
-// swapping rows k and p, pinv = 1 / O[k][k], f_i = O[i][k] pinv:
+// In-place Gauss-Jordan ("sweep") with row interchanges and ping-pong
+// buffers.  With O the matrix after swapping rows k and p, pinv = 1 / O[k][k],
+// f_i = O[i][k] pinv:
 //   new[i][j] = O[i][j] - f_i O[k][j]   (i != k, j != k)
 //   new[i][k] = -f_i,  new[k][j] = O[k][j] pinv,  new[k][k] = pinv.
 // After n sweeps the matrix is the inverse of the row-permuted input; undoing
@@ -412,71 +412,127 @@ __global__ void __launch_bounds__(256) k_gj_init(int n, const z64 *__restrict__ 
     gj_push_key(key, &keys[0]);
 }
 
-// 16 x 16 threads, each 2 rows x 2 columns of a 32 x 32 tile
-__global__ void __launch_bounds__(256) k_gj_sweep(int n, int k, const z64 *__restrict__ Ain, z64 *__restrict__ Aout,
-                                                  unsigned long long *__restrict__ keys, int *__restrict__ pivrow,
-                                                  int *__restrict__ info) {
-    // matrix blockIdx.z of the batch
-    Ain += (int64_t)blockIdx.z * n * n;
-    Aout += (int64_t)blockIdx.z * n * n;
-    keys += (int64_t)blockIdx.z * n;
-    pivrow += (int64_t)blockIdx.z * n;
-    __shared__ z64 s_pinv;
-    __shared__ int s_p;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const unsigned long long key = keys[k];
-        int p = k;
-        z64 pinv(0, 0);
-        if (key == 0ull) {
-            if (blockIdx.x == 0 && blockIdx.y == 0) info[0] = 1;   // no non-zero pivot in column k
-        } else {
-            p = (int)(GJ_IMASK - (key & GJ_IMASK));
-            pinv = cdiv(z64(1, 0), Ain[(int64_t)p * n + k]);
-        }
-        if (blockIdx.x == 0 && blockIdx.y == 0) pivrow[k] = p;
-        s_p = p;
-        s_pinv = pinv;
-    }
+// All n sweeps in one cooperative launch: persistent CTAs stride over the
+// 32 x 32 tiles of every matrix of the batch and meet at a grid barrier after
+// each sweep (a counter and a generation word in global memory; the wait gives
+// up after one second, sets *err and ends the kernel).  The ping-pong buffers
+// and the pivot keys are written by other SMs, so they are read through L2
+// only.  16 x 16 threads per CTA, each 2 rows x 2 columns of a 32 x 32 tile.
+constexpr int GJ_MAXB = 4;   // matrices per batch (pivot data cached per CTA)
+
+__device__ __forceinline__ bool gj_grid_sync(unsigned *cnt, unsigned *gen, unsigned nblocks, unsigned &g, int *abort_flag,
+                                             int *err) {
     __syncthreads();
-    const int p = s_p;
-    const z64 pinv = s_pinv;
-    const int j0 = blockIdx.x * 32 + threadIdx.x, i0 = blockIdx.y * 32 + threadIdx.y;
-    z64 r[2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const int j = j0 + 16 * c;
-        r[c] = j < n ? Ain[(int64_t)p * n + j] : z64(0, 0);   // O[k][j]
-    }
-    unsigned long long key = 0;
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr) {
-        const int i = i0 + 16 * rr;
-        if (i >= n) continue;
-        z64 *out = Aout + (int64_t)i * n;
-        if (i == k) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int j = j0 + 16 * c;
-                if (j < n) out[j] = j == k ? pinv : r[c] * pinv;
-            }
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();   // this CTA's writes before the arrival
+        const unsigned my = g;
+        if (atomicAdd(cnt, 1u) == nblocks - 1) {
+            atomicExch(cnt, 0u);
+            __threadfence();
+            atomicExch(gen, my + 1);
         } else {
-            const int src = i == p ? k : i;
-            const z64 *in = Ain + (int64_t)src * n;
-            const z64 f = in[k] * pinv;
+            uint64_t t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            while (atomicAdd(gen, 0u) == my) {
+                uint64_t t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                if (t - t0 > 1000000000ull) {
+                    *abort_flag = 1;
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        __threadfence();   // the others' writes after it
+    }
+    ++g;
+    __syncthreads();
+    return *(volatile int *)abort_flag == 0;
+}
+
+__global__ void __launch_bounds__(256) k_gj_persistent(int n, int nbatch, z64 *__restrict__ b0, z64 *__restrict__ b1,
+                                                       unsigned long long *__restrict__ keys,
+                                                       int *__restrict__ pivrow, int *__restrict__ info,
+                                                       unsigned *__restrict__ bar, int *__restrict__ err) {
+    __shared__ z64 s_pinv[GJ_MAXB];
+    __shared__ int s_p[GJ_MAXB];
+    __shared__ int s_abort;
+    const int tn = (n + 31) / 32;
+    const int64_t nn = (int64_t)n * n;
+    const int ntiles = nbatch * tn * tn;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_abort = 0;
+    unsigned g = 0;
+    for (int k = 0; k < n; ++k) {
+        const z64 *Ain = (k & 1) ? b1 : b0;
+        z64 *Aout = (k & 1) ? b0 : b1;
+        if (threadIdx.y == 0 && threadIdx.x < nbatch) {   // pivot of column k of every matrix
+            const int mb = threadIdx.x;
+            const unsigned long long key = __ldcg(keys + (int64_t)mb * n + k);
+            int p = k;
+            z64 pinv(0, 0);
+            if (key == 0ull) {
+                if (blockIdx.x == 0) info[0] = 1;   // no non-zero pivot in column k
+            } else {
+                p = (int)(GJ_IMASK - (key & GJ_IMASK));
+                const double2 v = __ldcg(reinterpret_cast<const double2 *>(Ain + mb * nn) + (int64_t)p * n + k);
+                pinv = cdiv(z64(1, 0), z64(v.x, v.y));
+            }
+            if (blockIdx.x == 0) pivrow[(int64_t)mb * n + k] = p;
+            s_p[mb] = p;
+            s_pinv[mb] = pinv;
+        }
+        __syncthreads();
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int mb = tile / (tn * tn), rem = tile - mb * tn * tn, by = rem / tn, bx = rem - by * tn;
+            const z64 *A = Ain + mb * nn;
+            z64 *O = Aout + mb * nn;
+            const int p = s_p[mb];
+            const z64 pinv = s_pinv[mb];
+            const int j0 = bx * 32 + threadIdx.x, i0 = by * 32 + threadIdx.y;
+            z64 r[2];
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int j = j0 + 16 * c;
-                if (j >= n) continue;
-                const z64 v = j == k ? -f : in[j] - f * r[c];
-                out[j] = v;
-                if (j == k + 1 && i > k) {
-                    const unsigned long long kk = gj_key(norm2(v), i);
-                    key = kk > key ? kk : key;
+                const double2 v = j < n ? __ldcg(reinterpret_cast<const double2 *>(A) + (int64_t)p * n + j)
+                                        : make_double2(0.0, 0.0);
+                r[c] = z64(v.x, v.y);   // O[k][j]
+            }
+            unsigned long long key = 0;
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const int i = i0 + 16 * rr;
+                if (i >= n) continue;
+                z64 *out = O + (int64_t)i * n;
+                if (i == k) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int j = j0 + 16 * c;
+                        if (j < n) out[j] = j == k ? pinv : r[c] * pinv;
+                    }
+                } else {
+                    const int src = i == p ? k : i;
+                    const double2 *in = reinterpret_cast<const double2 *>(A + (int64_t)src * n);
+                    const double2 fk = __ldcg(in + k);
+                    const z64 f = z64(fk.x, fk.y) * pinv;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int j = j0 + 16 * c;
+                        if (j >= n) continue;
+                        const double2 a = __ldcg(in + j);
+                        const z64 v = j == k ? -f : z64(a.x, a.y) - f * r[c];
+                        out[j] = v;
+                        if (j == k + 1 && i > k) {
+                            const unsigned long long kk = gj_key(norm2(v), i);
+                            key = kk > key ? kk : key;
+                        }
+                    }
                 }
             }
+            if (k + 1 < n && (k + 1) / 32 == bx) gj_push_key(key, keys + (int64_t)mb * n + k + 1);
         }
+        if (!gj_grid_sync(bar, bar + 1, gridDim.x, g, &s_abort, err)) return;
     }
-    if (k + 1 < n && (k + 1) / 32 == (int)blockIdx.x) gj_push_key(key, &keys[k + 1]);
 }
 
 // column order of the result: undo the interchanges, last first (one thread)
@@ -626,14 +682,32 @@ void gauss_jordan_inverse(int64_t n, int nbatch, z64 *Aug, z64 *inv, int *d_info
         k_gj_init<<<dim3(nb, nbatch), 256, 0, st>>>((int)n, inv, b0, keys.p);
         launched("k_gj_init");
     }
-    const dim3 g((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)nbatch), blk(16, 16);
-    for (int64_t k = 0; k < n; ++k) {
-        {
-            ProfScope ps_("k_gj_sweep", st);
-            k_gj_sweep<<<g, blk, 0, st>>>((int)n, (int)k, b0, b1, keys.p, pivrow.p, d_info);
-            launched("k_gj_sweep");
-        }
-        std::swap(b0, b1);
+    CBFM_REQUIRE(nbatch <= GJ_MAXB, "Gauss-Jordan: at most 4 matrices per batch");
+    DevBuf<unsigned> bar;
+    DevBuf<int> err;
+    bar.alloc(2);
+    err.alloc(1);
+    CBFM_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+    CBFM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    int dev = 0, nsm = 0, occ = 0;
+    CBFM_CUDA(cudaGetDevice(&dev));
+    CBFM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gj_persistent, 256, 0));
+    const int tiles = nbatch * (int)(((n + 31) / 32) * ((n + 31) / 32));
+    const unsigned grid = (unsigned)std::max(1, std::min(tiles, std::max(1, occ) * nsm));
+    {
+        int ni = (int)n;
+        void *args[] = {&ni, &nbatch, &b0, &b1, &keys.p, &pivrow.p, &d_info, &bar.p, &err.p};
+        ProfScope ps_("k_gj_sweep", st);
+        CBFM_CUDA(cudaLaunchCooperativeKernel((const void *)k_gj_persistent, dim3(grid), dim3(16, 16), args, 0, st));
+        launched("k_gj_sweep");
+    }
+    if (n & 1) std::swap(b0, b1);   // the last sweep wrote b1 when n is odd
+    {
+        int herr = 0;
+        CBFM_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        if (herr) throw Fail{CBFM_ETIMEOUT, "Gauss-Jordan: a grid barrier wait expired"};
     }
     prof_add_work("k_gj_sweep", 8.0 * nbatch * (double)n * n * n, 32.0 * nbatch * (double)n * n * n);
     k_gj_perm<<<nbatch, 32, 0, st>>>((int)n, pivrow.p, src.p);
