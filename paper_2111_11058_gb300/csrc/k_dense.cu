@@ -150,31 +150,31 @@ __global__ void __launch_bounds__(256) k_lu_solve(const int64_t *__restrict__ zo
     __shared__ int sidx[256];
     __shared__ int piv;
     __shared__ z64 pinv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = 0; k < n; ++k) {
-        // pivot search
-        double best = -1.0;
-        int bi = k;
-        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-            double v = norm2(Z[(int64_t)i * n + k]);
-            if (v > best) { best = v; bi = i; }
-        }
-        sval[threadIdx.x] = best;
-        sidx[threadIdx.x] = bi;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) {
-                double o = sval[threadIdx.x + w];
-                int oi = sidx[threadIdx.x + w];
-                if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
-                    sval[threadIdx.x] = o;
-                    sidx[threadIdx.x] = oi;
+        // pivot search by warp 0: largest |Z[i][k]|^2 (first on ties), bit patterns compared as integers
+        if (warp == 0) {
+            long long best = -1;
+            int bi = k;
+            for (int i = k + lane; i < n; i += 32) {
+                const long long v = __double_as_longlong(norm2(Z[(int64_t)i * n + k]));
+                if (v > best) {
+                    best = v;
+                    bi = i;
                 }
             }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            piv = sidx[0];
-            if (sval[0] <= 0.0) info[b] = 1;
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) {
+                    best = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                piv = bi;
+                if (best <= 0) info[b] = 1;
+            }
         }
         __syncthreads();
         const int p = piv;
@@ -196,13 +196,16 @@ __global__ void __launch_bounds__(256) k_lu_solve(const int64_t *__restrict__ zo
             pinv = (norm2(d) > 0.0) ? cdiv(z64(1, 0), d) : z64(0, 0);
         }
         __syncthreads();
+        // multipliers once per row, kept in column k
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) Z[(int64_t)i * n + k] = Z[(int64_t)i * n + k] * pinv;
+        __syncthreads();
         // eliminate below
         const int rows = n - k - 1;
         const int wcols = (n - k - 1) + s;
         for (int64_t idx = threadIdx.x; idx < (int64_t)rows * wcols; idx += blockDim.x) {
             int i = k + 1 + (int)(idx / wcols);
             int c = (int)(idx % wcols);
-            z64 l = Z[(int64_t)i * n + k] * pinv;
+            const z64 l = Z[(int64_t)i * n + k];
             if (c < n - k - 1) {
                 int j = k + 1 + c;
                 Z[(int64_t)i * n + j] -= l * Z[(int64_t)k * n + j];
@@ -215,8 +218,12 @@ __global__ void __launch_bounds__(256) k_lu_solve(const int64_t *__restrict__ zo
     }
     // backward substitution, column oriented
     for (int k = n - 1; k >= 0; --k) {
-        z64 d = Z[(int64_t)k * n + k];
-        z64 dinv = (norm2(d) > 0.0) ? cdiv(z64(1, 0), d) : z64(0, 0);
+        if (threadIdx.x == 0) {
+            const z64 d = Z[(int64_t)k * n + k];
+            pinv = (norm2(d) > 0.0) ? cdiv(z64(1, 0), d) : z64(0, 0);
+        }
+        __syncthreads();
+        const z64 dinv = pinv;
         for (int j = threadIdx.x; j < s; j += blockDim.x) V[(int64_t)k * s + j] = V[(int64_t)k * s + j] * dinv;
         __syncthreads();
         for (int64_t idx = threadIdx.x; idx < (int64_t)k * s; idx += blockDim.x) {
