@@ -306,3 +306,30 @@ def test_block_restart_small_basis(P, c1):
     a = P.solve(red, c1["exc"], tol=1e-9, solver=P.PER_RHS)
     b = P.solve(red, c1["exc"], tol=1e-9, solver=P.BLOCK, restart=180, maxit=2000)
     assert np.linalg.norm(a.j - b.j) / np.linalg.norm(a.j) < 1e-6
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_solve_odd_half_order_injected_cbfs(P, solver):
+    """A reduced system whose halves have odd order (n_h = 15) runs the
+    Gauss-Jordan inverse of G^CBF over an odd number of ping-pong sweeps;
+    both GMRES variants must reach the oracle's solution (GMRES with the
+    Gram matrix applied by an LU solve) on a lossy medium."""
+    g = W.icosphere(1, 0.4)
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = OM.cells_rcb(m, 3)
+    Ns = np.bincount(cell)
+    Ls = [5, 4, 6]
+    CM, CJ = W.random_cbfs(Ns, Ls, seed=21)
+    cbfs = [OC.CellCBF(np.nonzero(cell == c)[0], CM[c], CJ[c], np.ones(1), Ls[c]) for c in range(3)]
+    eps = 3.0 - 0.1j
+    A, CJM, CMJ = OC.reduced_system(m, cbfs, eps)
+    G = OC.cbf_gram(m, cbfs)
+    exc = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, 0.5], [2.2, 5.0, 1.3]])
+    b = CJM.conj().T @ OMo.rhs(m, exc)
+    ref = OC.solve_reduced(A, G, CMJ, b, 1e-12, restart=200, maxit=400)
+    gm = P.mesh(g.verts, g.tris, 3, eps, partition="rcb")
+    red = P.assemble_reduced(gm, P.cbf_import(gm, CM, CJ), P.FP64)
+    assert red.n == 30
+    P.cmp_setup(red)
+    res = P.solve(red, exc, tol=1e-12, maxit=400, solver=solver)
+    assert np.linalg.norm(res.j - ref.j) / np.linalg.norm(ref.j) < 1e-8
