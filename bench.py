@@ -129,6 +129,22 @@ def roofline(name, rec, peaks, peak_src):
     return out
 
 
+def max_over_ranks(x: float, device: str = "cuda") -> float:
+    """The largest x over all ranks: the slowest replica sets the whole job's step time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, n_rhs: int, t_max_ms: float) -> float:
+    """Whole-job throughput: every one of the ws replicas solves n_rhs right-hand sides per step."""
+    return ws * n_rhs / (t_max_ms / 1000.0)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -470,19 +486,15 @@ def main():
         ts = timed(args.steps, step)
     launches = (P.launch_count() - l0) // max(1, args.steps)
     t_step = float(np.mean(ts))
-    t_max = t_step
-    if ws > 1:
-        tt = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * N_RHS / (t_max / 1000.0)
+    t_max = max_over_ranks(t_step, "cuda")
+    value = job_value(ws, N_RHS, t_max)
 
     # end to end through the public API with pinned host buffers
     exc_h = torch.tensor(d["exc"], dtype=torch.float64).pin_memory()
     rcs_h = torch.zeros((N_RHS, 1, 2), dtype=torch.float64).pin_memory()
     step_host = make_step(P.MIXED, rcs_h.numpy(), solver, exc=exc_h.numpy())
     ts_e2e = timed(max(1, min(args.steps, 3)), step_host)
-    e2e = ws * N_RHS / (float(np.mean(ts_e2e)) / 1000.0)
+    e2e = job_value(ws, N_RHS, max_over_ranks(float(np.mean(ts_e2e)), "cuda"))
 
     # per-kernel profile of the same steps (CUDA events on the launching stream)
     P.profile(True)
