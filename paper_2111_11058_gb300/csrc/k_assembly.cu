@@ -668,7 +668,7 @@ __device__ __forceinline__ bool share_cell(const int32_t *__restrict__ tc, int t
 // strip of blockDim.x trial triangles) from an atomic counter, so meshes of
 // uneven size share the GPU without a tail per mesh.
 template <typename T>
-__global__ void __launch_bounds__(128) k_far(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t ntasks,
+__global__ void __launch_bounds__(128, 3) k_far(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t ntasks,
                                                    unsigned long long *__restrict__ counter) {
     __shared__ FarShared<T> S;
     __shared__ int64_t s_task;
