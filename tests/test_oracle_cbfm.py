@@ -10,6 +10,9 @@ Paper-given facts used as pins:
 * G^CBF is diagonal when no connected boundary is divided (Sec. III-C);
 * CMP needs far fewer GMRES iterations than the unpreconditioned system;
 * the single-cell CBFM with L = 70 reproduces the MoM RCS closely (Sec. IV-A).
+
+The printed values (Table I's wave grid; the group sizes, L = 70, N^CBF = 140 and
+N = 960 of Sec. IV-A-1) live in tests/golden/ with their citations.
 """
 import math
 
@@ -17,12 +20,15 @@ import numpy as np
 import pytest
 
 import workloads as W
+from conftest import golden
 from oracle import cbfm, mesh as OM, mom
 
 
 def _table1_waves():
-    th = np.deg2rad(np.arange(12) * 30.0)
-    ph = np.deg2rad(np.arange(6) * 30.0)
+    t = golden("sphere_table1_waves")
+    th = np.deg2rad(t["theta_start_deg"] + np.arange(t["n_theta"]) * t["theta_step_deg"])
+    ph = np.deg2rad(t["phi_start_deg"] + np.arange(t["n_phi"]) * t["phi_step_deg"])
+    assert t["polarisations"] == ["theta", "phi"]
     return W.plane_wave_set(np.array([(a, b) for a in th for b in ph]))
 
 
@@ -33,23 +39,29 @@ def small_sphere():
 
 
 def test_unknown_count(small_sphere):
-    assert 2 * small_sphere.ne == 960
+    assert 2 * small_sphere.ne == golden("sphere_singular_value_groups")["unknowns"]
 
 
 @pytest.mark.parametrize("eps", [1.0, 4.0])
 def test_singular_value_groups(small_sphere, eps):
     m = small_sphere
-    cb = cbfm.primary_cbfs(m, np.zeros(m.ne, np.int32), 1, eps, _table1_waves(), 1e-3, Lmax=70)
+    gv = golden("sphere_singular_value_groups")
+    assert gv["group_ends"] == np.cumsum(gv["group_sizes"]).tolist()
+    assert gv["group_sizes"] == [2 * (2 * l + 1) for l in range(1, 6)]
+    assert gv["n_cbf"] == 2 * gv["kept_singular_values"]
+    kept = gv["kept_singular_values"]
+    cb = cbfm.primary_cbfs(m, np.zeros(m.ne, np.int32), 1, eps, _table1_waves(), 1e-3, Lmax=kept)
     s = cb[0].sigma / cb[0].sigma[0]
-    gaps = s[:71] / s[1:72]
+    gaps = s[:kept + 1] / s[1:kept + 2]
     top5 = sorted((np.argsort(-gaps)[:5] + 1).tolist())
-    assert top5 == [6, 16, 30, 48, 70]
+    assert top5 == gv["group_ends"]
 
 
 def test_duality_and_single_cell_accuracy(small_sphere):
     m = small_sphere
     exc = np.array([[0.0, 0.0, 0.0], [0.7, 0.3, 0.5]])
-    R = cbfm.run(m, np.zeros(m.ne, np.int32), 1, 3.0, _table1_waves(), exc, 1e-3, 1e-8, Lmax=70)
+    R = cbfm.run(m, np.zeros(m.ne, np.int32), 1, 3.0, _table1_waves(), exc, 1e-3, 1e-8,
+                  Lmax=golden("sphere_singular_value_groups")["kept_singular_values"])
     c = R["cbfs"][0]
     Gm = cbfm.rwg_gram(m, c.edges, c.edges)
     D = c.CM.conj().T @ Gm @ c.CJ
@@ -90,7 +102,8 @@ def test_disjoint_cells_diagonal_gram_and_identical_sigma():
 def test_cmp_reduces_iterations(small_sphere, eps):
     m = small_sphere
     R = cbfm.run(m, np.zeros(m.ne, np.int32), 1, eps, _table1_waves(), np.array([[0.0, 0.0, 0.0]]),
-                 1e-3, 1e-6, restart=1000, Lmax=70)
+                 1e-3, 1e-6, restart=1000,
+                 Lmax=golden("sphere_singular_value_groups")["kept_singular_values"])
     nocmp = cbfm.solve_reduced(R["A"], R["G"], R["CMJ"], R["b"], 1e-6, restart=1000, use_cmp=False)
     assert R["sol"].iters[0] <= 0.6 * nocmp.iters[0]
     # both reach the same solution of A x = b
