@@ -41,26 +41,40 @@ constexpr int PCHOL_THREADS = 256;
 // factorisation (rank).
 //
 // It runs on a cluster of PC_CL CTAs (one per SM).  CTA c owns the rows of
-// original index a = c + PC_CL l of the Schur complement, stored in full in
-// its shared memory.  Step i: every CTA proposes its largest remaining
-// diagonal (lowest position on ties; without pivoting only the owner of
-// position i proposes) and writes that row, unscaled, with the diagonal and
-// its inverse square root into the shared memory of every CTA of the
-// cluster; after one cluster-wide synchronisation all CTAs pick the same
+// original index a = c + PC_CL l of the Schur complement U, stored in full in
+// its shared memory.  For step i every CTA has proposed a candidate (its
+// largest remaining diagonal, lowest position on ties; without pivoting only
+// the owner of position i proposes) by writing that row, unscaled, with its
+// diagonal, 1 / sqrt(diagonal), position and index into the shared memory of
+// every CTA.  After the synchronisation of step i all CTAs pick the same
 // winner q, CTA 0 writes row i of R (by original index; permuted to positions
-// after the loop), and each CTA updates its own rows only,
-//   U(a, b) -= conj(U(q, a)) U(q, b) / U(q, q).
-// The FP64 work of the updates is spread over the cluster's SMs.  The per-step
-// synchronisation is an mbarrier that every CTA arrives on remotely; its wait
-// gives up after one second (error flag, loop ends).  Hardware cluster
-// barriers are used only where every CTA arrives unconditionally: after
-// set-up and before exit.
+// after the loop), and each CTA applies
+//   U(a, b) -= conj(U(q, a)) U(q, b) / U(q, q)
+// to its own rows.  The chain from one synchronisation to the next is kept
+// short: a CTA updates the diagonals of its rows, picks its candidate for
+// step i + 1, updates that row while sending it, arrives, and only then
+// updates the rest of its rows, overlapping the other CTAs' chains.  A CTA
+// can therefore write the proposals of step i + 2 while another still reads
+// those of step i: proposals rotate through three buffers.  The
+// synchronisation of step k is the mbarrier pair of cluster.cuh, arrived on
+// remotely by every CTA; its wait gives up after one second (error flag,
+// loop ends).  Hardware cluster barriers are used only where every CTA
+// arrives unconditionally: after set-up and before exit.
 namespace cg = cooperative_groups;
 constexpr int PC_CL = 8;
 constexpr int PC_ROWS = (PCHOL_MAX + PC_CL - 1) / PC_CL;
+constexpr int PC_NBUF = 3;
 
-// dynamic shared memory: own rows [PC_ROWS][m] and proposals [2][PC_CL][m]
-constexpr size_t pchol_cl_smem(int m) { return (size_t)(PC_ROWS + 2 * PC_CL) * m * sizeof(z64); }
+// dynamic shared memory: own rows [PC_ROWS][m] and proposals [PC_NBUF][PC_CL][m]
+constexpr size_t pchol_cl_smem(int m) { return (size_t)(PC_ROWS + PC_NBUF * PC_CL) * m * sizeof(z64); }
+
+// u -= c r
+__device__ __forceinline__ void pc_axpy(z64 &u, z64 c, z64 r) {
+    u.re = fma(-c.re, r.re, u.re);
+    u.re = fma(c.im, r.im, u.re);
+    u.im = fma(-c.re, r.im, u.im);
+    u.im = fma(-c.im, r.re, u.im);
+}
 
 __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
     k_pchol_cl(int m, const z64 *__restrict__ M, int *__restrict__ perm, z64 *__restrict__ R,
@@ -69,14 +83,16 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
     const int me = (int)cl.block_rank();
     extern __shared__ __align__(16) unsigned char pc_raw[];
     z64 *Uloc = reinterpret_cast<z64 *>(pc_raw);   // [PC_ROWS][m]
-    z64 *crow = Uloc + (size_t)PC_ROWS * m;        // [2][PC_CL][m], by original index
-    __shared__ uint64_t cbar;
-    __shared__ double cval[2][PC_CL], crd[2][PC_CL];   // proposal: diagonal, 1 / sqrt(diagonal)
-    __shared__ int cpos[2][PC_CL];
-    __shared__ z64 s_coef[PC_ROWS];                     // conj(U(q, a)) / U(q, q) per own row
+    z64 *crow = Uloc + (size_t)PC_ROWS * m;        // [PC_NBUF][PC_CL][m], by original index
+    __shared__ uint64_t cbar[2];
+    __shared__ double cval[PC_NBUF][PC_CL], crd[PC_NBUF][PC_CL];   // proposal: diagonal, 1 / sqrt(diagonal)
+    __shared__ int cpos[PC_NBUF][PC_CL], cidx[PC_NBUF][PC_CL];     // proposal: position, original index
+    __shared__ z64 s_coef[PC_ROWS];                                 // conj(U(q, a)) / U(q, q) per own row
+    __shared__ int s_alive[PC_ROWS];                                // own row not yet eliminated
     __shared__ int piv[PCHOL_MAX], posof[PCHOL_MAX];
-    __shared__ int s_abort, s_rank, s_ls, s_stop;
-    __shared__ double s_thr, s_d, s_rd;
+    __shared__ int s_abort, s_stop, s_cand, s_cpos;
+    __shared__ double s_cd, s_crd;
+    __shared__ double s_thr;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nth = blockDim.x;
     const int nloc = me < m ? (m - me + PC_CL - 1) / PC_CL : 0;
     for (int idx = threadIdx.x; idx < nloc * m; idx += nth) {
@@ -88,6 +104,7 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
         piv[k] = k;
         posof[k] = k;
     }
+    if (threadIdx.x < nloc) s_alive[threadIdx.x] = 1;
     if (warp == 0) {
         double mx = 0.0;
         for (int k = lane; k < m; k += 32) mx = fmax(mx, M[(int64_t)k * m + k].re);
@@ -95,87 +112,106 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
         if (lane == 0) {
             s_thr = tol * mx;
             s_abort = 0;
-            s_rank = m;
             s_stop = m;
-            cl_bar_init(&cbar, PC_CL);
+            cl_bar_init(cbar, PC_CL);
         }
     }
     __syncthreads();
-    cl.sync();   // every CTA's barrier is initialised before the first remote arrive
+    cl.sync();   // every CTA's barriers are initialised before the first remote arrive
     const double thr = s_thr;
-    for (int i = 0; i < m; ++i) {
-        const int par = i & 1;
-        // ---- this CTA's proposal: its largest remaining diagonal and that row, unscaled
-        if (warp == 0) {
-            long long best = LLONG_MIN;
-            int bp = INT_MAX, bls = -1;
-            for (int ls = lane; ls < nloc; ls += 32) {
-                const int a = me + PC_CL * ls, pa = posof[a];
-                if (pa < i || (!pivot && pa != i)) continue;
-                const long long v = __double_as_longlong(Uloc[ls * m + a].re);   // orders positive doubles
-                if (bls < 0 || v > best || (v == best && pa < bp)) {
-                    best = v;
-                    bp = pa;
-                    bls = ls;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
-                const int op = __shfl_xor_sync(0xffffffffu, bp, o), ol = __shfl_xor_sync(0xffffffffu, bls, o);
-                if (ol >= 0 && (bls < 0 || ov > best || (ov == best && op < bp))) {
-                    best = ov;
-                    bp = op;
-                    bls = ol;
-                }
-            }
-            if (lane == 0) {
-                s_ls = bls;
-                s_rank = bp;   // position of the proposal (scratch until the loop ends)
-                s_d = bls >= 0 ? __longlong_as_double(best) : -1.0;
-            }
-        }
-        __syncthreads();
-        const int pls = s_ls;
-        if (pls >= 0) {
-            // raw row to every CTA; meanwhile lane 0 of warp 0 forms 1 / sqrt(diagonal)
+
+    // warp 0: this CTA's candidate for step i (diagonals up to date)
+    auto pick = [&](int i) {
+        if (!pivot) {   // no row exchanges: position i is row i, owned by CTA i % PC_CL
             if (threadIdx.x == 0) {
-                const double val = s_d;
-                s_rd = val > 0.0 ? 1.0 / sqrt(val) : 0.0;
+                const int ls = (i % PC_CL == me) ? i / PC_CL : -1;
+                const double d = ls >= 0 ? Uloc[ls * m + i].re : -1.0;
+                s_cand = ls;
+                s_cpos = ls >= 0 ? i : INT_MAX;
+                s_cd = d;
+                s_crd = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
             }
-            for (int idx = threadIdx.x; idx < PC_CL * m; idx += nth) {
-                const int r = idx / m, b = idx - r * m;
-                *cl.map_shared_rank(crow + ((size_t)par * PC_CL + me) * m + b, r) = Uloc[pls * m + b];
+            return;
+        }
+        if (warp != 0) return;
+        long long best = LLONG_MIN;
+        int bp = INT_MAX, bls = -1;
+        for (int ls = lane; ls < nloc; ls += 32) {
+            const int a = me + PC_CL * ls, pa = posof[a];
+            if (pa < i || (!pivot && pa != i)) continue;
+            const long long v = __double_as_longlong(Uloc[ls * m + a].re);   // orders positive doubles
+            if (bls < 0 || v > best || (v == best && pa < bp)) {
+                best = v;
+                bp = pa;
+                bls = ls;
             }
         }
-        __syncthreads();
-        if (threadIdx.x < PC_CL) {   // the scalars of the proposal, one CTA per lane
-            const int r = threadIdx.x;
-            *cl.map_shared_rank(&cval[par][me], r) = pls >= 0 ? s_d : -1.0;
-            *cl.map_shared_rank(&crd[par][me], r) = pls >= 0 ? s_rd : 0.0;
-            *cl.map_shared_rank(&cpos[par][me], r) = pls >= 0 ? s_rank : INT_MAX;
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int op = __shfl_xor_sync(0xffffffffu, bp, o), ol = __shfl_xor_sync(0xffffffffu, bls, o);
+            if (ol >= 0 && (bls < 0 || ov > best || (ov == best && op < bp))) {
+                best = ov;
+                bp = op;
+                bls = ol;
+            }
         }
-        if (!cl_sync(&cbar, (uint32_t)par, PC_CL, &s_abort, err)) break;
+        if (lane == 0) {
+            const double d = bls >= 0 ? __longlong_as_double(best) : -1.0;
+            s_cand = bls;
+            s_cpos = bls >= 0 ? bp : INT_MAX;
+            s_cd = d;
+            s_crd = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+        }
+    };
+    // the candidate's scalars to buffer i % PC_NBUF of every CTA (one CTA per thread)
+    auto send_scalars = [&](int i) {
+        if (threadIdx.x < PC_CL) {
+            const int r = threadIdx.x, buf = i % PC_NBUF, cls = s_cand;
+            *cl.map_shared_rank(&cval[buf][me], r) = s_cd;
+            *cl.map_shared_rank(&crd[buf][me], r) = s_crd;
+            *cl.map_shared_rank(&cpos[buf][me], r) = s_cpos;
+            *cl.map_shared_rank(&cidx[buf][me], r) = cls >= 0 ? me + PC_CL * cls : -1;
+        }
+    };
+
+    // step 0: candidates from the initial diagonals
+    pick(0);
+    __syncthreads();
+    if (s_cand >= 0) {
+        z64 *dst = crow + (size_t)me * m;
+        for (int b = threadIdx.x; b < m; b += nth) {
+            const z64 v = Uloc[s_cand * m + b];
+            for (int r = 0; r < PC_CL; ++r) *cl.map_shared_rank(dst + b, r) = v;
+        }
+    }
+    send_scalars(0);
+    __syncthreads();
+    cl_arrive(cbar, 0, PC_CL);
+
+    for (int i = 0; i < m; ++i) {
+        if (!cl_wait(cbar, i, &s_abort, err)) break;
+        const int buf = i % PC_NBUF;
         // ---- the same decision in every CTA
         int w = -1, bpos = INT_MAX;
         long long bv = 0;
         for (int r = 0; r < PC_CL; ++r) {
-            const int pr = cpos[par][r];
+            const int pr = cpos[buf][r];
             if (pr == INT_MAX) continue;
-            const long long vb = __double_as_longlong(cval[par][r]);
+            const long long vb = __double_as_longlong(cval[buf][r]);
             if (w < 0 || vb > bv || (vb == bv && pr < bpos)) {
                 w = r;
                 bv = vb;
                 bpos = pr;
             }
         }
-        const double dq = w >= 0 ? cval[par][w] : -1.0;
+        const double dq = w >= 0 ? cval[buf][w] : -1.0;
         if (w < 0 || !(dq > thr) || dq <= 0.0) {
             if (threadIdx.x == 0) s_stop = i;
             break;
         }
-        const z64 *Ri = crow + ((size_t)par * PC_CL + w) * m;   // row q of the Schur complement, unscaled
-        const double rdq = crd[par][w];                         // 1 / sqrt(U(q, q))
-        __syncthreads();   // everyone has read the positions of step i - 1
+        const int q = cidx[buf][w];
+        const z64 *Ri = crow + ((size_t)buf * PC_CL + w) * m;   // row q of the Schur complement, unscaled
+        const double rdq = crd[buf][w];                         // 1 / sqrt(U(q, q))
         if (threadIdx.x == 0 && bpos != i) {
             const int t = piv[i];
             piv[i] = piv[bpos];
@@ -183,41 +219,55 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
             posof[piv[i]] = i;
             posof[piv[bpos]] = bpos;
         }
-        if (threadIdx.x < nloc) {   // per own row: conj(U(q, a)) / U(q, q)
-            const double inv = rdq * rdq;
-            s_coef[threadIdx.x] = conj(Ri[me + PC_CL * threadIdx.x]) * inv;
+        if (threadIdx.x < nloc) {   // own row: coefficient, and its diagonal at once
+            const int ls = threadIdx.x, a = me + PC_CL * ls;
+            if (a == q) s_alive[ls] = 0;
+            const z64 c = conj(Ri[a]) * (rdq * rdq);
+            s_coef[ls] = c;
+            if (s_alive[ls]) pc_axpy(Uloc[ls * m + a], c, Ri[a]);
         }
         __syncthreads();
         // row i of R = row q / sqrt(U(q, q)), by original index for now (permuted to positions after the loop)
         if (me == 0) {
-            const int q = piv[i];
             for (int b = threadIdx.x; b < m; b += nth)
                 R[(int64_t)i * m + b] = posof[b] < i ? z64(0, 0) : (b == q ? z64(dq * rdq, 0) : Ri[b] * rdq);
         }
-        // ---- rank-1 update of this CTA's remaining rows over the remaining positions:
-        // U(a, b) -= conj(U(q, a)) U(q, b) / U(q, q)
+        if (i + 1 >= m) break;
+        // ---- candidate for step i + 1: updated while it is sent, then the arrival
+        pick(i + 1);
+        __syncthreads();
+        const int cls = s_cand;
+        if (cls >= 0) {
+            const int a = me + PC_CL * cls;
+            const z64 c = s_coef[cls];
+            z64 *dst = crow + ((size_t)((i + 1) % PC_NBUF) * PC_CL + me) * m;
+            for (int b = threadIdx.x; b < m; b += nth) {
+                z64 v = Uloc[cls * m + b];
+                if (b != a && posof[b] > i) {
+                    pc_axpy(v, c, Ri[b]);
+                    Uloc[cls * m + b] = v;
+                }
+                for (int r = 0; r < PC_CL; ++r) *cl.map_shared_rank(dst + b, r) = v;
+            }
+        }
+        send_scalars(i + 1);
+        __syncthreads();
+        cl_arrive(cbar, i + 1, PC_CL);
+        // ---- the rest of this CTA's rows over the remaining positions (diagonals done)
         const int rem = m - i - 1;
         for (int idx = threadIdx.x; idx < nloc * rem; idx += nth) {
             const int ls = idx / rem, pos = i + 1 + (idx - ls * rem);
-            const int a = me + PC_CL * ls;
-            if (posof[a] <= i) continue;
-            const int b = piv[pos];
-            const z64 c = s_coef[ls], rb_ = Ri[b];
-            z64 u = Uloc[ls * m + b];
-            u.re = fma(-c.re, rb_.re, u.re);
-            u.re = fma(c.im, rb_.im, u.re);
-            u.im = fma(-c.re, rb_.im, u.im);
-            u.im = fma(-c.im, rb_.re, u.im);
-            Uloc[ls * m + b] = u;
+            if (ls == cls || !s_alive[ls]) continue;
+            const int b = piv[pos], a = me + PC_CL * ls;
+            if (b == a) continue;
+            pc_axpy(Uloc[ls * m + b], s_coef[ls], Ri[b]);
         }
         __syncthreads();
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_rank = s_stop;
-    __syncthreads();
     cl.sync();   // rows of R written by CTA 0 are visible to every CTA; no proposal is in flight any more
     // R[i][pos] = row i by original index at piv[pos] (rows distributed over the CTAs)
-    const int rk = s_rank;
+    const int rk = s_stop;
     for (int i = me; i < rk; i += PC_CL) {
         for (int b = threadIdx.x; b < m; b += nth) crow[b] = R[(int64_t)i * m + b];
         __syncthreads();
@@ -233,48 +283,44 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
 
 // Rinv = R11^{-1} for the leading r x r block of the upper-triangular Cholesky
 // factor R (r = *rank; row-major, ld m, real positive diagonal), zero
-// elsewhere in the m x m output.  One warp per column j, column-oriented back
-// substitution: x_k = b_k / R[k][k] for k = j .. 0, then b_i -= R[i][k] x_k
-// for the rows i < k still open (b = e_j at the start); lane owns rows
-// lane + 32 t.  On GB300 a warp-wide FP64 instruction occupies its SMSP's FP64
-// pipe for ~64 cycles, so the step is kept to one real-complex product and
-// the multiply-adds of the row groups that are still open; the reciprocal
-// diagonals are formed up front.  The columns run on separate SMs.
-__global__ void __launch_bounds__(32) k_trinv(int m, const z64 *__restrict__ R, const int *__restrict__ rank,
-                                              z64 *__restrict__ Rinv) {
-    constexpr int NT = PCHOL_MAX / 32;
-    const int j = blockIdx.x, lane = threadIdx.x;
+// elsewhere in the m x m output.  One CTA of PCHOL_MAX threads per column j,
+// thread t owning row t; column-oriented back substitution from b = e_j:
+// for k = j .. 0, x_k = b_k / R[k][k] (the owner publishes it), then
+// b_t -= R[t][k] x_k for the rows t < k.  The triangle R[0..j][0..j] is staged
+// in shared memory first (column k packed at k(k+1)/2), so a step is one
+// barrier, one shared-memory read and one complex multiply-add per row; the
+// rows of a step are spread over the four warps (four FP64 pipes).
+constexpr size_t trinv_smem(int m) { return (size_t)m * (m + 1) / 2 * sizeof(z64); }
+
+__global__ void __launch_bounds__(PCHOL_MAX) k_trinv(int m, const z64 *__restrict__ R, const int *__restrict__ rank,
+                                                     z64 *__restrict__ Rinv) {
+    extern __shared__ __align__(16) unsigned char ti_raw[];
+    z64 *Rs = reinterpret_cast<z64 *>(ti_raw);   // packed columns of the upper triangle
+    __shared__ double s_inv[PCHOL_MAX];
+    __shared__ z64 s_x[2];
+    const int j = blockIdx.x, t = threadIdx.x;
     const int r = *rank;
-    z64 b[NT];
-    double inv[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        const int i = lane + 32 * t;
-        b[t] = z64(i == j && j < r ? 1.0 : 0.0, 0.0);
-        inv[t] = i < r ? 1.0 / R[(int64_t)i * m + i].re : 0.0;
-    }
     if (j < r) {
-        for (int k = j; k >= 0; --k) {
-            const int tk = k >> 5, owner = k & 31;
-            z64 xk(0, 0);
-#pragma unroll
-            for (int t = 0; t < NT; ++t)
-                if (t == tk) xk = b[t] * inv[t];
-            xk.re = __shfl_sync(0xffffffffu, xk.re, owner);
-            xk.im = __shfl_sync(0xffffffffu, xk.im, owner);
-#pragma unroll
-            for (int t = 0; t < NT; ++t) {
-                if (32 * t > k) break;   // warp-uniform: rows of this group are all >= k
-                const int i = lane + 32 * t;
-                if (i == k) b[t] = xk;
-                else if (i < k) b[t] -= R[(int64_t)i * m + k] * xk;
-            }
+        // thread k loads column k: R[i][k], i <= k (consecutive threads, consecutive addresses)
+        if (t <= j) {
+            z64 *col = Rs + (size_t)t * (t + 1) / 2;
+#pragma unroll 8
+            for (int i = 0; i <= t; ++i) col[i] = R[(int64_t)i * m + t];
+            s_inv[t] = 1.0 / R[(int64_t)t * m + t].re;
         }
-    }
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        const int i = lane + 32 * t;
-        if (i < m) Rinv[(int64_t)i * m + j] = i <= j ? b[t] : z64(0, 0);
+        __syncthreads();
+        z64 b(t == j ? 1.0 : 0.0, 0.0);
+        for (int k = j; k >= 0; --k) {
+            if (t == k) {
+                b = b * s_inv[k];
+                s_x[k & 1] = b;
+            }
+            __syncthreads();   // x_k published; the slot of step k + 2 is free again
+            if (t < k) b -= Rs[(size_t)k * (k + 1) / 2 + t] * s_x[k & 1];
+        }
+        if (t < m) Rinv[(int64_t)t * m + j] = t <= j ? b : z64(0, 0);
+    } else {
+        if (t < m) Rinv[(int64_t)t * m + j] = z64(0, 0);
     }
 }
 
@@ -409,6 +455,8 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
     if (dev < 64 && !attr_set[dev].load(std::memory_order_acquire)) {
         CBFM_CUDA(cudaFuncSetAttribute(k_pchol_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)pchol_cl_smem(PCHOL_MAX)));
+        CBFM_CUDA(cudaFuncSetAttribute(k_trinv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)trinv_smem(PCHOL_MAX)));
         attr_set[dev].store(true, std::memory_order_release);
     }
     {
@@ -423,7 +471,7 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
     }
     {
         ProfScope ps_("k_trinv", c.st);
-        k_trinv<<<m, 32, 0, c.st>>>(m, c.R.p, c.rank.p, c.Rinv.p);
+        k_trinv<<<m, PCHOL_MAX, trinv_smem(m), c.st>>>(m, c.R.p, c.rank.p, c.Rinv.p);
         launched("k_trinv");
     }
     int hr[2] = {0, 0};
@@ -596,6 +644,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
         CBFM_CUDA(cudaMemsetAsync(Qh.p, 0, sizeof(z64) * dcap2 * dcap, st));
         CBFM_CUDA(cudaMemsetAsync(Rh.p, 0, sizeof(z64) * dcap * dcap, st));
         const int p1 = cholqr2_rows(c, tmp.p, p, n, V.p, E1S.p, rank_tol, 0.0, drop_tol);
+        CBFM_CUDA(cudaMemcpyAsync(Rv.p, E1S.p, sizeof(z64) * dcap2 * p, cudaMemcpyDeviceToDevice, st));
         if (p1 == 0) {   // residual block is zero: current iterate is exact
             for (int r = 0; r < p; ++r) {
                 out.resid[r] = 0.0;
@@ -637,13 +686,24 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
                 k_copy2d<<<nb(rr * pjc), 256, 0, st>>>(rr, pjc, Rw.p, pjc, Hn.p + d1 * p, p, 0);
                 launched("k_copy2d");
             }
-            // QR update of Hbar: project the new column block on the previous Q (twice)
+            // QR update of Hbar: project the new column block on the previous Q (twice).
+            // Hbar is block upper Hessenberg, so column block i of its Q is zero
+            // below row dims[i+2]: block i is projected over those rows only, and
+            // row block r of the new column meets only the Q blocks i >= r - 1.
             if (d0 > 0) {
+                std::vector<GemmDesc> proj, upd;
+                for (int i = 0; i < J; ++i)
+                    proj.push_back(GemmDesc{dims[i + 1] - dims[i], pjc, dims[i + 2], dims[i], dcap, 0, p,
+                                            dims[i] * p, p});
+                for (int r = 0; r <= J; ++r) {
+                    const int64_t k0 = dims[std::max(0, r - 1)];
+                    if (k0 >= d0) continue;
+                    upd.push_back(GemmDesc{dims[r + 1] - dims[r], pjc, d0 - k0, dims[r] * dcap + k0, dcap, k0 * p,
+                                           p, dims[r] * p, p});
+                }
                 for (int pass = 0; pass < 2; ++pass) {
-                    gemm_grouped<double>({GemmDesc{d0, pjc, d2, 0, dcap, 0, p, 0, p}}, 2, 0, Qh.p, Hn.p, tmp2.p, false,
-                                         st);
-                    gemm_grouped<double>({GemmDesc{d2, pjc, d0, 0, dcap, 0, p, 0, p}}, 0, 0, Qh.p, tmp2.p, Hn.p, true,
-                                         st, -1.0);
+                    gemm_grouped<double>(proj, 2, 0, Qh.p, Hn.p, tmp2.p, false, st);
+                    gemm_grouped<double>(upd, 0, 0, Qh.p, tmp2.p, Hn.p, true, st, -1.0);
                     k_copy2d<<<nb(d0 * pjc), 256, 0, st>>>((int)d0, pjc, tmp2.p, p, Rh.p + d0, dcap, pass);
                     launched("k_copy2d");
                 }
@@ -653,10 +713,12 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             launched("k_copy2d");
             k_copy2d<<<nb(pjc * pjc), 256, 0, st>>>(pjc, pjc, Rout.p, p, Rh.p + d0 * dcap + d0, dcap, 0);
             launched("k_copy2d");
-            // projected right-hand side rows and the residual of the least-squares problem
-            gemm_grouped<double>({GemmDesc{pjc, p, d2, 0, p, 0, p, d0 * p, p}}, 2, 0, Hn.p, E1S.p, Gv.p, false, st);
-            CBFM_CUDA(cudaMemcpyAsync(Rv.p, E1S.p, sizeof(z64) * d2 * p, cudaMemcpyDeviceToDevice, st));
-            gemm_grouped<double>({GemmDesc{d2, p, d1, 0, dcap, 0, p, 0, p}}, 0, 0, Qh.p, Gv.p, Rv.p, true, st, -1.0);
+            // projected right-hand side rows and the residual of the least-squares
+            // problem, updated with the new Q block only (Rv = E1S - Q Q^H E1S):
+            //   G_J = Q_J^H Rv,  Rv <- Rv - Q_J G_J
+            gemm_grouped<double>({GemmDesc{pjc, p, d2, 0, p, 0, p, d0 * p, p}}, 2, 0, Hn.p, Rv.p, Gv.p, false, st);
+            gemm_grouped<double>({GemmDesc{d2, p, pjc, 0, p, d0 * p, p, 0, p}}, 0, 0, Hn.p, Gv.p, Rv.p, true, st,
+                                 -1.0);
             k_colnorm<<<p, 256, 0, st>>>((int)d2, p, Rv.p, p, rnorm.p);
             launched("k_colnorm");
             CBFM_CUDA(cudaMemcpyAsync(h_rn.data(), rnorm.p, sizeof(double) * p, cudaMemcpyDeviceToHost, st));

@@ -3,6 +3,7 @@
 // Jacobi SVD (dual orthogonalisation, Eq. (gram_CBF_SVD)) and Gauss-Jordan
 // inversion (CBF Gram matrix, Eq. (CBF_Gram_matrix)).
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -20,16 +21,19 @@ namespace {
 constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
 
 // Up to GB_MAXG problems per launch travel in the kernel parameters (no
-// device allocation, no host synchronisation).  A single large-K problem with
-// few output tiles is split along K into `ksplit` slices whose partial results
-// are summed in a fixed order by k_splitk_reduce.
-constexpr int GB_MAXG = 160;
+// device allocation, no host synchronisation).  When the output tiles of a
+// launch are too few to fill the GPU, each problem is split along K into
+// `ksplit[g]` slices whose partial results are summed in a fixed order by
+// k_splitk_reduce (deterministic).
+constexpr int GB_MAXG = 128;
 
 struct GemmBatch {
     int ng;
-    int ksplit;          // >= 1; > 1 only when ng == 1
-    int64_t kchunk;      // K range per slice
-    int64_t tile_off[GB_MAXG + 1];
+    int64_t tile_off[GB_MAXG + 1];   // work items (output tiles x K slices) before problem g
+    int64_t part_off[GB_MAXG + 1];   // first partial-sum element of problem g (split problems only)
+    int64_t red_off[GB_MAXG + 1];    // first output element of problem g in the reduction (split problems only)
+    int64_t kchunk[GB_MAXG];         // K range of one slice of problem g
+    int ksplit[GB_MAXG];             // K slices of problem g (>= 1)
     GemmDesc d[GB_MAXG];
 };
 
@@ -51,28 +55,26 @@ __global__ void __launch_bounds__(256) k_gemm(const __grid_constant__ GemmBatch 
                                               T alpha) {
     __shared__ cx<T> As[GB_K][GB_M + 1];
     __shared__ cx<T> Bs[GB_K][GB_N + 1];
-    int64_t tile = blockIdx.x;
-    int ks = 0;
-    if (bt.ksplit > 1) {
-        ks = (int)(tile % bt.ksplit);
-        tile /= bt.ksplit;
-    }
+    const int64_t item = blockIdx.x;
     int g = 0;
     {
         int lo = 0, hi = bt.ng - 1;
-        while (lo < hi) {   // last group with tile_off[g] <= tile
+        while (lo < hi) {   // last problem with tile_off[g] <= item
             int mid = (lo + hi + 1) / 2;
-            if (bt.tile_off[mid] <= tile) lo = mid;
+            if (bt.tile_off[mid] <= item) lo = mid;
             else hi = mid - 1;
         }
         g = lo;
     }
     const GemmDesc d = bt.d[g];
-    const int64_t local = tile - bt.tile_off[g];
+    const int nsplit = bt.ksplit[g];
+    int64_t local = item - bt.tile_off[g];
+    const int ks = (int)(local % nsplit);
+    local /= nsplit;
     const int64_t ntn = (d.N + GB_N - 1) / GB_N;
     const int64_t m0 = (local / ntn) * GB_M, n0 = (local % ntn) * GB_N;
-    const int64_t kb = (bt.ksplit > 1) ? (int64_t)ks * bt.kchunk : 0;
-    const int64_t ke = (bt.ksplit > 1) ? min(d.K, kb + bt.kchunk) : d.K;
+    const int64_t kb = (nsplit > 1) ? (int64_t)ks * bt.kchunk[g] : 0;
+    const int64_t ke = (nsplit > 1) ? min(d.K, kb + bt.kchunk[g]) : d.K;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     cx<T> acc[4][4];
     for (int i = 0; i < 4; ++i)
@@ -108,8 +110,8 @@ __global__ void __launch_bounds__(256) k_gemm(const __grid_constant__ GemmBatch 
         for (int j = 0; j < 4; ++j) {
             int64_t c = n0 + tx + 16 * j;
             if (c >= d.N) continue;
-            if (bt.ksplit > 1) {
-                part[((int64_t)ks * d.M + r) * d.N + c] = acc[i][j];
+            if (nsplit > 1) {
+                part[bt.part_off[g] + ((int64_t)ks * d.M + r) * d.N + c] = acc[i][j];
             } else {
                 cx<T> *p = C + d.c_off + r * d.ldc + c;
                 cx<T> v = alpha * acc[i][j];
@@ -120,19 +122,162 @@ __global__ void __launch_bounds__(256) k_gemm(const __grid_constant__ GemmBatch 
     }
 }
 
-// C = alpha * sum_s part[s] (+ C): fixed summation order (deterministic)
+// C[g] = alpha * sum_s part[g][s] (+ C[g]) for every split problem g: fixed
+// summation order (deterministic).
 template <typename T>
-__global__ void k_splitk_reduce(GemmDesc d, int ksplit, const cx<T> *__restrict__ part, cx<T> *__restrict__ C,
-                                int accumulate, T alpha) {
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < d.M * d.N;
+__global__ void k_splitk_reduce(const __grid_constant__ GemmBatch bt, const cx<T> *__restrict__ part,
+                                cx<T> *__restrict__ C, int accumulate, T alpha) {
+    const int64_t total = bt.red_off[bt.ng];
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = idx / d.N, c = idx % d.N;
+        int lo = 0, hi = bt.ng - 1;
+        while (lo < hi) {   // last problem with red_off[g] <= idx (problems that are not split have no width)
+            int mid = (lo + hi + 1) / 2;
+            if (bt.red_off[mid] <= idx) lo = mid;
+            else hi = mid - 1;
+        }
+        const GemmDesc &d = bt.d[lo];
+        const int64_t e = idx - bt.red_off[lo], mn = d.M * d.N;
+        const int64_t r = e / d.N, c = e % d.N;
+        const cx<T> *pp = part + bt.part_off[lo] + e;
         cx<T> v(0, 0);
-        for (int s = 0; s < ksplit; ++s) v += part[(int64_t)s * d.M * d.N + idx];
+        for (int s = 0; s < bt.ksplit[lo]; ++s) v += pp[(int64_t)s * mn];
         cx<T> *p = C + d.c_off + r * d.ldc + c;
         v = alpha * v;
         if (accumulate) *p += v;
         else *p = v;
+    }
+}
+
+// ------------------------------------------- stream-K grouped GEMM (FP64)
+// FP64 products are limited by the FP64 pipe of each SM (about two DFMA per
+// clock on GB300), so an FP64 GEMM runs at the speed of its busiest SM: the
+// work must be spread evenly, whatever the shapes.  The problems of one launch
+// are cut into units of one 32 x 32 output tile x 16 of K; the units, numbered
+// problem by problem, tile by tile, K-step by K-step, are dealt out to G
+// CTAs in equal contiguous runs (CTA c takes [c U / G, (c+1) U / G)).  A CTA
+// writes every tile it covers completely straight to C; the (at most two)
+// tiles cut at the ends of its run go to its two partial-sum slots, and
+// k_gemm_sk_fix adds the slots of each cut tile in CTA order (deterministic).
+constexpr int SK_T = 32, SK_K = 16;
+
+struct SkBatch {
+    int ng;
+    int G;                           // CTAs
+    int64_t U;                       // units
+    int64_t unit_off[GB_MAXG + 1];   // first unit of problem g
+    int64_t ksteps[GB_MAXG];         // K-steps per tile of problem g
+    GemmDesc d[GB_MAXG];
+};
+
+__device__ __forceinline__ int sk_group(const SkBatch &bt, int64_t u) {
+    int lo = 0, hi = bt.ng - 1;
+    while (lo < hi) {   // last problem with unit_off[g] <= u
+        int mid = (lo + hi + 1) / 2;
+        if (bt.unit_off[mid] <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int64_t sk_first(int64_t c, const SkBatch &bt) { return c * bt.U / bt.G; }
+__device__ __forceinline__ int64_t sk_owner(int64_t u, const SkBatch &bt) { return ((u + 1) * bt.G - 1) / bt.U; }
+
+__global__ void __launch_bounds__(256) k_gemm_sk(const __grid_constant__ SkBatch bt, int opA, int opB,
+                                                 const z64 *__restrict__ A, const z64 *__restrict__ B,
+                                                 z64 *__restrict__ C, z64 *__restrict__ part, int accumulate,
+                                                 double alpha) {
+    __shared__ z64 As[SK_K][SK_T + 1];
+    __shared__ z64 Bs[SK_K][SK_T + 1];
+    const int64_t c = blockIdx.x;
+    const int64_t u0 = sk_first(c, bt), u1 = sk_first(c + 1, bt);
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const bool rowA = (opA == 0 || opA == 3), rowB = (opB == 0 || opB == 3);
+    for (int64_t u = u0; u < u1;) {
+        const int g = sk_group(bt, u);
+        const GemmDesc &d = bt.d[g];
+        const int64_t ks = bt.ksteps[g];
+        const int64_t local = u - bt.unit_off[g];
+        const int64_t t = local / ks, kk0 = local % ks;
+        const int64_t seg_end = min(u1, bt.unit_off[g] + (t + 1) * ks);
+        const int64_t ntn = (d.N + SK_T - 1) / SK_T;
+        const int64_t m0 = (t / ntn) * SK_T, n0 = (t % ntn) * SK_T;
+        z64 acc[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) acc[i][j] = z64(0, 0);
+        for (int64_t kk = kk0; kk < kk0 + (seg_end - u); ++kk) {
+            const int64_t k0 = kk * SK_K;
+            for (int idx = threadIdx.x; idx < SK_T * SK_K; idx += 256) {
+                const int mm = rowA ? idx / SK_K : idx % SK_T;
+                const int kq = rowA ? idx % SK_K : idx / SK_T;
+                As[kq][mm] = load_op(A, d.a_off, d.lda, m0 + mm, k0 + kq, d.M, d.K, opA);
+                const int kb = rowB ? idx / SK_T : idx % SK_K;
+                const int nn = rowB ? idx % SK_T : idx / SK_K;
+                Bs[kb][nn] = load_op(B, d.b_off, d.ldb, k0 + kb, n0 + nn, d.K, d.N, opB);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kq = 0; kq < SK_K; ++kq) {
+                const z64 a0 = As[kq][ty], a1 = As[kq][ty + 16];
+                const z64 b0 = Bs[kq][tx], b1 = Bs[kq][tx + 16];
+                cfma(acc[0][0], a0, b0);
+                cfma(acc[0][1], a0, b1);
+                cfma(acc[1][0], a1, b0);
+                cfma(acc[1][1], a1, b1);
+            }
+            __syncthreads();
+        }
+        const bool whole = (kk0 == 0 && seg_end - u == ks);
+        z64 *slot = part + (2 * c + (u == u0 ? 0 : 1)) * (SK_T * SK_T);
+        for (int i = 0; i < 2; ++i) {
+            const int64_t r = m0 + ty + 16 * i;
+            for (int j = 0; j < 2; ++j) {
+                const int64_t col = n0 + tx + 16 * j;
+                if (!whole) {
+                    slot[(ty + 16 * i) * SK_T + tx + 16 * j] = acc[i][j];
+                } else if (r < d.M && col < d.N) {
+                    z64 *pc = C + d.c_off + r * d.ldc + col;
+                    const z64 v = alpha * acc[i][j];
+                    if (accumulate) *pc += v;
+                    else *pc = v;
+                }
+            }
+        }
+        u = seg_end;
+    }
+}
+
+// One CTA per boundary b between the runs of CTAs b and b+1: if the boundary
+// cuts a tile and b is the first CTA on that tile, sum the tile's slots over
+// the CTAs that cover it, in CTA order, and write C.
+__global__ void __launch_bounds__(256) k_gemm_sk_fix(const __grid_constant__ SkBatch bt,
+                                                     const z64 *__restrict__ part, z64 *__restrict__ C,
+                                                     int accumulate, double alpha) {
+    const int64_t b = blockIdx.x;
+    const int64_t ub = sk_first(b + 1, bt);   // first unit after the run of CTA b
+    if (ub <= 0 || ub >= bt.U) return;
+    const int64_t last = ub - 1;
+    const int g = sk_group(bt, last);
+    const GemmDesc &d = bt.d[g];
+    const int64_t ks = bt.ksteps[g];
+    const int64_t t = (last - bt.unit_off[g]) / ks;
+    const int64_t tu0 = bt.unit_off[g] + t * ks, tu1 = tu0 + ks;
+    if (ub >= tu1) return;                    // the tile ends with the run of CTA b
+    if (sk_owner(tu0, bt) != b) return;       // an earlier boundary cuts this tile
+    const int64_t clast = sk_owner(tu1 - 1, bt);
+    const int64_t ntn = (d.N + SK_T - 1) / SK_T;
+    const int64_t m0 = (t / ntn) * SK_T, n0 = (t % ntn) * SK_T;
+    for (int e = threadIdx.x; e < SK_T * SK_T; e += 256) {
+        const int64_t r = m0 + e / SK_T, col = n0 + e % SK_T;
+        if (r >= d.M || col >= d.N) continue;
+        z64 v(0, 0);
+        for (int64_t c = b; c <= clast; ++c) {
+            const int j = (sk_first(c, bt) >= tu0) ? 0 : 1;
+            v += part[(2 * c + j) * (SK_T * SK_T) + e];
+        }
+        z64 *pc = C + d.c_off + r * d.ldc + col;
+        v = alpha * v;
+        if (accumulate) *pc += v;
+        else *pc = v;
     }
 }
 
@@ -146,8 +291,6 @@ __global__ void __launch_bounds__(256) k_lu_solve(const int64_t *__restrict__ zo
     const int n = nsz[b];
     z64 *Z = Zall + zoff[b];
     z64 *V = Vall + voff[b];
-    __shared__ double sval[256];
-    __shared__ int sidx[256];
     __shared__ int piv;
     __shared__ z64 pinv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -260,19 +403,19 @@ __global__ void __cluster_dims__(JS_CL, 1, 1) __launch_bounds__(256)
     z64 *V = Vall + (int64_t)mat * s * s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int gw = me * nw + warp, ngw = JS_CL * nw;
-    __shared__ uint64_t cbar;
+    __shared__ uint64_t cbar[2];
     __shared__ int s_abort, rot_local, rotflag[JS_CL];
     __shared__ double s_wmax[32], s_big;
     for (int64_t i = (int64_t)me * blockDim.x + threadIdx.x; i < (int64_t)s * s; i += (int64_t)JS_CL * blockDim.x)
         V[i] = z64((i % s) == (i / s) ? 1.0 : 0.0, 0.0);
     if (threadIdx.x == 0) {
-        cl_bar_init(&cbar, JS_CL);
+        cl_bar_init(cbar, JS_CL);
         s_abort = 0;
     }
     __syncthreads();
     cl.sync();   // barriers initialised and V set in every CTA (unconditional)
     const int n2 = s + (s & 1);
-    uint32_t phase = 0;
+    int step = 0;   // cluster synchronisation count
     bool ok = true;
     int sweep = 0;
     for (; sweep < 60; ++sweep) {
@@ -342,12 +485,12 @@ __global__ void __cluster_dims__(JS_CL, 1, 1) __launch_bounds__(256)
                     vj[r] = sep * vu + c * vv;
                 }
             }
-            ok = cl_sync(&cbar, phase++ & 1u, JS_CL, &s_abort, info + mat);
+            ok = cl_sync(cbar, step++, JS_CL, &s_abort, info + mat);
         }
         if (!ok) break;
         // has any CTA rotated in this sweep?  (flags to every CTA, then one synchronisation)
         if (threadIdx.x < JS_CL) *cl.map_shared_rank(&rotflag[me], threadIdx.x) = rot_local;
-        if (!(ok = cl_sync(&cbar, phase++ & 1u, JS_CL, &s_abort, info + mat))) break;
+        if (!(ok = cl_sync(cbar, step++, JS_CL, &s_abort, info + mat))) break;
         int any = 0;
         for (int r = 0; r < JS_CL; ++r) any |= rotflag[r];
         if (!any) break;
@@ -575,6 +718,50 @@ __global__ void k_to64(const c32 *__restrict__ s, z64 *__restrict__ d, int64_t n
     if (i < n) d[i] = z64(s[i].re, s[i].im);
 }
 
+void gemm_sk(const std::vector<GemmDesc> &g, int opA, int opB, const z64 *A, const z64 *B, z64 *C, bool accumulate,
+             cudaStream_t st, double alpha) {
+    static std::atomic<int> s_grid[64];   // CTAs per launch, per device (zero: not yet queried)
+    int dev = 0;
+    CBFM_CUDA(cudaGetDevice(&dev));
+    int G0 = dev < 64 ? s_grid[dev].load(std::memory_order_relaxed) : 0;
+    if (G0 == 0) {
+        int nsm = 0, occ = 0;
+        CBFM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gemm_sk, 256, 0));
+        // two CTAs per SM: one keeps the FP64 pipe busy while the other
+        // stages its next K-step; more would only cut more tiles
+        G0 = std::max(1, nsm * std::max(1, std::min(occ, 2)));
+        if (dev < 64) s_grid[dev].store(G0, std::memory_order_relaxed);
+    }
+    for (size_t g0 = 0; g0 < g.size(); g0 += GB_MAXG) {
+        SkBatch bt;
+        bt.ng = (int)std::min<size_t>(GB_MAXG, g.size() - g0);
+        bt.unit_off[0] = 0;
+        for (int i = 0; i < bt.ng; ++i) {
+            const GemmDesc &d = g[g0 + i];
+            bt.d[i] = d;
+            const int64_t tiles = (d.M > 0 && d.N > 0) ? ((d.M + SK_T - 1) / SK_T) * ((d.N + SK_T - 1) / SK_T) : 0;
+            bt.ksteps[i] = std::max<int64_t>(1, (d.K + SK_K - 1) / SK_K);   // K = 0: one step of zeros
+            bt.unit_off[i + 1] = bt.unit_off[i] + tiles * bt.ksteps[i];
+        }
+        bt.U = bt.unit_off[bt.ng];
+        if (bt.U == 0) continue;
+        bt.G = (int)std::min<int64_t>(G0, bt.U);
+        z64 *part = nullptr;
+        if (bt.G > 1) CBFM_CUDA(cudaMallocAsync((void **)&part, sizeof(z64) * 2 * bt.G * SK_T * SK_T, st));
+        {
+            ProfScope ps_("k_gemm_z64", st);
+            k_gemm_sk<<<bt.G, 256, 0, st>>>(bt, opA, opB, A, B, C, part, accumulate ? 1 : 0, alpha);
+            launched("k_gemm_sk");
+            if (bt.G > 1) {
+                k_gemm_sk_fix<<<bt.G - 1, 256, 0, st>>>(bt, part, C, accumulate ? 1 : 0, alpha);
+                launched("k_gemm_sk_fix");
+            }
+        }
+        if (part) CBFM_CUDA(cudaFreeAsync(part, st));
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -589,50 +776,57 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
         }
         prof_add_work(sizeof(T) == 8 ? "k_gemm_z64" : "k_gemm_c32", fl, by);
     }
-    for (size_t g0 = 0; g0 < g.size(); g0 += GB_MAXG) {
-        GemmBatch bt;
-        bt.ng = (int)std::min<size_t>(GB_MAXG, g.size() - g0);
-        bt.ksplit = 1;
-        bt.kchunk = 0;
-        bt.tile_off[0] = 0;
-        for (int i = 0; i < bt.ng; ++i) {
-            const GemmDesc &d = g[g0 + i];
-            bt.d[i] = d;
-            int64_t t = (d.M > 0 && d.N > 0) ? ((d.M + GB_M - 1) / GB_M) * ((d.N + GB_N - 1) / GB_N) : 0;
-            bt.tile_off[i + 1] = bt.tile_off[i] + t;
-        }
-        const int64_t tiles = bt.tile_off[bt.ng];
-        if (tiles == 0) continue;
-        // few output tiles: split K (chunks of at least GB_K) until about two
-        // CTAs per SM exist.  A CTA of this kernel keeps its SM's FP64 pipe
-        // busy on its own, so for FP64 products the grid size, not the tile
-        // shape, decides the speed of the small GEMMs of block GMRES.
-        const GemmDesc &d0 = bt.d[0];
-        if (bt.ng == 1 && tiles < 2 * 152 && d0.K > GB_K) {
-            int64_t S = std::min<int64_t>((2 * 152 + tiles - 1) / tiles, (d0.K + GB_K - 1) / GB_K);
-            if (S > 1) {
-                int64_t chunk = (d0.K + S - 1) / S;
-                chunk = (chunk + GB_K - 1) / GB_K * GB_K;
-                bt.kchunk = chunk;
-                bt.ksplit = (int)((d0.K + chunk - 1) / chunk);
+    if constexpr (sizeof(T) == 8) {
+        gemm_sk(g, opA, opB, A, B, C, accumulate, st, alpha);
+    } else {
+        for (size_t g0 = 0; g0 < g.size(); g0 += GB_MAXG) {
+            GemmBatch bt;
+            bt.ng = (int)std::min<size_t>(GB_MAXG, g.size() - g0);
+            int64_t tiles = 0;
+            std::vector<int64_t> tg(bt.ng);
+            for (int i = 0; i < bt.ng; ++i) {
+                const GemmDesc &d = g[g0 + i];
+                bt.d[i] = d;
+                tg[i] = (d.M > 0 && d.N > 0) ? ((d.M + GB_M - 1) / GB_M) * ((d.N + GB_N - 1) / GB_N) : 0;
+                tiles += tg[i];
             }
-        }
-        cx<T> *part = nullptr;
-        if (bt.ksplit > 1) {
-            CBFM_CUDA(cudaMallocAsync((void **)&part, sizeof(cx<T>) * bt.ksplit * d0.M * d0.N, st));
-        }
-        {
-            ProfScope ps_(sizeof(T) == 8 ? "k_gemm_z64" : "k_gemm_c32", st);
-            k_gemm<T><<<(unsigned)(tiles * bt.ksplit), 256, 0, st>>>(bt, opA, opB, A, B, C, part,
-                                                                     accumulate ? 1 : 0, (T)alpha);
-            launched("k_gemm");
-        }
-        if (bt.ksplit > 1) {
-            const int64_t mn = d0.M * d0.N;
-            k_splitk_reduce<T><<<(unsigned)std::min<int64_t>((mn + 255) / 256, 4096), 256, 0, st>>>(
-                d0, bt.ksplit, part, C, accumulate ? 1 : 0, (T)alpha);
-            launched("k_splitk_reduce");
-            CBFM_CUDA(cudaFreeAsync(part, st));
+            if (tiles == 0) continue;
+            // few output tiles: split K (slices of at least GB_K) until about two
+            // CTAs per SM exist
+            const int64_t want = (tiles < 2 * 152) ? (2 * 152 + tiles - 1) / tiles : 1;
+            bt.tile_off[0] = bt.part_off[0] = bt.red_off[0] = 0;
+            for (int i = 0; i < bt.ng; ++i) {
+                const GemmDesc &d = bt.d[i];
+                int64_t S = 1, chunk = 0;
+                if (want > 1 && tg[i] > 0 && d.K > GB_K) {
+                    S = std::min<int64_t>(want, (d.K + GB_K - 1) / GB_K);
+                    chunk = (d.K + S - 1) / S;
+                    chunk = (chunk + GB_K - 1) / GB_K * GB_K;
+                    S = (d.K + chunk - 1) / chunk;
+                }
+                bt.ksplit[i] = (int)S;
+                bt.kchunk[i] = S > 1 ? chunk : 0;
+                bt.tile_off[i + 1] = bt.tile_off[i] + tg[i] * S;
+                bt.part_off[i + 1] = bt.part_off[i] + (S > 1 ? S * d.M * d.N : 0);
+                bt.red_off[i + 1] = bt.red_off[i] + (S > 1 ? d.M * d.N : 0);
+            }
+            const int64_t items = bt.tile_off[bt.ng];
+            cx<T> *part = nullptr;
+            if (bt.part_off[bt.ng] > 0) {
+                CBFM_CUDA(cudaMallocAsync((void **)&part, sizeof(cx<T>) * bt.part_off[bt.ng], st));
+            }
+            {
+                ProfScope ps_("k_gemm_c32", st);
+                k_gemm<T><<<(unsigned)items, 256, 0, st>>>(bt, opA, opB, A, B, C, part, accumulate ? 1 : 0, (T)alpha);
+                launched("k_gemm");
+            }
+            if (part) {
+                const int64_t mn = bt.red_off[bt.ng];
+                k_splitk_reduce<T><<<(unsigned)std::min<int64_t>((mn + 255) / 256, 4096), 256, 0, st>>>(
+                    bt, part, C, accumulate ? 1 : 0, (T)alpha);
+                launched("k_splitk_reduce");
+                CBFM_CUDA(cudaFreeAsync(part, st));
+            }
         }
     }
 }
