@@ -557,7 +557,7 @@ def main():
                 "gmres_iters": {"min": int(iters.min()), "max": int(iters.max()), "mean": float(iters.mean())},
                 "clocks": clocks, "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(exc_h.numel() * 8),
                                           "d2h_bytes_per_step": int(rcs_h.numel() * 8)},
-                "gpu_launches": int(launches), "roofline": roof,
+                "gpu_launches": int(launches), "roofline": roof, "tuning": P.tuning(),
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
                 "fp64_path": fp64, "other_solver": alt, "batch": batch, "serving": serving}

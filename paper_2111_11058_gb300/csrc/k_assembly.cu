@@ -15,6 +15,10 @@
 //     X = sum_q w_q g (d x rho'),  G = e^{-jkR}/(4 pi R), g = -(1+jkR) e^{-jkR}/(4 pi R^3)
 //     M0 = sum_p w_p S0, Mr = sum_p w_p rho S0, Ms = sum_p w_p S1, Mrs = sum_p w_p rho.S1,
 //     MW = sum_p w_p W, MrW = sum_p w_p rho x W, MX = sum_p w_p X, MrX = sum_p w_p rho.X
+//   The K sums are evaluated through Sg = sum_q w_q g and Y = sum_q w_q g rho':
+//   with Dp = (c_t - c_s) + rho, d x rho' = Dp x rho', so W = Dp Sg - Y and
+//   X = Dp x Y, and the sums over p of w_p Sg, w_p rho Sg, w_p Y, w_p rho x Y
+//   give MW, MX, MrW, MrX once per pair.
 //   The minus sign on T is the reading under which the paper's block matrix
 //   describes the exp(+j w t) problem.  Blocks are combined into
 //   Ks = K1 + K2, Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2.
@@ -36,11 +40,13 @@ namespace cbfm {
 namespace {
 
 constexpr int NCOMP = 27;   // 3 operators x 3 x 3
-// Floating-point operations of one point pair (both media) in k_far's inner
-// loop, counting an FMA as 2: shared geometry d, R^2, R, 1/R^2, d x rho' (19);
-// per medium: k R, 2-pi reduction, sin/cos argument scaling, amplitude,
-// w G, (1 + jkR), w g, and the S0, S1, W, X accumulations (62).
-constexpr double FAR_FLOP_PER_POINT_PAIR = 19.0 + 2.0 * 62.0;
+// Algorithmic work of one quadrature point pair, both media, counting an FMA
+// as 2: the direct evaluation of G and g (distance, R, 1/R, e^{-jkR}, the
+// (1 + jkR)/R^2 factor) and of the 14 complex moment sums of the far pair
+// (sum G, G r, G r', G r.r', g (r x r'), g (r - r')) per medium, about 170
+// flops.  The kernel reaches the same sums with fewer operations (moment
+// form, shared geometry); the achieved rate is quoted on this count.
+constexpr double FAR_FLOP_PER_POINT_PAIR = 170.0;
 
 struct Media {
     double k1r, k1i, k2r, k2i;
@@ -103,12 +109,13 @@ template <typename T>
 struct Mom {
     cx<T> M0, Mrs, MrX;
     cx<T> Mr[3], Ms[3], MW[3], MrW[3], MX[3];
+    cx<T> A0, A1[3], B0[3], B1[3];   // far kernel: sums over the test points that give MW, MX, MrW, MrX
 };
 
 template <typename T>
-__device__ __forceinline__ void zero(Mom<T> &m) {
-    m.M0 = m.Mrs = m.MrX = cx<T>(0, 0);
-    for (int d = 0; d < 3; ++d) m.Mr[d] = m.Ms[d] = m.MW[d] = m.MrW[d] = m.MX[d] = cx<T>(0, 0);
+__device__ __forceinline__ void zero(Mom<T> &m) {   // the accumulated sums (MW, MX, MrW, MrX are formed after)
+    m.M0 = m.Mrs = m.A0 = cx<T>(0, 0);
+    for (int d = 0; d < 3; ++d) m.Mr[d] = m.Ms[d] = m.A1[d] = m.B0[d] = m.B1[d] = cx<T>(0, 0);
 }
 
 __device__ __forceinline__ bool shares_vertex(const int32_t *a, const int32_t *b) {
@@ -134,37 +141,43 @@ __device__ __forceinline__ bool is_near(const double *rt, const double *rs, cons
 }
 
 // Entries of one medium from its moments; adds into out[27] with the
-// operator weights (wK for K into Ks; wTa, wTb for T into Ta, Tb).
+// operator weights (wK for K into Ks; wTa, wTb for T into Ta, Tb).  The
+// brackets are split into parts of the trial vertex b and of the test
+// vertex a:
+//   T: Mrs - pb.Mr - pa.Ms + (pa.pb - 4/k^2) M0 = u_b - v_a + (pa.pb) M0,
+//      u_b = Mrs - pb.Mr - (4/k^2) M0,  v_a = pa.Ms
+//   K: MrX - pa.MX - pb.MrW + pa.(MW x pb) = y_b + pa.z_b,
+//      y_b = MrX - pb.MrW,  z_b = MW x pb - MX
+// papb[a][b] = pa.pb and cc[a][b] = c_a c_b are shared by the two media.
 template <typename T>
-__device__ __forceinline__ void fold_entries(const Mom<T> &m, T kr, T ki, cx<T> four_k2, const T ca[3], const T cb[3],
-                                             const T pa[3][3], const T pb[3][3], cx<T> wTa, cx<T> wTb,
-                                             cx<T> *out) {
-    // -j k for complex k
-    cx<T> mjk(ki, -kr);
+__device__ __forceinline__ void fold_entries(const Mom<T> &m, T kr, T ki, cx<T> four_k2, const T cc[3][3],
+                                             const T papb[3][3], const T pa[3][3], const T pb[3][3], cx<T> wTa,
+                                             cx<T> wTb, cx<T> *out) {
+    const cx<T> mjk(ki, -kr);   // -j k for complex k
+    const cx<T> k2M0 = four_k2 * m.M0;
+    cx<T> u[3], y[3], z[3][3], v[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        u[b] = m.Mrs - k2M0;
+        y[b] = m.MrX;
+        for (int d = 0; d < 3; ++d) {
+            u[b] -= pb[b][d] * m.Mr[d];
+            y[b] -= pb[b][d] * m.MrW[d];
+        }
+        z[b][0] = m.MW[1] * pb[b][2] - m.MW[2] * pb[b][1] - m.MX[0];
+        z[b][1] = m.MW[2] * pb[b][0] - m.MW[0] * pb[b][2] - m.MX[1];
+        z[b][2] = m.MW[0] * pb[b][1] - m.MW[1] * pb[b][0] - m.MX[2];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = pa[a][0] * m.Ms[0] + pa[a][1] * m.Ms[1] + pa[a][2] * m.Ms[2];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
+#pragma unroll
         for (int b = 0; b < 3; ++b) {
-            T cc = ca[a] * cb[b];
-            T papb = pa[a][0] * pb[b][0] + pa[a][1] * pb[b][1] + pa[a][2] * pb[b][2];
-            // T bracket
-            cx<T> tb = m.Mrs;
-            for (int d = 0; d < 3; ++d) {
-                tb -= pb[b][d] * m.Mr[d];
-                tb -= pa[a][d] * m.Ms[d];
-            }
-            tb += (cx<T>(papb, 0) - four_k2) * m.M0;
-            cx<T> Tab = cc * (mjk * tb);
-            // K bracket: MrX - pa.MX - pb.MrW + pa.(MW x pb)
-            cx<T> kb = m.MrX;
-            for (int d = 0; d < 3; ++d) {
-                kb -= pa[a][d] * m.MX[d];
-                kb -= pb[b][d] * m.MrW[d];
-            }
-            cx<T> cr0 = m.MW[1] * pb[b][2] - m.MW[2] * pb[b][1];
-            cx<T> cr1 = m.MW[2] * pb[b][0] - m.MW[0] * pb[b][2];
-            cx<T> cr2 = m.MW[0] * pb[b][1] - m.MW[1] * pb[b][0];
-            kb += pa[a][0] * cr0 + pa[a][1] * cr1 + pa[a][2] * cr2;
-            cx<T> Kab = cc * kb;
-            out[0 * 9 + 3 * a + b] += Kab;
+            const cx<T> tb = u[b] - v[a] + papb[a][b] * m.M0;
+            const cx<T> kb = y[b] + pa[a][0] * z[b][0] + pa[a][1] * z[b][1] + pa[a][2] * z[b][2];
+            const cx<T> Tab = (cc[a][b] * mjk) * tb;
+            out[0 * 9 + 3 * a + b] += cc[a][b] * kb;
             out[1 * 9 + 3 * a + b] += wTa * Tab;
             out[2 * 9 + 3 * a + b] += wTb * Tab;
         }
@@ -192,47 +205,36 @@ __device__ __forceinline__ bool is_near_t(const T *rt_cen, const T *rt_lo, T ht,
     return is_near(rt64, rs64, vt, vs, alpha);
 }
 
-// Test-triangle data of the far kernel, staged in shared memory once per
-// test triangle and read by every trial-triangle thread.
+// One staged item of the far kernel, in shared memory: the test triangle t
+// (its record in the kernel's type, its FP64 record for the exact near test
+// and its vertex ids) and the records of up to 32 trial triangles (rows
+// padded by one element against bank conflicts).
 template <typename T>
-struct FarShared {
-    T sq[21], sw[7], sp[9], sc[3], scen[3], sclo[3], sh_t;
-    double sc64[TRI_REC];
-    int32_t sv[3];
+struct FarStage {
+    double trec64[TRI_REC];
+    T trec[TRI_REC];
+    int32_t tv[4];
+    T trial[32][TRI_REC + 1];
 };
 
-template <typename T>
-__device__ __forceinline__ void far_load(FarShared<T> &S, const T *__restrict__ rec, const double *__restrict__ rec64,
-                                         const int32_t *__restrict__ vid, int t) {
-    for (int i = threadIdx.x; i < TRI_REC; i += blockDim.x) {
-        const T v = rec[(int64_t)t * TRI_REC + i];
-        if (i < 21) S.sq[i] = v;
-        else if (i < 28) S.sw[i - 21] = v;
-        else if (i < 37) S.sp[i - 28] = v;
-        else if (i < 40) S.sc[i - 37] = v;
-        else if (i < 43) S.scen[i - 40] = v;   // centroid in the same frame as the points
-        else if (i == 43) S.sh_t = v;
-        else if (i < 47) S.sclo[i - 44] = v;
-        S.sc64[i] = rec64[(int64_t)t * TRI_REC + i];
-        if (i < 3) S.sv[i] = vid[3 * t + i];
-    }
+template <int B>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(dst_smem)),
+                 "l"(src), "n"(B)
+                 : "memory");
 }
 
+// One far (or, by the classification, near -> zero) triangle pair (t, s);
+// rs is the record of the trial triangle s.
 template <typename T>
-__device__ __forceinline__ void far_pair(const FarShared<T> &S, int nt, const T *__restrict__ rec,
-                                         const double *__restrict__ rec64, const int32_t *__restrict__ vid,
-                                         double alpha, const MediaT<T> &md, cx<T> *__restrict__ Zloc, int t, int s);
-
-// One far (or, by the classification, near -> zero) triangle pair (t, s).
-template <typename T>
-__device__ __forceinline__ void far_pair(const FarShared<T> &S, int nt, const T *__restrict__ rec,
+__device__ __forceinline__ void far_pair(const FarStage<T> &S, int nt, const T *rs,
                                          const double *__restrict__ rec64, const int32_t *__restrict__ vid,
                                          double alpha, const MediaT<T> &md, cx<T> *__restrict__ Zloc, int t, int s) {
-    const T *sq = S.sq, *sw = S.sw, *sp = S.sp, *sc = S.sc, *scen = S.scen, *sclo = S.sclo;
-    const T sh_t = S.sh_t;
-    const double *sc64 = S.sc64;
-    const int32_t *sv = S.sv;
-    const T *rs = rec + (int64_t)s * TRI_REC;
+    const T *sq = S.trec + TR_Q, *sw = S.trec + TR_W, *sp = S.trec + TR_P, *sc = S.trec + TR_C;
+    const T *scen = S.trec + TR_CEN, *sclo = S.trec + TR_CLO;
+    const T sh_t = S.trec[TR_H];
+    const double *sc64 = S.trec64;
+    const int32_t *sv = S.tv;
     const int64_t plane = (int64_t)nt * nt;
     const int64_t base = (int64_t)t * nt + s;
     int32_t vs[3] = {vid[3 * s], vid[3 * s + 1], vid[3 * s + 2]};
@@ -250,92 +252,124 @@ __device__ __forceinline__ void far_pair(const FarShared<T> &S, int nt, const T 
         if constexpr (sizeof(T) == 4) dc[d] += sclo[d] - rs[TR_CLO + d];
     }
     T rq[7][3], wq[7];
+    const T inv4pi = (T)(1.0 / (4.0 * PI));
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
         for (int d = 0; d < 3; ++d) rq[q][d] = rs[TR_Q + 3 * q + d] - cs[d];
-        wq[q] = rs[TR_W + q];
+        wq[q] = rs[TR_W + q] * inv4pi;
     }
     const T kr[2] = {md.kr[0], md.kr[1]};
     const T ki[2] = {md.ki[0], md.ki[1]};
     const bool lossy2 = md.ki[1] != (T)0;
-    const T inv4pi = (T)(1.0 / (4.0 * PI));
     Mom<T> mm[2];
     zero(mm[0]);
     zero(mm[1]);
     for (int p = 0; p < 7; ++p) {
         T rho[3] = {sq[3 * p] - ct[0], sq[3 * p + 1] - ct[1], sq[3 * p + 2] - ct[2]};
         T Dp[3] = {dc[0] + rho[0], dc[1] + rho[1], dc[2] + rho[2]};
-        cx<T> S0[2], S1[2][3], W[2][3], X[2][3];
+        // per medium over the trial points: S0 = sum w G, S1 = sum w G rho',
+        // Sg = sum w g, Y = sum w g rho'.  With d = Dp - rho' (and rho' x rho' = 0)
+        // the sums of the definition follow per test point:
+        //   W = sum w g d = Dp Sg - Y,  X = sum w g (d x rho') = Dp x Y.
+        cx<T> S0[2], S1[2][3], Sg[2], Y[2][3];
         for (int i = 0; i < 2; ++i) {
-            S0[i] = cx<T>(0, 0);
-            for (int d = 0; d < 3; ++d) S1[i][d] = W[i][d] = X[i][d] = cx<T>(0, 0);
+            S0[i] = Sg[i] = cx<T>(0, 0);
+            for (int d = 0; d < 3; ++d) S1[i][d] = Y[i][d] = cx<T>(0, 0);
         }
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
-            T d0 = Dp[0] - rq[q][0], d1 = Dp[1] - rq[q][1], d2 = Dp[2] - rq[q][2];
-            T R2 = d0 * d0 + d1 * d1 + d2 * d2;
-            T iR = rsqrt_t(R2);
-            T R = R2 * iR;
-            T iR2 = iR * iR;
-            // d x rho'
-            T x0 = d1 * rq[q][2] - d2 * rq[q][1];
-            T x1 = d2 * rq[q][0] - d0 * rq[q][2];
-            T x2 = d0 * rq[q][1] - d1 * rq[q][0];
+            const T d0 = Dp[0] - rq[q][0], d1 = Dp[1] - rq[q][1], d2 = Dp[2] - rq[q][2];
+            const T R2 = d0 * d0 + d1 * d1 + d2 * d2;
+            const T iR = rsqrt_t(R2);
+            const T R = R2 * iR;
+            const T niR2 = -(iR * iR);
+            const T amp = iR * wq[q];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
+                const T kR = kr[i] * R;
                 T sn, cs_;
-                sincos_red(kr[i] * R, &sn, &cs_);
-                T amp = iR * inv4pi * wq[q];
-                if (i == 1 && lossy2) amp *= exp_t(ki[i] * R);
-                // w G = amp (cos - j sin)
-                cx<T> wG(amp * cs_, -amp * sn);
-                // w g = -(1 + j k R) w G / R^2, with j k R = -ki R + j kr R
-                cx<T> one_jkR((T)1 - ki[i] * R, kr[i] * R);
-                cx<T> wg = (-iR2) * (one_jkR * wG);
+                sincos_red(kR, &sn, &cs_);
+                T a_i = amp;
+                if (i == 1 && lossy2) a_i *= exp_t(ki[i] * R);
+                // w G = amp (cos - j sin);  w g = -(1 + j k R) w G / R^2, j k R = -ki R + j kr R
+                const cx<T> wG(a_i * cs_, -a_i * sn);
+                T gx, gy;
+                if (i == 1 && lossy2) {
+                    const T o = (T)1 - ki[i] * R;
+                    gx = o * wG.re - kR * wG.im;
+                    gy = o * wG.im + kR * wG.re;
+                } else {
+                    gx = wG.re - kR * wG.im;
+                    gy = wG.im + kR * wG.re;
+                }
+                const cx<T> wg(niR2 * gx, niR2 * gy);
                 S0[i] += wG;
-                S1[i][0] += rq[q][0] * wG; S1[i][1] += rq[q][1] * wG; S1[i][2] += rq[q][2] * wG;
-                W[i][0] += d0 * wg; W[i][1] += d1 * wg; W[i][2] += d2 * wg;
-                X[i][0] += x0 * wg; X[i][1] += x1 * wg; X[i][2] += x2 * wg;
+                Sg[i] += wg;
+                for (int d = 0; d < 3; ++d) {
+                    S1[i][d] += rq[q][d] * wG;
+                    Y[i][d] += rq[q][d] * wg;
+                }
             }
         }
         const T wp = sw[p];
+        const T rw[3] = {wp * rho[0], wp * rho[1], wp * rho[2]};
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             Mom<T> &m = mm[i];
             m.M0 += wp * S0[i];
-            cx<T> rS1(0, 0), rX(0, 0);
+            m.A0 += wp * Sg[i];
             for (int d = 0; d < 3; ++d) {
-                m.Mr[d] += (wp * rho[d]) * S0[i];
+                m.Mr[d] += rw[d] * S0[i];
                 m.Ms[d] += wp * S1[i][d];
-                rS1 += rho[d] * S1[i][d];
-                m.MW[d] += wp * W[i][d];
-                m.MX[d] += wp * X[i][d];
-                rX += rho[d] * X[i][d];
+                m.Mrs += rw[d] * S1[i][d];
+                m.A1[d] += rw[d] * Sg[i];
+                m.B0[d] += wp * Y[i][d];
             }
-            m.Mrs += wp * rS1;
-            m.MrX += wp * rX;
-            // rho x W
-            m.MrW[0] += wp * (rho[1] * W[i][2] - rho[2] * W[i][1]);
-            m.MrW[1] += wp * (rho[2] * W[i][0] - rho[0] * W[i][2]);
-            m.MrW[2] += wp * (rho[0] * W[i][1] - rho[1] * W[i][0]);
+            // B1 += w rho x Y
+            m.B1[0] += rw[1] * Y[i][2] - rw[2] * Y[i][1];
+            m.B1[1] += rw[2] * Y[i][0] - rw[0] * Y[i][2];
+            m.B1[2] += rw[0] * Y[i][1] - rw[1] * Y[i][0];
+        }
+    }
+    // K moments from the sums over the test points (Dp = dc + rho):
+    //   MW = dc A0 + A1 - B0,  MX = dc x B0 + B1,  MrW = A1 x dc - B1,  MrX = -dc.B1
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        Mom<T> &m = mm[i];
+        cx<T> MW[3], MX[3], MrW[3];
+        for (int d = 0; d < 3; ++d) MW[d] = dc[d] * m.A0 + m.A1[d] - m.B0[d];
+        MX[0] = dc[1] * m.B0[2] - dc[2] * m.B0[1] + m.B1[0];
+        MX[1] = dc[2] * m.B0[0] - dc[0] * m.B0[2] + m.B1[1];
+        MX[2] = dc[0] * m.B0[1] - dc[1] * m.B0[0] + m.B1[2];
+        MrW[0] = m.A1[1] * dc[2] - m.A1[2] * dc[1] - m.B1[0];
+        MrW[1] = m.A1[2] * dc[0] - m.A1[0] * dc[2] - m.B1[1];
+        MrW[2] = m.A1[0] * dc[1] - m.A1[1] * dc[0] - m.B1[2];
+        m.MrX = -(dc[0] * m.B1[0] + dc[1] * m.B1[1] + dc[2] * m.B1[2]);
+        for (int d = 0; d < 3; ++d) {
+            m.MW[d] = MW[d];
+            m.MX[d] = MX[d];
+            m.MrW[d] = MrW[d];
         }
     }
     // local vertex offsets and coefficients
-    T pa[3][3], pb[3][3], ca[3], cb[3];
+    T pa[3][3], pb[3][3], cc[3][3], papb[3][3];
     for (int a = 0; a < 3; ++a) {
         for (int d = 0; d < 3; ++d) {
             pa[a][d] = sp[3 * a + d] - ct[d];
             pb[a][d] = rs[TR_P + 3 * a + d] - cs[d];
         }
-        ca[a] = sc[a];
-        cb[a] = rs[TR_C + a];
     }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            cc[a][b] = sc[a] * rs[TR_C + b];
+            papb[a][b] = pa[a][0] * pb[b][0] + pa[a][1] * pb[b][1] + pa[a][2] * pb[b][2];
+        }
+    // Ks = K1 + K2, Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2
     cx<T> out[NCOMP];
     for (int c = 0; c < NCOMP; ++c) out[c] = cx<T>(0, 0);
-    // Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2
 #pragma unroll
     for (int i = 0; i < 2; ++i)
-        fold_entries<T>(mm[i], kr[i], ki[i], cx<T>(md.fk2r[i], md.fk2i[i]), ca, cb, pa, pb,
+        fold_entries<T>(mm[i], kr[i], ki[i], cx<T>(md.fk2r[i], md.fk2i[i]), cc, papb, pa, pb,
                         cx<T>(md.wTar[i], md.wTai[i]), cx<T>(md.wTbr[i], md.wTbi[i]), out);
     for (int c = 0; c < NCOMP; ++c) Zloc[c * plane + base] = out[c];
 }
@@ -639,7 +673,7 @@ struct AsmJob {
     MediaT<T> mdt;
     Media md;
     double alpha;
-    int nt, nstrip;
+    int nt, strip, nstrip;   // far tasks: trial triangles per task (multiple of 32), tasks per test triangle
     int64_t ne, far0, near0, row0;   // first far task, near pair and gather row of the job
 };
 
@@ -664,33 +698,91 @@ __device__ __forceinline__ bool share_cell(const int32_t *__restrict__ tc, int t
     return r;
 }
 
-// Far pairs of all meshes: persistent CTAs take tasks (mesh, test triangle,
-// strip of blockDim.x trial triangles) from an atomic counter, so meshes of
-// uneven size share the GPU without a tail per mesh.
+// Far pairs of all meshes: persistent warps take tasks (mesh, test triangle,
+// strip of trial triangles) from an atomic counter, so meshes of uneven size
+// share the GPU without a tail per mesh.  A warp works through its task 32
+// trial triangles at a time; each item (test triangle and 32 trial records)
+// is staged in the warp's own shared memory by asynchronous copies, the next
+// item (the task's next 32, or the first 32 of a newly taken task) while the
+// current one is computed, so warps never wait on one another and rarely on
+// memory.
 template <typename T>
-__global__ void __launch_bounds__(128, 3) k_far(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t ntasks,
-                                                   unsigned long long *__restrict__ counter) {
-    __shared__ FarShared<T> S;
-    __shared__ int64_t s_task;
-    while (true) {
-        if (threadIdx.x == 0) s_task = (int64_t)atomicAdd(counter, 1ull);
-        __syncthreads();
-        const int64_t task = s_task;
-        if (task >= ntasks) break;
-        const AsmJob<T> &J = jobs[find_job<T, &AsmJob<T>::far0>(jobs, njobs, task)];
-        const int64_t local = task - J.far0;
-        const int t = (int)(local / J.nstrip), s = (int)(local % J.nstrip) * blockDim.x + threadIdx.x;
-        far_load(S, J.rec, J.rec64, J.vid, t);
-        __syncthreads();
-        if (s < J.nt) {
-            if (J.tri_cell && !share_cell(J.tri_cell, t, s)) {
-                const int64_t plane = (int64_t)J.nt * J.nt, base = (int64_t)t * J.nt + s;
-                for (int c = 0; c < NCOMP; ++c) J.Zloc[c * plane + base] = cx<T>(0, 0);
-            } else {
-                far_pair(S, J.nt, J.rec, J.rec64, J.vid, J.alpha, J.mdt, J.Zloc, t, s);
+__host__ __device__ constexpr int far_warps() { return sizeof(T) == 4 ? 4 : 2; }
+template <typename T>
+constexpr size_t far_smem() { return (size_t)2 * far_warps<T>() * sizeof(FarStage<T>); }
+
+template <typename T>
+__device__ __forceinline__ void far_stage(FarStage<T> &S, const AsmJob<T> &J, int t, int s0, int cnt, int lane) {
+    for (int i = lane; i < TRI_REC; i += 32) {
+        cp_async<sizeof(T)>(&S.trec[i], J.rec + (int64_t)t * TRI_REC + i);
+        cp_async<8>(&S.trec64[i], J.rec64 + (int64_t)t * TRI_REC + i);
+    }
+    if (lane < 3) cp_async<4>(&S.tv[lane], J.vid + 3 * (int64_t)t + lane);
+    const T *src = J.rec + (int64_t)s0 * TRI_REC;
+#pragma unroll 4
+    for (int idx = lane; idx < cnt * TRI_REC; idx += 32)
+        cp_async<sizeof(T)>(&S.trial[idx / TRI_REC][idx % TRI_REC], src + idx);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// FP32: three blocks of four warps per SM (168 registers) for more warps in
+// flight; FP64: four blocks of two warps, where the wider accumulators would
+// otherwise spill.
+template <typename T>
+__global__ void __launch_bounds__(32 * far_warps<T>(), sizeof(T) == 4 ? 3 : 4)
+    k_far(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t ntasks, unsigned long long *__restrict__ counter) {
+    extern __shared__ __align__(16) unsigned char far_raw[];
+    const int lane = threadIdx.x & 31;
+    FarStage<T> *stage = reinterpret_cast<FarStage<T> *>(far_raw) + 2 * (threadIdx.x >> 5);
+    // the task being staged: job, test triangle, end of its strip
+    int tj = 0, tt = 0, tse = 0;
+    auto grab = [&](int &s0) -> bool {
+        unsigned long long task = 0;
+        if (lane == 0) task = atomicAdd(counter, 1ull);
+        task = __shfl_sync(0xffffffffu, task, 0);
+        if ((int64_t)task >= ntasks) return false;
+        tj = find_job<T, &AsmJob<T>::far0>(jobs, njobs, (int64_t)task);
+        const AsmJob<T> &J = jobs[tj];
+        const int64_t local = (int64_t)task - J.far0;
+        tt = (int)(local / J.nstrip);
+        s0 = (int)(local % J.nstrip) * J.strip;
+        tse = min(s0 + J.strip, J.nt);
+        return true;
+    };
+    int cs0 = 0;
+    if (!grab(cs0)) return;
+    int cj = tj, ct = tt, ccnt = min(32, tse - cs0);
+    far_stage(stage[0], jobs[cj], ct, cs0, ccnt, lane);
+    for (int b = 0;; b ^= 1) {
+        int ns0 = cs0 + 32;
+        bool more = ns0 < tse;
+        if (!more) more = grab(ns0);
+        const int nj = tj, nt_ = tt, ncnt = more ? min(32, tse - ns0) : 0;
+        if (more) {
+            far_stage(stage[b ^ 1], jobs[nj], nt_, ns0, ncnt, lane);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncwarp();
+        {
+            const AsmJob<T> &J = jobs[cj];
+            const int s = cs0 + lane;
+            if (lane < ccnt) {
+                if (J.tri_cell && !share_cell(J.tri_cell, ct, s)) {
+                    const int64_t plane = (int64_t)J.nt * J.nt, base = (int64_t)ct * J.nt + s;
+                    for (int c = 0; c < NCOMP; ++c) J.Zloc[c * plane + base] = cx<T>(0, 0);
+                } else {
+                    far_pair(stage[b], J.nt, stage[b].trial[lane], J.rec64, J.vid, J.alpha, J.mdt, J.Zloc, ct, s);
+                }
             }
         }
-        __syncthreads();   // S and s_task are rewritten by the next task
+        __syncwarp();   // the stage is restaged two items later
+        if (!more) break;
+        cj = nj;
+        ct = nt_;
+        cs0 = ns0;
+        ccnt = ncnt;
     }
 }
 
@@ -756,8 +848,9 @@ template void assemble_rwg<double>(Mesh &, z64 *, cudaStream_t, bool);
 template void assemble_rwg<float>(Mesh &, c32 *, cudaStream_t, bool);
 // Local blocks, far/near pairs and RWG gather of several meshes, one launch
 // per stage.  The far stage's strip width (trial triangles per task) is
-// picked once per device and precision by timing the candidates on the first
-// batch (every candidate writes the same values, so no run is repeated).
+// picked once per device and precision by timing the candidates, twice each,
+// on the first batch (every candidate writes the same values, so the batch
+// is not run again afterwards).
 template <typename T>
 void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st,
                         bool diag_cells) {
@@ -805,19 +898,26 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
     const std::string key = std::string("far_strip_") + (sizeof(T) == 8 ? "f64" : "f32") + "_dev" + std::to_string(dev);
     int tuned = tuning_get(key);
     const std::vector<int> cands = tuned > 0 ? std::vector<int>{tuned} : std::vector<int>{32, 64, 128};
-    float best_ms = 1e30f;
-    int best = cands[0];
-    for (int W : cands) {
+    std::vector<float> t_ms(cands.size(), 1e30f);
+    // while tuning, every candidate runs twice (the faster run counts) so that
+    // a first-launch delay or one noisy timing does not decide
+    const int reps = tuned > 0 ? 1 : 2;
+    for (int rep = 0; rep < reps; ++rep)
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+        const int W = cands[ci];
         int64_t ntask = 0;
         for (auto &J : jobs) {
+            J.strip = W;
             J.nstrip = (J.nt + W - 1) / W;
             J.far0 = ntask;
             ntask += (int64_t)J.nt * J.nstrip;
         }
         CBFM_CUDA(cudaMemcpyAsync(djobs.p, jobs.data(), sizeof(AsmJob<T>) * nj, cudaMemcpyHostToDevice, st));
         CBFM_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), st));
+        constexpr int FB = 32 * far_warps<T>();
+        CBFM_CUDA(cudaFuncSetAttribute(k_far<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)far_smem<T>()));
         int occ = 0;
-        CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_far<T>, W, 0));
+        CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_far<T>, FB, far_smem<T>()));
         const unsigned grid = (unsigned)std::max(1, occ) * (unsigned)nsm;
         cudaEvent_t e0, e1;
         CBFM_CUDA(cudaEventCreate(&e0));
@@ -825,7 +925,7 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
         CBFM_CUDA(cudaEventRecord(e0, st));
         {
             ProfScope ps_("k_far", st);
-            k_far<T><<<grid, W, 0, st>>>(djobs.p, nj, ntask, counter.p);
+            k_far<T><<<grid, FB, far_smem<T>(), st>>>(djobs.p, nj, ntask, counter.p);
             launched("k_far");
         }
         CBFM_CUDA(cudaEventRecord(e1, st));
@@ -834,12 +934,14 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
         CBFM_CUDA(cudaEventElapsedTime(&ms_, e0, e1));
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        if (ms_ < best_ms) {
-            best_ms = ms_;
-            best = W;
-        }
+        t_ms[ci] = std::min(t_ms[ci], ms_);
     }
-    if (tuned <= 0) tuning_set(key, best);
+    if (tuned <= 0) {
+        size_t bi = 0;
+        for (size_t ci = 1; ci < cands.size(); ++ci)
+            if (t_ms[ci] < t_ms[bi]) bi = ci;
+        tuning_set(key, cands[bi]);
+    }
     prof_add_work("k_far", far_flop, far_bytes);
     if (npairs > 0) {
         int occ = 0;
