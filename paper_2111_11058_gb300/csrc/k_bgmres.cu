@@ -10,12 +10,14 @@
 // FP64 throughout except the operator product (complex64 B and FP32
 // accumulation in CBFM_MIXED):
 //   * block Arnoldi with block classical Gram-Schmidt applied twice (BCGS2);
-//   * the new block is orthonormalised by Cholesky QR applied twice, the
-//     first Cholesky pivoted so that numerically dependent directions
-//     (saturation of the space, dependent right-hand sides) are dropped;
+//   * the new block is orthonormalised by Cholesky QR, the Cholesky pivoted
+//     so that numerically dependent directions (saturation of the space,
+//     dependent right-hand sides) are dropped, and repeated once (CholQR2)
+//     unless the first pass already gives ||Q^H Q - I||_F <= ORTH_TOL;
 //   * the block Hessenberg least-squares problem min ||E1 S - Hbar Z|| is
 //     solved through a QR of Hbar kept up to date block column by block
-//     column (block Gram-Schmidt + Cholesky QR, again applied twice).
+//     column (block Gram-Schmidt twice + Cholesky QR, repeated under the
+//     same test).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -433,6 +435,25 @@ __global__ void k_sub_rows(int64_t count, const z64 *__restrict__ a, const z64 *
     if (i < count) out[i] = a[i] - b[i];
 }
 
+// ||M - I||_F of an m x m matrix (one block; fixed summation order)
+__global__ void __launch_bounds__(256) k_gram_dev(int m, const z64 *__restrict__ M, double *__restrict__ out) {
+    __shared__ double part[8];
+    double s = 0.0;
+    for (int idx = threadIdx.x; idx < m * m; idx += 256) {
+        z64 v = M[idx];
+        if (idx / m == idx % m) v.re -= 1.0;
+        s += v.re * v.re + v.im * v.im;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += part[w];
+        *out = sqrt(t);
+    }
+}
+
 __global__ void k_ones(int n, int *a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = 1;
@@ -444,8 +465,24 @@ struct Ctx {
     cudaStream_t st;
     DevBuf<z64> M, R, Rinv, X, T1, Rf;
     DevBuf<int> perm, rank, err;
-    DevBuf<double> rnrm, scale;
+    DevBuf<double> rnrm, scale, dev;
 };
+
+// Cholesky QR applies its second pass only where the first leaves the block
+// visibly non-orthonormal: the second pass changes Q by about ||Q1^H Q1 - I||,
+// so below this bound on that Frobenius norm (and hence on the 2-norm) the
+// first pass is kept.
+constexpr double ORTH_TOL = 1e-12;
+
+// ||M - I||_F of the m x m Gram matrix in ctx.M (host sync).
+double gram_dev(Ctx &c, int m) {
+    k_gram_dev<<<1, 256, 0, c.st>>>(m, c.M.p, c.dev.p);
+    launched("k_gram_dev");
+    double h = 0.0;
+    CBFM_CUDA(cudaMemcpyAsync(&h, c.dev.p, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    CBFM_CUDA(cudaStreamSynchronize(c.st));
+    return h;
+}
 
 // Pivoted / plain Cholesky on the m x m Gram matrix already in ctx.M; returns rank (host sync).
 int pchol(Ctx &c, int m, double tol, bool pivot) {
@@ -484,8 +521,9 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
 
 // Rank-revealing orthonormalisation of m row vectors W (m x n, ld n; W is
 // overwritten): rows with norm <= drop * ref are treated as exhausted, the
-// others are scaled to unit norm, then Cholesky QR twice (the first Cholesky
-// pivoted, dropping directions whose scaled Gram pivot falls below tol).
+// others are scaled to unit norm, then Cholesky QR (the Cholesky pivoted,
+// dropping directions whose scaled Gram pivot falls below tol), repeated
+// without pivoting unless the first pass is orthonormal to ORTH_TOL.
 // Q (r x n) goes to Qdst and Rfull (r x m, ld m) satisfies
 // W_in[c] = sum_i Rfull[i][c] Q[i] up to the dropped parts.  Returns r.
 int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double tol, double ref, double drop) {
@@ -515,8 +553,16 @@ int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double
     launched("k_unpermute_r");
     // Q1 = X W  -> T1 (r x n)
     gemm_grouped<double>({GemmDesc{r, n, m, 0, m, 0, n, 0, n}}, 0, 0, c.X.p, W, c.T1.p, false, c.st);
-    // pass 2 (no pivoting) on Q1
+    // pass 2 (no pivoting) on Q1, unless Q1 is already orthonormal to ORTH_TOL
     gemm_grouped<double>({GemmDesc{r, r, n, 0, n, 0, n, 0, r}}, 3, 1, c.T1.p, c.T1.p, c.M.p, false, c.st);
+    if (gram_dev(c, r) <= ORTH_TOL) {
+        CBFM_CUDA(cudaMemcpyAsync(Qdst, c.T1.p, sizeof(z64) * r * n, cudaMemcpyDeviceToDevice, c.st));
+        k_copy2d<<<nb((int64_t)r * m), 256, 0, c.st>>>(r, m, c.Rf.p, m, Rfull, m, 0);
+        launched("k_copy2d");
+        k_scale_cols<<<nb((int64_t)r * m), 256, 0, c.st>>>(r, m, Rfull, c.scale.p);
+        launched("k_scale_cols");
+        return r;
+    }
     const int r2 = pchol(c, r, 0.0, false);
     if (r2 != r) throw Fail{CBFM_ESINGULAR, "block GMRES: second Cholesky QR pass lost rank"};
     // Q = Rinv2^T Q1 : X2[i][l] = Rinv2[l][i]  (identity permutation)
@@ -530,14 +576,16 @@ int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double
     return r;
 }
 
-// Cholesky QR (twice) of the p columns of a d x p matrix H (ld ldh) in place:
+// Cholesky QR of the p columns of a d x p matrix H (ld ldh) in place,
+// repeated unless the first pass is orthonormal to ORTH_TOL:
 // H <- Q (d x p), Rout (p x p, ld ldr) with H_in = Q Rout; RinvOut (p x p, ld
-// ldr) = Rout^{-1} (= R1^{-1} R2^{-1} from the two passes).  The Cholesky
+// ldr) = Rout^{-1} (= R1^{-1} R2^{-1} after two passes).  The Cholesky
 // factors of ctx have leading dimension p.
 void cholqr2_cols(Ctx &c, z64 *H, int d, int p, int64_t ldh, z64 *Rout, z64 *RinvOut, int64_t ldr,
                   DevBuf<z64> &tmp) {
     for (int pass = 0; pass < 2; ++pass) {
         gemm_grouped<double>({GemmDesc{p, p, d, 0, ldh, 0, ldh, 0, p}}, 2, 0, H, H, c.M.p, false, c.st);
+        if (pass == 1 && gram_dev(c, p) <= ORTH_TOL) break;   // the first pass is orthonormal already
         const int r = pchol(c, p, 0.0, false);
         if (r != p) throw Fail{CBFM_ESINGULAR, "block GMRES: block Hessenberg lost column rank"};
         // H <- H Rinv  (via tmp, ld p)
@@ -588,6 +636,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     CBFM_CUDA(cudaMemsetAsync(c.err.p, 0, sizeof(int), st));
     c.rnrm.alloc(p);
     c.scale.alloc(p);
+    c.dev.alloc(1);
     DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw;
     DevBuf<double> bnorm, rnorm;
     DevBuf<int> ones;
