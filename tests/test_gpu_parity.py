@@ -288,6 +288,29 @@ def test_block_matches_per_rhs_many_and_dependent(P, c1):
     assert np.allclose(b.j[:, -2:], b.j[:, :2], rtol=0, atol=1e-9 * np.abs(b.j).max())
 
 
+def test_block_nearly_dependent_rhs(P, c1):
+    """Plane waves 1e-4 rad apart give a right-hand-side block of condition
+    ~5e4: one Cholesky QR pass leaves it about u kappa^2 ~ 1e-7 away from
+    orthonormal, far above the 1e-12 under which the second pass is skipped,
+    so both passes run (while the smallest pivot, ~3e-10 of the scaled Gram
+    diagonal, stays far above the 1e-14 drop).  Block and per-right-hand-side
+    GMRES reach the same solutions."""
+    gm = _gpu_mesh(P, c1)
+    red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
+    P.cmp_setup(red)
+    exc = W.plane_wave_set(W.fibonacci_dirs(6))
+    near = exc.copy()
+    near[:, 0] += 1e-4
+    exc = np.vstack([exc, near])
+    v = OMo.rhs(c1["m"], exc)
+    s = np.linalg.svd(v / np.linalg.norm(v, axis=0), compute_uv=False)
+    assert 1e4 < s[0] / s[-1] < 1e6
+    a = P.solve(red, exc, tol=1e-10, solver=P.PER_RHS)
+    b = P.solve(red, exc, tol=1e-10, solver=P.BLOCK)
+    err = np.linalg.norm(a.j - b.j, axis=0) / np.linalg.norm(a.j, axis=0)
+    assert err.max() < 1e-7
+
+
 def test_block_single_rhs_is_gmres(P, c1):
     gm = _gpu_mesh(P, c1)
     red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), P.FP64)
