@@ -762,6 +762,248 @@ void gemm_sk(const std::vector<GemmDesc> &g, int opA, int opB, const z64 *A, con
     }
 }
 
+// ------------------------------------------------ blocked Gauss-Jordan
+// Inverse by Gauss-Jordan with GJB x GJB block pivots and no row exchanges
+// between blocks:  with D = A_kk^{-1},
+//   A_kj <- D A_kj,  A_ij <- A_ij - A_ik D A_kj,  A_ik <- -A_ik D,  A_kk <- D.
+// The products are the FP64 stream-K GEMMs; only the diagonal-block
+// inverses are serial.  Used where the block pivots are safe (checked), else
+// the pivoted sweep above.
+constexpr int GJB = 32;
+
+// column panel C = A[:, k0:k0+b] (n x b, ld b) and row panel Rw = A[k0:k0+b, :] (b x n, ld n), per matrix
+__global__ void k_gjb_panels(int n, int k0, int b, const z64 *__restrict__ A, z64 *__restrict__ C,
+                             z64 *__restrict__ Rw) {
+    const int t = blockIdx.y;
+    A += (int64_t)t * n * n;
+    C += (int64_t)t * n * b;
+    Rw += (int64_t)t * b * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * b;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / b, j = idx % b;
+        C[idx] = A[i * n + k0 + j];
+        const int64_t r = idx / n, c = idx % n;
+        Rw[idx] = A[(k0 + r) * n + c];
+    }
+}
+
+// D = inverse of the b x b diagonal block Rw[:, k0:k0+b] (ld n), one CTA per
+// matrix: Gauss-Jordan in place in shared memory with partial pivoting inside
+// the block (row exchanges undone on the columns at the end).  A pivot below
+// 1e-13 of the block's largest entry sets *flag.  The column block k of A is
+// zeroed (it is accumulated into next; its old values are in the panel copy).
+__global__ void __launch_bounds__(256) k_gjb_inv(int n, int k0, int b, const z64 *__restrict__ Rw,
+                                                 z64 *__restrict__ D, int *__restrict__ flag,
+                                                 z64 *__restrict__ A) {
+    __shared__ z64 a[GJB][GJB + 1];
+    __shared__ z64 fcol[GJB];
+    __shared__ int perm[GJB];
+    __shared__ int s_p;
+    __shared__ double s_amax;
+    __shared__ z64 s_pinv;
+    const int t = blockIdx.x;
+    Rw += (int64_t)t * b * n;
+    D += (int64_t)t * GJB * GJB;
+    A += (int64_t)t * n * n;
+    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) a[idx / b][idx % b] = Rw[(idx / b) * (int64_t)n + k0 + idx % b];
+    for (int idx = threadIdx.x; idx < n * b; idx += blockDim.x) A[(int64_t)(idx / b) * n + k0 + idx % b] = z64(0.0, 0.0);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double m = 0.0;
+        for (int idx = threadIdx.x; idx < b * b; idx += 32) m = fmax(m, norm2(a[idx / b][idx % b]));
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) s_amax = m;
+    }
+    __syncthreads();
+    for (int k = 0; k < b; ++k) {
+        if (threadIdx.x < 32) {   // pivot: largest |a[r][k]|^2, r >= k (first on ties); the bit
+                                  // patterns of non-negative doubles order as integers
+            long long bv = -1;
+            int bp = k;
+            for (int r = k + threadIdx.x; r < b; r += 32) {
+                const long long v = __double_as_longlong(norm2(a[r][k]));
+                if (v > bv) {
+                    bv = v;
+                    bp = r;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+                if (ov > bv || (ov == bv && op < bp)) {
+                    bv = ov;
+                    bp = op;
+                }
+            }
+            if (threadIdx.x == 0) {
+                s_p = bp;
+                perm[k] = bp;
+                if (!(__longlong_as_double(bv) > 1e-26 * s_amax)) atomicExch(flag, 1);   // |pivot| < 1e-13 max|entry|
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int c = threadIdx.x; c < b; c += blockDim.x) {
+                const z64 u = a[k][c];
+                a[k][c] = a[p][c];
+                a[p][c] = u;
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) {   // one reciprocal per pivot (an FP64 division is long on GB300)
+            const z64 piv = a[k][k];
+            s_pinv = norm2(piv) > 0.0 ? cdiv(z64(1.0, 0.0), piv) : z64(0.0, 0.0);
+        }
+        __syncthreads();
+        const z64 pinv = s_pinv;
+        // row k scaled (a[k][k] becomes 1/piv), then every other row eliminated
+        for (int c = threadIdx.x; c < b; c += blockDim.x) a[k][c] = (c == k) ? pinv : a[k][c] * pinv;
+        for (int r = threadIdx.x; r < b; r += blockDim.x) fcol[r] = a[r][k];   // multipliers, read before any write
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+            const int r = idx / b, c = idx % b;
+            if (r == k) continue;
+            const z64 f = fcol[r];
+            a[r][c] = (c == k) ? -(f * a[k][k]) : a[r][c] - f * a[k][c];
+        }
+        __syncthreads();
+    }
+    // undo the row exchanges as column exchanges, in reverse order
+    for (int k = b - 1; k >= 0; --k) {
+        const int p = perm[k];
+        if (p != k)
+            for (int r = threadIdx.x; r < b; r += blockDim.x) {
+                const z64 u = a[r][k];
+                a[r][k] = a[r][p];
+                a[r][p] = u;
+            }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < GJB * GJB; idx += blockDim.x) {
+        const int r = idx / GJB, c = idx % GJB;
+        D[idx] = (r < b && c < b) ? a[r][c] : z64(0.0, 0.0);
+    }
+}
+
+// row block k of A <- Rwp (b x n); then A_kk <- D
+__global__ void k_gjb_place(int n, int k0, int b, const z64 *__restrict__ Rwp, const z64 *__restrict__ D,
+                            z64 *__restrict__ A) {
+    const int t = blockIdx.y;
+    A += (int64_t)t * n * n;
+    Rwp += (int64_t)t * b * n;
+    D += (int64_t)t * GJB * GJB;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)b * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / n, c = idx % n;
+        const bool diag = c >= k0 && c < k0 + b;
+        A[(k0 + r) * n + c] = diag ? D[r * GJB + (c - k0)] : Rwp[idx];
+    }
+}
+
+// probe vector x_i = cos(i) + j sin(2 i), and err[t] = ||y_t - x|| / ||x||
+__global__ void k_gjb_probe(int n, z64 *__restrict__ x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] = z64(cos((double)i), sin(2.0 * i));
+}
+__global__ void __launch_bounds__(256) k_gjb_err(int n, const z64 *__restrict__ y, const z64 *__restrict__ x,
+                                                 double *__restrict__ err) {
+    __shared__ double p0[8], p1[8];
+    const int t = blockIdx.x;
+    y += (int64_t)t * n;
+    double e = 0.0, r = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) {
+        e += norm2(y[i] - x[i]);
+        r += norm2(x[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        p0[threadIdx.x >> 5] = e;
+        p1[threadIdx.x >> 5] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double se = 0.0, sr = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            se += p0[w];
+            sr += p1[w];
+        }
+        err[t] = (se == se && sr > 0.0) ? sqrt(se / sr) : 1e300;   // NaN -> failure
+    }
+}
+
+// Blocked Gauss-Jordan of nbatch n x n matrices in place (inv: A on entry);
+// true when no diagonal block had a pivot below 1e-13 of its largest entry
+// and A^{-1} (A x) reproduces a fixed probe x to 1e-8 for every matrix.
+bool gj_blocked(int64_t n, int nbatch, const z64 *Aorig, z64 *inv, cudaStream_t st) {
+    DevBuf<z64> C, Rw, RD, x, z, y;
+    DevBuf<int> flag;
+    DevBuf<double> err;
+    C.alloc((size_t)nbatch * n * GJB);
+    Rw.alloc((size_t)nbatch * GJB * n);
+    // D A_kj (nbatch x b x n) followed by D (nbatch x GJB x GJB): one base
+    // pointer, so the update and the column block share a launch
+    RD.alloc((size_t)nbatch * GJB * n + (size_t)nbatch * GJB * GJB);
+    z64 *const Rwp = RD.p, *const D = RD.p + (size_t)nbatch * GJB * n;
+    const int64_t doff = (int64_t)nbatch * GJB * n;
+    flag.alloc(1);
+    CBFM_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    const unsigned nbk = (unsigned)std::min<int64_t>((n * GJB + 255) / 256, 1024);
+    for (int64_t k0 = 0; k0 < n; k0 += GJB) {
+        const int b = (int)std::min<int64_t>(GJB, n - k0);
+        k_gjb_panels<<<dim3(nbk, nbatch), 256, 0, st>>>((int)n, (int)k0, b, inv, C.p, Rw.p);
+        launched("k_gjb_panels");
+        {
+            ProfScope ps_("k_gjb_inv", st);
+            k_gjb_inv<<<nbatch, 256, 0, st>>>((int)n, (int)k0, b, Rw.p, D, flag.p, inv);
+            launched("k_gjb_inv");
+        }
+        std::vector<GemmDesc> dr, du;
+        const int64_t k1 = k0 + b;
+        for (int t = 0; t < nbatch; ++t) {
+            const int64_t tb = (int64_t)t * b * n, tc = (int64_t)t * n * b, td = (int64_t)t * GJB * GJB,
+                          tn = (int64_t)t * n * n;
+            dr.push_back(GemmDesc{b, n, b, td, GJB, tb, n, tb, n});   // Rwp = D Rw
+            // one launch, disjoint columns of A: A -= C Rwp left and right of column block k, and
+            // A[:, k] -= C D (the block was zeroed, so it becomes -C D)
+            if (k0 > 0) du.push_back(GemmDesc{n, k0, b, tc, b, tb, n, tn, n});
+            if (k1 < n) du.push_back(GemmDesc{n, n - k1, b, tc, b, tb + k1, n, tn + k1, n});
+            du.push_back(GemmDesc{n, b, b, tc, b, doff + td, GJB, tn + k0, n});
+        }
+        gemm_grouped<double>(dr, 0, 0, D, Rw.p, Rwp, false, st);
+        gemm_grouped<double>(du, 0, 0, C.p, RD.p, inv, true, st, -1.0);
+        k_gjb_place<<<dim3(nbk, nbatch), 256, 0, st>>>((int)n, (int)k0, b, Rwp, D, inv);
+        launched("k_gjb_place");
+    }
+    // probe: y = A^{-1} (A x)
+    x.alloc((size_t)n);
+    z.alloc((size_t)nbatch * n);
+    y.alloc((size_t)nbatch * n);
+    err.alloc((size_t)nbatch);
+    k_gjb_probe<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int)n, x.p);
+    launched("k_gjb_probe");
+    std::vector<GemmDesc> d1, d2;
+    for (int t = 0; t < nbatch; ++t) {
+        d1.push_back(GemmDesc{n, 1, n, (int64_t)t * n * n, n, 0, 1, (int64_t)t * n, 1});
+        d2.push_back(GemmDesc{n, 1, n, (int64_t)t * n * n, n, (int64_t)t * n, 1, (int64_t)t * n, 1});
+    }
+    gemm_grouped<double>(d1, 0, 0, Aorig, x.p, z.p, false, st);
+    gemm_grouped<double>(d2, 0, 0, inv, z.p, y.p, false, st);
+    k_gjb_err<<<nbatch, 256, 0, st>>>((int)n, y.p, x.p, err.p);
+    launched("k_gjb_err");
+    int hflag = 0;
+    std::vector<double> herr(nbatch);
+    CBFM_CUDA(cudaMemcpyAsync(&hflag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBFM_CUDA(cudaMemcpyAsync(herr.data(), err.p, sizeof(double) * nbatch, cudaMemcpyDeviceToHost, st));
+    CBFM_CUDA(cudaStreamSynchronize(st));
+    if (hflag) return false;
+    for (double e : herr)
+        if (!(e <= 1e-8)) return false;
+    return true;
+}
+
 }  // namespace
 
 template <typename T>
@@ -867,9 +1109,17 @@ void gauss_jordan_inverse(int64_t n, int nbatch, z64 *Aug, z64 *inv, int *d_info
     // nbatch matrices n x n, consecutive in `inv` (A on entry, A^{-1} on
     // return); Aug holds 2 nbatch n x n scratch matrices.  The batch shares
     // every launch.
+    //
+    // First the blocked form (block pivots, no exchanges between blocks: its
+    // work is GEMMs), kept when it passes its checks; otherwise the pivoted
+    // sweep below runs on the original matrices.
     if (n <= 0 || nbatch <= 0) return;
     CBFM_REQUIRE(n < (int64_t)GJ_IMASK, "Gauss-Jordan: matrix too large for the pivot key");
     CBFM_REQUIRE(nbatch <= 65535, "Gauss-Jordan: batch too large");
+    const size_t bytes = sizeof(z64) * (size_t)nbatch * n * n;
+    CBFM_CUDA(cudaMemcpyAsync(Aug, inv, bytes, cudaMemcpyDeviceToDevice, st));   // the originals
+    if (gj_blocked(n, nbatch, Aug, inv, st)) return;
+    CBFM_CUDA(cudaMemcpyAsync(inv, Aug, bytes, cudaMemcpyDeviceToDevice, st));
     z64 *b0 = Aug, *b1 = Aug + (int64_t)nbatch * n * n;
     DevBuf<unsigned long long> keys;
     DevBuf<int> pivrow, src;
