@@ -191,10 +191,24 @@ cbfm_status cbfm_red_export_noalloc(cbfm_red_t red, double *A, void *stream);
 
 /*
  * cbfm_cmp_setup -- CBF Gram matrix G^CBF = (C^JM)^H G_ffff C^MJ (paper Eq.
- * (CBF_Gram_matrix)) and its inverse by Gauss-Jordan elimination with partial
- * pivoting in FP64.  Returns CBFM_ESINGULAR on a zero pivot.
+ * (CBF_Gram_matrix)) and the inverse of each of its two diagonal halves in
+ * FP64 (the off-half blocks are zero): Gauss-Jordan elimination with 32 x 32
+ * block pivots (no row exchanges between blocks), kept when every diagonal
+ * block's pivots stay above 1e-13 of its largest entry and A^{-1}(A x)
+ * reproduces a fixed probe x to 1e-8; otherwise Gauss-Jordan with partial
+ * pivoting.  Returns CBFM_ESINGULAR on a zero pivot.
  */
 cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream);
+
+/*
+ * cbfm_gram_inverse -- the inverse routine of cbfm_cmp_setup applied to
+ * caller matrices: a testing hook for both of its paths (the paper has no
+ * counterpart).  A: nbatch complex128 row-major n x n matrices, consecutive,
+ * host or device (read only); Ainv: the inverses in the same layout, host or
+ * device, caller-owned.  Returns CBFM_ESINGULAR when a matrix is singular to
+ * working precision, CBFM_EINVAL on bad arguments.
+ */
+cbfm_status cbfm_gram_inverse(const double *A, int64_t n, int32_t nbatch, double *Ainv, void *stream);
 
 /* G^CBF as complex128 row-major (n_cbf, n_cbf), host or device. */
 cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream);

@@ -5,9 +5,9 @@ include/cbfm.h); `cbfm` is its thin Python binding, `build` compiles it and
 `serve` is the continuous-batching solve service built on the binding.
 """
 from .cbfm import (BLOCK, FP64, MIXED, MIXED_SIMT, PER_RHS, CbfmError, assemble_reduced, assemble_reduced_batch,
-                   build_cbfs, cbf_import, cmp_setup, launch_count, mesh, mesh_edges, profile, profile_read, solve,
-                   tuning)
+                   build_cbfs, cbf_import, cmp_setup, gram_inverse, launch_count, mesh, mesh_edges, profile,
+                   profile_read, solve, tuning)
 
 __all__ = ["BLOCK", "PER_RHS", "FP64", "MIXED", "MIXED_SIMT", "CbfmError", "assemble_reduced", "assemble_reduced_batch",
-           "build_cbfs", "cbf_import", "cmp_setup", "launch_count", "mesh", "mesh_edges", "profile", "profile_read",
+           "build_cbfs", "cbf_import", "cmp_setup", "gram_inverse", "launch_count", "mesh", "mesh_edges", "profile", "profile_read",
            "solve", "tuning"]

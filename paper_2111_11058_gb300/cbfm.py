@@ -68,6 +68,7 @@ def lib():
             "cbfm_red_export_noalloc": [_vp, _vp, _vp],
             "cbfm_cmp_setup": [_vp, _vp],
             "cbfm_gram_export": [_vp, _vp, _vp],
+            "cbfm_gram_inverse": [_vp, _i64, _i32, _vp, _vp],
             "cbfm_solve": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp],
         }
         for name, args in sig.items():
@@ -94,7 +95,7 @@ def exported_symbols():
     """Names of the C entry points declared in include/cbfm.h."""
     return ["cbfm_mesh", "cbfm_mesh_edges", "cbfm_mesh_info", "cbfm_mesh_cells", "cbfm_build_cbfs", "cbfm_cbf_import",
             "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_gram_export",
-            "cbfm_solve", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
+            "cbfm_gram_inverse", "cbfm_solve", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
             "cbfm_profile_read"]
 
 
@@ -125,6 +126,21 @@ def _ptr(a, dtype):
         return ctypes.c_void_p(a.data_ptr()), a
     arr = np.ascontiguousarray(a, dtype=dtype)
     return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def gram_inverse(A, stream=None) -> np.ndarray:
+    """cbfm_gram_inverse: inverses of a (nbatch, n, n) complex128 batch by the
+    routine cbfm_cmp_setup uses (testing hook)."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    if A.ndim == 2:
+        A = A[None]
+    nb, n, n2 = A.shape
+    if n != n2:
+        raise ValueError("square matrices expected")
+    out = np.zeros_like(A)
+    _check(lib().cbfm_gram_inverse(ctypes.c_void_p(A.ctypes.data), n, nb, ctypes.c_void_p(out.ctypes.data),
+                                   _stream(stream)))
+    return out
 
 
 def launch_count() -> int:

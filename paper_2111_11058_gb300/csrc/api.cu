@@ -973,6 +973,30 @@ cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
     });
 }
 
+cbfm_status cbfm_gram_inverse(const double *A, int64_t n, int32_t nbatch, double *Ainv, void *stream) {
+    return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
+        CBFM_REQUIRE(A && Ainv, "NULL matrix");
+        CBFM_REQUIRE(n >= 1 && nbatch >= 1, "n and nbatch must be positive");
+        cudaStream_t st = (cudaStream_t)stream;
+        const size_t cnt = (size_t)nbatch * n * n;
+        DevBuf<z64> blk, aug;
+        DevBuf<int> info;
+        blk.alloc(cnt);
+        aug.alloc(2 * cnt);
+        info.alloc(1);
+        CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int), st));
+        copy_in(blk.p, A, cnt * sizeof(z64), st);
+        gauss_jordan_inverse(n, nbatch, aug.p, blk.p, info.p, st);
+        int hinfo = 0;
+        CBFM_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        if (hinfo) throw Fail{CBFM_ESINGULAR, "matrix is singular"};
+        copy_out(Ainv, blk.p, cnt * sizeof(z64), st);
+        CBFM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
 cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream) {
     return guarded([&] {
         StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream

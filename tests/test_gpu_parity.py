@@ -259,6 +259,52 @@ def test_degenerate_eps1_matches_oracle(P):
     assert _peak_rcs_err(res.rcs.sum(-1), st + sp) < 1e-6
 
 
+# ------------------------------------------------ (G^CBF)^{-1} routine paths
+def _inv_path(P, A):
+    P.profile(True)
+    P.profile_read(reset=True)
+    X = P.gram_inverse(A)
+    prof = P.profile_read(reset=True)
+    P.profile(False)
+    return X, prof
+
+
+def test_gram_inverse_blocked_path(P):
+    """Two 70 x 70 matrices (three block steps, the last of 6 columns) whose
+    diagonal blocks need row exchanges inside the block (zero diagonal): the
+    blocked Gauss-Jordan is kept and matches numpy's inverse."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((2, 70, 70)) + 1j * rng.standard_normal((2, 70, 70))
+    for t in range(2):
+        np.fill_diagonal(A[t], 0.0)
+    X, prof = _inv_path(P, A)
+    assert "k_gjb_inv" in prof and "k_gj_sweep" not in prof
+    for t in range(2):
+        ref = np.linalg.inv(A[t])
+        assert np.abs(X[t] - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_gram_inverse_pivoted_fallback(P):
+    """A leading 32 x 32 block that is singular (zero) in an invertible matrix:
+    the block check fails and Gauss-Jordan with partial pivoting gives the
+    inverse."""
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((1, 64, 64)) + 1j * rng.standard_normal((1, 64, 64))
+    A[0, :32, :32] = 0.0
+    assert np.linalg.cond(A[0]) < 1e6
+    X, prof = _inv_path(P, A)
+    assert "k_gj_sweep" in prof
+    ref = np.linalg.inv(A[0])
+    assert np.abs(X[0] - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_gram_inverse_singular(P):
+    A = np.zeros((1, 40, 40), np.complex128)
+    A[0, :39, :39] = np.eye(39)
+    with pytest.raises(P.CbfmError):
+        P.gram_inverse(A)
+
+
 # ------------------------------------------------------------ block GMRES
 @pytest.mark.parametrize("prec,tol_rcs", [(0, 1e-8), (1, 1e-4)])
 def test_block_gmres_c1(P, c1, prec, tol_rcs):
