@@ -9,15 +9,18 @@
 //
 // FP64 throughout except the operator product (complex64 B and FP32
 // accumulation in CBFM_MIXED):
-//   * block Arnoldi with block classical Gram-Schmidt applied twice (BCGS2);
+//   * block Arnoldi with block classical Gram-Schmidt, repeated where one
+//     pass is not enough (BCGS2 with the second pass skipped when every
+//     vector kept GS_KEEP of its norm, or applied only when its coefficients
+//     exceed ORTH_TOL of the block);
 //   * the new block is orthonormalised by Cholesky QR, the Cholesky pivoted
 //     so that numerically dependent directions (saturation of the space,
 //     dependent right-hand sides) are dropped, and repeated once (CholQR2)
 //     unless the first pass already gives ||Q^H Q - I||_F <= ORTH_TOL;
 //   * the block Hessenberg least-squares problem min ||E1 S - Hbar Z|| is
 //     solved through a QR of Hbar kept up to date block column by block
-//     column (block Gram-Schmidt twice + Cholesky QR, repeated under the
-//     same test).
+//     column (block Gram-Schmidt and Cholesky QR, each repeated under the
+//     same tests).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -435,6 +438,22 @@ __global__ void k_sub_rows(int64_t count, const z64 *__restrict__ a, const z64 *
     if (i < count) out[i] = a[i] - b[i];
 }
 
+// ||X||_F of a rows x cols matrix (ld ld; one block; fixed summation order)
+__global__ void __launch_bounds__(256) k_fro(int rows, int cols, const z64 *__restrict__ X, int64_t ld,
+                                             double *__restrict__ out) {
+    __shared__ double part[8];
+    double s = 0.0;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)rows * cols; idx += 256) s += norm2(X[(idx / cols) * ld + idx % cols]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += part[w];
+        *out = sqrt(t);
+    }
+}
+
 // ||M - I||_F of an m x m matrix (one block; fixed summation order)
 __global__ void __launch_bounds__(256) k_gram_dev(int m, const z64 *__restrict__ M, double *__restrict__ out) {
     __shared__ double part[8];
@@ -473,6 +492,12 @@ struct Ctx {
 // so below this bound on that Frobenius norm (and hence on the 2-norm) the
 // first pass is kept.
 constexpr double ORTH_TOL = 1e-12;
+// Block Gram-Schmidt: one pass leaves a vector about u ||w0|| / ||w1|| away
+// from orthogonal to the basis, so the second pass is skipped when every
+// vector kept at least GS_KEEP of its norm (dimension factors included, well
+// under ORTH_TOL); otherwise its coefficients are formed and applied when
+// they exceed ORTH_TOL of the block.
+constexpr double GS_KEEP = 0.1;
 
 // ||M - I||_F of the m x m Gram matrix in ctx.M (host sync).
 double gram_dev(Ctx &c, int m) {
@@ -663,7 +688,31 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     CBFM_CUDA(cudaMemsetAsync(Y.p, 0, sizeof(z64) * p * n, st));
     k_rownorm<<<p, 256, 0, st>>>(n, d_b, bnorm.p);
     launched("k_rownorm");
-    std::vector<double> h_bn(p), h_rn(p);
+    std::vector<double> h_bn(p), h_rn(p), h_w1(p), h_h0(p), h_h1(p);
+    DevBuf<double> fro_out;
+    fro_out.alloc(1);
+    // ||X||_F of a rows x cols block (host sync)
+    auto fro = [&](int rows, int cols, const z64 *X, int64_t ld) {
+        k_fro<<<1, 256, 0, st>>>(rows, cols, X, ld, fro_out.p);
+        launched("k_fro");
+        double h = 0.0;
+        CBFM_CUDA(cudaMemcpyAsync(&h, fro_out.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        return h;
+    };
+    // sqrt of the sum of squares of the first k norms; the smallest ratio
+    // after / before over the vectors that had a norm
+    auto norm_sum = [](const std::vector<double> &v, int k) {
+        double a = 0.0;
+        for (int i = 0; i < k; ++i) a += v[i] * v[i];
+        return std::sqrt(a);
+    };
+    auto min_ratio = [](const std::vector<double> &after, const std::vector<double> &before, int k) {
+        double r = 1.0;
+        for (int i = 0; i < k; ++i)
+            if (before[i] > 0.0) r = std::min(r, after[i] / before[i]);
+        return r;
+    };
     CBFM_CUDA(cudaMemcpyAsync(h_bn.data(), bnorm.p, sizeof(double) * p, cudaMemcpyDeviceToHost, st));
     CBFM_CUDA(cudaStreamSynchronize(st));
 
@@ -719,10 +768,18 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             // block classical Gram-Schmidt, twice; HcT (pjc x d1) collects the coefficients
             for (int pass = 0; pass < 2; ++pass) {
                 gemm_grouped<double>({GemmDesc{pjc, d1, n, 0, n, 0, n, 0, dcap}}, 0, 2, W.p, V.p, tmp2.p, false, st);
+                if (pass == 1 && fro(pjc, (int)d1, tmp2.p, dcap) <= ORTH_TOL * norm_sum(h_w1, pjc)) break;
                 gemm_grouped<double>({GemmDesc{pjc, n, d1, 0, dcap, 0, n, 0, n}}, 0, 0, tmp2.p, V.p, W.p, true, st,
                                      -1.0);
                 k_copy2d<<<nb(pjc * d1), 256, 0, st>>>(pjc, (int)d1, tmp2.p, dcap, HcT.p, dcap, pass);
                 launched("k_copy2d");
+                if (pass == 0) {
+                    k_rownorm<<<pjc, 256, 0, st>>>(n, W.p, rnorm.p);
+                    launched("k_rownorm");
+                    CBFM_CUDA(cudaMemcpyAsync(h_w1.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
+                    CBFM_CUDA(cudaStreamSynchronize(st));
+                    if (min_ratio(h_w1, h_rn, pjc) >= GS_KEEP) break;
+                }
             }
             // orthonormalise the new block (pivoted: drops dependent directions)
             const int r = wref > 0.0 ? cholqr2_rows(c, W.p, pjc, n, V.p + d1 * n, Rw.p, rank_tol, wref, drop_tol) : 0;
@@ -750,11 +807,23 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
                     upd.push_back(GemmDesc{dims[r + 1] - dims[r], pjc, d0 - k0, dims[r] * dcap + k0, dcap, k0 * p,
                                            p, dims[r] * p, p});
                 }
+                k_colnorm<<<pjc, 256, 0, st>>>((int)d2, pjc, Hn.p, p, rnorm.p);   // before the projection
+                launched("k_colnorm");
+                CBFM_CUDA(cudaMemcpyAsync(h_h0.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
                 for (int pass = 0; pass < 2; ++pass) {
                     gemm_grouped<double>(proj, 2, 0, Qh.p, Hn.p, tmp2.p, false, st);
+                    if (pass == 1 && fro((int)d0, pjc, tmp2.p, p) <= ORTH_TOL * norm_sum(h_h1, pjc)) break;
                     gemm_grouped<double>(upd, 0, 0, Qh.p, tmp2.p, Hn.p, true, st, -1.0);
                     k_copy2d<<<nb(d0 * pjc), 256, 0, st>>>((int)d0, pjc, tmp2.p, p, Rh.p + d0, dcap, pass);
                     launched("k_copy2d");
+                    if (pass == 0) {
+                        k_colnorm<<<pjc, 256, 0, st>>>((int)d2, pjc, Hn.p, p, rnorm.p);
+                        launched("k_colnorm");
+                        CBFM_CUDA(cudaMemcpyAsync(h_h1.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost,
+                                                  st));
+                        CBFM_CUDA(cudaStreamSynchronize(st));
+                        if (min_ratio(h_h1, h_h0, pjc) >= GS_KEEP) break;
+                    }
                 }
             }
             cholqr2_cols(c, Hn.p, (int)d2, pjc, p, Rout.p, RinvBlk.p + d0 * p, p, tmp);
