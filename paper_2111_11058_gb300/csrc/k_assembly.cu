@@ -51,7 +51,17 @@ constexpr double FAR_FLOP_PER_POINT_PAIR = 170.0;
 struct Media {
     double k1r, k1i, k2r, k2i;
     double e1r, e1i, e2r, e2i;   // eta1, eta2
+    double f1r, f1i, f2r, f2i;   // 4 / k1^2, 4 / k2^2
+    double i1r, i1i, i2r, i2i;   // 1 / eta1, 1 / eta2
 };
+
+// the derived constants of a Media from k1, k2, eta1, eta2 (host)
+inline Media media_full(z64 k1, z64 k2, z64 e1, z64 e2) {
+    const z64 f1 = cdiv(z64(4.0, 0.0), k1 * k1), f2 = cdiv(z64(4.0, 0.0), k2 * k2);
+    const z64 i1 = cdiv(z64(1.0, 0.0), e1), i2 = cdiv(z64(1.0, 0.0), e2);
+    return Media{k1.re, k1.im, k2.re, k2.im, e1.re, e1.im, e2.re, e2.im,
+                 f1.re, f1.im, f2.re, f2.im, i1.re, i1.im, i2.re, i2.im};
+}
 
 // Per-medium constants in the arithmetic type of the far-pair kernel,
 // computed once on the host: k, 4/k^2 and the operator weights of T into
@@ -555,35 +565,46 @@ __device__ __forceinline__ void near_pair2(int t, int s, int nt, const double *_
         const double wp = A[TR_W + p];
         const double rr[3] = {r[0] - A[TR_CEN], r[1] - A[TR_CEN + 1], r[2] - A[TR_CEN + 2]};
         const double r2 = dot3(rr, rr);
+        // trial points: d = r - r', R, weights; shared by the two media.  On the
+        // mixed path the smooth remainders and their 7-point sums are FP32 and
+        // only the closed forms (and the sums with them) FP64.
+        T dq[7][3], Rq[7], wq[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            double dv[3];
+            sub3(r, B + TR_Q + 3 * q, dv);
+            for (int d = 0; d < 3; ++d) dq[q][d] = (T)dv[d];
+            if constexpr (sizeof(T) == 4) Rq[q] = sqrtf(dq[q][0] * dq[q][0] + dq[q][1] * dq[q][1] + dq[q][2] * dq[q][2]);
+            else Rq[q] = sqrt(dot3(dv, dv));
+            wq[q] = (T)B[TR_W + q];
+        }
 #pragma unroll
         for (int med = 0; med < 2; ++med) {
             const z64 k = med == 0 ? z64(md.k1r, md.k1i) : z64(md.k2r, md.k2i);
             const z64 kk = k * k;
-            z64 S0(I1 / (4.0 * PI), 0), Sr[3], Wv[3];
-            for (int d = 0; d < 3; ++d) {
-                Sr[d] = z64(Iv[d] / (4.0 * PI), 0);
-                Wv[d] = z64(-I3[d] / (4.0 * PI), 0) + kk * (Iv[d] / (8.0 * PI));
-            }
+            cx<T> g0(0, 0), gr[3], hw[3];   // sum w g, sum w g (-d), sum w h d over the trial points
+            for (int d = 0; d < 3; ++d) gr[d] = hw[d] = cx<T>(0, 0);
+#pragma unroll
             for (int q = 0; q < 7; ++q) {
-                double dv[3];
-                sub3(r, B + TR_Q + 3 * q, dv);
-                const double R = sqrt(dot3(dv, dv));
-                z64 gs, hs;
-                if constexpr (sizeof(T) == 4) {   // mixed path: smooth remainders in FP32
-                    c32 g32, h32;
-                    green_rems_f((float)k.re, (float)k.im, (float)R, g32, h32);
-                    gs = z64(g32.re, g32.im);
-                    hs = z64(h32.re, h32.im);
+                cx<T> gs, hs;
+                if constexpr (sizeof(T) == 4) {
+                    green_rems_f((float)k.re, (float)k.im, Rq[q], gs, hs);
                 } else {
-                    green_rems(k, R, gs, hs);
+                    green_rems(k, Rq[q], gs, hs);
                 }
-                gs = gs * B[TR_W + q];
-                hs = hs * B[TR_W + q];
-                S0 += gs;
+                gs = gs * wq[q];
+                hs = hs * wq[q];
+                g0 += gs;
                 for (int d = 0; d < 3; ++d) {
-                    Sr[d] += gs * (-dv[d]);
-                    Wv[d] += hs * dv[d];
+                    gr[d] += gs * (-dq[q][d]);
+                    hw[d] += hs * dq[q][d];
                 }
+            }
+            const z64 S0 = z64(I1 / (4.0 * PI) + (double)g0.re, (double)g0.im);
+            z64 Sr[3], Wv[3];
+            for (int d = 0; d < 3; ++d) {
+                Sr[d] = z64(Iv[d] / (4.0 * PI) + (double)gr[d].re, (double)gr[d].im);
+                Wv[d] = z64(-I3[d] / (4.0 * PI), 0) + kk * (Iv[d] / (8.0 * PI)) + z64((double)hw[d].re, (double)hw[d].im);
             }
             z64 *m = mom[med];
             const z64 wS0 = wp * S0;
@@ -641,11 +662,13 @@ __device__ __forceinline__ void near_pair2(int t, int s, int nt, const double *_
             const z64 *m = sm[slot][oo][med];
             const z64 k = med == 0 ? z64(md.k1r, md.k1i) : z64(md.k2r, md.k2i);
             const z64 eta = med == 0 ? z64(md.e1r, md.e1i) : z64(md.e2r, md.e2i);
+            const z64 f4k2 = med == 0 ? z64(md.f1r, md.f1i) : z64(md.f2r, md.f2i);   // 4 / k^2
+            const z64 ieta = med == 0 ? z64(md.i1r, md.i1i) : z64(md.i2r, md.i2i);   // 1 / eta
             z64 br = m[8] + m[4] - (P[0] * m[5] + P[1] * m[6] + P[2] * m[7]) -
-                     (PpQ[0] * m[1] + PpQ[1] * m[2] + PpQ[2] * m[3]) + PQ * m[0] - cdiv(z64(4, 0), k * k) * m[0];
+                     (PpQ[0] * m[1] + PpQ[1] * m[2] + PpQ[2] * m[3]) + PQ * m[0] - f4k2 * m[0];
             const z64 Tv = cc * (z64(k.im, -k.re) * br);
             ta += -eta * Tv;
-            tb += cdiv(Tv, eta);
+            tb += Tv * ieta;
             if (t != s)
                 ks += cc * (QmP[0] * m[12] + QmP[1] * m[13] + QmP[2] * m[14] + QxP[0] * m[9] + QxP[1] * m[10] +
                             QxP[2] * m[11]);
@@ -864,7 +887,7 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
         Mesh &m = *ms[k];
         const int nt = (int)m.h.nt;
         Zloc[k].alloc((size_t)NCOMP * nt * nt);
-        Media md{m.k1.re, m.k1.im, m.k2.re, m.k2.im, m.eta1.re, m.eta1.im, m.eta2.re, m.eta2.im};
+        const Media md = media_full(m.k1, m.k2, m.eta1, m.eta2);
         AsmJob<T> &J = jobs[k];
         if constexpr (sizeof(T) == 8) J.rec = (const T *)m.tri64.p;
         else J.rec = (const T *)m.tri32.p;
