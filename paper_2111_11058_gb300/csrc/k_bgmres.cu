@@ -473,11 +473,6 @@ __global__ void __launch_bounds__(256) k_gram_dev(int m, const z64 *__restrict__
     }
 }
 
-__global__ void k_ones(int n, int *a) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = 1;
-}
-
 inline unsigned nb(int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096)); }
 
 struct Ctx {
@@ -635,6 +630,30 @@ void cholqr2_cols(Ctx &c, z64 *H, int d, int p, int64_t ldh, z64 *Rout, z64 *Rin
     }
 }
 
+// Row vectors times a matrix, out[r] = M in[r] for r < rows (M n x n
+// row-major, rows of length n), as one GEMM out = in M^T: complex64 M with
+// the rows rounded to complex64 and FP32 accumulation when M32 is given,
+// else FP64.  With `halves` only the two diagonal halves of M are used (M is
+// block diagonal: the inverse of G^CBF).  s_in, s_out: rows x n scratch.
+void rows_times(int64_t n, const z64 *M64, const c32 *M32, const z64 *in, z64 *out, int rows, bool halves,
+                cudaStream_t st, c32 *s_in, c32 *s_out) {
+    std::vector<GemmDesc> g;
+    if (halves) {
+        const int64_t h = n / 2;
+        g.push_back(GemmDesc{rows, h, h, 0, n, 0, n, 0, n});
+        g.push_back(GemmDesc{rows, h, h, h, n, h * n + h, n, h, n});
+    } else {
+        g.push_back(GemmDesc{rows, n, n, 0, n, 0, n, 0, n});
+    }
+    if (M32) {
+        launch_z64_to_c32(in, s_in, (int64_t)rows * n, st);
+        gemm_grouped<float>(g, 0, 1, s_in, M32, s_out, false, st);
+        launch_c32_to_z64(s_out, out, (int64_t)rows * n, st);
+    } else {
+        gemm_grouped<double>(g, 0, 1, in, M64, out, false, st);
+    }
+}
+
 }  // namespace
 
 GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp, z64 *d_x,
@@ -664,7 +683,6 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     c.dev.alloc(1);
     DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw;
     DevBuf<double> bnorm, rnorm;
-    DevBuf<int> ones;
     V.alloc((size_t)dcap * n);
     W.alloc((size_t)p * n);
     HcT.alloc((size_t)p * dcap);
@@ -682,9 +700,6 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     Rw.alloc((size_t)p * p);
     bnorm.alloc(p);
     rnorm.alloc(p);
-    ones.alloc(p);
-    k_ones<<<(p + 127) / 128, 128, 0, st>>>(p, ones.p);
-    launched("k_ones");
     CBFM_CUDA(cudaMemsetAsync(Y.p, 0, sizeof(z64) * p * n, st));
     k_rownorm<<<p, 256, 0, st>>>(n, d_b, bnorm.p);
     launched("k_rownorm");
@@ -716,9 +731,15 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     CBFM_CUDA(cudaMemcpyAsync(h_bn.data(), bnorm.p, sizeof(double) * p, cudaMemcpyDeviceToHost, st));
     CBFM_CUDA(cudaStreamSynchronize(st));
 
+    DevBuf<c32> s_in, s_out;   // complex64 rows for the mixed-precision products
+    if (rd.prec != CBFM_FP64) {
+        s_in.alloc((size_t)p * n);
+        s_out.alloc((size_t)p * n);
+    }
     auto applyB = [&](const z64 *in, z64 *out, int rows) {
-        if (rd.prec != CBFM_FP64) apply_rows(rd, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, rows, ones.p, st);
-        else apply_rows(rd, use_cmp ? rd.B64.p : rd.A64.p, nullptr, in, out, rows, ones.p, st);
+        if (rd.prec != CBFM_FP64)
+            rows_times(n, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, rows, false, st, s_in.p, s_out.p);
+        else rows_times(n, use_cmp ? rd.B64.p : rd.A64.p, nullptr, in, out, rows, false, st, nullptr, nullptr);
     };
 
     GmresOut out;
@@ -873,7 +894,10 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
         if (breakdown) break;
     }
     // x = P y
-    if (use_cmp) apply_rows(rd, rd.Ginv.p, nullptr, Y.p, d_x, p, ones.p, st);
+    if (use_cmp) {   // G^CBF^{-1} is block diagonal (its two halves)
+        if (rd.prec != CBFM_FP64) rows_times(n, nullptr, rd.Ginv32.p, Y.p, d_x, p, true, st, s_in.p, s_out.p);
+        else rows_times(n, rd.Ginv.p, nullptr, Y.p, d_x, p, true, st, nullptr, nullptr);
+    }
     else CBFM_CUDA(cudaMemcpyAsync(d_x, Y.p, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
     CBFM_CUDA(cudaStreamSynchronize(st));
     for (int q = 0; q < p; ++q) out.iters[q] = conv_at[q] >= 0 ? conv_at[q] : -total_blocks - 1;
