@@ -1034,7 +1034,7 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
         DevBuf<z64> vE, vH, bt, b, x, jint;
         vE.alloc((size_t)ne * nrhs);
         vH.alloc((size_t)ne * nrhs);
-        launch_rhs(m, dexc.p, nrhs, vE.p, vH.p, st);
+        launch_rhs(m, dexc.p, nrhs, vE.p, vH.p, st, r->prec != CBFM_FP64);
         // b = (C^JM)^H v  -> (n x nrhs), then rows per rhs
         bt.alloc((size_t)n * nrhs);
         std::vector<GemmDesc> gE, gH;
@@ -1082,7 +1082,7 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
                 copy_in(dobs.p, obs, 2 * sizeof(double) * ndir, st);
             }
             drcs.alloc((size_t)nrhs * nd * 2);
-            launch_farfield(m, jint.p, nrhs, dobs.p, nd, mono, dexc.p, drcs.p, st);
+            launch_farfield(m, jint.p, nrhs, dobs.p, nd, mono, dexc.p, drcs.p, st, r->prec != CBFM_FP64);
             copy_out(rcs_out, drcs.p, sizeof(double) * nrhs * nd * 2, st);
         }
         if (j_out) {

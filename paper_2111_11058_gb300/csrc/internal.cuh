@@ -83,9 +83,10 @@ struct Red : HandleBase {
 void launch_tri_records(Mesh &m, const double *d_verts, const int32_t *d_tris, cudaStream_t st);
 void launch_near_pairs(Mesh &m, cudaStream_t st);
 void launch_gram_rows(Mesh &m, cudaStream_t st);
-void launch_rhs(const Mesh &m, const double *d_waves, int nw, z64 *vE, z64 *vH, cudaStream_t st);
+// f32: the plane-wave phase factors by FP32 reduced sin/cos (mixed-precision solve), else FP64
+void launch_rhs(const Mesh &m, const double *d_waves, int nw, z64 *vE, z64 *vH, cudaStream_t st, bool f32 = false);
 void launch_farfield(const Mesh &m, const z64 *j, int nrhs, const double *d_obs, int ndir, bool monostatic,
-                     const double *d_exc, double *d_rcs, cudaStream_t st);
+                     const double *d_exc, double *d_rcs, cudaStream_t st, bool f32 = false);
 
 // assembly (k_assembly.cu): local blocks of all triangle pairs, then the RWG
 // matrices Z_op (op = Ks, Ta, Tb), row-major ne x ne, internal edge order.

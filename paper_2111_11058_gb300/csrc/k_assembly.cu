@@ -95,21 +95,6 @@ MediaT<T> media_t(const Media &md) {
     return o;
 }
 
-// -------------------------------------------------------------- FP32 trig
-// sin/cos of x >= 0 with a two-constant Cody-Waite reduction by 2 pi (round
-// to nearest multiple with the 1.5*2^23 shifter) and the hardware
-// approximation on [-pi, pi].
-__device__ __forceinline__ void sincos_red(float x, float *s, float *c) {
-    const float INV2PI = 0.159154943091895335768883763372514362f;
-    const float TWOPI_HI = 6.28318548202514648437500f;      // float(2 pi)
-    const float TWOPI_LO = -1.7484555314695172e-7f;         // 2 pi - TWOPI_HI
-    const float SHIFT = 12582912.0f;                        // 1.5 * 2^23
-    float n = __fadd_rn(__fmaf_rn(x, INV2PI, SHIFT), -SHIFT);
-    float r = __fmaf_rn(-n, TWOPI_HI, x);
-    r = __fmaf_rn(-n, TWOPI_LO, r);
-    __sincosf(r, s, c);
-}
-__device__ __forceinline__ void sincos_red(double x, double *s, double *c) { sincos(x, s, c); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float exp_t(float x) { return __expf(x); }

@@ -163,25 +163,41 @@ __device__ inline void sph_basis(double th, double ph, double rh[3], double thh[
     phh[0] = -sp; phh[1] = cp; phh[2] = 0.0;
 }
 
+// Per wave w: r_hat (arrival direction), polarisation p and k_hat x p
+// (k_hat = -r_hat), 9 doubles.
+__global__ void k_wave_basis(int nw, const double *__restrict__ waves, double *__restrict__ wb) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    double rh[3], thh[3], phh[3];
+    sph_basis(waves[3 * w], waves[3 * w + 1], rh, thh, phh);
+    double sps, cps;
+    sincos(waves[3 * w + 2], &sps, &cps);
+    double p[3];
+    for (int d = 0; d < 3; ++d) p[d] = cps * thh[d] + sps * phh[d];
+    double *o = wb + 9 * (int64_t)w;
+    for (int d = 0; d < 3; ++d) {
+        o[d] = rh[d];
+        o[3 + d] = p[d];
+    }
+    o[6] = -(rh[1] * p[2] - rh[2] * p[1]);
+    o[7] = -(rh[2] * p[0] - rh[0] * p[2]);
+    o[8] = -(rh[0] * p[1] - rh[1] * p[0]);
+}
+
 // v^E_i = int f_i . E_inc, v^H_i = -int f_i . H_inc (paper Eq. (v)), one thread
 // per (edge, wave); E_inc = p exp(j k0 r_hat . r), H_inc = (k_hat x p)/eta0 (...).
+// F32: the phase factor exp(j k0 r_hat . r) by the FP32 reduced sin/cos (the
+// mixed-precision solve), else FP64.
+template <bool F32>
 __global__ void k_rhs(int64_t ne, int nw, const double *__restrict__ rec, const int32_t *__restrict__ edge_tri,
-                      const int32_t *__restrict__ edge_loc, const double *__restrict__ waves, z64 *__restrict__ vE,
+                      const int32_t *__restrict__ edge_loc, const double *__restrict__ wb, z64 *__restrict__ vE,
                       z64 *__restrict__ vH) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= ne * nw) return;
     int64_t i = idx / nw;
     int w = (int)(idx % nw);
-    double rh[3], thh[3], phh[3];
-    sph_basis(waves[3 * w], waves[3 * w + 1], rh, thh, phh);
-    double sps, cps;
-    sincos(waves[3 * w + 2], &sps, &cps);
-    double p[3], hp[3];
-    for (int d = 0; d < 3; ++d) p[d] = cps * thh[d] + sps * phh[d];
-    // k_hat = -r_hat ; k_hat x p
-    hp[0] = -(rh[1] * p[2] - rh[2] * p[1]);
-    hp[1] = -(rh[2] * p[0] - rh[0] * p[2]);
-    hp[2] = -(rh[0] * p[1] - rh[1] * p[0]);
+    const double *o = wb + 9 * (int64_t)w;
+    const double rh[3] = {o[0], o[1], o[2]}, p[3] = {o[3], o[4], o[5]}, hp[3] = {o[6], o[7], o[8]};
     z64 e(0, 0), h(0, 0);
     for (int s = 0; s < 2; ++s) {
         int t = edge_tri[2 * i + s], a = edge_loc[2 * i + s];
@@ -192,7 +208,14 @@ __global__ void k_rhs(int64_t ne, int nw, const double *__restrict__ rec, const 
             double f0 = x[0] - r[TR_P + 3 * a], f1 = x[1] - r[TR_P + 3 * a + 1], f2 = x[2] - r[TR_P + 3 * a + 2];
             double ph = K0 * (rh[0] * x[0] + rh[1] * x[1] + rh[2] * x[2]);
             double sn, cs;
-            sincos(ph, &sn, &cs);
+            if constexpr (F32) {
+                float sf, cf;
+                sincos_red((float)ph, &sf, &cf);
+                sn = sf;
+                cs = cf;
+            } else {
+                sincos(ph, &sn, &cs);
+            }
             double wfe = r[TR_W + q] * c * (f0 * p[0] + f1 * p[1] + f2 * p[2]);
             double wfh = -r[TR_W + q] * c * (f0 * hp[0] + f1 * hp[1] + f2 * hp[2]) / ETA0;
             e.re += wfe * cs; e.im += wfe * sn;
@@ -206,6 +229,8 @@ __global__ void k_rhs(int64_t ne, int nw, const double *__restrict__ rec, const 
 // Far field of J = sum aJ f, M = sum aM f radiating into free space:
 // F = (j k0/4pi) [ -eta0 (N - r (r.N)) + r x L ], N = int J e^{j k0 r.r'}, L likewise.
 // One block per (rhs, direction); j is (2 ne, nrhs) internal order [M; J].
+// F32: the phase factors by the FP32 reduced sin/cos (mixed-precision solve).
+template <bool F32>
 __global__ void k_farfield(int64_t nt, int64_t ne, int nrhs, const double *__restrict__ rec,
                            const int32_t *__restrict__ tri_edge, const z64 *__restrict__ j,
                            const double *__restrict__ obs, int ndir, int monostatic,
@@ -231,7 +256,14 @@ __global__ void k_farfield(int64_t nt, int64_t ne, int nrhs, const double *__res
             const double *x = r + TR_Q + 3 * q;
             double phs = K0 * (rh[0] * x[0] + rh[1] * x[1] + rh[2] * x[2]);
             double sn, cs;
-            sincos(phs, &sn, &cs);
+            if constexpr (F32) {
+                float sf, cf;
+                sincos_red((float)phs, &sf, &cf);
+                sn = sf;
+                cs = cf;
+            } else {
+                sincos(phs, &sn, &cs);
+            }
             z64 e(cs * r[TR_W + q], sn * r[TR_W + q]);
             for (int d = 0; d < 3; ++d) {
                 z64 sJ(0, 0), sM(0, 0);
@@ -332,23 +364,32 @@ void launch_gram_rows(Mesh &m, cudaStream_t st) {
     }
 }
 
-void launch_rhs(const Mesh &m, const double *d_waves, int nw, z64 *vE, z64 *vH, cudaStream_t st) {
+void launch_rhs(const Mesh &m, const double *d_waves, int nw, z64 *vE, z64 *vH, cudaStream_t st, bool f32) {
     int64_t tot = m.h.ne * (int64_t)nw;
+    DevBuf<double> wb;
+    wb.alloc((size_t)9 * nw);
+    k_wave_basis<<<(unsigned)((nw + 127) / 128), 128, 0, st>>>(nw, d_waves, wb.p);
+    launched("k_wave_basis");
     {
         ProfScope ps_("k_rhs", st);
-        k_rhs<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(m.h.ne, nw, m.tri64.p, m.edge_tri.p, m.edge_loc.p, d_waves,
-                                                             vE, vH);
+        const unsigned g = (unsigned)((tot + 127) / 128);
+        if (f32) k_rhs<true><<<g, 128, 0, st>>>(m.h.ne, nw, m.tri64.p, m.edge_tri.p, m.edge_loc.p, wb.p, vE, vH);
+        else k_rhs<false><<<g, 128, 0, st>>>(m.h.ne, nw, m.tri64.p, m.edge_tri.p, m.edge_loc.p, wb.p, vE, vH);
         launched("k_rhs");
     }
 }
 
 void launch_farfield(const Mesh &m, const z64 *j, int nrhs, const double *d_obs, int ndir, bool monostatic,
-                     const double *d_exc, double *d_rcs, cudaStream_t st) {
+                     const double *d_exc, double *d_rcs, cudaStream_t st, bool f32) {
     dim3 grid(monostatic ? 1 : ndir, nrhs);
     {
         ProfScope ps_("k_farfield", st);
-        k_farfield<<<grid, 256, 0, st>>>(m.h.nt, m.h.ne, nrhs, m.tri64.p, m.tri_edge.p, j, d_obs, ndir,
-                                         monostatic ? 1 : 0, d_exc, d_rcs);
+        if (f32)
+            k_farfield<true><<<grid, 256, 0, st>>>(m.h.nt, m.h.ne, nrhs, m.tri64.p, m.tri_edge.p, j, d_obs, ndir,
+                                                   monostatic ? 1 : 0, d_exc, d_rcs);
+        else
+            k_farfield<false><<<grid, 256, 0, st>>>(m.h.nt, m.h.ne, nrhs, m.tri64.p, m.tri_edge.p, j, d_obs, ndir,
+                                                    monostatic ? 1 : 0, d_exc, d_rcs);
         launched("k_farfield");
     }
 }
