@@ -47,20 +47,21 @@ constexpr int PCHOL_THREADS = 256;
 //
 // It runs on a cluster of PC_CL CTAs (one per SM).  CTA c owns the rows of
 // original index a = c + PC_CL l of the Schur complement U, stored in full in
-// its shared memory.  For step i every CTA has proposed a candidate (its
-// largest remaining diagonal, lowest position on ties; without pivoting only
-// the owner of position i proposes) by writing that row, unscaled, with its
-// diagonal, 1 / sqrt(diagonal), position and index into the shared memory of
-// every CTA.  After the synchronisation of step i all CTAs pick the same
-// winner q, CTA 0 writes row i of R (by original index; permuted to positions
-// after the loop), and each CTA applies
+// its shared memory (the diagonals also in a compact array).  For step i every
+// CTA has proposed a candidate (its largest remaining diagonal, lowest
+// position on ties; without pivoting only the owner of position i proposes):
+// the row, unscaled, in its own shared memory, and its diagonal,
+// 1 / sqrt(diagonal), position and index in the shared memory of every CTA.
+// After the synchronisation of step i all CTAs pick the same winner q and read
+// its row from the shared memory of its owner, CTA 0 writes row i of R (by
+// original index; permuted to positions after the loop), and each CTA applies
 //   U(a, b) -= conj(U(q, a)) U(q, b) / U(q, q)
 // to its own rows.  The chain from one synchronisation to the next is kept
 // short: a CTA updates the diagonals of its rows, picks its candidate for
-// step i + 1, updates that row while sending it, arrives, and only then
-// updates the rest of its rows, overlapping the other CTAs' chains.  A CTA
-// can therefore write the proposals of step i + 2 while another still reads
-// those of step i: proposals rotate through three buffers.  The
+// step i + 1, updates that row and stores it, sends the scalars, arrives, and
+// only then updates the rest of its rows, overlapping the other CTAs' chains.
+// A CTA can therefore write its proposal of step i + 2 while another still
+// reads the one of step i: proposals rotate through three buffers.  The
 // synchronisation of step k is the mbarrier pair of cluster.cuh, arrived on
 // remotely by every CTA; its wait gives up after one second (error flag,
 // loop ends).  Hardware cluster barriers are used only where every CTA
@@ -70,8 +71,8 @@ constexpr int PC_CL = 8;
 constexpr int PC_ROWS = (PCHOL_MAX + PC_CL - 1) / PC_CL;
 constexpr int PC_NBUF = 3;
 
-// dynamic shared memory: own rows [PC_ROWS][m] and proposals [PC_NBUF][PC_CL][m]
-constexpr size_t pchol_cl_smem(int m) { return (size_t)(PC_ROWS + PC_NBUF * PC_CL) * m * sizeof(z64); }
+// dynamic shared memory: own rows [PC_ROWS][m] and own candidate rows [PC_NBUF][m]
+constexpr size_t pchol_cl_smem(int m) { return (size_t)(PC_ROWS + PC_NBUF) * m * sizeof(z64); }
 
 // u -= c r
 __device__ __forceinline__ void pc_axpy(z64 &u, z64 c, z64 r) {
@@ -88,11 +89,13 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
     const int me = (int)cl.block_rank();
     extern __shared__ __align__(16) unsigned char pc_raw[];
     z64 *Uloc = reinterpret_cast<z64 *>(pc_raw);   // [PC_ROWS][m]
-    z64 *crow = Uloc + (size_t)PC_ROWS * m;        // [PC_NBUF][PC_CL][m], by original index
+    z64 *crow = Uloc + (size_t)PC_ROWS * m;        // [PC_NBUF][m]: this CTA's candidate rows, by original index
     __shared__ uint64_t cbar[2];
     __shared__ double cval[PC_NBUF][PC_CL], crd[PC_NBUF][PC_CL];   // proposal: diagonal, 1 / sqrt(diagonal)
     __shared__ int cpos[PC_NBUF][PC_CL], cidx[PC_NBUF][PC_CL];     // proposal: position, original index
     __shared__ z64 s_coef[PC_ROWS];                                 // conj(U(q, a)) / U(q, q) per own row
+    __shared__ double s_dg[PC_ROWS];                                // diagonal U(a, a) per own row
+    __shared__ z64 rowq[PCHOL_MAX];                                 // the winning row of the step
     __shared__ int s_alive[PC_ROWS];                                // own row not yet eliminated
     __shared__ int piv[PCHOL_MAX], posof[PCHOL_MAX];
     __shared__ int s_abort, s_stop, s_cand, s_cpos;
@@ -109,7 +112,11 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
         piv[k] = k;
         posof[k] = k;
     }
-    if (threadIdx.x < nloc) s_alive[threadIdx.x] = 1;
+    if (threadIdx.x < nloc) {
+        const int a = me + PC_CL * threadIdx.x;
+        s_alive[threadIdx.x] = 1;
+        s_dg[threadIdx.x] = M[(int64_t)a * m + a].re;
+    }
     if (warp == 0) {
         double mx = 0.0;
         for (int k = lane; k < m; k += 32) mx = fmax(mx, M[(int64_t)k * m + k].re);
@@ -130,7 +137,7 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
         if (!pivot) {   // no row exchanges: position i is row i, owned by CTA i % PC_CL
             if (threadIdx.x == 0) {
                 const int ls = (i % PC_CL == me) ? i / PC_CL : -1;
-                const double d = ls >= 0 ? Uloc[ls * m + i].re : -1.0;
+                const double d = ls >= 0 ? s_dg[ls] : -1.0;
                 s_cand = ls;
                 s_cpos = ls >= 0 ? i : INT_MAX;
                 s_cd = d;
@@ -144,7 +151,7 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
         for (int ls = lane; ls < nloc; ls += 32) {
             const int a = me + PC_CL * ls, pa = posof[a];
             if (pa < i || (!pivot && pa != i)) continue;
-            const long long v = __double_as_longlong(Uloc[ls * m + a].re);   // orders positive doubles
+            const long long v = __double_as_longlong(s_dg[ls]);   // orders positive doubles
             if (bls < 0 || v > best || (v == best && pa < bp)) {
                 best = v;
                 bp = pa;
@@ -182,13 +189,8 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
     // step 0: candidates from the initial diagonals
     pick(0);
     __syncthreads();
-    if (s_cand >= 0) {
-        z64 *dst = crow + (size_t)me * m;
-        for (int b = threadIdx.x; b < m; b += nth) {
-            const z64 v = Uloc[s_cand * m + b];
-            for (int r = 0; r < PC_CL; ++r) *cl.map_shared_rank(dst + b, r) = v;
-        }
-    }
+    if (s_cand >= 0)
+        for (int b = threadIdx.x; b < m; b += nth) crow[b] = Uloc[s_cand * m + b];
     send_scalars(0);
     __syncthreads();
     cl_arrive(cbar, 0, PC_CL);
@@ -215,7 +217,12 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
             break;
         }
         const int q = cidx[buf][w];
-        const z64 *Ri = crow + ((size_t)buf * PC_CL + w) * m;   // row q of the Schur complement, unscaled
+        {   // row q of the Schur complement, unscaled, from the shared memory of its owner
+            const z64 *src = cl.map_shared_rank(crow + (size_t)buf * m, w);
+            for (int b = threadIdx.x; b < m; b += nth) rowq[b] = src[b];
+        }
+        __syncthreads();
+        const z64 *Ri = rowq;
         const double rdq = crd[buf][w];                         // 1 / sqrt(U(q, q))
         if (threadIdx.x == 0 && bpos != i) {
             const int t = piv[i];
@@ -229,7 +236,12 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
             if (a == q) s_alive[ls] = 0;
             const z64 c = conj(Ri[a]) * (rdq * rdq);
             s_coef[ls] = c;
-            if (s_alive[ls]) pc_axpy(Uloc[ls * m + a], c, Ri[a]);
+            if (s_alive[ls]) {   // real part of U(a, a) -= c U(q, a) (the diagonal is real)
+                double d = s_dg[ls];
+                d = fma(-c.re, Ri[a].re, d);
+                d = fma(c.im, Ri[a].im, d);
+                s_dg[ls] = d;
+            }
         }
         __syncthreads();
         // row i of R = row q / sqrt(U(q, q)), by original index for now (permuted to positions after the loop)
@@ -245,14 +257,14 @@ __global__ void __cluster_dims__(PC_CL, 1, 1) __launch_bounds__(PCHOL_THREADS)
         if (cls >= 0) {
             const int a = me + PC_CL * cls;
             const z64 c = s_coef[cls];
-            z64 *dst = crow + ((size_t)((i + 1) % PC_NBUF) * PC_CL + me) * m;
+            z64 *dst = crow + (size_t)((i + 1) % PC_NBUF) * m;
             for (int b = threadIdx.x; b < m; b += nth) {
                 z64 v = Uloc[cls * m + b];
                 if (b != a && posof[b] > i) {
                     pc_axpy(v, c, Ri[b]);
                     Uloc[cls * m + b] = v;
                 }
-                for (int r = 0; r < PC_CL; ++r) *cl.map_shared_rank(dst + b, r) = v;
+                dst[b] = v;
             }
         }
         send_scalars(i + 1);
