@@ -450,22 +450,6 @@ __global__ void k_sub_rows(int64_t count, const z64 *__restrict__ a, const z64 *
     if (i < count) out[i] = a[i] - b[i];
 }
 
-// ||X||_F of a rows x cols matrix (ld ld; one block; fixed summation order)
-__global__ void __launch_bounds__(256) k_fro(int rows, int cols, const z64 *__restrict__ X, int64_t ld,
-                                             double *__restrict__ out) {
-    __shared__ double part[8];
-    double s = 0.0;
-    for (int64_t idx = threadIdx.x; idx < (int64_t)rows * cols; idx += 256) s += norm2(X[(idx / cols) * ld + idx % cols]);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < 8; ++w) t += part[w];
-        *out = sqrt(t);
-    }
-}
-
 // ||M - I||_F of an m x m matrix (one block; fixed summation order)
 __global__ void __launch_bounds__(256) k_gram_dev(int m, const z64 *__restrict__ M, double *__restrict__ out) {
     __shared__ double part[8];
@@ -716,16 +700,18 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     k_rownorm<<<p, 256, 0, st>>>(n, d_b, bnorm.p);
     launched("k_rownorm");
     std::vector<double> h_bn(p), h_rn(p), h_w1(p), h_h0(p), h_h1(p);
-    DevBuf<double> fro_out;
-    fro_out.alloc(1);
-    // ||X||_F of a rows x cols block (host sync)
+    DevBuf<double> fro_col;
+    fro_col.alloc((size_t)std::max<int64_t>(dcap, p));
+    std::vector<double> h_col((size_t)std::max<int64_t>(dcap, p));
+    // ||X||_F of a rows x cols block: column norms (one block each), summed on the host (host sync)
     auto fro = [&](int rows, int cols, const z64 *X, int64_t ld) {
-        k_fro<<<1, 256, 0, st>>>(rows, cols, X, ld, fro_out.p);
-        launched("k_fro");
-        double h = 0.0;
-        CBFM_CUDA(cudaMemcpyAsync(&h, fro_out.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        k_colnorm<<<cols, 256, 0, st>>>(rows, cols, X, ld, fro_col.p);
+        launched("k_colnorm");
+        CBFM_CUDA(cudaMemcpyAsync(h_col.data(), fro_col.p, sizeof(double) * cols, cudaMemcpyDeviceToHost, st));
         CBFM_CUDA(cudaStreamSynchronize(st));
-        return h;
+        double a = 0.0;
+        for (int c = 0; c < cols; ++c) a += h_col[c] * h_col[c];
+        return std::sqrt(a);
     };
     // sqrt of the sum of squares of the first k norms; the smallest ratio
     // after / before over the vectors that had a norm
