@@ -792,7 +792,7 @@ __global__ void k_gjb_panels(int n, int k0, int b, const z64 *__restrict__ A, z6
 // the block (row exchanges undone on the columns at the end).  A pivot below
 // 1e-13 of the block's largest entry sets *flag.  The column block k of A is
 // zeroed (it is accumulated into next; its old values are in the panel copy).
-__global__ void __launch_bounds__(256) k_gjb_inv(int n, int k0, int b, const z64 *__restrict__ Rw,
+__global__ void __launch_bounds__(1024) k_gjb_inv(int n, int k0, int b, const z64 *__restrict__ Rw,
                                                  z64 *__restrict__ D, int *__restrict__ flag,
                                                  z64 *__restrict__ A) {
     __shared__ z64 a[GJB][GJB + 1];
@@ -850,9 +850,11 @@ __global__ void __launch_bounds__(256) k_gjb_inv(int n, int k0, int b, const z64
                 a[p][c] = u;
             }
         __syncthreads();
-        if (threadIdx.x == 0) {   // one reciprocal per pivot (an FP64 division is long on GB300)
+        if (threadIdx.x == 0) {   // one reciprocal per pivot, one FP64 division (long on GB300)
             const z64 piv = a[k][k];
-            s_pinv = norm2(piv) > 0.0 ? cdiv(z64(1.0, 0.0), piv) : z64(0.0, 0.0);
+            const double d = norm2(piv);
+            const double id = d > 0.0 ? 1.0 / d : 0.0;
+            s_pinv = z64(piv.re * id, -piv.im * id);
         }
         __syncthreads();
         const z64 pinv = s_pinv;
@@ -955,9 +957,9 @@ bool gj_blocked(int64_t n, int nbatch, const z64 *Aorig, z64 *inv, cudaStream_t 
         const int b = (int)std::min<int64_t>(GJB, n - k0);
         k_gjb_panels<<<dim3(nbk, nbatch), 256, 0, st>>>((int)n, (int)k0, b, inv, C.p, Rw.p);
         launched("k_gjb_panels");
-        {
+        {   // one thread per entry of the block in the elimination: 1024 threads
             ProfScope ps_("k_gjb_inv", st);
-            k_gjb_inv<<<nbatch, 256, 0, st>>>((int)n, (int)k0, b, Rw.p, D, flag.p, inv);
+            k_gjb_inv<<<nbatch, GJB * GJB, 0, st>>>((int)n, (int)k0, b, Rw.p, D, flag.p, inv);
             launched("k_gjb_inv");
         }
         std::vector<GemmDesc> dr, du;
