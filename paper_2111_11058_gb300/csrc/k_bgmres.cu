@@ -678,7 +678,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     c.scale.alloc(p);
     c.dev.alloc(1);
     DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw;
-    DevBuf<double> bnorm, rnorm;
+    DevBuf<double> bnorm, rnorm, rnorm0;
     V.alloc((size_t)dcap * n);
     W.alloc((size_t)p * n);
     HcT.alloc((size_t)p * dcap);
@@ -696,6 +696,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     Rw.alloc((size_t)p * p);
     bnorm.alloc(p);
     rnorm.alloc(p);
+    rnorm0.alloc(p);
     CBFM_CUDA(cudaMemsetAsync(Y.p, 0, sizeof(z64) * p * n, st));
     k_rownorm<<<p, 256, 0, st>>>(n, d_b, bnorm.p);
     launched("k_rownorm");
@@ -778,12 +779,10 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             if (dcap - d1 < pjc) break;   // no room for another block: solve and restart
             // W = B V_J; the norms before orthogonalisation set the scale for exhaustion
             applyB(V.p + d0 * n, W.p, pjc);
-            k_rownorm<<<pjc, 256, 0, st>>>(n, W.p, rnorm.p);
+            // the norms before the orthogonalisation, read back with those after its first pass
+            k_rownorm<<<pjc, 256, 0, st>>>(n, W.p, rnorm0.p);
             launched("k_rownorm");
-            CBFM_CUDA(cudaMemcpyAsync(h_rn.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
-            CBFM_CUDA(cudaStreamSynchronize(st));
             double wref = 0.0;
-            for (int q = 0; q < pjc; ++q) wref = std::max(wref, h_rn[q]);
             // block classical Gram-Schmidt, twice; HcT (pjc x d1) collects the coefficients
             for (int pass = 0; pass < 2; ++pass) {
                 gemm_grouped<double>({GemmDesc{pjc, d1, n, 0, n, 0, n, 0, dcap}}, 0, 2, W.p, V.p, tmp2.p, false, st);
@@ -795,8 +794,10 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
                 if (pass == 0) {
                     k_rownorm<<<pjc, 256, 0, st>>>(n, W.p, rnorm.p);
                     launched("k_rownorm");
+                    CBFM_CUDA(cudaMemcpyAsync(h_rn.data(), rnorm0.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
                     CBFM_CUDA(cudaMemcpyAsync(h_w1.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
                     CBFM_CUDA(cudaStreamSynchronize(st));
+                    for (int q = 0; q < pjc; ++q) wref = std::max(wref, h_rn[q]);
                     if (min_ratio(h_w1, h_rn, pjc) >= GS_KEEP) break;
                 }
             }
