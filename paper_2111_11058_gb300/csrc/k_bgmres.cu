@@ -450,6 +450,12 @@ __global__ void k_sub_rows(int64_t count, const z64 *__restrict__ a, const z64 *
     if (i < count) out[i] = a[i] - b[i];
 }
 
+// Y += X (complex64 into complex128), n elements
+__global__ void k_add32to64(int64_t n, const c32 *__restrict__ X, z64 *__restrict__ Y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        Y[i] += z64(X[i].re, X[i].im);
+}
+
 // ||M - I||_F of an m x m matrix (one block; fixed summation order)
 __global__ void __launch_bounds__(256) k_gram_dev(int m, const z64 *__restrict__ M, double *__restrict__ out) {
     __shared__ double part[8];
@@ -731,6 +737,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     CBFM_CUDA(cudaStreamSynchronize(st));
 
     DevBuf<c32> s_in, s_out;   // complex64 rows for the mixed-precision products
+    DevBuf<c32> V32, Z32;      // complex64 basis and coefficients for the mixed-precision solution update
     if (rd.prec != CBFM_FP64) {
         s_in.alloc((size_t)p * n);
         s_out.alloc((size_t)p * n);
@@ -888,7 +895,21 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             gemm_grouped<double>({GemmDesc{pi, p, pi, a0 * p, p, 0, p, a0 * p, p}}, 0, 0, RinvBlk.p, tmp2.p, Z.p,
                                  false, st);
         }
-        gemm_grouped<double>({GemmDesc{p, n, dJ, 0, p, 0, n, 0, n}}, 1, 0, Z.p, V.p, Y.p, true, st);
+        if (rd.prec != CBFM_FP64) {
+            // mixed precision: the solution update Y += Z^T V (not part of the orthogonalisation or the
+            // residual) in FP32, like the operator product
+            if (V32.p == nullptr) {
+                V32.alloc((size_t)dcap * n);
+                Z32.alloc((size_t)dcap * p);
+            }
+            launch_z64_to_c32(V.p, V32.p, dJ * n, st);
+            launch_z64_to_c32(Z.p, Z32.p, dJ * p, st);
+            gemm_grouped<float>({GemmDesc{p, n, dJ, 0, p, 0, n, 0, n}}, 1, 0, Z32.p, V32.p, s_out.p, false, st);
+            k_add32to64<<<nb((int64_t)p * n), 256, 0, st>>>((int64_t)p * n, s_out.p, Y.p);
+            launched("k_add32to64");
+        } else {
+            gemm_grouped<double>({GemmDesc{p, n, dJ, 0, p, 0, n, 0, n}}, 1, 0, Z.p, V.p, Y.p, true, st);
+        }
         CBFM_CUDA(cudaStreamSynchronize(st));
         if (breakdown) break;
     }
