@@ -1043,8 +1043,21 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
             gE.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, c.coff[k] * nrhs, nrhs});
             gH.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, (nh + c.coff[k]) * nrhs, nrhs});
         }
-        gemm_grouped<double>(gE, 2, 0, c.CJ.p, vE.p, bt.p, false, st);
-        gemm_grouped<double>(gH, 2, 0, c.CM.p, vH.p, bt.p, false, st);
+        const bool f32 = r->prec != CBFM_FP64;   // mixed precision: right-hand side and recovery in FP32
+        if (f32) {
+            DevBuf<c32> e32, h32, b32;
+            e32.alloc((size_t)ne * nrhs);
+            h32.alloc((size_t)ne * nrhs);
+            b32.alloc((size_t)n * nrhs);
+            launch_z64_to_c32(vE.p, e32.p, ne * nrhs, st);
+            launch_z64_to_c32(vH.p, h32.p, ne * nrhs, st);
+            gemm_grouped<float>(gE, 2, 0, c.CJ32.p, e32.p, b32.p, false, st);
+            gemm_grouped<float>(gH, 2, 0, c.CM32.p, h32.p, b32.p, false, st);
+            launch_c32_to_z64(b32.p, bt.p, n * nrhs, st);
+        } else {
+            gemm_grouped<double>(gE, 2, 0, c.CJ.p, vE.p, bt.p, false, st);
+            gemm_grouped<double>(gH, 2, 0, c.CM.p, vH.p, bt.p, false, st);
+        }
         b.alloc((size_t)nrhs * n);
         {
             ProfScope ps_("k_transpose", st);
@@ -1073,8 +1086,18 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
             jM.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, c.coff[k], n, off * nrhs, nrhs});
             jJ.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, nh + c.coff[k], n, (ne + off) * nrhs, nrhs});
         }
-        gemm_grouped<double>(jM, 0, 1, c.CM.p, x.p, jint.p, false, st);
-        gemm_grouped<double>(jJ, 0, 1, c.CJ.p, x.p, jint.p, false, st);
+        if (f32) {
+            DevBuf<c32> x32, j32;
+            x32.alloc((size_t)nrhs * n);
+            j32.alloc((size_t)2 * ne * nrhs);
+            launch_z64_to_c32(x.p, x32.p, nrhs * n, st);
+            gemm_grouped<float>(jM, 0, 1, c.CM32.p, x32.p, j32.p, false, st);
+            gemm_grouped<float>(jJ, 0, 1, c.CJ32.p, x32.p, j32.p, false, st);
+            launch_c32_to_z64(j32.p, jint.p, 2 * ne * nrhs, st);
+        } else {
+            gemm_grouped<double>(jM, 0, 1, c.CM.p, x.p, jint.p, false, st);
+            gemm_grouped<double>(jJ, 0, 1, c.CJ.p, x.p, jint.p, false, st);
+        }
         if (rcs_out && (mono || ndir > 0)) {
             int nd = mono ? 1 : ndir;
             if (!mono) {
