@@ -186,8 +186,8 @@ __global__ void k_wave_basis(int nw, const double *__restrict__ waves, double *_
 
 // v^E_i = int f_i . E_inc, v^H_i = -int f_i . H_inc (paper Eq. (v)), one thread
 // per (edge, wave); E_inc = p exp(j k0 r_hat . r), H_inc = (k_hat x p)/eta0 (...).
-// F32: the phase factor exp(j k0 r_hat . r) by the FP32 reduced sin/cos (the
-// mixed-precision solve), else FP64.
+// F32: the integrand in FP32 with the phase factor exp(j k0 r_hat . r) by the
+// FP32 reduced sin/cos (the mixed-precision solve), else FP64.
 template <bool F32>
 __global__ void k_rhs(int64_t ne, int nw, const double *__restrict__ rec, const int32_t *__restrict__ edge_tri,
                       const int32_t *__restrict__ edge_loc, const double *__restrict__ wb, z64 *__restrict__ vE,
@@ -198,6 +198,33 @@ __global__ void k_rhs(int64_t ne, int nw, const double *__restrict__ rec, const 
     int w = (int)(idx % nw);
     const double *o = wb + 9 * (int64_t)w;
     const double rh[3] = {o[0], o[1], o[2]}, p[3] = {o[3], o[4], o[5]}, hp[3] = {o[6], o[7], o[8]};
+    if constexpr (F32) {   // the whole integrand in FP32 (phase reduced), 14 terms summed in FP32
+        const float pf[3] = {(float)p[0], (float)p[1], (float)p[2]},
+                    hpf[3] = {(float)(hp[0] / ETA0), (float)(hp[1] / ETA0), (float)(hp[2] / ETA0)};
+        float er = 0.f, ei = 0.f, hr = 0.f, hi = 0.f;
+        for (int s = 0; s < 2; ++s) {
+            const int t = edge_tri[2 * i + s], a = edge_loc[2 * i + s];
+            const double *r = rec + (int64_t)t * TRI_REC;
+            const float c = (float)r[TR_C + a];
+            for (int q = 0; q < 7; ++q) {
+                const double *x = r + TR_Q + 3 * q;
+                const float f0 = (float)(x[0] - r[TR_P + 3 * a]), f1 = (float)(x[1] - r[TR_P + 3 * a + 1]),
+                            f2 = (float)(x[2] - r[TR_P + 3 * a + 2]);
+                // the phase argument in FP64 (coordinates may lie far from the origin), reduced in FP32
+                const float ph = (float)(K0 * (rh[0] * x[0] + rh[1] * x[1] + rh[2] * x[2]));
+                float sn, cs;
+                sincos_red(ph, &sn, &cs);
+                const float wc = (float)r[TR_W + q] * c;
+                const float wfe = wc * (f0 * pf[0] + f1 * pf[1] + f2 * pf[2]);
+                const float wfh = -wc * (f0 * hpf[0] + f1 * hpf[1] + f2 * hpf[2]);
+                er += wfe * cs; ei += wfe * sn;
+                hr += wfh * cs; hi += wfh * sn;
+            }
+        }
+        vE[i * nw + w] = z64(er, ei);
+        vH[i * nw + w] = z64(hr, hi);
+        return;
+    }
     z64 e(0, 0), h(0, 0);
     for (int s = 0; s < 2; ++s) {
         int t = edge_tri[2 * i + s], a = edge_loc[2 * i + s];
@@ -208,14 +235,7 @@ __global__ void k_rhs(int64_t ne, int nw, const double *__restrict__ rec, const 
             double f0 = x[0] - r[TR_P + 3 * a], f1 = x[1] - r[TR_P + 3 * a + 1], f2 = x[2] - r[TR_P + 3 * a + 2];
             double ph = K0 * (rh[0] * x[0] + rh[1] * x[1] + rh[2] * x[2]);
             double sn, cs;
-            if constexpr (F32) {
-                float sf, cf;
-                sincos_red((float)ph, &sf, &cf);
-                sn = sf;
-                cs = cf;
-            } else {
-                sincos(ph, &sn, &cs);
-            }
+            sincos(ph, &sn, &cs);
             double wfe = r[TR_W + q] * c * (f0 * p[0] + f1 * p[1] + f2 * p[2]);
             double wfh = -r[TR_W + q] * c * (f0 * hp[0] + f1 * hp[1] + f2 * hp[2]) / ETA0;
             e.re += wfe * cs; e.im += wfe * sn;
