@@ -249,7 +249,8 @@ __global__ void k_rhs(int64_t ne, int nw, const double *__restrict__ rec, const 
 // Far field of J = sum aJ f, M = sum aM f radiating into free space:
 // F = (j k0/4pi) [ -eta0 (N - r (r.N)) + r x L ], N = int J e^{j k0 r.r'}, L likewise.
 // One block per (rhs, direction); j is (2 ne, nrhs) internal order [M; J].
-// F32: the phase factors by the FP32 reduced sin/cos (mixed-precision solve).
+// F32: each thread's share of the sums in FP32, with the phase factors by the
+// FP32 reduced sin/cos (mixed-precision solve); the sums over threads in FP64.
 template <bool F32>
 __global__ void k_farfield(int64_t nt, int64_t ne, int nrhs, const double *__restrict__ rec,
                            const int32_t *__restrict__ tri_edge, const z64 *__restrict__ j,
@@ -264,6 +265,40 @@ __global__ void k_farfield(int64_t nt, int64_t ne, int nrhs, const double *__res
     sph_basis(th, ph, rh, thh, phh);
     double acc[12];
     for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+    if constexpr (F32) {   // each thread's terms (a few tens) in FP32; the sums over threads below in FP64
+        float af[12];
+        for (int k = 0; k < 12; ++k) af[k] = 0.f;
+        for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) {
+            const double *r = rec + t * TRI_REC;
+            c32 aJ[3], aM[3];
+            for (int a = 0; a < 3; ++a) {
+                const int e = tri_edge[3 * t + a];
+                const z64 jm = j[(int64_t)e * nrhs + w], jj = j[(ne + e) * nrhs + w];
+                const float c = (float)r[TR_C + a];
+                aM[a] = c32(c * (float)jm.re, c * (float)jm.im);
+                aJ[a] = c32(c * (float)jj.re, c * (float)jj.im);
+            }
+            for (int q = 0; q < 7; ++q) {
+                const double *x = r + TR_Q + 3 * q;
+                float sn, cs;
+                sincos_red((float)(K0 * (rh[0] * x[0] + rh[1] * x[1] + rh[2] * x[2])), &sn, &cs);
+                const float wq = (float)r[TR_W + q];
+                const c32 e(cs * wq, sn * wq);
+                for (int d = 0; d < 3; ++d) {
+                    c32 sJ(0, 0), sM(0, 0);
+                    for (int a = 0; a < 3; ++a) {
+                        const float f = (float)(x[d] - r[TR_P + 3 * a + d]);
+                        sJ += f * aJ[a];
+                        sM += f * aM[a];
+                    }
+                    const c32 vJ = sJ * e, vM = sM * e;
+                    af[2 * d] += vJ.re; af[2 * d + 1] += vJ.im;
+                    af[6 + 2 * d] += vM.re; af[6 + 2 * d + 1] += vM.im;
+                }
+            }
+        }
+        for (int k = 0; k < 12; ++k) acc[k] = af[k];
+    } else {
     for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) {
         const double *r = rec + t * TRI_REC;
         z64 aJ[3], aM[3];
@@ -276,14 +311,7 @@ __global__ void k_farfield(int64_t nt, int64_t ne, int nrhs, const double *__res
             const double *x = r + TR_Q + 3 * q;
             double phs = K0 * (rh[0] * x[0] + rh[1] * x[1] + rh[2] * x[2]);
             double sn, cs;
-            if constexpr (F32) {
-                float sf, cf;
-                sincos_red((float)phs, &sf, &cf);
-                sn = sf;
-                cs = cf;
-            } else {
-                sincos(phs, &sn, &cs);
-            }
+            sincos(phs, &sn, &cs);
             z64 e(cs * r[TR_W + q], sn * r[TR_W + q]);
             for (int d = 0; d < 3; ++d) {
                 z64 sJ(0, 0), sM(0, 0);
@@ -297,6 +325,7 @@ __global__ void k_farfield(int64_t nt, int64_t ne, int nrhs, const double *__res
                 acc[6 + 2 * d] += vM.re; acc[6 + 2 * d + 1] += vM.im;
             }
         }
+    }
     }
     __shared__ double red[12][32];
     for (int k = 0; k < 12; ++k) {
