@@ -103,7 +103,7 @@ class ClockSampler:
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (CUDA cores)
 FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
 FP64_KERNELS = {"k_dots", "k_orth_update", "k_near_blocks", "k_finish", "k_lu_solve", "k_jacobi_svd",
-                "k_gemm_z64", "k_pchol", "k_trinv", "k_gj_sweep"}
+                "k_gemm_z64", "k_pchol", "k_trinv", "k_gj_sweep", "k_gjb_inv"}
 FP32_KERNELS = {"k_far", "k_matvec", "k_gemm_c32"}
 
 

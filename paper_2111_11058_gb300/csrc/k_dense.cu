@@ -958,6 +958,7 @@ bool gj_blocked(int64_t n, int nbatch, const z64 *Aorig, z64 *inv, cudaStream_t 
         k_gjb_panels<<<dim3(nbk, nbatch), 256, 0, st>>>((int)n, (int)k0, b, inv, C.p, Rw.p);
         launched("k_gjb_panels");
         {   // one thread per entry of the block in the elimination: 1024 threads
+            prof_add_work("k_gjb_inv", 8.0 * nbatch * (double)b * b * b, 32.0 * nbatch * (double)b * b);
             ProfScope ps_("k_gjb_inv", st);
             k_gjb_inv<<<nbatch, GJB * GJB, 0, st>>>((int)n, (int)k0, b, Rw.p, D, flag.p, inv);
             launched("k_gjb_inv");
