@@ -37,6 +37,7 @@ METRIC = "solved RHS/sec and p99 solve latency vs plain FP64 GPU path at <=1e-4 
 UNIT = "RHS/s"
 N_RHS = 128
 GMRES_TOL = 1e-6
+MOM_RESTART = 200      # GMRES restart of the MoM comparison (the paper does not state one)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
 
@@ -377,6 +378,40 @@ def run_batch(count: int = 200) -> dict:
             "tuning": P.tuning()}
 
 
+def run_mom(P, mesh, d, exc_d, cbfm_rcs, t_cbfm_ms: float, timed) -> dict:
+    """The paper's comparison method on the same scatterer and right-hand sides:
+    the RWG matrix of Eq. (Z) in the T-diagonal arrangement with the diagonal
+    preconditioner (Eq. (MoM_T)), mixed precision, per-RHS GMRES to the same
+    tolerance, monostatic RCS.  Times are reported as in Sec. IV: CBF generation
+    and the CBFM step (reduced assembly, CMP, solve), each relative to the MoM
+    total; the RCS difference as the RMSE of Eq. (RMSE), MoM as reference."""
+    import torch
+    rcs_m = torch.zeros((N_RHS, 1, 2), dtype=torch.float64, device="cuda")
+    out = {}
+
+    def step():
+        mo = P.assemble_mom(mesh, P.MIXED)
+        P.tdiag_setup(mo, jacobi=True)
+        res = P.solve(mo, exc_d, tol=GMRES_TOL, maxit=5000, restart=MOM_RESTART, monostatic=True, want_j=False,
+                      out_rcs=rcs_m, allow_noconv=True, solver=P.PER_RHS, precond=P.PC_TDIAG)
+        out["iters"], out["status"] = res.iters.copy(), res.status
+        mo.free()
+
+    step()
+    t_mom = float(np.mean(timed(2, step)))
+    t_cbf = float(np.mean(timed(2, lambda: P.build_cbfs(mesh, d["gen"], 1e-3).free())))
+    sm = rcs_m.sum(-1).cpu().numpy().ravel()
+    sc = np.asarray(cbfm_rcs).ravel()
+    rmse = 10.0 * math.log10(math.sqrt(float(np.mean((sc - sm) ** 2))) / float(sm.max() - sm.min()))
+    it = out["iters"]
+    return {"arrangement": "T-diagonal, diagonal preconditioner", "precision": "mixed", "solver": "per_rhs",
+            "restart": MOM_RESTART, "n": 2 * mesh.n_edges, "ms_per_step": t_mom,
+            "value": N_RHS / (t_mom / 1000.0), "converged": out["status"] == 0,
+            "gmres_iters": {"min": int(it.min()), "max": int(it.max()), "mean": float(it.mean())},
+            "relative_time": {"cbf_generation": t_cbf / t_mom, "cbfm_step": t_cbfm_ms / t_mom},
+            "rcs_rmse_db_cbfm_vs_mom": rmse}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -415,6 +450,7 @@ def main():
     ap.add_argument("--no-alt", action="store_true", help="skip the comparison with the other GMRES variant")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving (continuous batching) run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-scatterer assembly run")
+    ap.add_argument("--no-mom", action="store_true", help="skip the conventional-MoM comparison")
     ap.add_argument("--solver", default="block", choices=["block", "per_rhs"],
                     help="GMRES variant of the timed step: block GMRES over all right-hand sides, or one per RHS")
     ap.add_argument("--workload", default="cube9216", choices=["cube9216", "cube2304", "sphere960"],
@@ -535,6 +571,10 @@ def main():
         fp64 = {"value": ws * N_RHS / (t64[0] / 1000.0), "ms_per_step": t64[0], "rcs_err_mixed_vs_fp64": err,
                 "speedup_mixed_over_fp64": (t64[0] / t_step)}
 
+    mom = None
+    if not args.no_mom and ws == 1:
+        mom = run_mom(P, mesh, d, exc_d, mixed_rcs, t_step, timed)
+
     batch = None
     if not args.no_batch and ws == 1 and WORKLOAD == "cube9216":
         batch = run_batch()
@@ -560,7 +600,7 @@ def main():
                 "gpu_launches": int(launches), "roofline": roof, "tuning": P.tuning(),
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
-                "fp64_path": fp64, "other_solver": alt, "batch": batch, "serving": serving}
+                "fp64_path": fp64, "other_solver": alt, "mom": mom, "batch": batch, "serving": serving}
         if not args.no_cpu and ws == 1 and WORKLOAD == "cube9216":
             try:
                 line["cpu_baseline"] = cpu_sample()

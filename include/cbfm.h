@@ -65,6 +65,13 @@ typedef enum {
                              the CUDA cores (for comparison with the tensor-core path) */
 } cbfm_precision;
 
+/* Right preconditioner / unknown arrangement of cbfm_solve (its `precond` argument). */
+typedef enum {
+    CBFM_PC_NONE = 0,     /* the K-diagonal system as assembled (Eq. (Z) order), no preconditioner */
+    CBFM_PC_CMP = 1,      /* Calderon multiplicative preconditioner (G^CBF)^{-1} (cbfm_cmp_setup) */
+    CBFM_PC_TDIAG = 2     /* T-diagonal arrangement with optional Jacobi scaling (cbfm_tdiag_setup) */
+} cbfm_precond;
+
 /*
  * cbfm_mesh -- geometry staging of a closed triangle surface (paper Sec. II-B,
  * RWG functions; Sec. III-A, division into cells).
@@ -166,6 +173,43 @@ cbfm_status cbfm_assemble_reduced_batch(const cbfm_mesh_t *meshes, const cbfm_cb
  */
 int64_t cbfm_tuning(char *buf, int64_t cap);
 
+/*
+ * cbfm_assemble_mom -- the conventional method of moments (paper Sec. IV,
+ * the comparison method): the PMCHWT Galerkin matrix Z of Eq. (Z) over all N =
+ * 2 ne RWG functions, from the same far-pair quadrature and near-pair
+ * singularity extraction as cbfm_assemble_reduced, with no CBFs.  The result
+ * is a reduced-system handle whose basis functions are the RWG functions
+ * themselves (C^M = C^J = I):
+ *   - cbfm_solve takes it with precond CBFM_PC_NONE or CBFM_PC_TDIAG; the
+ *     right-hand side is v = [v^E; v^H] and the solution the RWG currents;
+ *   - cbfm_red_export returns Z (N x N) in canonical edge order, columns
+ *     [alpha^M; alpha^J], rows [E-tested; H-tested];
+ *   - cbfm_cmp_setup and cbfm_red_export_noalloc refuse it (CBFM_EINVAL): a
+ *     Calderon preconditioner on RWG functions alone has a singular Gram
+ *     matrix (Sec. III-A).
+ *   prec  CBFM_FP64 (complex128 Z) or a mixed mode (FP32 far pairs, complex64 Z)
+ *   n     out, N = 2 ne (may be NULL)
+ * Memory: 7 N^2/4 complex entries while assembling, N^2 kept.
+ */
+cbfm_status cbfm_assemble_mom(cbfm_mesh_t mesh, cbfm_precision prec, void *stream, cbfm_red_t *out, int64_t *n);
+
+/*
+ * cbfm_tdiag_setup -- the T-diagonal arrangement of Eq. (MoM_T) for a handle
+ * from cbfm_assemble_mom or cbfm_assemble_reduced.  The operator's two column
+ * halves are swapped (Z_t = Z P: unknowns [alpha^J; alpha^M], so that the
+ * diagonal blocks hold the T operators), then right-scaled by D^{-1}:
+ *   jacobi != 0: D = diag(Z_t), the diagonal preconditioner of the paper's
+ *                conventional MoM;
+ *   jacobi == 0: D = I; on a reduced system this is the T-diagonal CBFM of
+ *                Eq. (cbfm_Tdiag), whose matrix (C^JM)^H Z_t C^JM is A with its
+ *                column halves swapped and whose right-hand side is unchanged.
+ * cbfm_solve with precond CBFM_PC_TDIAG then runs GMRES on Z_t D^{-1} y = b and
+ * returns x = P D^{-1} y in the K-diagonal unknown order.  The scaled operator
+ * (N^2 entries) is kept in the handle; a later call replaces it.  Returns
+ * CBFM_ESINGULAR when jacobi != 0 and a diagonal entry of Z_t is zero.
+ */
+cbfm_status cbfm_tdiag_setup(cbfm_red_t red, int32_t jacobi, void *stream);
+
 /* A as complex128 row-major (n_cbf, n_cbf), host or device. */
 cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream);
 
@@ -219,7 +263,9 @@ cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream);
  * (Eq. (trans_current)), far field and RCS.  Each right-hand side runs its own
  * GMRES (x0 = 0, restart `restart`, stop at ||b - A P y|| / ||b|| <= tol).
  *   exc     (nrhs, 3) excitations (theta, phi, psi)
- *   use_cmp 1: P = (G^CBF)^{-1} (requires cbfm_cmp_setup); 0: P = I
+ *   precond CBFM_PC_CMP: P = (G^CBF)^{-1} (requires cbfm_cmp_setup);
+ *           CBFM_PC_NONE: P = I; CBFM_PC_TDIAG: P = (column-half swap) D^{-1}
+ *           as set by cbfm_tdiag_setup (required)
  *   j_out   (2 ne, nrhs) complex128 RWG coefficients in canonical edge order, or NULL
  *   obs     (ndir, 2) observation directions (theta, phi); obs == NULL with
  *           ndir == -1 selects monostatic: each RHS observed at its own arrival
@@ -237,7 +283,7 @@ cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream);
  * Returns CBFM_ENOCONV when some RHS did not converge within maxit.
  */
 cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double tol, int32_t maxit,
-                       int32_t restart, int32_t use_cmp, int32_t solver, double *j_out, const double *obs,
+                       int32_t restart, int32_t precond, int32_t solver, double *j_out, const double *obs,
                        int32_t ndir, double *rcs_out, int32_t *iters_out, double *resid_out,
                        void *stream);
 

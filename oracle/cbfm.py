@@ -18,6 +18,11 @@ Follows paper Sec. III in its own order:
 Readings where the paper is silent: GMRES with x0 = 0, modified Gram-Schmidt
 Arnoldi, restart length `restart`, stopping on ||b - A P y|| / ||b|| <= tol;
 (G^CBF)^{-1} applied exactly by an LU factorisation.
+
+The comparison arrangements of Sec. IV: the T-diagonal system Z_t of Eq.
+(MoM_T) (unknowns [alpha^J; alpha^M]) with the diagonal preconditioner D, the
+paper's conventional MoM, and the T-diagonal CBFM of Eq. (cbfm_Tdiag) without
+a preconditioner.
 """
 from __future__ import annotations
 
@@ -223,6 +228,41 @@ def solve_reduced(A: np.ndarray, Gcbf: np.ndarray, CMJ: np.ndarray, b: np.ndarra
         hs.append(h)
     jcbf = np.stack(X, axis=1)
     return Solution(CMJ @ jcbf, jcbf, its, hs)
+
+
+def tdiag(A: np.ndarray) -> np.ndarray:
+    """Eq. (MoM_T): a system in the unknown order of Eq. (Z) ([alpha^M;
+    alpha^J], or the reduced system's [M-coefficient; J-coefficient] halves)
+    rearranged for the unknowns [alpha^J; alpha^M] -- the same rows, the two
+    column halves exchanged, so that the T blocks lie on the diagonal."""
+    h = A.shape[1] // 2
+    return np.concatenate([A[:, h:], A[:, :h]], axis=1)
+
+
+def solve_tdiag(A: np.ndarray, b: np.ndarray, tol: float, restart: int = 200, maxit: int = 1000,
+                jacobi: bool = True):
+    """GMRES on Z_t D^{-1} j~ = b with j_t = D^{-1} j~ (Eq. (MoM_T)), Z_t = tdiag(A);
+    D = diag(Z_t) when `jacobi` (the diagonal preconditioner of the paper's
+    conventional MoM), else D = I (the T-diagonal CBFM, Eq. (cbfm_Tdiag)).
+    Returns (x, iterations) with x = j_t brought back to A's unknown order."""
+    Zt = tdiag(A)
+    d = np.diag(Zt).copy() if jacobi else np.ones(Zt.shape[0], np.complex128)
+    h = A.shape[1] // 2
+    X, its = [], []
+    for c in range(b.shape[1]):
+        jt, it, _ = gmres(lambda z: Zt @ z, b[:, c], tol, restart, maxit, lambda z: z / d)
+        X.append(np.concatenate([jt[h:], jt[:h]]))
+        its.append(it)
+    return np.stack(X, axis=1), its
+
+
+def conventional_mom(m: RWGMesh, eps_r: complex, waves: np.ndarray, tol: float, restart: int = 1000,
+                     maxit: int = 5000, mu_r: float = 1.0):
+    """The paper's MoM (Sec. IV): PMCHWT matrix of Eq. (Z) in the T-diagonal
+    arrangement with the diagonal preconditioner, solved by GMRES.  Returns
+    (j in the order [alpha^M; alpha^J], iterations)."""
+    Z = mom.pmchwt_matrix(m, eps_r, mu_r)
+    return solve_tdiag(Z, mom.rhs(m, waves), tol, restart, maxit, jacobi=True)
 
 
 def run(m: RWGMesh, cell, ncell, eps_r, gen, exc, delta_svd, tol, restart=200, maxit=1000,

@@ -64,6 +64,8 @@ def lib():
             "cbfm_cbf_export": [_vp, _vp, _vp, _vp],
             "cbfm_assemble_reduced": [_vp, _vp, _i32, _vp, _vp, _vp],
             "cbfm_assemble_reduced_batch": [_vp, _vp, _i32, _i32, _vp, _vp, _vp],
+            "cbfm_assemble_mom": [_vp, _i32, _vp, _vp, _vp],
+            "cbfm_tdiag_setup": [_vp, _i32, _vp],
             "cbfm_red_export": [_vp, _vp, _vp],
             "cbfm_red_export_noalloc": [_vp, _vp, _vp],
             "cbfm_cmp_setup": [_vp, _vp],
@@ -94,7 +96,7 @@ def lib():
 def exported_symbols():
     """Names of the C entry points declared in include/cbfm.h."""
     return ["cbfm_mesh", "cbfm_mesh_edges", "cbfm_mesh_info", "cbfm_mesh_cells", "cbfm_build_cbfs", "cbfm_cbf_import",
-            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_gram_export",
+            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_assemble_mom", "cbfm_tdiag_setup", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_gram_export",
             "cbfm_gram_inverse", "cbfm_solve", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
             "cbfm_profile_read"]
 
@@ -224,9 +226,12 @@ class CBFs(_Handle):
 
 
 class Reduced(_Handle):
-    def __init__(self, h, cbf: CBFs, n: int, prec: int):
+    """A reduced system (cbf set) or the conventional MoM system (cbf None)."""
+
+    def __init__(self, h, cbf: CBFs | None, n: int, prec: int, mesh: Mesh | None = None):
         super().__init__(h)
         self.cbf = cbf
+        self.mesh = mesh if mesh is not None else cbf.mesh
         self.n = n
         self.prec = prec
 
@@ -326,6 +331,19 @@ def assemble_reduced_batch(meshes, cbfs, prec: int = MIXED, stream=None) -> list
     return [Reduced(ctypes.c_void_p(out[k]), cbfs[k], int(n[k]), prec) for k in range(cnt)]
 
 
+def assemble_mom(m: Mesh, prec: int = FP64, stream=None) -> Reduced:
+    """cbfm_assemble_mom: the conventional MoM matrix Z over all RWG functions (N = 2 ne)."""
+    h = ctypes.c_void_p()
+    n = ctypes.c_int64()
+    _check(lib().cbfm_assemble_mom(m.handle, int(prec), _stream(stream), ctypes.byref(h), ctypes.byref(n)))
+    return Reduced(h, None, int(n.value), prec, mesh=m)
+
+
+def tdiag_setup(r: Reduced, jacobi: bool = True, stream=None) -> None:
+    """cbfm_tdiag_setup: T-diagonal arrangement Z_t D^{-1} (D = diag(Z_t) when jacobi, else I)."""
+    _check(lib().cbfm_tdiag_setup(r.handle, 1 if jacobi else 0, _stream(stream)))
+
+
 def tuning() -> dict:
     """cbfm_tuning: launch parameters tuned so far in this process."""
     n = lib().cbfm_tuning(None, 0)
@@ -351,14 +369,20 @@ class SolveResult:
 PER_RHS = 0
 BLOCK = 1
 
+PC_NONE = 0     # K-diagonal system, no preconditioner
+PC_CMP = 1      # Calderon multiplicative preconditioner (cmp_setup)
+PC_TDIAG = 2    # T-diagonal arrangement (tdiag_setup)
+
 
 def solve(r: Reduced, exc, tol: float = 1e-6, maxit: int = 2000, restart: int = 1000, use_cmp: bool = True,
           obs=None, monostatic: bool = False, want_j: bool = True, out_j=None, out_rcs=None, stream=None,
-          allow_noconv: bool = False, solver: int = PER_RHS) -> SolveResult:
-    """cbfm_solve: GMRES on the reduced system (solver PER_RHS or BLOCK), currents and RCS."""
+          allow_noconv: bool = False, solver: int = PER_RHS, precond: int | None = None) -> SolveResult:
+    """cbfm_solve: GMRES on the reduced system (solver PER_RHS or BLOCK), currents and RCS.
+    precond (PC_NONE, PC_CMP, PC_TDIAG) overrides use_cmp when given."""
     e, ke = _ptr(exc, np.float64)
     nrhs = int(ke.shape[0])
-    ne = r.cbf.mesh.n_edges
+    ne = r.mesh.n_edges
+    pc = int(precond) if precond is not None else (PC_CMP if use_cmp else PC_NONE)
     iters = np.zeros(nrhs, np.int32)
     resid = np.zeros(nrhs, np.float64)
     j = None
@@ -386,7 +410,7 @@ def solve(r: Reduced, exc, tol: float = 1e-6, maxit: int = 2000, restart: int = 
         rp = ctypes.c_void_p(rcs.ctypes.data)
     else:
         rp = None
-    st = lib().cbfm_solve(r.handle, e, nrhs, float(tol), int(maxit), int(restart), 1 if use_cmp else 0, int(solver), jp, op,
+    st = lib().cbfm_solve(r.handle, e, nrhs, float(tol), int(maxit), int(restart), pc, int(solver), jp, op,
                           int(nd), rp, ctypes.c_void_p(iters.ctypes.data), ctypes.c_void_p(resid.ctypes.data),
                           _stream(stream))
     if st != 0 and not (st == 5 and allow_noconv):

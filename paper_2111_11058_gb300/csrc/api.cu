@@ -786,6 +786,53 @@ cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precisi
     });
 }
 
+cbfm_status cbfm_assemble_mom(cbfm_mesh_t mesh, cbfm_precision prec, void *stream, cbfm_red_t *out, int64_t *n) {
+    return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
+        Mesh *m = (Mesh *)mesh;
+        check_device(m, H_MESH, "mesh");
+        CBFM_REQUIRE(out, "NULL out");
+        CBFM_REQUIRE(prec == CBFM_FP64 || prec == CBFM_MIXED || prec == CBFM_MIXED_SIMT, "unknown precision");
+        *out = nullptr;
+        cudaStream_t st = (cudaStream_t)stream;
+        std::unique_ptr<Red> r(new Red());
+        r->kind = H_RED;
+        r->device = m->device;
+        r->mesh = m;
+        r->cbf = nullptr;
+        r->prec = prec;
+        const int64_t ne = m->h.ne;
+        r->n = 2 * ne;
+        // Z = [[Ks, Ta], [Tb, Ks]] (Eq. (Z)) from the RWG blocks
+        if (prec == CBFM_FP64) {
+            DevBuf<z64> Z;
+            Z.alloc(3 * (size_t)ne * ne);
+            assemble_rwg<double>(*m, Z.p, st);
+            r->A64.alloc((size_t)r->n * r->n);
+            mom_place<double>(ne, Z.p, r->A64.p, st);
+        } else {
+            DevBuf<c32> Z;
+            Z.alloc(3 * (size_t)ne * ne);
+            assemble_rwg<float>(*m, Z.p, st);
+            r->A32.alloc((size_t)r->n * r->n);
+            mom_place<float>(ne, Z.p, r->A32.p, st);
+        }
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        if (n) *n = r->n;
+        *out = (cbfm_red_t)r.release();
+    });
+}
+
+cbfm_status cbfm_tdiag_setup(cbfm_red_t red, int32_t jacobi, void *stream) {
+    return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
+        Red *r = (Red *)red;
+        check_device(r, H_RED, "reduced system");
+        if (!tdiag_build(*r, jacobi != 0, (cudaStream_t)stream))
+            throw Fail{CBFM_ESINGULAR, "a diagonal entry of the T-diagonal arrangement is zero"};
+    });
+}
+
 cbfm_status cbfm_assemble_reduced_batch(const cbfm_mesh_t *meshes, const cbfm_cbf_t *cbfs, int32_t count,
                                         cbfm_precision prec, void *stream, cbfm_red_t *out, int64_t *n_cbf) {
     // created handles are freed again if a later wave fails
@@ -866,7 +913,21 @@ cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream) {
         CBFM_REQUIRE(A, "NULL A");
         cudaStream_t st = (cudaStream_t)stream;
         int64_t nn = r->n * r->n;
-        if (r->prec == CBFM_FP64) {
+        if (r->cbf == nullptr) {   // conventional MoM: Z in canonical edge order
+            DevBuf<z64> t, c;
+            const z64 *src = r->A64.p;
+            if (r->prec != CBFM_FP64) {
+                t.alloc(nn);
+                launch_c32_to_z64(r->A32.p, t.p, nn, st);
+                src = t.p;
+            }
+            DevBuf<int32_t> dmap;
+            upload(dmap, r->mesh->h.int_of_canon, st);
+            c.alloc(nn);
+            mom_to_canonical(r->mesh->h.ne, dmap.p, src, c.p, st);
+            copy_out(A, c.p, nn * sizeof(z64), st);
+            CBFM_CUDA(cudaStreamSynchronize(st));
+        } else if (r->prec == CBFM_FP64) {
             copy_out(A, r->A64.p, nn * sizeof(z64), st);
         } else {
             DevBuf<z64> t;
@@ -892,6 +953,8 @@ cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
         StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Red *r = (Red *)red;
         check_device(r, H_RED, "reduced system");
+        CBFM_REQUIRE(r->cbf != nullptr,
+                     "no CBFs: the Calderon preconditioner of the RWG-only system has a singular Gram matrix");
         cudaStream_t st = (cudaStream_t)stream;
         Mesh &m = *r->mesh;
         Cbf &c = *r->cbf;
@@ -1010,7 +1073,7 @@ cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream) {
 }
 
 cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double tol, int32_t maxit, int32_t restart,
-                       int32_t use_cmp, int32_t solver, double *j_out, const double *obs, int32_t ndir,
+                       int32_t precond, int32_t solver, double *j_out, const double *obs, int32_t ndir,
                        double *rcs_out, int32_t *iters_out, double *resid_out, void *stream) {
     cbfm_status conv = CBFM_OK;
     cbfm_status st_ = guarded([&] {
@@ -1019,14 +1082,17 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
         check_device(r, H_RED, "reduced system");
         CBFM_REQUIRE(exc && nrhs >= 1, "need at least one excitation");
         CBFM_REQUIRE(tol > 0.0 && maxit >= 1 && restart >= 1, "tol, maxit and restart must be positive");
-        CBFM_REQUIRE(!use_cmp || r->cmp_ready, "use_cmp requires cbfm_cmp_setup");
+        CBFM_REQUIRE(precond == CBFM_PC_NONE || precond == CBFM_PC_CMP || precond == CBFM_PC_TDIAG,
+                     "precond must be CBFM_PC_NONE, CBFM_PC_CMP or CBFM_PC_TDIAG");
+        CBFM_REQUIRE(precond != CBFM_PC_CMP || r->cmp_ready, "CBFM_PC_CMP requires cbfm_cmp_setup");
+        CBFM_REQUIRE(precond != CBFM_PC_TDIAG || r->tdiag_ready, "CBFM_PC_TDIAG requires cbfm_tdiag_setup");
         const bool mono = (obs == nullptr && ndir == -1);
         CBFM_REQUIRE(mono || ndir >= 0, "ndir must be >= 0, or -1 with obs == NULL for monostatic");
         CBFM_REQUIRE(mono || ndir == 0 || obs != nullptr, "obs is NULL");
         cudaStream_t st = (cudaStream_t)stream;
         Mesh &m = *r->mesh;
-        Cbf &c = *r->cbf;
-        const int64_t ne = m.h.ne, nh = c.nhalf, n = r->n;
+        Cbf *cp = r->cbf;   // NULL: conventional MoM, the basis is the RWG functions (C^M = C^J = I)
+        const int64_t ne = m.h.ne, nh = cp ? cp->nhalf : ne, n = r->n;
         const int nc = m.h.ncell;
         DevBuf<double> dexc, dobs, drcs;
         dexc.alloc(3 * (size_t)nrhs);
@@ -1037,26 +1103,32 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
         launch_rhs(m, dexc.p, nrhs, vE.p, vH.p, st, r->prec != CBFM_FP64);
         // b = (C^JM)^H v  -> (n x nrhs), then rows per rhs
         bt.alloc((size_t)n * nrhs);
-        std::vector<GemmDesc> gE, gH;
-        for (int k = 0; k < nc; ++k) {
-            int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
-            gE.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, c.coff[k] * nrhs, nrhs});
-            gH.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, (nh + c.coff[k]) * nrhs, nrhs});
-        }
         const bool f32 = r->prec != CBFM_FP64;   // mixed precision: right-hand side and recovery in FP32
-        if (f32) {
-            DevBuf<c32> e32, h32, b32;
-            e32.alloc((size_t)ne * nrhs);
-            h32.alloc((size_t)ne * nrhs);
-            b32.alloc((size_t)n * nrhs);
-            launch_z64_to_c32(vE.p, e32.p, ne * nrhs, st);
-            launch_z64_to_c32(vH.p, h32.p, ne * nrhs, st);
-            gemm_grouped<float>(gE, 2, 0, c.CJ32.p, e32.p, b32.p, false, st);
-            gemm_grouped<float>(gH, 2, 0, c.CM32.p, h32.p, b32.p, false, st);
-            launch_c32_to_z64(b32.p, bt.p, n * nrhs, st);
+        if (!cp) {   // b = v = [v^E; v^H]
+            CBFM_CUDA(cudaMemcpyAsync(bt.p, vE.p, sizeof(z64) * ne * nrhs, cudaMemcpyDeviceToDevice, st));
+            CBFM_CUDA(cudaMemcpyAsync(bt.p + ne * nrhs, vH.p, sizeof(z64) * ne * nrhs, cudaMemcpyDeviceToDevice, st));
         } else {
-            gemm_grouped<double>(gE, 2, 0, c.CJ.p, vE.p, bt.p, false, st);
-            gemm_grouped<double>(gH, 2, 0, c.CM.p, vH.p, bt.p, false, st);
+            const Cbf &c = *cp;
+            std::vector<GemmDesc> gE, gH;
+            for (int k = 0; k < nc; ++k) {
+                int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
+                gE.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, c.coff[k] * nrhs, nrhs});
+                gH.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, (nh + c.coff[k]) * nrhs, nrhs});
+            }
+            if (f32) {
+                DevBuf<c32> e32, h32, b32;
+                e32.alloc((size_t)ne * nrhs);
+                h32.alloc((size_t)ne * nrhs);
+                b32.alloc((size_t)n * nrhs);
+                launch_z64_to_c32(vE.p, e32.p, ne * nrhs, st);
+                launch_z64_to_c32(vH.p, h32.p, ne * nrhs, st);
+                gemm_grouped<float>(gE, 2, 0, c.CJ32.p, e32.p, b32.p, false, st);
+                gemm_grouped<float>(gH, 2, 0, c.CM32.p, h32.p, b32.p, false, st);
+                launch_c32_to_z64(b32.p, bt.p, n * nrhs, st);
+            } else {
+                gemm_grouped<double>(gE, 2, 0, c.CJ.p, vE.p, bt.p, false, st);
+                gemm_grouped<double>(gH, 2, 0, c.CM.p, vH.p, bt.p, false, st);
+            }
         }
         b.alloc((size_t)nrhs * n);
         {
@@ -1068,11 +1140,11 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
         x.alloc((size_t)nrhs * n);
         GmresOut go;
         if (solver == 0) {
-            go = gmres_solve(*r, b.p, nrhs, tol, maxit, restart, use_cmp != 0, x.p, st);
+            go = gmres_solve(*r, b.p, nrhs, tol, maxit, restart, precond, x.p, st);
         } else {
             for (int r0 = 0; r0 < nrhs; r0 += 128) {
                 const int cnt = std::min(128, nrhs - r0);
-                GmresOut g = bgmres_solve(*r, b.p + (int64_t)r0 * n, cnt, tol, maxit, restart, use_cmp != 0,
+                GmresOut g = bgmres_solve(*r, b.p + (int64_t)r0 * n, cnt, tol, maxit, restart, precond,
                                           x.p + (int64_t)r0 * n, st);
                 go.iters.insert(go.iters.end(), g.iters.begin(), g.iters.end());
                 go.resid.insert(go.resid.end(), g.resid.begin(), g.resid.end());
@@ -1080,23 +1152,30 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
         }
         // j = C^MJ x  (internal order, (2 ne) x nrhs)
         jint.alloc((size_t)2 * ne * nrhs);
-        std::vector<GemmDesc> jM, jJ;
-        for (int k = 0; k < nc; ++k) {
-            int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
-            jM.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, c.coff[k], n, off * nrhs, nrhs});
-            jJ.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, nh + c.coff[k], n, (ne + off) * nrhs, nrhs});
-        }
-        if (f32) {
-            DevBuf<c32> x32, j32;
-            x32.alloc((size_t)nrhs * n);
-            j32.alloc((size_t)2 * ne * nrhs);
-            launch_z64_to_c32(x.p, x32.p, nrhs * n, st);
-            gemm_grouped<float>(jM, 0, 1, c.CM32.p, x32.p, j32.p, false, st);
-            gemm_grouped<float>(jJ, 0, 1, c.CJ32.p, x32.p, j32.p, false, st);
-            launch_c32_to_z64(j32.p, jint.p, 2 * ne * nrhs, st);
+        if (!cp) {   // j = x
+            ProfScope ps_("k_transpose", st);
+            k_transpose<<<nblk(n * nrhs), 256, 0, st>>>(nrhs, n, x.p, jint.p);
+            launched("k_transpose");
         } else {
-            gemm_grouped<double>(jM, 0, 1, c.CM.p, x.p, jint.p, false, st);
-            gemm_grouped<double>(jJ, 0, 1, c.CJ.p, x.p, jint.p, false, st);
+            const Cbf &c = *cp;
+            std::vector<GemmDesc> jM, jJ;
+            for (int k = 0; k < nc; ++k) {
+                int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
+                jM.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, c.coff[k], n, off * nrhs, nrhs});
+                jJ.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, nh + c.coff[k], n, (ne + off) * nrhs, nrhs});
+            }
+            if (f32) {
+                DevBuf<c32> x32, j32;
+                x32.alloc((size_t)nrhs * n);
+                j32.alloc((size_t)2 * ne * nrhs);
+                launch_z64_to_c32(x.p, x32.p, nrhs * n, st);
+                gemm_grouped<float>(jM, 0, 1, c.CM32.p, x32.p, j32.p, false, st);
+                gemm_grouped<float>(jJ, 0, 1, c.CJ32.p, x32.p, j32.p, false, st);
+                launch_c32_to_z64(j32.p, jint.p, 2 * ne * nrhs, st);
+            } else {
+                gemm_grouped<double>(jM, 0, 1, c.CM.p, x.p, jint.p, false, st);
+                gemm_grouped<double>(jJ, 0, 1, c.CJ.p, x.p, jint.p, false, st);
+            }
         }
         if (rcs_out && (mono || ndir > 0)) {
             int nd = mono ? 1 : ndir;

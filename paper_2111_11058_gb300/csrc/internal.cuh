@@ -65,7 +65,7 @@ struct Cbf : HandleBase {
 
 struct Red : HandleBase {
     Mesh *mesh;
-    Cbf *cbf;
+    Cbf *cbf;                     // NULL for the conventional MoM system (basis = the RWG functions)
     cbfm_precision prec;
     int64_t n = 0;                // N^CBF
     DevBuf<z64> A64;
@@ -76,6 +76,12 @@ struct Red : HandleBase {
     DevBuf<z64> B64;              // B = A (G^CBF)^{-1}, the operator GMRES iterates with
     DevBuf<c32> B32;
     bool cmp_ready = false;
+    // T-diagonal arrangement (Eq. (MoM_T)): Bt = A P D^{-1} (P swaps the column halves),
+    // tdinv[k] = 1 / D_{p(k)}: the recovery x_k = y_{p(k)} tdinv[k]
+    DevBuf<z64> Bt64;
+    DevBuf<c32> Bt32;
+    DevBuf<z64> tdinv;
+    bool tdiag_ready = false;
 };
 
 // ------------------------------------------------------------- kernels
@@ -133,12 +139,30 @@ struct GmresOut {
 // out[r] = M in[r] for rows with mask[r] != 0 (M32 != NULL: complex64 / FP32 arithmetic)
 void apply_rows(const Red &rd, const z64 *M64, const c32 *M32, const z64 *in, z64 *out, int nrhs, const int *mask,
                 cudaStream_t st);
-GmresOut gmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp,
+GmresOut gmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, int pc,
                      z64 *d_x, cudaStream_t st);
 // Block GMRES over all right-hand sides at once (k_bgmres.cu); maxit counts block iterations,
 // restart caps the basis dimension; iters report the block iteration of convergence.
-GmresOut bgmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp,
+GmresOut bgmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, int pc,
                       z64 *d_x, cudaStream_t st);
+// pc (cbfm_precond): the operator GMRES iterates with, in the reduced system's precision
+inline const z64 *pc_op64(const Red &r, int pc) {
+    return pc == CBFM_PC_CMP ? r.B64.p : pc == CBFM_PC_TDIAG ? r.Bt64.p : r.A64.p;
+}
+inline const c32 *pc_op32(const Red &r, int pc) {
+    return pc == CBFM_PC_CMP ? r.B32.p : pc == CBFM_PC_TDIAG ? r.Bt32.p : r.A32.p;
+}
+
+// T-diagonal arrangement (k_tdiag.cu): builds r.Bt*, r.tdinv (jacobi: D = diag(A P), else I);
+// returns false when a diagonal entry is zero
+bool tdiag_build(Red &r, bool jacobi, cudaStream_t st);
+// x[q][k] = y[q][p(k)] tdinv[k] for nrhs rows of length r.n
+void tdiag_recover(const Red &r, const z64 *y, z64 *x, int nrhs, cudaStream_t st);
+// the conventional MoM matrix A = [[Ks, Ta], [Tb, Ks]] (2 ne x 2 ne) from Z (3 x ne x ne), internal edge order
+template <typename T>
+void mom_place(int64_t ne, const cx<T> *Z, cx<T> *A, cudaStream_t st);
+// A (n x n, n = 2 ne, internal edge order) -> canonical edge order on both sides
+void mom_to_canonical(int64_t ne, const int32_t *d_int_of_canon, const z64 *A, z64 *out, cudaStream_t st);
 
 // export of the reduced matrix without device allocation (noalloc.cu)
 void red_export_noalloc(Red &r, double *A, cudaStream_t st);

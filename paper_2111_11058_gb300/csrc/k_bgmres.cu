@@ -658,7 +658,7 @@ void rows_times(int64_t n, const z64 *M64, const c32 *M32, const z64 *in, z64 *o
 
 }  // namespace
 
-GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp, z64 *d_x,
+GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, int restart, int pc, z64 *d_x,
                       cudaStream_t st) {
     const int64_t n = rd.n;
     CBFM_REQUIRE(nrhs >= 1 && nrhs <= PCHOL_MAX, "block GMRES handles at most 128 right-hand sides per call");
@@ -744,8 +744,8 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     }
     auto applyB = [&](const z64 *in, z64 *out, int rows) {
         if (rd.prec != CBFM_FP64)
-            rows_times(n, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, rows, false, st, s_in.p, s_out.p);
-        else rows_times(n, use_cmp ? rd.B64.p : rd.A64.p, nullptr, in, out, rows, false, st, nullptr, nullptr);
+            rows_times(n, nullptr, pc_op32(rd, pc), in, out, rows, false, st, s_in.p, s_out.p);
+        else rows_times(n, pc_op64(rd, pc), nullptr, in, out, rows, false, st, nullptr, nullptr);
     };
 
     GmresOut out;
@@ -914,10 +914,11 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
         if (breakdown) break;
     }
     // x = P y
-    if (use_cmp) {   // G^CBF^{-1} is block diagonal (its two halves)
+    if (pc == CBFM_PC_CMP) {   // G^CBF^{-1} is block diagonal (its two halves)
         if (rd.prec != CBFM_FP64) rows_times(n, nullptr, rd.Ginv32.p, Y.p, d_x, p, true, st, s_in.p, s_out.p);
         else rows_times(n, rd.Ginv.p, nullptr, Y.p, d_x, p, true, st, nullptr, nullptr);
     }
+    else if (pc == CBFM_PC_TDIAG) tdiag_recover(rd, Y.p, d_x, p, st);
     else CBFM_CUDA(cudaMemcpyAsync(d_x, Y.p, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
     CBFM_CUDA(cudaStreamSynchronize(st));
     for (int q = 0; q < p; ++q) out.iters[q] = conv_at[q] >= 0 ? conv_at[q] : -total_blocks - 1;

@@ -358,12 +358,12 @@ void apply_rows(const Red &rd, const z64 *M64, const c32 *M32, const z64 *in, z6
     launched("k_matvec");
 }
 
-static void apply_B(const Red &rd, bool use_cmp, const z64 *in, z64 *out, int nrhs, const int *mask, cudaStream_t st) {
-    if (rd.prec != CBFM_FP64) apply_rows(rd, nullptr, use_cmp ? rd.B32.p : rd.A32.p, in, out, nrhs, mask, st);
-    else apply_rows(rd, use_cmp ? rd.B64.p : rd.A64.p, nullptr, in, out, nrhs, mask, st);
+static void apply_B(const Red &rd, int pc, const z64 *in, z64 *out, int nrhs, const int *mask, cudaStream_t st) {
+    if (rd.prec != CBFM_FP64) apply_rows(rd, nullptr, pc_op32(rd, pc), in, out, nrhs, mask, st);
+    else apply_rows(rd, pc_op64(rd, pc), nullptr, in, out, nrhs, mask, st);
 }
 
-GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, int restart, bool use_cmp, z64 *d_x,
+GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, int restart, int pc, z64 *d_x,
                      cudaStream_t st) {
     const int64_t n = rd.n;
     CBFM_REQUIRE(nrhs <= 65535, "nrhs must be <= 65535");
@@ -422,7 +422,7 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
     int total = 0;
     bool first = true;
     while (total < maxit) {
-        if (!first) apply_B(rd, use_cmp, y.p, w.p, nrhs, ones.p, st);
+        if (!first) apply_B(rd, pc, y.p, w.p, nrhs, ones.p, st);
         {
             ProfScope ps_("k_start", st);
             k_start<<<nrhs, 256, 0, st>>>(n, nrhs, m, d_b, w.p, first ? 0 : 1, V.p, g.p, bnorm.p, resid.p, done.p,
@@ -449,7 +449,7 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
                 k_active<<<(nrhs + 127) / 128, 128, 0, st>>>(nrhs, done.p, flag.p);
                 launched("k_active");
             }
-            apply_B(rd, use_cmp, vk, w.p, nrhs, flag.p, st);
+            apply_B(rd, pc, vk, w.p, nrhs, flag.p, st);
             dim3 gd((unsigned)((k + 1 + JB - 1) / JB), nrhs), gu((unsigned)((n + 255) / 256), nrhs);
             {
                 ProfScope ps_("k_dots", st);
@@ -522,7 +522,8 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
         CBFM_CUDA(cudaMemsetAsync(H.p, 0, sizeof(z64) * nrhs * (m + 1) * m, st));
     }
     // x = P y
-    if (use_cmp) apply_rows(rd, rd.Ginv.p, nullptr, y.p, d_x, nrhs, ones.p, st);
+    if (pc == CBFM_PC_CMP) apply_rows(rd, rd.Ginv.p, nullptr, y.p, d_x, nrhs, ones.p, st);
+    else if (pc == CBFM_PC_TDIAG) tdiag_recover(rd, y.p, d_x, nrhs, st);
     else CBFM_CUDA(cudaMemcpyAsync(d_x, y.p, sizeof(z64) * nrhs * n, cudaMemcpyDeviceToDevice, st));
     GmresOut out;
     out.iters = h_iters;
@@ -540,7 +541,7 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
         prof_add_work("k_dots", 8.0 * n * (pass1 + p2), cb * n * (pass1 + p2));
         prof_add_work("k_orth_update", 8.0 * n * (pass1 + p2), cb * n * (pass1 + p2));
         const double eb = rd.prec != CBFM_FP64 ? sizeof(c32) : sizeof(z64);
-        prof_add_work("k_matvec", 8.0 * n * n * (nmatvec + (use_cmp ? nrhs : 0)), eb * n * n * (nmatvec + 1.0));
+        prof_add_work("k_matvec", 8.0 * n * n * (nmatvec + (pc == CBFM_PC_CMP ? nrhs : 0)), eb * n * n * (nmatvec + 1.0));
     }
     return out;
 }

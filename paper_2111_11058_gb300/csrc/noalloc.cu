@@ -59,6 +59,7 @@ void red_export_noalloc(Red &r, double *A, cudaStream_t st) {
     CBFM_REQUIRE(nn <= NOALLOC_MAX_ELEMS,
                  "n_cbf = " + std::to_string(r.n) + " exceeds the no-alloc export limit of 512");
     CBFM_REQUIRE(A != nullptr, "NULL A");
+    CBFM_REQUIRE(r.cbf != nullptr, "a conventional MoM system is exported with cbfm_red_export");
     if (r.prec == CBFM_FP64) {
         // already complex128: a plain copy, no scratch needed
         copy_out(A, r.A64.p, nn * sizeof(z64), st);

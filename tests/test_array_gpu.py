@@ -10,7 +10,12 @@ sphere), one cell per sphere, eps_r 1..6, FP64 path.
   reports < 40 on its 4 x 4 x 2 array) and needs several times fewer
   iterations to 1e-4 than the K-diagonal CBFM without it (the paper reports
   1/5 at eps_r = 6 to 1/70 at eps_r = 1; measured here 38 vs 192, 14 vs 153
-  and 3 vs 136 at eps_r = 6, 3, 1); its count grows with eps_r.
+  and 3 vs 136 at eps_r = 6, 3, 1) and than the T-diagonal CBFM of Eq.
+  (cbfm_Tdiag) (measured 206, 157 and 30); its count grows with eps_r.
+* Accuracy against the conventional MoM (Eq. (MoM_T), same quadrature): the
+  RMSE of Eq. (RMSE) between the CBFM and MoM bistatic RCS at eps_r = 3 (the
+  paper reports -39.98 dB on its 4 x 4 x 2 array) stays below -30 dB
+  (measured -54.9 and -55.3 dB on the phi = 0 and 90 degree cuts).
 """
 import math
 
@@ -98,9 +103,12 @@ def array_iters(P):
         c4 = P.solve(red, EXC_MINUS_Z, tol=1e-4, maxit=1000, restart=1000, want_j=False)
         n4 = P.solve(red, EXC_MINUS_Z, tol=1e-4, maxit=2000, restart=1000, use_cmp=False, want_j=False,
                      allow_noconv=True)
-        out[eps] = (int(c6.iters[0]), int(c4.iters[0]), int(n4.iters[0]))
+        P.tdiag_setup(red, jacobi=False)
+        t4 = P.solve(red, EXC_MINUS_Z, tol=1e-4, maxit=2000, restart=1000, precond=P.PC_TDIAG, want_j=False,
+                     allow_noconv=True)
+        out[eps] = (int(c6.iters[0]), int(c4.iters[0]), int(n4.iters[0]), int(t4.iters[0]))
         red.free()
-    print("array 2x2x2 GMRES iterations (CMP 1e-6, CMP 1e-4, no CMP 1e-4):", out)
+    print("array 2x2x2 GMRES iterations (CMP 1e-6, CMP 1e-4, K-diagonal 1e-4, T-diagonal 1e-4):", out)
     return out
 
 
@@ -110,8 +118,41 @@ def test_array_cmp_reaches_1e6_under_40(array_iters):
 
 @pytest.mark.parametrize("eps", [1.0, 3.0, 6.0])
 def test_array_cmp_vs_kdiag(array_iters, eps):
-    c6, c4, n4 = array_iters[eps]
+    c6, c4, n4, t4 = array_iters[eps]
     assert c4 >= 1 and (n4 < 0 or n4 >= 4 * c4)
+
+
+@pytest.mark.parametrize("eps", [1.0, 3.0, 6.0])
+def test_array_cmp_vs_tdiag(array_iters, eps):
+    c6, c4, n4, t4 = array_iters[eps]
+    assert t4 < 0 or t4 >= 4 * c4
+
+
+def _rmse_db(sc, sm):
+    # Eq. (RMSE): RMS difference over the cut, over the reference pattern's range, in dB
+    return 10.0 * math.log10(math.sqrt(float(np.mean((sc - sm) ** 2))) / float(sm.max() - sm.min()))
+
+
+def test_array_cbfm_vs_mom_rmse(P):
+    g = W.sphere_array(2, 2, 2, SPACING, level=2, radius=1.0 / 6.0)
+    gm = _gpu_array(P, g, 8, 3.0)
+    obs = W.bistatic_cut(1.0)
+    cb = P.build_cbfs(gm, _table1_waves(), 1e-12, lmax=L_KEPT)
+    red = P.assemble_reduced(gm, cb, P.FP64)
+    P.cmp_setup(red)
+    rc = P.solve(red, EXC_MINUS_Z, tol=1e-6, maxit=1000, restart=1000, obs=obs, want_j=False)
+    red.free()
+    mo = P.assemble_mom(gm, P.FP64)
+    assert mo.n == 7680
+    P.tdiag_setup(mo, jacobi=True)
+    rm = P.solve(mo, EXC_MINUS_Z, tol=1e-6, maxit=5000, restart=1000, precond=P.PC_TDIAG, obs=obs, want_j=False)
+    mo.free()
+    nth = len(obs) // 2
+    sc, sm = rc.rcs[0].sum(-1), rm.rcs[0].sum(-1)
+    rmse = [_rmse_db(sc[k * nth:(k + 1) * nth], sm[k * nth:(k + 1) * nth]) for k in range(2)]
+    print(f"array 2x2x2 eps 3: CBFM vs MoM RCS RMSE {rmse[0]:.2f} dB (phi 0), {rmse[1]:.2f} dB (phi 90); "
+          f"GMRES iterations CBFM+CMP {int(rc.iters[0])}, MoM T-diagonal+D {int(rm.iters[0])}")
+    assert max(rmse) < -30.0
 
 
 def test_array_cmp_iterations_grow_with_eps(array_iters):
