@@ -210,6 +210,30 @@ cbfm_status cbfm_assemble_mom(cbfm_mesh_t mesh, cbfm_precision prec, void *strea
  */
 cbfm_status cbfm_tdiag_setup(cbfm_red_t red, int32_t jacobi, void *stream);
 
+/*
+ * cbfm_build_ipcbfs -- IPCBFs, GMRES version (paper Sec. III-A, the proposal
+ * after Eq. (ipcbf)), with the dual SVD orthogonalisation of cbfm_build_cbfs.
+ * Every generating wave's whole-system MoM problem, in the arrangement of Eq.
+ * (MoM_T) with its diagonal preconditioner, is solved by per-RHS GMRES and
+ * stopped at the relative residual delta_r; the coefficient sets J_m^M, J_m^J
+ * of cell m are those solutions restricted to the cell's RWG functions.  Unlike
+ * primary CBFs they carry the coupling between cells, so a connected
+ * scatterer divided into cells has no fictitious open edges.
+ *   mom        handle from cbfm_assemble_mom on the mesh the CBFs are for (its
+ *              T-diagonal Jacobi operator is built here if cbfm_tdiag_setup
+ *              was not called with jacobi != 0); its precision is the solve's
+ *   waves      (s, 3) generating plane waves (theta, phi, psi), s <= 1024
+ *   delta_r    GMRES residual allowance (the paper uses 1e-1 to 1e-3)
+ *   maxit, restart  GMRES limits per wave
+ *   delta_svd, lmax, L_per_cell, sigma_out   as for cbfm_build_cbfs
+ *   iters_out  (s) int32 GMRES iterations per wave, or NULL
+ *   out        new CBF handle for mom's mesh
+ * Returns CBFM_ENOCONV (and no handle) when a wave does not reach delta_r.
+ */
+cbfm_status cbfm_build_ipcbfs(cbfm_red_t mom, const double *waves, int32_t s, double delta_r, int32_t maxit,
+                              int32_t restart, double delta_svd, int32_t lmax, void *stream, cbfm_cbf_t *out,
+                              int32_t *L_per_cell, double *sigma_out, int32_t *iters_out);
+
 /* A as complex128 row-major (n_cbf, n_cbf), host or device. */
 cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream);
 

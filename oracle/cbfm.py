@@ -96,17 +96,39 @@ def primary_cbfs(m: RWGMesh, cell: np.ndarray, ncell: int, eps_r: complex, gen: 
         Vm = np.vstack([v[lam], v[ne + lam]])
         lu = sla.lu_factor(Zmm)
         Jm = sla.lu_solve(lu, Vm)
-        JM, JJ = Jm[:Nm], Jm[Nm:]
-        Gm = rwg_gram(m, lam, lam)
-        Gp = JM.conj().T @ Gm @ JJ
-        U, S, Vh = np.linalg.svd(Gp)
-        L = int(np.sum(S / S[0] >= delta_svd))
-        if Lmax is not None:
-            L = min(L, Lmax)
-        CM = JM @ U[:, :L]
-        CJ = JJ @ Vh.conj().T[:, :L]
-        out.append(CellCBF(lam, CM, CJ, S, L))
+        out.append(cell_dual_cbfs(m, lam, Jm[:Nm], Jm[Nm:], delta_svd, Lmax))
     return out
+
+
+def cell_dual_cbfs(m: RWGMesh, lam: np.ndarray, JM: np.ndarray, JJ: np.ndarray, delta_svd: float,
+                   Lmax: int | None = None) -> CellCBF:
+    """Steps 2-4 for one cell from its coefficient sets J^M, J^J (N_m x s)."""
+    Gm = rwg_gram(m, lam, lam)
+    Gp = JM.conj().T @ Gm @ JJ
+    U, S, Vh = np.linalg.svd(Gp)
+    L = int(np.sum(S / S[0] >= delta_svd))
+    if Lmax is not None:
+        L = min(L, Lmax)
+    CM = JM @ U[:, :L]
+    CJ = JJ @ Vh.conj().T[:, :L]
+    return CellCBF(lam, CM, CJ, S, L)
+
+
+def ipcbfs(m: RWGMesh, cell: np.ndarray, ncell: int, eps_r: complex, gen: np.ndarray, delta_r: float,
+           delta_svd: float, mu_r: float = 1.0, Lmax: int | None = None, restart: int = 1000, maxit: int = 5000):
+    """IPCBFs, GMRES version (Sec. III-A, after Eq. (ipcbf)): the whole MoM system,
+    arranged as in Eq. (MoM_T) with its diagonal preconditioner, solved by GMRES
+    for each generating wave and stopped at the relative residual delta_r; the
+    coefficient sets J_m^M, J_m^J of cell m are those solutions restricted to the
+    cell's RWG functions; steps 2-4 follow as for primary CBFs.  Returns (CBFs of
+    every cell, GMRES iterations per wave)."""
+    j, its = conventional_mom(m, eps_r, gen, delta_r, restart, maxit, mu_r)
+    ne = m.ne
+    out = []
+    for c in range(ncell):
+        lam = np.nonzero(cell == c)[0]
+        out.append(cell_dual_cbfs(m, lam, j[lam], j[ne + lam], delta_svd, Lmax))
+    return out, its
 
 
 def block_C(cbfs, ne: int, which: str) -> np.ndarray:

@@ -66,6 +66,7 @@ def lib():
             "cbfm_assemble_reduced_batch": [_vp, _vp, _i32, _i32, _vp, _vp, _vp],
             "cbfm_assemble_mom": [_vp, _i32, _vp, _vp, _vp],
             "cbfm_tdiag_setup": [_vp, _i32, _vp],
+            "cbfm_build_ipcbfs": [_vp, _vp, _i32, _f64, _i32, _i32, _f64, _i32, _vp, _vp, _vp, _vp, _vp],
             "cbfm_red_export": [_vp, _vp, _vp],
             "cbfm_red_export_noalloc": [_vp, _vp, _vp],
             "cbfm_cmp_setup": [_vp, _vp],
@@ -96,7 +97,7 @@ def lib():
 def exported_symbols():
     """Names of the C entry points declared in include/cbfm.h."""
     return ["cbfm_mesh", "cbfm_mesh_edges", "cbfm_mesh_info", "cbfm_mesh_cells", "cbfm_build_cbfs", "cbfm_cbf_import",
-            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_assemble_mom", "cbfm_tdiag_setup", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_gram_export",
+            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_assemble_mom", "cbfm_tdiag_setup", "cbfm_build_ipcbfs", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_gram_export",
             "cbfm_gram_inverse", "cbfm_solve", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
             "cbfm_profile_read"]
 
@@ -342,6 +343,28 @@ def assemble_mom(m: Mesh, prec: int = FP64, stream=None) -> Reduced:
 def tdiag_setup(r: Reduced, jacobi: bool = True, stream=None) -> None:
     """cbfm_tdiag_setup: T-diagonal arrangement Z_t D^{-1} (D = diag(Z_t) when jacobi, else I)."""
     _check(lib().cbfm_tdiag_setup(r.handle, 1 if jacobi else 0, _stream(stream)))
+
+
+def build_ipcbfs(mom: Reduced, waves, delta_r: float = 1e-2, delta_svd: float = 1e-3, lmax: int = 0,
+                 maxit: int = 5000, restart: int = 200, stream=None) -> CBFs:
+    """cbfm_build_ipcbfs: IPCBFs from loose-tolerance GMRES solutions of the whole MoM
+    system (a handle from assemble_mom), dual SVD orthogonalised.  The GMRES
+    iteration count of every wave is kept in the result's `iters`."""
+    if mom.cbf is not None:
+        raise ValueError("build_ipcbfs needs a handle from assemble_mom")
+    m = mom.mesh
+    w, kw = _ptr(waves, np.float64)
+    s = int(kw.shape[0])
+    L = np.zeros(m.n_cells, np.int32)
+    sig = np.zeros((m.n_cells, s), np.float64)
+    its = np.zeros(s, np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().cbfm_build_ipcbfs(mom.handle, w, s, float(delta_r), int(maxit), int(restart), float(delta_svd),
+                                   int(lmax), _stream(stream), ctypes.byref(h), ctypes.c_void_p(L.ctypes.data),
+                                   ctypes.c_void_p(sig.ctypes.data), ctypes.c_void_p(its.ctypes.data)))
+    cb = CBFs(h, m, L, sig)
+    cb.iters = its
+    return cb
 
 
 def tuning() -> dict:

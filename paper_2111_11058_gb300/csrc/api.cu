@@ -154,6 +154,19 @@ __global__ void k_extract_v(int ncell, const int32_t *__restrict__ cell_off, con
     }
 }
 
+// IPCBF coefficient sets: [J^M; J^J] of cell c from the whole-system solutions x (s rows of
+// [alpha^M; alpha^J], length 2 ne, internal edge order)
+__global__ void k_ipcbf_gather(int ncell, const int32_t *__restrict__ cell_off, const int64_t *__restrict__ voff,
+                               int s, int64_t ne, const z64 *__restrict__ x, z64 *__restrict__ out) {
+    const int c = blockIdx.y;
+    const int64_t off = cell_off[c], N = cell_off[c + 1] - off;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < 2 * N * s;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / s, w = idx % s;
+        out[voff[c] + idx] = x[w * 2 * ne + (i < N ? off + i : ne + off + i - N)];
+    }
+}
+
 // dense G_m (N_m x N_m) of every cell from the sparse Gram rows
 __global__ void k_cell_gram(int ncell, const int32_t *__restrict__ cell_off, const int64_t *__restrict__ goff,
                             const double *__restrict__ val, const int32_t *__restrict__ col, z64 *__restrict__ G) {
@@ -311,6 +324,130 @@ void cbf_make32(Cbf &c, cudaStream_t st) {
     c.CJ32.alloc(tot);
     launch_z64_to_c32(c.CM.p, c.CM32.p, tot, st);
     launch_z64_to_c32(c.CJ.p, c.CJ32.p, tot, st);
+}
+
+// Steps after the coefficient sets (paper Eqs. (gram_CBF), (gram_CBF_SVD), (CBF)): G'_m = (J^M)^H G_m J^J,
+// SVD, truncation sigma_i / sigma_1 >= delta_svd (at most lmax when > 0), C^M = J^M U_L, C^J = J^J V_L.
+// Vm holds, per cell, [J^M; J^J] (2 N_m x s, row-major) at voff[c].
+std::unique_ptr<Cbf> dual_cbfs(Mesh *m, int s, const z64 *Vm, const std::vector<int64_t> &voff, double delta_svd,
+                               int lmax, int32_t *L_per_cell, double *sigma_out, cudaStream_t st) {
+    const HostMesh &h = m->h;
+    const int nc = h.ncell;
+    std::vector<int64_t> goff(nc + 1, 0), soff(nc);
+    std::vector<int> nn(nc);
+    for (int c = 0; c < nc; ++c) {
+        int64_t N = h.cell_off[c + 1] - h.cell_off[c];
+        nn[c] = (int)(2 * N);
+        goff[c + 1] = goff[c] + N * N;
+        soff[c] = (int64_t)c * s * s;
+    }
+    DevBuf<int32_t> dcoff;
+    upload(dcoff, h.cell_off, st);
+    DevBuf<int64_t> dgoff;
+    upload(dgoff, goff, st);
+    DevBuf<int> info;
+    info.alloc(nc);
+    std::vector<int> hinfo(nc);
+    // Gram of every cell, G'_m = (J^M)^H G_m J^J
+    DevBuf<z64> Gm, T1, Gp, X, Vs;
+    Gm.alloc(goff[nc]);
+    {
+        ProfScope ps_("k_cell_gram", st);
+        k_cell_gram<<<dim3(nblk(4096), nc), 256, 0, st>>>(nc, dcoff.p, dgoff.p, m->gram_val.p, m->gram_col.p, Gm.p);
+        launched("k_cell_gram");
+    }
+    std::vector<int64_t> t1off(nc);
+    int64_t t1t = 0;
+    for (int c = 0; c < nc; ++c) {
+        t1off[c] = t1t;
+        t1t += (int64_t)(nn[c] / 2) * s;
+    }
+    T1.alloc(t1t);
+    Gp.alloc((size_t)nc * s * s);
+    std::vector<GemmDesc> g1, g2;
+    for (int c = 0; c < nc; ++c) {
+        int64_t N = nn[c] / 2;
+        // T1 = G_m J^J  (J^J = rows N..2N-1 of V_m)
+        g1.push_back(GemmDesc{N, s, N, goff[c], N, voff[c] + N * s, s, t1off[c], s});
+        // G' = (J^M)^H T1
+        g2.push_back(GemmDesc{s, s, N, voff[c], s, t1off[c], s, soff[c], s});
+    }
+    gemm_grouped<double>(g1, 0, 0, Gm.p, Vm, T1.p, false, st);
+    gemm_grouped<double>(g2, 2, 0, Vm, T1.p, Gp.p, false, st);
+    X.alloc((size_t)nc * s * s);
+    Vs.alloc((size_t)nc * s * s);
+    {
+        ProfScope ps_("k_to_colmajor", st);
+        k_to_colmajor<<<dim3(nblk((int64_t)s * s), nc), 256, 0, st>>>(s, Gp.p, X.p);
+        launched("k_to_colmajor");
+    }
+    DevBuf<double> sig;
+    sig.alloc((size_t)nc * s);
+    CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int) * nc, st));
+    jacobi_svd_batched(nc, s, X.p, Vs.p, sig.p, info.p, st);
+    std::vector<double> hs((size_t)nc * s);
+    CBFM_CUDA(cudaMemcpyAsync(hs.data(), sig.p, sizeof(double) * nc * s, cudaMemcpyDeviceToHost, st));
+    CBFM_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
+    CBFM_CUDA(cudaStreamSynchronize(st));
+    for (int c = 0; c < nc; ++c)
+        if (hinfo[c]) throw Fail{hinfo[c] == 1 ? CBFM_ETIMEOUT : CBFM_ECUDA,
+                                 (hinfo[c] == 1 ? "Jacobi SVD: a cluster synchronisation expired in cell "
+                                                : "Jacobi SVD did not converge in cell ") + std::to_string(c)};
+    // truncation: keep sigma_i / sigma_1 >= delta_svd (paper Eq. (gram_CBF_SVD))
+    std::unique_ptr<Cbf> cb(new Cbf());
+    cb->kind = H_CBF;
+    cb->device = m->device;
+    cb->mesh = m;
+    cb->L.assign(nc, 0);
+    std::vector<int32_t> perm((size_t)nc * s);
+    std::vector<int64_t> loff(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) {
+        int32_t *pc = perm.data() + (size_t)c * s;
+        std::iota(pc, pc + s, 0);
+        const double *sc = hs.data() + (size_t)c * s;
+        std::stable_sort(pc, pc + s, [&](int a, int b) { return sc[a] > sc[b]; });
+        double s1 = sc[pc[0]];
+        CBFM_REQUIRE(s1 > 0.0, "zero CBF Gram matrix in cell " + std::to_string(c));
+        int L = 0;
+        for (int i = 0; i < s; ++i)
+            if (sc[pc[i]] / s1 >= delta_svd) ++L;
+        if (lmax > 0) L = std::min(L, (int)lmax);
+        L = std::min<int>(L, nn[c] / 2);
+        L = std::max(L, 1);
+        cb->L[c] = L;
+        L_per_cell[c] = L;
+        if (sigma_out)
+            for (int i = 0; i < s; ++i) sigma_out[(size_t)c * s + i] = sc[pc[i]] / s1;
+        loff[c + 1] = loff[c] + (int64_t)s * L;
+    }
+    cbf_finish(*cb);
+    DevBuf<int32_t> dperm, dL;
+    DevBuf<int64_t> dloff;
+    upload(dperm, perm, st);
+    upload(dL, cb->L, st);
+    upload(dloff, loff, st);
+    DevBuf<z64> UL, VL;
+    UL.alloc(loff[nc]);
+    VL.alloc(loff[nc]);
+    {
+        ProfScope ps_("k_select", st);
+        k_select<<<dim3(nblk((int64_t)s * 64), nc), 256, 0, st>>>(s, dperm.p, dL.p, dloff.p, X.p, Vs.p, sig.p, UL.p,
+                                                                  VL.p);
+        launched("k_select");
+    }
+    // C^M = J^M U_L, C^J = J^J V_L (paper Eq. (CBF))
+    cb->CM.alloc(cb->boff[nc]);
+    cb->CJ.alloc(cb->boff[nc]);
+    std::vector<GemmDesc> gm, gj;
+    for (int c = 0; c < nc; ++c) {
+        int64_t N = nn[c] / 2, L = cb->L[c];
+        gm.push_back(GemmDesc{N, L, s, voff[c], s, loff[c], L, cb->boff[c], L});
+        gj.push_back(GemmDesc{N, L, s, voff[c] + N * s, s, loff[c], L, cb->boff[c], L});
+    }
+    gemm_grouped<double>(gm, 0, 0, Vm, UL.p, cb->CM.p, false, st);
+    gemm_grouped<double>(gj, 0, 0, Vm, VL.p, cb->CJ.p, false, st);
+    cbf_make32(*cb, st);
+    return cb;
 }
 
 }  // namespace
@@ -515,7 +652,7 @@ cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, do
         vH.alloc((size_t)ne * s);
         launch_rhs(*m, dw.p, s, vE.p, vH.p, st);
         // per-cell systems
-        std::vector<int64_t> zoff(nc), voff(nc), goff(nc + 1, 0), soff(nc);
+        std::vector<int64_t> zoff(nc), voff(nc);
         std::vector<int> nn(nc);
         int64_t zt = 0, vt = 0;
         for (int c = 0; c < nc; ++c) {
@@ -525,18 +662,15 @@ cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, do
             nn[c] = (int)(2 * N);
             zt += 4 * N * N;
             vt += 2 * N * s;
-            goff[c + 1] = goff[c] + N * N;
-            soff[c] = (int64_t)c * s * s;
         }
         DevBuf<z64> Zmm, Vm;
         Zmm.alloc(zt);
         Vm.alloc(vt);
         DevBuf<int32_t> dcoff;
         upload(dcoff, h.cell_off, st);
-        DevBuf<int64_t> dzoff, dvoff, dgoff;
+        DevBuf<int64_t> dzoff, dvoff;
         upload(dzoff, zoff, st);
         upload(dvoff, voff, st);
-        upload(dgoff, goff, st);
         {
             ProfScope ps_("k_extract_zmm", st);
             k_extract_zmm<<<dim3(nblk(4096 * 16), nc), 256, 0, st>>>(nc, dcoff.p, dzoff.p, ne, Z.p, Zmm.p);
@@ -558,105 +692,81 @@ cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, do
         for (int c = 0; c < nc; ++c)
             if (hinfo[c]) throw Fail{CBFM_ESINGULAR, "singular Z_mm in cell " + std::to_string(c)};
         Zmm.release();
-        // Gram of every cell, G'_m = (J^M)^H G_m J^J
-        DevBuf<z64> Gm, T1, Gp, X, Vs;
-        Gm.alloc(goff[nc]);
-        {
-            ProfScope ps_("k_cell_gram", st);
-            k_cell_gram<<<dim3(nblk(4096), nc), 256, 0, st>>>(nc, dcoff.p, dgoff.p, m->gram_val.p, m->gram_col.p, Gm.p);
-            launched("k_cell_gram");
-        }
-        std::vector<int64_t> t1off(nc);
-        int64_t t1t = 0;
-        for (int c = 0; c < nc; ++c) {
-            t1off[c] = t1t;
-            t1t += (int64_t)(nn[c] / 2) * s;
-        }
-        T1.alloc(t1t);
-        Gp.alloc((size_t)nc * s * s);
-        std::vector<GemmDesc> g1, g2;
-        for (int c = 0; c < nc; ++c) {
-            int64_t N = nn[c] / 2;
-            // T1 = G_m J^J  (J^J = rows N..2N-1 of V_m)
-            g1.push_back(GemmDesc{N, s, N, goff[c], N, voff[c] + N * s, s, t1off[c], s});
-            // G' = (J^M)^H T1
-            g2.push_back(GemmDesc{s, s, N, voff[c], s, t1off[c], s, soff[c], s});
-        }
-        gemm_grouped<double>(g1, 0, 0, Gm.p, Vm.p, T1.p, false, st);
-        gemm_grouped<double>(g2, 2, 0, Vm.p, T1.p, Gp.p, false, st);
-        X.alloc((size_t)nc * s * s);
-        Vs.alloc((size_t)nc * s * s);
-        {
-            ProfScope ps_("k_to_colmajor", st);
-            k_to_colmajor<<<dim3(nblk((int64_t)s * s), nc), 256, 0, st>>>(s, Gp.p, X.p);
-            launched("k_to_colmajor");
-        }
-        DevBuf<double> sig;
-        sig.alloc((size_t)nc * s);
-        CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int) * nc, st));
-        jacobi_svd_batched(nc, s, X.p, Vs.p, sig.p, info.p, st);
-        std::vector<double> hs((size_t)nc * s);
-        CBFM_CUDA(cudaMemcpyAsync(hs.data(), sig.p, sizeof(double) * nc * s, cudaMemcpyDeviceToHost, st));
-        CBFM_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
+        std::unique_ptr<Cbf> cb = dual_cbfs(m, s, Vm.p, voff, delta_svd, lmax, L_per_cell, sigma_out, st);
         CBFM_CUDA(cudaStreamSynchronize(st));
-        for (int c = 0; c < nc; ++c)
-            if (hinfo[c]) throw Fail{hinfo[c] == 1 ? CBFM_ETIMEOUT : CBFM_ECUDA,
-                                     (hinfo[c] == 1 ? "Jacobi SVD: a cluster synchronisation expired in cell "
-                                                    : "Jacobi SVD did not converge in cell ") + std::to_string(c)};
-        // truncation: keep sigma_i / sigma_1 >= delta_svd (paper Eq. (gram_CBF_SVD))
-        std::unique_ptr<Cbf> cb(new Cbf());
-        cb->kind = H_CBF;
-        cb->device = m->device;
-        cb->mesh = m;
-        cb->L.assign(nc, 0);
-        std::vector<int32_t> perm((size_t)nc * s);
-        std::vector<int64_t> loff(nc + 1, 0);
-        for (int c = 0; c < nc; ++c) {
-            int32_t *pc = perm.data() + (size_t)c * s;
-            std::iota(pc, pc + s, 0);
-            const double *sc = hs.data() + (size_t)c * s;
-            std::stable_sort(pc, pc + s, [&](int a, int b) { return sc[a] > sc[b]; });
-            double s1 = sc[pc[0]];
-            CBFM_REQUIRE(s1 > 0.0, "zero CBF Gram matrix in cell " + std::to_string(c));
-            int L = 0;
-            for (int i = 0; i < s; ++i)
-                if (sc[pc[i]] / s1 >= delta_svd) ++L;
-            if (lmax > 0) L = std::min(L, (int)lmax);
-            L = std::min<int>(L, nn[c] / 2);
-            L = std::max(L, 1);
-            cb->L[c] = L;
-            L_per_cell[c] = L;
-            if (sigma_out)
-                for (int i = 0; i < s; ++i) sigma_out[(size_t)c * s + i] = sc[pc[i]] / s1;
-            loff[c + 1] = loff[c] + (int64_t)s * L;
-        }
-        cbf_finish(*cb);
-        DevBuf<int32_t> dperm, dL;
-        DevBuf<int64_t> dloff;
-        upload(dperm, perm, st);
-        upload(dL, cb->L, st);
-        upload(dloff, loff, st);
-        DevBuf<z64> UL, VL;
-        UL.alloc(loff[nc]);
-        VL.alloc(loff[nc]);
+        *out = (cbfm_cbf_t)cb.release();
+    });
+}
+
+cbfm_status cbfm_build_ipcbfs(cbfm_red_t mom, const double *waves, int32_t s, double delta_r, int32_t maxit,
+                              int32_t restart, double delta_svd, int32_t lmax, void *stream, cbfm_cbf_t *out,
+                              int32_t *L_per_cell, double *sigma_out, int32_t *iters_out) {
+    return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
+        Red *r = (Red *)mom;
+        check_device(r, H_RED, "MoM system");
+        CBFM_REQUIRE(r->cbf == nullptr, "IPCBFs are generated from a cbfm_assemble_mom handle");
+        CBFM_REQUIRE(out && waves && L_per_cell, "NULL argument");
+        *out = nullptr;
+        CBFM_REQUIRE(s >= 1 && s <= 1024, "s must be in [1, 1024]");
+        CBFM_REQUIRE(delta_r > 0.0 && maxit >= 1 && restart >= 1, "delta_r, maxit and restart must be positive");
+        CBFM_REQUIRE(delta_svd >= 0.0 && delta_svd <= 1.0, "delta_svd must be in [0, 1]");
+        cudaStream_t st = (cudaStream_t)stream;
+        Mesh *m = r->mesh;
+        const HostMesh &h = m->h;
+        const int nc = h.ncell;
+        const int64_t ne = h.ne, n = r->n;
+        // the MoM arrangement of Eq. (MoM_T): T-diagonal with the diagonal preconditioner
+        if (!(r->tdiag_ready && r->tdiag_jacobi) && !tdiag_build(*r, true, st))
+            throw Fail{CBFM_ESINGULAR, "a diagonal entry of the T-diagonal arrangement is zero"};
+        DevBuf<double> dw;
+        dw.alloc(3 * (size_t)s);
+        copy_in(dw.p, waves, 3 * sizeof(double) * s, st);
+        DevBuf<z64> vE, vH, bt, b, x;
+        vE.alloc((size_t)ne * s);
+        vH.alloc((size_t)ne * s);
+        launch_rhs(*m, dw.p, s, vE.p, vH.p, st, r->prec != CBFM_FP64);
+        bt.alloc((size_t)n * s);
+        CBFM_CUDA(cudaMemcpyAsync(bt.p, vE.p, sizeof(z64) * ne * s, cudaMemcpyDeviceToDevice, st));
+        CBFM_CUDA(cudaMemcpyAsync(bt.p + ne * s, vH.p, sizeof(z64) * ne * s, cudaMemcpyDeviceToDevice, st));
+        vE.release();
+        vH.release();
+        b.alloc((size_t)n * s);
         {
-            ProfScope ps_("k_select", st);
-            k_select<<<dim3(nblk((int64_t)s * 64), nc), 256, 0, st>>>(s, dperm.p, dL.p, dloff.p, X.p, Vs.p, sig.p, UL.p,
-                                                                      VL.p);
-            launched("k_select");
+            ProfScope ps_("k_transpose", st);
+            k_transpose<<<nblk(n * s), 256, 0, st>>>(n, s, bt.p, b.p);
+            launched("k_transpose");
         }
-        // C^M = J^M U_L, C^J = J^J V_L (paper Eq. (CBF))
-        cb->CM.alloc(cb->boff[nc]);
-        cb->CJ.alloc(cb->boff[nc]);
-        std::vector<GemmDesc> gm, gj;
+        bt.release();
+        // each generating wave's whole-system GMRES solution, stopped at relative residual delta_r
+        x.alloc((size_t)n * s);
+        GmresOut go = gmres_solve(*r, b.p, s, delta_r, maxit, restart, CBFM_PC_TDIAG, x.p, st);
+        for (int w = 0; w < s; ++w) {
+            if (iters_out) iters_out[w] = go.iters[w] >= 0 ? go.iters[w] : -go.iters[w] - 1;
+            if (go.iters[w] < 0)
+                throw Fail{CBFM_ENOCONV, "IPCBF wave " + std::to_string(w) + " did not reach delta_r within maxit"};
+        }
+        b.release();
+        // coefficient sets of every cell: the solutions restricted to the cell's RWG functions
+        std::vector<int64_t> voff(nc);
+        int64_t vt = 0;
         for (int c = 0; c < nc; ++c) {
-            int64_t N = nn[c] / 2, L = cb->L[c];
-            gm.push_back(GemmDesc{N, L, s, voff[c], s, loff[c], L, cb->boff[c], L});
-            gj.push_back(GemmDesc{N, L, s, voff[c] + N * s, s, loff[c], L, cb->boff[c], L});
+            voff[c] = vt;
+            vt += 2 * (int64_t)(h.cell_off[c + 1] - h.cell_off[c]) * s;
         }
-        gemm_grouped<double>(gm, 0, 0, Vm.p, UL.p, cb->CM.p, false, st);
-        gemm_grouped<double>(gj, 0, 0, Vm.p, VL.p, cb->CJ.p, false, st);
-        cbf_make32(*cb, st);
+        DevBuf<z64> Vm;
+        Vm.alloc(vt);
+        DevBuf<int32_t> dcoff;
+        upload(dcoff, h.cell_off, st);
+        DevBuf<int64_t> dvoff;
+        upload(dvoff, voff, st);
+        {
+            ProfScope ps_("k_ipcbf_gather", st);
+            k_ipcbf_gather<<<dim3(nblk(4096 * 4), nc), 256, 0, st>>>(nc, dcoff.p, dvoff.p, s, ne, x.p, Vm.p);
+            launched("k_ipcbf_gather");
+        }
+        x.release();
+        std::unique_ptr<Cbf> cb = dual_cbfs(m, s, Vm.p, voff, delta_svd, lmax, L_per_cell, sigma_out, st);
         CBFM_CUDA(cudaStreamSynchronize(st));
         *out = (cbfm_cbf_t)cb.release();
     });

@@ -82,6 +82,7 @@ struct Red : HandleBase {
     DevBuf<c32> Bt32;
     DevBuf<z64> tdinv;
     bool tdiag_ready = false;
+    bool tdiag_jacobi = false;
 };
 
 // ------------------------------------------------------------- kernels

@@ -131,6 +131,7 @@ bool tdiag_build(Red &r, bool jacobi, cudaStream_t st) {
     CBFM_CUDA(cudaStreamSynchronize(st));
     if (h) return false;
     r.tdiag_ready = true;
+    r.tdiag_jacobi = jacobi;
     return true;
 }
 
