@@ -69,7 +69,8 @@ typedef enum {
 typedef enum {
     CBFM_PC_NONE = 0,     /* the K-diagonal system as assembled (Eq. (Z) order), no preconditioner */
     CBFM_PC_CMP = 1,      /* Calderon multiplicative preconditioner (G^CBF)^{-1} (cbfm_cmp_setup) */
-    CBFM_PC_TDIAG = 2     /* T-diagonal arrangement with optional Jacobi scaling (cbfm_tdiag_setup) */
+    CBFM_PC_TDIAG = 2,    /* T-diagonal arrangement with optional Jacobi scaling (cbfm_tdiag_setup) */
+    CBFM_PC_CMP_INEXACT = 3   /* CMP with (G^CBF)^{-1} by an inner GMRES (cbfm_cmp_setup_inexact) */
 } cbfm_precond;
 
 /*
@@ -269,6 +270,21 @@ cbfm_status cbfm_red_export_noalloc(cbfm_red_t red, double *A, void *stream);
 cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream);
 
 /*
+ * cbfm_cmp_setup_inexact -- the CMP as the paper applies it (Sec. III-C, after
+ * Eq. (CBFM_inner); Sec. IV): G^CBF as in cbfm_cmp_setup, but no inverse.
+ * Every application of (G^CBF)^{-1} inside cbfm_solve (precond
+ * CBFM_PC_CMP_INEXACT: once per outer GMRES step and once for j^CBF) is an
+ * inner per-RHS GMRES on G^CBF z = v, right-preconditioned by the diagonal
+ * D^CBF = 1 / diag(G^CBF), FP64, x0 = 0, stopped at relative residual
+ * inner_tol (the paper: 1e-5) or after inner_maxit steps (restart
+ * inner_restart).  The outer preconditioner then varies slightly from step to
+ * step, as in the paper.  Returns CBFM_ESINGULAR when a diagonal entry of
+ * G^CBF is zero.
+ */
+cbfm_status cbfm_cmp_setup_inexact(cbfm_red_t red, double inner_tol, int32_t inner_maxit, int32_t inner_restart,
+                                   void *stream);
+
+/*
  * cbfm_gram_inverse -- the inverse routine of cbfm_cmp_setup applied to
  * caller matrices: a testing hook for both of its paths (the paper has no
  * counterpart).  A: nbatch complex128 row-major n x n matrices, consecutive,
@@ -289,7 +305,8 @@ cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream);
  *   exc     (nrhs, 3) excitations (theta, phi, psi)
  *   precond CBFM_PC_CMP: P = (G^CBF)^{-1} (requires cbfm_cmp_setup);
  *           CBFM_PC_NONE: P = I; CBFM_PC_TDIAG: P = (column-half swap) D^{-1}
- *           as set by cbfm_tdiag_setup (required)
+ *           as set by cbfm_tdiag_setup (required); CBFM_PC_CMP_INEXACT: P =
+ *           the inner GMRES of cbfm_cmp_setup_inexact (required)
  *   j_out   (2 ne, nrhs) complex128 RWG coefficients in canonical edge order, or NULL
  *   obs     (ndir, 2) observation directions (theta, phi); obs == NULL with
  *           ndir == -1 selects monostatic: each RHS observed at its own arrival

@@ -13,7 +13,8 @@ Follows paper Sec. III in its own order:
      A = (C^JM)^H Z C^MJ and b = (C^JM)^H v  (Eq. (CBFM_outer));
   6. G^CBF = (C^JM)^H G_ffff C^MJ  (Eq. (CBF_Gram_matrix));
   7. GMRES on A (G^CBF)^{-1} y = b, then G^CBF j^CBF = y (Eq. (CBFM_inner))
-     and j = C^MJ j^CBF  (Eq. (trans_current)).
+     and j = C^MJ j^CBF  (Eq. (trans_current)); (G^CBF)^{-1} exact (LU) or, as
+     the paper does, by an inner GMRES with the diagonal preconditioner D^CBF.
 
 Readings where the paper is silent: GMRES with x0 = 0, modified Gram-Schmidt
 Arnoldi, restart length `restart`, stopping on ||b - A P y|| / ||b|| <= tol;
@@ -234,10 +235,29 @@ class Solution:
     hist: list
 
 
+def cmp_inexact(G: np.ndarray, inner_tol: float, restart: int = 200, maxit: int = 1000, its: list | None = None):
+    """(G^CBF)^{-1} applied inexactly, as the paper proposes (Sec. III-C after Eq.
+    (CBFM_inner), Sec. IV): GMRES on G^CBF z = v right-preconditioned by the
+    diagonal D^CBF = 1 / diag(G^CBF), stopped at relative residual inner_tol.
+    Inner iteration counts are appended to `its` when given."""
+    d = np.diag(G).copy()
+
+    def apply(v):
+        z, it, _ = gmres(lambda u: G @ u, v, inner_tol, restart, maxit, lambda u: u / d)
+        if its is not None:
+            its.append(it)
+        return z
+    return apply
+
+
 def solve_reduced(A: np.ndarray, Gcbf: np.ndarray, CMJ: np.ndarray, b: np.ndarray, tol: float,
-                  restart: int = 200, maxit: int = 1000, use_cmp: bool = True) -> Solution:
-    """Step 7 for every right-hand side column of b."""
-    if use_cmp:
+                  restart: int = 200, maxit: int = 1000, use_cmp: bool = True,
+                  inner_tol: float | None = None) -> Solution:
+    """Step 7 for every right-hand side column of b; with inner_tol the CMP's
+    (G^CBF)^{-1} is the inexact inner GMRES of cmp_inexact, else an LU solve."""
+    if use_cmp and inner_tol is not None:
+        P = cmp_inexact(Gcbf, inner_tol)
+    elif use_cmp:
         lu = sla.lu_factor(Gcbf)
         P = lambda z: sla.lu_solve(lu, z)  # noqa: E731
     else:

@@ -70,6 +70,7 @@ def lib():
             "cbfm_red_export": [_vp, _vp, _vp],
             "cbfm_red_export_noalloc": [_vp, _vp, _vp],
             "cbfm_cmp_setup": [_vp, _vp],
+            "cbfm_cmp_setup_inexact": [_vp, _f64, _i32, _i32, _vp],
             "cbfm_gram_export": [_vp, _vp, _vp],
             "cbfm_gram_inverse": [_vp, _i64, _i32, _vp, _vp],
             "cbfm_solve": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp],
@@ -97,7 +98,7 @@ def lib():
 def exported_symbols():
     """Names of the C entry points declared in include/cbfm.h."""
     return ["cbfm_mesh", "cbfm_mesh_edges", "cbfm_mesh_info", "cbfm_mesh_cells", "cbfm_build_cbfs", "cbfm_cbf_import",
-            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_assemble_mom", "cbfm_tdiag_setup", "cbfm_build_ipcbfs", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_gram_export",
+            "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_assemble_mom", "cbfm_tdiag_setup", "cbfm_build_ipcbfs", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_cmp_setup_inexact", "cbfm_gram_export",
             "cbfm_gram_inverse", "cbfm_solve", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
             "cbfm_profile_read"]
 
@@ -375,9 +376,15 @@ def tuning() -> dict:
     return json.loads(buf.value.decode())
 
 
-def cmp_setup(r: Reduced, stream=None) -> None:
-    """cbfm_cmp_setup: G^CBF and its inverse."""
-    _check(lib().cbfm_cmp_setup(r.handle, _stream(stream)))
+def cmp_setup(r: Reduced, stream=None, inexact: bool = False, inner_tol: float = 1e-5, inner_maxit: int = 1000,
+              inner_restart: int = 200) -> None:
+    """cbfm_cmp_setup: G^CBF and its inverse; inexact=True: cbfm_cmp_setup_inexact, G^CBF
+    applied later by an inner GMRES with D^CBF (solve with precond=PC_CMP_INEXACT)."""
+    if inexact:
+        _check(lib().cbfm_cmp_setup_inexact(r.handle, float(inner_tol), int(inner_maxit), int(inner_restart),
+                                            _stream(stream)))
+    else:
+        _check(lib().cbfm_cmp_setup(r.handle, _stream(stream)))
 
 
 @dataclass
@@ -395,6 +402,7 @@ BLOCK = 1
 PC_NONE = 0     # K-diagonal system, no preconditioner
 PC_CMP = 1      # Calderon multiplicative preconditioner (cmp_setup)
 PC_TDIAG = 2    # T-diagonal arrangement (tdiag_setup)
+PC_CMP_INEXACT = 3   # CMP with (G^CBF)^{-1} by an inner GMRES (cmp_setup(inexact=True))
 
 
 def solve(r: Reduced, exc, tol: float = 1e-6, maxit: int = 2000, restart: int = 1000, use_cmp: bool = True,

@@ -864,6 +864,52 @@ void project(Red &r, cudaStream_t st) {
     }
 }
 
+
+// G^CBF = (C^JM)^H G_ffff C^MJ (paper Eq. (CBF_Gram_matrix)) into r.G: the sparse RWG Gram rows
+// times the CBF blocks, then the two halves' cell-block products
+void gram_cbf(Red &r, cudaStream_t st) {
+    Mesh &m = *r.mesh;
+    Cbf &c = *r.cbf;
+    const int64_t ne = m.h.ne, nh = c.nhalf, n = r.n;
+    const int nc = m.h.ncell;
+    DevBuf<int32_t> dcoff, dL;
+    DevBuf<int64_t> dcoff64, dboff;
+    upload(dcoff, m.h.cell_off, st);
+    upload(dL, c.L, st);
+    upload(dcoff64, c.coff, st);
+    upload(dboff, c.boff, st);
+    DevBuf<z64> XM, XJ;
+    XM.alloc((size_t)ne * nh);
+    XJ.alloc((size_t)ne * nh);
+    dim3 gx(nblk(nh), (unsigned)ne);
+    CBFM_REQUIRE(ne <= 65535, "too many edges for the Gram product grid");
+    {
+        ProfScope ps_("k_gram_times_c", st);
+        k_gram_times_c<<<gx, 256, 0, st>>>(ne, nh, m.edge_cell.p, dcoff.p, dcoff64.p, dboff.p, dL.p, m.gram_val.p,
+                                           m.gram_col.p, c.CM.p, XM.p);
+        launched("k_gram_times_c");
+    }
+    {
+        ProfScope ps_("k_gram_times_c", st);
+        k_gram_times_c<<<gx, 256, 0, st>>>(ne, nh, m.edge_cell.p, dcoff.p, dcoff64.p, dboff.p, dL.p, m.gram_val.p,
+                                           m.gram_col.p, c.CJ.p, XJ.p);
+        launched("k_gram_times_c");
+    }
+    r.G.alloc((size_t)n * n);
+    CBFM_CUDA(cudaMemsetAsync(r.G.p, 0, sizeof(z64) * n * n, st));
+    std::vector<GemmDesc> gJ, gM;
+    for (int k = 0; k < nc; ++k) {
+        int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
+        // first half: (C^J)^H Gf C^M ; second half: (C^M)^H Gf C^J
+        gJ.push_back(GemmDesc{L, nh, N, c.boff[k], L, off * nh, nh, c.coff[k] * n, n});
+        gM.push_back(GemmDesc{L, nh, N, c.boff[k], L, off * nh, nh, (nh + c.coff[k]) * n + nh, n});
+    }
+    gemm_grouped<double>(gJ, 2, 0, c.CJ.p, XM.p, r.G.p, false, st);
+    gemm_grouped<double>(gM, 2, 0, c.CM.p, XJ.p, r.G.p, false, st);
+    XM.release();
+    XJ.release();
+}
+
 }  // namespace
 
 extern "C" {
@@ -1066,46 +1112,8 @@ cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
         CBFM_REQUIRE(r->cbf != nullptr,
                      "no CBFs: the Calderon preconditioner of the RWG-only system has a singular Gram matrix");
         cudaStream_t st = (cudaStream_t)stream;
-        Mesh &m = *r->mesh;
-        Cbf &c = *r->cbf;
-        const int64_t ne = m.h.ne, nh = c.nhalf, n = r->n;
-        const int nc = m.h.ncell;
-        DevBuf<int32_t> dcoff, dL;
-        DevBuf<int64_t> dcoff64, dboff;
-        upload(dcoff, m.h.cell_off, st);
-        upload(dL, c.L, st);
-        upload(dcoff64, c.coff, st);
-        upload(dboff, c.boff, st);
-        DevBuf<z64> XM, XJ;
-        XM.alloc((size_t)ne * nh);
-        XJ.alloc((size_t)ne * nh);
-        dim3 gx(nblk(nh), (unsigned)ne);
-        CBFM_REQUIRE(ne <= 65535, "too many edges for the Gram product grid");
-        {
-            ProfScope ps_("k_gram_times_c", st);
-            k_gram_times_c<<<gx, 256, 0, st>>>(ne, nh, m.edge_cell.p, dcoff.p, dcoff64.p, dboff.p, dL.p, m.gram_val.p,
-                                               m.gram_col.p, c.CM.p, XM.p);
-            launched("k_gram_times_c");
-        }
-        {
-            ProfScope ps_("k_gram_times_c", st);
-            k_gram_times_c<<<gx, 256, 0, st>>>(ne, nh, m.edge_cell.p, dcoff.p, dcoff64.p, dboff.p, dL.p, m.gram_val.p,
-                                               m.gram_col.p, c.CJ.p, XJ.p);
-            launched("k_gram_times_c");
-        }
-        r->G.alloc((size_t)n * n);
-        CBFM_CUDA(cudaMemsetAsync(r->G.p, 0, sizeof(z64) * n * n, st));
-        std::vector<GemmDesc> gJ, gM;
-        for (int k = 0; k < nc; ++k) {
-            int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
-            // first half: (C^J)^H Gf C^M ; second half: (C^M)^H Gf C^J
-            gJ.push_back(GemmDesc{L, nh, N, c.boff[k], L, off * nh, nh, c.coff[k] * n, n});
-            gM.push_back(GemmDesc{L, nh, N, c.boff[k], L, off * nh, nh, (nh + c.coff[k]) * n + nh, n});
-        }
-        gemm_grouped<double>(gJ, 2, 0, c.CJ.p, XM.p, r->G.p, false, st);
-        gemm_grouped<double>(gM, 2, 0, c.CM.p, XJ.p, r->G.p, false, st);
-        XM.release();
-        XJ.release();
+        gram_cbf(*r, st);
+        const int64_t nh = r->cbf->nhalf, n = r->n;
         // inverse of each half by Gauss-Jordan (FP64)
         r->Ginv.alloc((size_t)n * n);
         CBFM_CUDA(cudaMemsetAsync(r->Ginv.p, 0, sizeof(z64) * n * n, st));
@@ -1143,6 +1151,38 @@ cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
         }
         CBFM_CUDA(cudaStreamSynchronize(st));
         r->cmp_ready = true;
+    });
+}
+
+cbfm_status cbfm_cmp_setup_inexact(cbfm_red_t red, double inner_tol, int32_t inner_maxit, int32_t inner_restart,
+                                   void *stream) {
+    return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
+        Red *r = (Red *)red;
+        check_device(r, H_RED, "reduced system");
+        CBFM_REQUIRE(r->cbf != nullptr,
+                     "no CBFs: the Calderon preconditioner of the RWG-only system has a singular Gram matrix");
+        CBFM_REQUIRE(inner_tol > 0.0 && inner_maxit >= 1 && inner_restart >= 1,
+                     "inner_tol, inner_maxit and inner_restart must be positive");
+        cudaStream_t st = (cudaStream_t)stream;
+        r->cmp_inexact_ready = false;
+        if (r->G.p == nullptr) gram_cbf(*r, st);
+        // the inner system: G^CBF (FP64) iterated with its Jacobi operator G D^{-1}, D = diag(G^CBF)
+        std::unique_ptr<Red> g(new Red());
+        g->kind = H_RED;
+        g->device = r->device;
+        g->mesh = r->mesh;
+        g->cbf = r->cbf;
+        g->prec = CBFM_FP64;
+        g->n = r->n;
+        g->A64.alloc((size_t)r->n * r->n);
+        CBFM_CUDA(cudaMemcpyAsync(g->A64.p, r->G.p, sizeof(z64) * r->n * r->n, cudaMemcpyDeviceToDevice, st));
+        if (!tdiag_build(*g, true, st, false)) throw Fail{CBFM_ESINGULAR, "a diagonal entry of G^CBF is zero"};
+        r->ginner = std::move(g);
+        r->inner_tol = inner_tol;
+        r->inner_maxit = inner_maxit;
+        r->inner_restart = inner_restart;
+        r->cmp_inexact_ready = true;
     });
 }
 
@@ -1192,9 +1232,12 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
         check_device(r, H_RED, "reduced system");
         CBFM_REQUIRE(exc && nrhs >= 1, "need at least one excitation");
         CBFM_REQUIRE(tol > 0.0 && maxit >= 1 && restart >= 1, "tol, maxit and restart must be positive");
-        CBFM_REQUIRE(precond == CBFM_PC_NONE || precond == CBFM_PC_CMP || precond == CBFM_PC_TDIAG,
-                     "precond must be CBFM_PC_NONE, CBFM_PC_CMP or CBFM_PC_TDIAG");
+        CBFM_REQUIRE(precond == CBFM_PC_NONE || precond == CBFM_PC_CMP || precond == CBFM_PC_TDIAG ||
+                         precond == CBFM_PC_CMP_INEXACT,
+                     "precond must be CBFM_PC_NONE, CBFM_PC_CMP, CBFM_PC_TDIAG or CBFM_PC_CMP_INEXACT");
         CBFM_REQUIRE(precond != CBFM_PC_CMP || r->cmp_ready, "CBFM_PC_CMP requires cbfm_cmp_setup");
+        CBFM_REQUIRE(precond != CBFM_PC_CMP_INEXACT || r->cmp_inexact_ready,
+                     "CBFM_PC_CMP_INEXACT requires cbfm_cmp_setup_inexact");
         CBFM_REQUIRE(precond != CBFM_PC_TDIAG || r->tdiag_ready, "CBFM_PC_TDIAG requires cbfm_tdiag_setup");
         const bool mono = (obs == nullptr && ndir == -1);
         CBFM_REQUIRE(mono || ndir >= 0, "ndir must be >= 0, or -1 with obs == NULL for monostatic");

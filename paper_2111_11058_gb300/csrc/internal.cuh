@@ -1,6 +1,7 @@
 // internal.cuh -- handle structures and kernel entry points of the library.
 #pragma once
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -83,6 +84,12 @@ struct Red : HandleBase {
     DevBuf<z64> tdinv;
     bool tdiag_ready = false;
     bool tdiag_jacobi = false;
+    bool tdiag_swap = true;       // false: Jacobi scaling only (the inner system of the inexact CMP)
+    // inexact CMP: G^CBF as a system of its own, iterated with its Jacobi operator G D^{-1}
+    std::unique_ptr<Red> ginner;
+    double inner_tol = 1e-5;
+    int inner_maxit = 1000, inner_restart = 200;
+    bool cmp_inexact_ready = false;
 };
 
 // ------------------------------------------------------------- kernels
@@ -154,11 +161,13 @@ inline const c32 *pc_op32(const Red &r, int pc) {
     return pc == CBFM_PC_CMP ? r.B32.p : pc == CBFM_PC_TDIAG ? r.Bt32.p : r.A32.p;
 }
 
-// T-diagonal arrangement (k_tdiag.cu): builds r.Bt*, r.tdinv (jacobi: D = diag(A P), else I);
-// returns false when a diagonal entry is zero
-bool tdiag_build(Red &r, bool jacobi, cudaStream_t st);
+// T-diagonal arrangement (k_tdiag.cu): builds r.Bt*, r.tdinv (jacobi: D = diag(A P), else I;
+// swap = false: P = I, a plain Jacobi scaling); returns false when a diagonal entry is zero
+bool tdiag_build(Red &r, bool jacobi, cudaStream_t st, bool swap = true);
 // x[q][k] = y[q][p(k)] tdinv[k] for nrhs rows of length r.n
 void tdiag_recover(const Red &r, const z64 *y, z64 *x, int nrhs, cudaStream_t st);
+// z ~ (G^CBF)^{-1} v for nrhs rows: inner GMRES on r.ginner (inexact CMP)
+void cmp_inner_apply(Red &r, const z64 *v, z64 *z, int nrhs, cudaStream_t st);
 // the conventional MoM matrix A = [[Ks, Ta], [Tb, Ks]] (2 ne x 2 ne) from Z (3 x ne x ne), internal edge order
 template <typename T>
 void mom_place(int64_t ne, const cx<T> *Z, cx<T> *A, cudaStream_t st);

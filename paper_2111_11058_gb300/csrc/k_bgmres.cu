@@ -742,7 +742,13 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
         s_in.alloc((size_t)p * n);
         s_out.alloc((size_t)p * n);
     }
+    DevBuf<z64> zin;           // inexact CMP: the inner GMRES's (G^CBF)^{-1} in, the input of the product with A
     auto applyB = [&](const z64 *in, z64 *out, int rows) {
+        if (pc == CBFM_PC_CMP_INEXACT) {
+            if (zin.p == nullptr) zin.alloc((size_t)p * n);
+            cmp_inner_apply(rd, in, zin.p, rows, st);
+            in = zin.p;
+        }
         if (rd.prec != CBFM_FP64)
             rows_times(n, nullptr, pc_op32(rd, pc), in, out, rows, false, st, s_in.p, s_out.p);
         else rows_times(n, pc_op64(rd, pc), nullptr, in, out, rows, false, st, nullptr, nullptr);
@@ -919,6 +925,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
         else rows_times(n, rd.Ginv.p, nullptr, Y.p, d_x, p, true, st, nullptr, nullptr);
     }
     else if (pc == CBFM_PC_TDIAG) tdiag_recover(rd, Y.p, d_x, p, st);
+    else if (pc == CBFM_PC_CMP_INEXACT) cmp_inner_apply(rd, Y.p, d_x, p, st);
     else CBFM_CUDA(cudaMemcpyAsync(d_x, Y.p, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
     CBFM_CUDA(cudaStreamSynchronize(st));
     for (int q = 0; q < p; ++q) out.iters[q] = conv_at[q] >= 0 ? conv_at[q] : -total_blocks - 1;

@@ -358,7 +358,26 @@ void apply_rows(const Red &rd, const z64 *M64, const c32 *M32, const z64 *in, z6
     launched("k_matvec");
 }
 
-static void apply_B(const Red &rd, int pc, const z64 *in, z64 *out, int nrhs, const int *mask, cudaStream_t st) {
+// out[r] = mask[r] ? in[r] : 0 (rows of length n)
+__global__ void k_mask_rows(int64_t n, int nrhs, const int *__restrict__ mask, const z64 *__restrict__ in,
+                            z64 *__restrict__ out) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nrhs;
+         idx += (int64_t)gridDim.x * blockDim.x)
+        out[idx] = mask[idx / n] ? in[idx] : z64(0, 0);
+}
+
+static void apply_B(Red &rd, int pc, const z64 *in, z64 *out, int nrhs, const int *mask, cudaStream_t st) {
+    DevBuf<z64> v, z;
+    if (pc == CBFM_PC_CMP_INEXACT) {   // A (G^CBF)^{-1} in: the inner GMRES, then the product with A
+        // rows the mask leaves out may hold stale basis vectors: they enter the inner solve as zero
+        v.alloc((size_t)nrhs * rd.n);
+        z.alloc((size_t)nrhs * rd.n);
+        const int64_t work = rd.n * nrhs;
+        k_mask_rows<<<(unsigned)std::min<int64_t>((work + 255) / 256, 65535), 256, 0, st>>>(rd.n, nrhs, mask, in, v.p);
+        launched("k_mask_rows");
+        cmp_inner_apply(rd, v.p, z.p, nrhs, st);
+        in = z.p;
+    }
     if (rd.prec != CBFM_FP64) apply_rows(rd, nullptr, pc_op32(rd, pc), in, out, nrhs, mask, st);
     else apply_rows(rd, pc_op64(rd, pc), nullptr, in, out, nrhs, mask, st);
 }
@@ -524,6 +543,7 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
     // x = P y
     if (pc == CBFM_PC_CMP) apply_rows(rd, rd.Ginv.p, nullptr, y.p, d_x, nrhs, ones.p, st);
     else if (pc == CBFM_PC_TDIAG) tdiag_recover(rd, y.p, d_x, nrhs, st);
+    else if (pc == CBFM_PC_CMP_INEXACT) cmp_inner_apply(rd, y.p, d_x, nrhs, st);
     else CBFM_CUDA(cudaMemcpyAsync(d_x, y.p, sizeof(z64) * nrhs * n, cudaMemcpyDeviceToDevice, st));
     GmresOut out;
     out.iters = h_iters;

@@ -9,6 +9,8 @@
 // where p(j) = j + n/2 (mod n) is its own inverse, and recovers
 //     x = P D^{-1} y,    x_k = y_{p(k)} / D_{p(k)} = y_{p(k)} tdinv[k],
 //     tdinv[k] = 1 / A[p(k)][k].
+// With the swap switched off (p(k) = k) the same kernels give the plain Jacobi scaling A D^{-1},
+// D = diag(A), which the inexact CMP's inner GMRES on G^CBF uses (the paper's D^CBF).
 // Every kernel here is a grid-stride elementwise pass, bound by HBM bandwidth.
 #include <algorithm>
 
@@ -23,16 +25,19 @@ inline unsigned grid_for(int64_t work) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 65535));
 }
 
-__device__ __forceinline__ int64_t half_swap(int64_t k, int64_t h) { return k < h ? k + h : k - h; }
+// p(k): the partner of k under the half swap (swap != 0), else k itself
+__device__ __forceinline__ int64_t half_swap(int64_t k, int64_t h, int swap) {
+    return swap ? (k < h ? k + h : k - h) : k;
+}
 
 template <typename T>
-__global__ void k_tdiag_dinv(int64_t n, const cx<T> *__restrict__ A, int jacobi, z64 *__restrict__ tdinv,
+__global__ void k_tdiag_dinv(int64_t n, const cx<T> *__restrict__ A, int jacobi, int swap, z64 *__restrict__ tdinv,
                              int *__restrict__ zero_pivot) {
     const int64_t h = n / 2;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         z64 d(1.0, 0.0);
         if (jacobi) {
-            const cx<T> a = A[half_swap(k, h) * n + k];
+            const cx<T> a = A[half_swap(k, h, swap) * n + k];
             const z64 a64((double)a.re, (double)a.im);
             if (a64.re == 0.0 && a64.im == 0.0) {
                 atomicExch(zero_pivot, 1);
@@ -47,12 +52,12 @@ __global__ void k_tdiag_dinv(int64_t n, const cx<T> *__restrict__ A, int jacobi,
 
 // Bt[i][j] = A[i][p(j)] tdinv[p(j)]; the product in FP64, rounded once to T
 template <typename T>
-__global__ void k_tdiag_operator(int64_t n, const cx<T> *__restrict__ A, const z64 *__restrict__ tdinv,
+__global__ void k_tdiag_operator(int64_t n, const cx<T> *__restrict__ A, const z64 *__restrict__ tdinv, int swap,
                                  cx<T> *__restrict__ Bt) {
     const int64_t h = n / 2;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * n;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / n, pj = half_swap(idx % n, h);
+        const int64_t i = idx / n, pj = half_swap(idx % n, h, swap);
         const cx<T> a = A[i * n + pj];
         const z64 s = tdinv[pj];
         const double re = (double)a.re * s.re - (double)a.im * s.im;
@@ -61,13 +66,13 @@ __global__ void k_tdiag_operator(int64_t n, const cx<T> *__restrict__ A, const z
     }
 }
 
-__global__ void k_tdiag_recover(int64_t n, int64_t nrhs, const z64 *__restrict__ tdinv, const z64 *__restrict__ y,
-                                z64 *__restrict__ x) {
+__global__ void k_tdiag_recover(int64_t n, int64_t nrhs, const z64 *__restrict__ tdinv, int swap,
+                                const z64 *__restrict__ y, z64 *__restrict__ x) {
     const int64_t h = n / 2;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nrhs * n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = idx / n, k = idx % n;
-        x[idx] = y[q * n + half_swap(k, h)] * tdinv[k];
+        x[idx] = y[q * n + half_swap(k, h, swap)] * tdinv[k];
     }
 }
 
@@ -98,9 +103,10 @@ __global__ void k_mom_canon(int64_t ne, const int32_t *__restrict__ int_of_canon
 
 }  // namespace
 
-bool tdiag_build(Red &r, bool jacobi, cudaStream_t st) {
+bool tdiag_build(Red &r, bool jacobi, cudaStream_t st, bool swap) {
     const int64_t n = r.n;
-    CBFM_REQUIRE(n > 0 && n % 2 == 0, "the system has no two halves to swap");
+    CBFM_REQUIRE(n > 0 && (!swap || n % 2 == 0), "the system has no two halves to swap");
+    const int sw = swap ? 1 : 0;
     DevBuf<int> flag;
     flag.alloc(1);
     CBFM_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
@@ -109,8 +115,8 @@ bool tdiag_build(Red &r, bool jacobi, cudaStream_t st) {
     const bool f64 = r.prec == CBFM_FP64;
     {
         ProfScope ps_("k_tdiag_dinv", st);
-        if (f64) k_tdiag_dinv<double><<<grid_for(n), 256, 0, st>>>(n, r.A64.p, jacobi ? 1 : 0, r.tdinv.p, flag.p);
-        else k_tdiag_dinv<float><<<grid_for(n), 256, 0, st>>>(n, r.A32.p, jacobi ? 1 : 0, r.tdinv.p, flag.p);
+        if (f64) k_tdiag_dinv<double><<<grid_for(n), 256, 0, st>>>(n, r.A64.p, jacobi ? 1 : 0, sw, r.tdinv.p, flag.p);
+        else k_tdiag_dinv<float><<<grid_for(n), 256, 0, st>>>(n, r.A32.p, jacobi ? 1 : 0, sw, r.tdinv.p, flag.p);
         launched("k_tdiag_dinv");
     }
     {
@@ -118,11 +124,11 @@ bool tdiag_build(Red &r, bool jacobi, cudaStream_t st) {
         if (f64) {
             r.Bt32.release();
             r.Bt64.alloc((size_t)n * n);
-            k_tdiag_operator<double><<<grid_for(n * n), 256, 0, st>>>(n, r.A64.p, r.tdinv.p, r.Bt64.p);
+            k_tdiag_operator<double><<<grid_for(n * n), 256, 0, st>>>(n, r.A64.p, r.tdinv.p, sw, r.Bt64.p);
         } else {
             r.Bt64.release();
             r.Bt32.alloc((size_t)n * n);
-            k_tdiag_operator<float><<<grid_for(n * n), 256, 0, st>>>(n, r.A32.p, r.tdinv.p, r.Bt32.p);
+            k_tdiag_operator<float><<<grid_for(n * n), 256, 0, st>>>(n, r.A32.p, r.tdinv.p, sw, r.Bt32.p);
         }
         launched("k_tdiag_operator");
     }
@@ -132,13 +138,19 @@ bool tdiag_build(Red &r, bool jacobi, cudaStream_t st) {
     if (h) return false;
     r.tdiag_ready = true;
     r.tdiag_jacobi = jacobi;
+    r.tdiag_swap = swap;
     return true;
 }
 
 void tdiag_recover(const Red &r, const z64 *y, z64 *x, int nrhs, cudaStream_t st) {
     ProfScope ps_("k_tdiag_recover", st);
-    k_tdiag_recover<<<grid_for(r.n * nrhs), 256, 0, st>>>(r.n, nrhs, r.tdinv.p, y, x);
+    k_tdiag_recover<<<grid_for(r.n * nrhs), 256, 0, st>>>(r.n, nrhs, r.tdinv.p, r.tdiag_swap ? 1 : 0, y, x);
     launched("k_tdiag_recover");
+}
+
+void cmp_inner_apply(Red &r, const z64 *v, z64 *z, int nrhs, cudaStream_t st) {
+    // the inner iterate is used as it stands when inner_maxit is reached (an inexact preconditioner)
+    gmres_solve(*r.ginner, v, nrhs, r.inner_tol, r.inner_maxit, r.inner_restart, CBFM_PC_TDIAG, z, st);
 }
 
 template <typename T>
