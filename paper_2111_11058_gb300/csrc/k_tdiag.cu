@@ -1,5 +1,5 @@
 // T-diagonal arrangement and the conventional MoM matrix (paper Sec. IV, Eq. (MoM_T);
-// Sec. IV-B, Eq. (cbfm_Tdiag)).
+// Sec. IV-A, Eq. (cbfm_Tdiag)).
 //
 // The K-diagonal operator A (Eq. (Z) order: columns [alpha^M; alpha^J], or the
 // reduced system's [M-coefficient; J-coefficient] CBFs) has its two column halves

@@ -1,4 +1,4 @@
-"""Sphere arrays (paper Sec. IV-B): identical disjoint spheres of the
+"""Sphere arrays (paper Sec. IV-A): identical disjoint spheres of the
 single-sphere example (radius lambda/6, 320 triangles, Table I generating
 waves, the 70 singular values of the groups l = 1..5 kept, so 140 CBFs per
 sphere), one cell per sphere, eps_r 1..6, FP64 path.

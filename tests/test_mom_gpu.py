@@ -130,7 +130,7 @@ def _table1_waves():
 
 @pytest.fixture(scope="module")
 def pair():
-    """Two disjoint lambda/3 spheres (Sec. IV-B), one cell each, Table I waves,
+    """Two disjoint lambda/3 spheres (Sec. IV-A), one cell each, Table I waves,
     L = 70 kept per sphere (N^CBF = 280), eps_r = 1: GMRES stops well below the
     dimension, so the iteration counts tell the arrangements apart."""
     g = W.sphere_array(2, 1, 1, 0.5, level=2, radius=1.0 / 6.0)
