@@ -14,6 +14,13 @@ before timing (set-up, excitation independent) and stay resident.
 N > 1 runs independent replicas, one per GPU (torchrun, NCCL only for the
 barrier and the max over ranks).  --impl reference times the CPU oracle on a
 bounded sample of the same workload.
+
+Besides the headline, the JSON line carries comparisons on the same cube and
+right-hand sides (each can be switched off): the plain FP64 path, the other GMRES
+variant, the paper's conventional MoM (T-diagonal arrangement with its diagonal
+preconditioner) with the times in the paper's relative format and the RCS RMSE of
+the CBFM against it, IPCBFs generated from that MoM, the inexact (G^CBF)^{-1} of
+the paper, batched assembly of mixed scatterers and the serving loop.
 """
 from __future__ import annotations
 
