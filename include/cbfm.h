@@ -294,7 +294,7 @@ cbfm_status cbfm_cmp_setup_inexact(cbfm_red_t red, double inner_tol, int32_t inn
  */
 cbfm_status cbfm_gram_inverse(const double *A, int64_t n, int32_t nbatch, double *Ainv, void *stream);
 
-/* G^CBF as complex128 row-major (n_cbf, n_cbf), host or device. */
+/* G^CBF as complex128 row-major (n_cbf, n_cbf), host or device; after cbfm_cmp_setup or cbfm_cmp_setup_inexact. */
 cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream);
 
 /*

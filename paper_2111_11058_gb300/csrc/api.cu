@@ -1215,7 +1215,7 @@ cbfm_status cbfm_gram_export(cbfm_red_t red, double *G, void *stream) {
         StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         Red *r = (Red *)red;
         check_device(r, H_RED, "reduced system");
-        CBFM_REQUIRE(r->cmp_ready, "call cbfm_cmp_setup first");
+        CBFM_REQUIRE(r->G.p != nullptr, "call cbfm_cmp_setup or cbfm_cmp_setup_inexact first");
         CBFM_REQUIRE(G, "NULL G");
         copy_out(G, r->G.p, r->n * r->n * sizeof(z64), (cudaStream_t)stream);
         CBFM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
