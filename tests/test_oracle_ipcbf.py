@@ -65,3 +65,18 @@ def test_ipcbf_accuracy_trend_on_a_divided_cube():
     primary = rmse(cbfm.primary_cbfs(m, cell, 8, eps, W.plane_wave_set(W.fibonacci_dirs(32)), 1e-3))
     assert tight < -18.0
     assert tight < loose - 8.0 and tight < primary - 8.0
+
+
+def test_ipcbf_single_wave():
+    # s = 1: one CBF per cell and current type, and the CBFM reproduces that wave's MoM solution
+    g = W.icosphere(1, 0.3)
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = OM.cells_octant(m)
+    gen = _cut_plane_waves(1, 0.0)
+    cb, its = cbfm.ipcbfs(m, cell, 8, 2.0, gen, 1e-12, 0.0)
+    assert [c.L for c in cb] == [1] * 8 and len(its) == 1
+    Z = mom.pmchwt_matrix(m, 2.0)
+    v = mom.rhs(m, gen)
+    j = _cbfm_currents(m, cb, 2.0, Z, v)
+    jm = np.linalg.solve(Z, v)
+    assert np.linalg.norm(j - jm) / np.linalg.norm(jm) < 1e-8

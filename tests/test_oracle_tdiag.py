@@ -77,3 +77,15 @@ def test_jacobi_cuts_iterations_and_keeps_the_solution(sphere1):
     for x in (xj, xn):
         assert np.linalg.norm(x - jd) / np.linalg.norm(jd) < 1e-5
     assert 2 * ij[0] < inn[0]
+
+
+def test_zero_excitation_and_two_unknowns():
+    # degenerate inputs: a zero right-hand side stops at once with x = 0; the smallest
+    # system with two halves is arranged and solved like any other
+    rng = np.random.default_rng(5)
+    A = np.array([[0.3 + 0.1j, 2.0 - 1.0j], [1.5 + 0.5j, -0.2j]])
+    assert np.array_equal(cbfm.tdiag(A), A[:, ::-1])
+    b = np.stack([np.zeros(2, complex), rng.standard_normal(2) + 0j], axis=1)
+    x, its = cbfm.solve_tdiag(A, b, 1e-12)
+    assert its[0] == 0 and not x[:, 0].any()
+    assert np.linalg.norm(A @ x[:, 1] - b[:, 1]) < 1e-12 * np.linalg.norm(b[:, 1])
