@@ -31,6 +31,17 @@
  * Errors: every call returns a cbfm_status and never aborts the process; the
  * message of the last failure on the calling thread is cbfm_last_error().
  * Device-side waits are bounded and report CBFM_ETIMEOUT.
+ *
+ * Call sequence
+ *   CBFM with the CMP:   cbfm_mesh -> cbfm_build_cbfs (or cbfm_build_ipcbfs) ->
+ *                        cbfm_assemble_reduced -> cbfm_cmp_setup -> cbfm_solve (CBFM_PC_CMP)
+ *                        (cbfm_cmp_setup_inexact -> cbfm_solve (CBFM_PC_CMP_INEXACT): the paper's
+ *                        inner-GMRES inverse of G^CBF)
+ *   conventional MoM:    cbfm_mesh -> cbfm_assemble_mom -> cbfm_tdiag_setup(jacobi = 1) ->
+ *                        cbfm_solve (CBFM_PC_TDIAG)
+ *   T-diagonal CBFM:     ... cbfm_assemble_reduced -> cbfm_tdiag_setup(jacobi = 0) ->
+ *                        cbfm_solve (CBFM_PC_TDIAG)
+ *   every handle ends with cbfm_free.
  */
 #ifndef CBFM_H
 #define CBFM_H
