@@ -36,6 +36,28 @@ def test_exports_every_declared_symbol(P):
     assert sorted(P.cbfm.exported_symbols()) == names
 
 
+def _enum_values():
+    """name -> value of every enumerator in include/cbfm.h."""
+    src = open(os.path.join(ROOT, "include", "cbfm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body in re.findall(r"typedef enum \{(.*?)\}", src, flags=re.S):
+        for name, val in re.findall(r"\b(CBFM_[A-Z_0-9]+)\s*=\s*(\d+)", body):
+            out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_header(P):
+    e = _enum_values()
+    C = P.cbfm
+    assert (e["CBFM_FP64"], e["CBFM_MIXED"], e["CBFM_MIXED_SIMT"]) == (C.FP64, C.MIXED, C.MIXED_SIMT)
+    assert (e["CBFM_PC_NONE"], e["CBFM_PC_CMP"], e["CBFM_PC_TDIAG"], e["CBFM_PC_CMP_INEXACT"]) == \
+        (C.PC_NONE, C.PC_CMP, C.PC_TDIAG, C.PC_CMP_INEXACT)
+    for name, val in e.items():
+        if name in ("CBFM_OK",) or name.startswith("CBFM_E"):
+            assert C.STATUS[val] == name
+
+
 @pytest.mark.parametrize("case", ["sphere_octant", "cube_rcb", "cylinder_rcb7", "array_rcb"])
 def test_host_mesh_tables_match_oracle(P, case):
     g, nc, part = {
