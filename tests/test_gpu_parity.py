@@ -4,8 +4,10 @@ Tolerances (relative, max-abs normalised unless stated):
   * FP64 path: reduced matrix and CBF Gram <= 1e-11; currents <= 1e-7 and
     RCS <= 1e-8 with both sides solved to tol 1e-10 (solver tolerance times
     the conditioning of A dominates);
-  * mixed path: reduced matrix <= 1e-4 (FP32 quadrature / complex64
-    projections, derived in the design doc), peak-normalised RCS <= 1e-4.
+  * mixed path: reduced matrix <= 1e-4 (FP32 quadrature, relative error
+    ~1e-7 per point pair; split-TF32 products, ~2^-21 each; FP32 accumulation
+    over a few hundred terms), peak-normalised RCS <= 1e-4, currents (relative
+    L2 over all right-hand sides, GMRES tol 1e-6) <= J_MIXED.
 """
 import math
 
@@ -18,6 +20,10 @@ from oracle import cbfm as OC, mesh as OM, mom as OMo
 pytestmark = pytest.mark.gpu
 
 TOL_SOLVE = 1e-10
+# Mixed-path bound on the currents: ~1e-6 relative error of the reduced matrix
+# (its largest entry) times the conditioning of the CMP-preconditioned system,
+# plus the GMRES tolerance 1e-6.
+J_MIXED = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -180,8 +186,11 @@ def test_solve_mixed_c1_rcs_within_1e4(P, c1, prec):
     P.cmp_setup(red)
     res = P.solve(red, c1["exc"], tol=1e-6, obs=c1["obs"])
     err = _peak_rcs_err(res.rcs.sum(-1), c1["rcs"].sum(-1))
-    print(f"mixed RCS error {err:.2e}, iterations {res.iters.tolist()}")
+    jo = c1["ref"]["sol"].j
+    errj = float(np.linalg.norm(res.j - jo) / np.linalg.norm(jo))
+    print(f"mixed RCS error {err:.2e}, current error {errj:.2e}, iterations {res.iters.tolist()}")
     assert err < 1e-4
+    assert errj < J_MIXED
 
 
 def test_end_to_end_gpu_cbfs_c1(P, c1):
@@ -313,9 +322,10 @@ def test_block_gmres_c1(P, c1, prec, tol_rcs):
     P.cmp_setup(red)
     res = P.solve(red, c1["exc"], tol=TOL_SOLVE if prec == 0 else 1e-6, obs=c1["obs"], solver=P.BLOCK)
     assert _peak_rcs_err(res.rcs.sum(-1), c1["rcs"].sum(-1)) < tol_rcs
-    if prec == 0:
-        jo = c1["ref"]["sol"].j
-        assert np.linalg.norm(res.j - jo) / np.linalg.norm(jo) < 1e-7
+    jo = c1["ref"]["sol"].j
+    errj = float(np.linalg.norm(res.j - jo) / np.linalg.norm(jo))
+    print(f"block GMRES prec {prec}: current error {errj:.2e}")
+    assert errj < (1e-7 if prec == 0 else J_MIXED)
     assert (res.iters >= 1).all()
 
 
