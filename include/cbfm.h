@@ -258,14 +258,19 @@ cbfm_status cbfm_red_export(cbfm_red_t red, double *A, void *stream);
  * library service, not part of the method.
  *   Calls no cudaMalloc, cudaFree or allocating library routine.  A mixed-
  *   precision matrix is widened to complex128 in a fixed 4 MiB scratch array
- *   built into the library (held by every GPU that loads it until exit), so
- *   n_cbf must be <= 512; larger systems return CBFM_EINVAL.
- *   The first call on each device looks up the scratch array's device address
- *   (cudaGetSymbolAddress with that device current); make that first call
- *   before any stream capture.  All calls share the one scratch array, which
- *   keeps the last call's contents: calls that overlap on the GPU (different
- *   streams or threads) race and must be serialised by the caller.  Returns
- *   after the copy into A (host or device) has completed.
+ *   built into the library, so n_cbf must be <= 512; larger systems, and
+ *   conventional-MoM handles, return CBFM_EINVAL.
+ *   CUDA loads the scratch array on a device lazily; the library does so in
+ *   its first call on each device (any entry point, e.g. cbfm_mesh), which is
+ *   where those 4 MiB are taken and then held until the process exits, so the
+ *   export itself never needs new device memory.  Each call looks the array's
+ *   device address up again (cudaGetSymbolAddress with the handle's device
+ *   current), so a re-created context is handled.  Like every entry point it
+ *   synchronises `stream`: never call it on a stream that is being captured.
+ *   All calls share the one scratch array, which keeps the last call's
+ *   contents: calls that overlap on the GPU (different streams or threads)
+ *   race and must be serialised by the caller.  Returns after the copy into A
+ *   (host or device) has completed.
  */
 cbfm_status cbfm_red_export_noalloc(cbfm_red_t red, double *A, void *stream);
 

@@ -44,6 +44,7 @@ void pool_setup() {
         uint64_t keep = 8ull << 30;   // freed scratch stays cached up to 8 GiB between calls
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
+    noalloc_prepare();   // the no-alloc export's scratch is taken now, not when memory may be full
     done.fetch_or(1ull << dev, std::memory_order_acq_rel);
 }
 std::atomic<bool> g_prof{false};
@@ -108,6 +109,20 @@ void prof_flush() {
 }
 
 void set_error(const std::string &msg) { t_err = msg; }
+
+int sm_count() {
+    static std::atomic<int> cache[64];   // zero-initialised (static storage)
+    int dev = 0;
+    CBFM_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    CBFM_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
 
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;

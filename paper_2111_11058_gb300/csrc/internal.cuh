@@ -35,6 +35,8 @@ struct HostMesh {
 void build_host_mesh(const double *verts, int64_t nv, const int32_t *tris, int64_t nt,
                      const int32_t *edge_cell, int32_t ncell, int32_t partition, HostMesh &hm);
 
+struct FusedTables;   // k_fused.cu
+
 struct Mesh : HandleBase {
     HostMesh h;
     double eps_re, eps_im, mu_r, alpha;
@@ -49,6 +51,7 @@ struct Mesh : HandleBase {
     DevBuf<int32_t> edge_cell;   // ne, cell of each internal edge
     DevBuf<int32_t> near_pairs;  // n_near*2 (t, s), t <= s, both orders needed
     int64_t n_near = 0;
+    std::shared_ptr<FusedTables> fused;   // tables of the fused assembly (k_fused.cu), built on first use
     DevBuf<double> gram_val;     // ne*6 sparse RWG Gram row values
     DevBuf<int32_t> gram_col;    // ne*6 internal edge columns (-1 unused)
     double centre[3];
@@ -130,6 +133,14 @@ void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info,
 template <typename T>
 void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &Z, cudaStream_t st,
                         bool diag_cells = false);
+// near-pair blocks only, compact (27 complex64 per pair of each mesh's near list) (k_assembly.cu)
+void near_blocks_compact(const std::vector<Mesh *> &ms, const std::vector<c32 *> &out, cudaStream_t st);
+// Fused mixed-precision assembly and projection (k_fused.cu): A[k] = (C^JM)^H Z C^MJ
+// for each mesh, with no RWG or local-block matrix in device memory.  fused_fits
+// tells whether the scatterer's cells fit the kernel's tile limits.
+bool fused_fits(const Mesh &m, const Cbf &c);
+void assemble_project_fused(const std::vector<Mesh *> &ms, const std::vector<Cbf *> &cs, const std::vector<c32 *> &A,
+                            cudaStream_t st);
 // tuned launch parameters, per key (api.cu); 0 when not tuned yet
 int tuning_get(const std::string &key);
 void tuning_set(const std::string &key, int value);
@@ -176,6 +187,8 @@ void mom_to_canonical(int64_t ne, const int32_t *d_int_of_canon, const z64 *A, z
 
 // export of the reduced matrix without device allocation (noalloc.cu)
 void red_export_noalloc(Red &r, double *A, cudaStream_t st);
+// loads the export's scratch array on the current device (once per device, from pool_setup)
+void noalloc_prepare();
 
 // elementwise helpers (k_dense.cu)
 void launch_z64_to_c32(const z64 *src, c32 *dst, int64_t n, cudaStream_t st);

@@ -10,12 +10,14 @@
 // into a fixed scratch array compiled into the library instead.
 //
 // The scratch is a file-scope __device__ array of NOALLOC_MAX_ELEMS complex128
-// values (4 MiB); every GPU that loads the library holds it until the process
-// exits.  In host code its name is only a host-side stand-in, so its device
-// address is looked up once per device with cudaGetSymbolAddress (with that
-// device current) and passed to the kernel.
-#include <mutex>
-
+// values (4 MiB).  CUDA loads a module (and with it this array) on a device
+// lazily, the first time something in it is used, so the library looks the
+// array up during the first API call on each device (noalloc_prepare, called
+// from pool_setup) -- that first call is where the 4 MiB is taken, before the
+// caller can have filled device memory.  In host code the array's name is only
+// a host-side stand-in; its device address comes from cudaGetSymbolAddress
+// with the device current, on every call (no cached address survives a
+// context reset).
 #include "internal.cuh"
 
 namespace cbfm {
@@ -23,27 +25,16 @@ namespace cbfm {
 namespace {
 
 constexpr int64_t NOALLOC_MAX_ELEMS = 512 * 512;   // n_cbf <= 512
-constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) z64 g_noalloc_scratch[NOALLOC_MAX_ELEMS];
 
-std::mutex g_sym_mu;
-z64 *g_sym_addr[NOALLOC_MAX_DEVICES] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device.
 z64 *scratch_address() {
-    int dev = -1;
-    CBFM_CUDA(cudaGetDevice(&dev));
-    CBFM_REQUIRE(dev >= 0 && dev < NOALLOC_MAX_DEVICES, "device index beyond the no-alloc table");
-    std::lock_guard<std::mutex> lk(g_sym_mu);
-    if (!g_sym_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            throw Fail{CBFM_ECUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e)};
-        g_sym_addr[dev] = (z64 *)p;
-    }
-    return g_sym_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        throw Fail{CBFM_ECUDA, std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e)};
+    return (z64 *)p;
 }
 
 __global__ void k_c32_to_z64_scratch(const c32 *__restrict__ src, z64 *__restrict__ dst, int64_t n) {
@@ -54,12 +45,21 @@ __global__ void k_c32_to_z64_scratch(const c32 *__restrict__ src, z64 *__restric
 }  // namespace
 
 // Body of cbfm_red_export_noalloc; the C entry point lives in api.cu.
+// Loads this file's module (and its scratch array) on the current device; run
+// once per device by the library's first API call there.  Errors are left to
+// the export itself to report.
+void noalloc_prepare() {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) cudaGetLastError();
+}
+
+// Body of cbfm_red_export_noalloc; the C entry point lives in api.cu.
 void red_export_noalloc(Red &r, double *A, cudaStream_t st) {
+    CBFM_REQUIRE(A != nullptr, "NULL A");
+    CBFM_REQUIRE(r.cbf != nullptr, "a conventional MoM system is exported with cbfm_red_export");
     const int64_t nn = r.n * r.n;
     CBFM_REQUIRE(nn <= NOALLOC_MAX_ELEMS,
                  "n_cbf = " + std::to_string(r.n) + " exceeds the no-alloc export limit of 512");
-    CBFM_REQUIRE(A != nullptr, "NULL A");
-    CBFM_REQUIRE(r.cbf != nullptr, "a conventional MoM system is exported with cbfm_red_export");
     if (r.prec == CBFM_FP64) {
         // already complex128: a plain copy, no scratch needed
         copy_out(A, r.A64.p, nn * sizeof(z64), st);

@@ -1,8 +1,10 @@
 """cbfm_red_export_noalloc: the reduced-matrix export for callers that cannot
 allocate device memory (for example a serving process whose HBM is full of
 cached matrices).  Called through the C ABI, its output must equal that of
-cbfm_red_export on two calls in a row, and sizes beyond its fixed scratch
-must be refused.  Kept in its own file so that pytest collects it last."""
+cbfm_red_export on two calls in a row (into host memory and into a device
+tensor), free device memory must not change across a call, and sizes beyond
+its fixed scratch, or a conventional-MoM handle, must be refused.  Kept in its
+own file so that pytest collects it last."""
 import ctypes
 
 import numpy as np
@@ -50,6 +52,17 @@ def test_noalloc_export_matches_export(P, prec):
     np.testing.assert_allclose(got1, ref1, rtol=1e-12, atol=0)
     np.testing.assert_allclose(got2, ref2, rtol=1e-12, atol=0)
     assert np.abs(ref1).max() > 0
+    # a device destination, and no change of free device memory across the call
+    import torch
+    Ad = torch.zeros((red.n, red.n, 2), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    st = P.cbfm.lib().cbfm_red_export_noalloc(red.handle, ctypes.c_void_p(Ad.data_ptr()), ctypes.c_void_p(0))
+    free1 = torch.cuda.mem_get_info()[0]
+    assert st == 0, P.cbfm.lib().cbfm_last_error().decode()
+    assert free1 == free0
+    got3 = Ad.cpu().numpy()
+    np.testing.assert_allclose(got3[..., 0] + 1j * got3[..., 1], ref1, rtol=1e-12, atol=0)
 
 
 def test_noalloc_export_rejects_oversize(P):
@@ -64,3 +77,13 @@ def test_noalloc_export_rejects_oversize(P):
     st = P.cbfm.lib().cbfm_red_export_noalloc(red.handle, ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(0))
     assert st == 1
     assert "512" in P.cbfm.lib().cbfm_last_error().decode()
+
+
+def test_noalloc_export_rejects_mom_handle(P):
+    g = W.icosphere(1, 0.3)
+    gm = P.mesh(g.verts, g.tris, 8, 4.0, partition="octant")
+    mo = P.assemble_mom(gm, 0)
+    A = np.zeros((mo.n, mo.n), np.complex128)
+    st = P.cbfm.lib().cbfm_red_export_noalloc(mo.handle, ctypes.c_void_p(A.ctypes.data), ctypes.c_void_p(0))
+    assert st == 1
+    assert "cbfm_red_export" in P.cbfm.lib().cbfm_last_error().decode()
