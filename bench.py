@@ -48,7 +48,7 @@ MOM_RESTART = 200      # GMRES restart of the MoM comparison (the paper does not
 IPCBF_DELTA_R = 1e-2   # residual allowance of the IPCBF generation (the paper uses 1e-1 to 1e-3)
 CMP_INNER_TOL = 1e-5   # inner GMRES tolerance of the inexact (G^CBF)^{-1} (the paper's value)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
+FP32_LANES_PER_SM = 128
 
 
 def _peaks():
@@ -111,7 +111,12 @@ class ClockSampler:
 
 
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 (CUDA cores)
-FP32_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5
+# FP32 peak derived from the device's SM count and the maximum SM clock (set in main)
+DEV = {"n_sm": 152, "sm_max_mhz": 2070.0}
+
+
+def fp32_peak_tflops() -> float:
+    return DEV["n_sm"] * FP32_LANES_PER_SM * 2 * DEV["sm_max_mhz"] * 1e6 / 1e12
 FP64_KERNELS = {"k_dots", "k_orth_update", "k_near_blocks", "k_finish", "k_lu_solve", "k_jacobi_svd",
                 "k_gemm_z64", "k_pchol", "k_trinv", "k_gj_sweep", "k_gjb_inv"}
 FP32_KERNELS = {"k_far", "k_matvec", "k_gemm_c32"}
@@ -125,12 +130,13 @@ def roofline(name, rec, peaks, peak_src):
            "traffic": None}
     if name in FP64_KERNELS or name in FP32_KERNELS:
         fp64 = name in FP64_KERNELS
-        peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+        peak = FP64_PEAK_TFLOPS if fp64 else fp32_peak_tflops()
         ach = rec.get("flop", 0.0) / secs / 1e12 if secs > 0 and rec.get("flop") else None
         out.update({"bound": "alu", "unit": "TFLOP/s", "peak": peak, "achieved": ach,
                     "frac": (ach / peak) if ach else None,
                     "peak_source": ("nominal FP64 1.25 TFLOP/s (FP64 units, 2070 MHz)" if fp64 else
-                                    "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz")})
+                                    f"derived: {DEV['n_sm']} SM x 128 FP32 lanes x 2 flop x "
+                                    f"{DEV['sm_max_mhz']:.0f} MHz")})
     else:
         peak = peaks.get("hbm_gbs")
         ach = rec.get("bytes", 0.0) / secs / 1e9 if secs > 0 and rec.get("bytes") else None
@@ -502,6 +508,9 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "dielectric cube 9216 unknowns, 32 cells, 128 RHS (CPU oracle sample)"},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "ms_per_step_kind": "extrapolated: the measured sample (a fraction of the step's cell-pair blocks and "
+                                "right-hand sides) scaled to the whole step",
+            "sample_ms_per_step": 1000.0 * float(np.median([x["measured_s"] for x in vals])),
             "wall_s": wall}
     print(json.dumps(line), flush=True)
 
@@ -533,6 +542,8 @@ def main():
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     torch.cuda.init()
+    DEV["n_sm"] = torch.cuda.get_device_properties(local).multi_processor_count
+    DEV["sm_max_mhz"] = float(_peaks()[0].get("sm_max_mhz", DEV["sm_max_mhz"]))
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

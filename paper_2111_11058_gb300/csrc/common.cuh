@@ -201,6 +201,9 @@ struct DevBuf {
     }
 };
 
+// streaming multiprocessors of the current device (queried once per device)
+int sm_count();
+
 // copies that accept host or device sources/destinations
 void copy_in(void *dst_dev, const void *src_any, size_t bytes, cudaStream_t st);
 void copy_out(void *dst_any, const void *src_dev, size_t bytes, cudaStream_t st);

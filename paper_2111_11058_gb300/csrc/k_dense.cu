@@ -1038,7 +1038,8 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
             if (tiles == 0) continue;
             // few output tiles: split K (slices of at least GB_K) until about two
             // CTAs per SM exist
-            const int64_t want = (tiles < 2 * 152) ? (2 * 152 + tiles - 1) / tiles : 1;
+            const int64_t nsm2 = 2 * (int64_t)sm_count();
+            const int64_t want = (tiles < nsm2) ? (nsm2 + tiles - 1) / tiles : 1;
             bt.tile_off[0] = bt.part_off[0] = bt.red_off[0] = 0;
             for (int i = 0; i < bt.ng; ++i) {
                 const GemmDesc &d = bt.d[i];
@@ -1130,7 +1131,7 @@ void gauss_jordan_inverse(int64_t n, int nbatch, z64 *Aug, z64 *inv, int *d_info
     pivrow.alloc((size_t)nbatch * n);
     src.alloc((size_t)nbatch * n);
     CBFM_CUDA(cudaMemsetAsync(keys.p, 0, sizeof(unsigned long long) * nbatch * n, st));
-    const unsigned nb = (unsigned)std::min<int64_t>((n * n + 255) / 256, 2 * 152);
+    const unsigned nb = (unsigned)std::min<int64_t>((n * n + 255) / 256, 2 * (int64_t)sm_count());
     {
         ProfScope ps_("k_gj_init", st);
         k_gj_init<<<dim3(nb, nbatch), 256, 0, st>>>((int)n, inv, b0, keys.p);
