@@ -119,7 +119,7 @@ def fp32_peak_tflops() -> float:
     return DEV["n_sm"] * FP32_LANES_PER_SM * 2 * DEV["sm_max_mhz"] * 1e6 / 1e12
 FP64_KERNELS = {"k_dots", "k_orth_update", "k_near_blocks", "k_finish", "k_lu_solve", "k_jacobi_svd",
                 "k_gemm_z64", "k_pchol", "k_trinv", "k_gj_sweep", "k_gjb_inv"}
-FP32_KERNELS = {"k_far", "k_matvec", "k_gemm_c32"}
+FP32_KERNELS = {"k_far", "k_fused", "k_matvec", "k_gemm_c32"}
 
 
 def roofline(name, rec, peaks, peak_src):

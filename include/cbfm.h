@@ -71,9 +71,19 @@ typedef enum {
     CBFM_MIXED = 1,       /* FP32 far-pair quadrature; projections on the tensor cores
                              (split-TF32 products, FP32 accumulation); complex64 reduced
                              matrix; FP64 singular near pairs, SVD, CMP Gram inverse,
-                             GMRES Arnoldi / residual */
-    CBFM_MIXED_SIMT = 2   /* as CBFM_MIXED, but the projections run as FP32 products on
+                             GMRES Arnoldi / residual.  Chooses the faster form that fits:
+                             CBFM_MIXED_UNFUSED when its RWG matrices fit in a quarter of
+                             the free device memory and 16 GiB, else CBFM_MIXED_FUSED
+                             (when the cells fit its tiles) */
+    CBFM_MIXED_SIMT = 2,  /* as CBFM_MIXED, but the projections run as FP32 products on
                              the CUDA cores (for comparison with the tensor-core path) */
+    CBFM_MIXED_UNFUSED = 3,  /* RWG matrices Z assembled in device memory (27 T^2 + 7 N^2 / 4
+                             complex64 entries of scratch), then projected by a separate
+                             tensor-core GEMM */
+    CBFM_MIXED_FUSED = 4  /* assembly fused with the tensor-core projection, per cell pair:
+                             no local-block or RWG matrix in device memory.  Its tiles take
+                             cells with L_m <= 32 CBFs and N_m <= 256 RWG functions; a
+                             scatterer with a larger cell is assembled as CBFM_MIXED_UNFUSED */
 } cbfm_precision;
 
 /* Right preconditioner / unknown arrangement of cbfm_solve (its `precond` argument). */
@@ -160,19 +170,23 @@ cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precisi
 
 /*
  * cbfm_assemble_reduced_batch -- cbfm_assemble_reduced for `count` scatterers
- * at once (mixed precision only: prec must be CBFM_MIXED).  Each stage of the
- * assembly (far pairs, near pairs, RWG gather, the two tensor-core projection
- * products) is one launch over the work of all scatterers: the far stage runs
- * persistent CTAs that take (scatterer, test triangle, strip of trial
- * triangles) tasks from an atomic counter, so scatterers of uneven size share
- * the GPU.  The strip width is picked on the first call per device by timing
- * the candidates (see cbfm_tuning).  Scatterers are processed in waves whose
- * transient operators fit in half of the free device memory and in 6 GiB.
+ * at once (mixed precision only: prec CBFM_MIXED or CBFM_MIXED_FUSED).  The
+ * scatterers that take the fused form (all that fit its tiles under
+ * CBFM_MIXED_FUSED; under CBFM_MIXED those whose unfused scratch would not
+ * fit) are assembled by one launch of the near-pair stage and one launch of the
+ * fused assembly-projection kernel over all their cell pairs: persistent CTAs take (scatterer, test cell,
+ * trial cell) items from an atomic counter, largest first, so scatterers of
+ * uneven size share the GPU.  The others go through the unfused stages (far
+ * pairs with a strip width picked on the first call per device by timing the
+ * candidates, see cbfm_tuning; near pairs; RWG gather; two tensor-core GEMMs),
+ * in waves whose transient operators fit in half of the free device memory and
+ * in 6 GiB.
  *   meshes, cbfs  count handles (cbfs[k] built on meshes[k])
  *   out           count new reduced-system handles (NULL on failure)
  *   n_cbf         out, count values of N^CBF (may be NULL)
- * Each out[k] equals what cbfm_assemble_reduced(meshes[k], cbfs[k],
- * CBFM_MIXED) returns.  Returns after the work has completed.
+ * Each out[k] equals what cbfm_assemble_reduced(meshes[k], cbfs[k], prec)
+ * returns (up to the summation order of the fused kernel's FP32 atomic adds:
+ * last-bit differences).  Returns after the work has completed.
  */
 cbfm_status cbfm_assemble_reduced_batch(const cbfm_mesh_t *meshes, const cbfm_cbf_t *cbfs, int32_t count,
                                         cbfm_precision prec, void *stream, cbfm_red_t *out, int64_t *n_cbf);

@@ -24,6 +24,8 @@ _LIB_PATH = os.path.join(_HERE, "libcbfm.so")
 FP64 = 0
 MIXED = 1
 MIXED_SIMT = 2   # mixed precision with the projections on the CUDA cores instead of the tensor cores
+MIXED_UNFUSED = 3   # mixed precision, RWG matrices assembled in memory, then projected on the tensor cores
+MIXED_FUSED = 4     # mixed precision, assembly fused with the tensor-core projection (no RWG matrix in memory)
 
 STATUS = {0: "CBFM_OK", 1: "CBFM_EINVAL", 2: "CBFM_ENOMEM", 3: "CBFM_ECUDA", 4: "CBFM_ESINGULAR",
           5: "CBFM_ENOCONV", 6: "CBFM_ETIMEOUT"}

@@ -840,13 +840,22 @@ void project(Red &r, cudaStream_t st) {
     Cbf &c = *r.cbf;
     const int64_t ne = m.h.ne, nh = c.nhalf, n = 2 * nh;
     const int nc = m.h.ncell;
-    DevBuf<cx<T>> Z;
-    Z.alloc(3 * (size_t)ne * ne);
-    assemble_rwg<T>(m, Z.p, st);
     DevBuf<cx<T>> A;
     A.alloc((size_t)n * n);
     if constexpr (sizeof(T) == 4) {
-        if (r.prec == CBFM_MIXED) {
+        // mixed precision: assembly fused with the tensor-core projection (no RWG
+        // matrix in memory) when the cells fit the fused kernel's tiles
+        if ((r.prec == CBFM_MIXED_FUSED && fused_fits(m, c)) || (r.prec == CBFM_MIXED && mixed_takes_fused(m, c))) {
+            assemble_project_fused({&m}, {&c}, {A.p}, st);
+            A.give(r.A32);
+            return;
+        }
+    }
+    DevBuf<cx<T>> Z;
+    Z.alloc(3 * (size_t)ne * ne);
+    assemble_rwg<T>(m, Z.p, st);
+    if constexpr (sizeof(T) == 4) {
+        if (r.prec == CBFM_MIXED || r.prec == CBFM_MIXED_UNFUSED || r.prec == CBFM_MIXED_FUSED) {
             project_tc(m, c, Z.p, A.p, st);
             A.give(r.A32);
             return;
@@ -939,7 +948,9 @@ cbfm_status cbfm_assemble_reduced(cbfm_mesh_t mesh, cbfm_cbf_t cbf, cbfm_precisi
         check_device(c, H_CBF, "cbf");
         CBFM_REQUIRE(c->mesh == m, "cbf handle belongs to another mesh");
         CBFM_REQUIRE(out, "NULL out");
-        CBFM_REQUIRE(prec == CBFM_FP64 || prec == CBFM_MIXED || prec == CBFM_MIXED_SIMT, "unknown precision");
+        CBFM_REQUIRE(prec == CBFM_FP64 || prec == CBFM_MIXED || prec == CBFM_MIXED_SIMT || prec == CBFM_MIXED_UNFUSED ||
+                         prec == CBFM_MIXED_FUSED,
+                     "unknown precision");
         *out = nullptr;
         cudaStream_t st = (cudaStream_t)stream;
         std::unique_ptr<Red> r(new Red());
@@ -1012,7 +1023,8 @@ cbfm_status cbfm_assemble_reduced_batch(const cbfm_mesh_t *meshes, const cbfm_cb
         StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream
         CBFM_REQUIRE(count >= 0, "negative count");
         CBFM_REQUIRE(count == 0 || (meshes && cbfs && out), "NULL array");
-        CBFM_REQUIRE(prec == CBFM_MIXED, "batched assembly runs the mixed-precision path (CBFM_MIXED) only");
+        CBFM_REQUIRE(prec == CBFM_MIXED || prec == CBFM_MIXED_FUSED,
+                     "batched assembly runs the mixed-precision path (CBFM_MIXED or CBFM_MIXED_FUSED) only");
         for (int32_t k = 0; k < count; ++k) out[k] = nullptr;
         cudaStream_t st = (cudaStream_t)stream;
         std::vector<Mesh *> ms(count);
@@ -1024,9 +1036,41 @@ cbfm_status cbfm_assemble_reduced_batch(const cbfm_mesh_t *meshes, const cbfm_cb
             check_device(cs[k], H_CBF, "cbf");
             CBFM_REQUIRE(cs[k]->mesh == ms[k], "cbf handle belongs to another mesh");
         }
-        // waves of scatterers whose transient operators fit in half of the free
-        // device memory and in the 8 GiB the stream-ordered pool keeps between
-        // calls (larger waves would map fresh memory every call)
+        made.resize(count);
+        auto make = [&](int32_t k) -> Red * {
+            std::unique_ptr<Red> r(new Red());
+            r->kind = H_RED;
+            r->device = ms[k]->device;
+            r->mesh = ms[k];
+            r->cbf = cs[k];
+            r->prec = prec;
+            r->n = 2 * cs[k]->nhalf;
+            r->A32.alloc((size_t)r->n * r->n);
+            made[k] = std::move(r);
+            return made[k].get();
+        };
+        // scatterers whose cells fit the fused kernel: one launch over all their cell pairs
+        std::vector<int32_t> rest;
+        {
+            std::vector<Mesh *> fm;
+            std::vector<Cbf *> fc;
+            std::vector<c32 *> fa;
+            for (int32_t k = 0; k < count; ++k) {
+                const bool fused = prec == CBFM_MIXED_FUSED ? fused_fits(*ms[k], *cs[k]) : mixed_takes_fused(*ms[k], *cs[k]);
+                if (!fused) {
+                    rest.push_back(k);
+                    continue;
+                }
+                Red *r = make(k);
+                fm.push_back(ms[k]);
+                fc.push_back(cs[k]);
+                fa.push_back(r->A32.p);
+            }
+            assemble_project_fused(fm, fc, fa, st);
+        }
+        // the others: RWG matrices in memory, in waves of scatterers whose transient
+        // operators fit in half of the free device memory and in 6 GiB (larger waves
+        // would map fresh memory from the stream-ordered pool on every call)
         size_t free_b = 0, total_b = 0;
         CBFM_CUDA(cudaMemGetInfo(&free_b, &total_b));
         const double budget = std::min(0.5 * (double)free_b, 6.0 * (1ull << 30));
@@ -1036,37 +1080,31 @@ cbfm_status cbfm_assemble_reduced_batch(const cbfm_mesh_t *meshes, const cbfm_cb
             return 27.0 * nt * nt * 8 + 3.0 * ne * ne * 8 + 6.0 * ne * ldz * 4 + 8.0 * 2 * nh * ldz * 4 +
                    4.0 * nh * nh * 8;
         };
-        made.resize(count);
-        int32_t k0 = 0;
-        while (k0 < count) {
-            int32_t k1 = k0;
+        size_t i0 = 0;
+        while (i0 < rest.size()) {
+            size_t i1 = i0;
             double used = 0.0;
-            while (k1 < count && (k1 == k0 || used + transient(k1) <= budget)) used += transient(k1++);
-            std::vector<Mesh *> wm(ms.begin() + k0, ms.begin() + k1);
-            std::vector<Cbf *> wc(cs.begin() + k0, cs.begin() + k1);
-            std::vector<DevBuf<c32>> Z(k1 - k0);
+            while (i1 < rest.size() && (i1 == i0 || used + transient(rest[i1]) <= budget)) used += transient(rest[i1++]);
+            std::vector<Mesh *> wm;
+            std::vector<Cbf *> wc;
+            std::vector<DevBuf<c32>> Z(i1 - i0);
             std::vector<c32 *> Zp, Ap;
             std::vector<const c32 *> Zc;
-            for (int32_t k = k0; k < k1; ++k) {
-                std::unique_ptr<Red> r(new Red());
-                r->kind = H_RED;
-                r->device = ms[k]->device;
-                r->mesh = ms[k];
-                r->cbf = cs[k];
-                r->prec = CBFM_MIXED;
-                r->n = 2 * cs[k]->nhalf;
-                r->A32.alloc((size_t)r->n * r->n);
+            for (size_t i = i0; i < i1; ++i) {
+                const int32_t k = rest[i];
+                Red *r = make(k);
+                wm.push_back(ms[k]);
+                wc.push_back(cs[k]);
                 const int64_t ne = ms[k]->h.ne;
-                Z[k - k0].alloc((size_t)3 * ne * ne);
-                Zp.push_back(Z[k - k0].p);
-                Zc.push_back(Z[k - k0].p);
+                Z[i - i0].alloc((size_t)3 * ne * ne);
+                Zp.push_back(Z[i - i0].p);
+                Zc.push_back(Z[i - i0].p);
                 Ap.push_back(r->A32.p);
-                made[k] = std::move(r);
             }
             assemble_rwg_batch<float>(wm, Zp, st);
             project_tc_batch(wm, wc, Zc, Ap, st);
             CBFM_CUDA(cudaStreamSynchronize(st));
-            k0 = k1;
+            i0 = i1;
         }
         for (int32_t k = 0; k < count; ++k) {
             if (n_cbf) n_cbf[k] = made[k]->n;

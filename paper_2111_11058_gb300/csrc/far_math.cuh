@@ -173,18 +173,26 @@ __device__ __forceinline__ bool is_near_t(const T *rt_cen, const T *rt_lo, T ht,
 // The 27 local entries (op x 3 x 3, op = Ks, Ta, Tb) of a far triangle pair:
 // rt is the record of the test triangle, rs that of the trial triangle (the
 // kernel's type; FP32 records carry the centroid as hi + lo).
-template <typename T>
-__device__ __forceinline__ void far_entries(const T *rt, const T *rs, const MediaT<T> &md, cx<T> *out) {
-    const T *sq = rt + TR_Q, *sw = rt + TR_W, *sp = rt + TR_P, *sc = rt + TR_C;
-    const T *scen = rt + TR_CEN, *sclo = rt + TR_CLO;
+// SOA: the test record is stored field-major, element f at rt[f * rts] (a
+// structure-of-arrays copy whose consecutive triangles sit in consecutive
+// lanes); otherwise at rt[f].
+template <typename T, bool SOA = false>
+__device__ __forceinline__ void far_entries(const T *rt, int64_t rts, const T *rs, const MediaT<T> &md, cx<T> *out) {
+    auto R = [&](int f) -> T { return SOA ? rt[(int64_t)f * rts] : rt[f]; };
+    auto sq = [&](int i) -> T { return R(TR_Q + i); };
+    auto sw = [&](int i) -> T { return R(TR_W + i); };
+    auto sp = [&](int i) -> T { return R(TR_P + i); };
+    auto sc = [&](int i) -> T { return R(TR_C + i); };
+    auto scen = [&](int i) -> T { return R(TR_CEN + i); };
+    auto sclo = [&](int i) -> T { return R(TR_CLO + i); };
     // trial data (local to its centroid)
     T cs[3] = {rs[TR_CEN], rs[TR_CEN + 1], rs[TR_CEN + 2]};
-    T ct[3] = {scen[0], scen[1], scen[2]};
+    T ct[3] = {scen(0), scen(1), scen(2)};
     // centroid difference: hi/lo parts in the FP32 records keep it FP64-accurate
     T dc[3];
     for (int d = 0; d < 3; ++d) {
         dc[d] = ct[d] - cs[d];
-        if constexpr (sizeof(T) == 4) dc[d] += sclo[d] - rs[TR_CLO + d];
+        if constexpr (sizeof(T) == 4) dc[d] += sclo(d) - rs[TR_CLO + d];
     }
     T rq[7][3], wq[7];
     const T inv4pi = (T)(1.0 / (4.0 * PI));
@@ -200,7 +208,7 @@ __device__ __forceinline__ void far_entries(const T *rt, const T *rs, const Medi
     zero(mm[0]);
     zero(mm[1]);
     for (int p = 0; p < 7; ++p) {
-        T rho[3] = {sq[3 * p] - ct[0], sq[3 * p + 1] - ct[1], sq[3 * p + 2] - ct[2]};
+        T rho[3] = {sq(3 * p) - ct[0], sq(3 * p + 1) - ct[1], sq(3 * p + 2) - ct[2]};
         T Dp[3] = {dc[0] + rho[0], dc[1] + rho[1], dc[2] + rho[2]};
         // per medium over the trial points: S0 = sum w G, S1 = sum w G rho',
         // Sg = sum w g, Y = sum w g rho'.  With d = Dp - rho' (and rho' x rho' = 0)
@@ -246,7 +254,7 @@ __device__ __forceinline__ void far_entries(const T *rt, const T *rs, const Medi
                 }
             }
         }
-        const T wp = sw[p];
+        const T wp = sw(p);
         const T rw[3] = {wp * rho[0], wp * rho[1], wp * rho[2]};
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -290,13 +298,13 @@ __device__ __forceinline__ void far_entries(const T *rt, const T *rs, const Medi
     T pa[3][3], pb[3][3], cc[3][3], papb[3][3];
     for (int a = 0; a < 3; ++a) {
         for (int d = 0; d < 3; ++d) {
-            pa[a][d] = sp[3 * a + d] - ct[d];
+            pa[a][d] = sp(3 * a + d) - ct[d];
             pb[a][d] = rs[TR_P + 3 * a + d] - cs[d];
         }
     }
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
-            cc[a][b] = sc[a] * rs[TR_C + b];
+            cc[a][b] = sc(a) * rs[TR_C + b];
             papb[a][b] = pa[a][0] * pb[b][0] + pa[a][1] * pb[b][1] + pa[a][2] * pb[b][2];
         }
     // Ks = K1 + K2, Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2

@@ -139,6 +139,10 @@ void near_blocks_compact(const std::vector<Mesh *> &ms, const std::vector<c32 *>
 // for each mesh, with no RWG or local-block matrix in device memory.  fused_fits
 // tells whether the scatterer's cells fit the kernel's tile limits.
 bool fused_fits(const Mesh &m, const Cbf &c);
+// the form CBFM_MIXED takes: fused when the unfused scratch (local blocks, RWG
+// matrices, split operands) would not fit in a quarter of the free device memory and 16 GiB
+bool mixed_takes_fused(const Mesh &m, const Cbf &c);
+double unfused_scratch_bytes(const Mesh &m, const Cbf &c);
 void assemble_project_fused(const std::vector<Mesh *> &ms, const std::vector<Cbf *> &cs, const std::vector<c32 *> &A,
                             cudaStream_t st);
 // tuned launch parameters, per key (api.cu); 0 when not tuned yet

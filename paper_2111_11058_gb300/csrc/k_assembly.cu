@@ -75,7 +75,7 @@ __device__ __forceinline__ void far_pair(const FarStage<T> &S, int nt, const T *
         return;
     }
     cx<T> out[NCOMP];
-    far_entries<T>(S.trec, rs, md, out);
+    far_entries<T>(S.trec, 1, rs, md, out);
     for (int c = 0; c < NCOMP; ++c) Zloc[c * plane + base] = out[c];
 }
 

@@ -5,6 +5,7 @@
 // Every mbarrier wait is bounded (TC_WAIT_NS of wall clock).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap
 #include <stdint.h>
 
 namespace cbfm {
@@ -125,6 +126,21 @@ __device__ __forceinline__ void split64(double x, float &hi, float &lo) {
 // f (0..31) of row r from a 1024-byte-aligned tile base.
 __device__ __forceinline__ uint32_t swz128(int r, int f) {
     return (uint32_t)r * 128u + ((((uint32_t)(f >> 2)) ^ ((uint32_t)r & 7u)) << 4) + ((uint32_t)(f & 3) << 2);
+}
+
+// 64-byte-swizzled K-major tile of 16 floats per row: byte offset of float f
+// (0..15) of row r from a 512-byte-aligned tile base (16-byte chunk index XOR
+// address bits 7-8, i.e. the row pair within the 8-row, 512-byte atom).
+__device__ __forceinline__ uint32_t swz64(int r, int f) {
+    return (uint32_t)r * 64u + ((((uint32_t)(f >> 2)) ^ (((uint32_t)r >> 1) & 3u)) << 4) + ((uint32_t)(f & 3) << 2);
+}
+
+// Shared-memory matrix descriptor for a K-major operand with the 64-byte
+// swizzle: 8-row groups 512 bytes apart (stride byte offset), descriptor
+// version 1, swizzle mode 4.
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512u >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
 
 }  // namespace tc

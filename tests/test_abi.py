@@ -50,7 +50,8 @@ def _enum_values():
 def test_binding_constants_match_header(P):
     e = _enum_values()
     C = P.cbfm
-    assert (e["CBFM_FP64"], e["CBFM_MIXED"], e["CBFM_MIXED_SIMT"]) == (C.FP64, C.MIXED, C.MIXED_SIMT)
+    assert (e["CBFM_FP64"], e["CBFM_MIXED"], e["CBFM_MIXED_SIMT"], e["CBFM_MIXED_UNFUSED"], e["CBFM_MIXED_FUSED"]) == (
+        C.FP64, C.MIXED, C.MIXED_SIMT, C.MIXED_UNFUSED, C.MIXED_FUSED)
     assert (e["CBFM_PC_NONE"], e["CBFM_PC_CMP"], e["CBFM_PC_TDIAG"], e["CBFM_PC_CMP_INEXACT"]) == \
         (C.PC_NONE, C.PC_CMP, C.PC_TDIAG, C.PC_CMP_INEXACT)
     for name, val in e.items():

@@ -1,7 +1,11 @@
-"""Batched reduced-matrix assembly (one launch per stage over all
-scatterers): every reduced system equals the one assembled on its own, for a
-seeded mix of spheres, cubes and cylinders of uneven size with injected
-seeded CBFs, and batched systems solve to the same RCS as single ones."""
+"""Batched reduced-matrix assembly (one fused launch over the cell pairs of
+all scatterers that fit the fused kernel, one launch per unfused stage for the
+rest): every reduced system equals the one assembled on its own, for a seeded
+mix of spheres, cubes and cylinders of uneven size with injected seeded CBFs
+(one scatterer with cells beyond the fused kernel's limit of 256 RWG functions),
+and batched systems solve to the same RCS as single ones.  The fused kernel adds
+triangle-pair contributions with FP32 atomics, so two assemblies of the same
+system agree to rounding (1e-6 of the largest entry), not bit for bit."""
 import numpy as np
 import pytest
 
@@ -36,12 +40,20 @@ def _mix(P, count, seed):
     return meshes, cbfs
 
 
-def test_batch_equals_single_on_uneven_mix(P):
+@pytest.mark.parametrize("prec", [1, 4])
+def test_batch_equals_single_on_uneven_mix(P, prec):
     meshes, cbfs = _mix(P, 10, seed=3)
-    reds = P.assemble_reduced_batch(meshes, cbfs, P.MIXED)
-    assert len(reds) == 10
+    # one scatterer whose cells (about 430 RWG functions) exceed the fused kernel's tile
+    g = W.cube(12, 0.9)
+    big = P.mesh(g.verts, g.tris, 6, 3.0)
+    Ns = np.bincount(big.cells(), minlength=6)
+    CM, CJ = W.random_cbfs(Ns, [9] * 6, seed=11)
+    meshes.append(big)
+    cbfs.append(P.cbf_import(big, CM, CJ))
+    reds = P.assemble_reduced_batch(meshes, cbfs, prec)
+    assert len(reds) == 11
     for gm, c, rb in zip(meshes, cbfs, reds):
-        rs = P.assemble_reduced(gm, c, P.MIXED)
+        rs = P.assemble_reduced(gm, c, prec)
         a, b = rs.export(), rb.export()
         assert a.shape == b.shape and rb.n == rs.n
         assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
@@ -49,21 +61,22 @@ def test_batch_equals_single_on_uneven_mix(P):
     assert any(k.startswith("far_strip_f32") and v in (32, 64, 128) for k, v in tuned.items()), tuned
 
 
-def test_batch_solves_like_single(P):
+@pytest.mark.parametrize("prec", [1, 4])
+def test_batch_solves_like_single(P, prec):
     sph = W.icosphere(2, 0.3)
     cub = W.cube(6, 0.6)
     gen = W.plane_wave_set(W.fibonacci_dirs(12))
     exc = W.plane_wave_set(W.fibonacci_dirs(8))
     ms = [P.mesh(sph.verts, sph.tris, 8, 4.0, partition="octant"), P.mesh(cub.verts, cub.tris, 6, 2.5 - 0.1j)]
     cs = [P.build_cbfs(m, gen, 1e-3) for m in ms]
-    reds = P.assemble_reduced_batch(ms, cs, P.MIXED)
+    reds = P.assemble_reduced_batch(ms, cs, prec)
     for m, c, rb in zip(ms, cs, reds):
-        rs = P.assemble_reduced(m, c, P.MIXED)
+        rs = P.assemble_reduced(m, c, prec)
         for r in (rs, rb):
             P.cmp_setup(r)
         a = P.solve(rs, exc, tol=1e-8, monostatic=True, want_j=False, solver=P.BLOCK).rcs.sum(-1)
         b = P.solve(rb, exc, tol=1e-8, monostatic=True, want_j=False, solver=P.BLOCK).rcs.sum(-1)
-        assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
 
 
 def test_batch_rejects_other_precisions_and_empty(P):

@@ -86,13 +86,15 @@ def test_c2_cbf_counts_equal_oracle(cube, gold):
     assert cube["cbf"].L.tolist() == gold["L_per_cell"]
 
 
-def test_c2_bench_path_mixed_block_gmres(P, cube, gold):
-    red = P.assemble_reduced(cube["mesh"], cube["cbf"], P.MIXED)
+@pytest.mark.parametrize("prec", [1, 4])
+def test_c2_bench_path_mixed_block_gmres(P, cube, gold, prec):
+    """prec 1: the form CBFM_MIXED picks (the benchmark's); prec 4: the fused assembly-projection kernel."""
+    red = P.assemble_reduced(cube["mesh"], cube["cbf"], prec)
     assert red.n == gold["n_cbf"]
     P.cmp_setup(red)
     res = P.solve(red, cube["d"]["exc"], tol=1e-6, maxit=2000, restart=1000, monostatic=True, solver=P.BLOCK)
     e_rcs, e_j, e_norm = _errors(res, gold)
-    print(f"c2 MIXED block GMRES vs oracle: RCS {e_rcs:.2e}, currents {e_j:.2e}, norms {e_norm:.2e}, "
+    print(f"c2 mixed ({prec}) block GMRES vs oracle: RCS {e_rcs:.2e}, currents {e_j:.2e}, norms {e_norm:.2e}, "
           f"block iterations {int(res.iters.max())}")
     assert e_rcs <= 1e-4
     assert e_j <= J_MIXED

@@ -81,10 +81,11 @@ def test_reduced_fp64_c1(P, c1):
     assert _relmax(red.export(), c1["ref"]["A"]) < 1e-11
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3, 4])
 def test_reduced_mixed_c1(P, c1, prec):
     """Mixed paths: FP32 far-pair quadrature, projections as split-TF32 tensor-core
-    products (prec 1) or FP32 CUDA-core products (prec 2).  Stated bound on the
+    products after the assembly (prec 3; what prec 1 picks when memory allows)
+    or fused with it (prec 4), or FP32 CUDA-core products (prec 2).  Stated bound on the
     reduced matrix: 2e-5 of its largest entry (FP32 quadrature ~1e-7, split TF32
     ~2^-21 per product, FP32 accumulation over a few hundred terms)."""
     gm = _gpu_mesh(P, c1)
@@ -94,7 +95,7 @@ def test_reduced_mixed_c1(P, c1, prec):
     assert err < 2e-5
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5), (2, 2e-5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-5), (2, 2e-5), (3, 2e-5), (4, 2e-5)])
 def test_reduced_lossy_random_cbfs(P, prec, tol):
     g = W.icosphere(1, 0.4)
     m = OM.build_rwg(g.verts, g.tris)
@@ -108,7 +109,7 @@ def test_reduced_lossy_random_cbfs(P, prec, tol):
     assert _relmax(red.export(), A) < tol
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 5e-5), (2, 5e-5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 5e-5), (2, 5e-5), (3, 5e-5), (4, 5e-5)])
 def test_reduced_cube_full_size_sampled(P, prec, tol):
     """Full-size cube (T = 3072, 32 cells) with seeded injected CBFs; blocks
     the oracle can compute on their own (Z restricted to two cells)."""
@@ -132,6 +133,26 @@ def test_reduced_cube_full_size_sampled(P, prec, tol):
         got = [A[rm, rn], A[rm, rn2], A[rm2, rn], A[rm2, rn2]]
         for gb, ob in zip(got, blocks):
             assert _relmax(gb, ob) < tol, (mi, ni)
+
+
+def test_fused_equals_unfused_cube(P):
+    """The fused assembly-projection kernel and the unfused path (RWG matrices in
+    memory, then the tensor-core GEMMs) compute the same A: both sum the same FP32
+    local entries, in different orders, and the unfused path rounds Y to split
+    TF32 once more for its second GEMM where the fused kernel forms C_m^H Y in
+    FP32; each lies ~2e-6 of the largest entry from the exact A, so they agree to
+    5e-6.  Every entry of A is written by the fused kernel (all finite)."""
+    g = W.cube(10, 0.8)
+    gm = P.mesh(g.verts, g.tris, 12, 2.5 - 0.05j, partition="rcb")
+    Ns = np.bincount(gm.cells(), minlength=12)
+    CM, CJ = W.random_cbfs(Ns, [5 + (c * 7) % 23 for c in range(12)], seed=21)
+    cb = P.cbf_import(gm, CM, CJ)
+    Af = P.assemble_reduced(gm, cb, P.MIXED_FUSED).export()
+    Au = P.assemble_reduced(gm, cb, P.MIXED_UNFUSED).export()
+    assert np.isfinite(Af).all()
+    err = _relmax(Af, Au)
+    print(f"fused vs unfused: {err:.2e}")
+    assert err < 5e-6
 
 
 def test_build_cbfs_c1(P, c1):
@@ -179,7 +200,7 @@ def test_solve_fp64_c1(P, c1):
     assert (res.resid <= TOL_SOLVE).all()
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 4])
 def test_solve_mixed_c1_rcs_within_1e4(P, c1, prec):
     gm = _gpu_mesh(P, c1)
     red = P.assemble_reduced(gm, _inject(P, gm, c1["ref"]["cbfs"]), prec)
