@@ -460,6 +460,142 @@ def run_mom(P, mesh, d, exc_d, cbfm_rcs, t_cbfm_ms: float, timed) -> dict:
                       "rcs_rmse_db_cbfm_fp64_vs_mom": rmse_db(rcs_i64.sum(-1).cpu().numpy())}}
 
 
+def run_fused(P, mesh, cbf, exc_d, headline_rcs, t_headline_ms: float, timed, peaks, peak_src) -> dict:
+    """The headline step with the assembly fused with the tensor-core projection
+    (CBFM_MIXED_FUSED: no local-block or RWG matrix in memory) instead of the form
+    CBFM_MIXED picks when memory allows (RWG matrices in memory, then the GEMMs)."""
+    import torch
+    rcs = torch.zeros((N_RHS, 1, 2), dtype=torch.float64, device="cuda")
+
+    def step():
+        red = P.assemble_reduced(mesh, cbf, P.MIXED_FUSED)
+        P.cmp_setup(red)
+        P.solve(red, exc_d, tol=GMRES_TOL, maxit=2000, restart=1000, monostatic=True, want_j=False, out_rcs=rcs,
+                allow_noconv=True, solver=P.BLOCK)
+        red.free()
+    step()
+    t = float(np.mean(timed(2, step)))
+    P.profile(True)
+    P.profile_read(reset=True)
+    red = P.assemble_reduced(mesh, cbf, P.MIXED_FUSED)
+    pr = P.profile_read(reset=True)
+    red.free()
+    P.profile(False)
+    a = rcs.sum(-1).cpu().numpy()
+    return {"ms_per_step": t, "value": N_RHS / (t / 1000.0), "time_vs_headline": t / t_headline_ms,
+            "rcs_err_vs_headline": float(np.abs(a - headline_rcs).max() / np.abs(headline_rcs).max()),
+            "k_fused": roofline("k_fused", pr["k_fused"], peaks, peak_src),
+            "assembly_kernels_ms": {k: v["ms"] for k, v in sorted(pr.items(), key=lambda kv: -kv[1]["ms"])}}
+
+
+C5_CPU_BLOCKS = 2   # oracle cell-pair blocks per host core in the c5 CPU sample
+
+
+def _cpu_c5_block(pair):
+    from oracle import cbfm as OC
+    return OC.reduced_block(_CPU["m5"], _CPU["cbfs5"], _CPU["eps5"], pair[0], pair[1]) is not None
+
+
+def _cpu_c5_init(L):
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    from oracle import cbfm as OC, mesh as OM
+    d = W.spheroid_c5()
+    g = d["mesh"]
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = OM.cells_rcb(m, d["ncell"])
+    Ns = np.bincount(cell, minlength=d["ncell"])
+    CM, CJ = W.random_cbfs(Ns, L, seed=2)
+    _CPU.update(m5=m, eps5=complex(*d["eps"]),
+                cbfs5=[OC.CellCBF(np.nonzero(cell == c)[0], CM[c], CJ[c], np.ones(1), L[c]) for c in range(len(L))])
+
+
+def run_c5(P, timed, peaks, peak_src, cpu: bool) -> dict:
+    """The 90 000-unknown lossy prolate spheroid (256 cells, 256 directions x 2
+    polarisations as generating waves and as 512 monostatic excitations): set-up
+    (mesh, primary CBFs), then the step -- reduced matrix (CBFM_MIXED takes the
+    fused form: the unfused scratch would not fit), CMP, block GMRES to 1e-6 over
+    the whole basis -- timed with CUDA events.  The plain FP64 path is not run: its
+    assembly needs ~390 GB of scratch."""
+    import time as _t
+    import torch
+    d = W.spheroid_c5()
+    g = d["mesh"]
+    t0 = _t.perf_counter()
+    mesh = P.mesh(g.verts, g.tris, d["ncell"], complex(*d["eps"]), partition=d["partition"])
+    cbf = P.build_cbfs(mesh, d["gen"], 1e-3)
+    torch.cuda.synchronize()
+    t_setup = _t.perf_counter() - t0
+    exc = torch.tensor(d["exc"], dtype=torch.float64, device="cuda")
+    nrhs = exc.shape[0]
+    rcs = torch.zeros((nrhs, 1, 2), dtype=torch.float64, device="cuda")
+    st = {}
+
+    def step():
+        red = P.assemble_reduced(mesh, cbf, P.MIXED)
+        st["n"] = red.n
+        P.cmp_setup(red)
+        res = P.solve(red, exc, tol=GMRES_TOL, maxit=200, restart=red.n + 256, monostatic=True, want_j=False,
+                      out_rcs=rcs, allow_noconv=True, solver=P.BLOCK)
+        st["iters"], st["status"] = res.iters.copy(), res.status
+        red.free()
+    step()
+    ts = timed(2, step)
+    t = float(np.mean(ts))
+    P.profile(True)
+    P.profile_read(reset=True)
+    step()
+    pr = P.profile_read(reset=True)
+    P.profile(False)
+    out = {"workload": "lossy prolate spheroid, semi-axes 2 and 0.5 lambda0, eps_r 3-0.1j, T=30000, N=90000, "
+                       "256 cells, s=512 generating waves, 512 monostatic RHS, GMRES tol 1e-6, mixed precision",
+           "n_cbf": st["n"], "L_range": [int(cbf.L.min()), int(cbf.L.max())], "setup_s": t_setup,
+           "ms_per_step": t, "value": nrhs / (t / 1000.0), "unit": UNIT,
+           "latency_ms": {"p50": float(np.percentile(ts, 50)), "p99": float(np.percentile(ts, 99))},
+           "block_iters": int(st["iters"].max()), "converged": st["status"] == 0,
+           "k_fused": roofline("k_fused", pr["k_fused"], peaks, peak_src),
+           "kernels_ms": {k: v["ms"] for k, v in sorted(pr.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+           "fp64_path": "not run: the plain FP64 assembly needs ~390 GB of scratch"}
+    if cpu:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        Ls = [int(x) for x in cbf.L]
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        for k in keys:
+            os.environ[k] = "1"
+        try:
+            pool = cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"), initializer=_cpu_c5_init,
+                                          initargs=(Ls,))
+            list(pool.map(_cpu_noop, range(cores)))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        try:
+            rng = np.random.default_rng(0)
+            nc = len(Ls)
+            pick = [(int(a), int(b)) for a, b in rng.integers(0, nc, size=(C5_CPU_BLOCKS * cores, 2))]
+            t1 = _t.perf_counter()
+            assert all(pool.map(_cpu_c5_block, pick))
+            dt = _t.perf_counter() - t1
+        finally:
+            pool.shutdown()
+        t_asm = dt * nc * nc / len(pick)
+        out["cpu_baseline"] = {"kind": "oracle", "cores": cores, "assembly_s_extrapolated": t_asm,
+                               "sample": f"{len(pick)} of {nc * nc} cell-pair blocks of the reduced matrix (oracle dense "
+                                         f"definition, both media, seeded stand-in CBFs of the GPU's L_m), extrapolated "
+                                         f"to all blocks; the oracle's solve is not included",
+                               "measured_s": dt,
+                               "value": nrhs / t_asm, "unit": UNIT + " (upper bound: assembly only)"}
+    return out
+
+
 def run_cmp_inexact(P, mesh, cbf, exc_d, exact_rcs, t_exact_ms: float, timed) -> dict:
     """The headline step with the paper's inexact (G^CBF)^{-1} (an inner GMRES with
     the diagonal preconditioner D^CBF to 1e-5, Sec. III-C and IV) in place of the
@@ -528,6 +664,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-scatterer assembly run")
     ap.add_argument("--no-mom", action="store_true", help="skip the conventional-MoM comparison")
     ap.add_argument("--no-inexact", action="store_true", help="skip the inexact-CMP comparison")
+    ap.add_argument("--no-fused", action="store_true", help="skip the fused assembly-projection step on the headline cube")
+    ap.add_argument("--no-c5", action="store_true", help="skip the 90 000-unknown spheroid section")
     ap.add_argument("--solver", default="block", choices=["block", "per_rhs"],
                     help="GMRES variant of the timed step: block GMRES over all right-hand sides, or one per RHS")
     ap.add_argument("--workload", default="cube9216", choices=["cube9216", "cube2304", "sphere960"],
@@ -654,6 +792,14 @@ def main():
     if not args.no_mom and ws == 1:
         mom = run_mom(P, mesh, d, exc_d, mixed_rcs, t_step, timed)
 
+    fused = None
+    if not args.no_fused and ws == 1:
+        fused = run_fused(P, mesh, cbf, exc_d, mixed_rcs, t_step, timed, peaks, peak_src)
+
+    c5 = None
+    if not args.no_c5 and ws == 1 and WORKLOAD == "cube9216":
+        c5 = run_c5(P, timed, peaks, peak_src, cpu=not args.no_cpu)
+
     inexact = None
     if not args.no_inexact and ws == 1:
         try:
@@ -687,7 +833,7 @@ def main():
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
                 "fp64_path": fp64, "other_solver": alt, "mom": mom, "cmp_inexact": inexact, "batch": batch,
-                "serving": serving}
+                "serving": serving, "fused": fused, "c5": c5}
         if not args.no_cpu and ws == 1 and WORKLOAD == "cube9216":
             try:
                 line["cpu_baseline"] = cpu_sample()

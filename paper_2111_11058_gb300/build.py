@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcbfm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "mesh_host.cpp", "k_geom.cu", "k_assembly.cu", "k_dense.cu", "k_gmres.cu", "k_bgmres.cu", "noalloc.cu", "k_tc.cu", "k_tdiag.cu", "k_fused.cu"]
+SOURCES = ["api.cu", "mesh_host.cpp", "k_geom.cu", "k_assembly.cu", "k_dense.cu", "k_gmres.cu", "k_bgmres.cu", "noalloc.cu", "k_tc.cu", "k_tdiag.cu", "k_fused.cu", "k_celldiag.cu"]
 
 
 def nvcc() -> str:

@@ -144,19 +144,6 @@ namespace {
 
 // ------------------------------------------------------- helper kernels
 // Z_mm = [[Ks, Ta], [Tb, Ks]] restricted to the cell's edges (paper Eq. (pcbf)).
-__global__ void k_extract_zmm(int ncell, const int32_t *__restrict__ cell_off, const int64_t *__restrict__ zoff,
-                              int64_t ne, const z64 *__restrict__ Z, z64 *__restrict__ out) {
-    const int c = blockIdx.y;
-    const int64_t off = cell_off[c], N = cell_off[c + 1] - off, n2 = 2 * N;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n2 * n2;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = idx / n2, j = idx % n2;
-        int bi = i >= N, bj = j >= N;
-        int op = (bi == bj) ? 0 : (bi == 0 ? 1 : 2);
-        out[zoff[c] + idx] = Z[((int64_t)op * ne + off + (i - bi * N)) * ne + off + (j - bj * N)];
-    }
-}
-
 // V_m = [vE(Lambda_m); vH(Lambda_m)]
 __global__ void k_extract_v(int ncell, const int32_t *__restrict__ cell_off, const int64_t *__restrict__ voff, int s,
                             const z64 *__restrict__ vE, const z64 *__restrict__ vH, z64 *__restrict__ out) {
@@ -659,10 +646,8 @@ cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, do
         DevBuf<double> dw;
         dw.alloc(3 * (size_t)s);
         copy_in(dw.p, waves, 3 * sizeof(double) * s, st);
-        // RWG operators (FP64) and plane-wave RHS
-        DevBuf<z64> Z, vE, vH;
-        Z.alloc(3 * (size_t)ne * ne);
-        assemble_rwg<double>(*m, Z.p, st, true);   // the cells' diagonal blocks Z_mm only
+        // plane-wave RHS
+        DevBuf<z64> vE, vH;
         vE.alloc((size_t)ne * s);
         vH.alloc((size_t)ne * s);
         launch_rhs(*m, dw.p, s, vE.p, vH.p, st);
@@ -683,20 +668,14 @@ cbfm_status cbfm_build_cbfs(cbfm_mesh_t mesh, const double *waves, int32_t s, do
         Vm.alloc(vt);
         DevBuf<int32_t> dcoff;
         upload(dcoff, h.cell_off, st);
-        DevBuf<int64_t> dzoff, dvoff;
-        upload(dzoff, zoff, st);
+        DevBuf<int64_t> dvoff;
         upload(dvoff, voff, st);
-        {
-            ProfScope ps_("k_extract_zmm", st);
-            k_extract_zmm<<<dim3(nblk(4096 * 16), nc), 256, 0, st>>>(nc, dcoff.p, dzoff.p, ne, Z.p, Zmm.p);
-            launched("k_extract_zmm");
-        }
+        assemble_cell_diag(*m, Zmm.p, zoff, st);   // the cells' diagonal blocks Z_mm (FP64)
         {
             ProfScope ps_("k_extract_v", st);
             k_extract_v<<<dim3(nblk(4096 * 4), nc), 256, 0, st>>>(nc, dcoff.p, dvoff.p, s, vE.p, vH.p, Vm.p);
             launched("k_extract_v");
         }
-        Z.release();
         DevBuf<int> info;
         info.alloc(nc);
         CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int) * nc, st));

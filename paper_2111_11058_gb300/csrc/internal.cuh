@@ -51,7 +51,7 @@ struct Mesh : HandleBase {
     DevBuf<int32_t> edge_cell;   // ne, cell of each internal edge
     DevBuf<int32_t> near_pairs;  // n_near*2 (t, s), t <= s, both orders needed
     int64_t n_near = 0;
-    std::shared_ptr<FusedTables> fused;   // tables of the fused assembly (k_fused.cu), built on first use
+    std::shared_ptr<FusedTables> fused;   // triangle tables per cell (k_fused.cu), built on first use
     DevBuf<double> gram_val;     // ne*6 sparse RWG Gram row values
     DevBuf<int32_t> gram_col;    // ne*6 internal edge columns (-1 unused)
     double centre[3];
@@ -193,6 +193,32 @@ void mom_to_canonical(int64_t ne, const int32_t *d_int_of_canon, const z64 *A, z
 void red_export_noalloc(Red &r, double *A, cudaStream_t st);
 // loads the export's scratch array on the current device (once per device, from pool_setup)
 void noalloc_prepare();
+
+// Per-mesh triangle tables (k_fused.cu; built once per mesh, on first use): for
+// every cell the triangles that carry one of its RWG functions (spatially
+// ordered), the fused kernel's chunks of them, and the near list as a CSR.
+struct FusedTables {
+    std::vector<int32_t> tl_off, ch_off;   // per cell: offsets into tl and into the chunk table (host)
+    DevBuf<int4> tl;                       // per list entry: {triangle, rows a0 | a1 << 16, row a2 | cols b0, b1 << 24, col b2}
+    DevBuf<int32_t> dtl_off, dch_off;
+    DevBuf<int2> chunk;                    // per chunk: [begin, end) into tl
+    DevBuf<int16_t> chunk_cols;            // per chunk: the fused kernel's cell-local RWG columns (-1: padding)
+    DevBuf<float> recT;                    // FP32 triangle records of the list entries, field-major (48 x entries)
+    DevBuf<int32_t> vidT;                  // vertex ids of the list entries, field-major (3 x entries)
+    DevBuf<int2> rwg_pos;                  // per internal edge: list positions (in its cell's list) of its + and - triangles
+    DevBuf<int32_t> near_row;              // nt + 1: CSR of the near list over test triangles
+    DevBuf<int2> near_ent;                 // {trial triangle, 2 l + transposed}
+    int64_t n_near = 0;
+    int nmax = 0;                          // largest N_m
+};
+FusedTables &fused_tables(Mesh &m, cudaStream_t st);
+// near-pair blocks only, compact (27 complex per pair of each mesh's near list),
+// FP64 closed forms with FP32 (T = float) or FP64 (T = double) smooth remainders (k_assembly.cu)
+template <typename T>
+void near_blocks_compact_t(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &out, cudaStream_t st);
+// Z_mm of every cell in FP64, the 2 N_m x 2 N_m matrix [[Ks, Ta], [Tb, Ks]] of its RWG functions
+// (row-major, at Zmm + zoff[c]), from the triangle pairs of the cell alone (k_celldiag.cu)
+void assemble_cell_diag(Mesh &m, z64 *Zmm, const std::vector<int64_t> &zoff, cudaStream_t st);
 
 // elementwise helpers (k_dense.cu)
 void launch_z64_to_c32(const z64 *src, c32 *dst, int64_t n, cudaStream_t st);

@@ -686,23 +686,25 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
 }
 
 // The near-pair stage alone, in compact form: out[k][27 l + c] is component c
-// (op x 3 x 3) of the (t, s) block of near pair l of mesh k (FP64 closed forms,
-// FP32 smooth remainders: the mixed path).  One launch over all meshes.
-void near_blocks_compact(const std::vector<Mesh *> &ms, const std::vector<c32 *> &out, cudaStream_t st) {
+// (op x 3 x 3) of the (t, s) block of near pair l of mesh k (FP64 closed forms;
+// smooth remainders in T).  One launch over all meshes.
+template <typename T>
+void near_blocks_compact_t(const std::vector<Mesh *> &ms, const std::vector<cx<T> *> &out, cudaStream_t st) {
     const int nj = (int)ms.size();
-    std::vector<AsmJob<float>> jobs(nj);
+    std::vector<AsmJob<T>> jobs(nj);
     int64_t npairs = 0;
     for (int k = 0; k < nj; ++k) {
         Mesh &m = *ms[k];
-        AsmJob<float> &J = jobs[k];
-        J = AsmJob<float>{};
-        J.rec = m.tri32.p;
+        AsmJob<T> &J = jobs[k];
+        J = AsmJob<T>{};
+        if constexpr (sizeof(T) == 8) J.rec = (const T *)m.tri64.p;
+        else J.rec = (const T *)m.tri32.p;
         J.rec64 = m.tri64.p;
         J.vid = m.tri_vid.p;
         J.pairs = m.near_pairs.p;
         J.nearblk = out[k];
         J.md = media_full(m.k1, m.k2, m.eta1, m.eta2);
-        J.mdt = media_t<float>(J.md);
+        J.mdt = media_t<T>(J.md);
         J.alpha = m.alpha;
         J.nt = (int)m.h.nt;
         J.ne = m.h.ne;
@@ -710,19 +712,26 @@ void near_blocks_compact(const std::vector<Mesh *> &ms, const std::vector<c32 *>
         npairs += m.n_near;
     }
     if (npairs == 0) return;
-    DevBuf<AsmJob<float>> djobs;
+    DevBuf<AsmJob<T>> djobs;
     djobs.alloc(nj);
-    CBFM_CUDA(cudaMemcpyAsync(djobs.p, jobs.data(), sizeof(AsmJob<float>) * nj, cudaMemcpyHostToDevice, st));
+    CBFM_CUDA(cudaMemcpyAsync(djobs.p, jobs.data(), sizeof(AsmJob<T>) * nj, cudaMemcpyHostToDevice, st));
     int occ = 0;
-    CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_near_blocks<float>, 128, 0));
+    CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_near_blocks<T>, 128, 0));
     const unsigned grid =
         (unsigned)std::min<int64_t>((int64_t)std::max(1, occ) * sm_count(), ((npairs + 1) / 2 * 32 + 127) / 128);
     {
         ProfScope ps_("k_near_blocks", st);
-        k_near_blocks<float><<<grid, 128, 0, st>>>(djobs.p, nj, npairs);
+        k_near_blocks<T><<<grid, 128, 0, st>>>(djobs.p, nj, npairs);
         launched("k_near_blocks");
     }
     CBFM_CUDA(cudaStreamSynchronize(st));   // djobs is released on return
+}
+
+template void near_blocks_compact_t<float>(const std::vector<Mesh *> &, const std::vector<c32 *> &, cudaStream_t);
+template void near_blocks_compact_t<double>(const std::vector<Mesh *> &, const std::vector<z64 *> &, cudaStream_t);
+
+void near_blocks_compact(const std::vector<Mesh *> &ms, const std::vector<c32 *> &out, cudaStream_t st) {
+    near_blocks_compact_t<float>(ms, out, st);
 }
 
 template void assemble_rwg_batch<double>(const std::vector<Mesh *> &, const std::vector<z64 *> &, cudaStream_t, bool);

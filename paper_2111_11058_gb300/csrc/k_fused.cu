@@ -48,21 +48,6 @@
 
 namespace cbfm {
 
-// Per-mesh tables of the fused kernel (built once per mesh, on first use).
-struct FusedTables {
-    std::vector<int32_t> tl_off, ch_off;   // per cell: offsets into tl and into the chunk table (host)
-    DevBuf<int4> tl;                       // per list entry: {triangle, rows a0 | a1 << 16, row a2 | cols b0, b1 << 24, col b2}
-    DevBuf<int32_t> dtl_off, dch_off;
-    DevBuf<int2> chunk;                    // per chunk: [begin, end) into tl
-    DevBuf<int16_t> chunk_cols;            // per chunk: FU_KC cell-local RWG indices (-1: padding)
-    DevBuf<float> recT;                    // FP32 triangle records of the list entries, field-major (48 x entries)
-    DevBuf<int32_t> vidT;                  // vertex ids of the list entries, field-major (3 x entries)
-    DevBuf<int32_t> near_row;              // nt + 1: CSR of the near list over test triangles
-    DevBuf<int2> near_ent;                 // {trial triangle, 2 l + transposed}
-    int64_t n_near = 0;
-    int nmax = 0;                          // largest N_m
-};
-
 namespace {
 
 using namespace fm;
@@ -567,6 +552,8 @@ __global__ void k_tl_soa(int64_t ntl, const int4 *__restrict__ tl, const float *
     }
 }
 
+}  // namespace
+
 FusedTables &fused_tables(Mesh &m, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_fused_mu);
     if (m.fused) return *m.fused;
@@ -664,6 +651,20 @@ FusedTables &fused_tables(Mesh &m, cudaStream_t st) {
     }
     ft->tl_off[nc] = (int32_t)ent.size();
     ft->ch_off[nc] = (int32_t)chunks.size();
+    // list positions of the two triangles of every RWG function (both carry it, so both are in its cell's list)
+    std::vector<int2> rpos(h.ne, make_int2(-1, -1));
+    for (int c = 0; c < nc; ++c)
+        for (int32_t q = ft->tl_off[c]; q < ft->tl_off[c + 1]; ++q) {
+            const int32_t t = ent[q].x;
+            for (int a = 0; a < 3; ++a) {
+                const int32_t e = h.tri_edge[3 * t + a];
+                if (ecell[e] != c) continue;
+                if (h.edge_tri[2 * e] == t) rpos[e].x = q - ft->tl_off[c];
+                if (h.edge_tri[2 * e + 1] == t) rpos[e].y = q - ft->tl_off[c];
+            }
+        }
+    for (int64_t e = 0; e < h.ne; ++e)
+        CBFM_REQUIRE(rpos[e].x >= 0 && rpos[e].y >= 0, "triangle tables: an RWG function's triangle is missing");
     CBFM_REQUIRE(ft->nmax <= 0xfffe, "cell too large for the fused tables");
     // near list as CSR over the test triangle, both orientations
     std::vector<int32_t> np(2 * m.n_near);
@@ -695,6 +696,7 @@ FusedTables &fused_tables(Mesh &m, cudaStream_t st) {
     up(ft->dch_off, ft->ch_off);
     up(ft->chunk, chunks);
     up(ft->chunk_cols, ccols);
+    up(ft->rwg_pos, rpos);
     up(ft->near_row, rowc);
     up(ft->near_ent, ne);
     {
@@ -711,6 +713,8 @@ FusedTables &fused_tables(Mesh &m, cudaStream_t st) {
     m.fused = ft;
     return *ft;
 }
+
+namespace {
 
 FuPlan fu_plan(int lmax, int nmax) {
     FuPlan p;

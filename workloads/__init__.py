@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "Mesh", "icosphere", "cube", "cylinder", "spheroid", "sphere_array",
     "fibonacci_dirs", "plane_wave_set", "bistatic_cut", "cube_c2", "sphere_c1",
-    "scatterer_mix",
+    "scatterer_mix", "spheroid_c5",
 ]
 
 
@@ -285,6 +285,17 @@ def cube_c2(n_rhs: int = 128):
     exc = plane_wave_set(fibonacci_dirs(max(1, n_rhs // 2)))[:n_rhs]
     obs = exc[:, :2].copy()
     return dict(mesh=mesh, eps=(2.5, 0.0), ncell=32, partition="rcb", gen=gen, exc=exc, obs=obs)
+
+
+def spheroid_c5(n_dirs: int = 256):
+    """Lossy prolate spheroid, semi-axes 2 (z) and 0.5 (x, y), eps_r 3 - 0.1j,
+    100 rings x 150 longitudes (T = 30000, E = 45000, N = 90000), 256 RCB cells,
+    `n_dirs` Fibonacci directions x 2 polarisations as generating waves and as
+    monostatic excitations."""
+    mesh = spheroid(2.0, 0.5, 100, 150)
+    waves = plane_wave_set(fibonacci_dirs(n_dirs))
+    return dict(mesh=mesh, eps=(3.0, -0.1), ncell=256, partition="rcb", gen=waves, exc=waves,
+                obs=waves[:, :2].copy())
 
 
 def scatterer_mix(count: int, seed: int = 0):
