@@ -668,6 +668,9 @@ def main():
     ap.add_argument("--no-c5", action="store_true", help="skip the 90 000-unknown spheroid section")
     ap.add_argument("--solver", default="block", choices=["block", "per_rhs"],
                     help="GMRES variant of the timed step: block GMRES over all right-hand sides, or one per RHS")
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fused", "unfused"],
+                    help="form of the timed step's mixed-precision assembly: CBFM_MIXED (the faster form that fits), "
+                         "CBFM_MIXED_FUSED or CBFM_MIXED_UNFUSED")
     ap.add_argument("--workload", default="cube9216", choices=["cube9216", "cube2304", "sphere960"],
                     help="cube9216 is the benchmark; the others are small cases for profiler captures")
     args = ap.parse_args()
@@ -713,7 +716,8 @@ def main():
             red.free()
         return fn
 
-    step = make_step(P.MIXED, rcs_d, solver)
+    prec = {"mixed": P.MIXED, "fused": P.MIXED_FUSED, "unfused": P.MIXED_UNFUSED}[args.prec]
+    step = make_step(prec, rcs_d, solver)
     for _ in range(args.warmup):
         step()
     iters = state["iters"].copy()
@@ -745,7 +749,7 @@ def main():
     # end to end through the public API with pinned host buffers
     exc_h = torch.tensor(d["exc"], dtype=torch.float64).pin_memory()
     rcs_h = torch.zeros((N_RHS, 1, 2), dtype=torch.float64).pin_memory()
-    step_host = make_step(P.MIXED, rcs_h.numpy(), solver, exc=exc_h.numpy())
+    step_host = make_step(prec, rcs_h.numpy(), solver, exc=exc_h.numpy())
     ts_e2e = timed(max(1, min(args.steps, 3)), step_host)
     e2e = job_value(ws, N_RHS, max_over_ranks(float(np.mean(ts_e2e)), "cuda"))
 
@@ -768,7 +772,7 @@ def main():
     alt = None
     if not args.no_alt:
         rcs_alt = torch.zeros_like(rcs_d)
-        step_alt = make_step(P.MIXED, rcs_alt, other)
+        step_alt = make_step(prec, rcs_alt, other)
         step_alt()
         alt_iters = state["iters"].copy()
         ts_alt = timed(max(1, min(args.steps, 3)), step_alt)
