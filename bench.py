@@ -169,6 +169,13 @@ def _dist():
 
 
 WORKLOAD = "cube9216"
+WORKLOAD_TEXT = {
+    "cube9216": "dielectric cube side 1 lambda0, eps_r 2.5, T=3072, N=9216, 32 cells, s=128 generating waves",
+    "cube2304": "dielectric cube side 1 lambda0, eps_r 2.5, T=768, N=2304, 16 cells, s=128 generating waves",
+    "sphere960": "dielectric sphere radius 0.3 lambda0, eps_r 4, T=320, N=960, 8 cells, s=24 generating waves (12 directions x 2)",
+}
+PREC_TEXT = {"mixed": "mixed precision", "fused": "mixed precision, fused assembly-projection",
+             "unfused": "mixed precision, unfused assembly-projection"}
 
 
 def workload():
@@ -824,8 +831,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": "dielectric cube side 1 lambda0, eps_r 2.5, T=3072, N=9216, 32 cells, "
-                                       "s=128 generating waves, 128 monostatic RHS, GMRES tol 1e-6, mixed precision",
+                "config": {"workload": WORKLOAD_TEXT[WORKLOAD] + f", {N_RHS} monostatic RHS, GMRES tol 1e-6, "
+                                       + PREC_TEXT[args.prec],
                            "solver": args.solver,
                            "n_cbf": state.get("n"), "l2": "512 MB buffer written between timed steps",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
