@@ -29,6 +29,7 @@
 #include <atomic>
 #include <vector>
 
+#include "chol_blk.cuh"
 #include "cluster.cuh"
 #include "internal.cuh"
 
@@ -36,7 +37,7 @@ namespace cbfm {
 
 namespace {
 
-constexpr int PCHOL_MAX = 128;
+using namespace chol;
 constexpr int PCHOL_THREADS = 256;
 // ------------------------------------------------ pivoted Cholesky factor
 // Pivoted Cholesky of the Hermitian m x m matrix M (row-major): with the order
@@ -479,8 +480,8 @@ inline unsigned nb(int64_t work) { return (unsigned)std::max<int64_t>(1, std::mi
 
 struct Ctx {
     cudaStream_t st;
-    DevBuf<z64> M, R, Rinv, X, T1, Rf;
-    DevBuf<int> perm, rank, err;
+    DevBuf<z64> M, R, Rinv, X, T1, Rf, Dinv;
+    DevBuf<int> perm, rank, err, status;
     DevBuf<double> rnrm, scale, dev;
 };
 
@@ -506,7 +507,54 @@ double gram_dev(Ctx &c, int m) {
     return h;
 }
 
-// Pivoted / plain Cholesky on the m x m Gram matrix already in ctx.M; returns rank (host sync).
+// Cluster size of the blocked Cholesky on this device: 16 CTAs where a
+// cluster of 16 can be resident (non-portable size), else 8.
+template <int CC>
+cudaLaunchConfig_t chol_cfg(int m, cudaStream_t st, cudaLaunchAttribute *at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CC, 1, 1);
+    cfg.blockDim = dim3(CH_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = chol_cl_smem<CC>(m);
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CC;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int chol_cluster_size() {
+    static std::atomic<int> size[64];   // zero-initialised: not yet chosen
+    int dev = 0;
+    CBFM_CUDA(cudaGetDevice(&dev));
+    if (dev < 64) {
+        const int known = size[dev].load(std::memory_order_acquire);
+        if (known) return known;
+    }
+    CBFM_CUDA(cudaFuncSetAttribute(k_chol_cl<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)chol_cl_smem<8>(PCHOL_MAX)));
+    CBFM_CUDA(cudaFuncSetAttribute(k_chol_cl<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)chol_cl_smem<16>(PCHOL_MAX)));
+    int pick = 8;
+    if (cudaFuncSetAttribute(k_chol_cl<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        cudaLaunchAttribute at[1];
+        const cudaLaunchConfig_t cfg = chol_cfg<16>(PCHOL_MAX, 0, at);
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_chol_cl<16>, &cfg) == cudaSuccess && nclusters >= 1) pick = 16;
+    }
+    (void)cudaGetLastError();   // a refused non-portable size is not an error here
+    if (dev < 64) size[dev].store(pick, std::memory_order_release);
+    return pick;
+}
+
+// Cholesky on the m x m Gram matrix already in ctx.M; returns rank (host sync).
+// First the blocked factorisation without pivoting (rows with a zero
+// diagonal moved last); where one of its pivots falls below tol * max
+// diagonal and `pivot` is set, the pivoted factorisation runs instead, which
+// drops the dependent directions.  Without `pivot` the position of the
+// failing pivot is returned as the rank.
 int pchol(Ctx &c, int m, double tol, bool pivot) {
     static std::atomic<bool> attr_set[64];   // zero-initialised (static storage)
     int dev = 0;
@@ -518,14 +566,43 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
                                        (int)trinv_smem(PCHOL_MAX)));
         attr_set[dev].store(true, std::memory_order_release);
     }
+    CBFM_REQUIRE(m >= 1 && m <= PCHOL_MAX, "Cholesky: block width out of range");
+    const int cc = chol_cluster_size();
     {
-        CBFM_REQUIRE(m >= 1 && m <= PCHOL_MAX, "pivoted Cholesky: block width out of range");
         // algorithmic work of a full-rank factorisation and of the triangular inverse: m^3/6 complex MACs each
+        prof_add_work("k_chol_blk", 8.0 * m * m * m / 6.0, 16.0 * m * m);
+        ProfScope ps_("k_chol_blk", c.st);
+        cudaLaunchAttribute at[1];
+        if (cc == 16) {
+            const cudaLaunchConfig_t cfg = chol_cfg<16>(m, c.st, at);
+            CBFM_CUDA(cudaLaunchKernelEx(&cfg, k_chol_cl<16>, m, (const z64 *)c.M.p, tol, c.perm.p, c.R.p, c.Dinv.p,
+                                         c.rank.p, c.status.p, c.err.p));
+        } else {
+            const cudaLaunchConfig_t cfg = chol_cfg<8>(m, c.st, at);
+            CBFM_CUDA(cudaLaunchKernelEx(&cfg, k_chol_cl<8>, m, (const z64 *)c.M.p, tol, c.perm.p, c.R.p, c.Dinv.p,
+                                         c.rank.p, c.status.p, c.err.p));
+        }
+        launched("k_chol_cl");
+    }
+    {
+        prof_add_work("k_trinv_blk", 8.0 * m * m * m / 6.0, 32.0 * m * m);
+        ProfScope ps_("k_trinv_blk", c.st);
+        k_trinv_blk<<<m, 128, 0, c.st>>>(m, c.R.p, c.Dinv.p, c.rank.p, c.status.p, c.Rinv.p);
+        launched("k_trinv_blk");
+    }
+    int hr[3] = {0, 0, 0};
+    CBFM_CUDA(cudaMemcpyAsync(&hr[0], c.rank.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    CBFM_CUDA(cudaMemcpyAsync(&hr[1], c.err.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    CBFM_CUDA(cudaMemcpyAsync(&hr[2], c.status.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    CBFM_CUDA(cudaStreamSynchronize(c.st));
+    if (hr[1]) throw Fail{CBFM_ETIMEOUT, "Cholesky: a cluster synchronisation expired"};
+    if (hr[2] == 0 || !pivot) return hr[0];
+    {
         prof_add_work("k_pchol", 8.0 * m * m * m / 6.0, 16.0 * m * m);
         prof_add_work("k_trinv", 8.0 * m * m * m / 6.0, 32.0 * m * m);
         ProfScope ps_("k_pchol", c.st);
-        k_pchol_cl<<<PC_CL, PCHOL_THREADS, pchol_cl_smem(m), c.st>>>(m, c.M.p, c.perm.p, c.R.p, c.rank.p, tol,
-                                                                     pivot ? 1 : 0, c.err.p);
+        k_pchol_cl<<<PC_CL, PCHOL_THREADS, pchol_cl_smem(m), c.st>>>(m, c.M.p, c.perm.p, c.R.p, c.rank.p, tol, 1,
+                                                                     c.err.p);
         launched("k_pchol");
     }
     {
@@ -533,7 +610,6 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
         k_trinv<<<m, PCHOL_MAX, trinv_smem(m), c.st>>>(m, c.R.p, c.rank.p, c.Rinv.p);
         launched("k_trinv");
     }
-    int hr[2] = {0, 0};
     CBFM_CUDA(cudaMemcpyAsync(&hr[0], c.rank.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
     CBFM_CUDA(cudaMemcpyAsync(&hr[1], c.err.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
     CBFM_CUDA(cudaStreamSynchronize(c.st));
@@ -679,6 +755,8 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     c.perm.alloc(p);
     c.rank.alloc(1);
     c.err.alloc(1);
+    c.status.alloc(1);
+    c.Dinv.alloc((size_t)CH_NPAN * CH_B * CH_B);
     CBFM_CUDA(cudaMemsetAsync(c.err.p, 0, sizeof(int), st));
     c.rnrm.alloc(p);
     c.scale.alloc(p);

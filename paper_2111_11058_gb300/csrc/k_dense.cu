@@ -159,6 +159,15 @@ __global__ void k_splitk_reduce(const __grid_constant__ GemmBatch bt, const cx<T
 // writes every tile it covers completely straight to C; the (at most two)
 // tiles cut at the ends of its run go to its two partial-sum slots, and
 // k_gemm_sk_fix adds the slots of each cut tile in CTA order (deterministic).
+//
+// Every FP64 warp instruction holds its SM sub-partition's FP64 pipe for
+// about 64 clocks, so the complex products use three real multiplications
+// instead of four (Higham, "Stability of a method for multiplying complex
+// matrices with three real matrix multiplications", SIAM J. Matrix Anal.
+// Appl. 13, 1992):  with t1 = sum a_re b_re, t2 = sum a_im b_im and
+// t3 = sum (a_re + a_im)(b_re + b_im),  re = t1 - t2,  im = t3 - t1 - t2.
+// The sums a_re + a_im and b_re + b_im are formed once per staged element;
+// the error stays within a small multiple of the usual bound, normwise.
 constexpr int SK_T = 32, SK_K = 16;
 
 struct SkBatch {
@@ -188,6 +197,8 @@ __global__ void __launch_bounds__(256) k_gemm_sk(const __grid_constant__ SkBatch
                                                  double alpha) {
     __shared__ z64 As[SK_K][SK_T + 1];
     __shared__ z64 Bs[SK_K][SK_T + 1];
+    __shared__ double Ass[SK_K][SK_T + 1];   // a_re + a_im
+    __shared__ double Bss[SK_K][SK_T + 1];   // b_re + b_im
     const int64_t c = blockIdx.x;
     const int64_t u0 = sk_first(c, bt), u1 = sk_first(c + 1, bt);
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -201,31 +212,42 @@ __global__ void __launch_bounds__(256) k_gemm_sk(const __grid_constant__ SkBatch
         const int64_t seg_end = min(u1, bt.unit_off[g] + (t + 1) * ks);
         const int64_t ntn = (d.N + SK_T - 1) / SK_T;
         const int64_t m0 = (t / ntn) * SK_T, n0 = (t % ntn) * SK_T;
-        z64 acc[2][2];
+        double t1[2][2], t2[2][2], t3[2][2];
         for (int i = 0; i < 2; ++i)
-            for (int j = 0; j < 2; ++j) acc[i][j] = z64(0, 0);
+            for (int j = 0; j < 2; ++j) t1[i][j] = t2[i][j] = t3[i][j] = 0.0;
         for (int64_t kk = kk0; kk < kk0 + (seg_end - u); ++kk) {
             const int64_t k0 = kk * SK_K;
             for (int idx = threadIdx.x; idx < SK_T * SK_K; idx += 256) {
                 const int mm = rowA ? idx / SK_K : idx % SK_T;
                 const int kq = rowA ? idx % SK_K : idx / SK_T;
-                As[kq][mm] = load_op(A, d.a_off, d.lda, m0 + mm, k0 + kq, d.M, d.K, opA);
+                const z64 va = load_op(A, d.a_off, d.lda, m0 + mm, k0 + kq, d.M, d.K, opA);
+                As[kq][mm] = va;
+                Ass[kq][mm] = va.re + va.im;
                 const int kb = rowB ? idx / SK_T : idx % SK_K;
                 const int nn = rowB ? idx % SK_T : idx / SK_K;
-                Bs[kb][nn] = load_op(B, d.b_off, d.ldb, k0 + kb, n0 + nn, d.K, d.N, opB);
+                const z64 vb = load_op(B, d.b_off, d.ldb, k0 + kb, n0 + nn, d.K, d.N, opB);
+                Bs[kb][nn] = vb;
+                Bss[kb][nn] = vb.re + vb.im;
             }
             __syncthreads();
 #pragma unroll
             for (int kq = 0; kq < SK_K; ++kq) {
-                const z64 a0 = As[kq][ty], a1 = As[kq][ty + 16];
-                const z64 b0 = Bs[kq][tx], b1 = Bs[kq][tx + 16];
-                cfma(acc[0][0], a0, b0);
-                cfma(acc[0][1], a0, b1);
-                cfma(acc[1][0], a1, b0);
-                cfma(acc[1][1], a1, b1);
+                const z64 a[2] = {As[kq][ty], As[kq][ty + 16]}, b[2] = {Bs[kq][tx], Bs[kq][tx + 16]};
+                const double sa[2] = {Ass[kq][ty], Ass[kq][ty + 16]}, sb[2] = {Bss[kq][tx], Bss[kq][tx + 16]};
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        t1[i][j] = fma(a[i].re, b[j].re, t1[i][j]);
+                        t2[i][j] = fma(a[i].im, b[j].im, t2[i][j]);
+                        t3[i][j] = fma(sa[i], sb[j], t3[i][j]);
+                    }
             }
             __syncthreads();
         }
+        z64 acc[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) acc[i][j] = z64(t1[i][j] - t2[i][j], t3[i][j] - t1[i][j] - t2[i][j]);
         const bool whole = (kk0 == 0 && seg_end - u == ks);
         z64 *slot = part + (2 * c + (u == u0 ? 0 : 1)) * (SK_T * SK_T);
         for (int i = 0; i < 2; ++i) {
@@ -769,7 +791,7 @@ void gemm_sk(const std::vector<GemmDesc> &g, int opA, int opB, const z64 *A, con
 // The products are the FP64 stream-K GEMMs; only the diagonal-block
 // inverses are serial.  Used where the block pivots are safe (checked), else
 // the pivoted sweep above.
-constexpr int GJB = 32;
+constexpr int GJB = 16;   // small diagonal blocks: their serial inverses are cheap, the GEMMs carry the work
 
 // column panel C = A[:, k0:k0+b] (n x b, ld b) and row panel Rw = A[k0:k0+b, :] (b x n, ld n), per matrix
 __global__ void k_gjb_panels(int n, int k0, int b, const z64 *__restrict__ A, z64 *__restrict__ C,
@@ -792,7 +814,7 @@ __global__ void k_gjb_panels(int n, int k0, int b, const z64 *__restrict__ A, z6
 // the block (row exchanges undone on the columns at the end).  A pivot below
 // 1e-13 of the block's largest entry sets *flag.  The column block k of A is
 // zeroed (it is accumulated into next; its old values are in the panel copy).
-__global__ void __launch_bounds__(1024) k_gjb_inv(int n, int k0, int b, const z64 *__restrict__ Rw,
+__global__ void __launch_bounds__(GJB * GJB) k_gjb_inv(int n, int k0, int b, const z64 *__restrict__ Rw,
                                                  z64 *__restrict__ D, int *__restrict__ flag,
                                                  z64 *__restrict__ A) {
     __shared__ z64 a[GJB][GJB + 1];
@@ -850,10 +872,10 @@ __global__ void __launch_bounds__(1024) k_gjb_inv(int n, int k0, int b, const z6
                 a[p][c] = u;
             }
         __syncthreads();
-        if (threadIdx.x == 0) {   // one reciprocal per pivot, one FP64 division (long on GB300)
+        if (threadIdx.x == 0) {   // one reciprocal per pivot (correctly rounded)
             const z64 piv = a[k][k];
             const double d = norm2(piv);
-            const double id = d > 0.0 ? 1.0 / d : 0.0;
+            const double id = d > 0.0 ? __drcp_rn(d) : 0.0;
             s_pinv = z64(piv.re * id, -piv.im * id);
         }
         __syncthreads();
@@ -957,7 +979,7 @@ bool gj_blocked(int64_t n, int nbatch, const z64 *Aorig, z64 *inv, cudaStream_t 
         const int b = (int)std::min<int64_t>(GJB, n - k0);
         k_gjb_panels<<<dim3(nbk, nbatch), 256, 0, st>>>((int)n, (int)k0, b, inv, C.p, Rw.p);
         launched("k_gjb_panels");
-        {   // one thread per entry of the block in the elimination: 1024 threads
+        {   // one thread per entry of the block in the elimination: GJB x GJB threads
             prof_add_work("k_gjb_inv", 8.0 * nbatch * (double)b * b * b, 32.0 * nbatch * (double)b * b);
             ProfScope ps_("k_gjb_inv", st);
             k_gjb_inv<<<nbatch, GJB * GJB, 0, st>>>((int)n, (int)k0, b, Rw.p, D, flag.p, inv);
@@ -1015,8 +1037,10 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
     if (g.empty()) return;
     {
         double fl = 0, by = 0;
+        // complex MACs: 3 real multiply-adds each in the FP64 kernel (three-multiplication form), 4 in FP32
+        const double flop_per_cmac = sizeof(T) == 8 ? 6.0 : 8.0;
         for (auto &d : g) {
-            fl += 8.0 * d.M * d.N * d.K;
+            fl += flop_per_cmac * d.M * d.N * d.K;
             by += (double)(d.M * d.K + d.K * d.N + d.M * d.N) * sizeof(cx<T>);
         }
         prof_add_work(sizeof(T) == 8 ? "k_gemm_z64" : "k_gemm_c32", fl, by);
