@@ -384,6 +384,7 @@ def run_batch(count: int = 200) -> dict:
     P.profile_read(reset=True)
     _t, reds = timed(lambda: P.assemble_reduced_batch(meshes, cbfs, P.MIXED))
     prof = P.profile_read(reset=True)
+    prof = {k: v for k, v in prof.items() if not k.startswith("site:")}
     P.profile(False)
     t_single, singles = timed(lambda: [P.assemble_reduced(m, c, P.MIXED) for m, c in zip(meshes, cbfs)])
     worst = 0.0
@@ -486,6 +487,7 @@ def run_fused(P, mesh, cbf, exc_d, headline_rcs, t_headline_ms: float, timed, pe
     P.profile_read(reset=True)
     red = P.assemble_reduced(mesh, cbf, P.MIXED_FUSED)
     pr = P.profile_read(reset=True)
+    pr = {k: v for k, v in pr.items() if not k.startswith("site:")}
     red.free()
     P.profile(False)
     a = rcs.sum(-1).cpu().numpy()
@@ -553,6 +555,7 @@ def run_c5(P, timed, peaks, peak_src, cpu: bool) -> dict:
     P.profile_read(reset=True)
     step()
     pr = P.profile_read(reset=True)
+    pr = {k: v for k, v in pr.items() if not k.startswith("site:")}
     P.profile(False)
     out = {"workload": "lossy prolate spheroid, semi-axes 2 and 0.5 lambda0, eps_r 3-0.1j, T=30000, N=90000, "
                        "256 cells, s=512 generating waves, 512 monostatic RHS, GMRES tol 1e-6, mixed precision",
@@ -767,6 +770,9 @@ def main():
     timed(n_prof, step)
     prof = P.profile_read(reset=True)
     P.profile(False)
+    # "site:*" records split the FP64 products by the solver step that launched them
+    sites = {k[5:]: round(v["ms"] / n_prof, 3) for k, v in prof.items() if k.startswith("site:")}
+    prof = {k: v for k, v in prof.items() if not k.startswith("site:")}
     tot = sum(v["ms"] for v in prof.values())
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     peaks, peak_src = _peaks()
@@ -843,6 +849,7 @@ def main():
                 "gpu_launches": int(launches), "roofline": roof, "tuning": P.tuning(),
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
+                "fp64_products_ms_by_step": dict(sorted(sites.items(), key=lambda kv: -kv[1])),
                 "fp64_path": fp64, "other_solver": alt, "mom": mom, "cmp_inexact": inexact, "batch": batch,
                 "serving": serving, "fused": fused, "c5": c5}
         if not args.no_cpu and ws == 1 and WORKLOAD == "cube9216":

@@ -260,6 +260,17 @@ __global__ void k_place_block(int64_t n, int64_t nh, int64_t r0, const z64 *__re
     }
 }
 
+// out[(r0 + i) * n + r0 + j] = -conj(blk[j * nh + i]): minus the adjoint of an nh x nh block
+__global__ void k_place_neg_adjoint(int64_t n, int64_t nh, int64_t r0, const z64 *__restrict__ blk, int64_t ldb,
+                                    z64 *__restrict__ out) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nh * nh;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = idx / nh, j = idx % nh;
+        const z64 v = blk[j * ldb + i];
+        out[(r0 + i) * n + r0 + j] = z64(-v.re, v.im);
+    }
+}
+
 __global__ void k_copy_block(int64_t n, int64_t nh, int64_t r0, const z64 *__restrict__ full, z64 *__restrict__ blk) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nh * nh;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -881,9 +892,8 @@ void gram_cbf(Red &r, cudaStream_t st) {
     upload(dL, c.L, st);
     upload(dcoff64, c.coff, st);
     upload(dboff, c.boff, st);
-    DevBuf<z64> XM, XJ;
+    DevBuf<z64> XM;
     XM.alloc((size_t)ne * nh);
-    XJ.alloc((size_t)ne * nh);
     dim3 gx(nblk(nh), (unsigned)ne);
     CBFM_REQUIRE(ne <= 65535, "too many edges for the Gram product grid");
     {
@@ -892,25 +902,23 @@ void gram_cbf(Red &r, cudaStream_t st) {
                                            m.gram_col.p, c.CM.p, XM.p);
         launched("k_gram_times_c");
     }
-    {
-        ProfScope ps_("k_gram_times_c", st);
-        k_gram_times_c<<<gx, 256, 0, st>>>(ne, nh, m.edge_cell.p, dcoff.p, dcoff64.p, dboff.p, dL.p, m.gram_val.p,
-                                           m.gram_col.p, c.CJ.p, XJ.p);
-        launched("k_gram_times_c");
-    }
     r.G.alloc((size_t)n * n);
     CBFM_CUDA(cudaMemsetAsync(r.G.p, 0, sizeof(z64) * n * n, st));
-    std::vector<GemmDesc> gJ, gM;
+    std::vector<GemmDesc> gJ;
     for (int k = 0; k < nc; ++k) {
         int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
-        // first half: (C^J)^H Gf C^M ; second half: (C^M)^H Gf C^J
+        // first half: (C^J)^H Gf C^M
         gJ.push_back(GemmDesc{L, nh, N, c.boff[k], L, off * nh, nh, c.coff[k] * n, n});
-        gM.push_back(GemmDesc{L, nh, N, c.boff[k], L, off * nh, nh, (nh + c.coff[k]) * n + nh, n});
     }
     gemm_grouped<double>(gJ, 2, 0, c.CJ.p, XM.p, r.G.p, false, st);
-    gemm_grouped<double>(gM, 2, 0, c.CM.p, XJ.p, r.G.p, false, st);
+    // second half (C^M)^H Gf C^J = -((C^J)^H Gf C^M)^H: the RWG Gram Gf = <f_a, n x f_b> is
+    // real and antisymmetric (a . (n x b) = -b . (n x a), entry by entry in k_gram_rows)
+    {
+        ProfScope ps_("k_place_neg_adjoint", st);
+        k_place_neg_adjoint<<<nblk(nh * nh), 256, 0, st>>>(n, nh, nh, r.G.p, n, r.G.p);
+        launched("k_place_neg_adjoint");
+    }
     XM.release();
-    XJ.release();
 }
 
 }  // namespace
@@ -1146,25 +1154,28 @@ cbfm_status cbfm_cmp_setup(cbfm_red_t red, void *stream) {
         cudaStream_t st = (cudaStream_t)stream;
         gram_cbf(*r, st);
         const int64_t nh = r->cbf->nhalf, n = r->n;
-        // inverse of each half by Gauss-Jordan (FP64)
+        // inverse of the first half by Gauss-Jordan (FP64); the second half of G^CBF is
+        // minus the adjoint of the first, so its inverse is minus the adjoint of this one
         r->Ginv.alloc((size_t)n * n);
         CBFM_CUDA(cudaMemsetAsync(r->Ginv.p, 0, sizeof(z64) * n * n, st));
         DevBuf<z64> blk, aug;
         DevBuf<int> info;
-        blk.alloc((size_t)2 * nh * nh);   // the two halves, inverted as one batch
-        aug.alloc((size_t)4 * nh * nh);
+        blk.alloc((size_t)nh * nh);
+        aug.alloc((size_t)2 * nh * nh);
         info.alloc(1);
         CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int), st));
-        for (int half = 0; half < 2; ++half) {
+        {
             ProfScope ps_("k_copy_block", st);
-            k_copy_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, half * nh, r->G.p, blk.p + half * nh * nh);
+            k_copy_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, 0, r->G.p, blk.p);
             launched("k_copy_block");
         }
-        gauss_jordan_inverse(nh, 2, aug.p, blk.p, info.p, st);
-        for (int half = 0; half < 2; ++half) {
+        gauss_jordan_inverse(nh, 1, aug.p, blk.p, info.p, st);
+        {
             ProfScope ps_("k_place_block", st);
-            k_place_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, half * nh, blk.p + half * nh * nh, r->Ginv.p);
+            k_place_block<<<nblk(nh * nh), 256, 0, st>>>(n, nh, 0, blk.p, r->Ginv.p);
             launched("k_place_block");
+            k_place_neg_adjoint<<<nblk(nh * nh), 256, 0, st>>>(n, nh, nh, blk.p, nh, r->Ginv.p);
+            launched("k_place_neg_adjoint");
         }
         int hinfo = 0;
         CBFM_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -120,6 +120,14 @@ struct GemmDesc {
 template <typename T>
 void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> *A, const cx<T> *B, cx<T> *C,
                   bool accumulate, cudaStream_t st, double alpha = 1.0);
+// Profiling label of the FP64 products launched while an object is alive
+// (reported as "site:<label>" beside the kernel's own record).
+extern thread_local const char *g_gemm_site;
+struct GemmSite {
+    const char *prev;
+    explicit GemmSite(const char *label) : prev(g_gemm_site) { g_gemm_site = label; }
+    ~GemmSite() { g_gemm_site = prev; }
+};
 // Solve Z_b X_b = V_b in place (V overwritten by X) for nb independent systems of size n_b x n_b, s columns;
 // Z and V are overwritten. Returns singular flag per system in d_info (1 = zero pivot).
 void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, const int *h_n, int s, z64 *Z, z64 *V,

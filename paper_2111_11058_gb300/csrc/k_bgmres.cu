@@ -457,14 +457,17 @@ __global__ void k_add32to64(int64_t n, const c32 *__restrict__ X, z64 *__restric
         Y[i] += z64(X[i].re, X[i].im);
 }
 
-// ||M - I||_F of an m x m matrix (one block; fixed summation order)
+// ||M - I||_F of a Hermitian m x m matrix from its upper triangle (one block;
+// fixed summation order)
 __global__ void __launch_bounds__(256) k_gram_dev(int m, const z64 *__restrict__ M, double *__restrict__ out) {
     __shared__ double part[8];
     double s = 0.0;
     for (int idx = threadIdx.x; idx < m * m; idx += 256) {
+        const int a = idx / m, b = idx % m;
+        if (a > b) continue;
         z64 v = M[idx];
-        if (idx / m == idx % m) v.re -= 1.0;
-        s += v.re * v.re + v.im * v.im;
+        if (a == b) v.re -= 1.0;
+        s += (a == b ? 1.0 : 2.0) * (v.re * v.re + v.im * v.im);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
@@ -476,6 +479,61 @@ __global__ void __launch_bounds__(256) k_gram_dev(int m, const z64 *__restrict__
     }
 }
 
+// M[a][b] = conj(M[b][a]) for a > b: the lower triangle of a Hermitian matrix from its upper one
+__global__ void k_mirror_lower(int m, z64 *__restrict__ M) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * m; idx += gridDim.x * blockDim.x) {
+        const int a = idx / m, b = idx % m;
+        if (a > b) M[idx] = conj(M[(int64_t)b * m + a]);
+    }
+}
+
+// Part of a product: rows [r0, r0 + rows), columns [c0, c0 + cols) of op(A) op(B)
+// over the summation range [k0, k0 + ks) (offsets in the storage of each op).
+GemmDesc sub_desc(GemmDesc d, int opA, int opB, int64_t r0, int64_t rows, int64_t c0, int64_t cols, int64_t k0,
+                  int64_t ks) {
+    const bool rowA = opA == 0 || opA == 3, rowB = opB == 0 || opB == 3;
+    d.a_off += rowA ? r0 * d.lda + k0 : r0 + k0 * d.lda;
+    d.b_off += rowB ? k0 * d.ldb + c0 : k0 + c0 * d.ldb;
+    d.c_off += r0 * d.ldc + c0;
+    d.M = rows;
+    d.N = cols;
+    d.K = ks;
+    return d;
+}
+constexpr int64_t TT = 32;   // tile edge of the FP64 product kernel
+// The block upper triangle (tiles on or above the diagonal) of a Hermitian square product
+std::vector<GemmDesc> upper_tiles(const GemmDesc &d, int opA, int opB) {
+    std::vector<GemmDesc> g;
+    for (int64_t r0 = 0; r0 < d.M; r0 += TT)
+        g.push_back(sub_desc(d, opA, opB, r0, std::min(TT, d.M - r0), r0, d.N - r0, 0, d.K));
+    return g;
+}
+// op(A) lower triangular (row i is zero beyond column i): row tiles summed up to their last row
+std::vector<GemmDesc> lower_a_tiles(const GemmDesc &d, int opA, int opB) {
+    std::vector<GemmDesc> g;
+    for (int64_t r0 = 0; r0 < d.M; r0 += TT) {
+        const int64_t rows = std::min(TT, d.M - r0);
+        g.push_back(sub_desc(d, opA, opB, r0, rows, 0, d.N, 0, std::min(d.K, r0 + rows)));
+    }
+    return g;
+}
+// op(A) upper triangular (row i is zero before column i): row tiles summed from their first row
+std::vector<GemmDesc> upper_a_tiles(const GemmDesc &d, int opA, int opB) {
+    std::vector<GemmDesc> g;
+    for (int64_t r0 = 0; r0 < d.M; r0 += TT)
+        if (r0 < d.K) g.push_back(sub_desc(d, opA, opB, r0, std::min(TT, d.M - r0), 0, d.N, r0, d.K - r0));
+    return g;
+}
+// op(B) upper triangular (column j is zero below row j): column tiles summed up to their last column
+std::vector<GemmDesc> upper_b_tiles(const GemmDesc &d, int opA, int opB) {
+    std::vector<GemmDesc> g;
+    for (int64_t c0 = 0; c0 < d.N; c0 += TT) {
+        const int64_t cols = std::min(TT, d.N - c0);
+        g.push_back(sub_desc(d, opA, opB, 0, d.M, c0, cols, 0, std::min(d.K, c0 + cols)));
+    }
+    return g;
+}
+
 inline unsigned nb(int64_t work) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 4096)); }
 
 struct Ctx {
@@ -483,6 +541,8 @@ struct Ctx {
     DevBuf<z64> M, R, Rinv, X, T1, Rf, Dinv;
     DevBuf<int> perm, rank, err, status;
     DevBuf<double> rnrm, scale, dev;
+    bool perm_id = true;   // the last factorisation kept the order (perm is the identity)
+    std::vector<int> hperm;
 };
 
 // Cholesky QR applies its second pass only where the first leaves the block
@@ -591,12 +651,19 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
         launched("k_trinv_blk");
     }
     int hr[3] = {0, 0, 0};
+    c.hperm.resize(m);
     CBFM_CUDA(cudaMemcpyAsync(&hr[0], c.rank.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
     CBFM_CUDA(cudaMemcpyAsync(&hr[1], c.err.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
     CBFM_CUDA(cudaMemcpyAsync(&hr[2], c.status.p, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    CBFM_CUDA(cudaMemcpyAsync(c.hperm.data(), c.perm.p, sizeof(int) * m, cudaMemcpyDeviceToHost, c.st));
     CBFM_CUDA(cudaStreamSynchronize(c.st));
     if (hr[1]) throw Fail{CBFM_ETIMEOUT, "Cholesky: a cluster synchronisation expired"};
+    c.perm_id = true;
+    for (int i = 0; i < m; ++i) c.perm_id &= c.hperm[i] == i;
     if (hr[2] == 0 || !pivot) return hr[0];
+    c.perm_id = false;
+    k_mirror_lower<<<nb((int64_t)m * m), 256, 0, c.st>>>(m, c.M.p);   // the pivoted kernel reads whole rows
+    launched("k_mirror_lower");
     {
         prof_add_work("k_pchol", 8.0 * m * m * m / 6.0, 16.0 * m * m);
         prof_add_work("k_trinv", 8.0 * m * m * m / 6.0, 32.0 * m * m);
@@ -625,6 +692,7 @@ int pchol(Ctx &c, int m, double tol, bool pivot) {
 // Q (r x n) goes to Qdst and Rfull (r x m, ld m) satisfies
 // W_in[c] = sum_i Rfull[i][c] Q[i] up to the dropped parts.  Returns r.
 int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double tol, double ref, double drop) {
+    GemmSite site_("site:cholqr_rows");
     k_rownorm<<<m, 256, 0, c.st>>>(n, W, c.rnrm.p);
     launched("k_rownorm");
     if (ref <= 0.0) {
@@ -639,8 +707,8 @@ int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double
         k_scale_rows<<<g, 256, 0, c.st>>>(n, W, c.rnrm.p, ref, drop, c.scale.p);
         launched("k_scale_rows");
     }
-    // pass 1 (pivoted): M[a][b] = sum_k conj(W[a][k]) W[b][k]
-    gemm_grouped<double>({GemmDesc{m, m, n, 0, n, 0, n, 0, m}}, 3, 1, W, W, c.M.p, false, c.st);
+    // pass 1 (pivoted): M[a][b] = sum_k conj(W[a][k]) W[b][k], upper triangle
+    gemm_grouped<double>(upper_tiles(GemmDesc{m, m, n, 0, n, 0, n, 0, m}, 3, 1), 3, 1, W, W, c.M.p, false, c.st);
     const int r = pchol(c, m, tol, true);
     if (r == 0) return 0;
     k_make_x<<<1, 256, 0, c.st>>>(m, r, c.perm.p, c.Rinv.p, c.X.p);
@@ -649,10 +717,15 @@ int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double
     launched("k_zero2d");
     k_unpermute_r<<<nb((int64_t)r * m), 256, 0, c.st>>>(m, r, c.perm.p, c.R.p, c.Rf.p);
     launched("k_unpermute_r");
-    // Q1 = X W  -> T1 (r x n)
-    gemm_grouped<double>({GemmDesc{r, n, m, 0, m, 0, n, 0, n}}, 0, 0, c.X.p, W, c.T1.p, false, c.st);
+    // Q1 = X W  -> T1 (r x n); X is lower triangular when the order was kept
+    {
+        const GemmDesc dq{r, n, m, 0, m, 0, n, 0, n};
+        gemm_grouped<double>(c.perm_id ? lower_a_tiles(dq, 0, 0) : std::vector<GemmDesc>{dq}, 0, 0, c.X.p, W, c.T1.p,
+                             false, c.st);
+    }
     // pass 2 (no pivoting) on Q1, unless Q1 is already orthonormal to ORTH_TOL
-    gemm_grouped<double>({GemmDesc{r, r, n, 0, n, 0, n, 0, r}}, 3, 1, c.T1.p, c.T1.p, c.M.p, false, c.st);
+    gemm_grouped<double>(upper_tiles(GemmDesc{r, r, n, 0, n, 0, n, 0, r}, 3, 1), 3, 1, c.T1.p, c.T1.p, c.M.p, false,
+                         c.st);
     if (gram_dev(c, r) <= ORTH_TOL) {
         CBFM_CUDA(cudaMemcpyAsync(Qdst, c.T1.p, sizeof(z64) * r * n, cudaMemcpyDeviceToDevice, c.st));
         k_copy2d<<<nb((int64_t)r * m), 256, 0, c.st>>>(r, m, c.Rf.p, m, Rfull, m, 0);
@@ -666,9 +739,11 @@ int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double
     // Q = Rinv2^T Q1 : X2[i][l] = Rinv2[l][i]  (identity permutation)
     k_make_x<<<1, 256, 0, c.st>>>(r, r, c.perm.p, c.Rinv.p, c.X.p);
     launched("k_make_x");
-    gemm_grouped<double>({GemmDesc{r, n, r, 0, r, 0, n, 0, n}}, 0, 0, c.X.p, c.T1.p, Qdst, false, c.st);
-    // Rfull = R2 Rfull1 diag(scale) (r x m), R2 is r x r with leading dimension r
-    gemm_grouped<double>({GemmDesc{r, m, r, 0, r, 0, m, 0, m}}, 0, 0, c.R.p, c.Rf.p, Rfull, false, c.st);
+    gemm_grouped<double>(lower_a_tiles(GemmDesc{r, n, r, 0, r, 0, n, 0, n}, 0, 0), 0, 0, c.X.p, c.T1.p, Qdst, false,
+                         c.st);
+    // Rfull = R2 Rfull1 diag(scale) (r x m), R2 is r x r upper triangular with leading dimension r
+    gemm_grouped<double>(upper_a_tiles(GemmDesc{r, m, r, 0, r, 0, m, 0, m}, 0, 0), 0, 0, c.R.p, c.Rf.p, Rfull, false,
+                         c.st);
     k_scale_cols<<<nb((int64_t)r * m), 256, 0, c.st>>>(r, m, Rfull, c.scale.p);
     launched("k_scale_cols");
     return r;
@@ -681,13 +756,16 @@ int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double
 // factors of ctx have leading dimension p.
 void cholqr2_cols(Ctx &c, z64 *H, int d, int p, int64_t ldh, z64 *Rout, z64 *RinvOut, int64_t ldr,
                   DevBuf<z64> &tmp) {
+    GemmSite site_("site:cholqr_hess");
     for (int pass = 0; pass < 2; ++pass) {
-        gemm_grouped<double>({GemmDesc{p, p, d, 0, ldh, 0, ldh, 0, p}}, 2, 0, H, H, c.M.p, false, c.st);
+        gemm_grouped<double>(upper_tiles(GemmDesc{p, p, d, 0, ldh, 0, ldh, 0, p}, 2, 0), 2, 0, H, H, c.M.p, false,
+                             c.st);
         if (pass == 1 && gram_dev(c, p) <= ORTH_TOL) break;   // the first pass is orthonormal already
         const int r = pchol(c, p, 0.0, false);
         if (r != p) throw Fail{CBFM_ESINGULAR, "block GMRES: block Hessenberg lost column rank"};
         // H <- H Rinv  (via tmp, ld p)
-        gemm_grouped<double>({GemmDesc{d, p, p, 0, ldh, 0, p, 0, p}}, 0, 0, H, c.Rinv.p, tmp.p, false, c.st);
+        gemm_grouped<double>(upper_b_tiles(GemmDesc{d, p, p, 0, ldh, 0, p, 0, p}, 0, 0), 0, 0, H, c.Rinv.p, tmp.p,
+                             false, c.st);
         k_copy2d<<<nb((int64_t)d * p), 256, 0, c.st>>>(d, p, tmp.p, p, H, ldh, 0);
         launched("k_copy2d");
         if (pass == 0) {
@@ -697,11 +775,12 @@ void cholqr2_cols(Ctx &c, z64 *H, int d, int p, int64_t ldh, z64 *Rout, z64 *Rin
             launched("k_copy2d");
         } else {
             // Rout = R2 R1, RinvOut = R1^{-1} R2^{-1}
-            gemm_grouped<double>({GemmDesc{p, p, p, 0, p, 0, ldr, 0, p}}, 0, 0, c.R.p, Rout, tmp.p, false, c.st);
+            gemm_grouped<double>(upper_a_tiles(GemmDesc{p, p, p, 0, p, 0, ldr, 0, p}, 0, 0), 0, 0, c.R.p, Rout, tmp.p,
+                                 false, c.st);
             k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, tmp.p, p, Rout, ldr, 0);
             launched("k_copy2d");
-            gemm_grouped<double>({GemmDesc{p, p, p, 0, ldr, 0, p, 0, p}}, 0, 0, RinvOut, c.Rinv.p, tmp.p, false,
-                                 c.st);
+            gemm_grouped<double>(upper_a_tiles(GemmDesc{p, p, p, 0, ldr, 0, p, 0, p}, 0, 0), 0, 0, RinvOut, c.Rinv.p,
+                                 tmp.p, false, c.st);
             k_copy2d<<<nb((int64_t)p * p), 256, 0, c.st>>>(p, p, tmp.p, p, RinvOut, ldr, 0);
             launched("k_copy2d");
         }
@@ -876,6 +955,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             double wref = 0.0;
             // block classical Gram-Schmidt, twice; HcT (pjc x d1) collects the coefficients
             for (int pass = 0; pass < 2; ++pass) {
+                GemmSite site_(pass == 0 ? "site:gs1" : "site:gs2");
                 gemm_grouped<double>({GemmDesc{pjc, d1, n, 0, n, 0, n, 0, dcap}}, 0, 2, W.p, V.p, tmp2.p, false, st);
                 if (pass == 1 && fro(pjc, (int)d1, tmp2.p, dcap) <= ORTH_TOL * norm_sum(h_w1, pjc)) break;
                 gemm_grouped<double>({GemmDesc{pjc, n, d1, 0, dcap, 0, n, 0, n}}, 0, 0, tmp2.p, V.p, W.p, true, st,
@@ -922,6 +1002,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
                 launched("k_colnorm");
                 CBFM_CUDA(cudaMemcpyAsync(h_h0.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
                 for (int pass = 0; pass < 2; ++pass) {
+                    GemmSite site_(pass == 0 ? "site:hess_proj1" : "site:hess_proj2");
                     gemm_grouped<double>(proj, 2, 0, Qh.p, Hn.p, tmp2.p, false, st);
                     if (pass == 1 && fro((int)d0, pjc, tmp2.p, p) <= ORTH_TOL * norm_sum(h_h1, pjc)) break;
                     gemm_grouped<double>(upd, 0, 0, Qh.p, tmp2.p, Hn.p, true, st, -1.0);
@@ -945,6 +1026,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             // projected right-hand side rows and the residual of the least-squares
             // problem, updated with the new Q block only (Rv = E1S - Q Q^H E1S):
             //   G_J = Q_J^H Rv,  Rv <- Rv - Q_J G_J
+            GemmSite site_ls_("site:ls_rhs");
             gemm_grouped<double>({GemmDesc{pjc, p, d2, 0, p, 0, p, d0 * p, p}}, 2, 0, Hn.p, Rv.p, Gv.p, false, st);
             gemm_grouped<double>({GemmDesc{d2, p, pjc, 0, p, d0 * p, p, 0, p}}, 0, 0, Hn.p, Gv.p, Rv.p, true, st,
                                  -1.0);
@@ -967,6 +1049,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             if (all || r == 0 || total_blocks >= maxit) break;
         }
         // solve Rh Z = Gv (block back substitution) and update Y += Z^T V
+        GemmSite site_sol_("site:solution");
         const int64_t dJ = dims[J];
         for (int i = J - 1; i >= 0; --i) {
             const int64_t a0 = dims[i], a1 = dims[i + 1];

@@ -157,8 +157,9 @@ __global__ void k_splitk_reduce(const __grid_constant__ GemmBatch bt, const cx<T
 // problem by problem, tile by tile, K-step by K-step, are dealt out to G
 // CTAs in equal contiguous runs (CTA c takes [c U / G, (c+1) U / G)).  A CTA
 // writes every tile it covers completely straight to C; the (at most two)
-// tiles cut at the ends of its run go to its two partial-sum slots, and
-// k_gemm_sk_fix adds the slots of each cut tile in CTA order (deterministic).
+// tiles cut at the ends of its run go to its two partial-sum slots.  The last
+// CTA to finish its part of a cut tile (a counter per tile) adds the slots of
+// the tile's CTAs in CTA order (deterministic) and writes C.
 //
 // Every FP64 warp instruction holds its SM sub-partition's FP64 pipe for
 // about 64 clocks, so the complex products use three real multiplications
@@ -175,6 +176,7 @@ struct SkBatch {
     int G;                           // CTAs
     int64_t U;                       // units
     int64_t unit_off[GB_MAXG + 1];   // first unit of problem g
+    int64_t tile_off[GB_MAXG + 1];   // first tile of problem g (index of its cut-tile counter)
     int64_t ksteps[GB_MAXG];         // K-steps per tile of problem g
     GemmDesc d[GB_MAXG];
 };
@@ -191,10 +193,31 @@ __device__ __forceinline__ int sk_group(const SkBatch &bt, int64_t u) {
 __device__ __forceinline__ int64_t sk_first(int64_t c, const SkBatch &bt) { return c * bt.U / bt.G; }
 __device__ __forceinline__ int64_t sk_owner(int64_t u, const SkBatch &bt) { return ((u + 1) * bt.G - 1) / bt.U; }
 
+// The last CTA of a cut tile: C tile = alpha * (sum of the tile's slots in CTA order) (+ C)
+__device__ __noinline__ void sk_sum_tile(const SkBatch &bt, int g, int64_t m0, int64_t n0, int64_t tu0, int64_t cf,
+                                         int64_t cl, const z64 *part, z64 *C, int accumulate, double alpha) {
+    const GemmDesc &d = bt.d[g];
+    for (int e = threadIdx.x; e < SK_T * SK_T; e += blockDim.x) {
+        const int64_t r = m0 + e / SK_T, col = n0 + e % SK_T;
+        if (r >= d.M || col >= d.N) continue;
+        z64 v(0, 0);
+        for (int64_t cc = cf; cc <= cl; ++cc) {
+            const int jslot = (sk_first(cc, bt) >= tu0) ? 0 : 1;
+            const double2 pv = __ldcg(reinterpret_cast<const double2 *>(part) + (2 * cc + jslot) * (SK_T * SK_T) + e);
+            v += z64(pv.x, pv.y);
+        }
+        z64 *pc = C + d.c_off + r * d.ldc + col;
+        v = alpha * v;
+        if (accumulate) *pc += v;
+        else *pc = v;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_gemm_sk(const __grid_constant__ SkBatch bt, int opA, int opB,
                                                  const z64 *__restrict__ A, const z64 *__restrict__ B,
-                                                 z64 *__restrict__ C, z64 *__restrict__ part, int accumulate,
-                                                 double alpha) {
+                                                 z64 *__restrict__ C, z64 *__restrict__ part,
+                                                 unsigned *__restrict__ tile_cnt, int accumulate, double alpha) {
+    __shared__ int s_last;
     __shared__ z64 As[SK_K][SK_T + 1];
     __shared__ z64 Bs[SK_K][SK_T + 1];
     __shared__ double Ass[SK_K][SK_T + 1];   // a_re + a_im
@@ -249,57 +272,37 @@ __global__ void __launch_bounds__(256) k_gemm_sk(const __grid_constant__ SkBatch
         for (int i = 0; i < 2; ++i)
             for (int j = 0; j < 2; ++j) acc[i][j] = z64(t1[i][j] - t2[i][j], t3[i][j] - t1[i][j] - t2[i][j]);
         const bool whole = (kk0 == 0 && seg_end - u == ks);
-        z64 *slot = part + (2 * c + (u == u0 ? 0 : 1)) * (SK_T * SK_T);
-        for (int i = 0; i < 2; ++i) {
-            const int64_t r = m0 + ty + 16 * i;
-            for (int j = 0; j < 2; ++j) {
-                const int64_t col = n0 + tx + 16 * j;
-                if (!whole) {
-                    slot[(ty + 16 * i) * SK_T + tx + 16 * j] = acc[i][j];
-                } else if (r < d.M && col < d.N) {
-                    z64 *pc = C + d.c_off + r * d.ldc + col;
-                    const z64 v = alpha * acc[i][j];
-                    if (accumulate) *pc += v;
-                    else *pc = v;
+        if (whole) {
+            for (int i = 0; i < 2; ++i) {
+                const int64_t r = m0 + ty + 16 * i;
+                for (int j = 0; j < 2; ++j) {
+                    const int64_t col = n0 + tx + 16 * j;
+                    if (r < d.M && col < d.N) {
+                        z64 *pc = C + d.c_off + r * d.ldc + col;
+                        const z64 v = alpha * acc[i][j];
+                        if (accumulate) *pc += v;
+                        else *pc = v;
+                    }
                 }
             }
+        } else {
+            z64 *slot = part + (2 * c + (u == u0 ? 0 : 1)) * (SK_T * SK_T);
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) slot[(ty + 16 * i) * SK_T + tx + 16 * j] = acc[i][j];
+            // the tile's CTAs are the owners of its first to its last unit
+            const int64_t tu0 = bt.unit_off[g] + t * ks, tu1 = tu0 + ks;
+            const int64_t cf = sk_owner(tu0, bt), cl = sk_owner(tu1 - 1, bt);
+            __threadfence();   // this CTA's slot before its count
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned prev = atomicAdd(&tile_cnt[bt.tile_off[g] + t], 1u);
+                s_last = prev == (unsigned)(cl - cf) ? 1 : 0;
+                __threadfence();
+            }
+            __syncthreads();
+            if (s_last) sk_sum_tile(bt, g, m0, n0, tu0, cf, cl, part, C, accumulate, alpha);
         }
         u = seg_end;
-    }
-}
-
-// One CTA per boundary b between the runs of CTAs b and b+1: if the boundary
-// cuts a tile and b is the first CTA on that tile, sum the tile's slots over
-// the CTAs that cover it, in CTA order, and write C.
-__global__ void __launch_bounds__(256) k_gemm_sk_fix(const __grid_constant__ SkBatch bt,
-                                                     const z64 *__restrict__ part, z64 *__restrict__ C,
-                                                     int accumulate, double alpha) {
-    const int64_t b = blockIdx.x;
-    const int64_t ub = sk_first(b + 1, bt);   // first unit after the run of CTA b
-    if (ub <= 0 || ub >= bt.U) return;
-    const int64_t last = ub - 1;
-    const int g = sk_group(bt, last);
-    const GemmDesc &d = bt.d[g];
-    const int64_t ks = bt.ksteps[g];
-    const int64_t t = (last - bt.unit_off[g]) / ks;
-    const int64_t tu0 = bt.unit_off[g] + t * ks, tu1 = tu0 + ks;
-    if (ub >= tu1) return;                    // the tile ends with the run of CTA b
-    if (sk_owner(tu0, bt) != b) return;       // an earlier boundary cuts this tile
-    const int64_t clast = sk_owner(tu1 - 1, bt);
-    const int64_t ntn = (d.N + SK_T - 1) / SK_T;
-    const int64_t m0 = (t / ntn) * SK_T, n0 = (t % ntn) * SK_T;
-    for (int e = threadIdx.x; e < SK_T * SK_T; e += 256) {
-        const int64_t r = m0 + e / SK_T, col = n0 + e % SK_T;
-        if (r >= d.M || col >= d.N) continue;
-        z64 v(0, 0);
-        for (int64_t c = b; c <= clast; ++c) {
-            const int j = (sk_first(c, bt) >= tu0) ? 0 : 1;
-            v += part[(2 * c + j) * (SK_T * SK_T) + e];
-        }
-        z64 *pc = C + d.c_off + r * d.ldc + col;
-        v = alpha * v;
-        if (accumulate) *pc += v;
-        else *pc = v;
     }
 }
 
@@ -758,29 +761,33 @@ void gemm_sk(const std::vector<GemmDesc> &g, int opA, int opB, const z64 *A, con
     for (size_t g0 = 0; g0 < g.size(); g0 += GB_MAXG) {
         SkBatch bt;
         bt.ng = (int)std::min<size_t>(GB_MAXG, g.size() - g0);
-        bt.unit_off[0] = 0;
+        bt.unit_off[0] = bt.tile_off[0] = 0;
         for (int i = 0; i < bt.ng; ++i) {
             const GemmDesc &d = g[g0 + i];
             bt.d[i] = d;
             const int64_t tiles = (d.M > 0 && d.N > 0) ? ((d.M + SK_T - 1) / SK_T) * ((d.N + SK_T - 1) / SK_T) : 0;
             bt.ksteps[i] = std::max<int64_t>(1, (d.K + SK_K - 1) / SK_K);   // K = 0: one step of zeros
             bt.unit_off[i + 1] = bt.unit_off[i] + tiles * bt.ksteps[i];
+            bt.tile_off[i + 1] = bt.tile_off[i] + tiles;
         }
         bt.U = bt.unit_off[bt.ng];
         if (bt.U == 0) continue;
         bt.G = (int)std::min<int64_t>(G0, bt.U);
-        z64 *part = nullptr;
-        if (bt.G > 1) CBFM_CUDA(cudaMallocAsync((void **)&part, sizeof(z64) * 2 * bt.G * SK_T * SK_T, st));
+        // partial-sum slots (two per CTA) and one arrival counter per tile, zeroed
+        const size_t slot_bytes = sizeof(z64) * 2 * (size_t)bt.G * SK_T * SK_T;
+        const size_t cnt_bytes = sizeof(unsigned) * (size_t)bt.tile_off[bt.ng];
+        unsigned char *scratch = nullptr;
+        CBFM_CUDA(cudaMallocAsync((void **)&scratch, slot_bytes + cnt_bytes, st));
+        z64 *part = reinterpret_cast<z64 *>(scratch);
+        unsigned *tile_cnt = reinterpret_cast<unsigned *>(scratch + slot_bytes);
+        CBFM_CUDA(cudaMemsetAsync(tile_cnt, 0, cnt_bytes, st));
         {
             ProfScope ps_("k_gemm_z64", st);
-            k_gemm_sk<<<bt.G, 256, 0, st>>>(bt, opA, opB, A, B, C, part, accumulate ? 1 : 0, alpha);
+            ProfScope site_(g_gemm_site ? g_gemm_site : "site:other", st);
+            k_gemm_sk<<<bt.G, 256, 0, st>>>(bt, opA, opB, A, B, C, part, tile_cnt, accumulate ? 1 : 0, alpha);
             launched("k_gemm_sk");
-            if (bt.G > 1) {
-                k_gemm_sk_fix<<<bt.G - 1, 256, 0, st>>>(bt, part, C, accumulate ? 1 : 0, alpha);
-                launched("k_gemm_sk_fix");
-            }
         }
-        if (part) CBFM_CUDA(cudaFreeAsync(part, st));
+        CBFM_CUDA(cudaFreeAsync(scratch, st));
     }
 }
 
@@ -810,44 +817,52 @@ __global__ void k_gjb_panels(int n, int k0, int b, const z64 *__restrict__ A, z6
 }
 
 // D = inverse of the b x b diagonal block Rw[:, k0:k0+b] (ld n), one CTA per
-// matrix: Gauss-Jordan in place in shared memory with partial pivoting inside
-// the block (row exchanges undone on the columns at the end).  A pivot below
-// 1e-13 of the block's largest entry sets *flag.  The column block k of A is
-// zeroed (it is accumulated into next; its old values are in the panel copy).
+// matrix: Gauss-Jordan with partial pivoting inside the block (row exchanges
+// undone on the columns when D is stored).  A pivot below 1e-13 of the
+// block's largest entry sets *flag.  The column block k of A is zeroed (it is
+// accumulated into next; its old values are in the panel copy).
+//
+// Each step is two phases over ping-pong copies of the block: warp 0 finds the
+// pivot, inverts it and scales the pivot row (the new row k); then every
+// entry of the other rows is updated from the old copy with four FMAs.  FP64
+// warp instructions are the cost here (each holds a sub-partition's FP64 pipe
+// for ~64 clocks whatever its active lanes), so the pivot-row work is done
+// once, by one warp, instead of once per entry.
 __global__ void __launch_bounds__(GJB * GJB) k_gjb_inv(int n, int k0, int b, const z64 *__restrict__ Rw,
                                                  z64 *__restrict__ D, int *__restrict__ flag,
                                                  z64 *__restrict__ A) {
-    __shared__ z64 a[GJB][GJB + 1];
-    __shared__ z64 fcol[GJB];
+    __shared__ z64 buf[2][GJB][GJB + 1];
+    __shared__ z64 nrow[GJB];   // row k of the next copy: pivot row times 1/pivot, 1/pivot at k
+    __shared__ z64 s_pinv;
     __shared__ int perm[GJB];
     __shared__ int s_p;
     __shared__ double s_amax;
-    __shared__ z64 s_pinv;
-    const int t = blockIdx.x;
+    const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
     Rw += (int64_t)t * b * n;
     D += (int64_t)t * GJB * GJB;
     A += (int64_t)t * n * n;
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) a[idx / b][idx % b] = Rw[(idx / b) * (int64_t)n + k0 + idx % b];
-    for (int idx = threadIdx.x; idx < n * b; idx += blockDim.x) A[(int64_t)(idx / b) * n + k0 + idx % b] = z64(0.0, 0.0);
+    const int r = tid / GJB, c = tid % GJB;
+    buf[0][r][c] = (r < b && c < b) ? Rw[(int64_t)r * n + k0 + c] : z64(0.0, 0.0);
+    for (int idx = tid; idx < n * b; idx += blockDim.x) A[(int64_t)(idx / b) * n + k0 + idx % b] = z64(0.0, 0.0);
     __syncthreads();
-    if (threadIdx.x < 32) {
+    if (tid < 32) {
         double m = 0.0;
-        for (int idx = threadIdx.x; idx < b * b; idx += 32) m = fmax(m, norm2(a[idx / b][idx % b]));
+        for (int idx = lane; idx < b * b; idx += 32) m = fmax(m, norm2(buf[0][idx / b][idx % b]));
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) s_amax = m;
+        if (lane == 0) s_amax = m;
     }
     __syncthreads();
+    int cur = 0;
     for (int k = 0; k < b; ++k) {
-        if (threadIdx.x < 32) {   // pivot: largest |a[r][k]|^2, r >= k (first on ties); the bit
-                                  // patterns of non-negative doubles order as integers
+        const z64(*X)[GJB + 1] = buf[cur];
+        z64(*Y)[GJB + 1] = buf[cur ^ 1];
+        if (tid < 32) {   // pivot: largest |X[r][k]|^2, r >= k (first on ties); bit patterns of
+                          // non-negative doubles order as integers
             long long bv = -1;
             int bp = k;
-            for (int r = k + threadIdx.x; r < b; r += 32) {
-                const long long v = __double_as_longlong(norm2(a[r][k]));
-                if (v > bv) {
-                    bv = v;
-                    bp = r;
-                }
+            if (lane >= k && lane < b) {
+                bv = __double_as_longlong(norm2(X[lane][k]));
+                bp = lane;
             }
             for (int o = 16; o > 0; o >>= 1) {
                 const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
@@ -857,56 +872,60 @@ __global__ void __launch_bounds__(GJB * GJB) k_gjb_inv(int n, int k0, int b, con
                     bp = op;
                 }
             }
-            if (threadIdx.x == 0) {
+            z64 pinv(0.0, 0.0);
+            if (lane == 0) {
+                const double d = __longlong_as_double(bv);
+                if (!(d > 1e-26 * s_amax)) atomicExch(flag, 1);   // |pivot| < 1e-13 max|entry|
+                const z64 piv = X[bp][k];
+                const double id = d > 0.0 ? __drcp_rn(d) : 0.0;
+                pinv = z64(piv.re * id, -piv.im * id);
                 s_p = bp;
+                s_pinv = pinv;
                 perm[k] = bp;
-                if (!(__longlong_as_double(bv) > 1e-26 * s_amax)) atomicExch(flag, 1);   // |pivot| < 1e-13 max|entry|
             }
+            pinv.re = __shfl_sync(0xffffffffu, pinv.re, 0);
+            pinv.im = __shfl_sync(0xffffffffu, pinv.im, 0);
+            if (lane < b) nrow[lane] = lane == k ? pinv : X[bp][lane] * pinv;
         }
         __syncthreads();
         const int p = s_p;
-        if (p != k)
-            for (int c = threadIdx.x; c < b; c += blockDim.x) {
-                const z64 u = a[k][c];
-                a[k][c] = a[p][c];
-                a[p][c] = u;
+        if (r < b && c < b) {
+            if (r == k) {
+                Y[k][c] = nrow[c];
+            } else {
+                const int src = r == p ? k : r;   // rows k and p exchanged
+                const z64 f = X[src][k];
+                z64 v;
+                if (c == k) {
+                    v = -(f * s_pinv);
+                } else {
+                    v = X[src][c];
+                    const z64 w = nrow[c];
+                    v.re = fma(-f.re, w.re, v.re);
+                    v.re = fma(f.im, w.im, v.re);
+                    v.im = fma(-f.re, w.im, v.im);
+                    v.im = fma(-f.im, w.re, v.im);
+                }
+                Y[r][c] = v;
             }
-        __syncthreads();
-        if (threadIdx.x == 0) {   // one reciprocal per pivot (correctly rounded)
-            const z64 piv = a[k][k];
-            const double d = norm2(piv);
-            const double id = d > 0.0 ? __drcp_rn(d) : 0.0;
-            s_pinv = z64(piv.re * id, -piv.im * id);
         }
         __syncthreads();
-        const z64 pinv = s_pinv;
-        // row k scaled (a[k][k] becomes 1/piv), then every other row eliminated
-        for (int c = threadIdx.x; c < b; c += blockDim.x) a[k][c] = (c == k) ? pinv : a[k][c] * pinv;
-        for (int r = threadIdx.x; r < b; r += blockDim.x) fcol[r] = a[r][k];   // multipliers, read before any write
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-            const int r = idx / b, c = idx % b;
-            if (r == k) continue;
-            const z64 f = fcol[r];
-            a[r][c] = (c == k) ? -(f * a[k][k]) : a[r][c] - f * a[k][c];
+        cur ^= 1;
+    }
+    // undo the row exchanges as column exchanges, in reverse order: column j of
+    // the inverse is column idx[j] of the eliminated block
+    __shared__ int colsrc[GJB];
+    if (tid == 0) {
+        for (int j = 0; j < GJB; ++j) colsrc[j] = j;
+        for (int k = b - 1; k >= 0; --k) {
+            const int q = perm[k];
+            const int u = colsrc[k];
+            colsrc[k] = colsrc[q];
+            colsrc[q] = u;
         }
-        __syncthreads();
     }
-    // undo the row exchanges as column exchanges, in reverse order
-    for (int k = b - 1; k >= 0; --k) {
-        const int p = perm[k];
-        if (p != k)
-            for (int r = threadIdx.x; r < b; r += blockDim.x) {
-                const z64 u = a[r][k];
-                a[r][k] = a[r][p];
-                a[r][p] = u;
-            }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < GJB * GJB; idx += blockDim.x) {
-        const int r = idx / GJB, c = idx % GJB;
-        D[idx] = (r < b && c < b) ? a[r][c] : z64(0.0, 0.0);
-    }
+    __syncthreads();
+    D[r * GJB + c] = (r < b && c < b) ? buf[cur][r][colsrc[c]] : z64(0.0, 0.0);
 }
 
 // row block k of A <- Rwp (b x n); then A_kk <- D
@@ -975,6 +994,7 @@ bool gj_blocked(int64_t n, int nbatch, const z64 *Aorig, z64 *inv, cudaStream_t 
     flag.alloc(1);
     CBFM_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
     const unsigned nbk = (unsigned)std::min<int64_t>((n * GJB + 255) / 256, 1024);
+    GemmSite site_("site:gauss_jordan");
     for (int64_t k0 = 0; k0 < n; k0 += GJB) {
         const int b = (int)std::min<int64_t>(GJB, n - k0);
         k_gjb_panels<<<dim3(nbk, nbatch), 256, 0, st>>>((int)n, (int)k0, b, inv, C.p, Rw.p);
@@ -1100,6 +1120,8 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
         }
     }
 }
+
+thread_local const char *g_gemm_site = nullptr;
 
 template void gemm_grouped<double>(const std::vector<GemmDesc> &, int, int, const z64 *, const z64 *, z64 *, bool,
                                    cudaStream_t, double);

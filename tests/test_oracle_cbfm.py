@@ -122,6 +122,23 @@ def test_cmp_on_divided_sphere():
     assert np.abs(G - np.diag(np.diag(G))).max() > 1e-3 * np.abs(np.diag(G)).max()   # not diagonal
 
 
+def test_cbf_gram_halves_are_negative_adjoints():
+    # Gf = <n x f_i, f_j> is real and antisymmetric, so (C^M)^H Gf C^J = -((C^J)^H Gf C^M)^H
+    # (Eq. (CBF_Gram_matrix)); the GPU path inverts one half of G^CBF and takes the other's
+    # inverse as minus the adjoint.  Checked on an octant-divided sphere with coupled cells.
+    g = W.icosphere(2, 0.3)
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = OM.cells_octant(m)
+    cb = cbfm.primary_cbfs(m, cell, 8, 4.0, W.plane_wave_set(W.fibonacci_dirs(12)), 1e-3)
+    G = cbfm.cbf_gram(m, cb)
+    nh = G.shape[0] // 2
+    g1, g2 = G[:nh, :nh], G[nh:, nh:]
+    assert np.abs(g1).max() > 0 and np.abs(G[:nh, nh:]).max() == 0.0 and np.abs(G[nh:, :nh]).max() == 0.0
+    assert np.abs(g1 - np.diag(np.diag(g1))).max() > 1e-3 * np.abs(g1).max()   # cells coupled
+    assert np.abs(g2 + g1.conj().T).max() < 1e-13 * np.abs(g1).max()
+    assert np.abs(np.linalg.inv(g2) + np.linalg.inv(g1).conj().T).max() < 1e-9 * np.abs(np.linalg.inv(g1)).max()
+
+
 def test_gmres_against_direct_solve():
     rng = np.random.default_rng(3)
     n = 60
