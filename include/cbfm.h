@@ -55,6 +55,7 @@ extern "C" {
 typedef struct cbfm_mesh_s *cbfm_mesh_t;
 typedef struct cbfm_cbf_s *cbfm_cbf_t;
 typedef struct cbfm_red_s *cbfm_red_t;
+typedef struct cbfm_session_s *cbfm_session_t;
 
 typedef enum {
     CBFM_OK = 0,
@@ -63,7 +64,8 @@ typedef enum {
     CBFM_ECUDA = 3,       /* CUDA runtime error */
     CBFM_ESINGULAR = 4,   /* zero pivot in an LU / Gauss-Jordan factorisation */
     CBFM_ENOCONV = 5,     /* GMRES reached maxit without meeting tol (results are the last iterate) */
-    CBFM_ETIMEOUT = 6     /* a bounded device wait expired */
+    CBFM_ETIMEOUT = 6,    /* a bounded device wait expired */
+    CBFM_EFULL = 7        /* a solve session has finished or holds 128 right-hand sides */
 } cbfm_status;
 
 typedef enum {
@@ -358,7 +360,43 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
                        int32_t ndir, double *rcs_out, int32_t *iters_out, double *resid_out,
                        void *stream);
 
-/* Release any handle (mesh, cbf or reduced system); NULL is a no-op. */
+/* ---------------------------------------------------------------------
+ * Solve sessions: block GMRES (paper Eqs. (CBFM_outer)/(CBFM_inner), the
+ * right-preconditioned reduced system) on a set of right-hand sides that
+ * may grow while the solve runs -- continuous batching in the serving loop.
+ *
+ * cbfm_session_create -- a session on a CMP-ready (or T-diagonal / plain)
+ *   reduced system with its first 1-128 monostatic excitations exc
+ *   (nrhs x (theta, phi, pol), host, copied); tol, maxit (block iterations),
+ *   restart (basis dimensions) and precond as for cbfm_solve.  The session
+ *   is owned by the caller until cbfm_free.
+ * cbfm_session_join -- queue nrhs more excitations (host, copied); any
+ *   thread, also while cbfm_session_run runs.  *first_slot (nullable)
+ *   receives the slot of the first one; slots number the right-hand sides
+ *   in the order they were accepted.  CBFM_EFULL once the session has
+ *   finished or would exceed 128 right-hand sides.
+ * cbfm_session_run -- runs the solve on the caller's stream: queued
+ *   right-hand sides are taken at every block-iteration boundary (the
+ *   running cycle restarts there with them added: their starting guess is
+ *   zero, the others keep their iterate and the converged ones stay out of
+ *   the new block); when every right-hand side has converged and nothing is
+ *   queued the session closes.  Then currents and monostatic RCS for every
+ *   slot.  Once per session; CBFM_ENOCONV as cbfm_solve.  Joins still
+ *   queued when maxit ends the solve get no result (the slot count below
+ *   tells).
+ * cbfm_session_results -- after run: *nslots (nullable) = slots solved;
+ *   with capacity >= that, rcs_out (nslots x 2, the |E_theta|^2 and
+ *   |E_phi|^2 parts of the monostatic RCS as cbfm_solve), iters_out
+ *   (block iterations since the slot joined) and resid_out (nullable each).
+ */
+cbfm_status cbfm_session_create(cbfm_red_t red, const double *exc, int32_t nrhs, double tol, int32_t maxit,
+                                int32_t restart, int32_t precond, cbfm_session_t *out);
+cbfm_status cbfm_session_join(cbfm_session_t sess, const double *exc, int32_t nrhs, int32_t *first_slot);
+cbfm_status cbfm_session_run(cbfm_session_t sess, void *stream);
+cbfm_status cbfm_session_results(cbfm_session_t sess, int32_t capacity, double *rcs_out, int32_t *iters_out,
+                                 double *resid_out, int32_t *nslots);
+
+/* Release any handle (mesh, cbf, reduced system or session); NULL is a no-op. */
 void cbfm_free(void *handle);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -28,7 +28,7 @@ MIXED_UNFUSED = 3   # mixed precision, RWG matrices assembled in memory, then pr
 MIXED_FUSED = 4     # mixed precision, assembly fused with the tensor-core projection (no RWG matrix in memory)
 
 STATUS = {0: "CBFM_OK", 1: "CBFM_EINVAL", 2: "CBFM_ENOMEM", 3: "CBFM_ECUDA", 4: "CBFM_ESINGULAR",
-          5: "CBFM_ENOCONV", 6: "CBFM_ETIMEOUT"}
+          5: "CBFM_ENOCONV", 6: "CBFM_ETIMEOUT", 7: "CBFM_EFULL"}
 
 ETA0 = 376.730313668
 
@@ -76,6 +76,10 @@ def lib():
             "cbfm_gram_export": [_vp, _vp, _vp],
             "cbfm_gram_inverse": [_vp, _i64, _i32, _vp, _vp],
             "cbfm_solve": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp],
+            "cbfm_session_create": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _vp],
+            "cbfm_session_join": [_vp, _vp, _i32, _vp],
+            "cbfm_session_run": [_vp, _vp],
+            "cbfm_session_results": [_vp, _i32, _vp, _vp, _vp, _vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -101,7 +105,8 @@ def exported_symbols():
     """Names of the C entry points declared in include/cbfm.h."""
     return ["cbfm_mesh", "cbfm_mesh_edges", "cbfm_mesh_info", "cbfm_mesh_cells", "cbfm_build_cbfs", "cbfm_cbf_import",
             "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_assemble_mom", "cbfm_tdiag_setup", "cbfm_build_ipcbfs", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_cmp_setup_inexact", "cbfm_gram_export",
-            "cbfm_gram_inverse", "cbfm_solve", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
+            "cbfm_gram_inverse", "cbfm_solve", "cbfm_session_create", "cbfm_session_join", "cbfm_session_run",
+            "cbfm_session_results", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
             "cbfm_profile_read"]
 
 
@@ -449,3 +454,48 @@ def solve(r: Reduced, exc, tol: float = 1e-6, maxit: int = 2000, restart: int = 
     if st != 0 and not (st == 5 and allow_noconv):
         _check(st)
     return SolveResult(j, rcs, iters, resid, st)
+
+
+class Session(_Handle):
+    """cbfm_session_*: a block solve that right-hand sides may join while it runs."""
+
+    def __init__(self, h, red: Reduced):
+        super().__init__(h)
+        self.red = red
+
+    def join(self, exc) -> int:
+        """Queue excitations (n x 3); returns the slot of the first.  CbfmError with
+        status 7 (CBFM_EFULL) once the session has finished or is full."""
+        e, ke = _ptr(exc, np.float64)
+        first = ctypes.c_int32(0)
+        _check(lib().cbfm_session_join(self.handle, e, int(ke.shape[0]), ctypes.byref(first)))
+        return int(first.value)
+
+    def run(self, stream=None, allow_noconv: bool = False) -> int:
+        st = lib().cbfm_session_run(self.handle, _stream(stream))
+        if st != 0 and not (st == 5 and allow_noconv):
+            _check(st)
+        return st
+
+    def results(self):
+        """(rcs (nslots, 2), iters (nslots,), resid (nslots,)) in slot order."""
+        ns = ctypes.c_int32(0)
+        _check(lib().cbfm_session_results(self.handle, 0, None, None, None, ctypes.byref(ns)))
+        k = int(ns.value)
+        rcs = np.zeros((k, 2), np.float64)
+        iters = np.zeros(k, np.int32)
+        resid = np.zeros(k, np.float64)
+        _check(lib().cbfm_session_results(self.handle, k, ctypes.c_void_p(rcs.ctypes.data),
+                                          ctypes.c_void_p(iters.ctypes.data), ctypes.c_void_p(resid.ctypes.data),
+                                          ctypes.byref(ns)))
+        return rcs, iters, resid
+
+
+def session(r: Reduced, exc, tol: float = 1e-6, maxit: int = 2000, restart: int = 1000,
+            precond: int = PC_CMP) -> Session:
+    """cbfm_session_create on reduced system r with the first excitations exc (n x 3)."""
+    e, ke = _ptr(exc, np.float64)
+    h = ctypes.c_void_p()
+    _check(lib().cbfm_session_create(r.handle, e, int(ke.shape[0]), float(tol), int(maxit), int(restart),
+                                     int(precond), ctypes.byref(h)))
+    return Session(h, r)

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI (include/cbfm.h): handles, argument checks, error
 // reporting and the orchestration of the kernels of each step.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <memory>
@@ -921,6 +922,134 @@ void gram_cbf(Red &r, cudaStream_t st) {
     XM.release();
 }
 
+// Rows b (nrhs x n) of the reduced right-hand sides for plane-wave excitations
+// d_exc (device, nrhs x (theta, phi, pol)): v = the tested incident fields
+// (paper Eq. (V)), b = (C^JM)^H v (b = v for the RWG system).  FP32 products
+// for the mixed-precision systems.
+void reduced_rhs_rows(Red &r, const double *d_exc, int nrhs, z64 *b, cudaStream_t st) {
+    Mesh &m = *r.mesh;
+    Cbf *cp = r.cbf;
+    const int64_t ne = m.h.ne, nh = cp ? cp->nhalf : ne, n = r.n;
+    const int nc = m.h.ncell;
+    DevBuf<z64> vE, vH, bt;
+    vE.alloc((size_t)ne * nrhs);
+    vH.alloc((size_t)ne * nrhs);
+    launch_rhs(m, d_exc, nrhs, vE.p, vH.p, st, r.prec != CBFM_FP64);
+    // b = (C^JM)^H v  -> (n x nrhs), then rows per rhs
+    bt.alloc((size_t)n * nrhs);
+    const bool f32 = r.prec != CBFM_FP64;   // mixed precision: right-hand side and recovery in FP32
+    if (!cp) {   // b = v = [v^E; v^H]
+        CBFM_CUDA(cudaMemcpyAsync(bt.p, vE.p, sizeof(z64) * ne * nrhs, cudaMemcpyDeviceToDevice, st));
+        CBFM_CUDA(cudaMemcpyAsync(bt.p + ne * nrhs, vH.p, sizeof(z64) * ne * nrhs, cudaMemcpyDeviceToDevice, st));
+    } else {
+        const Cbf &c = *cp;
+        std::vector<GemmDesc> gE, gH;
+        for (int k = 0; k < nc; ++k) {
+            int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
+            gE.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, c.coff[k] * nrhs, nrhs});
+            gH.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, (nh + c.coff[k]) * nrhs, nrhs});
+        }
+        if (f32) {
+            DevBuf<c32> e32, h32, b32;
+            e32.alloc((size_t)ne * nrhs);
+            h32.alloc((size_t)ne * nrhs);
+            b32.alloc((size_t)n * nrhs);
+            launch_z64_to_c32(vE.p, e32.p, ne * nrhs, st);
+            launch_z64_to_c32(vH.p, h32.p, ne * nrhs, st);
+            gemm_grouped<float>(gE, 2, 0, c.CJ32.p, e32.p, b32.p, false, st);
+            gemm_grouped<float>(gH, 2, 0, c.CM32.p, h32.p, b32.p, false, st);
+            launch_c32_to_z64(b32.p, bt.p, n * nrhs, st);
+        } else {
+            gemm_grouped<double>(gE, 2, 0, c.CJ.p, vE.p, bt.p, false, st);
+            gemm_grouped<double>(gH, 2, 0, c.CM.p, vH.p, bt.p, false, st);
+        }
+    }
+    {
+        ProfScope ps_("k_transpose", st);
+        k_transpose<<<nblk(n * nrhs), 256, 0, st>>>(n, nrhs, bt.p, b);
+        launched("k_transpose");
+    }
+}
+
+// Currents (internal edge order, (2 ne) x nrhs) j = C^MJ x from the reduced
+// solutions x (nrhs x n rows), paper Eq. (trans_current); j = x for the RWG system.
+void recover_currents(Red &r, const z64 *x, int nrhs, z64 *jint, cudaStream_t st) {
+    Mesh &m = *r.mesh;
+    Cbf *cp = r.cbf;
+    const int64_t ne = m.h.ne, nh = cp ? cp->nhalf : ne, n = r.n;
+    const int nc = m.h.ncell;
+    const bool f32 = r.prec != CBFM_FP64;
+    if (!cp) {   // j = x
+        ProfScope ps_("k_transpose", st);
+        k_transpose<<<nblk(n * nrhs), 256, 0, st>>>(nrhs, n, x, jint);
+        launched("k_transpose");
+        return;
+    }
+    const Cbf &c = *cp;
+    std::vector<GemmDesc> jM, jJ;
+    for (int k = 0; k < nc; ++k) {
+        int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
+        jM.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, c.coff[k], n, off * nrhs, nrhs});
+        jJ.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, nh + c.coff[k], n, (ne + off) * nrhs, nrhs});
+    }
+    if (f32) {
+        DevBuf<c32> x32, j32;
+        x32.alloc((size_t)nrhs * n);
+        j32.alloc((size_t)2 * ne * nrhs);
+        launch_z64_to_c32(x, x32.p, nrhs * n, st);
+        gemm_grouped<float>(jM, 0, 1, c.CM32.p, x32.p, j32.p, false, st);
+        gemm_grouped<float>(jJ, 0, 1, c.CJ32.p, x32.p, j32.p, false, st);
+        launch_c32_to_z64(j32.p, jint, 2 * ne * nrhs, st);
+    } else {
+        gemm_grouped<double>(jM, 0, 1, c.CM.p, x, jint, false, st);
+        gemm_grouped<double>(jJ, 0, 1, c.CJ.p, x, jint, false, st);
+    }
+}
+
+constexpr uint32_t H_SESSION = 0x53455353u;
+
+// A block solve that right-hand sides may join while it runs (the serving
+// loop's continuous batching).  Joins are queued under the mutex by any
+// thread and taken by the solver at block-iteration boundaries.
+struct Session : HandleBase, BgmresJoin {
+    Red *r = nullptr;
+    double tol = 1e-6;
+    int maxit = 0, restart = 0, precond = CBFM_PC_CMP;
+    std::mutex mu;
+    std::vector<double> queued;        // excitations waiting to join, 3 per right-hand side
+    std::atomic<int> nqueued{0};
+    int accepted = 0;                  // right-hand sides accepted so far (slots)
+    bool closed = false, ran = false;
+    std::vector<double> exc_all;       // excitations in slot order (taken by the solver)
+    std::vector<double> rcs;           // monostatic RCS parts, 2 per slot
+    std::vector<int> iters;
+    std::vector<double> resid;
+    bool pending() override { return nqueued.load(std::memory_order_acquire) > 0; }
+    int take(cudaStream_t st, DevBuf<z64> &rows) override {
+        std::vector<double> exc;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            exc.swap(queued);
+            nqueued.store(0, std::memory_order_release);
+        }
+        const int k = (int)(exc.size() / 3);
+        if (k == 0) return 0;
+        DevBuf<double> dexc;
+        dexc.alloc(exc.size());
+        CBFM_CUDA(cudaMemcpyAsync(dexc.p, exc.data(), sizeof(double) * exc.size(), cudaMemcpyHostToDevice, st));
+        rows.alloc((size_t)k * r->n);
+        reduced_rhs_rows(*r, dexc.p, k, rows.p, st);
+        exc_all.insert(exc_all.end(), exc.begin(), exc.end());
+        return k;
+    }
+    bool close_if_idle() override {
+        std::lock_guard<std::mutex> lk(mu);
+        if (nqueued.load() > 0) return false;
+        closed = true;
+        return true;
+    }
+};
+
 }  // namespace
 
 extern "C" {
@@ -1287,51 +1416,13 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
         CBFM_REQUIRE(mono || ndir == 0 || obs != nullptr, "obs is NULL");
         cudaStream_t st = (cudaStream_t)stream;
         Mesh &m = *r->mesh;
-        Cbf *cp = r->cbf;   // NULL: conventional MoM, the basis is the RWG functions (C^M = C^J = I)
-        const int64_t ne = m.h.ne, nh = cp ? cp->nhalf : ne, n = r->n;
-        const int nc = m.h.ncell;
+        const int64_t ne = m.h.ne, n = r->n;
         DevBuf<double> dexc, dobs, drcs;
         dexc.alloc(3 * (size_t)nrhs);
         copy_in(dexc.p, exc, 3 * sizeof(double) * nrhs, st);
-        DevBuf<z64> vE, vH, bt, b, x, jint;
-        vE.alloc((size_t)ne * nrhs);
-        vH.alloc((size_t)ne * nrhs);
-        launch_rhs(m, dexc.p, nrhs, vE.p, vH.p, st, r->prec != CBFM_FP64);
-        // b = (C^JM)^H v  -> (n x nrhs), then rows per rhs
-        bt.alloc((size_t)n * nrhs);
-        const bool f32 = r->prec != CBFM_FP64;   // mixed precision: right-hand side and recovery in FP32
-        if (!cp) {   // b = v = [v^E; v^H]
-            CBFM_CUDA(cudaMemcpyAsync(bt.p, vE.p, sizeof(z64) * ne * nrhs, cudaMemcpyDeviceToDevice, st));
-            CBFM_CUDA(cudaMemcpyAsync(bt.p + ne * nrhs, vH.p, sizeof(z64) * ne * nrhs, cudaMemcpyDeviceToDevice, st));
-        } else {
-            const Cbf &c = *cp;
-            std::vector<GemmDesc> gE, gH;
-            for (int k = 0; k < nc; ++k) {
-                int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
-                gE.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, c.coff[k] * nrhs, nrhs});
-                gH.push_back(GemmDesc{L, nrhs, N, c.boff[k], L, off * nrhs, nrhs, (nh + c.coff[k]) * nrhs, nrhs});
-            }
-            if (f32) {
-                DevBuf<c32> e32, h32, b32;
-                e32.alloc((size_t)ne * nrhs);
-                h32.alloc((size_t)ne * nrhs);
-                b32.alloc((size_t)n * nrhs);
-                launch_z64_to_c32(vE.p, e32.p, ne * nrhs, st);
-                launch_z64_to_c32(vH.p, h32.p, ne * nrhs, st);
-                gemm_grouped<float>(gE, 2, 0, c.CJ32.p, e32.p, b32.p, false, st);
-                gemm_grouped<float>(gH, 2, 0, c.CM32.p, h32.p, b32.p, false, st);
-                launch_c32_to_z64(b32.p, bt.p, n * nrhs, st);
-            } else {
-                gemm_grouped<double>(gE, 2, 0, c.CJ.p, vE.p, bt.p, false, st);
-                gemm_grouped<double>(gH, 2, 0, c.CM.p, vH.p, bt.p, false, st);
-            }
-        }
+        DevBuf<z64> b, x, jint;
         b.alloc((size_t)nrhs * n);
-        {
-            ProfScope ps_("k_transpose", st);
-            k_transpose<<<nblk(n * nrhs), 256, 0, st>>>(n, nrhs, bt.p, b.p);
-            launched("k_transpose");
-        }
+        reduced_rhs_rows(*r, dexc.p, nrhs, b.p, st);
         CBFM_REQUIRE(solver == 0 || solver == 1, "solver must be 0 (per right-hand side) or 1 (block)");
         x.alloc((size_t)nrhs * n);
         GmresOut go;
@@ -1348,31 +1439,7 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
         }
         // j = C^MJ x  (internal order, (2 ne) x nrhs)
         jint.alloc((size_t)2 * ne * nrhs);
-        if (!cp) {   // j = x
-            ProfScope ps_("k_transpose", st);
-            k_transpose<<<nblk(n * nrhs), 256, 0, st>>>(nrhs, n, x.p, jint.p);
-            launched("k_transpose");
-        } else {
-            const Cbf &c = *cp;
-            std::vector<GemmDesc> jM, jJ;
-            for (int k = 0; k < nc; ++k) {
-                int64_t off = m.h.cell_off[k], N = m.h.cell_off[k + 1] - off, L = c.L[k];
-                jM.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, c.coff[k], n, off * nrhs, nrhs});
-                jJ.push_back(GemmDesc{N, nrhs, L, c.boff[k], L, nh + c.coff[k], n, (ne + off) * nrhs, nrhs});
-            }
-            if (f32) {
-                DevBuf<c32> x32, j32;
-                x32.alloc((size_t)nrhs * n);
-                j32.alloc((size_t)2 * ne * nrhs);
-                launch_z64_to_c32(x.p, x32.p, nrhs * n, st);
-                gemm_grouped<float>(jM, 0, 1, c.CM32.p, x32.p, j32.p, false, st);
-                gemm_grouped<float>(jJ, 0, 1, c.CJ32.p, x32.p, j32.p, false, st);
-                launch_c32_to_z64(j32.p, jint.p, 2 * ne * nrhs, st);
-            } else {
-                gemm_grouped<double>(jM, 0, 1, c.CM.p, x.p, jint.p, false, st);
-                gemm_grouped<double>(jJ, 0, 1, c.CJ.p, x.p, jint.p, false, st);
-            }
-        }
+        recover_currents(*r, x.p, nrhs, jint.p, st);
         if (rcs_out && (mono || ndir > 0)) {
             int nd = mono ? 1 : ndir;
             if (!mono) {
@@ -1410,6 +1477,116 @@ cbfm_status cbfm_solve(cbfm_red_t red, const double *exc, int32_t nrhs, double t
     return st_;
 }
 
+cbfm_status cbfm_session_create(cbfm_red_t red, const double *exc, int32_t nrhs, double tol, int32_t maxit,
+                                int32_t restart, int32_t precond, cbfm_session_t *out) {
+    return guarded([&] {
+        Red *r = (Red *)red;
+        check_device(r, H_RED, "reduced system");
+        CBFM_REQUIRE(out != nullptr, "out is NULL");
+        CBFM_REQUIRE(exc && nrhs >= 1 && nrhs <= 128, "a session starts with 1 to 128 excitations");
+        CBFM_REQUIRE(tol > 0.0 && maxit >= 1 && restart >= 1, "tol, maxit and restart must be positive");
+        CBFM_REQUIRE(precond == CBFM_PC_NONE || precond == CBFM_PC_CMP || precond == CBFM_PC_TDIAG,
+                     "precond must be CBFM_PC_NONE, CBFM_PC_CMP or CBFM_PC_TDIAG");
+        CBFM_REQUIRE(precond != CBFM_PC_CMP || r->cmp_ready, "CBFM_PC_CMP requires cbfm_cmp_setup");
+        CBFM_REQUIRE(precond != CBFM_PC_TDIAG || r->tdiag_ready, "CBFM_PC_TDIAG requires cbfm_tdiag_setup");
+        std::unique_ptr<Session> s(new Session());
+        s->kind = H_SESSION;
+        CBFM_CUDA(cudaGetDevice(&s->device));
+        s->r = r;
+        s->tol = tol;
+        s->maxit = maxit;
+        s->restart = restart;
+        s->precond = precond;
+        s->queued.assign(exc, exc + 3 * (size_t)nrhs);
+        s->nqueued.store(nrhs);
+        s->accepted = nrhs;
+        *out = (cbfm_session_t)s.release();
+    });
+}
+
+cbfm_status cbfm_session_join(cbfm_session_t sess, const double *exc, int32_t nrhs, int32_t *first_slot) {
+    return guarded([&] {
+        Session *s = (Session *)sess;
+        CBFM_REQUIRE(s != nullptr && s->kind == H_SESSION, "bad session handle");
+        CBFM_REQUIRE(exc && nrhs >= 1, "need at least one excitation");
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->closed || s->accepted + nrhs > 128)
+            throw Fail{CBFM_EFULL, s->closed ? "the session has finished" : "the session holds 128 right-hand sides"};
+        if (first_slot) *first_slot = s->accepted;
+        s->queued.insert(s->queued.end(), exc, exc + 3 * (size_t)nrhs);
+        s->accepted += nrhs;
+        s->nqueued.store((int)(s->queued.size() / 3), std::memory_order_release);
+    });
+}
+
+cbfm_status cbfm_session_run(cbfm_session_t sess, void *stream) {
+    cbfm_status conv = CBFM_OK;
+    cbfm_status st_ = guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);
+        Session *s = (Session *)sess;
+        CBFM_REQUIRE(s != nullptr && s->kind == H_SESSION, "bad session handle");
+        check_device(s->r, H_RED, "reduced system");
+        CBFM_REQUIRE(!s->ran, "a session runs once");
+        s->ran = true;
+        cudaStream_t st = (cudaStream_t)stream;
+        Red &r = *s->r;
+        const int64_t ne = r.mesh->h.ne, n = r.n;
+        DevBuf<z64> b0, xall;
+        const int k0 = s->take(st, b0);
+        GmresOut go = bgmres_solve(r, b0.p, k0, s->tol, s->maxit, s->restart, s->precond, nullptr, st, s, &xall);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->closed = true;   // joins left waiting (the iteration limit came first) have no result
+        }
+        const int ns = (int)(s->exc_all.size() / 3);
+        CBFM_REQUIRE(ns == (int)go.iters.size(), "session bookkeeping");
+        DevBuf<z64> jint;
+        DevBuf<double> dexc, drcs;
+        jint.alloc((size_t)2 * ne * ns);
+        recover_currents(r, xall.p, ns, jint.p, st);
+        dexc.alloc(s->exc_all.size());
+        CBFM_CUDA(cudaMemcpyAsync(dexc.p, s->exc_all.data(), sizeof(double) * s->exc_all.size(),
+                                  cudaMemcpyHostToDevice, st));
+        drcs.alloc((size_t)ns * 2);
+        launch_farfield(*r.mesh, jint.p, ns, nullptr, 1, true, dexc.p, drcs.p, st, r.prec != CBFM_FP64);
+        s->rcs.resize((size_t)ns * 2);
+        CBFM_CUDA(cudaMemcpyAsync(s->rcs.data(), drcs.p, sizeof(double) * ns * 2, cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        s->iters.resize(ns);
+        s->resid.resize(ns);
+        for (int i = 0; i < ns; ++i) {
+            s->iters[i] = go.iters[i] >= 0 ? go.iters[i] : -go.iters[i] - 1;
+            s->resid[i] = go.resid[i];
+            if (go.iters[i] < 0) conv = CBFM_ENOCONV;
+        }
+    });
+    if (st_ == CBFM_OK && conv != CBFM_OK) {
+        t_err = "GMRES did not converge for at least one right-hand side";
+        return conv;
+    }
+    return st_;
+}
+
+cbfm_status cbfm_session_results(cbfm_session_t sess, int32_t capacity, double *rcs_out, int32_t *iters_out,
+                                 double *resid_out, int32_t *nslots) {
+    return guarded([&] {
+        Session *s = (Session *)sess;
+        CBFM_REQUIRE(s != nullptr && s->kind == H_SESSION, "bad session handle");
+        CBFM_REQUIRE(s->ran, "the session has not run");
+        const int ns = (int)s->iters.size();
+        if (nslots) *nslots = ns;
+        CBFM_REQUIRE(capacity >= ns || (!rcs_out && !iters_out && !resid_out), "output capacity too small");
+        for (int i = 0; i < ns; ++i) {
+            if (rcs_out) {
+                rcs_out[2 * i] = s->rcs[2 * i];
+                rcs_out[2 * i + 1] = s->rcs[2 * i + 1];
+            }
+            if (iters_out) iters_out[i] = s->iters[i];
+            if (resid_out) resid_out[i] = s->resid[i];
+        }
+    });
+}
+
 void cbfm_free(void *handle) {
     if (!handle) return;
     HandleBase *h = (HandleBase *)handle;
@@ -1417,6 +1594,7 @@ void cbfm_free(void *handle) {
         case H_MESH: h->kind = 0; delete (Mesh *)h; break;
         case H_CBF: h->kind = 0; delete (Cbf *)h; break;
         case H_RED: h->kind = 0; delete (Red *)h; break;
+        case H_SESSION: h->kind = 0; delete (Session *)h; break;
         default: break;
     }
 }

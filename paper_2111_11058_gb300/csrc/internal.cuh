@@ -174,8 +174,23 @@ GmresOut gmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, in
                      z64 *d_x, cudaStream_t st);
 // Block GMRES over all right-hand sides at once (k_bgmres.cu); maxit counts block iterations,
 // restart caps the basis dimension; iters report the block iteration of convergence.
+// Right-hand sides joining a running block solve (the serving loop): polled
+// at every block-iteration boundary.
+struct BgmresJoin {
+    virtual ~BgmresJoin() = default;
+    // some right-hand sides wait to join (cheap, any thread)
+    virtual bool pending() = 0;
+    // the waiting right-hand sides as rows of the reduced system (k x n, device), k returned
+    virtual int take(cudaStream_t st, DevBuf<z64> &rows) = 0;
+    // every right-hand side has converged: close to further joins unless some wait (then false)
+    virtual bool close_if_idle() = 0;
+};
+// join == nullptr: the right-hand sides d_b (nrhs x n) are solved into d_x.
+// With join, right-hand sides may join at block-iteration boundaries (the
+// cycle restarts there with them added, y = 0 for the new ones); the
+// solutions of all of them, in joining order, go to *x_all (allocated here).
 GmresOut bgmres_solve(Red &r, const z64 *d_b, int nrhs, double tol, int maxit, int restart, int pc,
-                      z64 *d_x, cudaStream_t st);
+                      z64 *d_x, cudaStream_t st, BgmresJoin *join = nullptr, DevBuf<z64> *x_all = nullptr);
 // pc (cbfm_precond): the operator GMRES iterates with, in the reduced system's precision
 inline const z64 *pc_op64(const Red &r, int pc) {
     return pc == CBFM_PC_CMP ? r.B64.p : pc == CBFM_PC_TDIAG ? r.Bt64.p : r.A64.p;

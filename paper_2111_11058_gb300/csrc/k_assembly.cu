@@ -238,6 +238,18 @@ __device__ inline void green_rems_f(float kre, float kim, float R, c32 &gr, c32 
 // Ks, Ta, Tb and store (t, s) and (s, t).
 constexpr int NEAR_MOM = 15;   // complex moments per (orientation, medium)
 
+// Work of one near pair, counted from the operations of near_pair2 with each
+// square root, logarithm, arctangent, sine/cosine pair and exponential as one:
+// per orientation and test point (14 lanes) the closed-form potentials of the
+// trial triangle (3 edges x 60 + 25) and the trial-point geometry (7 x 10) in
+// FP64, and for each medium the 7 remainder evaluations with their weighted
+// sums (7 x 60, FP32 on the mixed path) plus S0, Sr, Wv and the 15 moments
+// (90, FP64); then the moment reductions (15 complex x 2 media x 3 shuffle
+// steps on 16 lanes) and the 9 entries (2 orientations x 2 media x 60), FP64.
+// FP64 operations of the mixed form; the FP64 form also counts the remainders.
+constexpr double NEAR_FP64_OPS_MIXED = 14 * (205 + 70 + 2 * 90) + 16 * 15 * 2 * 3 * 2 + 9 * 2 * 2 * 60;
+constexpr double NEAR_REM_OPS = 14 * 2 * 7 * 60;
+
 template <typename T>
 __device__ __forceinline__ void near_pair2(int t, int s, int nt, const double *__restrict__ rec, const Media &md,
                                            cx<T> *__restrict__ Zloc, z64 (*sm)[2][2][NEAR_MOM],
@@ -668,6 +680,8 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
         tuning_set(key, cands[bi]);
     }
     prof_add_work("k_far", far_flop, far_bytes);
+    prof_add_work("k_near_blocks", (double)npairs * (NEAR_FP64_OPS_MIXED + (sizeof(T) == 8 ? NEAR_REM_OPS : 0.0)),
+                  (double)npairs * (2 * TRI_REC * sizeof(double) + 27 * sizeof(cx<T>)));
     if (npairs > 0) {
         int occ = 0;
         CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_near_blocks<T>, 128, 0));
@@ -719,6 +733,8 @@ void near_blocks_compact_t(const std::vector<Mesh *> &ms, const std::vector<cx<T
     CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_near_blocks<T>, 128, 0));
     const unsigned grid =
         (unsigned)std::min<int64_t>((int64_t)std::max(1, occ) * sm_count(), ((npairs + 1) / 2 * 32 + 127) / 128);
+    prof_add_work("k_near_blocks", (double)npairs * (NEAR_FP64_OPS_MIXED + (sizeof(T) == 8 ? NEAR_REM_OPS : 0.0)),
+                  (double)npairs * (2 * TRI_REC * sizeof(double) + 27 * sizeof(cx<T>)));
     {
         ProfScope ps_("k_near_blocks", st);
         k_near_blocks<T><<<grid, 128, 0, st>>>(djobs.p, nj, npairs);

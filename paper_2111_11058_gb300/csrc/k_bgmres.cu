@@ -451,6 +451,13 @@ __global__ void k_sub_rows(int64_t count, const z64 *__restrict__ a, const z64 *
     if (i < count) out[i] = a[i] - b[i];
 }
 
+// rows r of a rows x n matrix with mask[r] != 0 set to zero
+__global__ void k_zero_rows_masked(int rows, int64_t n, const int *__restrict__ mask, z64 *__restrict__ X) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)rows * n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (mask[i / n]) X[i] = z64(0.0, 0.0);
+}
+
 // Y += X (complex64 into complex128), n elements
 __global__ void k_add32to64(int64_t n, const c32 *__restrict__ X, z64 *__restrict__ Y) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -814,59 +821,85 @@ void rows_times(int64_t n, const z64 *M64, const c32 *M32, const z64 *in, z64 *o
 }  // namespace
 
 GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, int restart, int pc, z64 *d_x,
-                      cudaStream_t st) {
+                      cudaStream_t st, BgmresJoin *join, DevBuf<z64> *x_all) {
     const int64_t n = rd.n;
     CBFM_REQUIRE(nrhs >= 1 && nrhs <= PCHOL_MAX, "block GMRES handles at most 128 right-hand sides per call");
-    const int p = nrhs;
+    CBFM_REQUIRE(join == nullptr || x_all != nullptr, "block GMRES with joins needs an output buffer");
+    int p = nrhs;
     const double rank_tol = 1e-14;   // pivot threshold of the scaled Gram matrix (unit diagonal)
     const double drop_tol = 1e-12;   // rows below this fraction of the reference norm are exhausted
-    // basis capacity (dimensions), at least one block beyond the first
-    const int64_t dcap = std::max<int64_t>(2 * p, std::min<int64_t>((int64_t)std::max(restart, 2 * p), n + p));
-    const int64_t dcap2 = dcap + p;
+    // Buffers whose size follows the number of right-hand sides p are set up by
+    // setup() (again when right-hand sides join); the Cholesky factors of ctx
+    // are sized for the largest block width.
+    int64_t dcap = 0, dcap2 = 0;   // basis capacity (dimensions), at least one block beyond the first
     Ctx c;
     c.st = st;
-    c.M.alloc((size_t)p * p);
-    c.R.alloc((size_t)p * p);
-    c.Rinv.alloc((size_t)p * p);
-    c.X.alloc((size_t)p * p);
-    c.Rf.alloc((size_t)p * p);
-    c.T1.alloc((size_t)p * n);
-    c.perm.alloc(p);
+    c.M.alloc((size_t)PCHOL_MAX * PCHOL_MAX);
+    c.R.alloc((size_t)PCHOL_MAX * PCHOL_MAX);
+    c.Rinv.alloc((size_t)PCHOL_MAX * PCHOL_MAX);
+    c.X.alloc((size_t)PCHOL_MAX * PCHOL_MAX);
+    c.Rf.alloc((size_t)PCHOL_MAX * PCHOL_MAX);
+    c.perm.alloc(PCHOL_MAX);
     c.rank.alloc(1);
     c.err.alloc(1);
     c.status.alloc(1);
     c.Dinv.alloc((size_t)CH_NPAN * CH_B * CH_B);
     CBFM_CUDA(cudaMemsetAsync(c.err.p, 0, sizeof(int), st));
-    c.rnrm.alloc(p);
-    c.scale.alloc(p);
+    c.rnrm.alloc(PCHOL_MAX);
+    c.scale.alloc(PCHOL_MAX);
     c.dev.alloc(1);
-    DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw;
-    DevBuf<double> bnorm, rnorm, rnorm0;
-    V.alloc((size_t)dcap * n);
-    W.alloc((size_t)p * n);
-    HcT.alloc((size_t)p * dcap);
-    Hn.alloc((size_t)dcap2 * p);
-    Qh.alloc((size_t)dcap2 * dcap);
-    Rh.alloc((size_t)dcap * dcap);
-    Gv.alloc((size_t)dcap * p);
-    E1S.alloc((size_t)dcap2 * p);
-    Rv.alloc((size_t)dcap2 * p);
+    DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw, Bm, Rout;
+    DevBuf<double> bnorm, rnorm, rnorm0, fro_col;
+    DevBuf<int> dmask;
+    DevBuf<c32> s_in, s_out;   // complex64 rows for the mixed-precision products
+    DevBuf<c32> V32, Z32;      // complex64 basis and coefficients for the mixed-precision solution update
+    DevBuf<z64> zin;           // inexact CMP: the inner GMRES's (G^CBF)^{-1} in, the input of the product with A
+    std::vector<double> h_bn, h_rn, h_w1, h_h0, h_h1, h_col;
+    auto setup = [&]() {
+        dcap = std::max<int64_t>(2 * p, std::min<int64_t>((int64_t)std::max(restart, 2 * p), n + p));
+        dcap2 = dcap + p;
+        c.T1.alloc((size_t)p * n);
+        V.alloc((size_t)dcap * n);
+        W.alloc((size_t)p * n);
+        HcT.alloc((size_t)p * dcap);
+        Hn.alloc((size_t)dcap2 * p);
+        Qh.alloc((size_t)dcap2 * dcap);
+        Rh.alloc((size_t)dcap * dcap);
+        Gv.alloc((size_t)dcap * p);
+        E1S.alloc((size_t)dcap2 * p);
+        Rv.alloc((size_t)dcap2 * p);
+        Z.alloc((size_t)dcap * p);
+        tmp.alloc((size_t)std::max<int64_t>(dcap2 * p, p * n));
+        tmp2.alloc((size_t)dcap * p);
+        RinvBlk.alloc((size_t)dcap * p);   // diagonal blocks of Rh^{-1}, stacked (p_j x p_j each, ld p)
+        Rw.alloc((size_t)p * p);
+        Rout.alloc((size_t)p * p);
+        rnorm.alloc(p);
+        rnorm0.alloc(p);
+        fro_col.alloc((size_t)std::max<int64_t>(dcap, p));
+        h_col.assign((size_t)std::max<int64_t>(dcap, p), 0.0);
+        h_rn.assign(p, 0.0);
+        h_w1.assign(p, 0.0);
+        h_h0.assign(p, 0.0);
+        h_h1.assign(p, 0.0);
+        if (rd.prec != CBFM_FP64) {
+            s_in.alloc((size_t)p * n);
+            s_out.alloc((size_t)p * n);
+        }
+        V32.release();
+        Z32.release();
+        zin.release();
+    };
+    setup();
+    // the right-hand sides (rows), their solutions y and norms
+    Bm.alloc((size_t)p * n);
+    CBFM_CUDA(cudaMemcpyAsync(Bm.p, d_b, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
     Y.alloc((size_t)p * n);
-    Z.alloc((size_t)dcap * p);
-    tmp.alloc((size_t)std::max<int64_t>(dcap2 * p, p * n));
-    tmp2.alloc((size_t)dcap * p);
-    RinvBlk.alloc((size_t)dcap * p);   // diagonal blocks of Rh^{-1}, stacked (p_j x p_j each, ld p)
-    Rw.alloc((size_t)p * p);
-    bnorm.alloc(p);
-    rnorm.alloc(p);
-    rnorm0.alloc(p);
     CBFM_CUDA(cudaMemsetAsync(Y.p, 0, sizeof(z64) * p * n, st));
-    k_rownorm<<<p, 256, 0, st>>>(n, d_b, bnorm.p);
+    bnorm.alloc(PCHOL_MAX);
+    k_rownorm<<<p, 256, 0, st>>>(n, Bm.p, bnorm.p);
     launched("k_rownorm");
-    std::vector<double> h_bn(p), h_rn(p), h_w1(p), h_h0(p), h_h1(p);
-    DevBuf<double> fro_col;
-    fro_col.alloc((size_t)std::max<int64_t>(dcap, p));
-    std::vector<double> h_col((size_t)std::max<int64_t>(dcap, p));
+    h_bn.assign(p, 0.0);
     // ||X||_F of a rows x cols block: column norms (one block each), summed on the host (host sync)
     auto fro = [&](int rows, int cols, const z64 *X, int64_t ld) {
         k_colnorm<<<cols, 256, 0, st>>>(rows, cols, X, ld, fro_col.p);
@@ -893,13 +926,6 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     CBFM_CUDA(cudaMemcpyAsync(h_bn.data(), bnorm.p, sizeof(double) * p, cudaMemcpyDeviceToHost, st));
     CBFM_CUDA(cudaStreamSynchronize(st));
 
-    DevBuf<c32> s_in, s_out;   // complex64 rows for the mixed-precision products
-    DevBuf<c32> V32, Z32;      // complex64 basis and coefficients for the mixed-precision solution update
-    if (rd.prec != CBFM_FP64) {
-        s_in.alloc((size_t)p * n);
-        s_out.alloc((size_t)p * n);
-    }
-    DevBuf<z64> zin;           // inexact CMP: the inner GMRES's (G^CBF)^{-1} in, the input of the product with A
     auto applyB = [&](const z64 *in, z64 *out, int rows) {
         if (pc == CBFM_PC_CMP_INEXACT) {
             if (zin.p == nullptr) zin.alloc((size_t)p * n);
@@ -914,20 +940,73 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     GmresOut out;
     out.iters.assign(p, -1);
     out.resid.assign(p, 1.0);
-    std::vector<int> conv_at(p, -1);
+    std::vector<int> conv_at(p, -1), join_at(p, 0);
+    std::vector<char> frozen(p, 0);
     int total_blocks = 0;
     bool all_conv = false, breakdown = false;
-    DevBuf<z64> Rout;
-    Rout.alloc((size_t)p * p);
+    // Right-hand sides waiting to join: taken at a restart they asked for
+    // (`asked`), or when the others are done and the session does not close
+    // because some arrived meanwhile.  True when some were added (their
+    // starting guess zero; the others keep their iterate).
+    auto absorb_joins = [&](bool asked) {
+        if (join == nullptr) return false;
+        bool take = asked;
+        if ((all_conv || breakdown) && !join->close_if_idle()) take = true;
+        if (!take || total_blocks >= maxit) return false;
+        DevBuf<z64> rows;
+        const int k = join->take(st, rows);
+        if (k <= 0) return false;
+        CBFM_REQUIRE(p + k <= PCHOL_MAX, "block GMRES: more than 128 right-hand sides joined");
+        DevBuf<z64> Bn, Yn;
+        Bn.alloc((size_t)(p + k) * n);
+        Yn.alloc((size_t)(p + k) * n);
+        CBFM_CUDA(cudaMemcpyAsync(Bn.p, Bm.p, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
+        CBFM_CUDA(cudaMemcpyAsync(Bn.p + (int64_t)p * n, rows.p, sizeof(z64) * k * n, cudaMemcpyDeviceToDevice, st));
+        CBFM_CUDA(cudaMemcpyAsync(Yn.p, Y.p, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
+        CBFM_CUDA(cudaMemsetAsync(Yn.p + (int64_t)p * n, 0, sizeof(z64) * k * n, st));
+        k_rownorm<<<k, 256, 0, st>>>(n, rows.p, bnorm.p + p);
+        launched("k_rownorm");
+        h_bn.resize(p + k);
+        CBFM_CUDA(cudaMemcpyAsync(h_bn.data() + p, bnorm.p + p, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        Bn.give(Bm);
+        Yn.give(Y);
+        out.iters.resize(p + k, -1);
+        out.resid.resize(p + k, 1.0);
+        conv_at.resize(p + k, -1);
+        join_at.resize(p + k, total_blocks);
+        frozen.resize(p + k, 0);
+        p += k;
+        setup();
+        all_conv = breakdown = false;
+        return true;
+    };
     while (!all_conv && !breakdown && total_blocks < maxit) {
         // residual block R0 = Bm - B Y (rows), orthonormalised: R0[c] = sum_i S[i][c] V1[i]
-        if (total_blocks == 0) {
-            CBFM_CUDA(cudaMemcpyAsync(tmp.p, d_b, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
+        bool fresh = true;   // every right-hand side still at y = 0
+        for (int q = 0; q < p; ++q) fresh &= (join_at[q] == total_blocks);
+        if (fresh) {
+            CBFM_CUDA(cudaMemcpyAsync(tmp.p, Bm.p, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
         } else {
             applyB(Y.p, W.p, p);
-            k_sub_rows<<<nb(p * n), 256, 0, st>>>(p * n, d_b, W.p, tmp.p);
+            k_sub_rows<<<nb(p * n), 256, 0, st>>>(p * n, Bm.p, W.p, tmp.p);
             launched("k_sub_rows");
         }
+        // with joins, a restart keeps the converged right-hand sides out of the new block
+        bool any_frozen = false;
+        for (int q = 0; q < p; ++q) {
+            frozen[q] = join != nullptr && conv_at[q] >= 0;
+            any_frozen |= frozen[q] != 0;
+        }
+        if (any_frozen) {
+            std::vector<int> hm(frozen.begin(), frozen.end());
+            dmask.alloc(p);
+            CBFM_CUDA(cudaMemcpyAsync(dmask.p, hm.data(), sizeof(int) * p, cudaMemcpyHostToDevice, st));
+            k_zero_rows_masked<<<nb(p * n), 256, 0, st>>>(p, n, dmask.p, tmp.p);
+            launched("k_zero_rows_masked");
+            CBFM_CUDA(cudaStreamSynchronize(st));   // hm is released on return from this block
+        }
+        bool joined = false;
         CBFM_CUDA(cudaMemsetAsync(E1S.p, 0, sizeof(z64) * dcap2 * p, st));
         CBFM_CUDA(cudaMemsetAsync(Qh.p, 0, sizeof(z64) * dcap2 * dcap, st));
         CBFM_CUDA(cudaMemsetAsync(Rh.p, 0, sizeof(z64) * dcap * dcap, st));
@@ -935,10 +1014,12 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
         CBFM_CUDA(cudaMemcpyAsync(Rv.p, E1S.p, sizeof(z64) * dcap2 * p, cudaMemcpyDeviceToDevice, st));
         if (p1 == 0) {   // residual block is zero: current iterate is exact
             for (int r = 0; r < p; ++r) {
+                if (frozen[r]) continue;
                 out.resid[r] = 0.0;
                 if (conv_at[r] < 0) conv_at[r] = total_blocks;
             }
             all_conv = true;
+            if (absorb_joins(false)) continue;
             break;
         }
         std::vector<int64_t> dims{0, p1};   // dims[i] = first basis index of block i
@@ -1038,6 +1119,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             ++total_blocks;
             bool all = true;
             for (int q = 0; q < p; ++q) {
+                if (frozen[q]) continue;   // converged before this cycle; y is final
                 const double rel = h_bn[q] > 0 ? h_rn[q] / h_bn[q] : 0.0;
                 out.resid[q] = rel;
                 if (rel <= tol && conv_at[q] < 0) conv_at[q] = total_blocks;
@@ -1047,6 +1129,10 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             all_conv = all;
             if (r == 0) breakdown = !all;   // invariant subspace: least-squares solution is final
             if (all || r == 0 || total_blocks >= maxit) break;
+            if (join != nullptr && join->pending()) {   // right-hand sides wait to join: restart here
+                joined = true;
+                break;
+            }
         }
         // solve Rh Z = Gv (block back substitution) and update Y += Z^T V
         GemmSite site_sol_("site:solution");
@@ -1078,9 +1164,14 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             gemm_grouped<double>({GemmDesc{p, n, dJ, 0, p, 0, n, 0, n}}, 1, 0, Z.p, V.p, Y.p, true, st);
         }
         CBFM_CUDA(cudaStreamSynchronize(st));
+        if (absorb_joins(joined)) continue;
         if (breakdown) break;
     }
     // x = P y
+    if (join != nullptr) {
+        x_all->alloc((size_t)p * n);
+        d_x = x_all->p;
+    }
     if (pc == CBFM_PC_CMP) {   // G^CBF^{-1} is block diagonal (its two halves)
         if (rd.prec != CBFM_FP64) rows_times(n, nullptr, rd.Ginv32.p, Y.p, d_x, p, true, st, s_in.p, s_out.p);
         else rows_times(n, rd.Ginv.p, nullptr, Y.p, d_x, p, true, st, nullptr, nullptr);
@@ -1089,10 +1180,12 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     else if (pc == CBFM_PC_CMP_INEXACT) cmp_inner_apply(rd, Y.p, d_x, p, st);
     else CBFM_CUDA(cudaMemcpyAsync(d_x, Y.p, sizeof(z64) * p * n, cudaMemcpyDeviceToDevice, st));
     CBFM_CUDA(cudaStreamSynchronize(st));
-    for (int q = 0; q < p; ++q) out.iters[q] = conv_at[q] >= 0 ? conv_at[q] : -total_blocks - 1;
+    // iterations counted from the block iteration a right-hand side joined at
+    for (int q = 0; q < p; ++q)
+        out.iters[q] = conv_at[q] >= 0 ? conv_at[q] - join_at[q] : -(total_blocks - join_at[q]) - 1;
     if (breakdown)
         for (int q = 0; q < p; ++q)
-            if (conv_at[q] < 0) out.iters[q] = total_blocks;   // exact within the saturated space
+            if (conv_at[q] < 0) out.iters[q] = total_blocks - join_at[q];   // exact within the saturated space
     return out;
 }
 

@@ -14,8 +14,14 @@ The service
 * batches continuously: whenever a worker slot is free, the oldest waiting
   request that fits is taken together with every other waiting request for
   the same scatterer and frequency (up to 128 right-hand sides, one block
-  GMRES solve), so requests that arrive while others run join the next batch
-  instead of waiting for a queue to drain;
+  GMRES solve); when that is a cache miss and no other worker is free, the
+  cache misses of other waiting keys are built in the same batch (one
+  batched assembly launch for all of them, `cbfm_assemble_reduced_batch`);
+* lets requests join running work: a request whose key has an open group
+  (a batch building or solving it) joins that group -- appended while the
+  entry is built, and handed to the running block GMRES session otherwise,
+  which takes it at its next block-iteration boundary (`cbfm_session_join`);
+  only when no group is open, or the group is full, does it wait;
 * runs batches on several CUDA streams at once (one worker thread per
   stream; the library releases the GIL during its calls and its scratch
   memory is stream-ordered), so the kernels of different batches overlap.
@@ -172,6 +178,21 @@ class GpuBackend:
                            want_j=False, solver=self.C.BLOCK, stream=stream.cuda_stream, allow_noconv=True)
         return res.rcs[:, 0, :].copy(), res.iters.copy()
 
+    def build_many(self, items, stream) -> List[Tuple[Any, int]]:
+        """Several entries at once: meshes and CBFs one by one, the reduced
+        systems in one batched assembly, then the CMP of each."""
+        C, sp = self.C, stream.cuda_stream
+        ms = [C.mesh(np.ascontiguousarray(sc.verts * f), sc.tris, sc.ncell, sc.eps, partition=sc.partition, stream=sp)
+              for sc, f in items]
+        cs = [C.build_cbfs(m, self.gen, self.delta, stream=sp) for m in ms]
+        rs = C.assemble_reduced_batch(ms, cs, self.prec, stream=sp)
+        for r in rs:
+            C.cmp_setup(r, stream=sp)
+        return [((m, c, r), int(r.n)) for m, c, r in zip(ms, cs, rs)]
+
+    def open_session(self, handle, exc: np.ndarray, stream):
+        return _GpuSession(self, handle[2], exc, stream)
+
     def free(self, handle) -> None:
         for h in reversed(handle):
             h.free()
@@ -186,6 +207,30 @@ class GpuBackend:
         return float(e0.elapsed_time(e1))
 
 
+class _GpuSession:
+    """A block GMRES solve (cbfm_session_*) that requests may join while it runs."""
+
+    def __init__(self, be: GpuBackend, red, exc: np.ndarray, stream):
+        self.C, self.stream = be.C, stream
+        self.s = be.C.session(red, exc, tol=be.tol, maxit=be.maxit, restart=be.restart)
+
+    def join(self, exc: np.ndarray) -> Optional[int]:
+        try:
+            return self.s.join(exc)
+        except self.C.CbfmError as e:
+            if e.status == 7:       # CBFM_EFULL: finished or full
+                return None
+            raise
+
+    def run(self) -> Tuple[np.ndarray, np.ndarray]:
+        self.s.run(stream=self.stream.cuda_stream, allow_noconv=True)
+        rcs, iters, _resid = self.s.results()
+        return rcs, iters
+
+    def free(self) -> None:
+        self.s.free()
+
+
 def _plane_waves(ndirs: int) -> np.ndarray:
     """ndirs Fibonacci arrival directions x {theta, phi} polarisation (the CBF generating waves)."""
     i = np.arange(ndirs) + 0.5
@@ -198,16 +243,35 @@ def _plane_waves(ndirs: int) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ server
+class _Group:
+    """The requests of one key in a batch: open to joins until its solve finishes."""
+
+    def __init__(self, key, entry: Entry, hit: bool):
+        self.key = key
+        self.entry = entry
+        self.hit = hit
+        self.members: List[list] = []     # [request, future, first slot or None]
+        self.nrhs = 0
+        self.state = "pending"            # pending (joins append) -> running (joins go to the session) -> done
+        self.session: Any = None
+        self.scratch = 0                  # solve scratch accounted for this group
+        self.joined = 0                   # requests that joined after the batch started
+
+
 class Server:
     """Continuous-batching service.  `submit` returns a Future of `Result`."""
 
-    def __init__(self, backend, hbm_budget: int, n_streams: int = 3, max_batch_rhs: int = MAX_BLOCK_RHS):
+    def __init__(self, backend, hbm_budget: int, n_streams: int = 3, max_batch_rhs: int = MAX_BLOCK_RHS,
+                 max_build_keys: int = 4, joins: bool = True):
         self.be = backend
         self.budget = int(hbm_budget)
         self.max_rhs = int(min(max_batch_rhs, MAX_BLOCK_RHS))
+        self.max_build_keys = max(1, int(max_build_keys))
+        self.joins = joins
         self.lock = threading.Condition()
         self.waiting: List[Tuple[Request, Future]] = []      # arrival order
         self.cache: Dict[Tuple[str, float], Entry] = {}
+        self.open: Dict[Tuple[str, float], _Group] = {}      # groups of running batches that take joins
         self.inflight = 0                                      # scratch bytes of running batches
         self.peak_bytes = 0                                    # most bytes held at once (accounting)
         self.busy = [False] * n_streams
@@ -232,9 +296,17 @@ class Server:
             fut.set_exception(ValueError(f"request with {req.nrhs} right-hand sides exceeds {self.max_rhs}"))
             return fut
         with self.lock:
-            self.waiting.append((req, fut))
-            self._dispatch()
+            if not self._try_join(req, fut):
+                self.waiting.append((req, fut))
+                self._dispatch()
         return fut
+
+    def drain(self, timeout: float = 600.0) -> None:
+        """Wait until nothing waits or runs (every finished batch is in the log)."""
+        end = time.perf_counter() + timeout
+        with self.lock:
+            while (self.waiting or any(self.busy)) and time.perf_counter() < end:
+                self.lock.wait(timeout=0.05)
 
     def close(self) -> None:
         with self.lock:
@@ -252,6 +324,33 @@ class Server:
         return sum(e.bytes for e in self.cache.values())
 
     # ---- scheduling (called with the lock held)
+    def _account(self, delta: int) -> None:
+        self.inflight += delta
+        self.peak_bytes = max(self.peak_bytes, self.resident_bytes() + self.inflight)
+
+    def _try_join(self, req: Request, fut: Future) -> bool:
+        """Add a request to the open group of its key: appended while the group
+        waits for its build, handed to the running solve session otherwise."""
+        g = self.open.get(req.key)
+        if not self.joins or g is None or g.state == "done" or g.nrhs + req.nrhs > self.max_rhs:
+            return False
+        sc = req.scatterer
+        delta = solve_bytes(g.entry.n, g.nrhs + req.nrhs, sc.ne) - solve_bytes(g.entry.n, g.nrhs, sc.ne)
+        if self.resident_bytes() + self.inflight + delta > self.budget:
+            return False
+        if g.state == "running":
+            slot = g.session.join(req.exc)
+            if slot is None:          # the solve has finished or is full
+                return False
+        else:
+            slot = None
+        g.members.append([req, fut, slot])
+        g.nrhs += req.nrhs
+        g.scratch += delta
+        g.joined += 1
+        self._account(delta)
+        return True
+
     def _footprint(self, req: Request, nrhs: int) -> Tuple[int, bool]:
         """(bytes the batch adds, whether its entry is already resident or being built)."""
         sc = req.scatterer
@@ -275,46 +374,87 @@ class Server:
             self.evictions += 1
         return True
 
+    def _same_key(self, i: int, key) -> Tuple[list, int]:
+        """The waiting requests from index i on with this key, up to max_rhs right-hand sides."""
+        group, nrhs = [], 0
+        for r2, f2 in self.waiting[i:]:
+            if r2.key == key and nrhs + r2.nrhs <= self.max_rhs:
+                group.append((r2, f2))
+                nrhs += r2.nrhs
+        return group, nrhs
+
+    def _take(self, reqs: list) -> None:
+        ids = {id(r) for r, _ in reqs}
+        self.waiting = [w for w in self.waiting if id(w[0]) not in ids]
+
+    def _new_group(self, key, reqs: list, nrhs: int, hit: bool, entry: Entry, scratch: int) -> _Group:
+        g = _Group(key, entry, hit)
+        g.members = [[r, f, None] for r, f in reqs]
+        g.nrhs = nrhs
+        g.scratch = scratch
+        self.open[key] = g
+        entry.users += 1
+        return g
+
     def _dispatch(self) -> None:
         while self.running and self.waiting and False in self.busy:
             started = False
             for i, (req, _f) in enumerate(self.waiting):
-                # this request and every later one for the same key, up to max_rhs right-hand sides
-                group, nrhs = [], 0
-                for r2, f2 in self.waiting[i:]:
-                    if r2.key == req.key and nrhs + r2.nrhs <= self.max_rhs:
-                        group.append((r2, f2))
-                        nrhs += r2.nrhs
+                if req.key in self.open and self._try_join(req, _f):   # an open group took it meanwhile
+                    self._take([(req, _f)])
+                    started = True
+                    break
+                group, nrhs = self._same_key(i, req.key)
                 need, resident = self._footprint(req, nrhs)
                 if need > self.budget:
                     for r2, f2 in group:
                         f2.set_exception(MemoryError(f"request needs {need} bytes, budget {self.budget}"))
-                    self.waiting = [w for w in self.waiting if all(w[0] is not g[0] for g in group)]
+                    self._take(group)
                     started = True
                     break
                 if self.resident_bytes() + self.inflight + need > self.budget and not self._evict_for(need):
                     continue          # does not fit now; a smaller or resident one may
-                self.waiting = [w for w in self.waiting if all(w[0] is not g[0] for g in group)]
+                self._take(group)
+                groups, transient = [], 0
                 entry = self.cache.get(req.key)
-                hit = entry is not None
-                transient = 0
-                if hit:
+                if entry is not None:
                     self.hits += 1
-                    scratch = need
+                    groups.append(self._new_group(req.key, group, nrhs, True, entry, need))
+                    self._account(need)
                 else:
-                    self.misses += 1
-                    sc = req.scatterer
-                    n = estimate_n(sc, getattr(self.be, "s", 128))
-                    entry = Entry(req.key, n, entry_bytes(sc.nt, sc.ne, n, sc.ncell))
-                    self.cache[req.key] = entry
-                    scratch = need - entry.bytes
-                    transient = build_transient_bytes(sc.nt, sc.ne, n)
-                entry.users += 1
-                self.inflight += scratch
-                self.peak_bytes = max(self.peak_bytes, self.resident_bytes() + self.inflight)
+                    # a cache miss: when this is the last free worker, other waiting misses of other
+                    # keys are built in the same batch (idle workers would rather take them in parallel)
+                    todo = [(req.key, group, nrhs, need)]
+                    gather = self.busy.count(False) == 1
+                    for r3, _f3 in list(self.waiting):
+                        if not gather or len(todo) >= self.max_build_keys:
+                            break
+                        if r3.key in self.cache or r3.key in self.open or any(r3.key == t[0] for t in todo):
+                            continue
+                        j = next((i for i, w in enumerate(self.waiting) if w[0] is r3), None)
+                        if j is None:
+                            continue
+                        g3, n3 = self._same_key(j, r3.key)
+                        if not g3:
+                            continue
+                        need3, _res3 = self._footprint(r3, n3)
+                        if self.resident_bytes() + self.inflight + sum(t[3] for t in todo) + need3 > self.budget:
+                            continue
+                        todo.append((r3.key, g3, n3, need3))
+                        self._take(g3)
+                    for key, g3, n3, need3 in todo:
+                        self.misses += 1
+                        sc = g3[0][0].scatterer
+                        n = estimate_n(sc, getattr(self.be, "s", 128))
+                        e = Entry(key, n, entry_bytes(sc.nt, sc.ne, n, sc.ncell))
+                        self.cache[key] = e
+                        tr = build_transient_bytes(sc.nt, sc.ne, n)
+                        transient += tr
+                        groups.append(self._new_group(key, g3, n3, False, e, need3 - e.bytes - tr))
+                        self._account(need3 - e.bytes)
                 w = self.busy.index(False)
                 self.busy[w] = True
-                self.work[w] = (group, entry, hit, scratch, transient, next(self.bid))
+                self.work[w] = (groups, transient, next(self.bid))
                 self.lock.notify_all()
                 started = True
                 break
@@ -330,56 +470,93 @@ class Server:
                     self.lock.wait()
                 if self.work[w] is None:
                     return
-                group, entry, hit, scratch, transient, bid = self.work[w]
+                groups, transient, bid = self.work[w]
             t_start = time.perf_counter()
             ev0 = self.be.event(st) if self.t0_event is not None else None
-            err: Optional[BaseException] = None
-            rcs = iters = None
-            exc = np.concatenate([r.exc for r, _ in group], axis=0)
-            try:
-                if not hit:
-                    sc = group[0][0].scatterer
+            # builds of the cache misses, together
+            misses = [g for g in groups if not g.hit]
+            build_err: Optional[BaseException] = None
+            if misses:
+                items = [(g.members[0][0].scatterer, g.members[0][0].freq) for g in misses]
+                try:
+                    if len(items) > 1 and hasattr(self.be, "build_many"):
+                        built = self.be.build_many(items, st)
+                    else:
+                        built = [self.be.build(sc, f, st) for sc, f in items]
+                except BaseException as e:
+                    build_err = e
+                    built = None
+                with self.lock:
+                    for k, g in enumerate(misses):
+                        sc = items[k][0]
+                        if build_err is None:
+                            g.entry.handle, g.entry.n = built[k]
+                            g.entry.bytes = entry_bytes(sc.nt, sc.ne, g.entry.n, sc.ncell)
+                        else:
+                            g.entry.error = build_err
+                        g.entry.ready.set()
+                    self.inflight -= transient          # the builds' scratch is gone
+            for g in groups:
+                if g.hit:
+                    g.entry.ready.wait()
+            # the solves, one session per key; joins reach a session while it runs
+            for g in groups:
+                err: Optional[BaseException] = g.entry.error
+                rcs = iters = None
+                if err is None:
                     try:
-                        handle, n = self.be.build(sc, group[0][0].freq, st)
-                    except BaseException as e:
-                        entry.error = e
-                        raise
-                    finally:
-                        if entry.error is not None:
-                            entry.ready.set()
-                    with self.lock:
-                        entry.handle, entry.n = handle, n
-                        entry.bytes = entry_bytes(sc.nt, sc.ne, n, sc.ncell)
-                        self.inflight -= transient          # the build's scratch is gone
-                        scratch -= transient
-                    entry.ready.set()
-                else:
-                    entry.ready.wait()
-                    if entry.error is not None:
-                        raise entry.error
-                rcs, iters = self.be.solve(entry.handle, exc, st)
-            except BaseException as e:  # delivered to the requests of the batch
-                err = e
+                        with self.lock:
+                            exc = np.concatenate([m[0].exc for m in g.members], axis=0)
+                            ofs = 0
+                            for m in g.members:
+                                m[2] = ofs
+                                ofs += m[0].nrhs
+                            if hasattr(self.be, "open_session"):
+                                g.session = self.be.open_session(g.entry.handle, exc, st)
+                                g.state = "running"
+                            else:
+                                g.state = "done"
+                                del self.open[g.key]
+                        if g.session is not None:
+                            rcs, iters = g.session.run()
+                        else:
+                            rcs, iters = self.be.solve(g.entry.handle, exc, st)
+                    except BaseException as e:  # delivered to the requests of the group
+                        err = e
+                t_end = time.perf_counter()
+                with self.lock:
+                    if g.state != "done":
+                        g.state = "done"
+                        if self.open.get(g.key) is g:
+                            del self.open[g.key]
+                    requeue = []
+                    nsolved = 0 if rcs is None else int(rcs.shape[0])
+                    for req, fut, slot in g.members:
+                        if err is not None:
+                            fut.set_exception(err)
+                        elif slot is not None and slot + req.nrhs <= nsolved:
+                            fut.set_result(Result(req.rid, rcs[slot:slot + req.nrhs], iters[slot:slot + req.nrhs],
+                                                  t_end - req.arrival, bid, nsolved, g.hit))
+                        else:
+                            requeue.append((req, fut))   # joined too late for the solve: wait again
+                    if g.session is not None and hasattr(g.session, "free"):
+                        g.session.free()
+                    self.waiting[0:0] = requeue
             ev1 = self.be.event(st) if ev0 is not None else None
             t_end = time.perf_counter()
-            ofs = 0
-            for r, f in group:
-                if err is not None:
-                    f.set_exception(err)
-                else:
-                    f.set_result(Result(r.rid, rcs[ofs:ofs + r.nrhs], iters[ofs:ofs + r.nrhs], t_end - r.arrival, bid,
-                                        int(exc.shape[0]), hit))
-                ofs += r.nrhs
-            rec = {"batch": bid, "worker": w, "key": group[0][0].key, "requests": len(group),
-                   "rhs": int(exc.shape[0]), "hit": hit, "t_start": t_start, "t_end": t_end, "error": err is not None}
+            rec = {"batch": bid, "worker": w, "keys": [g.key for g in groups],
+                   "requests": sum(len(g.members) for g in groups), "joined": sum(g.joined for g in groups),
+                   "rhs": sum(g.nrhs for g in groups), "hit": all(g.hit for g in groups), "t_start": t_start,
+                   "t_end": t_end, "error": any(g.entry.error is not None for g in groups)}
             if ev0 is not None:
                 rec["dev_ms"] = (self.be.elapsed_ms(self.t0_event, ev0), self.be.elapsed_ms(self.t0_event, ev1))
             with self.lock:
-                entry.users -= 1
-                entry.last_used = t_end
-                if entry.error is not None and self.cache.get(entry.key) is entry:
-                    del self.cache[entry.key]                # a failed build is not cached
-                self.inflight -= scratch
+                for g in groups:
+                    g.entry.users -= 1
+                    g.entry.last_used = t_end
+                    if g.entry.error is not None and self.cache.get(g.entry.key) is g.entry:
+                        del self.cache[g.entry.key]               # a failed build is not cached
+                    self.inflight -= g.scratch
                 self.busy[w] = False
                 self.work[w] = None
                 self.log.append(rec)
@@ -408,7 +585,9 @@ def summarize(results: List[Result], log: List[dict], wall_s: float, server: Opt
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max())} if len(lat) else None,
            "batches": len(log), "mean_batch_requests": float(np.mean([b["requests"] for b in log])) if log else 0.0,
-           "max_batch_requests": max([b["requests"] for b in log], default=0)}
+           "max_batch_requests": max([b["requests"] for b in log], default=0),
+           "mean_batch_keys": float(np.mean([len(b.get("keys", [0])) for b in log])) if log else 0.0,
+           "joined_requests": int(sum(b.get("joined", 0) for b in log))}
     dev = [b["dev_ms"] for b in log if "dev_ms" in b]
     if dev:
         out["device_overlap_ms"] = overlap_ms(dev)

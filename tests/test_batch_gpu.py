@@ -84,3 +84,48 @@ def test_batch_rejects_other_precisions_and_empty(P):
     with pytest.raises(P.CbfmError):
         P.assemble_reduced_batch(meshes, cbfs, P.FP64)
     assert P.assemble_reduced_batch([], [], P.MIXED) == []
+
+
+def test_batch_member_with_real_cbfs_vs_oracle(P):
+    """One scatterer of the seeded uneven mix, assembled in the same batched
+    launches as the nine others, with real primary CBFs (generated on the GPU
+    from 12 directions x 2 polarisations, delta_SVD = 1e-3): sampled cell-pair
+    blocks of its A against oracle.cbfm.reduced_block with those CBFs injected
+    (Eq. (CBFM_outer)), within the mixed-path bound of 5e-5 of each block."""
+    from oracle import cbfm as OC, mesh as OM
+    gen = W.plane_wave_set(W.fibonacci_dirs(12))
+    mix = W.scatterer_mix(10, seed=3)
+    meshes, cbfs, geo = [], [], []
+    for d in mix:
+        g = d["mesh"]
+        ne = 3 * g.tris.shape[0] // 2
+        ncell = max(2, ne // 200)
+        gm = P.mesh(g.verts, g.tris, ncell, complex(*d["eps"]), partition="rcb")
+        meshes.append(gm)
+        cbfs.append(P.build_cbfs(gm, gen, 1e-3))
+        geo.append((g, complex(*d["eps"]), ncell, ne))
+    reds = P.assemble_reduced_batch(meshes, cbfs, P.MIXED)
+    # the first member small enough for the oracle's dense blocks, with at least three cells
+    k = next(i for i, (g, eps, nc, ne) in enumerate(geo) if nc >= 3 and ne <= 2400)
+    g, eps, ncell, ne = geo[k]
+    m = OM.build_rwg(g.verts, g.tris)
+    cell = meshes[k].cells()
+    CM, CJ = cbfs[k].export()
+    Ls = [int(x) for x in cbfs[k].L]
+    ocb = [OC.CellCBF(np.nonzero(cell == c)[0], CM[c], CJ[c], np.ones(1), Ls[c]) for c in range(ncell)]
+    A = reds[k].export()
+    offs = np.cumsum([0] + Ls)
+    nh = offs[-1]
+    mid = 0.5 * (m.verts[m.edges[:, 0]] + m.verts[m.edges[:, 1]])
+    cen = np.array([mid[cell == c].mean(0) for c in range(ncell)])
+    dist = np.linalg.norm(cen - cen[0], axis=1)
+    pairs = [(0, 0), (0, int(np.argsort(dist)[1])), (int(np.argmax(dist)), 0)]
+    for mi, ni in pairs:
+        ref = OC.reduced_block(m, ocb, eps, mi, ni)
+        rm, rn = slice(offs[mi], offs[mi + 1]), slice(offs[ni], offs[ni + 1])
+        rm2, rn2 = slice(nh + offs[mi], nh + offs[mi + 1]), slice(nh + offs[ni], nh + offs[ni + 1])
+        got = [A[rm, rn], A[rm, rn2], A[rm2, rn], A[rm2, rn2]]
+        for gb, ob in zip(got, ref):
+            err = float(np.abs(gb - ob).max() / np.abs(ob).max())
+            print(f"batch member {k} block ({mi}, {ni}): {err:.2e}")
+            assert err < 5e-5, (mi, ni, err)

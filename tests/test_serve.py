@@ -1,8 +1,9 @@
 """Host logic of the continuous-batching service (`serve.py`) with a fake
 backend: results reach the right request whether it runs alone or in a mix,
-requests for the same scatterer and frequency that wait together share one
-batch, the accounted device bytes never exceed the budget, idle entries are
-evicted least recently used first, and failures reach the caller."""
+requests join the open group of their key (while it builds, and while its
+solve session runs), cache misses of different keys are built in one batch,
+the accounted device bytes never exceed the budget, idle entries are evicted
+least recently used first, and failures reach the caller."""
 import threading
 import time
 
@@ -24,6 +25,8 @@ class FakeBackend:
         self.max_building = 0
         self.builds = []
         self.freed = []
+        self.build_many_calls = []
+        self.sessions = []
 
     def make_stream(self):
         return object()
@@ -53,6 +56,15 @@ class FakeBackend:
                 self.building -= 1
             self._leave()
 
+    def build_many(self, items, st):
+        self.build_many_calls.append([(sc.name, f) for sc, f in items])
+        return [self.build(sc, f, st) for sc, f in items]
+
+    def open_session(self, handle, exc, st):
+        s = FakeSession(self, handle, exc)
+        self.sessions.append(s)
+        return s
+
     def solve(self, handle, exc, st):
         self._enter()
         try:
@@ -63,6 +75,50 @@ class FakeBackend:
 
     def free(self, handle):
         self.freed.append(handle)
+
+
+class FakeSession:
+    """A solve that takes joins at 'block boundaries' (every tenth of the solve time) until it finishes."""
+
+    def __init__(self, be, handle, exc):
+        self.be, self.handle = be, handle
+        self.exc = [exc]
+        self.n = exc.shape[0]
+        self.queue = []
+        self.closed = False
+        self.joined = 0
+        self.lock = threading.Lock()
+
+    def join(self, exc):
+        with self.lock:
+            if self.closed or self.n + exc.shape[0] > S.MAX_BLOCK_RHS:
+                return None
+            slot, self.n = self.n, self.n + exc.shape[0]
+            self.queue.append(exc)
+            self.joined += 1
+            return slot
+
+    def run(self):
+        self.be._enter()
+        try:
+            t_end = time.perf_counter() + self.be.solve_s
+            while True:
+                time.sleep(self.be.solve_s / 10)
+                with self.lock:
+                    if self.queue:
+                        self.exc += self.queue
+                        self.queue = []
+                        t_end = max(t_end, time.perf_counter() + self.be.solve_s / 2)
+                    elif time.perf_counter() >= t_end:
+                        self.closed = True
+                        break
+            allx = np.concatenate(self.exc, axis=0)
+            return expected(self.handle, allx), np.full(allx.shape[0], 3, np.int32)
+        finally:
+            self.be._leave()
+
+    def free(self):
+        pass
 
 
 def expected(handle, exc):
@@ -99,22 +155,55 @@ def test_results_route_alone_and_in_mix():
         assert out.rcs.shape == (r.nrhs, 2) and out.rid == r.rid
     assert be.max_active >= 2                     # batches ran concurrently
     assert len(set(be.builds)) == len(be.builds)  # each (scatterer, frequency) built once
-    assert srv.hits + srv.misses == len(srv.log)
+    assert srv.hits + srv.misses == sum(len(b["keys"]) for b in srv.log)   # one count per key group
 
 
-def test_waiting_requests_share_a_batch():
+def test_requests_join_the_group_being_built():
     sc = scat("a")
     be = FakeBackend(build_s=0.2)
     srv = S.Server(be, hbm_budget=10**12, n_streams=1)
     first = srv.submit(req(sc, 1.0, 4, 0))           # occupies the only worker (build)
     time.sleep(0.05)
-    rest = [srv.submit(req(sc, 1.0, 40, k)) for k in range(1, 6)]   # 200 RHS wait
+    rest = [srv.submit(req(sc, 1.0, 40, k)) for k in range(1, 6)]   # 200 RHS arrive during the build
     res = [f.result(timeout=30) for f in [first] + rest]
     srv.close()
-    sizes = sorted({r.batch_id: r.batch_rhs for r in res[1:]}.values())
-    assert max(sizes) <= S.MAX_BLOCK_RHS
-    assert sizes == [80, 120]                        # 3 + 2 waiting requests, cut at 128 RHS
-    assert all(r.cache_hit for r in res[1:]) and not res[0].cache_hit
+    for k, r in enumerate(res):
+        np.testing.assert_array_equal(r.rcs, expected((sc.name, 1.0), req(sc, 1.0, 4 if k == 0 else 40, k).exc))
+    assert len({r.batch_id for r in res[:4]}) == 1 and res[0].batch_rhs == 124   # 3 joined, cut at 128 RHS
+    assert {r.batch_rhs for r in res[4:]} == {80} and res[4].batch_id == res[5].batch_id
+    assert all(r.cache_hit for r in res[4:]) and not res[0].cache_hit
+    assert srv.log[0]["joined"] == 3 and srv.log[0]["requests"] == 4
+
+
+def test_request_joins_a_running_solve():
+    sc = scat("a")
+    be = FakeBackend(build_s=0.01, solve_s=0.4)
+    srv = S.Server(be, hbm_budget=10**12, n_streams=1)
+    a = srv.submit(req(sc, 1.0, 8, 0))
+    time.sleep(0.15)                                  # built; its session runs
+    b = srv.submit(req(sc, 1.0, 8, 1))
+    ra, rb = a.result(timeout=30), b.result(timeout=30)
+    srv.close()
+    np.testing.assert_array_equal(rb.rcs, expected((sc.name, 1.0), req(sc, 1.0, 8, 1).exc))
+    np.testing.assert_array_equal(ra.rcs, expected((sc.name, 1.0), req(sc, 1.0, 8, 0).exc))
+    assert ra.batch_id == rb.batch_id and rb.batch_rhs == 16
+    assert be.sessions[0].joined == 1 and len(srv.log) == 1 and srv.log[0]["joined"] == 1
+
+
+def test_cache_misses_of_other_keys_build_together():
+    scs = [scat("a"), scat("b"), scat("c"), scat("d")]
+    be = FakeBackend(build_s=0.1)
+    srv = S.Server(be, hbm_budget=10**12, n_streams=1)
+    futs = [srv.submit(req(scs[i], 1.0, 4, i)) for i in range(4)]   # a starts alone; b, c and d wait
+    futs.append(srv.submit(req(scs[0], 1.0, 2, 9)))                 # joins the open group of a
+    res = [f.result(timeout=30) for f in futs]
+    srv.close()
+    for i, r in enumerate(res[:4]):
+        np.testing.assert_array_equal(r.rcs, expected((scs[i].name, 1.0), req(scs[i], 1.0, 4, i).exc))
+    np.testing.assert_array_equal(res[4].rcs, expected(("a", 1.0), req(scs[0], 1.0, 2, 9).exc))
+    assert be.build_many_calls == [[("b", 1.0), ("c", 1.0), ("d", 1.0)]]
+    assert [len(b["keys"]) for b in srv.log] == [1, 3] and srv.log[1]["requests"] == 3
+    assert srv.log[0]["joined"] == 1 and res[4].batch_id == res[0].batch_id
 
 
 def test_budget_admission_and_lru_eviction():
