@@ -451,6 +451,25 @@ __global__ void k_sub_rows(int64_t count, const z64 *__restrict__ a, const z64 *
     if (i < count) out[i] = a[i] - b[i];
 }
 
+// dst[r] = src[idx[r]] (rows of length n), r < k
+__global__ void k_gather_rows(int k, int64_t n, const int *__restrict__ idx, const z64 *__restrict__ src,
+                              z64 *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)k * n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[(int64_t)idx[i / n] * n + i % n];
+}
+
+// dst[idx[r]] (leading dimension ldd; 0: n) = src[r] (ld n) for r < k, += when ldd != 0
+__global__ void k_scatter_rows(int k, int64_t n, const int *__restrict__ idx, const z64 *__restrict__ src,
+                               z64 *__restrict__ dst, int64_t ldd) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)k * n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / n, c = i % n;
+        if (ldd == 0) dst[(int64_t)idx[r] * n + c] = src[r * n + c];
+        else dst[(int64_t)idx[r] * ldd + c] += src[r * ldd + c];
+    }
+}
+
 // rows r of a rows x n matrix with mask[r] != 0 set to zero
 __global__ void k_zero_rows_masked(int rows, int64_t n, const int *__restrict__ mask, z64 *__restrict__ X) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)rows * n;
@@ -850,7 +869,8 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     c.dev.alloc(1);
     DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw, Bm, Rout;
     DevBuf<double> bnorm, rnorm, rnorm0, fro_col;
-    DevBuf<int> dmask;
+    DevBuf<int> dmask, dsel;
+    DevBuf<z64> Ws;            // the vectors of a selective second Gram-Schmidt pass
     DevBuf<c32> s_in, s_out;   // complex64 rows for the mixed-precision products
     DevBuf<c32> V32, Z32;      // complex64 basis and coefficients for the mixed-precision solution update
     DevBuf<z64> zin;           // inexact CMP: the inner GMRES's (G^CBF)^{-1} in, the input of the product with A
@@ -859,6 +879,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
         dcap = std::max<int64_t>(2 * p, std::min<int64_t>((int64_t)std::max(restart, 2 * p), n + p));
         dcap2 = dcap + p;
         c.T1.alloc((size_t)p * n);
+        Ws.alloc((size_t)p * n);
         V.alloc((size_t)dcap * n);
         W.alloc((size_t)p * n);
         HcT.alloc((size_t)p * dcap);
@@ -1034,24 +1055,56 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             k_rownorm<<<pjc, 256, 0, st>>>(n, W.p, rnorm0.p);
             launched("k_rownorm");
             double wref = 0.0;
-            // block classical Gram-Schmidt, twice; HcT (pjc x d1) collects the coefficients
-            for (int pass = 0; pass < 2; ++pass) {
-                GemmSite site_(pass == 0 ? "site:gs1" : "site:gs2");
+            // block classical Gram-Schmidt; HcT (pjc x d1) collects the coefficients.  The second
+            // pass runs on the vectors that kept less than GS_KEEP of their norm in the first (the
+            // others are orthogonal to the basis to ~10 u already), gathered into Ws
+            {
+                GemmSite site_("site:gs1");
                 gemm_grouped<double>({GemmDesc{pjc, d1, n, 0, n, 0, n, 0, dcap}}, 0, 2, W.p, V.p, tmp2.p, false, st);
-                if (pass == 1 && fro(pjc, (int)d1, tmp2.p, dcap) <= ORTH_TOL * norm_sum(h_w1, pjc)) break;
                 gemm_grouped<double>({GemmDesc{pjc, n, d1, 0, dcap, 0, n, 0, n}}, 0, 0, tmp2.p, V.p, W.p, true, st,
                                      -1.0);
-                k_copy2d<<<nb(pjc * d1), 256, 0, st>>>(pjc, (int)d1, tmp2.p, dcap, HcT.p, dcap, pass);
+                k_copy2d<<<nb(pjc * d1), 256, 0, st>>>(pjc, (int)d1, tmp2.p, dcap, HcT.p, dcap, 0);
                 launched("k_copy2d");
-                if (pass == 0) {
-                    k_rownorm<<<pjc, 256, 0, st>>>(n, W.p, rnorm.p);
-                    launched("k_rownorm");
-                    CBFM_CUDA(cudaMemcpyAsync(h_rn.data(), rnorm0.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
-                    CBFM_CUDA(cudaMemcpyAsync(h_w1.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
-                    CBFM_CUDA(cudaStreamSynchronize(st));
-                    for (int q = 0; q < pjc; ++q) wref = std::max(wref, h_rn[q]);
-                    if (min_ratio(h_w1, h_rn, pjc) >= GS_KEEP) break;
+                k_rownorm<<<pjc, 256, 0, st>>>(n, W.p, rnorm.p);
+                launched("k_rownorm");
+                CBFM_CUDA(cudaMemcpyAsync(h_rn.data(), rnorm0.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
+                CBFM_CUDA(cudaMemcpyAsync(h_w1.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
+                CBFM_CUDA(cudaStreamSynchronize(st));
+                for (int q = 0; q < pjc; ++q) wref = std::max(wref, h_rn[q]);
+            }
+            std::vector<int> sel;   // vectors that need the second pass
+            std::vector<double> w1sel;
+            for (int q = 0; q < pjc; ++q)
+                if (h_rn[q] > 0.0 && h_w1[q] / h_rn[q] < GS_KEEP) {
+                    sel.push_back(q);
+                    w1sel.push_back(h_w1[q]);
                 }
+            if (!sel.empty()) {
+                GemmSite site_("site:gs2");
+                const int k = (int)sel.size();
+                const bool all = k == pjc;
+                if (!all) {
+                    dsel.alloc(k);
+                    CBFM_CUDA(cudaMemcpyAsync(dsel.p, sel.data(), sizeof(int) * k, cudaMemcpyHostToDevice, st));
+                    k_gather_rows<<<nb((int64_t)k * n), 256, 0, st>>>(k, n, dsel.p, W.p, Ws.p);
+                    launched("k_gather_rows");
+                }
+                z64 *Wk = all ? W.p : Ws.p;
+                gemm_grouped<double>({GemmDesc{k, d1, n, 0, n, 0, n, 0, dcap}}, 0, 2, Wk, V.p, tmp2.p, false, st);
+                if (fro(k, (int)d1, tmp2.p, dcap) > ORTH_TOL * norm_sum(w1sel, k)) {
+                    gemm_grouped<double>({GemmDesc{k, n, d1, 0, dcap, 0, n, 0, n}}, 0, 0, tmp2.p, V.p, Wk, true, st,
+                                         -1.0);
+                    if (all) {
+                        k_copy2d<<<nb(pjc * d1), 256, 0, st>>>(pjc, (int)d1, tmp2.p, dcap, HcT.p, dcap, 1);
+                        launched("k_copy2d");
+                    } else {
+                        k_scatter_rows<<<nb((int64_t)k * n), 256, 0, st>>>(k, n, dsel.p, Ws.p, W.p, 0);
+                        launched("k_scatter_rows");
+                        k_scatter_rows<<<nb((int64_t)k * d1), 256, 0, st>>>(k, d1, dsel.p, tmp2.p, HcT.p, dcap);
+                        launched("k_scatter_rows");
+                    }
+                }
+                if (!all) CBFM_CUDA(cudaStreamSynchronize(st));   // sel is a host vector of this scope
             }
             // orthonormalise the new block (pivoted: drops dependent directions)
             const int r = wref > 0.0 ? cholqr2_rows(c, W.p, pjc, n, V.p + d1 * n, Rw.p, rank_tol, wref, drop_tol) : 0;
@@ -1106,9 +1159,10 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
             launched("k_copy2d");
             // projected right-hand side rows and the residual of the least-squares
             // problem, updated with the new Q block only (Rv = E1S - Q Q^H E1S):
-            //   G_J = Q_J^H Rv,  Rv <- Rv - Q_J G_J
+            //   G_J = Q_J^H Rv = Q_J^H E1S  (Q_J is orthogonal to the earlier Q blocks,
+            //   and E1S is zero below its first p1 rows),  Rv <- Rv - Q_J G_J
             GemmSite site_ls_("site:ls_rhs");
-            gemm_grouped<double>({GemmDesc{pjc, p, d2, 0, p, 0, p, d0 * p, p}}, 2, 0, Hn.p, Rv.p, Gv.p, false, st);
+            gemm_grouped<double>({GemmDesc{pjc, p, p1, 0, p, 0, p, d0 * p, p}}, 2, 0, Hn.p, E1S.p, Gv.p, false, st);
             gemm_grouped<double>({GemmDesc{d2, p, pjc, 0, p, d0 * p, p, 0, p}}, 0, 0, Hn.p, Gv.p, Rv.p, true, st,
                                  -1.0);
             k_colnorm<<<p, 256, 0, st>>>((int)d2, p, Rv.p, p, rnorm.p);
