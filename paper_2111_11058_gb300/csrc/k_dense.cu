@@ -444,9 +444,13 @@ __global__ void __cluster_dims__(JS_CL, 1, 1) __launch_bounds__(256)
     bool ok = true;
     int sweep = 0;
     for (; sweep < 60; ++sweep) {
-        // largest squared column norm: a pair whose coupling is below tol times it is
-        // left alone (rotations at that level only stir the columns of singular values
-        // far below the largest, which carry no accuracy anyway)
+        // largest squared column norm: a pair whose coupling is below tol^2 times it is
+        // left alone.  Such a pair has both columns at the rounding level of the
+        // largest (|x_i| |x_j| <= (tol |x|max)^2 is needed unless the pair is already
+        // orthogonal), so rotating it only stirs noise; every pair above that is
+        // rotated to the relative criterion, which keeps singular values down to
+        // about tol sigma_1 accurate (a floor of tol |x|max^2 left pairs of columns
+        // near 1e-7 sigma_1 coupled and their singular values wrong at that level)
         double mx = 0.0;
         for (int i = warp; i < s; i += nw) {
             double al = 0;
@@ -463,7 +467,7 @@ __global__ void __cluster_dims__(JS_CL, 1, 1) __launch_bounds__(256)
             s_big = bmax;
         }
         __syncthreads();
-        const double floor_abs = tol * s_big;
+        const double floor_abs = tol * tol * s_big;
         for (int round = 0; round < n2 - 1 && ok; ++round) {
             for (int pr = gw; pr < n2 / 2; pr += ngw) {
                 // round-robin: position 0 fixed, others rotate
