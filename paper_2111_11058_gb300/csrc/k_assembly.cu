@@ -90,44 +90,61 @@ __device__ inline void cross3(const double *a, const double *b, double *c) {
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// ln(R + l) without cancellation for l < 0: (R + l)(R - l) = R0^2
-__device__ inline double log_r_plus_l(double l, double R, double R02) {
-    return (l >= 0.0) ? log(R + l) : log(R02 / (R - l));
-}
-
 // Closed-form potentials of a flat triangle V at r:
 //   I1 = int 1/R, Iv = int (r' - r)/R, I3 = int (r - r')/R^3 (principal value in plane).
+// Per edge (Wilton et al. 1984, Graglia 1993): F = ln((R+ + l+)/(R- + l-)) and
+// beta = atan(t0 l+ / (R0^2 + |h| R+)) - atan(t0 l- / (R0^2 + |h| R-)).  FP64
+// instructions are the cost on this GPU, so each edge takes one logarithm of
+// the ratio and one two-argument arctangent of the difference (exact
+// identities: atan(n1/d1) - atan(n2/d2) = atan2(n1 d2 - n2 d1, d1 d2 + n1 n2)
+// for d1, d2 > 0), normalisations multiply by reciprocal square roots, and the
+// distances to the three vertices are formed once.  R + l is taken as
+// R0^2 / (R - l) for l < 0 (no cancellation).
 __device__ void potentials(const double *V, const double *r, double &I1, double Iv[3], double I3[3]) {
     double e1[3], e2[3], n[3];
     sub3(V + 3, V, e1);
     sub3(V + 6, V, e2);
     cross3(e1, e2, n);
-    double nl = sqrt(dot3(n, n));
-    for (int d = 0; d < 3; ++d) n[d] /= nl;
+    const double nl2 = dot3(n, n), inl = rsqrt(nl2), nl = nl2 * inl;
+    for (int d = 0; d < 3; ++d) n[d] *= inl;
     double rv[3];
     sub3(r, V, rv);
     double h = dot3(n, rv), ah = fabs(h);
     double rho[3] = {r[0] - h * n[0], r[1] - h * n[1], r[2] - h * n[2]};
     double tiny = 1e-28 * nl;
+    double Rv[3];   // |r - vertex|
+    for (int i = 0; i < 3; ++i) {
+        double dv[3];
+        sub3(r, V + 3 * i, dv);
+        Rv[i] = sqrt(dot3(dv, dv));
+    }
     double sum_tF = 0.0, sum_beta = 0.0, vrho[3] = {0, 0, 0}, vF[3] = {0, 0, 0};
     for (int i = 0; i < 3; ++i) {
-        const double *A = V + 3 * i, *B = V + 3 * ((i + 1) % 3);
+        const int i1 = (i + 1) % 3;
+        const double *A = V + 3 * i, *B = V + 3 * i1;
         double l[3];
         sub3(B, A, l);
-        double ll = sqrt(dot3(l, l));
-        for (int d = 0; d < 3; ++d) l[d] /= ll;
+        const double ill = rsqrt(dot3(l, l));
+        for (int d = 0; d < 3; ++d) l[d] *= ill;
         double u[3];
         cross3(l, n, u);
-        double Ar[3], Br[3], rA[3], rB[3];
+        double Ar[3], Br[3];
         sub3(A, rho, Ar);
         sub3(B, rho, Br);
-        sub3(r, A, rA);
-        sub3(r, B, rB);
         double t0 = dot3(Ar, u), lp = dot3(Br, l), lm = dot3(Ar, l);
         double R02 = t0 * t0 + h * h;
-        double Rp = sqrt(dot3(rB, rB)), Rm = sqrt(dot3(rA, rA));
-        double F = (R02 > tiny) ? log_r_plus_l(lp, Rp, R02) - log_r_plus_l(lm, Rm, R02) : 0.0;
-        double beta = (ah > 0.0) ? atan(t0 * lp / (R02 + ah * Rp)) - atan(t0 * lm / (R02 + ah * Rm)) : 0.0;
+        const double Rp = Rv[i1], Rm = Rv[i];
+        double F = 0.0;
+        if (R02 > tiny) {   // (R+ + l+)/(R- + l-) as a_n b_d / (a_d b_n)
+            const double an = lp >= 0.0 ? Rp + lp : R02, ad = lp >= 0.0 ? 1.0 : Rp - lp;
+            const double bn = lm >= 0.0 ? Rm + lm : R02, bd = lm >= 0.0 ? 1.0 : Rm - lm;
+            F = log((an * bd) / (ad * bn));
+        }
+        double beta = 0.0;
+        if (ah > 0.0) {
+            const double d1 = R02 + ah * Rp, d2 = R02 + ah * Rm;
+            beta = atan2(t0 * (lp * d2 - lm * d1), d1 * d2 + t0 * t0 * lp * lm);
+        }
         sum_tF += t0 * F;
         sum_beta += beta;
         double cf = 0.5 * (R02 * F + lp * Rp - lm * Rm);
