@@ -98,20 +98,21 @@ def local_block(m: RWGMesh, k: complex, t: int, s: int, alpha: float = ALPHA_NEA
     return (Ko[0::2] + 1j * Ko[1::2]).reshape(3, 3), (To[0::2] + 1j * To[1::2]).reshape(3, 3), bool(near.value)
 
 
-def pmchwt_blocks(m: RWGMesh, eps_r: complex, mu_r: float = 1.0, rows=None, cols=None):
+def pmchwt_blocks(m: RWGMesh, eps_r: complex, mu_r: float = 1.0, rows=None, cols=None,
+                  alpha: float = ALPHA_NEAR):
     """Ks, Ta, Tb restricted to rows x cols (full matrices by default)."""
     k1, eta1, k2, eta2 = media(eps_r, mu_r)
-    K1, T1 = operator_block(m, k1, rows, cols)
-    K2, T2 = operator_block(m, k2, rows, cols)
+    K1, T1 = operator_block(m, k1, rows, cols, alpha)
+    K2, T2 = operator_block(m, k2, rows, cols, alpha)
     Ks = K1 + K2
     Ta = -(eta1 * T1 + eta2 * T2)
     Tb = T1 / eta1 + T2 / eta2
     return Ks, Ta, Tb
 
 
-def pmchwt_matrix(m: RWGMesh, eps_r: complex, mu_r: float = 1.0):
+def pmchwt_matrix(m: RWGMesh, eps_r: complex, mu_r: float = 1.0, alpha: float = ALPHA_NEAR):
     """Full N x N PMCHWT matrix, Eq. (Z), unknown order [alpha^M; alpha^J]."""
-    Ks, Ta, Tb = pmchwt_blocks(m, eps_r, mu_r)
+    Ks, Ta, Tb = pmchwt_blocks(m, eps_r, mu_r, alpha=alpha)
     return np.block([[Ks, Ta], [Tb, Ks]])
 
 

@@ -258,13 +258,14 @@ constexpr int NEAR_MOM = 15;   // complex moments per (orientation, medium)
 // Work of one near pair, counted from the operations of near_pair2 with each
 // square root, logarithm, arctangent, sine/cosine pair and exponential as one:
 // per orientation and test point (14 lanes) the closed-form potentials of the
-// trial triangle (3 edges x 60 + 25) and the trial-point geometry (7 x 10) in
-// FP64, and for each medium the 7 remainder evaluations with their weighted
-// sums (7 x 60, FP32 on the mixed path) plus S0, Sr, Wv and the 15 moments
-// (90, FP64); then the moment reductions (15 complex x 2 media x 3 shuffle
-// steps on 16 lanes) and the 9 entries (2 orientations x 2 media x 60), FP64.
+// trial triangle (3 edges x 50 + 40, the vertex distances formed once) and
+// the trial-point geometry (7 x 10) in FP64, and for each medium the 7
+// remainder evaluations with their weighted sums (7 x 60, FP32 on the mixed
+// path) plus S0, Sr, Wv and the 15 moments (90, FP64); then the moment
+// reductions (15 complex x 2 media x 3 shuffle steps on 16 lanes) and the 9
+// entries (2 orientations x 2 media x 60), FP64.
 // FP64 operations of the mixed form; the FP64 form also counts the remainders.
-constexpr double NEAR_FP64_OPS_MIXED = 14 * (205 + 70 + 2 * 90) + 16 * 15 * 2 * 3 * 2 + 9 * 2 * 2 * 60;
+constexpr double NEAR_FP64_OPS_MIXED = 14 * (190 + 70 + 2 * 90) + 16 * 15 * 2 * 3 * 2 + 9 * 2 * 2 * 60;
 constexpr double NEAR_REM_OPS = 14 * 2 * 7 * 60;
 
 template <typename T>
