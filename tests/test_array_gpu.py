@@ -10,13 +10,13 @@ sphere), one cell per sphere, eps_r 1..6, FP64 path.
   CMP reaches 1e-6 in fewer than 40 iterations at eps_r = 3 (the paper
   reports < 40 on its 4 x 4 x 2 array) and needs several times fewer
   iterations to 1e-4 than the K-diagonal CBFM without it (the paper reports
-  1/5 at eps_r = 6 to 1/70 at eps_r = 1; measured here 38 vs 192, 14 vs 153
+  1/5 at eps_r = 6 to 1/70 at eps_r = 1; measured here 36 vs 171, 14 vs 147
   and 3 vs 136 at eps_r = 6, 3, 1) and than the T-diagonal CBFM of Eq.
-  (cbfm_Tdiag) (measured 206, 157 and 30); its count grows with eps_r.
+  (cbfm_Tdiag) (measured 186, 149 and 30); its count grows with eps_r.
 * Accuracy against the conventional MoM (Eq. (MoM_T), same quadrature): the
   RMSE of Eq. (RMSE) between the CBFM and MoM bistatic RCS at eps_r = 3 (the
   paper reports -39.98 dB on its 4 x 4 x 2 array) stays below -30 dB
-  (measured -54.9 and -55.3 dB on the phi = 0 and 90 degree cuts).
+  (measured -52.8 and -52.7 dB on the phi = 0 and 90 degree cuts).
 """
 import math
 
