@@ -856,6 +856,8 @@ def main():
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
                 "fp64_products_ms_by_step": dict(sorted(sites.items(), key=lambda kv: -kv[1])),
+                # all timed kernels of a step together (the rest of ms_per_step is launch and host gaps)
+                "kernel_ms_per_step": round(tot / n_prof, 3),
                 "fp64_path": fp64, "other_solver": alt, "mom": mom, "cmp_inexact": inexact, "batch": batch,
                 "serving": serving, "fused": fused, "c5": c5}
         if not args.no_cpu and ws == 1 and WORKLOAD == "cube9216":

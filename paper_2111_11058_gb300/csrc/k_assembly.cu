@@ -4,7 +4,7 @@
 // Every stage runs over any number of meshes in one launch (a single mesh is
 // a batch of one).
 // Stage 1, far pairs (k_far): persistent CTAs take tasks (mesh, test triangle
-//   t, strip of trial triangles) from an atomic counter; one thread per trial
+//   t, strip of trial triangles s >= t) from an atomic counter; one thread per trial
 //   triangle s evaluates both media over the 7 x 7 point pairs and reduces them to 18
 //   complex moments per medium, from which the 3 x 3 local blocks follow:
 //     T_ab = -j k c_a c_b [ Mrs - pi'_b.Mr - pi_a.Ms + (pi_a.pi'_b - 4/k^2) M0 ]
@@ -27,7 +27,8 @@
 //   integrated in closed form over the trial triangle (Wilton et al. 1984,
 //   Graglia 1993 edge sums), bounded remainders by the 7-point rule, blocks
 //   symmetrised L(t,s) = (L~(t,s) + L~(s,t)^T)/2; K of a triangle with itself is 0.
-// Stage 3 (k_gather, one block per RWG row): RWG entries Z_op[i][j] = sum over
+// Stage 3 (k_mirror): the blocks of the pairs s < t, transposed from (s, t).
+// Stage 4 (k_gather, one block per RWG row): RWG entries Z_op[i][j] = sum over
 //   the 2 x 2 triangle pairs of the two supports.
 #include <algorithm>
 #include <string>
@@ -60,7 +61,15 @@ __device__ __forceinline__ void cp_async(void *dst_smem, const void *src) {
                  : "memory");
 }
 
-// One far (or, by the classification, near -> zero) triangle pair (t, s);
+// Exchanging test and trial triangle transposes a local block, L(s, t) =
+// L(t, s)^T, for T (G is symmetric) and for K (the triple product
+// f_a . ((r - r') x f_b') keeps its value when r <-> r' and a <-> b), in the
+// quadrature too since both triangles use the same 7-point rule.  So the far
+// and near stages evaluate and store each unordered pair once, as (t, s) with
+// t <= s in the row-major nt x nt planes, and k_mirror fills s < t from it by
+// a tiled transpose (component (a, b) of (t, s) is component (b, a) of (s, t)).
+
+// One far (or, by the classification, near -> zero) triangle pair (t, s), t <= s;
 // rs is the record of the trial triangle s.
 template <typename T>
 __device__ __forceinline__ void far_pair(const FarStage<T> &S, int nt, const T *rs,
@@ -203,8 +212,7 @@ __device__ inline void green_rems(z64 k, double R, z64 &gr, z64 &hr) {
 // test t / trial s, 1: test s / trial t), medium i, test point p < 7 (lane p = 7
 // of each group of eight idles).  Each lane forms its test point's
 // contribution to the 3 x 3 K and T blocks; groups of eight reduce over p, and
-// lane 0 symmetrises, weights the media into Ks, Ta, Tb and stores both (t,s)
-// and (s,t).
+// lane 0 symmetrises, weights the media into Ks, Ta, Tb and stores (t, s).
 // FP32 form of the same remainders for the mixed path.  The series branch is
 // widened to |kR| < 0.6 so that the direct forms cancel at most a factor
 // (kR)^-3 < 5 in single precision; 12 terms leave < 1e-11 relative there.
@@ -252,7 +260,7 @@ __device__ inline void green_rems_f(float kre, float kim, float R, c32 &gr, c32 
 //   K~_ab = c_a d_b [(Q - P).MX + P.(MW x Q)]        (0 when t = s)
 // The moments are summed over the 7 test points by shuffles and staged in
 // shared memory; lanes (slot, a, b) then symmetrise, weight the media into
-// Ks, Ta, Tb and store (t, s) and (s, t).
+// Ks, Ta, Tb and store (t, s), t <= s (the (s, t) block is its transpose).
 constexpr int NEAR_MOM = 15;   // complex moments per (orientation, medium)
 
 // Work of one near pair, counted from the operations of near_pair2 with each
@@ -408,8 +416,7 @@ __device__ __forceinline__ void near_pair2(int t, int s, int nt, const double *_
             blk[op * 9 + 3 * a + b] = val;
             continue;
         }
-        Zloc[(op * 9 + 3 * a + b) * plane + (int64_t)t * nt + s] = val;
-        if (t != s) Zloc[(op * 9 + 3 * b + a) * plane + (int64_t)s * nt + t] = val;
+        Zloc[(op * 9 + 3 * a + b) * plane + (int64_t)t * nt + s] = val;   // t <= s; (s, t) by k_mirror
     }
 }
 
@@ -428,7 +435,7 @@ struct AsmJob {
     Media md;
     double alpha;
     int nt, strip, nstrip;   // far tasks: trial triangles per task (multiple of 32), tasks per test triangle
-    int64_t ne, far0, near0, row0;   // first far task, near pair and gather row of the job
+    int64_t ne, far0, near0, row0, mir0;   // first far task, near pair, gather row and mirror tile of the job
 };
 
 template <typename T, int64_t AsmJob<T>::*F>
@@ -479,6 +486,18 @@ __device__ __forceinline__ void far_stage(FarStage<T> &S, const AsmJob<T> &J, in
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+// Far tasks of a job before test-triangle block i (blocks of one strip width,
+// block i taking the strips i .. nstrip - 1), and in the whole job.
+template <typename T>
+__host__ __device__ __forceinline__ int64_t far_before(const AsmJob<T> &J, int i) {
+    return (int64_t)J.strip * ((int64_t)i * J.nstrip - ((int64_t)i * (i - 1)) / 2);
+}
+template <typename T>
+int64_t far_tasks(const AsmJob<T> &J) {
+    const int last = J.nstrip - 1;
+    return far_before(J, last) + (int64_t)(J.nt - last * J.strip);
+}
+
 // FP32: three blocks of four warps per SM (168 registers) for more warps in
 // flight; FP64: four blocks of two warps, where the wider accumulators would
 // otherwise spill.
@@ -498,9 +517,21 @@ __global__ void __launch_bounds__(32 * far_warps<T>(), sizeof(T) == 4 ? 3 : 4)
         tj = find_job<T, &AsmJob<T>::far0>(jobs, njobs, (int64_t)task);
         const AsmJob<T> &J = jobs[tj];
         const int64_t local = (int64_t)task - J.far0;
-        tt = (int)(local / J.nstrip);
-        s0 = (int)(local % J.nstrip) * J.strip;
+        // upper triangle: the test triangles in blocks of one strip width W; block i
+        // takes the strips i .. nstrip - 1 for each of its test triangles, and the
+        // blocks before it hold far_before(i) = W (i nstrip - i (i - 1) / 2) tasks
+        int lo = 0, hi = J.nstrip - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (far_before(J, mid) <= local) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t l2 = local - far_before(J, lo);
+        const int per = J.nstrip - lo;
+        tt = lo * J.strip + (int)(l2 / per);
+        s0 = (lo + (int)(l2 % per)) * J.strip;
         tse = min(s0 + J.strip, J.nt);
+        s0 = max(s0, tt & ~31);   // on the diagonal strip, from the 32 trial triangles holding s = t
         return true;
     };
     int cs0 = 0;
@@ -522,7 +553,7 @@ __global__ void __launch_bounds__(32 * far_warps<T>(), sizeof(T) == 4 ? 3 : 4)
         {
             const AsmJob<T> &J = jobs[cj];
             const int s = cs0 + lane;
-            if (lane < ccnt) {
+            if (lane < ccnt && s >= ct) {
                 if (J.tri_cell && !share_cell(J.tri_cell, ct, s)) {
                     const int64_t plane = (int64_t)J.nt * J.nt, base = (int64_t)ct * J.nt + s;
                     for (int c = 0; c < NCOMP; ++c) J.Zloc[c * plane + base] = cx<T>(0, 0);
@@ -561,6 +592,51 @@ __global__ void __launch_bounds__(128) k_near_blocks(const AsmJob<T> *__restrict
         }
         cx<T> *blk = (J->nearblk && t >= 0) ? J->nearblk + (pid - J->near0) * NCOMP : nullptr;
         near_pair2<T>(t, s, J->nt, J->rec64, J->md, J->Zloc, sm_all[(threadIdx.x >> 5) & 3], blk);
+    }
+}
+
+// The blocks of the pairs s < t of all meshes from the stored (s, t): one
+// TM x TM tile of one component plane per CTA (TM x 256/TM threads; TM = 64
+// complex64 or 32 complex128 entries, 512-byte row segments), read along the
+// rows of (s, t) and written along the rows of (t, s) through shared memory;
+// the tiles of a mesh are those on and below the diagonal, tile l = (bi, bj)
+// with l = bi (bi + 1) / 2 + bj, and component (a, b) of (t, s) comes from
+// component (b, a) of (s, t).
+template <typename T>
+__host__ __device__ constexpr int mir_tile() { return sizeof(T) == 4 ? 64 : 32; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mirror(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t ntiles) {
+    constexpr int TM = mir_tile<T>(), TY = 256 / TM;
+    __shared__ cx<T> tile[TM][TM + 1];
+    const int c = blockIdx.y;   // destination component op * 9 + 3 a + b
+    const int csrc = (c / 9) * 9 + 3 * (c % 3) + (c % 9) / 3;
+    const int tx = threadIdx.x % TM, ty = threadIdx.x / TM;
+    for (int64_t l = blockIdx.x; l < ntiles; l += gridDim.x) {
+        const AsmJob<T> &J = jobs[find_job<T, &AsmJob<T>::mir0>(jobs, njobs, l)];
+        const int64_t loc = l - J.mir0;
+        int64_t bi = (int64_t)((sqrt(8.0 * (double)loc + 1.0) - 1.0) * 0.5);
+        while ((bi + 1) * (bi + 2) / 2 <= loc) ++bi;
+        while (bi * (bi + 1) / 2 > loc) --bi;
+        const int t0 = (int)bi * TM, s0 = (int)(loc - bi * (bi + 1) / 2) * TM;   // destination rows t, columns s
+        const int nt = J.nt;
+        const int64_t plane = (int64_t)nt * nt;
+        const cx<T> *src = J.Zloc + (int64_t)csrc * plane;
+        cx<T> *dst = J.Zloc + (int64_t)c * plane;
+        const int tc = t0 + tx;
+#pragma unroll
+        for (int y = ty; y < TM; y += TY) {   // tile[y][x] = (s0 + y, t0 + x) of the source
+            const int sr = s0 + y;
+            if (tc < nt && sr < tc) tile[y][tx] = src[(int64_t)sr * nt + tc];
+        }
+        __syncthreads();
+        const int sc = s0 + tx;
+#pragma unroll
+        for (int y = ty; y < TM; y += TY) {   // (t0 + y, s0 + x) = source (s0 + x, t0 + y)
+            const int tr = t0 + y;
+            if (tr < nt && sc < tr) dst[(int64_t)tr * nt + sc] = tile[tx][y];
+        }
+        __syncthreads();
     }
 }
 
@@ -613,8 +689,8 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
     if (nj == 0) return;
     std::vector<DevBuf<cx<T>>> Zloc(nj);
     std::vector<AsmJob<T>> jobs(nj);
-    int64_t npairs = 0, nrows = 0;
-    double far_flop = 0.0, far_bytes = 0.0;
+    int64_t npairs = 0, nrows = 0, ntiles = 0;
+    double far_flop = 0.0, far_bytes = 0.0, mir_bytes = 0.0, gat_bytes = 0.0;
     for (int k = 0; k < nj; ++k) {
         Mesh &m = *ms[k];
         const int nt = (int)m.h.nt;
@@ -638,10 +714,17 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
         J.ne = m.h.ne;
         J.near0 = npairs;
         J.row0 = nrows;
+        J.mir0 = ntiles;
         npairs += m.n_near;
         nrows += m.h.ne;
-        far_flop += ((double)nt * nt - (2.0 * m.n_near - nt)) * 49.0 * FAR_FLOP_PER_POINT_PAIR;
-        far_bytes += (double)NCOMP * nt * nt * sizeof(cx<T>);
+        const int64_t tb = (nt + mir_tile<T>() - 1) / mir_tile<T>();
+        ntiles += tb * (tb + 1) / 2;
+        mir_bytes += 2.0 * NCOMP * (0.5 * nt * (nt - 1.0)) * sizeof(cx<T>);   // pairs s < t read and written
+        // the gather reads every local block once and writes the three RWG planes
+        gat_bytes += ((double)NCOMP * nt * nt + 3.0 * (double)m.h.ne * m.h.ne) * sizeof(cx<T>);
+        const double upper = 0.5 * nt * (nt + 1.0);   // pairs t <= s
+        far_flop += (upper - (double)m.n_near) * 49.0 * FAR_FLOP_PER_POINT_PAIR;
+        far_bytes += (double)NCOMP * upper * sizeof(cx<T>);
     }
     int dev = 0, nsm = 0;
     CBFM_CUDA(cudaGetDevice(&dev));
@@ -665,7 +748,7 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
             J.strip = W;
             J.nstrip = (J.nt + W - 1) / W;
             J.far0 = ntask;
-            ntask += (int64_t)J.nt * J.nstrip;
+            ntask += far_tasks(J);
         }
         CBFM_CUDA(cudaMemcpyAsync(djobs.p, jobs.data(), sizeof(AsmJob<T>) * nj, cudaMemcpyHostToDevice, st));
         CBFM_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), st));
@@ -709,7 +792,15 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
         launched("k_near_blocks");
     }
     {
+        const dim3 grid((unsigned)std::min<int64_t>(ntiles, 1 << 20), NCOMP);
+        prof_add_work("k_mirror", 0.0, mir_bytes);
+        ProfScope ps_("k_mirror", st);
+        k_mirror<T><<<grid, 256, 0, st>>>(djobs.p, nj, ntiles);
+        launched("k_mirror");
+    }
+    {
         const unsigned grid = (unsigned)std::min<int64_t>(nrows, 8 * (int64_t)nsm);
+        prof_add_work("k_gather", 0.0, gat_bytes);
         ProfScope ps_("k_gather", st);
         k_gather<T><<<grid, 128, 0, st>>>(djobs.p, nj, nrows);
         launched("k_gather");
