@@ -118,7 +118,7 @@ DEV = {"n_sm": 152, "sm_max_mhz": 2070.0}
 def fp32_peak_tflops() -> float:
     return DEV["n_sm"] * FP32_LANES_PER_SM * 2 * DEV["sm_max_mhz"] * 1e6 / 1e12
 FP64_KERNELS = {"k_dots", "k_orth_update", "k_near_blocks", "k_finish", "k_lu_solve", "k_jacobi_svd",
-                "k_gemm_z64", "k_pchol", "k_trinv", "k_gj_sweep", "k_gjb_inv"}
+                "k_gemm_z64", "k_pchol", "k_trinv", "k_gj_sweep", "k_gjb_inv", "k_gjb_persistent"}
 FP32_KERNELS = {"k_far", "k_fused", "k_matvec", "k_gemm_c32"}
 
 
@@ -778,6 +778,8 @@ def main():
     P.profile(False)
     # "site:*" records split the FP64 products by the solver step that launched them
     sites = {k[5:]: round(v["ms"] / n_prof, 3) for k, v in prof.items() if k.startswith("site:")}
+    site_tflops = {k[5:]: round(v["flop"] / (v["ms"] / 1e3) / 1e12, 3) for k, v in prof.items()
+                   if k.startswith("site:") and v.get("flop") and v["ms"] > 0}
     prof = {k: v for k, v in prof.items() if not k.startswith("site:")}
     tot = sum(v["ms"] for v in prof.values())
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -856,6 +858,8 @@ def main():
                 "kernels": {k: roofline(k, v, peaks, peak_src) | {"ms_per_step": v["ms"] / n_prof}
                             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
                 "fp64_products_ms_by_step": dict(sorted(sites.items(), key=lambda kv: -kv[1])),
+                # the same products' rate per solver step (6 flop per complex MAC, the three-multiplication form)
+                "fp64_products_tflops_by_step": dict(sorted(site_tflops.items(), key=lambda kv: -kv[1])),
                 # all timed kernels of a step together (the rest of ms_per_step is launch and host gaps)
                 "kernel_ms_per_step": round(tot / n_prof, 3),
                 "fp64_path": fp64, "other_solver": alt, "mom": mom, "cmp_inexact": inexact, "batch": batch,

@@ -612,7 +612,10 @@ __device__ __forceinline__ bool gj_grid_sync(unsigned *cnt, unsigned *gen, unsig
         } else {
             uint64_t t0;
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-            while (atomicAdd(gen, 0u) == my) {
+            for (;;) {   // acquire loads: the waiting CTAs do not queue atomics on the line
+                unsigned cur;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
+                if (cur != my) break;
                 uint64_t t;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
                 if (t - t0 > 1000000000ull) {
@@ -832,22 +835,24 @@ __global__ void k_gjb_panels(int n, int k0, int b, const z64 *__restrict__ A, z6
 // warp instructions are the cost here (each holds a sub-partition's FP64 pipe
 // for ~64 clocks whatever its active lanes), so the pivot-row work is done
 // once, by one warp, instead of once per entry.
-__global__ void __launch_bounds__(GJB * GJB) k_gjb_inv(int n, int k0, int b, const z64 *__restrict__ Rw,
-                                                 z64 *__restrict__ D, int *__restrict__ flag,
-                                                 z64 *__restrict__ A) {
+// The elimination itself, by the GJB x GJB threads of a CTA: blk[r * ld + c]
+// (r, c < b) is the block, read through L2 (other SMs may have written it).
+__device__ void gjb_block_inverse(int b, const z64 *__restrict__ blk, int64_t ld, z64 *__restrict__ D,
+                                  int *__restrict__ flag) {
     __shared__ z64 buf[2][GJB][GJB + 1];
     __shared__ z64 nrow[GJB];   // row k of the next copy: pivot row times 1/pivot, 1/pivot at k
     __shared__ z64 s_pinv;
     __shared__ int perm[GJB];
     __shared__ int s_p;
     __shared__ double s_amax;
-    const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
-    Rw += (int64_t)t * b * n;
-    D += (int64_t)t * GJB * GJB;
-    A += (int64_t)t * n * n;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int r = tid / GJB, c = tid % GJB;
-    buf[0][r][c] = (r < b && c < b) ? Rw[(int64_t)r * n + k0 + c] : z64(0.0, 0.0);
-    for (int idx = tid; idx < n * b; idx += blockDim.x) A[(int64_t)(idx / b) * n + k0 + idx % b] = z64(0.0, 0.0);
+    if (r < b && c < b) {
+        const double2 v = __ldcg(reinterpret_cast<const double2 *>(blk + (int64_t)r * ld + c));
+        buf[0][r][c] = z64(v.x, v.y);
+    } else {
+        buf[0][r][c] = z64(0.0, 0.0);
+    }
     __syncthreads();
     if (tid < 32) {
         double m = 0.0;
@@ -932,6 +937,218 @@ __global__ void __launch_bounds__(GJB * GJB) k_gjb_inv(int n, int k0, int b, con
     D[r * GJB + c] = (r < b && c < b) ? buf[cur][r][colsrc[c]] : z64(0.0, 0.0);
 }
 
+__global__ void __launch_bounds__(GJB * GJB) k_gjb_inv(int n, int k0, int b, const z64 *__restrict__ Rw,
+                                                 z64 *__restrict__ D, int *__restrict__ flag,
+                                                 z64 *__restrict__ A) {
+    const int t = blockIdx.x;
+    Rw += (int64_t)t * b * n;
+    D += (int64_t)t * GJB * GJB;
+    A += (int64_t)t * n * n;
+    for (int idx = threadIdx.x; idx < n * b; idx += blockDim.x)
+        A[(int64_t)(idx / b) * n + k0 + idx % b] = z64(0.0, 0.0);
+    gjb_block_inverse(b, Rw + k0, n, D, flag);
+}
+
+// All block steps of the blocked Gauss-Jordan inverse in one cooperative
+// launch (nbatch matrices, in place).  Before the first step CTA t inverts
+// the first diagonal block of matrix t and every CTA copies its share of the
+// first column block; then per block step K, two phases separated by the
+// bounded grid barrier of k_gj_persistent:
+//   (B) Rwp = D_K A[K, :] (b x n) by 16 x 8 tiles staged in shared memory;
+//   (C) every 32 x 32 tile of A: A[K, K] = D_K, A[K, j] = Rwp[:, j],
+//       A[i, K] = -C_K[i, :] D_K, A[i, j] -= C_K[i, :] Rwp[:, j] for i, j outside
+//       K (complex products in three real multiplications: t1 = sum re re,
+//       t2 = sum im im, t3 = sum (re + im)(re + im)); the owner of a tile that
+//       holds columns of block K + 1 copies their new values into C_{K+1}.
+// Look-ahead: CTA t copies block K + 1 of matrix t in phase B (before any
+// update of this step), forms its updated values in phase C with the same
+// arithmetic as the tile update (so the same bits) and inverts it into
+// D_{K+1}, while the other CTAs update every tile: the serial inverse runs
+// beside the update instead of between two barriers.  C and D are
+// double-buffered by the parity of K; Sb holds, per matrix, the old block and
+// its update.
+// Buffers written by other SMs are read through L2.  *flag as k_gjb_inv.
+__global__ void __launch_bounds__(256, 2) k_gjb_persistent(int n, int nbatch, z64 *__restrict__ A, z64 *__restrict__ Cb,
+                                                            z64 *__restrict__ Rwp, z64 *__restrict__ Db,
+                                                            z64 *__restrict__ Sb, int *__restrict__ flag,
+                                                            unsigned *__restrict__ bar, int *__restrict__ err,
+                                                            int *__restrict__ smids, unsigned *__restrict__ tilectr) {
+    __shared__ double sC[3][32][GJB + 1];   // 32 rows of C: re, im, re + im
+    __shared__ double sR[3][GJB][32 + 1];   // b rows of the right operand (Rwp, or D in the columns of K)
+    __shared__ int s_abort, s_idle, s_tile;
+    if (threadIdx.x == 0) s_abort = 0;
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    if (blockIdx.x < nbatch && threadIdx.x == 0) smids[blockIdx.x] = (int)smid;   // read after the first barrier
+    unsigned g = 0;
+    const int64_t nn = (int64_t)n * n;
+    const int tn = (n + 31) / 32;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t csz = (int64_t)nbatch * n * GJB, dsz = (int64_t)nbatch * GJB * GJB;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    auto ld2 = [](const z64 *p) {
+        const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+        return z64(v.x, v.y);
+    };
+    // before the first step: C_0 and D_0
+    {
+        const int b = min(GJB, n);
+        for (int64_t idx = gtid; idx < (int64_t)nbatch * n * b; idx += nthr) {
+            const int t = (int)(idx / ((int64_t)n * b));
+            const int64_t rem = idx - (int64_t)t * n * b, i = rem / b, l = rem - i * b;
+            Cb[((int64_t)t * n + i) * GJB + l] = ld2(A + t * nn + i * n + l);
+        }
+        if (blockIdx.x < nbatch) gjb_block_inverse(b, A + blockIdx.x * nn, n, Db + (int64_t)blockIdx.x * GJB * GJB, flag);
+        if (!gj_grid_sync(bar, bar + 1, gridDim.x, g, &s_abort, err)) return;
+    }
+    // a CTA that shares its SM with a look-ahead CTA takes no tiles, so that the
+    // serial inverse has the SM's FP64 pipes to itself
+    if (threadIdx.x == 0) {   // (with more than 4 CTAs per look-ahead CTA, so others remain for the tiles)
+        int idle = 0;
+        for (int t = 0; t < nbatch && blockIdx.x >= nbatch && (int)gridDim.x > 4 * nbatch; ++t)
+            idle |= __ldcg(smids + t) == (int)smid;
+        s_idle = idle;
+    }
+    __syncthreads();
+    const bool idle = s_idle != 0;
+    for (int k0 = 0, par = 0; k0 < n; k0 += GJB, par ^= 1) {
+        const int b = min(GJB, n - k0);
+        const int kn = k0 + GJB, bn = min(GJB, n - kn);   // block K + 1 (bn <= 0: none)
+        const z64 *Ck = Cb + par * csz, *Dk = Db + par * dsz;
+        z64 *Cn = Cb + (par ^ 1) * csz, *Dn = Db + (par ^ 1) * dsz;
+        // (B): tiles of 16 rows x 8 columns, one output per thread of the first 128
+        {
+            const int tn8 = (n + 7) / 8;
+            for (int tile = blockIdx.x; tile < nbatch * tn8; tile += gridDim.x) {
+                const int t = tile / tn8, j0 = (tile - t * tn8) * 8;
+                const z64 *At = A + t * nn, *Dt = Dk + (int64_t)t * GJB * GJB;
+                __syncthreads();
+                {   // D_K into sC[0..2][l][m], the row block tile into sR[0..2][m][c] (re, im, re + im)
+                    const int l = threadIdx.x / 16, m = threadIdx.x % 16;
+                    const z64 d = (l < b && m < b) ? ld2(Dt + l * GJB + m) : z64(0.0, 0.0);
+                    sC[0][l][m] = d.re;
+                    sC[1][l][m] = d.im;
+                    sC[2][l][m] = d.re + d.im;
+                    if (threadIdx.x < GJB * 8) {
+                        const int mm = threadIdx.x / 8, c = threadIdx.x % 8, j = j0 + c;
+                        const z64 v = (mm < b && j < n) ? ld2(At + (int64_t)(k0 + mm) * n + j) : z64(0.0, 0.0);
+                        sR[0][mm][c] = v.re;
+                        sR[1][mm][c] = v.im;
+                        sR[2][mm][c] = v.re + v.im;
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x < GJB * 8) {
+                    const int l = threadIdx.x / 8, c = threadIdx.x % 8, j = j0 + c;
+                    if (l < b && j < n) {
+                        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+#pragma unroll
+                        for (int m = 0; m < GJB; ++m) {
+                            t1 = fma(sC[0][l][m], sR[0][m][c], t1);
+                            t2 = fma(sC[1][l][m], sR[1][m][c], t2);
+                            t3 = fma(sC[2][l][m], sR[2][m][c], t3);
+                        }
+                        Rwp[((int64_t)t * GJB + l) * n + j] = z64(t1 - t2, t3 - t1 - t2);
+                    }
+                }
+            }
+        }
+        if (blockIdx.x < nbatch && bn > 0) {   // block K + 1 before this step's update
+            const int r = threadIdx.x / GJB, c = threadIdx.x % GJB;
+            if (r < bn && c < bn)
+                Sb[(int64_t)blockIdx.x * 2 * GJB * GJB + r * GJB + c] =
+                    ld2(A + blockIdx.x * nn + (int64_t)(kn + r) * n + kn + c);
+        }
+        if (!gj_grid_sync(bar, bar + 1, gridDim.x, g, &s_abort, err)) return;
+        // (C): the update of one tile; CTA t < nbatch takes the diagonal tile of
+        // matrix t holding block K + 1 and then inverts that block
+        // C[i, :] Rwp[:, j] from the staging, one order of operations for every caller
+        auto cprod = [&](int ri, int cj) {
+            double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+#pragma unroll
+            for (int l = 0; l < GJB; ++l) {
+                t1 = fma(sC[0][ri][l], sR[0][l][cj], t1);
+                t2 = fma(sC[1][ri][l], sR[1][l][cj], t2);
+                t3 = fma(sC[2][ri][l], sR[2][l][cj], t3);
+            }
+            return z64(t1 - t2, t3 - t1 - t2);
+        };
+        auto stage = [&](int t, int i0, int j0) {   // C rows i0.., right-operand columns j0.. (32 each)
+            const z64 *Ct = Ck + (int64_t)t * n * GJB, *Rt = Rwp + (int64_t)t * GJB * n, *Dt = Dk + (int64_t)t * GJB * GJB;
+            __syncthreads();   // the previous reads of the staging are done
+            for (int e = threadIdx.x; e < 32 * GJB; e += blockDim.x) {
+                const int rr = e / GJB, l = e - rr * GJB, i = i0 + rr;
+                const z64 v = (i < n && l < b) ? ld2(Ct + (int64_t)i * GJB + l) : z64(0.0, 0.0);
+                sC[0][rr][l] = v.re;
+                sC[1][rr][l] = v.im;
+                sC[2][rr][l] = v.re + v.im;
+            }
+            for (int e = threadIdx.x; e < GJB * 32; e += blockDim.x) {
+                const int l = e / 32, cc = e - l * 32, j = j0 + cc;
+                z64 v(0.0, 0.0);
+                if (l < b && j < n)
+                    v = (j >= k0 && j < k0 + b) ? ld2(Dt + l * GJB + (j - k0)) : ld2(Rt + (int64_t)l * n + j);
+                sR[0][l][cc] = v.re;
+                sR[1][l][cc] = v.im;
+                sR[2][l][cc] = v.re + v.im;
+            }
+            __syncthreads();
+        };
+        const int dtile = bn > 0 ? kn / 32 : -1;
+        auto update = [&](int t, int bi, int bj) {
+            const int i0 = bi * 32, j0 = bj * 32;
+            z64 *At = A + t * nn;
+            const z64 *Rt = Rwp + (int64_t)t * GJB * n, *Dt = Dk + (int64_t)t * GJB * GJB;
+            z64 *Cnt = Cn + (int64_t)t * n * GJB;
+            stage(t, i0, j0);
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int ri = ty + 16 * rr, cj = tx + 16 * cc, i = i0 + ri, j = j0 + cj;
+                    if (i >= n || j >= n) continue;
+                    const bool ki = i >= k0 && i < k0 + b, kj = j >= k0 && j < k0 + b;
+                    z64 *out = At + (int64_t)i * n + j;
+                    z64 v;
+                    if (ki) {
+                        v = kj ? ld2(Dt + (i - k0) * GJB + (j - k0)) : ld2(Rt + (int64_t)(i - k0) * n + j);
+                    } else {
+                        const z64 prod = cprod(ri, cj);
+                        v = kj ? -prod : ld2(out) - prod;
+                    }
+                    *out = v;
+                    if (j >= kn && j < kn + bn) Cnt[(int64_t)i * GJB + (j - kn)] = v;
+                }
+            }
+        };
+        if (blockIdx.x < nbatch) {
+            if (dtile >= 0) {   // block K + 1 after this step, from its copy, then its inverse
+                const int t = blockIdx.x, i0 = (kn / 32) * 32, off = kn - i0;
+                z64 *S = Sb + (int64_t)t * 2 * GJB * GJB;
+                stage(t, i0, i0);
+                const int r = threadIdx.x / GJB, c = threadIdx.x % GJB;
+                if (r < bn && c < bn) S[GJB * GJB + r * GJB + c] = S[r * GJB + c] - cprod(off + r, off + c);
+                __threadfence();   // the block in L2, where the inverse reads it
+                __syncthreads();
+                gjb_block_inverse(bn, S + GJB * GJB, GJB, Dn + (int64_t)t * GJB * GJB, flag);
+            }
+        } else if (!idle) {   // tiles from this step's counter
+            const int ntc = nbatch * tn * tn;
+            for (;;) {
+                __syncthreads();   // s_tile of the previous claim has been read
+                if (threadIdx.x == 0) s_tile = (int)atomicAdd(tilectr + k0 / GJB, 1u);
+                __syncthreads();
+                const int tile = s_tile;
+                if (tile >= ntc) break;
+                const int t = tile / (tn * tn), rem = tile - t * tn * tn, bi = rem / tn, bj = rem - bi * tn;
+                update(t, bi, bj);
+            }
+        }
+        if (!gj_grid_sync(bar, bar + 1, gridDim.x, g, &s_abort, err)) return;
+    }
+}
+
 // row block k of A <- Rwp (b x n); then A_kk <- D
 __global__ void k_gjb_place(int n, int k0, int b, const z64 *__restrict__ Rwp, const z64 *__restrict__ D,
                             z64 *__restrict__ A) {
@@ -999,7 +1216,46 @@ bool gj_blocked(int64_t n, int nbatch, const z64 *Aorig, z64 *inv, cudaStream_t 
     CBFM_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
     const unsigned nbk = (unsigned)std::min<int64_t>((n * GJB + 255) / 256, 1024);
     GemmSite site_("site:gauss_jordan");
-    for (int64_t k0 = 0; k0 < n; k0 += GJB) {
+    // every block step in one cooperative launch (the per-step launches below remain
+    // for a device without cooperative launch)
+    int dev = 0, coop = 0, occ = 0;
+    CBFM_CUDA(cudaGetDevice(&dev));
+    CBFM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gjb_persistent, 256, 0));
+    const int64_t tn = (n + 31) / 32;
+    const bool persistent = coop && occ > 0 && (int64_t)occ * sm_count() > nbatch;
+    if (persistent) {
+        DevBuf<unsigned> bar, tilectr;
+        DevBuf<int> perr, smids;
+        DevBuf<z64> Cb, Db, Sb;   // C and D, double-buffered; the look-ahead block
+        Cb.alloc((size_t)2 * nbatch * n * GJB);
+        Db.alloc((size_t)2 * nbatch * GJB * GJB);
+        Sb.alloc((size_t)2 * nbatch * GJB * GJB);
+        bar.alloc(2);
+        perr.alloc(1);
+        smids.alloc(nbatch);
+        const int64_t nsteps = (n + GJB - 1) / GJB;
+        tilectr.alloc(nsteps);
+        CBFM_CUDA(cudaMemsetAsync(tilectr.p, 0, sizeof(unsigned) * nsteps, st));
+        CBFM_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+        CBFM_CUDA(cudaMemsetAsync(perr.p, 0, sizeof(int), st));
+        const unsigned grid =
+            (unsigned)std::min<int64_t>((int64_t)nbatch * (tn * tn + 1), (int64_t)occ * sm_count());
+        int ni = (int)n, nb = nbatch;
+        z64 *Ap = inv, *Cq = Cb.p, *Rq = Rwp, *Dq = Db.p, *Sq = Sb.p;
+        void *args[] = {&ni, &nb, &Ap, &Cq, &Rq, &Dq, &Sq, &flag.p, &bar.p, &perr.p, &smids.p, &tilectr.p};
+        prof_add_work("k_gjb_persistent", 6.0 * nbatch * (double)n * n * n, 16.0 * nbatch * (double)n * n * 2);
+        {
+            ProfScope ps_("k_gjb_persistent", st);
+            CBFM_CUDA(cudaLaunchCooperativeKernel((const void *)k_gjb_persistent, dim3(grid), dim3(256), args, 0, st));
+            launched("k_gjb_persistent");
+        }
+        int herr = 0;
+        CBFM_CUDA(cudaMemcpyAsync(&herr, perr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CBFM_CUDA(cudaStreamSynchronize(st));
+        if (herr) throw Fail{CBFM_ETIMEOUT, "Gauss-Jordan: a grid barrier wait expired"};
+    }
+    for (int64_t k0 = 0; !persistent && k0 < n; k0 += GJB) {
         const int b = (int)std::min<int64_t>(GJB, n - k0);
         k_gjb_panels<<<dim3(nbk, nbatch), 256, 0, st>>>((int)n, (int)k0, b, inv, C.p, Rw.p);
         launched("k_gjb_panels");
@@ -1068,6 +1324,7 @@ void gemm_grouped(const std::vector<GemmDesc> &g, int opA, int opB, const cx<T> 
             by += (double)(d.M * d.K + d.K * d.N + d.M * d.N) * sizeof(cx<T>);
         }
         prof_add_work(sizeof(T) == 8 ? "k_gemm_z64" : "k_gemm_c32", fl, by);
+        if (sizeof(T) == 8) prof_add_work(g_gemm_site ? g_gemm_site : "site:other", fl, by);   // per solver step
     }
     if constexpr (sizeof(T) == 8) {
         gemm_sk(g, opA, opB, A, B, C, accumulate, st, alpha);
