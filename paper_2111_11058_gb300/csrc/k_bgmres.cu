@@ -343,13 +343,13 @@ __global__ void __launch_bounds__(PCHOL_MAX) k_trinv(int m, const z64 *__restric
 }
 
 // X (r x m): X[i][perm[l]] = Rinv[l][i] (l <= i < r), else 0  -> Q = X W for row vectors W.
-// Launched as a single block (r x m <= 65536), so zeroing and filling are ordered by one barrier.
+// The zeroing is a launch of its own (k_zero2d) before this one; consecutive
+// threads read consecutive entries of a row of Rinv.
 __global__ void k_make_x(int m, int r, const int *__restrict__ perm, const z64 *__restrict__ Rinv,
                          z64 *__restrict__ X) {
-    for (int64_t idx = threadIdx.x; idx < (int64_t)r * m; idx += blockDim.x) X[idx] = z64(0, 0);
-    __syncthreads();
-    for (int64_t idx = threadIdx.x; idx < (int64_t)r * r; idx += blockDim.x) {
-        int i = (int)(idx / r), l = (int)(idx % r);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)r * r;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(idx / r), i = (int)(idx % r);
         if (l <= i) X[(int64_t)i * m + perm[l]] = Rinv[(int64_t)l * m + i];
     }
 }
@@ -485,24 +485,33 @@ __global__ void k_add32to64(int64_t n, const c32 *__restrict__ X, z64 *__restric
 
 // ||M - I||_F of a Hermitian m x m matrix from its upper triangle (one block;
 // fixed summation order)
-__global__ void __launch_bounds__(256) k_gram_dev(int m, const z64 *__restrict__ M, double *__restrict__ out) {
-    __shared__ double part[8];
+// Partial sums of ||M - I||_F^2 over the upper triangle (off-diagonal entries
+// counted twice): CTA c takes rows a = c, c + GD_CTAS, ... and writes part[c];
+// k_gram_dev_sum adds the GD_CTAS partials in a fixed order (same bits on
+// every run, so the pass-2 decision does not depend on scheduling).
+constexpr int GD_CTAS = 32;
+__global__ void __launch_bounds__(256) k_gram_dev(int m, const z64 *__restrict__ M, double *__restrict__ part) {
+    __shared__ double wp[8];
     double s = 0.0;
-    for (int idx = threadIdx.x; idx < m * m; idx += 256) {
-        const int a = idx / m, b = idx % m;
-        if (a > b) continue;
-        z64 v = M[idx];
-        if (a == b) v.re -= 1.0;
-        s += (a == b ? 1.0 : 2.0) * (v.re * v.re + v.im * v.im);
-    }
+    for (int a = blockIdx.x; a < m; a += gridDim.x)
+        for (int b = a + threadIdx.x; b < m; b += blockDim.x) {
+            z64 v = M[(int64_t)a * m + b];
+            if (a == b) v.re -= 1.0;
+            s += (a == b ? 1.0 : 2.0) * (v.re * v.re + v.im * v.im);
+        }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    if ((threadIdx.x & 31) == 0) wp[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < 8; ++w) t += part[w];
-        *out = sqrt(t);
+        for (int w = 0; w < 8; ++w) t += wp[w];
+        part[blockIdx.x] = t;
     }
+}
+__global__ void k_gram_dev_sum(const double *__restrict__ part, double *__restrict__ out) {
+    double s = threadIdx.x < GD_CTAS ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *out = sqrt(s);
 }
 
 // M[a][b] = conj(M[b][a]) for a > b: the lower triangle of a Hermitian matrix from its upper one
@@ -585,8 +594,10 @@ constexpr double GS_KEEP = 0.1;
 
 // ||M - I||_F of the m x m Gram matrix in ctx.M (host sync).
 double gram_dev(Ctx &c, int m) {
-    k_gram_dev<<<1, 256, 0, c.st>>>(m, c.M.p, c.dev.p);
+    k_gram_dev<<<GD_CTAS, 256, 0, c.st>>>(m, c.M.p, c.dev.p + 1);
     launched("k_gram_dev");
+    k_gram_dev_sum<<<1, 32, 0, c.st>>>(c.dev.p + 1, c.dev.p);
+    launched("k_gram_dev_sum");
     double h = 0.0;
     CBFM_CUDA(cudaMemcpyAsync(&h, c.dev.p, sizeof(double), cudaMemcpyDeviceToHost, c.st));
     CBFM_CUDA(cudaStreamSynchronize(c.st));
@@ -737,7 +748,9 @@ int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double
     gemm_grouped<double>(upper_tiles(GemmDesc{m, m, n, 0, n, 0, n, 0, m}, 3, 1), 3, 1, W, W, c.M.p, false, c.st);
     const int r = pchol(c, m, tol, true);
     if (r == 0) return 0;
-    k_make_x<<<1, 256, 0, c.st>>>(m, r, c.perm.p, c.Rinv.p, c.X.p);
+    k_zero2d<<<nb((int64_t)r * m), 256, 0, c.st>>>(r, m, c.X.p, m);
+    launched("k_zero2d");
+    k_make_x<<<nb((int64_t)r * r), 256, 0, c.st>>>(m, r, c.perm.p, c.Rinv.p, c.X.p);
     launched("k_make_x");
     k_zero2d<<<nb((int64_t)r * m), 256, 0, c.st>>>(r, m, c.Rf.p, m);
     launched("k_zero2d");
@@ -763,7 +776,9 @@ int cholqr2_rows(Ctx &c, z64 *W, int m, int64_t n, z64 *Qdst, z64 *Rfull, double
     const int r2 = pchol(c, r, 0.0, false);
     if (r2 != r) throw Fail{CBFM_ESINGULAR, "block GMRES: second Cholesky QR pass lost rank"};
     // Q = Rinv2^T Q1 : X2[i][l] = Rinv2[l][i]  (identity permutation)
-    k_make_x<<<1, 256, 0, c.st>>>(r, r, c.perm.p, c.Rinv.p, c.X.p);
+    k_zero2d<<<nb((int64_t)r * r), 256, 0, c.st>>>(r, r, c.X.p, r);
+    launched("k_zero2d");
+    k_make_x<<<nb((int64_t)r * r), 256, 0, c.st>>>(r, r, c.perm.p, c.Rinv.p, c.X.p);
     launched("k_make_x");
     gemm_grouped<double>(lower_a_tiles(GemmDesc{r, n, r, 0, r, 0, n, 0, n}, 0, 0), 0, 0, c.X.p, c.T1.p, Qdst, false,
                          c.st);
@@ -866,7 +881,7 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
     CBFM_CUDA(cudaMemsetAsync(c.err.p, 0, sizeof(int), st));
     c.rnrm.alloc(PCHOL_MAX);
     c.scale.alloc(PCHOL_MAX);
-    c.dev.alloc(1);
+    c.dev.alloc(1 + GD_CTAS);   // the deviation and its per-CTA partials
     DevBuf<z64> V, W, HcT, Hn, Qh, Rh, Gv, E1S, Rv, Y, Z, tmp, tmp2, RinvBlk, Rw, Bm, Rout;
     DevBuf<double> bnorm, rnorm, rnorm0, fro_col;
     DevBuf<int> dmask, dsel;
