@@ -22,8 +22,9 @@
 //   The minus sign on T is the reading under which the paper's block matrix
 //   describes the exp(+j w t) problem.  Blocks are combined into
 //   Ks = K1 + K2, Ta = -(eta1 T1 + eta2 T2), Tb = T1/eta1 + T2/eta2.
-// Stage 2, near pairs (k_near_blocks, one warp per pair; FP64 for the closed
-//   forms and all sums, FP32 for the smooth remainders on the mixed path): 1/R, 1/R^3 and k^2/(2R)
+// Stage 2, near pairs (k_near_blocks, two pairs per warp; FP64 for the closed
+//   forms, and on the mixed path FP32 for the smooth remainders and the outer
+//   test-point quadrature): 1/R, 1/R^3 and k^2/(2R)
 //   integrated in closed form over the trial triangle (Wilton et al. 1984,
 //   Graglia 1993 edge sums), bounded remainders by the 7-point rule, blocks
 //   symmetrised L(t,s) = (L~(t,s) + L~(s,t)^T)/2; K of a triangle with itself is 0.
@@ -266,42 +267,50 @@ constexpr int NEAR_MOM = 15;   // complex moments per (orientation, medium)
 // Work of one near pair, counted from the operations of near_pair2 with each
 // square root, logarithm, arctangent, sine/cosine pair and exponential as one:
 // per orientation and test point (14 lanes) the closed-form potentials of the
-// trial triangle (3 edges x 50 + 40, the vertex distances formed once) and
-// the trial-point geometry (7 x 10) in FP64, and for each medium the 7
-// remainder evaluations with their weighted sums (7 x 60, FP32 on the mixed
-// path) plus S0, Sr, Wv and the 15 moments (90, FP64); then the moment
+// trial triangle (3 edges x 50 + 40, the vertex distances formed once), the
+// trial-point geometry (7 x 10) and their sums into S0, Sr, Wv (2 media x 12),
+// FP64 on both paths; the outer quadrature, FP64 on the FP64 path and FP32 on
+// the mixed one: for each medium the 15 test-point moments (90), their
 // reductions (15 complex x 2 media x 3 shuffle steps on 16 lanes) and the 9
-// entries (2 orientations x 2 media x 60), FP64.
-// FP64 operations of the mixed form; the FP64 form also counts the remainders.
-constexpr double NEAR_FP64_OPS_MIXED = 14 * (190 + 70 + 2 * 90) + 16 * 15 * 2 * 3 * 2 + 9 * 2 * 2 * 60;
+// entries (2 orientations x 2 media x 60); and the 7 remainder evaluations with
+// their weighted sums per medium (7 x 60), likewise.
+constexpr double NEAR_FP64_OPS_CLOSED = 14 * (190 + 70 + 2 * 12);
+constexpr double NEAR_OUTER_OPS = 14 * 2 * 90 + 16 * 15 * 2 * 3 * 2 + 9 * 2 * 2 * 60;
 constexpr double NEAR_REM_OPS = 14 * 2 * 7 * 60;
+// FP64 operations per near pair of the near-pair kernel in type T
+template <typename T>
+constexpr double near_fp64_ops() {
+    return NEAR_FP64_OPS_CLOSED + (sizeof(T) == 8 ? NEAR_OUTER_OPS + NEAR_REM_OPS : 0.0);
+}
 
 template <typename T>
 __device__ __forceinline__ void near_pair2(int t, int s, int nt, const double *__restrict__ rec, const Media &md,
-                                           cx<T> *__restrict__ Zloc, z64 (*sm)[2][2][NEAR_MOM],
+                                           cx<T> *__restrict__ Zloc, cx<T> (*sm)[2][2][NEAR_MOM],
                                            cx<T> *__restrict__ blk = nullptr) {
     // (t, s): the pair of this lane's slot (t < 0: none); every lane reads only
     // its own slot's mesh, and all 32 lanes reach the shuffles and barriers
     const int lane = threadIdx.x & 31;
     const int slot = lane >> 4, o = (lane >> 3) & 1, p = lane & 7;
     __syncwarp();   // the slot's previous readers are done
-    z64 mom[2][NEAR_MOM];
+    // the test-point moments and the entries are the outer quadrature of the
+    // closed forms: in T (FP32 on the mixed path, like the remainders)
+    cx<T> mom[2][NEAR_MOM];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int c = 0; c < NEAR_MOM; ++c) mom[i][c] = z64(0, 0);
+        for (int c = 0; c < NEAR_MOM; ++c) mom[i][c] = cx<T>(0, 0);
     if (p < 7 && t >= 0) {
         const double *A = rec + (int64_t)(o == 0 ? t : s) * TRI_REC;
         const double *B = rec + (int64_t)(o == 0 ? s : t) * TRI_REC;
         const double *r = A + TR_Q + 3 * p;
         double I1, Iv[3], I3[3];
         potentials(B + TR_P, r, I1, Iv, I3);
-        const double wp = A[TR_W + p];
-        const double rr[3] = {r[0] - A[TR_CEN], r[1] - A[TR_CEN + 1], r[2] - A[TR_CEN + 2]};
-        const double r2 = dot3(rr, rr);
+        const T wp = (T)A[TR_W + p];
+        const T rr[3] = {(T)(r[0] - A[TR_CEN]), (T)(r[1] - A[TR_CEN + 1]), (T)(r[2] - A[TR_CEN + 2])};
+        const T r2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
         // trial points: d = r - r', R, weights; shared by the two media.  On the
-        // mixed path the smooth remainders and their 7-point sums are FP32 and
-        // only the closed forms (and the sums with them) FP64.
+        // mixed path the smooth remainders, their 7-point sums and the moments
+        // are FP32 and only the closed forms FP64.
         T dq[7][3], Rq[7], wq[7];
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
@@ -334,14 +343,15 @@ __device__ __forceinline__ void near_pair2(int t, int s, int nt, const double *_
                     hw[d] += hs * dq[q][d];
                 }
             }
-            const z64 S0 = z64(I1 / (4.0 * PI) + (double)g0.re, (double)g0.im);
-            z64 Sr[3], Wv[3];
+            const cx<T> S0((T)(I1 / (4.0 * PI)) + g0.re, g0.im);
+            cx<T> Sr[3], Wv[3];
             for (int d = 0; d < 3; ++d) {
-                Sr[d] = z64(Iv[d] / (4.0 * PI) + (double)gr[d].re, (double)gr[d].im);
-                Wv[d] = z64(-I3[d] / (4.0 * PI), 0) + kk * (Iv[d] / (8.0 * PI)) + z64((double)hw[d].re, (double)hw[d].im);
+                Sr[d] = cx<T>((T)(Iv[d] / (4.0 * PI)) + gr[d].re, gr[d].im);
+                const z64 kI = kk * (Iv[d] / (8.0 * PI));
+                Wv[d] = cx<T>((T)(kI.re - I3[d] / (4.0 * PI)), (T)kI.im) + hw[d];
             }
-            z64 *m = mom[med];
-            const z64 wS0 = wp * S0;
+            cx<T> *m = mom[med];
+            const cx<T> wS0 = wp * S0;
             m[0] = wS0;
             m[1] = rr[0] * wS0; m[2] = rr[1] * wS0; m[3] = rr[2] * wS0;
             m[4] = r2 * wS0;
@@ -374,33 +384,33 @@ __device__ __forceinline__ void near_pair2(int t, int s, int nt, const double *_
     if (e >= 9 || t < 0) return;
     // lane (slot, e = 3 a + b): entry (a, b) of (t, s) = 1/2 [L~_o0(a, b) + L~_o1(b, a)]
     const int a = e / 3, b = e % 3;
-    z64 ks(0, 0), ta(0, 0), tb(0, 0);
+    cx<T> ks(0, 0), ta(0, 0), tb(0, 0);
 #pragma unroll
     for (int oo = 0; oo < 2; ++oo) {
         const double *A = rec + (int64_t)(oo == 0 ? t : s) * TRI_REC;
         const double *B = rec + (int64_t)(oo == 0 ? s : t) * TRI_REC;
         const int ia = oo == 0 ? a : b, ib = oo == 0 ? b : a;   // test vertex, trial vertex
-        double P[3], Q[3];
+        T P[3], Q[3];
         for (int d = 0; d < 3; ++d) {
-            P[d] = A[TR_P + 3 * ia + d] - A[TR_CEN + d];
-            Q[d] = B[TR_P + 3 * ib + d] - A[TR_CEN + d];
+            P[d] = (T)(A[TR_P + 3 * ia + d] - A[TR_CEN + d]);
+            Q[d] = (T)(B[TR_P + 3 * ib + d] - A[TR_CEN + d]);
         }
-        const double cc = 0.5 * A[TR_C + ia] * B[TR_C + ib];
-        const double PQ = dot3(P, Q);
-        const double PpQ[3] = {P[0] + Q[0], P[1] + Q[1], P[2] + Q[2]};
-        const double QmP[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
+        const T cc = (T)(0.5 * A[TR_C + ia] * B[TR_C + ib]);
+        const T PQ = P[0] * Q[0] + P[1] * Q[1] + P[2] * Q[2];
+        const T PpQ[3] = {P[0] + Q[0], P[1] + Q[1], P[2] + Q[2]};
+        const T QmP[3] = {Q[0] - P[0], Q[1] - P[1], Q[2] - P[2]};
         // P x Q: P.(MW x Q) = MW.(Q x P)
-        const double QxP[3] = {Q[1] * P[2] - Q[2] * P[1], Q[2] * P[0] - Q[0] * P[2], Q[0] * P[1] - Q[1] * P[0]};
+        const T QxP[3] = {Q[1] * P[2] - Q[2] * P[1], Q[2] * P[0] - Q[0] * P[2], Q[0] * P[1] - Q[1] * P[0]};
 #pragma unroll
         for (int med = 0; med < 2; ++med) {
-            const z64 *m = sm[slot][oo][med];
-            const z64 k = med == 0 ? z64(md.k1r, md.k1i) : z64(md.k2r, md.k2i);
-            const z64 eta = med == 0 ? z64(md.e1r, md.e1i) : z64(md.e2r, md.e2i);
-            const z64 f4k2 = med == 0 ? z64(md.f1r, md.f1i) : z64(md.f2r, md.f2i);   // 4 / k^2
-            const z64 ieta = med == 0 ? z64(md.i1r, md.i1i) : z64(md.i2r, md.i2i);   // 1 / eta
-            z64 br = m[8] + m[4] - (P[0] * m[5] + P[1] * m[6] + P[2] * m[7]) -
-                     (PpQ[0] * m[1] + PpQ[1] * m[2] + PpQ[2] * m[3]) + PQ * m[0] - f4k2 * m[0];
-            const z64 Tv = cc * (z64(k.im, -k.re) * br);
+            const cx<T> *m = sm[slot][oo][med];
+            const cx<T> k = med == 0 ? cx<T>((T)md.k1r, (T)md.k1i) : cx<T>((T)md.k2r, (T)md.k2i);
+            const cx<T> eta = med == 0 ? cx<T>((T)md.e1r, (T)md.e1i) : cx<T>((T)md.e2r, (T)md.e2i);
+            const cx<T> f4k2 = med == 0 ? cx<T>((T)md.f1r, (T)md.f1i) : cx<T>((T)md.f2r, (T)md.f2i);   // 4 / k^2
+            const cx<T> ieta = med == 0 ? cx<T>((T)md.i1r, (T)md.i1i) : cx<T>((T)md.i2r, (T)md.i2i);   // 1 / eta
+            cx<T> br = m[8] + m[4] - (P[0] * m[5] + P[1] * m[6] + P[2] * m[7]) -
+                       (PpQ[0] * m[1] + PpQ[1] * m[2] + PpQ[2] * m[3]) + PQ * m[0] - f4k2 * m[0];
+            const cx<T> Tv = cc * (cx<T>(k.im, -k.re) * br);
             ta += -eta * Tv;
             tb += Tv * ieta;
             if (t != s)
@@ -408,10 +418,10 @@ __device__ __forceinline__ void near_pair2(int t, int s, int nt, const double *_
                             QxP[2] * m[11]);
         }
     }
-    const z64 v[3] = {ks, ta, tb};
+    const cx<T> v[3] = {ks, ta, tb};
     const int64_t plane = (int64_t)nt * nt;
     for (int op = 0; op < 3; ++op) {
-        cx<T> val((T)v[op].re, (T)v[op].im);
+        const cx<T> val = v[op];
         if (blk) {   // compact form: the (t, s) block of this pair; (s, t) is its transpose
             blk[op * 9 + 3 * a + b] = val;
             continue;
@@ -575,7 +585,7 @@ __global__ void __launch_bounds__(32 * far_warps<T>(), sizeof(T) == 4 ? 3 : 4)
 // belong to different meshes), grid-stride over pair couples.
 template <typename T>
 __global__ void __launch_bounds__(128) k_near_blocks(const AsmJob<T> *__restrict__ jobs, int njobs, int64_t npairs) {
-    __shared__ z64 sm_all[4][2][2][2][NEAR_MOM];
+    __shared__ cx<T> sm_all[4][2][2][2][NEAR_MOM];
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t ncouple = (npairs + 1) / 2;
     const int slot = (threadIdx.x >> 4) & 1;
@@ -615,7 +625,8 @@ __global__ void __launch_bounds__(256) k_mirror(const AsmJob<T> *__restrict__ jo
     for (int64_t l = blockIdx.x; l < ntiles; l += gridDim.x) {
         const AsmJob<T> &J = jobs[find_job<T, &AsmJob<T>::mir0>(jobs, njobs, l)];
         const int64_t loc = l - J.mir0;
-        int64_t bi = (int64_t)((sqrt(8.0 * (double)loc + 1.0) - 1.0) * 0.5);
+        // FP32 estimate (FP64 issue is scarce here), corrected to the exact row by the loops
+        int64_t bi = (int64_t)((sqrtf(8.0f * (float)loc + 1.0f) - 1.0f) * 0.5f);
         while ((bi + 1) * (bi + 2) / 2 <= loc) ++bi;
         while (bi * (bi + 1) / 2 > loc) --bi;
         const int t0 = (int)bi * TM, s0 = (int)(loc - bi * (bi + 1) / 2) * TM;   // destination rows t, columns s
@@ -781,7 +792,7 @@ void assemble_rwg_batch(const std::vector<Mesh *> &ms, const std::vector<cx<T> *
         tuning_set(key, cands[bi]);
     }
     prof_add_work("k_far", far_flop, far_bytes);
-    prof_add_work("k_near_blocks", (double)npairs * (NEAR_FP64_OPS_MIXED + (sizeof(T) == 8 ? NEAR_REM_OPS : 0.0)),
+    prof_add_work("k_near_blocks", (double)npairs * near_fp64_ops<T>(),
                   (double)npairs * (2 * TRI_REC * sizeof(double) + 27 * sizeof(cx<T>)));
     if (npairs > 0) {
         int occ = 0;
@@ -842,7 +853,7 @@ void near_blocks_compact_t(const std::vector<Mesh *> &ms, const std::vector<cx<T
     CBFM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_near_blocks<T>, 128, 0));
     const unsigned grid =
         (unsigned)std::min<int64_t>((int64_t)std::max(1, occ) * sm_count(), ((npairs + 1) / 2 * 32 + 127) / 128);
-    prof_add_work("k_near_blocks", (double)npairs * (NEAR_FP64_OPS_MIXED + (sizeof(T) == 8 ? NEAR_REM_OPS : 0.0)),
+    prof_add_work("k_near_blocks", (double)npairs * near_fp64_ops<T>(),
                   (double)npairs * (2 * TRI_REC * sizeof(double) + 27 * sizeof(cx<T>)));
     {
         ProfScope ps_("k_near_blocks", st);
