@@ -174,6 +174,7 @@ constexpr int SK_T = 32, SK_K = 16;
 struct SkBatch {
     int ng;
     int G;                           // CTAs
+    int defer;                       // 1: cut tiles are summed by k_sk_reduce after the launch
     int64_t U;                       // units
     int64_t unit_off[GB_MAXG + 1];   // first unit of problem g
     int64_t tile_off[GB_MAXG + 1];   // first tile of problem g (index of its cut-tile counter)
@@ -193,16 +194,29 @@ __device__ __forceinline__ int sk_group(const SkBatch &bt, int64_t u) {
 __device__ __forceinline__ int64_t sk_first(int64_t c, const SkBatch &bt) { return c * bt.U / bt.G; }
 __device__ __forceinline__ int64_t sk_owner(int64_t u, const SkBatch &bt) { return ((u + 1) * bt.G - 1) / bt.U; }
 
-// The last CTA of a cut tile: C tile = alpha * (sum of the tile's slots in CTA order) (+ C)
+// The slot a CTA cc used for the tile starting at unit tu0: 0 if the tile is
+// where the CTA's units begin, else 1 (a CTA's last, cut tile).
+__device__ __forceinline__ int sk_slot(int64_t cc, int64_t tu0, const SkBatch &bt) {
+    return (sk_first(cc, bt) >= tu0) ? 0 : 1;
+}
+constexpr int SK_MAXP = 1024;   // pieces of a cut tile whose slots are looked up once per tile
+
+// The last CTA of a cut tile: C tile = alpha * (sum of the tile's slots in CTA order) (+ C).
+// Called by the whole CTA.
 __device__ __noinline__ void sk_sum_tile(const SkBatch &bt, int g, int64_t m0, int64_t n0, int64_t tu0, int64_t cf,
                                          int64_t cl, const z64 *part, z64 *C, int accumulate, double alpha) {
+    __shared__ unsigned char s_js[SK_MAXP];
     const GemmDesc &d = bt.d[g];
+    const int np = (int)(cl - cf + 1);
+    for (int q = threadIdx.x; q < np && q < SK_MAXP; q += blockDim.x) s_js[q] = (unsigned char)sk_slot(cf + q, tu0, bt);
+    __syncthreads();
     for (int e = threadIdx.x; e < SK_T * SK_T; e += blockDim.x) {
         const int64_t r = m0 + e / SK_T, col = n0 + e % SK_T;
         if (r >= d.M || col >= d.N) continue;
         z64 v(0, 0);
         for (int64_t cc = cf; cc <= cl; ++cc) {
-            const int jslot = (sk_first(cc, bt) >= tu0) ? 0 : 1;
+            const int q = (int)(cc - cf);
+            const int jslot = q < SK_MAXP ? s_js[q] : sk_slot(cc, tu0, bt);
             const double2 pv = __ldcg(reinterpret_cast<const double2 *>(part) + (2 * cc + jslot) * (SK_T * SK_T) + e);
             v += z64(pv.x, pv.y);
         }
@@ -211,6 +225,45 @@ __device__ __noinline__ void sk_sum_tile(const SkBatch &bt, int g, int64_t m0, i
         if (accumulate) *pc += v;
         else *pc = v;
     }
+}
+
+// The cut tiles of a deferred launch: CTA (tile, chunk) sums the tile's
+// slots in CTA order for SK_RCH of its entries, one entry per thread, so the
+// FP64 adds of a tile cut into many pieces are spread over many SMs.
+constexpr int SK_RCH = 128;
+__global__ void __launch_bounds__(SK_RCH) k_sk_reduce(const __grid_constant__ SkBatch bt, const z64 *__restrict__ part,
+                                                      z64 *__restrict__ C, int accumulate, double alpha) {
+    __shared__ unsigned char s_js[SK_MAXP];
+    constexpr int nch = SK_T * SK_T / SK_RCH;
+    const int64_t T = blockIdx.x / nch;
+    const int e = (int)(blockIdx.x % nch) * SK_RCH + threadIdx.x;
+    int g = 0;
+    for (int lo = 0, hi = bt.ng - 1; lo <= hi;) {   // last problem with tile_off[g] <= T
+        const int mid = (lo + hi) >> 1;
+        if (bt.tile_off[mid] <= T) { g = mid; lo = mid + 1; } else hi = mid - 1;
+    }
+    const GemmDesc &d = bt.d[g];
+    const int64_t t = T - bt.tile_off[g], ks = bt.ksteps[g];
+    const int64_t tu0 = bt.unit_off[g] + t * ks;
+    const int64_t cf = sk_owner(tu0, bt), cl = sk_owner(tu0 + ks - 1, bt);
+    if (cf == cl) return;   // a whole tile, written by its CTA (uniform over the CTA)
+    const int np = (int)(cl - cf + 1);
+    for (int q = threadIdx.x; q < np && q < SK_MAXP; q += blockDim.x) s_js[q] = (unsigned char)sk_slot(cf + q, tu0, bt);
+    __syncthreads();
+    const int64_t ntn = (d.N + SK_T - 1) / SK_T;
+    const int64_t r = (t / ntn) * SK_T + e / SK_T, col = (t % ntn) * SK_T + e % SK_T;
+    if (r >= d.M || col >= d.N) return;
+    z64 v(0, 0);
+    for (int64_t cc = cf; cc <= cl; ++cc) {
+        const int q = (int)(cc - cf);
+        const int jslot = q < SK_MAXP ? s_js[q] : sk_slot(cc, tu0, bt);
+        const double2 pv = __ldcg(reinterpret_cast<const double2 *>(part) + (2 * cc + jslot) * (SK_T * SK_T) + e);
+        v += z64(pv.x, pv.y);
+    }
+    z64 *pc = C + d.c_off + r * d.ldc + col;
+    v = alpha * v;
+    if (accumulate) *pc += v;
+    else *pc = v;
 }
 
 __global__ void __launch_bounds__(256) k_gemm_sk(const __grid_constant__ SkBatch bt, int opA, int opB,
@@ -289,6 +342,10 @@ __global__ void __launch_bounds__(256) k_gemm_sk(const __grid_constant__ SkBatch
             z64 *slot = part + (2 * c + (u == u0 ? 0 : 1)) * (SK_T * SK_T);
             for (int i = 0; i < 2; ++i)
                 for (int j = 0; j < 2; ++j) slot[(ty + 16 * i) * SK_T + tx + 16 * j] = acc[i][j];
+            if (bt.defer) {   // summed by k_sk_reduce after this launch
+                u = seg_end;
+                continue;
+            }
             // the tile's CTAs are the owners of its first to its last unit
             const int64_t tu0 = bt.unit_off[g] + t * ks, tu1 = tu0 + ks;
             const int64_t cf = sk_owner(tu0, bt), cl = sk_owner(tu1 - 1, bt);
@@ -780,19 +837,29 @@ void gemm_sk(const std::vector<GemmDesc> &g, int opA, int opB, const z64 *A, con
         bt.U = bt.unit_off[bt.ng];
         if (bt.U == 0) continue;
         bt.G = (int)std::min<int64_t>(G0, bt.U);
+        // few tiles for many CTAs (a Gram of few columns over a long K): each tile is cut
+        // into ~G / tiles pieces, too many for one CTA to add; a second launch spreads
+        // the sums over many CTAs
+        const int64_t ntiles = bt.tile_off[bt.ng];
+        bt.defer = (int64_t)bt.G > 2 * ntiles ? 1 : 0;
         // partial-sum slots (two per CTA) and one arrival counter per tile, zeroed
         const size_t slot_bytes = sizeof(z64) * 2 * (size_t)bt.G * SK_T * SK_T;
-        const size_t cnt_bytes = sizeof(unsigned) * (size_t)bt.tile_off[bt.ng];
+        const size_t cnt_bytes = sizeof(unsigned) * (size_t)ntiles;
         unsigned char *scratch = nullptr;
         CBFM_CUDA(cudaMallocAsync((void **)&scratch, slot_bytes + cnt_bytes, st));
         z64 *part = reinterpret_cast<z64 *>(scratch);
         unsigned *tile_cnt = reinterpret_cast<unsigned *>(scratch + slot_bytes);
-        CBFM_CUDA(cudaMemsetAsync(tile_cnt, 0, cnt_bytes, st));
+        if (!bt.defer) CBFM_CUDA(cudaMemsetAsync(tile_cnt, 0, cnt_bytes, st));
         {
             ProfScope ps_("k_gemm_z64", st);
             ProfScope site_(g_gemm_site ? g_gemm_site : "site:other", st);
             k_gemm_sk<<<bt.G, 256, 0, st>>>(bt, opA, opB, A, B, C, part, tile_cnt, accumulate ? 1 : 0, alpha);
             launched("k_gemm_sk");
+            if (bt.defer) {
+                k_sk_reduce<<<(unsigned)(ntiles * (SK_T * SK_T / SK_RCH)), SK_RCH, 0, st>>>(bt, part, C,
+                                                                                             accumulate ? 1 : 0, alpha);
+                launched("k_sk_reduce");
+            }
         }
         CBFM_CUDA(cudaFreeAsync(scratch, st));
     }
