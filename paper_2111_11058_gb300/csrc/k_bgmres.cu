@@ -1147,9 +1147,10 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
                     upd.push_back(GemmDesc{dims[r + 1] - dims[r], pjc, d0 - k0, dims[r] * dcap + k0, dcap, k0 * p,
                                            p, dims[r] * p, p});
                 }
-                k_colnorm<<<pjc, 256, 0, st>>>((int)d2, pjc, Hn.p, p, rnorm.p);   // before the projection
+                // norms before the projection into rnorm0 (free again after the Gram-Schmidt
+                // read), read together with those after the first pass: one host wait, not two
+                k_colnorm<<<pjc, 256, 0, st>>>((int)d2, pjc, Hn.p, p, rnorm0.p);
                 launched("k_colnorm");
-                CBFM_CUDA(cudaMemcpyAsync(h_h0.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost, st));
                 for (int pass = 0; pass < 2; ++pass) {
                     GemmSite site_(pass == 0 ? "site:hess_proj1" : "site:hess_proj2");
                     gemm_grouped<double>(proj, 2, 0, Qh.p, Hn.p, tmp2.p, false, st);
@@ -1160,6 +1161,8 @@ GmresOut bgmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, 
                     if (pass == 0) {
                         k_colnorm<<<pjc, 256, 0, st>>>((int)d2, pjc, Hn.p, p, rnorm.p);
                         launched("k_colnorm");
+                        CBFM_CUDA(cudaMemcpyAsync(h_h0.data(), rnorm0.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost,
+                                                  st));
                         CBFM_CUDA(cudaMemcpyAsync(h_h1.data(), rnorm.p, sizeof(double) * pjc, cudaMemcpyDeviceToHost,
                                                   st));
                         CBFM_CUDA(cudaStreamSynchronize(st));
