@@ -398,7 +398,7 @@ std::unique_ptr<Cbf> dual_cbfs(Mesh *m, int s, const z64 *Vm, const std::vector<
     DevBuf<double> sig;
     sig.alloc((size_t)nc * s);
     CBFM_CUDA(cudaMemsetAsync(info.p, 0, sizeof(int) * nc, st));
-    jacobi_svd_batched(nc, s, X.p, Vs.p, sig.p, info.p, st);
+    jacobi_svd_batched(nc, s, X.p, Vs.p, sig.p, info.p, st, delta_svd);
     std::vector<double> hs((size_t)nc * s);
     CBFM_CUDA(cudaMemcpyAsync(hs.data(), sig.p, sizeof(double) * nc * s, cudaMemcpyDeviceToHost, st));
     CBFM_CUDA(cudaMemcpyAsync(hinfo.data(), info.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));

@@ -132,8 +132,10 @@ struct GemmSite {
 // Z and V are overwritten. Returns singular flag per system in d_info (1 = zero pivot).
 void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, const int *h_n, int s, z64 *Z, z64 *V,
                       int *d_info, cudaStream_t st);
-// One-sided Jacobi SVD of nb column-major s x s complex matrices X (overwritten by U Sigma), V out.
-void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info, cudaStream_t st);
+// One-sided Jacobi SVD of nb column-major s x s complex matrices X (overwritten by U Sigma), V out;
+// singular values below keep * sigma_1 (0: none) are not kept by the caller and need not be resolved.
+void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info, cudaStream_t st,
+                        double keep = 0.0);
 // In-place Gauss-Jordan inverse of an n x n FP64 complex matrix (row-major); info=1 on zero pivot.
 // local blocks and RWG operators of several meshes, one launch per stage (k_assembly.cu)
 // diag_cells: only triangle pairs that support RWGs of a common cell are

@@ -478,7 +478,7 @@ __device__ __forceinline__ double norm2d(double2 a) { return a.x * a.x + a.y * a
 
 __global__ void __cluster_dims__(JS_CL, 1, 1) __launch_bounds__(256)
     k_jacobi_svd(int s, z64 *__restrict__ Xall, z64 *__restrict__ Vall, double *__restrict__ sig,
-                 int *__restrict__ info, double tol) {
+                 int *__restrict__ info, double tol, double keep) {
     cg::cluster_group cl = cg::this_cluster();
     const int me = (int)cl.block_rank(), mat = blockIdx.x / JS_CL;
     z64 *X = Xall + (int64_t)mat * s * s;
@@ -501,13 +501,16 @@ __global__ void __cluster_dims__(JS_CL, 1, 1) __launch_bounds__(256)
     bool ok = true;
     int sweep = 0;
     for (; sweep < 60; ++sweep) {
-        // largest squared column norm: a pair whose coupling is below tol^2 times it is
-        // left alone.  Such a pair has both columns at the rounding level of the
-        // largest (|x_i| |x_j| <= (tol |x|max)^2 is needed unless the pair is already
-        // orthogonal), so rotating it only stirs noise; every pair above that is
-        // rotated to the relative criterion, which keeps singular values down to
-        // about tol sigma_1 accurate (a floor of tol |x|max^2 left pairs of columns
-        // near 1e-7 sigma_1 coupled and their singular values wrong at that level)
+        // largest squared column norm: a pair whose coupling is below f times it is
+        // left alone, f = max(tol^2, (1e-5 keep)^2) with keep the relative size of the
+        // smallest singular value the caller keeps.  Below tol^2 both columns are at
+        // the rounding level of the largest; below (1e-5 keep)^2 both columns are far
+        // below every kept singular value (sigma >= keep sigma_1), which such a
+        // coupling turns by at most 1e-10: rotating them would only sort directions
+        // that are discarded.  Every pair above f is rotated to the relative
+        // criterion, so the kept singular values and vectors keep full accuracy (a
+        // floor of tol |x|max^2 left pairs of columns near 1e-7 sigma_1 coupled and
+        // their singular values wrong at their own size)
         double mx = 0.0;
         for (int i = warp; i < s; i += nw) {
             double al = 0;
@@ -524,7 +527,7 @@ __global__ void __cluster_dims__(JS_CL, 1, 1) __launch_bounds__(256)
             s_big = bmax;
         }
         __syncthreads();
-        const double floor_abs = tol * tol * s_big;
+        const double floor_abs = fmax(tol * tol, 1e-10 * keep * keep) * s_big;
         for (int round = 0; round < n2 - 1 && ok; ++round) {
             for (int pr = gw; pr < n2 / 2; pr += ngw) {
                 // round-robin: position 0 fixed, others rotate
@@ -1474,11 +1477,11 @@ void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, cons
     CBFM_CUDA(cudaStreamSynchronize(st));
 }
 
-void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info, cudaStream_t st) {
+void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info, cudaStream_t st, double keep) {
     // rotation threshold: a few units of round-off in the column dot products
     {
         ProfScope ps_("k_jacobi_svd", st);
-        k_jacobi_svd<<<nb * JS_CL, 256, 0, st>>>(s, X, V, sig, d_info, 1e-15 * (s > 8 ? s : 8));
+        k_jacobi_svd<<<nb * JS_CL, 256, 0, st>>>(s, X, V, sig, d_info, 1e-15 * (s > 8 ? s : 8), keep);
         launched("k_jacobi_svd");
     }
 }
