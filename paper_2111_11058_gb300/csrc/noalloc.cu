@@ -44,7 +44,6 @@ __global__ void k_c32_to_z64_scratch(const c32 *__restrict__ src, z64 *__restric
 
 }  // namespace
 
-// Body of cbfm_red_export_noalloc; the C entry point lives in api.cu.
 // Loads this file's module (and its scratch array) on the current device; run
 // once per device by the library's first API call there.  Errors are left to
 // the export itself to report.
