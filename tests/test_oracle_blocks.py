@@ -5,7 +5,9 @@
 * near pairs: singularity extraction against direct high-order integration of
   the unsplit kernel over the trial triangle at the same seven test points
   (same outer rule, same symmetrisation), which isolates the analytic parts;
-* self pair: the K block vanishes on a flat triangle.
+* self pair: the K block vanishes on a flat triangle;
+* exchange: L(s, t) = L(t, s)^T for K and T, far and near pairs, lossless
+  and lossy wavenumbers.
 """
 import math
 
@@ -181,3 +183,31 @@ def test_near_block_singular_extraction(sphere, k, kind):
     assert np.abs(To - Tx).max() < 2e-3 * np.abs(Tx).max()
     if kind != "self":
         assert np.abs(Ko - Kx).max() < 2e-3 * np.abs(Kx).max()
+
+
+@pytest.mark.parametrize("k", [K_EXT, K_INT, 2 * math.pi * complex(np.sqrt(3.0 - 0.1j))])
+def test_blocks_transpose_under_exchange(sphere, k):
+    """Exchanging test and trial triangle transposes a local block,
+    L(s, t) = L(t, s)^T, for K and for T: G and |r - r'| are symmetric and the
+    triple product f_a . ((r - r') x f_b') keeps its value when r <-> r' and
+    a <-> b.  The discrete blocks keep it because both triangles use the same
+    7-point rule (far pairs, each ordered pair evaluated on its own here) and
+    because near blocks are symmetrised; the GPU path evaluates each unordered
+    pair once on the strength of it."""
+    m = sphere
+    c = m.verts[m.tris].mean(axis=1)
+    t = 3
+    dist = np.linalg.norm(c - c[t], axis=1)
+    order = np.argsort(dist)
+    tv = set(m.tris[t].tolist())
+    edge = next(q for q in range(m.nt) if q != t and len(tv & set(m.tris[q].tolist())) == 2)
+    pairs = [(t, edge), (t, int(order[20])), (t, int(order[60])), (int(order[5]), int(np.argmax(dist)))]
+    kinds = set()
+    for (a, b) in pairs:
+        K1, T1, n1 = mom.local_block(m, k, a, b)
+        K2, T2, n2 = mom.local_block(m, k, b, a)
+        assert n1 == n2
+        kinds.add(n1)
+        assert np.abs(K1 - K2.T).max() <= 1e-12 * np.abs(K1).max()
+        assert np.abs(T1 - T2.T).max() <= 1e-12 * np.abs(T1).max()
+    assert kinds == {True, False}   # near and far pairs both covered
