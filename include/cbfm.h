@@ -317,6 +317,21 @@ cbfm_status cbfm_cmp_setup_inexact(cbfm_red_t red, double inner_tol, int32_t inn
                                    void *stream);
 
 /*
+ * cbfm_wait_selftest -- a testing hook for the bounded device waits (the paper
+ * has no counterpart).  Every wait of the library's kernels on other CTAs (the
+ * grid barrier of the persistent Gauss-Jordan kernels, the cluster barriers of
+ * the Cholesky and Jacobi kernels) gives up after a time limit, sets an error
+ * word and lets the kernel end, so the call returns CBFM_ETIMEOUT and the
+ * device stays usable.  kind 0: a grid barrier awaited by 4 CTAs for 5
+ * arrivals (its fixed limit, one second, expires); kind 1: a cluster barrier
+ * of 2 CTAs initialised for 3 arrivals (expires after limit_s); kind 2: the
+ * same barrier for 2 arrivals (completes).  limit_s in (0, 1].  Returns
+ * CBFM_ETIMEOUT when the wait expired, CBFM_OK when it completed, CBFM_EINVAL
+ * on bad arguments.
+ */
+cbfm_status cbfm_wait_selftest(int32_t kind, double limit_s, void *stream);
+
+/*
  * cbfm_gram_inverse -- the inverse routine of cbfm_cmp_setup applied to
  * caller matrices: a testing hook for both of its paths (the paper has no
  * counterpart).  A: nbatch complex128 row-major n x n matrices, consecutive,

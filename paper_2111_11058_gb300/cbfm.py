@@ -75,6 +75,7 @@ def lib():
             "cbfm_cmp_setup_inexact": [_vp, _f64, _i32, _i32, _vp],
             "cbfm_gram_export": [_vp, _vp, _vp],
             "cbfm_gram_inverse": [_vp, _i64, _i32, _vp, _vp],
+            "cbfm_wait_selftest": [_i32, _f64, _vp],
             "cbfm_solve": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _vp],
             "cbfm_session_create": [_vp, _vp, _i32, _f64, _i32, _i32, _i32, _vp],
             "cbfm_session_join": [_vp, _vp, _i32, _vp],
@@ -105,9 +106,9 @@ def exported_symbols():
     """Names of the C entry points declared in include/cbfm.h."""
     return ["cbfm_mesh", "cbfm_mesh_edges", "cbfm_mesh_info", "cbfm_mesh_cells", "cbfm_build_cbfs", "cbfm_cbf_import",
             "cbfm_cbf_export", "cbfm_assemble_reduced", "cbfm_assemble_reduced_batch", "cbfm_assemble_mom", "cbfm_tdiag_setup", "cbfm_build_ipcbfs", "cbfm_tuning", "cbfm_red_export", "cbfm_red_export_noalloc", "cbfm_cmp_setup", "cbfm_cmp_setup_inexact", "cbfm_gram_export",
-            "cbfm_gram_inverse", "cbfm_solve", "cbfm_session_create", "cbfm_session_join", "cbfm_session_run",
-            "cbfm_session_results", "cbfm_free", "cbfm_last_error", "cbfm_launch_count", "cbfm_profile",
-            "cbfm_profile_read"]
+            "cbfm_gram_inverse", "cbfm_wait_selftest", "cbfm_solve", "cbfm_session_create", "cbfm_session_join",
+            "cbfm_session_run", "cbfm_session_results", "cbfm_free", "cbfm_last_error", "cbfm_launch_count",
+            "cbfm_profile", "cbfm_profile_read"]
 
 
 def _check(st: int):
@@ -152,6 +153,15 @@ def gram_inverse(A, stream=None) -> np.ndarray:
     _check(lib().cbfm_gram_inverse(ctypes.c_void_p(A.ctypes.data), n, nb, ctypes.c_void_p(out.ctypes.data),
                                    _stream(stream)))
     return out
+
+
+WAIT_GRID_EXPIRES, WAIT_CLUSTER_EXPIRES, WAIT_CLUSTER_COMPLETES = 0, 1, 2
+
+
+def wait_selftest(kind: int, limit_s: float = 0.05, stream=None) -> None:
+    """cbfm_wait_selftest: a bounded device wait that runs out (kinds 0, 1:
+    raises CbfmError with CBFM_ETIMEOUT) or completes (kind 2); testing hook."""
+    _check(lib().cbfm_wait_selftest(int(kind), float(limit_s), _stream(stream)))
 
 
 def launch_count() -> int:

@@ -1358,6 +1358,17 @@ cbfm_status cbfm_cmp_setup_inexact(cbfm_red_t red, double inner_tol, int32_t inn
     });
 }
 
+cbfm_status cbfm_wait_selftest(int32_t kind, double limit_s, void *stream) {
+    return guarded([&] {
+        StreamScope ss_((cudaStream_t)stream);
+        CBFM_REQUIRE(kind >= 0 && kind <= 2, "kind must be 0, 1 or 2");
+        CBFM_REQUIRE(limit_s > 0.0 && limit_s <= 1.0, "limit_s must be in (0, 1]");
+        if (wait_selftest(kind, limit_s, (cudaStream_t)stream))
+            throw Fail{CBFM_ETIMEOUT, kind == 0 ? "self-test: the grid barrier wait expired"
+                                                : "self-test: a cluster barrier wait expired"};
+    });
+}
+
 cbfm_status cbfm_gram_inverse(const double *A, int64_t n, int32_t nbatch, double *Ainv, void *stream) {
     return guarded([&] {
         StreamScope ss_((cudaStream_t)stream);   // scratch is stream-ordered on the caller's stream

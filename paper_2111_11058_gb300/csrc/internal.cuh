@@ -132,6 +132,8 @@ struct GemmSite {
 // Z and V are overwritten. Returns singular flag per system in d_info (1 = zero pivot).
 void lu_solve_batched(int nb, const int64_t *h_zoff, const int64_t *h_voff, const int *h_n, int s, z64 *Z, z64 *V,
                       int *d_info, cudaStream_t st);
+// Bounded-wait self-test (cbfm_wait_selftest); true when a wait expired.
+bool wait_selftest(int kind, double limit_s, cudaStream_t st);
 // One-sided Jacobi SVD of nb column-major s x s complex matrices X (overwritten by U Sigma), V out;
 // singular values below keep * sigma_1 (0: none) are not kept by the caller and need not be resolved.
 void jacobi_svd_batched(int nb, int s, z64 *X, z64 *V, double *sig, int *d_info, cudaStream_t st,

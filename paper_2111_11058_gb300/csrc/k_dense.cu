@@ -1219,6 +1219,38 @@ __global__ void __launch_bounds__(256, 2) k_gjb_persistent(int n, int nbatch, z6
     }
 }
 
+// ------------------------------------------------ bounded waits, self-test
+// Grid barrier of the persistent kernels waited on for `target` arrivals by
+// gridDim.x CTAs: with target > gridDim.x nothing completes it, every CTA
+// gives up after the barrier's one-second limit and sets *err.
+__global__ void k_wait_grid_selftest(unsigned target, unsigned *__restrict__ bar, int *__restrict__ err) {
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    unsigned g = 0;
+    gj_grid_sync(bar, bar + 1, target, g, &s_abort, err);
+}
+
+// Cluster mbarriers initialised for `expect` arrivals per phase, arrived at by
+// the cluster's CTAs: with expect > cluster size the phase never completes and
+// each CTA's wait gives up after limit_ns (sets *err); with expect equal to it
+// the barrier completes.  The closing hardware cluster barrier is reached by
+// every CTA either way.
+__global__ void __cluster_dims__(2, 1, 1) k_wait_cluster_selftest(int expect, unsigned long long limit_ns,
+                                                                 int *__restrict__ err) {
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ uint64_t cbar[2];
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        cl_bar_init(cbar, expect);
+    }
+    __syncthreads();
+    cl.sync();
+    cl_sync(cbar, 0, (int)cl.num_blocks(), &s_abort, err, limit_ns);
+    cl.sync();
+}
+
 // row block k of A <- Rwp (b x n); then A_kk <- D
 __global__ void k_gjb_place(int n, int k0, int b, const z64 *__restrict__ Rwp, const z64 *__restrict__ D,
                             z64 *__restrict__ A) {
@@ -1567,6 +1599,30 @@ void launch_c32_to_z64(const c32 *src, z64 *dst, int64_t n, cudaStream_t st) {
         k_to64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dst, n);
         launched("k_to64");
     }
+}
+
+// Bounded-wait self-test (see cbfm_wait_selftest): kind 0 grid barrier never
+// completed, 1 cluster barrier never completed, 2 cluster barrier completed.
+// Returns whether a wait expired.
+bool wait_selftest(int kind, double limit_s, cudaStream_t st) {
+    DevBuf<unsigned> bar;
+    DevBuf<int> err;
+    bar.alloc(2);
+    err.alloc(1);
+    CBFM_CUDA(cudaMemsetAsync(bar.p, 0, 2 * sizeof(unsigned), st));
+    CBFM_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    if (kind == 0) {
+        k_wait_grid_selftest<<<4, 32, 0, st>>>(5u, bar.p, err.p);   // 4 CTAs, 5 arrivals awaited
+        launched("k_wait_grid_selftest");
+    } else {
+        const unsigned long long ns = (unsigned long long)(limit_s * 1e9);
+        k_wait_cluster_selftest<<<2, 32, 0, st>>>(kind == 1 ? 3 : 2, ns, err.p);
+        launched("k_wait_cluster_selftest");
+    }
+    int h = 0;
+    CBFM_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CBFM_CUDA(cudaStreamSynchronize(st));
+    return h != 0;
 }
 
 }  // namespace cbfm
