@@ -412,14 +412,18 @@ GmresOut gmres_solve(Red &rd, const z64 *d_b, int nrhs, double tol, int maxit, i
     flag.alloc(nrhs);
     ones.alloc(nrhs);
     nact.alloc(m + 1);
-    int *h_nact = nullptr;
-    CBFM_CUDA(cudaMallocHost((void **)&h_nact, sizeof(int)));
-    struct PinnedFree {
-        int *p;
-        ~PinnedFree() {
+    // the polled active count lands in a pinned word kept per host thread (one API call at a
+    // time per thread), so a solve -- and every inner solve of the inexact CMP -- does no
+    // host allocation and no cudaFreeHost
+    struct PinnedWord {
+        int *p = nullptr;
+        ~PinnedWord() {
             if (p) cudaFreeHost(p);
         }
-    } pf{h_nact};
+    };
+    static thread_local PinnedWord t_nact;
+    if (t_nact.p == nullptr) CBFM_CUDA(cudaMallocHost((void **)&t_nact.p, sizeof(int)));
+    int *h_nact = t_nact.p;
     CBFM_CUDA(cudaMemsetAsync(y.p, 0, sizeof(z64) * nrhs * n, st));
     CBFM_CUDA(cudaMemsetAsync(H.p, 0, sizeof(z64) * nrhs * (m + 1) * m, st));
     CBFM_CUDA(cudaMemsetAsync(done.p, 0, sizeof(int) * nrhs, st));
